@@ -1,0 +1,355 @@
+"""Benchmark: N=25600 complex R-matrix solve, FP32+IR vs FP64, on GB300.
+
+One step = the whole hot path on one coupled-channel system already resident
+in HBM: assemble C and Phi (G1), blocked LU (G2-G4), triangular solves with
+FP64 structured-residual refinement until the residual stagnates (G6-G8), then
+R and U (G9-G10).  Default workload: nch=256 x nlag=100 (N=25600), 256
+right-hand sides, E=10 MeV, seed 11592 (the FP32+IR configuration); the
+complex128 path on the same system is timed once beside it and the two U's
+compared.  The matrix (5.2 GB complex64 / 10.5 GB complex128) is far larger
+than L2, so no flush is needed between steps.
+
+  value     algorithmic TFLOP/s of the FP32+IR step: (8/3 N^3 + 8 N^2 nrhs) / t
+  e2e       same, through the C ABI from pinned host buffers: V host->device,
+            full step, R and U device->host, all inside the timed region
+  roofline  the trailing-update kernel: algorithmic flops of its launches over
+            their CUDA-event time, against the tensor peak it runs on
+  cpu_baseline  the CPU oracle on a bounded sample (N=1600 of the same family)
+
+--impl reference times the CPU oracle (the reference arm of this build).
+Multi-GPU (torchrun): every rank solves its own system (replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+TF32_PER_BF16 = 0.5          # nominal dense tf32 : bf16 tensor rate on GB300 (1.1 : 2.25 PF)
+
+
+def peaks():
+    try:
+        with open(MEASURED) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+def lu_flops(N, nrhs):
+    return 8.0 / 3.0 * N ** 3 + 8.0 * N ** 2 * nrhs
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.index, self.samples, self.proc = index, [], None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if "Active" in s[3 + k]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+def workload(args):
+    import cc_problems as cp
+    if args.small:
+        return cp.config3(16), "config3 nch=16 nlag=100 N=1600 E=10 MeV seed 11592"
+    return cp.config3(256), "config3 nch=256 nlag=100 N=25600 E=10 MeV seed 11592"
+
+
+class Runner:
+    """One system on one GPU through the C ABI (device-resident buffers)."""
+
+    def __init__(self, p, precision, device):
+        import torch
+
+        import cc_problems as cp
+        import paper_2512_11590_gb300 as g
+        self.g, self.p, self.torch = g, p, torch
+        self.stream = torch.cuda.current_stream()
+        self.ctx = g.rmat_create(device, self.stream.cuda_stream)
+        m = g.rmat_mesh(p.nlag, p.a)
+        self.V_host = cp.potential_at(p, m["r"]).ravel()
+        self.Vd = torch.from_numpy(self.V_host).cuda()
+        self.prob, self._keep = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh,
+                                                      precision)
+        self.precision = precision
+        self.nopen = int(np.sum(p.E - p.thresh > 0))
+        self.X = torch.zeros((p.nch, p.N), dtype=torch.complex128, device="cuda")
+        self.R = torch.zeros(p.nch * p.nch, dtype=torch.complex128, device="cuda")
+        self.U = torch.zeros(max(1, self.nopen) ** 2, dtype=torch.complex128, device="cuda")
+        self.last = None
+
+    def step(self, Vptr=None):
+        g, p = self.g, self.p
+        g.rmat_assemble(self.ctx, self.prob, p.E, Vptr or self.Vd.data_ptr())
+        g.rmat_factor(self.ctx, want_info=False)
+        st, it, rel = g.rmat_solve(self.ctx, self.X.data_ptr(), p.N, max_refine=30, tol=1e-13)
+        g.rmat_collision(self.ctx, self.R.data_ptr(), self.U.data_ptr())
+        self.last = {"status": st, "iters": it, "rel_resid": rel}
+
+    def U_host(self):
+        n = self.nopen
+        return self.U.cpu().numpy()[:n * n].reshape(n, n).T
+
+    def close(self):
+        self.g.rmat_destroy(self.ctx)
+
+
+def time_steps(runner, K, W, sync_all):
+    torch = runner.torch
+    g = runner.g
+    for _ in range(W):
+        runner.step()
+    g.rmat_set_param(runner.ctx, g.RMAT_PARAM_TIMING, 1)
+    runner.step()                               # one timed-instrumented step for the roofline
+    torch.cuda.synchronize()
+    g.rmat_reset_counters(runner.ctx)
+    runner.step()
+    torch.cuda.synchronize()
+    stats = g.rmat_get_stats(runner.ctx)
+    g.rmat_set_param(runner.ctx, g.RMAT_PARAM_TIMING, 0)
+    g.rmat_reset_counters(runner.ctx)
+    sync_all()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(runner.stream)
+    for _ in range(K):
+        runner.step()
+    e1.record(runner.stream)
+    torch.cuda.synchronize()
+    sync_all()
+    launches = g.rmat_get_stats(runner.ctx)["launches"]
+    return e0.elapsed_time(e1) / K, stats, launches
+
+
+def time_e2e(runner, K):
+    """Same step from pinned host buffers: V H2D + step + R, U D2H, per step."""
+    torch = runner.torch
+    Vh = torch.from_numpy(runner.V_host).pin_memory()
+    Rh = torch.empty(runner.R.numel(), dtype=torch.complex128).pin_memory()
+    Uh = torch.empty(runner.U.numel(), dtype=torch.complex128).pin_memory()
+    Vd = torch.empty_like(runner.Vd)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(runner.stream)
+    for _ in range(K):
+        Vd.copy_(Vh, non_blocking=True)
+        runner.step(Vd.data_ptr())
+        Rh.copy_(runner.R, non_blocking=True)
+        Uh.copy_(runner.U, non_blocking=True)
+    e1.record(runner.stream)
+    torch.cuda.synchronize()
+    h2d = Vh.numel() * 16
+    d2h = (Rh.numel() + Uh.numel()) * 16
+    return e0.elapsed_time(e1) / K, h2d, d2h
+
+
+def cpu_baseline(budget_s=20.0):
+    """The CPU oracle (as it stands) on N=1600 systems of the same family."""
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    import cc_problems as cp
+    from oracle import oracle_solve
+    p = cp.config3(16)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle_solve(p, refine_steps=3)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 3:
+            break
+    dt = (time.perf_counter() - t0) / n
+    return {"value": lu_flops(p.N, p.nch) / dt / 1e12, "unit": "TFLOP/s", "cores": 1,
+            "kind": "oracle", "sample": f"{n} oracle solve(s) of config3 nch=16 nlag=100 "
+            f"(N=1600, 16 rhs): LU + 3 double-double refinement steps + R + U; "
+            f"{dt:.2f} s each"}
+
+
+def reference_main(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    _, desc = workload(args)
+    import cc_problems as cp
+    from oracle import oracle_solve
+    p = cp.config3(16)
+    for _ in range(args.warmup):
+        oracle_solve(p, refine_steps=3)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_solve(p, refine_steps=3)
+    dt = (time.perf_counter() - t0) / args.steps
+    val = lu_flops(p.N, p.nch) / dt / 1e12
+    line = {"impl": "reference", "metric": "N=25600 complex solve time & TFLOP/s: FP32+IR vs FP64 "
+            "at equal U error", "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "sample": "config3 nch=16 nlag=100 N=1600"},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step one oracle solve of config3 nch=16 nlag=100 (N=1600)"},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "simt"])
+    ap.add_argument("--small", action="store_true", help="N=1600 instead of N=25600")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the complex128 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warmup must be >= 3", file=sys.stderr)
+        return 2
+    if args.impl == "reference":
+        return reference_main(args)
+
+    import torch
+    import paper_2512_11590_gb300 as g
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    p, desc = workload(args)
+    prec = g.RMAT_C64_3XTF32_IR if args.precision == "tf32" else g.RMAT_C64_SIMT_IR
+    run = Runner(p, prec, local)
+    with ClockSampler(local) as clk:
+        ms, stats, launches = time_steps(run, args.steps, args.warmup, sync_all)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    flops = lu_flops(p.N, p.nch)
+    value = world * flops / (ms * 1e-3) / 1e12
+    e2e_ms, h2d, d2h = time_e2e(run, max(1, min(args.steps, 3)))
+    U32 = run.U_host()
+    ir = dict(run.last)
+    run.close()
+
+    fp64 = None
+    if not args.no_fp64:
+        r64 = Runner(p, g.RMAT_C128, local)
+        r64.step()                                  # warm-up (module load, buffers)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(r64.stream)
+        r64.step()
+        e1.record(r64.stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        U64 = r64.U_host()
+        fp64 = {"ms_per_step": ms64, "tflops": flops / (ms64 * 1e-3) / 1e12,
+                "refine": dict(r64.last),
+                "u_rel_diff_fp32ir_vs_fp64": float(np.max(np.abs(U32 - U64)) / np.max(np.abs(U64))),
+                "speedup_fp32ir_over_fp64": ms64 / ms}
+        r64.close()
+
+    pk, src = peaks()
+    tu_ms, tu_flops, tu_n = stats["tu_ms"], stats["tu_flops"], stats["tu_launches"]
+    if prec == g.RMAT_C64_3XTF32_IR:
+        # each complex product = 4 real GEMMs x 3 tf32 split products: 12 tensor GEMMs
+        peak = pk["bf16_tflops_sustained"] * TF32_PER_BF16 / 3.0
+        bound, unit, pname = "tensor", "TFLOP/s", ("bf16 sustained (%s) x 0.5 (tf32/bf16 nominal) / 3 "
+                                                    "(tf32 split products per fp32 product)" % src)
+    else:
+        peak = 152 * 128 * 2 * 2070e6 / 1e12
+        bound, unit, pname = "alu", "TFLOP/s", "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"
+    achieved = tu_flops / (tu_ms * 1e-3) / 1e12 if tu_ms and tu_ms > 0 else None
+    line = {
+        "metric": "N=25600 complex solve time & TFLOP/s: FP32+IR vs FP64 at equal U error",
+        "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+3xtf32 factor / f64 refinement" if prec == 1 else "c64 simt / f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "precision": args.precision, "nrhs": p.nch,
+                   "refinement": ir, "l2": "inputs larger than L2 (C is %.1f GB)" % (p.N * p.N * 8 / 1e9),
+                   "lu_block": stats["nb"], "panel_ctas": stats["panel_ctas"],
+                   "stage_ms": {k: stats[k] for k in ("assemble_ms", "factor_ms", "solve_ms",
+                                                       "refine_ms", "collision_ms")}},
+        "fp64_path": fp64,
+        "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "trailing update C22 -= L21 U12", "bound": bound,
+                     "achieved": achieved, "peak": peak, "peak_source": pname, "unit": unit,
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "launches": tu_n, "kernel_ms_per_step": tu_ms,
+                     "share_of_step": (tu_ms / ms) if tu_ms and tu_ms > 0 else None},
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        if world == 1 and not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

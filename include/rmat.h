@@ -1,0 +1,195 @@
+/*
+ * rmat.h -- C ABI of the GB300 (sm_103a) Lagrange-Legendre R-matrix library.
+ *
+ * The library implements the hot path of the R-matrix method as described in
+ * J. Lei, "HPRMAT: A high-performance R-matrix solver with GPU acceleration
+ * for coupled-channel problems in nuclear physics" (arXiv 2512.11590):
+ *
+ *   rmat_mesh       Gauss-Legendre mesh on (0,a) and basis values at a (Sec. 2)
+ *   rmat_assemble   C = T + L(B) + V - E*I, Eq. (block_structure), and the
+ *                   surface right-hand sides of Sec. 3.1 step 2, on the device
+ *   rmat_factor     blocked right-looking LU with partial pivoting, M = P L U
+ *                   (Sec. 3.1), in complex128 or complex64 (Sec. 3.2, 3.4)
+ *   rmat_solve      forward/backward substitution for all nch right-hand sides
+ *                   plus iterative refinement with an FP64 residual r = b - M x
+ *                   (Sec. 3.2; Sec. 3.4 step 7, here on the device)
+ *   rmat_collision  R-matrix contraction (Sec. 3.1 step 4) and the collision
+ *                   matrix U from matching at a (Sec. 1; Sec. 4.1)
+ *   rmat_load_dense a general dense system M X = B, the analogue of the
+ *                   paper's gpu_solve_mixed_(A, B, n, nrhs, ...) entry (Sec. 4.3)
+ *
+ * Conventions (all entry points):
+ *   - Return 0 (RMAT_OK) on success; -i when argument i (1-based) is invalid;
+ *     other negative values for CUDA / memory / state errors; positive values
+ *     for numerical outcomes (exactly singular pivot, refinement stagnation).
+ *   - Device pointers are plain CUDA device addresses owned by the caller; the
+ *     library never frees them.  Host pointers are owned by the caller too.
+ *   - Complex numbers are interleaved (re, im) pairs: complex128 = 2 doubles.
+ *   - Matrices exchanged with the caller are column-major ("Fortran order"),
+ *     the paper's layout (Sec. 3.4, Sec. 4.4).
+ *   - Work is enqueued on the stream given to rmat_create, in call order.
+ *     rmat_factor returns without waiting unless info is requested;
+ *     rmat_solve synchronises once per refinement step (its stopping rule is
+ *     decided on the host); rmat_collision synchronises before returning.
+ *   - There is no CPU fallback: without a usable sm_103 device every entry
+ *     point that needs one returns RMAT_ENODEV or RMAT_ECUDA.
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef RMAT_H_
+#define RMAT_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define RMAT_OK            0
+#define RMAT_ECUDA      (-100)  /* a CUDA runtime/driver call failed            */
+#define RMAT_ENOMEM     (-101)  /* device memory for the workspace not available */
+#define RMAT_ESTATE     (-102)  /* call out of order (e.g. solve before factor)  */
+#define RMAT_ETIMEOUT   (-103)  /* a bounded device-side wait gave up            */
+#define RMAT_ENODEV     (-104)  /* no CUDA device of compute capability 10.3     */
+#define RMAT_ESINGULAR     1    /* exactly zero pivot; info holds its column     */
+#define RMAT_ENOCONV       2    /* refinement stagnated above the tolerance      */
+
+/* ---- precisions --------------------------------------------------------- */
+/* complex128 matrix, FP64 LU (panel, TRSM and trailing update on FP64 units). */
+#define RMAT_C128            0
+/* complex64 matrix and LU; trailing updates on tcgen05 tensor cores as three
+ * TF32 products of a hi/lo split (~FP32 accuracy); FP64 residual refinement. */
+#define RMAT_C64_3XTF32_IR   1
+/* complex64 matrix and LU with FP32 CUDA-core trailing updates; FP64 refinement. */
+#define RMAT_C64_SIMT_IR     2
+
+/* ---- tunable parameters (rmat_set_param) -------------------------------- */
+#define RMAT_PARAM_NB          1  /* LU block width (multiple of 32; 0 = tuned) */
+#define RMAT_PARAM_PANEL_CTAS  2  /* CTAs of the cooperative panel (0 = auto)   */
+#define RMAT_PARAM_SPIN_LIMIT  3  /* polls before a device wait gives up        */
+#define RMAT_PARAM_TIMING      4  /* 1 = record per-stage CUDA events           */
+
+typedef struct rmat_ctx_s* rmat_ctx;
+
+/* One coupled-channel problem (Eq. cc_schrodinger of Sec. 2).  N = nch*nlag.
+ * Energies are in MeV, lengths in fm, hm = hbar^2/(2 mu) in MeV fm^2.  The
+ * unknowns are ordered channel-major: index (alpha, i) -> alpha*nlag + i, the
+ * (alpha-1)*nlag + i of the paper's R-matrix formula (Sec. 3.1), 0-based. */
+typedef struct {
+  int nch;               /* channels, >= 1                                     */
+  int nlag;              /* Lagrange-Legendre points per channel, 1..1024      */
+  double a;              /* channel radius (fm), > 0                           */
+  double hm;             /* hbar^2 / 2mu (MeV fm^2), > 0                       */
+  double bloch_B;        /* Bloch boundary constant B of L(B) (0 in the paper) */
+  const int* l;          /* host [nch]: orbital momentum of each channel, >= 0 */
+  const double* thresh;  /* host [nch]: channel threshold energies (MeV)       */
+  int precision;         /* RMAT_C128, RMAT_C64_3XTF32_IR or RMAT_C64_SIMT_IR  */
+} rmat_problem;
+
+/* Create a context bound to CUDA device `device` and stream `stream` (a
+ * cudaStream_t; NULL = legacy default stream).  The context owns all device
+ * workspace (matrix, factors, pivots, refinement buffers), allocated lazily by
+ * rmat_assemble/rmat_load_dense and reused while sizes do not grow, the
+ * persistent-buffer pattern of the paper's Sec. 3.4 step 1.
+ * Errors: -1 ctx NULL; RMAT_ENODEV when the device is not compute
+ * capability 10.3; RMAT_ECUDA for other CUDA failures. */
+int rmat_create(rmat_ctx* ctx, int device, void* stream);
+
+/* Release the context and its workspace (synchronises its stream). NULL is a no-op. */
+int rmat_destroy(rmat_ctx ctx);
+
+/* Set a tunable parameter (RMAT_PARAM_*).  Takes effect at the next call. */
+int rmat_set_param(rmat_ctx ctx, int key, long long value);
+
+/* Lagrange-Legendre mesh of Sec. 2, computed on the HOST in IEEE double:
+ *   x[i]   zeros of P_nlag(2x-1) on (0,1), ascending, correctly rounded
+ *   omx[i] 1 - x[i], correctly rounded
+ *   lam[i] Gauss weights on (0,1) (the paper's lambda_i on (0,a) is a*lam[i])
+ *   r[i]   a*x[i]
+ *   f_a[i] f_i(a) = (-1)^(nlag+i+1) / sqrt(a x_i (1-x_i)) (i 0-based): the
+ *          boundary values q2(r_i) of Sec. 3.1 step 2
+ *   T0     [nlag*nlag] kinetic+Bloch matrix int_0^a f_i' f_j' dr in fm^-2,
+ *          symmetric (Baye's regularised Lagrange-Legendre closed forms)
+ * Any output pointer may be NULL.  Needs no GPU.  Errors: -1 nlag out of
+ * 1..1024, -2 a <= 0. */
+int rmat_mesh(int nlag, double a, double* x, double* omx, double* lam, double* r,
+              double* f_a, double* T0);
+
+/* Assemble the internal-region matrix and right-hand sides on the device:
+ *   C[(al,i),(al,j)]  = hm*T0[i][j] - hm*(B/a) f_i(a) f_j(a)
+ *                       + delta_ij (hm l_al(l_al+1)/r_i^2 + V_alal(r_i) + E_al - E)
+ *   C[(al,i),(al',i)] = V_al al'(r_i), al != al';  all other entries 0
+ *   Phi[(al,i), be]   = delta_{al be} f_i(a)            (nch right-hand sides)
+ * V_dev: device complex128 array cpot(nlag, nch, nch) in Fortran order, i.e.
+ *   V_dev[i + nlag*(al + nch*al')] = V_{al al'}(r_i) in MeV, r_i = rmat_mesh's r,
+ *   symmetric in (al, al').  Read during this call only.
+ * C is stored in the precision's element type; the potential, thresholds and
+ * mesh tables are kept for the FP64 residual.  Asynchronous.
+ * Errors: -1 ctx, -2 problem fields invalid, -3 E not finite, -4 V_dev NULL,
+ * RMAT_ENOMEM when N x N does not fit next to the free device memory. */
+int rmat_assemble(rmat_ctx ctx, const rmat_problem* prob, double E, const void* V_dev);
+
+/* Load a general dense system (no R-matrix structure): A_dev complex128 n x n
+ * column-major with leading dimension lda >= n, B_dev complex128 n x nrhs
+ * column-major with ldb >= n.  Both are copied into the context (converted to
+ * the precision's element type); refinement then uses a dense FP64 residual
+ * b - A x from the stored complex128 copy of A.  Asynchronous.
+ * Errors: -1 ctx, -2 n < 1, -3 nrhs < 1, -4 A_dev, -5 lda, -6 B_dev, -7 ldb,
+ * -8 precision; RMAT_ENOMEM. */
+int rmat_load_dense(rmat_ctx ctx, int n, int nrhs, const void* A_dev, int lda,
+                    const void* B_dev, int ldb, int precision);
+
+/* Factor the assembled/loaded matrix in place: blocked right-looking LU with
+ * partial pivoting (pivot = largest |Re|+|Im| in the column, first row on
+ * ties).  If info != NULL the call synchronises and stores 0, or k > 0 (1-based
+ * column) for the first exactly zero pivot, returning RMAT_ESINGULAR; with
+ * info == NULL it returns after enqueueing.
+ * Errors: -1 ctx, RMAT_ESTATE (nothing assembled), RMAT_ETIMEOUT, RMAT_ECUDA. */
+int rmat_factor(rmat_ctx ctx, int* info);
+
+/* Solve C X = Phi (or A X = B) with the factors, then refine:
+ *   loop: r = Phi - C X in FP64 (structured for assembled problems, dense for
+ *   loaded ones); stop when max|r|/max|Phi| < tol, when the ratio fails to
+ *   drop below 0.5x the previous one twice in a row (stagnation), or after
+ *   max_refine steps; else solve C d = r with the factors and X += d (FP64).
+ * X_dev: device complex128 N x nrhs column-major, ldx >= N (caller-owned).
+ * iters (may be NULL): refinement steps taken.  rel_resid (may be NULL): the
+ * last max|r|/max|Phi| measured (0 when max_refine == 0 and tol <= 0, in
+ * which case no residual is formed).  Returns RMAT_ENOCONV when refinement
+ * stopped by stagnation or step count above tol (X is still the best
+ * iterate), RMAT_ESINGULAR after a zero pivot.
+ * Errors: -1 ctx, -2 X_dev, -3 ldx, -4 max_refine < 0, RMAT_ESTATE. */
+int rmat_solve(rmat_ctx ctx, void* X_dev, int ldx, int max_refine, double tol,
+               int* iters, double* rel_resid);
+
+/* R-matrix and collision matrix of the last solved assembled problem.
+ *   R[al][be] = (hm/a) sum_i f_i(a) X[(al,i), be]    (dimensionless, nch x nch)
+ *   k_c = sqrt(|E - E_c| / hm), rho_c = k_c a; open channels (E > E_c):
+ *   I = G - iF, O = G + iF with Riccati-Bessel F_l = rho j_l, G_l = -rho y_l
+ *   (eta = 0); closed: O = e^-rho sum_k (l+k)!/(k!(l-k)!) (2 rho)^-k, I = 0;
+ *   O' -> O' - (B/rho) O, I' -> I' - (B/rho) I;  R~ = a sqrt(k) R sqrt(k);
+ *   U = (diag O - R~ diag O')^-1 (diag I - R~ diag I'), open x open block.
+ * R_dev: device complex128 nch x nch column-major (may be NULL).
+ * U_dev: device complex128 nopen x nopen column-major, open channels in
+ * channel order (may be NULL).  nopen: host int (may be NULL).
+ * Synchronises.  Errors: -1 ctx, RMAT_ESTATE (no solved assembled problem),
+ * RMAT_ESINGULAR (the matching matrix is singular). */
+int rmat_collision(rmat_ctx ctx, void* R_dev, void* U_dev, int* nopen);
+
+/* Counters and timers of the last factor/solve, for benchmarks:
+ *   out[0] N, out[1] nrhs, out[2] LU block width, out[3] panel CTAs,
+ *   out[4] kernel launches enqueued since the last rmat_reset_counters,
+ *   out[5] trailing-update launches, out[6] trailing-update time (ms, events),
+ *   out[7] trailing-update algorithmic flops (8 M N K per launch),
+ *   out[8] assemble ms, out[9] factor ms, out[10] first solve ms,
+ *   out[11] refinement ms, out[12] collision ms  (timers need RMAT_PARAM_TIMING=1;
+ *   a stage's time is -1 when it was not timed).
+ * n: capacity of out; returns the number of values written (<= 13). */
+int rmat_get_stats(rmat_ctx ctx, double* out, int n);
+int rmat_reset_counters(rmat_ctx ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char* rmat_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RMAT_H_ */

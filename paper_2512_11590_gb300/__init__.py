@@ -1,0 +1,188 @@
+"""Thin Python binding of the GB300 R-matrix library (include/rmat.h).
+
+Argument marshalling only: every entry point forwards to the C ABI of
+librmat_gb300.so with plain integers, floats and device pointers (for example
+``tensor.data_ptr()`` of a torch CUDA tensor and
+``torch.cuda.current_stream().cuda_stream``).  There is no Python or CPU
+implementation of any step: importing the binding fails loudly when the
+shared library has not been built (``paper_2512_11590_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librmat_gb300.so")
+
+RMAT_OK = 0
+RMAT_ECUDA = -100
+RMAT_ENOMEM = -101
+RMAT_ESTATE = -102
+RMAT_ETIMEOUT = -103
+RMAT_ENODEV = -104
+RMAT_ESINGULAR = 1
+RMAT_ENOCONV = 2
+
+RMAT_C128 = 0
+RMAT_C64_3XTF32_IR = 1
+RMAT_C64_SIMT_IR = 2
+
+RMAT_PARAM_NB = 1
+RMAT_PARAM_PANEL_CTAS = 2
+RMAT_PARAM_SPIN_LIMIT = 3
+RMAT_PARAM_TIMING = 4
+
+EXPORTED = ("rmat_create", "rmat_destroy", "rmat_set_param", "rmat_mesh", "rmat_assemble",
+            "rmat_load_dense", "rmat_factor", "rmat_solve", "rmat_collision", "rmat_get_stats",
+            "rmat_reset_counters", "rmat_status_string")
+
+
+class rmat_problem(ct.Structure):
+    _fields_ = [("nch", ct.c_int), ("nlag", ct.c_int), ("a", ct.c_double), ("hm", ct.c_double),
+                ("bloch_B", ct.c_double), ("l", ct.POINTER(ct.c_int)),
+                ("thresh", ct.POINTER(ct.c_double)), ("precision", ct.c_int)]
+
+
+class RmatError(RuntimeError):
+    def __init__(self, name, status):
+        self.status = status
+        super().__init__(f"{name} -> {status} ({status_string(status)})")
+
+
+_lib = None
+
+
+def lib():
+    """Load librmat_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2512_11590_gb300.build.build() "
+                               "(nvcc, sm_103a); there is no fallback implementation")
+        L = ct.CDLL(LIB_PATH)
+        vp, i, d = ct.c_void_p, ct.c_int, ct.c_double
+        pd, pi = ct.POINTER(ct.c_double), ct.POINTER(ct.c_int)
+        sig = {
+            "rmat_create": (i, [ct.POINTER(vp), i, vp]),
+            "rmat_destroy": (i, [vp]),
+            "rmat_set_param": (i, [vp, i, ct.c_longlong]),
+            "rmat_mesh": (i, [i, d, pd, pd, pd, pd, pd, pd]),
+            "rmat_assemble": (i, [vp, ct.POINTER(rmat_problem), d, vp]),
+            "rmat_load_dense": (i, [vp, i, i, vp, i, vp, i, i]),
+            "rmat_factor": (i, [vp, pi]),
+            "rmat_solve": (i, [vp, vp, i, i, d, pi, pd]),
+            "rmat_collision": (i, [vp, vp, vp, pi]),
+            "rmat_get_stats": (i, [vp, pd, i]),
+            "rmat_reset_counters": (i, [vp]),
+            "rmat_status_string": (ct.c_char_p, [i]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().rmat_status_string(int(s)).decode()
+
+
+def _check(name, s, ok=(RMAT_OK,)):
+    if s not in ok:
+        raise RmatError(name, s)
+    return s
+
+
+# ---- entry points (same names as the C ABI) ---------------------------------
+
+def rmat_create(device: int = 0, stream: int = 0) -> int:
+    h = ct.c_void_p()
+    _check("rmat_create", lib().rmat_create(ct.byref(h), int(device), ct.c_void_p(stream or None)))
+    return h.value
+
+
+def rmat_destroy(ctx: int) -> None:
+    _check("rmat_destroy", lib().rmat_destroy(ct.c_void_p(ctx)))
+
+
+def rmat_set_param(ctx: int, key: int, value: int) -> None:
+    _check("rmat_set_param", lib().rmat_set_param(ct.c_void_p(ctx), int(key), int(value)))
+
+
+def rmat_mesh(nlag: int, a: float) -> dict:
+    """Host mesh tables: x, omx, lam, r, f_a (nlag,) and T0 (nlag, nlag), float64."""
+    out = {k: np.zeros(nlag) for k in ("x", "omx", "lam", "r", "f_a")}
+    T0 = np.zeros((nlag, nlag))
+    p = lambda arr: arr.ctypes.data_as(ct.POINTER(ct.c_double))  # noqa: E731
+    _check("rmat_mesh", lib().rmat_mesh(int(nlag), float(a), p(out["x"]), p(out["omx"]),
+                                         p(out["lam"]), p(out["r"]), p(out["f_a"]), p(T0)))
+    out["T0"] = T0
+    return out
+
+
+def make_problem_struct(nch, nlag, a, hm, l, thresh, precision, bloch_B=0.0):
+    """rmat_problem plus the host arrays it points to (keep the tuple alive)."""
+    l_arr = np.ascontiguousarray(l, dtype=np.int32)
+    t_arr = np.ascontiguousarray(thresh, dtype=np.float64)
+    s = rmat_problem(int(nch), int(nlag), float(a), float(hm), float(bloch_B),
+                     l_arr.ctypes.data_as(ct.POINTER(ct.c_int)),
+                     t_arr.ctypes.data_as(ct.POINTER(ct.c_double)), int(precision))
+    return s, (l_arr, t_arr)
+
+
+def rmat_assemble(ctx: int, prob: rmat_problem, E: float, V_dev: int) -> None:
+    _check("rmat_assemble", lib().rmat_assemble(ct.c_void_p(ctx), ct.byref(prob), float(E),
+                                                ct.c_void_p(V_dev)))
+
+
+def rmat_load_dense(ctx, n, nrhs, A_dev, lda, B_dev, ldb, precision) -> None:
+    _check("rmat_load_dense", lib().rmat_load_dense(ct.c_void_p(ctx), int(n), int(nrhs),
+                                                    ct.c_void_p(A_dev), int(lda),
+                                                    ct.c_void_p(B_dev), int(ldb), int(precision)))
+
+
+def rmat_factor(ctx: int, want_info: bool = True):
+    """Returns (status, info); info is None when not requested (no synchronisation)."""
+    if want_info:
+        info = ct.c_int(0)
+        s = lib().rmat_factor(ct.c_void_p(ctx), ct.byref(info))
+        _check("rmat_factor", s, ok=(RMAT_OK, RMAT_ESINGULAR))
+        return s, info.value
+    s = lib().rmat_factor(ct.c_void_p(ctx), None)
+    _check("rmat_factor", s)
+    return s, None
+
+
+def rmat_solve(ctx, X_dev, ldx, max_refine=0, tol=0.0):
+    """Returns (status, iters, rel_resid); RMAT_ENOCONV is returned, not raised."""
+    it = ct.c_int(0)
+    rel = ct.c_double(0.0)
+    s = lib().rmat_solve(ct.c_void_p(ctx), ct.c_void_p(X_dev), int(ldx), int(max_refine),
+                         float(tol), ct.byref(it), ct.byref(rel))
+    _check("rmat_solve", s, ok=(RMAT_OK, RMAT_ENOCONV))
+    return s, it.value, rel.value
+
+
+def rmat_collision(ctx, R_dev=0, U_dev=0) -> int:
+    """Returns nopen."""
+    nopen = ct.c_int(0)
+    _check("rmat_collision", lib().rmat_collision(ct.c_void_p(ctx), ct.c_void_p(R_dev or None),
+                                                  ct.c_void_p(U_dev or None), ct.byref(nopen)))
+    return nopen.value
+
+
+STAT_KEYS = ("N", "nrhs", "nb", "panel_ctas", "launches", "tu_launches", "tu_ms", "tu_flops",
+             "assemble_ms", "factor_ms", "solve_ms", "refine_ms", "collision_ms")
+
+
+def rmat_get_stats(ctx) -> dict:
+    buf = (ct.c_double * 13)()
+    n = lib().rmat_get_stats(ct.c_void_p(ctx), buf, 13)
+    return {k: buf[i] for i, k in enumerate(STAT_KEYS[:n])}
+
+
+def rmat_reset_counters(ctx) -> None:
+    _check("rmat_reset_counters", lib().rmat_reset_counters(ct.c_void_p(ctx)))

@@ -1,0 +1,491 @@
+// C ABI entry points (include/rmat.h): context, workspace, orchestration of
+// assemble -> factor -> solve/refine -> collision on one stream.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "cplx.cuh"
+#include "rmat_internal.h"
+
+namespace {
+
+size_t elem_bytes(int precision) { return precision == RMAT_C128 ? 16 : 8; }
+
+int default_nb(int precision, int N) {
+  if (precision == RMAT_C128) return N >= 2048 ? 64 : 32;
+  return N >= 4096 ? 128 : 64;
+}
+
+bool valid_precision(int p) {
+  return p == RMAT_C128 || p == RMAT_C64_3XTF32_IR || p == RMAT_C64_SIMT_IR;
+}
+
+int begin(rmat_ctx c) {
+  if (!c) return -1;
+  RMAT_CU(cudaSetDevice(c->device));
+  return RMAT_OK;
+}
+
+int read_status(rmat_ctx c) {
+  RMAT_CU(cudaMemcpyAsync(c->hstat, c->dstat, ST_COUNT * sizeof(int), cudaMemcpyDeviceToHost,
+                          c->stream));
+  RMAT_CU(cudaStreamSynchronize(c->stream));
+  return RMAT_OK;
+}
+
+double read_red(rmat_ctx c) {
+  unsigned long long bits = 0;
+  if (cudaMemcpyAsync(c->hstat + ST_COUNT, c->red, sizeof(bits), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess)
+    return NAN;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NAN;
+  std::memcpy(&bits, c->hstat + ST_COUNT, sizeof(bits));
+  double v;
+  std::memcpy(&v, &bits, sizeof(v));
+  return v;
+}
+
+// Reserve device memory for the problem; RMAT_ENOMEM when it cannot fit.
+int reserve(rmat_ctx c, bool dense) {
+  const size_t N = c->N, ld = c->ld, nrhs = c->nrhs;
+  const size_t eb = elem_bytes(c->precision);
+  const bool tensor = c->precision == RMAT_C64_3XTF32_IR;
+  size_t need = 0;
+  auto want = [&](size_t cap, size_t bytes) { need += bytes > cap ? bytes - cap : 0; };
+  want(c->C_cap, N * ld * eb);
+  want(c->X_cap, N * nrhs * 16);
+  want(c->Rres_cap, N * nrhs * 16);
+  want(c->Bw_cap, N * nrhs * eb);
+  if (tensor) {
+    want(c->Apl_cap, 4 * N * RMAT_MAX_NB * 4);
+    want(c->Bpl_cap, 4 * N * RMAT_MAX_NB * 4);
+  }
+  if (dense) {
+    want(c->A64_cap, N * N * 16);
+    want(c->B64_cap, N * nrhs * 16);
+  }
+  size_t free_b = 0, total_b = 0;
+  RMAT_CU(cudaMemGetInfo(&free_b, &total_b));
+  if (need + (size_t)256 * 1024 * 1024 > free_b) return RMAT_ENOMEM;
+  RMAT_CHECK(rmat_grow(c, &c->C, &c->C_cap, N * ld * eb));
+  RMAT_CHECK(rmat_grow(c, (void**)&c->X, &c->X_cap, N * nrhs * 16));
+  RMAT_CHECK(rmat_grow(c, (void**)&c->Rres, &c->Rres_cap, N * nrhs * 16));
+  RMAT_CHECK(rmat_grow(c, &c->Bw, &c->Bw_cap, N * nrhs * eb));
+  RMAT_CHECK(rmat_grow(c, (void**)&c->ipiv, &c->ipiv_cap, N * sizeof(int)));
+  if (tensor) {
+    RMAT_CHECK(rmat_grow(c, (void**)&c->Apl, &c->Apl_cap, 4 * N * RMAT_MAX_NB * 4));
+    RMAT_CHECK(rmat_grow(c, (void**)&c->Bpl, &c->Bpl_cap, 4 * N * RMAT_MAX_NB * 4));
+  }
+  if (dense) {
+    RMAT_CHECK(rmat_grow(c, (void**)&c->A64, &c->A64_cap, N * N * 16));
+    RMAT_CHECK(rmat_grow(c, (void**)&c->B64, &c->B64_cap, N * nrhs * 16));
+  }
+  return RMAT_OK;
+}
+
+void record_stage(rmat_ctx c, cudaEvent_t* ev) {
+  if (c->timing) {
+    *ev = rmat_event(c);
+    cudaEventRecord(*ev, c->stream);
+  } else {
+    *ev = nullptr;
+  }
+}
+
+double elapsed(cudaEvent_t a, cudaEvent_t b) {
+  if (!a || !b) return -1.0;
+  float ms = 0.f;
+  if (cudaEventSynchronize(b) != cudaSuccess) return -1.0;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return -1.0;
+  return ms;
+}
+
+}  // namespace
+
+int rmat_grow(rmat_ctx c, void** p, size_t* cap, size_t bytes) {
+  if (bytes <= *cap && *p) return RMAT_OK;
+  if (*p) {
+    RMAT_CU(cudaStreamSynchronize(c->stream));
+    RMAT_CU(cudaFree(*p));
+    *p = nullptr;
+    *cap = 0;
+  }
+  if (bytes == 0) return RMAT_OK;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return RMAT_ENOMEM;
+  }
+  *cap = bytes;
+  return RMAT_OK;
+}
+
+cudaEvent_t rmat_event(rmat_ctx c) {
+  if (c->ev_next >= c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_next++];
+}
+
+extern "C" {
+
+const char* rmat_status_string(int s) {
+  switch (s) {
+    case RMAT_OK: return "ok";
+    case RMAT_ECUDA: return "CUDA error";
+    case RMAT_ENOMEM: return "out of device memory";
+    case RMAT_ESTATE: return "call out of order";
+    case RMAT_ETIMEOUT: return "bounded device wait timed out";
+    case RMAT_ENODEV: return "no compute capability 10.3 device";
+    case RMAT_ESINGULAR: return "exactly singular pivot";
+    case RMAT_ENOCONV: return "refinement stagnated above tolerance";
+    default: return s < 0 && s > -100 ? "invalid argument" : "unknown status";
+  }
+}
+
+int rmat_create(rmat_ctx* out, int device, void* stream) {
+  if (!out) return -1;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return RMAT_ENODEV;
+  }
+  if (device < 0 || device >= ndev) return -2;
+  cudaDeviceProp prop;
+  RMAT_CU(cudaGetDeviceProperties(&prop, device));
+  if (prop.major != 10 || prop.minor != 3) return RMAT_ENODEV;
+  RMAT_CU(cudaSetDevice(device));
+  rmat_ctx c = new (std::nothrow) rmat_ctx_s();
+  if (!c) return RMAT_ENOMEM;
+  c->device = device;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  c->sm_count = prop.multiProcessorCount;
+  const size_t cs = sizeof(double2);
+  const size_t ps_bytes = 256 + 2 * RMAT_MAX_PANEL_CTAS * sizeof(double) +
+                          2 * RMAT_MAX_PANEL_CTAS * sizeof(int) +
+                          (size_t)2 * RMAT_MAX_PANEL_CTAS * RMAT_MAX_NB * cs +
+                          (size_t)2 * RMAT_MAX_NB * cs + 4 * 256;
+  if (cudaMalloc(&c->ps_mem, ps_bytes) != cudaSuccess ||
+      cudaMalloc((void**)&c->dstat, ST_COUNT * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&c->red, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->hstat, (ST_COUNT + 8) * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    rmat_destroy(c);
+    return RMAT_ENOMEM;
+  }
+  char* p = reinterpret_cast<char*>(c->ps_mem);
+  c->ps.bar = reinterpret_cast<unsigned*>(p);
+  p += 256;
+  c->ps.cval = p;
+  p += 2 * RMAT_MAX_PANEL_CTAS * sizeof(double);
+  c->ps.cidx = reinterpret_cast<int*>(p);
+  p += 2 * RMAT_MAX_PANEL_CTAS * sizeof(int);
+  p = reinterpret_cast<char*>(round_up(reinterpret_cast<uintptr_t>(p), 256));
+  c->ps.crow = p;
+  p += (size_t)2 * RMAT_MAX_PANEL_CTAS * RMAT_MAX_NB * cs;
+  c->ps.trow = p;
+  if (cudaMemset(c->dstat, 0, ST_COUNT * sizeof(int)) != cudaSuccess) {
+    rmat_destroy(c);
+    return RMAT_ECUDA;
+  }
+  *out = c;
+  return RMAT_OK;
+}
+
+int rmat_destroy(rmat_ctx c) {
+  if (!c) return RMAT_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  void* bufs[] = {c->C,    c->A64,  c->B64, c->ipiv, c->Kmat, c->T0,  c->rmesh,
+                  c->fa,   c->l_d,  c->th_d, c->Wpt, c->X,    c->Rres, c->Bw,
+                  c->Apl,  c->Bpl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
+                  c->ps_mem, c->dstat};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (c->hstat) cudaFreeHost(c->hstat);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+  return RMAT_OK;
+}
+
+int rmat_set_param(rmat_ctx c, int key, long long v) {
+  if (!c) return -1;
+  switch (key) {
+    case RMAT_PARAM_NB:
+      if (v < 0 || v > RMAT_MAX_NB || v % 32) return -3;
+      c->nb_param = (int)v;
+      return RMAT_OK;
+    case RMAT_PARAM_PANEL_CTAS:
+      if (v < 0 || v > RMAT_MAX_PANEL_CTAS) return -3;
+      c->panel_ctas_param = (int)v;
+      return RMAT_OK;
+    case RMAT_PARAM_SPIN_LIMIT:
+      if (v < 1) return -3;
+      c->spin_limit = v;
+      return RMAT_OK;
+    case RMAT_PARAM_TIMING:
+      c->timing = v ? 1 : 0;
+      return RMAT_OK;
+    default:
+      return -2;
+  }
+}
+
+int rmat_mesh(int nlag, double a, double* x, double* omx, double* lam, double* r, double* f_a,
+              double* T0) {
+  return rmat_mesh_host(nlag, a, x, omx, lam, r, f_a, T0);
+}
+
+int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_dev) {
+  RMAT_CHECK(begin(c));
+  if (!pb || pb->nch < 1 || pb->nlag < 1 || pb->nlag > 1024 || !(pb->a > 0) || !(pb->hm > 0) ||
+      !std::isfinite(pb->bloch_B) || !pb->l || !pb->thresh || !valid_precision(pb->precision))
+    return -2;
+  if ((long long)pb->nch * pb->nlag > 200000) return -2;
+  for (int k = 0; k < pb->nch; ++k)
+    if (pb->l[k] < 0 || pb->l[k] > 64 || !std::isfinite(pb->thresh[k])) return -2;
+  if (!std::isfinite(E)) return -3;
+  if (!V_dev) return -4;
+  const bool mesh_same = c->nlag == pb->nlag && c->a == pb->a && c->hm == pb->hm &&
+                         c->bloch_B == pb->bloch_B && c->Kmat != nullptr;
+  c->kind = 1;
+  c->precision = pb->precision;
+  c->nch = pb->nch;
+  c->nlag = pb->nlag;
+  c->N = pb->nch * pb->nlag;
+  c->nrhs = pb->nch;
+  c->ld = (int)round_up(c->N, 32);
+  c->a = pb->a;
+  c->hm = pb->hm;
+  c->bloch_B = pb->bloch_B;
+  c->E = E;
+  c->l.assign(pb->l, pb->l + pb->nch);
+  c->thresh.assign(pb->thresh, pb->thresh + pb->nch);
+  c->assembled = c->factored = c->solved = false;
+  c->nb = c->nb_param ? c->nb_param : default_nb(c->precision, c->N);
+  if (c->precision == RMAT_C128 && c->nb > 128) c->nb = 128;
+  RMAT_CHECK(reserve(c, false));
+  const int nlag = c->nlag, nch = c->nch;
+  RMAT_CHECK(rmat_grow(c, (void**)&c->Wpt, &c->Wpt_cap, (size_t)nlag * nch * nch * 16));
+  RMAT_CHECK(rmat_grow(c, (void**)&c->l_d, &c->l_cap, nch * sizeof(int)));
+  RMAT_CHECK(rmat_grow(c, (void**)&c->th_d, &c->th_cap, nch * sizeof(double)));
+  RMAT_CHECK(rmat_grow(c, (void**)&c->Rint, &c->Rint_cap, (size_t)nch * nch * 16));
+  RMAT_CHECK(rmat_grow(c, (void**)&c->Zbuf, &c->Zbuf_cap, collision_workspace_bytes(nch)));
+  RMAT_CHECK(rmat_grow(c, (void**)&c->zpiv, &c->zpiv_cap, nch * sizeof(int)));
+  RMAT_CHECK(rmat_grow(c, (void**)&c->open_d, &c->open_cap, nch * sizeof(int)));
+  if (!mesh_same) {
+    std::vector<double> r(nlag), fa(nlag), T0((size_t)nlag * nlag), K((size_t)nlag * nlag);
+    RMAT_CHECK(rmat_mesh_host(nlag, c->a, nullptr, nullptr, nullptr, r.data(), fa.data(), T0.data()));
+    const double s1 = c->hm * (c->bloch_B / c->a);
+    rmat_kinetic_table(nlag, c->hm, s1, T0.data(), fa.data(), K.data());
+    RMAT_CHECK(rmat_grow(c, (void**)&c->Kmat, &c->Kmat_cap, K.size() * 8));
+    RMAT_CHECK(rmat_grow(c, (void**)&c->T0, &c->T0_cap, T0.size() * 8));
+    RMAT_CHECK(rmat_grow(c, (void**)&c->rmesh, &c->rmesh_cap, nlag * 8));
+    RMAT_CHECK(rmat_grow(c, (void**)&c->fa, &c->fa_cap, nlag * 8));
+    RMAT_CU(cudaMemcpy(c->Kmat, K.data(), K.size() * 8, cudaMemcpyHostToDevice));
+    RMAT_CU(cudaMemcpy(c->T0, T0.data(), T0.size() * 8, cudaMemcpyHostToDevice));
+    RMAT_CU(cudaMemcpy(c->rmesh, r.data(), nlag * 8, cudaMemcpyHostToDevice));
+    RMAT_CU(cudaMemcpy(c->fa, fa.data(), nlag * 8, cudaMemcpyHostToDevice));
+    c->f_a_host = fa;
+  }
+  double pm = 0;
+  for (double v : c->f_a_host) pm = std::max(pm, std::fabs(v));
+  c->phi_max = pm;
+  RMAT_CU(cudaMemcpyAsync(c->l_d, c->l.data(), nch * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  RMAT_CU(cudaMemcpyAsync(c->th_d, c->thresh.data(), nch * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
+  cudaEvent_t e0, e1;
+  record_stage(c, &e0);
+  RMAT_CHECK(launch_assemble(c, reinterpret_cast<const double2*>(V_dev), E));
+  RMAT_CHECK(launch_point_coupling(c, reinterpret_cast<const double2*>(V_dev), E));
+  record_stage(c, &e1);
+  c->stage_ev[0][0] = e0;
+  c->stage_ev[0][1] = e1;
+  c->assembled = true;
+  return RMAT_OK;
+}
+
+int rmat_load_dense(rmat_ctx c, int n, int nrhs, const void* A_dev, int lda, const void* B_dev,
+                    int ldb, int precision) {
+  RMAT_CHECK(begin(c));
+  if (n < 1 || n > 200000) return -2;
+  if (nrhs < 1) return -3;
+  if (!A_dev) return -4;
+  if (lda < n) return -5;
+  if (!B_dev) return -6;
+  if (ldb < n) return -7;
+  if (!valid_precision(precision)) return -8;
+  c->kind = 2;
+  c->precision = precision;
+  c->N = n;
+  c->nrhs = nrhs;
+  c->nch = c->nlag = 0;
+  c->ld = (int)round_up(n, 32);
+  c->assembled = c->factored = c->solved = false;
+  c->nb = c->nb_param ? c->nb_param : default_nb(precision, n);
+  if (precision == RMAT_C128 && c->nb > 128) c->nb = 128;
+  RMAT_CHECK(reserve(c, true));
+  RMAT_CHECK(launch_load_dense(c, reinterpret_cast<const double2*>(A_dev), lda,
+                               reinterpret_cast<const double2*>(B_dev), ldb));
+  RMAT_CHECK(launch_absmax(c, c->B64, (size_t)n * nrhs));
+  c->phi_max = read_red(c);
+  if (!(c->phi_max > 0)) c->phi_max = 1.0;
+  c->assembled = true;
+  return RMAT_OK;
+}
+
+int rmat_factor(rmat_ctx c, int* info) {
+  RMAT_CHECK(begin(c));
+  if (!c->assembled) return RMAT_ESTATE;
+  RMAT_CU(cudaMemsetAsync(c->dstat, 0, ST_COUNT * sizeof(int), c->stream));
+  cudaEvent_t e0, e1;
+  record_stage(c, &e0);
+  const bool tensor = c->precision == RMAT_C64_3XTF32_IR;
+  int st;
+  if (c->precision == RMAT_C128)
+    st = lu_factor_dev<double>(c, c->C, c->N, c->ld, c->ipiv, c->nb, false);
+  else
+    st = lu_factor_dev<float>(c, c->C, c->N, c->ld, c->ipiv, c->nb, tensor);
+  if (st != RMAT_OK) return st;
+  record_stage(c, &e1);
+  c->factored = true;
+  c->solved = false;
+  c->stage_ev[1][0] = e0;
+  c->stage_ev[1][1] = e1;
+  if (info) {
+    RMAT_CHECK(read_status(c));
+    if (c->hstat[ST_TIMEOUT]) return RMAT_ETIMEOUT;
+    *info = c->hstat[ST_INFO];
+    if (*info) return RMAT_ESINGULAR;
+  }
+  return RMAT_OK;
+}
+
+static int solve_factors(rmat_ctx c) {
+  if (c->precision == RMAT_C128)
+    return lu_solve_dev<double>(c, c->C, c->N, c->ld, c->ipiv, c->nb, c->Bw, c->nrhs, c->nrhs);
+  return lu_solve_dev<float>(c, c->C, c->N, c->ld, c->ipiv, c->nb, c->Bw, c->nrhs, c->nrhs);
+}
+
+int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int* iters,
+               double* rel_resid) {
+  RMAT_CHECK(begin(c));
+  if (!X_dev) return -2;
+  if (ldx < c->N) return -3;
+  if (max_refine < 0) return -4;
+  if (!c->factored) return RMAT_ESTATE;
+  cudaEvent_t e0, e1, e2;
+  record_stage(c, &e0);
+  RMAT_CHECK(launch_w_from_phi(c));
+  RMAT_CHECK(solve_factors(c));
+  RMAT_CHECK(launch_x_from_w(c));
+  record_stage(c, &e1);
+  int it = 0, status = RMAT_OK;
+  double rel = 0.0;
+  if (max_refine > 0 || tol > 0) {
+    double prev = INFINITY;
+    int stagn = 0;
+    for (;;) {
+      RMAT_CHECK(launch_residual(c, nullptr));
+      rel = read_red(c) / c->phi_max;
+      if (!std::isfinite(rel)) {
+        status = RMAT_ENOCONV;
+        break;
+      }
+      if (rel < tol) break;
+      if (it >= max_refine) {
+        status = tol > 0 ? RMAT_ENOCONV : RMAT_OK;
+        break;
+      }
+      if (rel > 0.5 * prev) {
+        if (++stagn >= 2) {
+          status = RMAT_ENOCONV;
+          break;
+        }
+      } else {
+        stagn = 0;
+      }
+      prev = rel;
+      RMAT_CHECK(solve_factors(c));
+      RMAT_CHECK(launch_update(c));
+      ++it;
+    }
+  }
+  record_stage(c, &e2);
+  RMAT_CHECK(launch_x_out(c, reinterpret_cast<double2*>(X_dev), ldx));
+  RMAT_CHECK(read_status(c));
+  c->stage_ev[2][0] = e0;
+  c->stage_ev[2][1] = e1;
+  c->stage_ev[3][0] = e1;
+  c->stage_ev[3][1] = e2;
+  if (c->hstat[ST_TIMEOUT]) return RMAT_ETIMEOUT;
+  if (c->hstat[ST_BADARG]) return RMAT_ESTATE;
+  c->solved = true;
+  if (iters) *iters = it;
+  if (rel_resid) *rel_resid = rel;
+  if (c->hstat[ST_INFO]) return RMAT_ESINGULAR;
+  return status;
+}
+
+int rmat_collision(rmat_ctx c, void* R_dev, void* U_dev, int* nopen) {
+  RMAT_CHECK(begin(c));
+  if (!c->solved || c->kind != 1) return RMAT_ESTATE;
+  std::vector<int> open;
+  for (int k = 0; k < c->nch; ++k)
+    if (c->E - c->thresh[k] > 0) open.push_back(k);
+  const int no = (int)open.size();
+  if (nopen) *nopen = no;
+  cudaEvent_t e0, e1;
+  record_stage(c, &e0);
+  if (no > 0)
+    RMAT_CU(cudaMemcpyAsync(c->open_d, open.data(), no * sizeof(int), cudaMemcpyHostToDevice,
+                            c->stream));
+  RMAT_CU(cudaMemsetAsync(c->dstat, 0, ST_COUNT * sizeof(int), c->stream));
+  RMAT_CHECK(launch_collision(c, reinterpret_cast<double2*>(R_dev), reinterpret_cast<double2*>(U_dev),
+                              no));
+  record_stage(c, &e1);
+  RMAT_CHECK(read_status(c));
+  c->stage_ev[4][0] = e0;
+  c->stage_ev[4][1] = e1;
+  if (c->hstat[ST_TIMEOUT]) return RMAT_ETIMEOUT;
+  if (c->hstat[ST_INFO]) return RMAT_ESINGULAR;
+  return RMAT_OK;
+}
+
+int rmat_get_stats(rmat_ctx c, double* out, int n) {
+  if (!c) return -1;
+  if (!out || n < 0) return -2;
+  double tu = 0;
+  bool ok = true;
+  for (auto& pr : c->tu_events) {
+    double ms = elapsed(pr.first, pr.second);
+    if (ms < 0) ok = false;
+    tu += ms;
+  }
+  for (int k = 0; k < 5; ++k)
+    c->stage_ms[k] = elapsed(c->stage_ev[k][0], c->stage_ev[k][1]);
+  const double v[13] = {(double)c->N, (double)c->nrhs, (double)c->nb,
+                        (double)panel_ctas_for(c, c->N > 0 ? c->N : 1), (double)c->launches,
+                        (double)c->tu_launches, (ok && !c->tu_events.empty()) ? tu : -1.0,
+                        c->tu_flops, c->stage_ms[0], c->stage_ms[1], c->stage_ms[2],
+                        c->stage_ms[3], c->stage_ms[4]};
+  const int m = n < 13 ? n : 13;
+  for (int k = 0; k < m; ++k) out[k] = v[k];
+  return m;
+}
+
+int rmat_reset_counters(rmat_ctx c) {
+  if (!c) return -1;
+  c->launches = c->tu_launches = 0;
+  c->tu_flops = 0;
+  c->tu_events.clear();
+  c->ev_next = 0;
+  for (double& s : c->stage_ms) s = -1;
+  for (auto& pr : c->stage_ev) pr[0] = pr[1] = nullptr;
+  return RMAT_OK;
+}
+
+}  // extern "C"

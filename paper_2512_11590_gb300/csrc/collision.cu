@@ -1,0 +1,206 @@
+// G9/G10: R-matrix contraction and collision matrix (FP64, on the device).
+//
+// R (Sec. 3.1 step 4): R_{al be} = sum_i q2(r_i) X[(al,i), be] with q2 = f_i(a);
+// with C in MeV the dimensionless R-matrix carries hm/a:
+//   R = (hm/a) Phi^T X.
+// U: matching to the free asymptotic solutions at the channel radius (Sec. 1,
+// Coulomb/Whittaker functions of Sec. 4.1, here eta = 0):
+//   R~ = a sqrt(k) R sqrt(k),
+//   U  = (diag O - R~ diag O')^-1 (diag I - R~ diag I'),  open x open block,
+// I = G - iF, O = G + iF (Riccati-Bessel F = rho j_l, G = -rho y_l) for open
+// channels; O = reduced Whittaker function, I = 0 for closed ones.  The
+// matching system (nch x nch, nopen right-hand sides) is solved with this
+// library's FP64 LU.
+#include <algorithm>
+
+#include "cplx.cuh"
+#include "rmat_internal.h"
+
+namespace {
+
+__global__ void r_contract_kernel(const double2* __restrict__ X, int nch, int nlag, int nrhs,
+                                  const double* __restrict__ fa, double scale,
+                                  double2* __restrict__ Rint, double2* __restrict__ Rout) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nch * nch) return;
+  const int al = e / nch, be = e % nch;
+  double sr = 0.0, si = 0.0;
+  for (int i = 0; i < nlag; ++i) {
+    const double2 x = X[((size_t)al * nlag + i) * nrhs + be];
+    sr = fma(fa[i], x.x, sr);
+    si = fma(fa[i], x.y, si);
+  }
+  const double2 r = make_double2(scale * sr, scale * si);
+  Rint[(size_t)al * nch + be] = r;
+  if (Rout) Rout[al + (size_t)nch * be] = r;
+}
+
+// F_l, G_l and derivatives (eta = 0).  G by upward recurrence from
+// G_0 = cos, G_1 = cos/rho + sin; F by upward recurrence for rho >= l+1, else by
+// the power series rho^(l+1) sum_k (-rho^2/2)^k / (k! (2l+2k+1)!!).
+// X_l' = X_{l-1} - (l/rho) X_l.
+__device__ void riccati_fg(int l, double rho, double* F, double* G, double* dF, double* dG) {
+  const double s = sin(rho), c = cos(rho);
+  if (l == 0) {
+    *F = s; *G = c; *dF = c; *dG = -s;
+    return;
+  }
+  double g0 = c, g1 = c / rho + s;
+  for (int q = 1; q < l; ++q) {
+    const double g2 = (2 * q + 1) / rho * g1 - g0;
+    g0 = g1;
+    g1 = g2;
+  }
+  double f0, f1;
+  if (rho >= l + 1) {
+    f0 = s;
+    f1 = s / rho - c;
+    for (int q = 1; q < l; ++q) {
+      const double f2 = (2 * q + 1) / rho * f1 - f0;
+      f0 = f1;
+      f1 = f2;
+    }
+  } else {
+    double fl[2];
+    for (int L = l - 1; L <= l; ++L) {
+      double df = 1.0;
+      for (int q = 1; q <= 2 * L + 1; q += 2) df *= q;
+      double term = pow(rho, L + 1) / df, acc = term;
+      for (int k = 1; k < 200; ++k) {
+        term *= -(rho * rho / 2.0) / (k * (2.0 * L + 2 * k + 1));
+        acc += term;
+        if (fabs(term) < 1e-18 * fabs(acc)) break;
+      }
+      fl[L - (l - 1)] = acc;
+    }
+    f0 = fl[0];
+    f1 = fl[1];
+  }
+  *F = f1;
+  *G = g1;
+  *dF = f0 - l / rho * f1;
+  *dG = g0 - l / rho * g1;
+}
+
+// e^-rho sum_{k=0}^{l} (l+k)!/(k!(l-k)!) (2 rho)^-k and its rho-derivative
+__device__ void whittaker_w(int l, double rho, double* W, double* dW) {
+  double w = 0.0, dw = 0.0, ck = 1.0;  // ck = (l+k)!/(k!(l-k)!) for k = 0
+  for (int k = 0; k <= l; ++k) {
+    if (k > 0) ck = ck * (double)(l + k) * (double)(l - k + 1) / (double)k;
+    const double t = ck * pow(2.0 * rho, -k);
+    w += t;
+    dw += t * (-1.0 - k / rho);
+  }
+  const double e = exp(-rho);
+  *W = e * w;
+  *dW = e * dw;
+}
+
+struct ChanFn {
+  double2 I, O, dI, dO;
+  double k;
+};
+
+__global__ void chan_fn_kernel(ChanFn* __restrict__ out, int nch, const int* __restrict__ l,
+                               const double* __restrict__ th, double E, double hm, double a,
+                               double B) {
+  const int ch = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ch >= nch) return;
+  const double ecm = E - th[ch];
+  const double k = sqrt(fabs(ecm) / hm), rho = k * a;
+  ChanFn f;
+  f.k = k;
+  if (ecm > 0) {
+    double F, G, dF, dG;
+    riccati_fg(l[ch], rho, &F, &G, &dF, &dG);
+    f.I = make_double2(G, -F);
+    f.O = make_double2(G, F);
+    f.dI = make_double2(dG, -dF);
+    f.dO = make_double2(dG, dF);
+  } else {
+    double W, dW;
+    whittaker_w(l[ch], rho, &W, &dW);
+    f.I = make_double2(0, 0);
+    f.dI = make_double2(0, 0);
+    f.O = make_double2(W, 0);
+    f.dO = make_double2(dW, 0);
+  }
+  f.dI.x -= B / rho * f.I.x;
+  f.dI.y -= B / rho * f.I.y;
+  f.dO.x -= B / rho * f.O.x;
+  f.dO.y -= B / rho * f.O.y;
+  out[ch] = f;
+}
+
+// ZO (nch x nch) and ZI (nch x nopen), row-major, from R and the channel functions.
+__global__ void z_build_kernel(const double2* __restrict__ Rint, const ChanFn* __restrict__ f,
+                               int nch, int nopen, const int* __restrict__ open, double a,
+                               double2* __restrict__ ZO, double2* __restrict__ ZI) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ncol = nch + nopen;
+  if (e >= nch * ncol) return;
+  const int row = e / ncol, col = e % ncol;
+  const int cp = col < nch ? col : open[col - nch];
+  const double2 R = Rint[(size_t)row * nch + cp];
+  const double s = a * sqrt(f[row].k) * sqrt(f[cp].k);
+  const double2 Rt = make_double2(s * R.x, s * R.y);
+  if (col < nch) {
+    double2 z = cmul<double>(Rt, f[cp].dO);
+    z.x = -z.x;
+    z.y = -z.y;
+    if (row == cp) { z.x += f[row].O.x; z.y += f[row].O.y; }
+    ZO[(size_t)row * nch + col] = z;
+  } else {
+    double2 z = cmul<double>(Rt, f[cp].dI);
+    z.x = -z.x;
+    z.y = -z.y;
+    if (row == cp) { z.x += f[row].I.x; z.y += f[row].I.y; }
+    ZI[(size_t)row * nopen + (col - nch)] = z;
+  }
+}
+
+__global__ void u_extract_kernel(const double2* __restrict__ Ufull, int nopen,
+                                 const int* __restrict__ open, double2* __restrict__ U) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nopen * nopen) return;
+  const int q = e % nopen, q2 = e / nopen;  // U(q, q2), column-major
+  U[e] = Ufull[(size_t)open[q] * nopen + q2];
+}
+
+}  // namespace
+
+int launch_collision(rmat_ctx c, double2* R_dev, double2* U_dev, int nopen) {
+  const int nch = c->nch;
+  r_contract_kernel<<<ceil_div(nch * nch, 128), 128, 0, c->stream>>>(
+      c->X, nch, c->nlag, c->nrhs, c->fa, c->hm / c->a, c->Rint, R_dev);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  if (!U_dev || nopen == 0) return RMAT_OK;
+  ChanFn* fn = reinterpret_cast<ChanFn*>(c->Zbuf);
+  double2* ZO = reinterpret_cast<double2*>(reinterpret_cast<char*>(c->Zbuf) +
+                                           round_up(sizeof(ChanFn) * nch, 256));
+  double2* ZI = ZO + (size_t)nch * nch;
+  chan_fn_kernel<<<ceil_div(nch, 64), 64, 0, c->stream>>>(fn, nch, c->l_d, c->th_d, c->E, c->hm,
+                                                           c->a, c->bloch_B);
+  z_build_kernel<<<ceil_div((long long)nch * (nch + nopen), 128), 128, 0, c->stream>>>(
+      c->Rint, fn, nch, nopen, c->open_d, c->a, ZO, ZI);
+  c->launches += 2;
+  RMAT_CU(cudaGetLastError());
+  const long long tl = c->tu_launches;
+  const double tf = c->tu_flops;
+  const size_t tev = c->tu_events.size();
+  const int nb = std::min(64, nch);
+  RMAT_CHECK(lu_factor_dev<double>(c, ZO, nch, nch, c->zpiv, nb, false));
+  RMAT_CHECK(lu_solve_dev<double>(c, ZO, nch, nch, c->zpiv, nb, ZI, nopen, nopen));
+  c->tu_launches = tl;
+  c->tu_flops = tf;
+  c->tu_events.resize(tev);
+  u_extract_kernel<<<ceil_div(nopen * nopen, 128), 128, 0, c->stream>>>(ZI, nopen, c->open_d, U_dev);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+size_t collision_workspace_bytes(int nch) {
+  return round_up(sizeof(ChanFn) * nch, 256) + (size_t)nch * 2 * nch * sizeof(double2);
+}

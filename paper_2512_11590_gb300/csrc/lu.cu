@@ -1,0 +1,526 @@
+// Blocked right-looking LU with partial pivoting and the triangular solves.
+//
+// Paper: Type-1 solver M = P L U with partial pivoting followed by forward and
+// backward substitution for all nch right-hand sides (Sec. 3.1); the same
+// factorisation in single precision for the mixed-precision solvers
+// (Sec. 3.2, 3.4).  Layout: row-major working matrix (the R-matrix C is
+// complex symmetric, so row-major C equals the paper's column-major C), block
+// width nb.  For each block column k0:
+//   G2  panel:  cooperative kernel over rows k0..n-1, columns k0..k0+jb; one
+//               grid barrier per column; warp-shuffle argmax of |Re|+|Im|
+//               (first row on ties); the pivot row travels through a slot in
+//               global memory, so swap, scaling and rank-1 update need no
+//               second barrier.
+//   G3  swaps + TRSM: the panel's row interchanges applied to the trailing
+//               columns, then U12 = L11^-1 A12.
+//   G4  trailing update C22 -= L21 U12 (tensor cores, gemm_tc.cu, or the
+//               SIMT kernel below).
+// Interchanges are NOT applied to the columns left of the panel: the forward
+// solve replays the panel permutations block by block, which is equivalent to
+// LAPACK's P^T applied once.
+#include <algorithm>
+#include <climits>
+
+#include "cplx.cuh"
+#include "rmat_internal.h"
+
+namespace {
+
+constexpr int PANEL_THREADS = 256;
+constexpr int MAX_RPC = 4096;  // rows per panel CTA
+
+template <class T>
+__global__ void __launch_bounds__(PANEL_THREADS)
+panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __restrict__ ipiv,
+             int* __restrict__ stat, PanelScratch ps, int rpc, long long spin_limit) {
+  using C2 = cplx<T>;
+  const int P = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = PANEL_THREADS / 32;
+  const int r_lo = k0 + cta * rpc;
+  const int r_hi = min(k0 + (cta + 1) * rpc, n);
+  T* cval = (T*)ps.cval;
+  C2* crow = (C2*)ps.crow;
+  C2* trow = (C2*)ps.trow;
+
+  __shared__ T s_v[32];
+  __shared__ int s_i[32];
+  __shared__ int s_c[32];
+  __shared__ int s_win, s_wcta, s_zero, s_abort;
+  extern __shared__ unsigned char smem_raw[];
+  C2* s_prow = reinterpret_cast<C2*>(smem_raw);  // [RMAT_MAX_NB]
+  C2* s_l = s_prow + RMAT_MAX_NB;                // [rpc]
+  if (tid == 0) s_abort = 0;
+
+  for (int j = 0; j < jb; ++j) {
+    const int gj = k0 + j;
+    const int par = j & 1;
+    // ---- phase A: local candidate for column gj among own rows >= gj ----
+    T best = (T)-1;
+    int bidx = INT_MAX;
+    for (int r = max(r_lo, gj) + tid; r < r_hi; r += PANEL_THREADS) {
+      T m = cabs1<T>(A[(size_t)r * ld + gj]);
+      if (m > best) { best = m; bidx = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if (lane == 0) { s_v[warp] = best; s_i[warp] = bidx; }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nwarp ? s_v[lane] : (T)-1;
+      bidx = lane < nwarp ? s_i[lane] : INT_MAX;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+      }
+      if (lane == 0) {
+        s_win = bidx;
+        cval[par * RMAT_MAX_PANEL_CTAS + cta] = best;
+        ps.cidx[par * RMAT_MAX_PANEL_CTAS + cta] = bidx;
+      }
+    }
+    __syncthreads();
+    {
+      const int cr = s_win;
+      C2* slot = crow + ((size_t)par * RMAT_MAX_PANEL_CTAS + cta) * RMAT_MAX_NB;
+      if (cr != INT_MAX)
+        for (int c = tid; c < jb; c += PANEL_THREADS) slot[c] = A[(size_t)cr * ld + k0 + c];
+      if (gj >= r_lo && gj < r_hi)
+        for (int c = tid; c < jb; c += PANEL_THREADS)
+          trow[(size_t)par * RMAT_MAX_NB + c] = A[(size_t)gj * ld + k0 + c];
+    }
+    // ---- grid barrier (bounded spin) ----
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(ps.bar, 1u);
+      const unsigned target = (unsigned)(j + 1) * (unsigned)P;
+      long long polls = 0;
+      while (ld_acquire_gpu(ps.bar) < target) {
+        if (++polls > spin_limit) {
+          atomicExch(&stat[ST_TIMEOUT], 1);
+          s_abort = 1;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_abort) return;
+    // ---- phase B: global winner ----
+    if (warp == 0) {
+      best = (T)-1;
+      bidx = INT_MAX;
+      int bc = -1;
+      for (int q = lane; q < P; q += 32) {
+        T v = ld_cg(cval + par * RMAT_MAX_PANEL_CTAS + q);
+        int ix = ld_cg(ps.cidx + par * RMAT_MAX_PANEL_CTAS + q);
+        if (v > best || (v == best && ix < bidx)) { best = v; bidx = ix; bc = q; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; bc = oc; }
+      }
+      if (lane == 0) {
+        s_win = bidx;
+        s_wcta = bc;
+        s_zero = !(best > (T)0);
+      }
+    }
+    __syncthreads();
+    const int p = (s_win >= gj && s_win < n) ? s_win : gj;
+    const int wc = (s_wcta >= 0 && s_wcta < P) ? s_wcta : 0;
+    const C2* wslot = crow + ((size_t)par * RMAT_MAX_PANEL_CTAS + wc) * RMAT_MAX_NB;
+    for (int c = tid; c < jb; c += PANEL_THREADS) s_prow[c] = ld_cg(wslot + c);
+    if (cta == 0 && tid == 0) {
+      ipiv[gj] = p;
+      if (s_zero) atomicCAS(&stat[ST_INFO], 0, gj + 1);
+    }
+    __syncthreads();
+    if (p != gj) {
+      if (gj >= r_lo && gj < r_hi)
+        for (int c = tid; c < jb; c += PANEL_THREADS) A[(size_t)gj * ld + k0 + c] = s_prow[c];
+      if (p >= r_lo && p < r_hi)
+        for (int c = tid; c < jb; c += PANEL_THREADS)
+          A[(size_t)p * ld + k0 + c] = ld_cg(trow + (size_t)par * RMAT_MAX_NB + c);
+    }
+    __syncthreads();
+    if (s_zero) continue;  // exactly zero column: no scaling, no update (LAPACK)
+    const C2 piv = s_prow[j];
+    const int r_first = max(r_lo, gj + 1);
+    for (int r = r_first + tid; r < r_hi; r += PANEL_THREADS) {
+      C2 lm = cdiv<T>(A[(size_t)r * ld + gj], piv);
+      A[(size_t)r * ld + gj] = lm;
+      s_l[r - r_lo] = lm;
+    }
+    __syncthreads();
+    if (j + 1 < jb) {
+      for (int r = r_first + warp; r < r_hi; r += nwarp) {
+        const C2 lm = s_l[r - r_lo];
+        C2* Ar = A + (size_t)r * ld + k0;
+        for (int c = j + 1 + lane; c < jb; c += 32) {
+          C2 x = Ar[c];
+          csub_mul<T>(x, lm, s_prow[c]);
+          Ar[c] = x;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---- G3: row interchanges on the trailing columns + U12 = L11^-1 A12 ------
+// (the interchanges use rhs_swap_kernel and the solve trsm_block_rhs_kernel,
+// both below, on the trailing columns viewed as right-hand sides)
+
+__device__ __forceinline__ float tf32_round(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// B operand planes of the tensor update: U12^T split into tf32 hi/lo planes.
+// Plane row = trailing column c, K index t (plane row stride RMAT_MAX_NB floats):
+// [re_hi | re_lo | im_hi | im_lo].  K indices jb..round_up(jb,32)-1 are zeroed.
+// 32 x 32 tiles transposed through shared memory (coalesced on both sides).
+__global__ void __launch_bounds__(256)
+split_u12_kernel(const float2* __restrict__ A, int ld, int k0, int jb, int n,
+                 float* __restrict__ Bpl, size_t plane) {
+  __shared__ float2 tile[32][33];
+  const int c0 = k0 + jb + blockIdx.x * 32;
+  const int t0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int i = ty; i < 32; i += 8) {
+    const int t = t0 + i, c = c0 + tx;
+    tile[i][tx] = (t < jb && c < n) ? A[(size_t)(k0 + t) * ld + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int c = c0 + i, t = t0 + tx;
+    if (c >= n) continue;
+    const float2 z = tile[tx][i];
+    const float rh = tf32_round(z.x), ih = tf32_round(z.y);
+    const size_t o = (size_t)c * RMAT_MAX_NB + t;
+    Bpl[o] = rh;
+    Bpl[plane + o] = z.x - rh;
+    Bpl[2 * plane + o] = ih;
+    Bpl[3 * plane + o] = z.y - ih;
+  }
+}
+
+// A operand planes of the tensor update: L21 rows r in [k0+jb, n), K index t.
+__global__ void split_l21_kernel(const float2* __restrict__ A, int ld, int k0, int jb, int n,
+                                 float* __restrict__ Apl, size_t plane) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int r = k0 + jb + warp;
+  if (r >= n) return;
+  for (int t = lane; t < RMAT_MAX_NB; t += 32) {
+    float re = 0.f, im = 0.f;
+    if (t < jb) {
+      float2 z = A[(size_t)r * ld + k0 + t];
+      re = z.x;
+      im = z.y;
+    }
+    float rh = tf32_round(re), ih = tf32_round(im);
+    size_t o = (size_t)r * RMAT_MAX_NB + t;
+    Apl[o] = rh;
+    Apl[plane + o] = re - rh;
+    Apl[2 * plane + o] = ih;
+    Apl[3 * plane + o] = im - ih;
+  }
+}
+
+// ---- SIMT complex GEMM: C -= A B (all row-major) -----------------------------
+constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+
+template <class T>
+__global__ void __launch_bounds__(256)
+cgemm_sub_kernel(int M, int N, int K, const cplx<T>* __restrict__ A, int lda,
+                 const cplx<T>* __restrict__ B, int ldb, cplx<T>* __restrict__ C, int ldc) {
+  using C2 = cplx<T>;
+  __shared__ C2 As[GB_K][GB_M + 1];
+  __shared__ C2 Bs[GB_K][GB_N];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+  C2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mkc<T>(0, 0);
+  for (int kk = 0; kk < K; kk += GB_K) {
+#pragma unroll
+    for (int e = tid; e < GB_M * GB_K; e += 256) {
+      const int m = e / GB_K, k = e % GB_K;
+      const int gm = m0 + m, gk = kk + k;
+      As[k][m] = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : mkc<T>(0, 0);
+    }
+#pragma unroll
+    for (int e = tid; e < GB_K * GB_N; e += 256) {
+      const int k = e / GB_N, nn = e % GB_N;
+      const int gk = kk + k, gn = n0 + nn;
+      Bs[k][nn] = (gk < K && gn < N) ? B[(size_t)gk * ldb + gn] : mkc<T>(0, 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < GB_K; ++k) {
+      C2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cadd_mul<T>(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      C2 c = C[(size_t)gm * ldc + gn];
+      c.x -= acc[i][j].x;
+      c.y -= acc[i][j].y;
+      C[(size_t)gm * ldc + gn] = c;
+    }
+  }
+}
+
+// ---- solve kernels (right-hand sides row-major, ldb) -------------------------
+// Row interchanges of one panel applied to nrhs columns.  Pivot indices are
+// checked against [k0+t, n): an index outside it (only possible after a panel
+// that gave up on a bounded wait) is skipped and flagged, never dereferenced.
+template <class T>
+__global__ void rhs_swap_kernel(cplx<T>* __restrict__ B, int ldb, int nrhs, int k0, int jb, int n,
+                                const int* __restrict__ ipiv, int* __restrict__ stat) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nrhs) return;
+  for (int t = 0; t < jb; ++t) {
+    const int p = __ldg(ipiv + k0 + t);
+    if (p < k0 + t || p >= n) {
+      if (col == 0) atomicExch(&stat[ST_BADARG], 1);
+      continue;
+    }
+    if (p != k0 + t) {
+      cplx<T> u = B[(size_t)(k0 + t) * ldb + col];
+      B[(size_t)(k0 + t) * ldb + col] = B[(size_t)p * ldb + col];
+      B[(size_t)p * ldb + col] = u;
+    }
+  }
+}
+
+// Triangular solve on a jb x jb diagonal block for 32 right-hand-side columns
+// per CTA (lane = column).  Rows are processed in groups of 8 (one per warp):
+// each warp first accumulates the contributions of all rows solved before its
+// group in parallel, then warp 0 finishes the 8 x 8 triangle sequentially.
+// LOWER: unit lower, rows top-down; else upper (divide by the diagonal), bottom-up.
+template <class T, bool LOWER>
+__global__ void __launch_bounds__(256)
+trsm_block_rhs_kernel(const cplx<T>* __restrict__ A, int ld, int k0, int jb,
+                      cplx<T>* __restrict__ B, int ldb, int nrhs) {
+  using C2 = cplx<T>;
+  extern __shared__ unsigned char smem_raw[];
+  C2* xs = reinterpret_cast<C2*>(smem_raw);  // [jb][32]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.x * 32 + lane;
+  const bool act = col < nrhs;
+  const int ngroups = (jb + 7) / 8;
+  for (int g = 0; g < ngroups; ++g) {
+    // local row index (within the block) handled by this warp
+    const int li = LOWER ? g * 8 + warp : jb - 1 - (g * 8 + warp);
+    const bool rowok = (g * 8 + warp) < jb;
+    if (rowok) {
+      C2 acc = act ? B[(size_t)(k0 + li) * ldb + col] : mkc<T>(0, 0);
+      const C2* Ar = A + (size_t)(k0 + li) * ld + k0;
+      if (LOWER) {
+        for (int t = 0; t < g * 8; ++t) csub_mul<T>(acc, __ldg(Ar + t), xs[t * 32 + lane]);
+      } else {
+        for (int t = jb - g * 8; t < jb; ++t) csub_mul<T>(acc, __ldg(Ar + t), xs[t * 32 + lane]);
+      }
+      xs[li * 32 + lane] = acc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int w = 0; w < 8 && g * 8 + w < jb; ++w) {
+        const int ri = LOWER ? g * 8 + w : jb - 1 - (g * 8 + w);
+        const C2* Ar = A + (size_t)(k0 + ri) * ld + k0;
+        C2 acc = xs[ri * 32 + lane];
+        for (int w2 = 0; w2 < w; ++w2) {
+          const int tj = LOWER ? g * 8 + w2 : jb - 1 - (g * 8 + w2);
+          csub_mul<T>(acc, __ldg(Ar + tj), xs[tj * 32 + lane]);
+        }
+        if (!LOWER) acc = cdiv<T>(acc, __ldg(Ar + ri));
+        xs[ri * 32 + lane] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  if (act)
+    for (int i = warp; i < jb; i += 8) B[(size_t)(k0 + i) * ldb + col] = xs[i * 32 + lane];
+}
+
+template <class T>
+int gemm_sub(rmat_ctx c, int M, int N, int K, const cplx<T>* A, int lda, const cplx<T>* B,
+             int ldb, cplx<T>* C, int ldc) {
+  if (M <= 0 || N <= 0 || K <= 0) return RMAT_OK;
+  dim3 grid(ceil_div(N, GB_N), ceil_div(M, GB_M));
+  cgemm_sub_kernel<T><<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, B, ldb, C, ldc);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+int panel_ctas_for(rmat_ctx c, int M) {
+  int P = c->panel_ctas_param > 0 ? c->panel_ctas_param : c->sm_count;
+  P = std::min(P, RMAT_MAX_PANEL_CTAS);
+  P = std::min(P, std::max(1, ceil_div(M, 32)));
+  while (ceil_div(M, P) > MAX_RPC) ++P;
+  return P;
+}
+
+template <class T>
+int launch_panel(rmat_ctx c, cplx<T>* A, int ld, int k0, int n, int jb, int* ipiv) {
+  const int M = n - k0;
+  const int P = panel_ctas_for(c, M);
+  const int rpc = ceil_div(M, P);
+  const size_t smem = (size_t)(RMAT_MAX_NB + rpc) * sizeof(cplx<T>);
+  static bool attr_set[2] = {false, false};
+  auto kern = panel_kernel<T>;
+  if (!attr_set[sizeof(T) == 8]) {
+    RMAT_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((RMAT_MAX_NB + MAX_RPC) * sizeof(cplx<T>))));
+    attr_set[sizeof(T) == 8] = true;
+  }
+  RMAT_CU(cudaMemsetAsync(c->ps.bar, 0, sizeof(unsigned), c->stream));
+  PanelScratch ps = c->ps;
+  long long spin = c->spin_limit;
+  int* stat = c->dstat;
+  void* args[] = {&A, &ld, (void*)&k0, (void*)&n, (void*)&jb, &ipiv, &stat, &ps, (void*)&rpc, &spin};
+  RMAT_CU(cudaLaunchCooperativeKernel((const void*)kern, dim3(P), dim3(PANEL_THREADS), args, smem,
+                                      c->stream));
+  c->launches++;
+  return RMAT_OK;
+}
+
+template <class T>
+int set_trsm_attrs() {
+  static bool done = false;
+  if (done) return RMAT_OK;
+  const int smem_max = (int)((size_t)RMAT_MAX_NB * 32 * sizeof(cplx<T>));
+  RMAT_CU(cudaFuncSetAttribute(trsm_block_rhs_kernel<T, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  RMAT_CU(cudaFuncSetAttribute(trsm_block_rhs_kernel<T, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  done = true;
+  return RMAT_OK;
+}
+
+template <class T>
+int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool tensor) {
+  using C2 = cplx<T>;
+  C2* A = reinterpret_cast<C2*>(Av);
+  if (nb < 1 || nb > RMAT_MAX_NB || (sizeof(T) == 8 && nb > 128)) return RMAT_ESTATE;
+  RMAT_CHECK(set_trsm_attrs<T>());
+  RMAT_CU(cudaMemsetAsync(ipiv, 0xff, (size_t)n * sizeof(int), c->stream));  // -1: "not pivoted"
+  for (int k0 = 0; k0 < n; k0 += nb) {
+    const int jb = std::min(nb, n - k0);
+    RMAT_CHECK(launch_panel<T>(c, A, ld, k0, n, jb, ipiv));
+    const int rest = n - k0 - jb;
+    if (rest <= 0) continue;
+    // G3: interchanges on the trailing columns, then U12 = L11^-1 A12
+    rhs_swap_kernel<T><<<ceil_div(rest, 128), 128, 0, c->stream>>>(A + k0 + jb, ld, rest, k0, jb,
+                                                                     n, ipiv, c->dstat);
+    trsm_block_rhs_kernel<T, true><<<ceil_div(rest, 32), 256, (size_t)jb * 32 * sizeof(C2),
+                                     c->stream>>>(A, ld, k0, jb, A + k0 + jb, ld, rest);
+    c->launches += 2;
+    RMAT_CU(cudaGetLastError());
+    if (tensor && sizeof(T) == 4) {
+      const size_t plane = (size_t)n * RMAT_MAX_NB;
+      const int kpad = (int)round_up(jb, 32);
+      split_u12_kernel<<<dim3(ceil_div(rest, 32), kpad / 32), 256, 0, c->stream>>>(
+          reinterpret_cast<const float2*>(A), ld, k0, jb, n, c->Bpl, plane);
+      split_l21_kernel<<<ceil_div((long long)rest * 32, 256), 256, 0, c->stream>>>(
+          reinterpret_cast<const float2*>(A), ld, k0, jb, n, c->Apl, plane);
+      c->launches += 2;
+      RMAT_CU(cudaGetLastError());
+      RMAT_CHECK(launch_trailing_tc(c, reinterpret_cast<float2*>(A), ld, k0, jb, n));
+    } else {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (c->timing) {
+        e0 = rmat_event(c);
+        e1 = rmat_event(c);
+        RMAT_CU(cudaEventRecord(e0, c->stream));
+      }
+      RMAT_CHECK(gemm_sub<T>(c, rest, rest, jb, A + (size_t)(k0 + jb) * ld + k0, ld,
+                             A + (size_t)k0 * ld + k0 + jb, ld, A + (size_t)(k0 + jb) * ld + k0 + jb,
+                             ld));
+      if (c->timing) {
+        RMAT_CU(cudaEventRecord(e1, c->stream));
+        c->tu_events.push_back({e0, e1});
+      }
+      c->tu_launches++;
+      c->tu_flops += 8.0 * rest * (double)rest * jb;
+    }
+  }
+  return RMAT_OK;
+}
+
+template <class T>
+int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const int* ipiv, int nb, void* Bv,
+                 int ldb, int nrhs) {
+  using C2 = cplx<T>;
+  const C2* A = reinterpret_cast<const C2*>(Av);
+  C2* B = reinterpret_cast<C2*>(Bv);
+  RMAT_CHECK(set_trsm_attrs<T>());
+  const int gx = ceil_div(nrhs, 32);
+  // forward: replay each panel's interchanges, then L11 solve and update below
+  for (int k0 = 0; k0 < n; k0 += nb) {
+    const int jb = std::min(nb, n - k0);
+    rhs_swap_kernel<T><<<ceil_div(nrhs, 128), 128, 0, c->stream>>>(B, ldb, nrhs, k0, jb, n, ipiv,
+                                                                     c->dstat);
+    trsm_block_rhs_kernel<T, true><<<gx, 256, (size_t)jb * 32 * sizeof(C2), c->stream>>>(
+        A, ld, k0, jb, B, ldb, nrhs);
+    c->launches += 2;
+    RMAT_CU(cudaGetLastError());
+    RMAT_CHECK(gemm_sub<T>(c, n - k0 - jb, nrhs, jb, A + (size_t)(k0 + jb) * ld + k0, ld,
+                           B + (size_t)k0 * ldb, ldb, B + (size_t)(k0 + jb) * ldb, ldb));
+  }
+  // backward: U11 solve, then update the rows above (right-looking)
+  const int last = ((n - 1) / nb) * nb;
+  for (int k0 = last; k0 >= 0; k0 -= nb) {
+    const int jb = std::min(nb, n - k0);
+    trsm_block_rhs_kernel<T, false><<<gx, 256, (size_t)jb * 32 * sizeof(C2), c->stream>>>(
+        A, ld, k0, jb, B, ldb, nrhs);
+    c->launches++;
+    RMAT_CU(cudaGetLastError());
+    RMAT_CHECK(gemm_sub<T>(c, k0, nrhs, jb, A + k0, ld, B + (size_t)k0 * ldb, ldb, B, ldb));
+  }
+  return RMAT_OK;
+}
+
+template int lu_factor_dev<float>(rmat_ctx, void*, int, int, int*, int, bool);
+template int lu_factor_dev<double>(rmat_ctx, void*, int, int, int*, int, bool);
+template int lu_solve_dev<float>(rmat_ctx, const void*, int, int, const int*, int, void*, int, int);
+template int lu_solve_dev<double>(rmat_ctx, const void*, int, int, const int*, int, void*, int, int);
+
+int gemm_sub_c128(rmat_ctx c, int M, int N, int K, const double2* A, int lda, const double2* B,
+                  int ldb, double2* C, int ldc) {
+  return gemm_sub<double>(c, M, N, K, A, lda, B, ldb, C, ldc);
+}

@@ -1,0 +1,283 @@
+// G7/G8: FP64 residual and refinement update (Sec. 3.2; Sec. 3.4 step 7).
+//
+// The paper forms r = b - M x in double precision on the host (dense ZGEMM,
+// 8 N^2 nrhs flops).  Here the residual of an assembled problem is formed on
+// the device from the block structure of Eq. (block_structure):
+//   r[(al,i),be] = delta_{al be} f_i(a) - sum_j K[i][j] X[(al,j),be]
+//                  - sum_al' W_i[al][al'] X[(al',i),be]
+// with K = hm T0 - hm (B/a) f f^T (nlag x nlag, real) and W_i the full local
+// coupling at mesh point i (potential plus centrifugal/threshold/-E diagonal):
+// 4 nlag^2 nch nrhs + 8 nch^2 nlag nrhs flops instead of 8 N^2 nrhs, and no
+// N x N matrix in FP64.  A loaded dense system uses the dense FP64 product.
+// All solution/residual arrays here are row-major N x nrhs.
+#include <algorithm>
+
+#include "cplx.cuh"
+#include "rmat_internal.h"
+
+namespace {
+
+// r = Phi - K X  (one CTA per (channel, 32 right-hand sides); warps over mesh rows)
+__global__ void __launch_bounds__(256)
+resid_kinetic_kernel(double2* __restrict__ R, const double2* __restrict__ X, int nrhs, int nlag,
+                     const double* __restrict__ K, const double* __restrict__ fa) {
+  const int al = blockIdx.y;
+  const int be = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int warp = threadIdx.x >> 5;
+  if (be >= nrhs) return;
+  const double2* Xa = X + (size_t)al * nlag * nrhs + be;
+  for (int i = warp; i < nlag; i += 8) {
+    const double* Ki = K + (size_t)i * nlag;
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < nlag; ++j) {
+      const double k = __ldg(Ki + j);
+      const double2 x = Xa[(size_t)j * nrhs];
+      sr = fma(k, x.x, sr);
+      si = fma(k, x.y, si);
+    }
+    const double phi = (al == be) ? fa[i] : 0.0;
+    R[((size_t)al * nlag + i) * nrhs + be] = make_double2(phi - sr, -si);
+  }
+}
+
+// r -= W_i X_i at every mesh point: complex FP64 GEMM (nch x nch) x (nch x nrhs)
+// per point; 32 x 32 output tile per CTA, 16-deep K chunks in shared memory.
+__global__ void __launch_bounds__(256)
+resid_coupling_kernel(double2* __restrict__ R, const double2* __restrict__ X, int nrhs, int nlag,
+                      int nch, const double2* __restrict__ W) {
+  __shared__ double2 Ws[16][33];
+  __shared__ double2 Xs[16][32];
+  const int i = blockIdx.z;
+  const int a0 = blockIdx.y * 32, b0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const double2* Wi = W + (size_t)i * nch * nch;
+  double2 acc[2][2];
+  for (int p = 0; p < 2; ++p)
+    for (int q = 0; q < 2; ++q) acc[p][q] = make_double2(0, 0);
+  for (int k0 = 0; k0 < nch; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+      const int kk = e & 15, aa = e >> 4;  // W row a0+aa, column k0+kk
+      const int ga = a0 + aa, gk = k0 + kk;
+      Ws[kk][aa] = (ga < nch && gk < nch) ? Wi[(size_t)ga * nch + gk] : make_double2(0, 0);
+      const int kb = e >> 5, bb = e & 31;  // X row (k0+kb, i), column b0+bb
+      const int gk2 = k0 + kb, gb = b0 + bb;
+      Xs[kb][bb] = (gk2 < nch && gb < nrhs) ? X[((size_t)gk2 * nlag + i) * nrhs + gb]
+                                           : make_double2(0, 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double2 w[2], x[2];
+      w[0] = Ws[kk][ty];
+      w[1] = Ws[kk][ty + 16];
+      x[0] = Xs[kk][tx];
+      x[1] = Xs[kk][tx + 16];
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) cadd_mul<double>(acc[p][q], w[p], x[q]);
+    }
+    __syncthreads();
+  }
+  for (int p = 0; p < 2; ++p) {
+    const int ga = a0 + ty + 16 * p;
+    if (ga >= nch) continue;
+    for (int q = 0; q < 2; ++q) {
+      const int gb = b0 + tx + 16 * q;
+      if (gb >= nrhs) continue;
+      double2* r = R + ((size_t)ga * nlag + i) * nrhs + gb;
+      double2 v = *r;
+      v.x -= acc[p][q].x;
+      v.y -= acc[p][q].y;
+      *r = v;
+    }
+  }
+}
+
+// max |r| (bit pattern of a non-negative double is monotone) and r -> solve precision
+template <class T>
+__global__ void resid_norm_convert_kernel(const double2* __restrict__ R, size_t total,
+                                          cplx<T>* __restrict__ Bw,
+                                          unsigned long long* __restrict__ red) {
+  double m = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double2 z = R[e];
+    m = fmax(m, hypot(z.x, z.y));
+    Bw[e] = to_c(z, T());
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) atomicMax(red, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+__global__ void absmax_kernel(const double2* __restrict__ v, size_t total,
+                              unsigned long long* __restrict__ red) {
+  double m = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x)
+    m = fmax(m, hypot(v[e].x, v[e].y));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) atomicMax(red, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+template <class T>
+__global__ void x_update_kernel(double2* __restrict__ X, const cplx<T>* __restrict__ D,
+                                size_t total) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double2 d = to_d(D[e]);
+    double2 x = X[e];
+    x.x += d.x;
+    x.y += d.y;
+    X[e] = x;
+  }
+}
+
+template <class T>
+__global__ void x_from_w_kernel(double2* __restrict__ X, const cplx<T>* __restrict__ D,
+                                size_t total) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x)
+    X[e] = to_d(D[e]);
+}
+
+// right-hand sides into the solve buffer: surface terms (assembled) or B (dense)
+template <class T>
+__global__ void w_from_phi_kernel(cplx<T>* __restrict__ Bw, int N, int nrhs, int nlag,
+                                  const double* __restrict__ fa, const double2* __restrict__ B64) {
+  const size_t total = (size_t)N * nrhs;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(e / nrhs), be = (int)(e % nrhs);
+    double2 z;
+    if (B64) {
+      z = B64[e];
+    } else {
+      const int al = row / nlag, i = row - al * nlag;
+      z = make_double2(al == be ? fa[i] : 0.0, 0.0);
+    }
+    Bw[e] = to_c(z, T());
+  }
+}
+
+// row-major N x nrhs (internal) -> column-major N x nrhs with leading dimension ldx
+__global__ void x_to_colmajor_kernel(const double2* __restrict__ X, int N, int nrhs,
+                                     double2* __restrict__ Xo, int ldx) {
+  __shared__ double2 tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int k = ty; k < 32; k += 8) {
+    const int rr = r0 + k, cc = c0 + tx;
+    tile[k][tx] = (rr < N && cc < nrhs) ? X[(size_t)rr * nrhs + cc] : make_double2(0, 0);
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int cc = c0 + k, rr = r0 + tx;
+    if (rr < N && cc < nrhs) Xo[rr + (size_t)ldx * cc] = tile[tx][k];
+  }
+}
+
+int grid_for(rmat_ctx c, size_t total) {
+  return std::max(1, (int)std::min<size_t>((size_t)c->sm_count * 8, (total + 255) / 256));
+}
+
+}  // namespace
+
+// r = Phi - C X (FP64) and max|r| -> red[0]; r is also written to Bw in the
+// factor precision for the correction solve.
+int launch_residual(rmat_ctx c, double*) {
+  const int N = c->N, nrhs = c->nrhs;
+  const size_t total = (size_t)N * nrhs;
+  RMAT_CU(cudaMemsetAsync(c->red, 0, sizeof(unsigned long long), c->stream));
+  if (c->kind == 1) {
+    dim3 gk(ceil_div(nrhs, 32), c->nch);
+    resid_kinetic_kernel<<<gk, 256, 0, c->stream>>>(c->Rres, c->X, nrhs, c->nlag, c->Kmat, c->fa);
+    dim3 gc(ceil_div(nrhs, 32), ceil_div(c->nch, 32), c->nlag);
+    resid_coupling_kernel<<<gc, 256, 0, c->stream>>>(c->Rres, c->X, nrhs, c->nlag, c->nch, c->Wpt);
+    c->launches += 2;
+  } else {
+    RMAT_CU(cudaMemcpyAsync(c->Rres, c->B64, total * sizeof(double2), cudaMemcpyDeviceToDevice,
+                            c->stream));
+    RMAT_CHECK(gemm_sub_c128(c, N, nrhs, N, c->A64, N, c->X, nrhs, c->Rres, nrhs));
+  }
+  RMAT_CU(cudaGetLastError());
+  if (c->precision == RMAT_C128)
+    resid_norm_convert_kernel<double><<<grid_for(c, total), 256, 0, c->stream>>>(
+        c->Rres, total, reinterpret_cast<double2*>(c->Bw), c->red);
+  else
+    resid_norm_convert_kernel<float><<<grid_for(c, total), 256, 0, c->stream>>>(
+        c->Rres, total, reinterpret_cast<float2*>(c->Bw), c->red);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+int launch_update(rmat_ctx c) {
+  const size_t total = (size_t)c->N * c->nrhs;
+  if (c->precision == RMAT_C128)
+    x_update_kernel<double><<<grid_for(c, total), 256, 0, c->stream>>>(
+        c->X, reinterpret_cast<const double2*>(c->Bw), total);
+  else
+    x_update_kernel<float><<<grid_for(c, total), 256, 0, c->stream>>>(
+        c->X, reinterpret_cast<const float2*>(c->Bw), total);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+int launch_x_from_w(rmat_ctx c) {
+  const size_t total = (size_t)c->N * c->nrhs;
+  if (c->precision == RMAT_C128)
+    x_from_w_kernel<double><<<grid_for(c, total), 256, 0, c->stream>>>(
+        c->X, reinterpret_cast<const double2*>(c->Bw), total);
+  else
+    x_from_w_kernel<float><<<grid_for(c, total), 256, 0, c->stream>>>(
+        c->X, reinterpret_cast<const float2*>(c->Bw), total);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+int launch_w_from_phi(rmat_ctx c) {
+  const size_t total = (size_t)c->N * c->nrhs;
+  const double2* B64 = (c->kind == 2) ? c->B64 : nullptr;
+  if (c->precision == RMAT_C128)
+    w_from_phi_kernel<double><<<grid_for(c, total), 256, 0, c->stream>>>(
+        reinterpret_cast<double2*>(c->Bw), c->N, c->nrhs, c->nlag, c->fa, B64);
+  else
+    w_from_phi_kernel<float><<<grid_for(c, total), 256, 0, c->stream>>>(
+        reinterpret_cast<float2*>(c->Bw), c->N, c->nrhs, c->nlag, c->fa, B64);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+int launch_x_out(rmat_ctx c, double2* Xo, int ldx) {
+  dim3 grid(ceil_div(c->nrhs, 32), ceil_div(c->N, 32));
+  x_to_colmajor_kernel<<<grid, 256, 0, c->stream>>>(c->X, c->N, c->nrhs, Xo, ldx);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+int launch_absmax(rmat_ctx c, const double2* v, size_t n) {
+  RMAT_CU(cudaMemsetAsync(c->red, 0, sizeof(unsigned long long), c->stream));
+  absmax_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(v, n, c->red);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}

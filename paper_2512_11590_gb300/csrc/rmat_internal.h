@@ -1,0 +1,143 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/rmat.h"
+
+// Maximum CTAs of the cooperative panel kernel (one per SM on GB300: 152).
+#define RMAT_MAX_PANEL_CTAS 256
+// Largest LU block width supported by the panel/TRSM kernels.
+#define RMAT_MAX_NB 256
+
+struct PanelScratch {
+  // barrier counter + candidate slots of the one-barrier-per-column panel
+  unsigned int* bar;   // [1]
+  void* cval;          // [2][RMAT_MAX_PANEL_CTAS] of T
+  int* cidx;           // [2][RMAT_MAX_PANEL_CTAS]
+  void* crow;          // [2][RMAT_MAX_PANEL_CTAS][RMAT_MAX_NB] of complex T
+  void* trow;          // [2][RMAT_MAX_NB] of complex T
+};
+
+// Device status words written by kernels (read back by the host).
+enum { ST_INFO = 0, ST_TIMEOUT = 1, ST_BADARG = 2, ST_COUNT = 8 };
+
+struct rmat_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  // parameters
+  int nb_param = 0;
+  int panel_ctas_param = 0;
+  long long spin_limit = 20000000LL;   // ~ seconds of polling
+  int timing = 0;
+
+  // problem description
+  int kind = 0;          // 0 none, 1 assembled, 2 dense
+  int precision = RMAT_C128;
+  int N = 0, nrhs = 0, nch = 0, nlag = 0;
+  int ld = 0;            // leading dimension (row-major) of the working matrix
+  int nb = 0;            // LU block width in use
+  double a = 0, hm = 0, bloch_B = 0, E = 0;
+  std::vector<int> l;
+  std::vector<double> thresh;
+  std::vector<double> f_a_host;
+  double phi_max = 1.0;  // max |Phi| (denominator of the relative residual)
+
+  // device buffers (capacity-managed)
+  void* C = nullptr;       size_t C_cap = 0;        // working matrix, complex T, row-major N x ld
+  double2* A64 = nullptr;  size_t A64_cap = 0;      // dense loaded system in complex128 (row-major)
+  double2* B64 = nullptr;  size_t B64_cap = 0;      // dense loaded right-hand sides (row-major N x nrhs)
+  int* ipiv = nullptr;     size_t ipiv_cap = 0;
+  double* Kmat = nullptr;  size_t Kmat_cap = 0;     // hm*T0 - hm*(B/a) f f^T  [nlag*nlag]
+  double* T0 = nullptr;    size_t T0_cap = 0;       // T0 [nlag*nlag]
+  double* rmesh = nullptr; size_t rmesh_cap = 0;    // r_i
+  double* fa = nullptr;    size_t fa_cap = 0;       // f_i(a)
+  int* l_d = nullptr;      size_t l_cap = 0;
+  double* th_d = nullptr;  size_t th_cap = 0;
+  double2* Wpt = nullptr;  size_t Wpt_cap = 0;      // [nlag][nch][nch] point coupling incl. diagonal
+  double2* X = nullptr;    size_t X_cap = 0;        // FP64 solution, row-major N x nrhs
+  double2* Rres = nullptr; size_t Rres_cap = 0;     // FP64 residual, row-major N x nrhs
+  void* Bw = nullptr;      size_t Bw_cap = 0;       // solve work in the factor precision
+  float* Apl = nullptr;    size_t Apl_cap = 0;      // tensor A operand planes (L21 split)
+  float* Bpl = nullptr;    size_t Bpl_cap = 0;      // tensor B operand planes (U12^T split)
+  double2* Rint = nullptr; size_t Rint_cap = 0;     // R-matrix (row-major nch x nch)
+  double2* Zbuf = nullptr; size_t Zbuf_cap = 0;     // matching system (nch x nch + nch x nopen)
+  int* zpiv = nullptr;     size_t zpiv_cap = 0;
+  int* open_d = nullptr;   size_t open_cap = 0;
+  unsigned long long* red = nullptr;                // reduction scratch [8]
+  PanelScratch ps{};
+  void* ps_mem = nullptr;
+  int* dstat = nullptr;    // [ST_COUNT]
+  int* hstat = nullptr;    // pinned mirror
+
+  bool assembled = false, factored = false, solved = false;
+
+  // statistics
+  long long launches = 0, tu_launches = 0;
+  double tu_flops = 0, tu_ms = 0;
+  double stage_ms[5] = {-1, -1, -1, -1, -1};
+  cudaEvent_t stage_ev[5][2] = {};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tu_events;
+  size_t ev_next = 0;
+};
+
+// --- helpers implemented in api.cu ---------------------------------------
+int rmat_grow(rmat_ctx c, void** p, size_t* cap, size_t bytes);
+cudaEvent_t rmat_event(rmat_ctx c);
+
+// --- host mesh (mesh.cpp) --------------------------------------------------
+int rmat_mesh_host(int nlag, double a, double* x, double* omx, double* lam, double* r,
+                   double* f_a, double* T0);
+
+// --- kernel launchers ------------------------------------------------------
+// assemble.cu
+int launch_assemble(rmat_ctx c, const double2* V, double E);
+int launch_point_coupling(rmat_ctx c, const double2* V, double E);
+int launch_load_dense(rmat_ctx c, const double2* A, int lda, const double2* B, int ldb);
+// lu.cu
+template <class T>
+int lu_factor_dev(rmat_ctx c, void* A, int n, int ld, int* ipiv, int nb, bool tensor);
+template <class T>
+int lu_solve_dev(rmat_ctx c, const void* A, int n, int ld, const int* ipiv, int nb,
+                 void* B, int ldb, int nrhs);
+// gemm_tc.cu
+int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n);
+int tc_prepare(rmat_ctx c, int n, int nb);
+// lu.cu (SIMT complex GEMM C -= A B, row-major)
+int gemm_sub_c128(rmat_ctx c, int M, int N, int K, const double2* A, int lda, const double2* B,
+                  int ldb, double2* C, int ldc);
+int panel_ctas_for(rmat_ctx c, int M);
+// residual.cu
+int launch_residual(rmat_ctx c, double* relres_dev_unused);
+int launch_x_out(rmat_ctx c, double2* Xo, int ldx);
+int launch_absmax(rmat_ctx c, const double2* v, size_t n);
+int launch_update(rmat_ctx c);
+int launch_x_from_w(rmat_ctx c);
+int launch_w_from_phi(rmat_ctx c);
+// collision.cu
+int launch_collision(rmat_ctx c, double2* R_dev, double2* U_dev, int nopen);
+size_t collision_workspace_bytes(int nch);
+// mesh.cpp: K = hm*T0 - (hm*(B/a)) * (f_i*f_j) in IEEE double, no contraction
+void rmat_kinetic_table(int nlag, double hm, double s1, const double* T0, const double* fa, double* K);
+
+#define RMAT_CU(x)                                  \
+  do {                                              \
+    cudaError_t e__ = (x);                          \
+    if (e__ != cudaSuccess) return RMAT_ECUDA;      \
+  } while (0)
+
+#define RMAT_CHECK(x)                               \
+  do {                                              \
+    int s__ = (x);                                  \
+    if (s__ != RMAT_OK) return s__;                 \
+  } while (0)
+
+static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+static inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }

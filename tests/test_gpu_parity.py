@@ -1,0 +1,136 @@
+"""GPU parity against the CPU oracle, through the C ABI (-m gpu).
+
+Tolerances (max|dU| / max|U_truth|, truth = oracle FP64 LU + double-double
+refinement): 1e-12 for the complex128 path after FP64 refinement, 1e-10 for
+the complex64 paths after FP64 refinement (the paper's FP64-vs-mixed targets).
+The solution X and the R-matrix are held to the same bounds.
+"""
+import numpy as np
+import pytest
+
+import cc_problems as cp
+from oracle import oracle_solve
+from rmat_gpu import relerr, run_dense, run_problem
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-10, 2: 1e-10}
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_2512_11590_gb300 as mod
+    mod.lib()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(g):
+    import torch
+    torch.cuda.set_device(0)
+    h = g.rmat_create(0, torch.cuda.current_stream().cuda_stream)
+    yield h
+    g.rmat_destroy(h)
+
+
+_TRUTH = {}
+
+
+def truth(p, key):
+    if key not in _TRUTH:
+        _TRUTH[key] = oracle_solve(p, refine_steps=3)
+    return _TRUTH[key]
+
+
+PRECS = [0, 2]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_config1_vs_oracle(g, ctx, prec):
+    p = cp.config1()
+    ref = truth(p, "c1")
+    out = run_problem(ctx, p, prec, max_refine=30, tol=1e-14)
+    assert out["info"] == 0
+    assert out["nopen"] == ref["nopen"] == 4
+    for k in ("U", "R", "X"):
+        e = relerr(out[k], ref[k])
+        assert e < TOL[prec], (k, e)
+    lu_only = run_problem(ctx, p, prec, max_refine=0)
+    e0 = relerr(lu_only["U"], ref["U"])
+    assert e0 < (1e-9 if prec == 0 else 1e-3)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nch,nlag,nb", [(5, 37, 32), (3, 50, 64), (7, 23, 32), (1, 40, 32)])
+def test_ragged_multi_panel(g, ctx, prec, nch, nlag, nb):
+    p = cp.make_problem(1000 + nch * nlag, nch, nlag, 12.0)
+    ref = truth(p, ("rag", nch, nlag))
+    out = run_problem(ctx, p, prec, max_refine=30, tol=1e-14, nb=nb)
+    for k in ("U", "R"):
+        assert relerr(out[k], ref[k]) < TOL[prec], k
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_closed_channels(g, ctx, prec):
+    p = cp.config1()
+    p.E = 3.0
+    p.thresh = np.array([0.0, 1.0, 4.0, 4.5])
+    ref = truth(p, "closed")
+    out = run_problem(ctx, p, prec, max_refine=30, tol=1e-14)
+    assert out["nopen"] == 2
+    assert relerr(out["U"], ref["U"]) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_nch16_nlag100_many_tiles(g, ctx, prec):
+    p = cp.config2(16)                      # N = 1600, 16 right-hand sides
+    ref = truth(p, "c2-16")
+    out = run_problem(ctx, p, prec, max_refine=30, tol=1e-14)
+    for k in ("U", "R"):
+        assert relerr(out[k], ref[k]) < TOL[prec], k
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_dense_pivoting_vs_lapack(g, ctx, prec):
+    A, B = cp.random_dense(77, 300, nrhs=3)
+    Xe = np.linalg.solve(A, B)
+    out = run_dense(ctx, A, B, prec, max_refine=20, tol=1e-15, nb=64)
+    assert relerr(out["X"], Xe) < 1e-12
+
+
+def test_prescribed_condition_refinement(g, ctx):
+    A, B, _ = cp.prescribed_kappa_hermitian(3, 256, 1e6, nrhs=2)
+    Xe = np.linalg.solve(A, B)
+    plain = run_dense(ctx, A, B, 2, max_refine=0)
+    ref = run_dense(ctx, A, B, 2, max_refine=30, tol=1e-15)
+    assert ref["iters"] >= 1
+    assert relerr(ref["X"], Xe) < 1e-11 < relerr(plain["X"], Xe)
+
+
+def test_exactly_singular_reports_info(g, ctx):
+    A, B = cp.random_dense(5, 64, nrhs=1)
+    A[:, 10] = 0.0
+    out = run_dense(ctx, A, B, 0, nb=32)
+    assert out["factor_status"] == g.RMAT_ESINGULAR and out["info"] == 11
+
+
+def test_bounded_panel_wait_times_out_cleanly(g, ctx):
+    """A panel barrier with a 1-poll limit gives up and reports RMAT_ETIMEOUT;
+    the context stays usable afterwards (no hang, no fault)."""
+    import torch
+    A, B = cp.random_dense(9, 2048, nrhs=1)
+    g.rmat_set_param(ctx, g.RMAT_PARAM_PANEL_CTAS, 8)
+    g.rmat_set_param(ctx, g.RMAT_PARAM_SPIN_LIMIT, 1)
+    try:
+        Ad = torch.from_numpy(np.asfortranarray(A).ravel(order="F")).cuda()
+        Bd = torch.from_numpy(np.asfortranarray(B).ravel(order="F")).cuda()
+        g.rmat_load_dense(ctx, 2048, 1, Ad.data_ptr(), 2048, Bd.data_ptr(), 2048, 0)
+        import ctypes as ct
+        info = ct.c_int(0)
+        s = g.lib().rmat_factor(ct.c_void_p(ctx), ct.byref(info))
+        assert s == g.RMAT_ETIMEOUT
+    finally:
+        g.rmat_set_param(ctx, g.RMAT_PARAM_SPIN_LIMIT, 20000000)
+        g.rmat_set_param(ctx, g.RMAT_PARAM_PANEL_CTAS, 0)
+    out = run_dense(ctx, A[:200, :200], B[:200], 0)
+    assert relerr(out["X"], np.linalg.solve(A[:200, :200], B[:200])) < 1e-12
