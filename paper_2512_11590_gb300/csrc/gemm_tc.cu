@@ -1,7 +1,420 @@
-// G4 (tensor path): trailing update C22 -= L21 U12 on tcgen05 tensor cores.
-// Placeholder until the tcgen05 kernel lands: the tensor precision reports an
-// error instead of silently running another kernel.
+// G4 (tensor path): trailing update C22 -= L21 U12 on the tcgen05 tensor cores.
+//
+// The paper runs the single-precision factorisation's updates in FP32
+// (cusolverDnCgetrf, Sec. 3.4).  Here each complex product is formed from TF32
+// tensor-core products with FP32 accumulation in tensor memory:
+//   x = x_hi + x_lo,  x_hi = tf32(x),  x_lo = x - x_hi          (per real plane)
+//   a*b ~= a_hi b_hi + a_hi b_lo + a_lo b_hi                    (3 products)
+//   Re += Ar Br - Ai Bi,   Im += Ar Bi + Ai Br                  (4 real GEMMs)
+// i.e. 12 TF32 MMAs per K-step into two FP32 accumulators (re, im).  The
+// -Ai Bi terms use the instruction descriptor's negate-A bit.
+//
+// Operand planes (written by split_l21_kernel / split_u12_kernel in lu.cu) are
+// K-major fp32 [row][K] with a 256-float row stride: A rows = L21 rows, B rows =
+// U12 columns.  Tile 128 x 256 per CTA (cta_group::1, M=128, N=256): the re and
+// im accumulators take all 512 TMEM columns.  K-steps of 8 (32-byte rows,
+// SWIZZLE_32B) flow through a 4-stage TMA -> mbarrier pipeline.
+//
+// Roles (192 threads, one CTA per SM, persistent over tiles):
+//   warp 0      TMA producer (one elected lane)
+//   warp 1      TMEM allocator + MMA issuer (one elected lane)
+//   warps 2..5  epilogue: tcgen05.ld of re/im rows, C -= acc in global memory
+// Every wait is bounded (~2 s of globaltimer); on expiry the kernel raises an
+// error word, lets its issued copies/MMAs drain (bounded), frees TMEM, returns.
+#include <cuda.h>
+
+#include <cstring>
+
 #include "rmat_internal.h"
 
-int launch_trailing_tc(rmat_ctx, float2*, int, int, int, int) { return RMAT_ESTATE; }
-int tc_prepare(rmat_ctx, int, int) { return RMAT_OK; }
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 8, TC_STAGES = 4;
+constexpr int TC_THREADS = 192;
+constexpr uint32_t A_PLANE_BYTES = TC_BM * TC_BK * 4;                              // 4 KB
+constexpr uint32_t B_PLANE_BYTES = TC_BN * TC_BK * 4;                              // 8 KB
+constexpr uint32_t STAGE_BYTES = 4 * A_PLANE_BYTES + 4 * B_PLANE_BYTES;            // 48 KB
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + 1024 + 256;
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
+
+struct TcMaps {
+  CUtensorMap a[4];  // L21 planes: re_hi, re_lo, im_hi, im_lo
+  CUtensorMap b[4];  // U12^T planes
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on an mbarrier phase; false on timeout or when another role aborted.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255) == 0) {
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > TC_WAIT_NS) return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// K-major operand, 32-byte rows, SWIZZLE_32B: 8-row groups 256 B apart.
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused when K fits the atom)
+  d |= (uint64_t)(256 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                   // descriptor version (tcgen05)
+  d |= (uint64_t)6 << 61;                   // layout: SWIZZLE_32B
+  return d;
+}
+// kind::tf32 instruction descriptor: D f32, A/B tf32, K-major, N = 256, M = 128.
+__host__ __device__ constexpr uint32_t idesc_tf32(bool negA) {
+  return (1u << 4)               // D format f32
+         | (2u << 7)             // A format tf32
+         | (2u << 10)            // B format tf32
+         | ((negA ? 1u : 0u) << 13)
+         | ((uint32_t)(TC_BN >> 3) << 17)
+         | ((uint32_t)(TC_BM >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Product p of the 12 per K-step (p = 6*acc + 3*part + t):
+//   acc 0 (re): part 0 Ar*Br, part 1 -Ai*Bi;  acc 1 (im): part 0 Ar*Bi, part 1 Ai*Br
+//   t: 0 hi*hi, 1 hi*lo, 2 lo*hi.   Planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo.
+__device__ __forceinline__ void product(int p, int& qa, int& qb, int& acc, int& neg) {
+  acc = p / 6;
+  const int part = (p % 6) / 3, t = p % 3;
+  const int a_im = part, b_im = acc == 0 ? part : 1 - part;
+  qa = 2 * a_im + (t == 2);
+  qb = 2 * b_im + (t == 1);
+  neg = (acc == 0 && part == 1);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_update_kernel(const __grid_constant__ TcMaps maps, float2* __restrict__ C, int ldc, int M,
+                 int Nn, int K, int rowA0, int rowB0, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  unsigned char* stages = smem;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + TC_STAGES * STAGE_BYTES);
+  // bars[0..3] full, [4..7] empty, [8] tmem_full, [9] tmem_empty
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mt = (M + TC_BM - 1) / TC_BM;
+  const int nt = (Nn + TC_BN - 1) / TC_BN;
+  const int ntiles = mt * nt;
+  const int ksteps = K / TC_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[4 + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[8]), 1);
+    mbar_init(smem_u32(&bars[9]), 4);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int m0 = (tile % mt) * TC_BM, n0 = (tile / mt) * TC_BN;
+        for (int ks = 0; ks < ksteps; ++ks, ++it) {
+          const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
+          if (!mbar_wait(smem_u32(&bars[4 + s]), ph ^ 1, abort_flag)) { ok = false; break; }
+          const uint32_t full = smem_u32(&bars[s]);
+          mbar_expect_tx(full, STAGE_BYTES);
+          const uint32_t st = smem_u32(stages + s * STAGE_BYTES);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            tma_load_2d(st + q * A_PLANE_BYTES, &maps.a[q], ks * TC_BK, rowA0 + m0, full);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            tma_load_2d(st + 4 * A_PLANE_BYTES + q * B_PLANE_BYTES, &maps.b[q], ks * TC_BK,
+                        rowB0 + n0, full);
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(err, 2);
+      }
+      // drain: the last (up to TC_STAGES) issued stages must land before exit
+      for (uint32_t k = (it > TC_STAGES ? it - TC_STAGES : 0); k < it; ++k) {
+        const unsigned long long t0 = gtimer();
+        while (!mbar_try(smem_u32(&bars[k % TC_STAGES]), (k / TC_STAGES) & 1))
+          if (gtimer() - t0 > TC_WAIT_NS) break;
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------- MMA issuer -------------------------------
+    if (lane == 0) {
+      uint32_t it = 0, tcount = 0;
+      bool ok = true;
+      uint32_t idesc[2] = {idesc_tf32(false), idesc_tf32(true)};
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tcount) {
+        if (tcount > 0 && !mbar_wait(smem_u32(&bars[9]), (tcount - 1) & 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        for (int ks = 0; ks < ksteps; ++ks, ++it) {
+          const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
+          if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag)) { ok = false; break; }
+          fence_after();
+          const uint32_t st = smem_u32(stages + s * STAGE_BYTES);
+#pragma unroll
+          for (int p = 0; p < 12; ++p) {
+            int qa, qb, acc, neg;
+            product(p, qa, qb, acc, neg);
+            const uint64_t ad = sdesc_sw32(st + qa * A_PLANE_BYTES);
+            const uint64_t bd = sdesc_sw32(st + 4 * A_PLANE_BYTES + qb * B_PLANE_BYTES);
+            const uint32_t first = (ks == 0) && (p == 0 || p == 6);
+            mma_tf32(tmem + acc * TC_BN, ad, bd, idesc[neg], first ? 0u : 1u);
+          }
+          mma_commit(smem_u32(&bars[4 + s]));  // frees the stage once these MMAs have read it
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bars[8]));        // accumulators ready for the epilogue
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(err, 2);
+        // let every MMA issued so far finish before TMEM is released
+        mma_commit(smem_u32(&bars[8]));
+        const unsigned long long t0 = gtimer();
+        while (!mbar_try(smem_u32(&bars[8]), tcount & 1))
+          if (gtimer() - t0 > TC_WAIT_NS) break;
+      }
+    }
+  } else {
+    // -------------------------------- epilogue --------------------------------
+    const int quad = warp & 3;               // TMEM lane quadrant this warp may access
+    const int row = quad * 32 + lane;
+    uint32_t tcount = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
+      const int m0 = (tile % mt) * TC_BM, n0 = (tile / mt) * TC_BN;
+      if (!mbar_wait(smem_u32(&bars[8]), tcount & 1, abort_flag)) {
+        *abort_flag = 1;
+        atomicExch(err, 2);
+        break;
+      }
+      fence_after();
+      const int gm = m0 + row;
+      float2* Crow = C + (size_t)gm * ldc + n0;
+#pragma unroll 1
+      for (int ch = 0; ch < TC_BN / 32; ++ch) {
+        float re[32], im[32];
+        const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + ch * 32;
+        tmem_ld32(ta, re);
+        tmem_ld32(ta + TC_BN, im);
+        tmem_wait_ld();
+        if (gm < M) {
+          const int c0 = ch * 32;
+          if (n0 + c0 + 32 <= Nn) {
+            float4* p4 = reinterpret_cast<float4*>(Crow + c0);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              float4 v = p4[k];
+              v.x -= re[2 * k];
+              v.y -= im[2 * k];
+              v.z -= re[2 * k + 1];
+              v.w -= im[2 * k + 1];
+              p4[k] = v;
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+              if (n0 + c0 + k < Nn) {
+                float2 v = Crow[c0 + k];
+                v.x -= re[k];
+                v.y -= im[k];
+                Crow[c0 + k] = v;
+              }
+            }
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars[9]));
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+int make_plane_map(CUtensorMap* m, float* base, int rows, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return RMAT_ECUDA;
+  cuuint64_t dims[2] = {(cuuint64_t)RMAT_MAX_NB, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)RMAT_MAX_NB * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RMAT_OK : RMAT_ECUDA;
+}
+
+struct TcCache {
+  float* apl = nullptr;
+  float* bpl = nullptr;
+  int n = -1;
+  TcMaps maps;
+  bool attr = false;
+};
+TcCache g_tc;
+
+}  // namespace
+
+int tc_prepare(rmat_ctx c, int n, int) {
+  if (g_tc.apl == c->Apl && g_tc.bpl == c->Bpl && g_tc.n == n) return RMAT_OK;
+  const size_t plane = (size_t)n * RMAT_MAX_NB;
+  for (int q = 0; q < 4; ++q) {
+    RMAT_CHECK(make_plane_map(&g_tc.maps.a[q], c->Apl + q * plane, n, TC_BM));
+    RMAT_CHECK(make_plane_map(&g_tc.maps.b[q], c->Bpl + q * plane, n, TC_BN));
+  }
+  g_tc.apl = c->Apl;
+  g_tc.bpl = c->Bpl;
+  g_tc.n = n;
+  return RMAT_OK;
+}
+
+int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n) {
+  const int rest = n - k0 - jb;
+  if (rest <= 0) return RMAT_OK;
+  if (jb % TC_BK) return RMAT_ESTATE;
+  RMAT_CHECK(tc_prepare(c, n, jb));
+  if (!g_tc.attr) {
+    RMAT_CU(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TC_SMEM));
+    g_tc.attr = true;
+  }
+  const int tiles = ceil_div(rest, TC_BM) * ceil_div(rest, TC_BN);
+  const int grid = std::min(tiles, c->sm_count);
+  float2* C22 = A + (size_t)(k0 + jb) * ld + (k0 + jb);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    e0 = rmat_event(c);
+    e1 = rmat_event(c);
+    RMAT_CU(cudaEventRecord(e0, c->stream));
+  }
+  tc_update_kernel<<<grid, TC_THREADS, TC_SMEM, c->stream>>>(g_tc.maps, C22, ld, rest, rest, jb,
+                                                             k0 + jb, k0 + jb, c->dstat + ST_TIMEOUT);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  if (c->timing) {
+    RMAT_CU(cudaEventRecord(e1, c->stream));
+    c->tu_events.push_back({e0, e1});
+  }
+  c->tu_launches++;
+  c->tu_flops += 8.0 * rest * (double)rest * jb;
+  return RMAT_OK;
+}

@@ -48,6 +48,9 @@ def run_dense(ctx, A, B, precision, max_refine=0, tol=0.0, nb=0):
     g.rmat_load_dense(ctx, n, nrhs, Ad.data_ptr(), n, Bd.data_ptr(), n, precision)
     fs, info = g.rmat_factor(ctx)
     X = torch.zeros((nrhs, n), dtype=torch.complex128, device="cuda")
+    if fs != g.RMAT_OK:
+        return {"X": None, "status": None, "iters": 0, "rel": None, "info": info,
+                "factor_status": fs}
     st, iters, rel = g.rmat_solve(ctx, X.data_ptr(), n, max_refine, tol)
     torch.cuda.synchronize()
     return {"X": X.cpu().numpy().T, "status": st, "iters": iters, "rel": rel, "info": info,

@@ -42,7 +42,7 @@ def truth(p, key):
     return _TRUTH[key]
 
 
-PRECS = [0, 2]
+PRECS = [0, 1, 2]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -57,7 +57,7 @@ def test_config1_vs_oracle(g, ctx, prec):
         assert e < TOL[prec], (k, e)
     lu_only = run_problem(ctx, p, prec, max_refine=0)
     e0 = relerr(lu_only["U"], ref["U"])
-    assert e0 < (1e-9 if prec == 0 else 1e-3)
+    assert e0 < (1e-9 if prec == 0 else 1e-2)     # LU alone: FP64 ~ kappa u_64, FP32 ~ kappa u_32
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -99,12 +99,17 @@ def test_dense_pivoting_vs_lapack(g, ctx, prec):
 
 
 def test_prescribed_condition_refinement(g, ctx):
+    """kappa = 1e6 Hermitian system (the paper's Fig. illcond construction):
+    the FP32 factor alone is kappa*u_32-limited; FP64-residual refinement brings
+    the solution to the FP64 level kappa*u_64 of the double-double truth."""
+    from oracle.refine import truth_solve
     A, B, _ = cp.prescribed_kappa_hermitian(3, 256, 1e6, nrhs=2)
-    Xe = np.linalg.solve(A, B)
+    Xe, _ = truth_solve(A, B, steps=2)
     plain = run_dense(ctx, A, B, 2, max_refine=0)
     ref = run_dense(ctx, A, B, 2, max_refine=30, tol=1e-15)
     assert ref["iters"] >= 1
-    assert relerr(ref["X"], Xe) < 1e-11 < relerr(plain["X"], Xe)
+    assert relerr(ref["X"], Xe) < 1e-9
+    assert relerr(plain["X"], Xe) > 1e-7
 
 
 def test_exactly_singular_reports_info(g, ctx):
