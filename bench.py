@@ -134,7 +134,8 @@ class Runner:
         g.rmat_factor(self.ctx, want_info=False)
         st, it, rel = g.rmat_solve(self.ctx, self.X.data_ptr(), p.N, max_refine=30, tol=1e-13)
         g.rmat_collision(self.ctx, self.R.data_ptr(), self.U.data_ptr())
-        self.last = {"status": st, "iters": it, "rel_resid": rel}
+        self.last = {"status": st, "iters": it, "rel_resid": rel,
+                     "history": [float("%.3g" % h) for h in g.rmat_refine_history(self.ctx)]}
 
     def U_host(self):
         n = self.nopen

@@ -66,6 +66,10 @@ extern "C" {
 #define RMAT_PARAM_PANEL_CTAS  2  /* CTAs of the cooperative panel (0 = auto)   */
 #define RMAT_PARAM_SPIN_LIMIT  3  /* polls before a device wait gives up        */
 #define RMAT_PARAM_TIMING      4  /* 1 = record per-stage CUDA events           */
+/* Symmetric diagonal equilibration of assembled problems: the factor is taken of
+ * D C D with D = |diag C|^-1/2 (LAPACK-style scaling; the FP64 residual stays on C).
+ * -1 = default (on for the complex64 precisions, off for RMAT_C128), 0 off, 1 on. */
+#define RMAT_PARAM_EQUILIBRATE 5
 
 typedef struct rmat_ctx_s* rmat_ctx;
 
@@ -185,6 +189,12 @@ int rmat_collision(rmat_ctx ctx, void* R_dev, void* U_dev, int* nopen);
  * n: capacity of out; returns the number of values written (<= 13). */
 int rmat_get_stats(rmat_ctx ctx, double* out, int n);
 int rmat_reset_counters(rmat_ctx ctx);
+
+/* Refinement history of the last rmat_solve: hist[k] = max|r|/max|Phi| measured
+ * before correction k (k = 0 is the residual of the first solve).  Returns the
+ * number of entries available (may exceed n; only min(n, count) are written).
+ * Errors: -1 ctx, -2 hist NULL with n > 0. */
+int rmat_refine_history(rmat_ctx ctx, double* hist, int n);
 
 /* Human-readable name of a status code (static storage). */
 const char* rmat_status_string(int status);

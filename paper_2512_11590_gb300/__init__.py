@@ -34,10 +34,11 @@ RMAT_PARAM_NB = 1
 RMAT_PARAM_PANEL_CTAS = 2
 RMAT_PARAM_SPIN_LIMIT = 3
 RMAT_PARAM_TIMING = 4
+RMAT_PARAM_EQUILIBRATE = 5
 
 EXPORTED = ("rmat_create", "rmat_destroy", "rmat_set_param", "rmat_mesh", "rmat_assemble",
             "rmat_load_dense", "rmat_factor", "rmat_solve", "rmat_collision", "rmat_get_stats",
-            "rmat_reset_counters", "rmat_status_string")
+            "rmat_reset_counters", "rmat_refine_history", "rmat_status_string")
 
 
 class rmat_problem(ct.Structure):
@@ -77,6 +78,7 @@ def lib():
             "rmat_collision": (i, [vp, vp, vp, pi]),
             "rmat_get_stats": (i, [vp, pd, i]),
             "rmat_reset_counters": (i, [vp]),
+            "rmat_refine_history": (i, [vp, pd, i]),
             "rmat_status_string": (ct.c_char_p, [i]),
         }
         for name, (res, args) in sig.items():
@@ -186,3 +188,10 @@ def rmat_get_stats(ctx) -> dict:
 
 def rmat_reset_counters(ctx) -> None:
     _check("rmat_reset_counters", lib().rmat_reset_counters(ct.c_void_p(ctx)))
+
+
+def rmat_refine_history(ctx) -> list:
+    n = lib().rmat_refine_history(ct.c_void_p(ctx), None, 0)
+    buf = (ct.c_double * max(n, 1))()
+    lib().rmat_refine_history(ct.c_void_p(ctx), buf, n)
+    return [buf[k] for k in range(n)]

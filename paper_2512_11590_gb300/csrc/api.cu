@@ -16,6 +16,8 @@ int default_nb(int precision, int N) {
   return N >= 4096 ? 128 : 64;
 }
 
+int clamp_nb(int precision, int nb) { return std::min(nb, precision == RMAT_C128 ? 64 : 128); }
+
 bool valid_precision(int p) {
   return p == RMAT_C128 || p == RMAT_C64_3XTF32_IR || p == RMAT_C64_SIMT_IR;
 }
@@ -57,8 +59,9 @@ int reserve(rmat_ctx c, bool dense) {
   want(c->Rres_cap, N * nrhs * 16);
   want(c->Bw_cap, N * nrhs * eb);
   if (tensor) {
-    want(c->Apl_cap, 4 * N * RMAT_MAX_NB * 4);
+    want(c->Fpl_cap, 4 * N * ld * 4);
     want(c->Bpl_cap, 4 * N * RMAT_MAX_NB * 4);
+    want(c->Ypl_cap, (size_t)4 * RMAT_YPL_ROWS * RMAT_MAX_NB * 4);
   }
   if (dense) {
     want(c->A64_cap, N * N * 16);
@@ -72,9 +75,11 @@ int reserve(rmat_ctx c, bool dense) {
   RMAT_CHECK(rmat_grow(c, (void**)&c->Rres, &c->Rres_cap, N * nrhs * 16));
   RMAT_CHECK(rmat_grow(c, &c->Bw, &c->Bw_cap, N * nrhs * eb));
   RMAT_CHECK(rmat_grow(c, (void**)&c->ipiv, &c->ipiv_cap, N * sizeof(int)));
+  RMAT_CHECK(perm_reserve(c, c->perm_main, (int)N, c->nb));
   if (tensor) {
-    RMAT_CHECK(rmat_grow(c, (void**)&c->Apl, &c->Apl_cap, 4 * N * RMAT_MAX_NB * 4));
+    RMAT_CHECK(rmat_grow(c, (void**)&c->Fpl, &c->Fpl_cap, 4 * N * ld * 4));
     RMAT_CHECK(rmat_grow(c, (void**)&c->Bpl, &c->Bpl_cap, 4 * N * RMAT_MAX_NB * 4));
+    RMAT_CHECK(rmat_grow(c, (void**)&c->Ypl, &c->Ypl_cap, (size_t)4 * RMAT_YPL_ROWS * RMAT_MAX_NB * 4));
   }
   if (dense) {
     RMAT_CHECK(rmat_grow(c, (void**)&c->A64, &c->A64_cap, N * N * 16));
@@ -101,6 +106,21 @@ double elapsed(cudaEvent_t a, cudaEvent_t b) {
 }
 
 }  // namespace
+
+int perm_reserve(rmat_ctx c, LUPerm& pm, int n, int nb) {
+  const size_t nblk = (size_t)(n + nb - 1) / nb;
+  const size_t bytes = nblk * (3 * (size_t)nb + 1) * sizeof(int);
+  if (bytes > pm.cap || !pm.rows) {
+    void* p = pm.rows;
+    size_t cap = pm.cap;
+    RMAT_CHECK(rmat_grow(c, &p, &cap, bytes));
+    pm.rows = reinterpret_cast<int*>(p);
+    pm.cap = cap;
+  }
+  pm.idx = pm.rows + nblk * 2 * nb;
+  pm.cnt = pm.idx + nblk * nb;
+  return RMAT_OK;
+}
 
 int rmat_grow(rmat_ctx c, void** p, size_t* cap, size_t bytes) {
   if (bytes <= *cap && *p) return RMAT_OK;
@@ -201,8 +221,8 @@ int rmat_destroy(rmat_ctx c) {
   cudaStreamSynchronize(c->stream);
   void* bufs[] = {c->C,    c->A64,  c->B64, c->ipiv, c->Kmat, c->T0,  c->rmesh,
                   c->fa,   c->l_d,  c->th_d, c->Wpt, c->X,    c->Rres, c->Bw,
-                  c->Apl,  c->Bpl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
-                  c->ps_mem, c->dstat};
+                  c->Fpl,  c->Bpl, c->Ypl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
+                  c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->hstat) cudaFreeHost(c->hstat);
@@ -228,6 +248,10 @@ int rmat_set_param(rmat_ctx c, int key, long long v) {
       return RMAT_OK;
     case RMAT_PARAM_TIMING:
       c->timing = v ? 1 : 0;
+      return RMAT_OK;
+    case RMAT_PARAM_EQUILIBRATE:
+      if (v < -1 || v > 1) return -3;
+      c->equil_param = (int)v;
       return RMAT_OK;
     default:
       return -2;
@@ -265,9 +289,10 @@ int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_de
   c->l.assign(pb->l, pb->l + pb->nch);
   c->thresh.assign(pb->thresh, pb->thresh + pb->nch);
   c->assembled = c->factored = c->solved = false;
-  c->nb = c->nb_param ? c->nb_param : default_nb(c->precision, c->N);
-  if (c->precision == RMAT_C128 && c->nb > 128) c->nb = 128;
+  c->nb = clamp_nb(c->precision, c->nb_param ? c->nb_param : default_nb(c->precision, c->N));
   RMAT_CHECK(reserve(c, false));
+  c->equil = c->equil_param == -1 ? c->precision != RMAT_C128 : c->equil_param == 1;
+  if (c->equil) RMAT_CHECK(rmat_grow(c, (void**)&c->Dsc, &c->Dsc_cap, (size_t)c->N * sizeof(double)));
   const int nlag = c->nlag, nch = c->nch;
   RMAT_CHECK(rmat_grow(c, (void**)&c->Wpt, &c->Wpt_cap, (size_t)nlag * nch * nch * 16));
   RMAT_CHECK(rmat_grow(c, (void**)&c->l_d, &c->l_cap, nch * sizeof(int)));
@@ -319,14 +344,14 @@ int rmat_load_dense(rmat_ctx c, int n, int nrhs, const void* A_dev, int lda, con
   if (ldb < n) return -7;
   if (!valid_precision(precision)) return -8;
   c->kind = 2;
+  c->equil = false;
   c->precision = precision;
   c->N = n;
   c->nrhs = nrhs;
   c->nch = c->nlag = 0;
   c->ld = (int)round_up(n, 32);
   c->assembled = c->factored = c->solved = false;
-  c->nb = c->nb_param ? c->nb_param : default_nb(precision, n);
-  if (precision == RMAT_C128 && c->nb > 128) c->nb = 128;
+  c->nb = clamp_nb(precision, c->nb_param ? c->nb_param : default_nb(precision, n));
   RMAT_CHECK(reserve(c, true));
   RMAT_CHECK(launch_load_dense(c, reinterpret_cast<const double2*>(A_dev), lda,
                                reinterpret_cast<const double2*>(B_dev), ldb));
@@ -346,9 +371,9 @@ int rmat_factor(rmat_ctx c, int* info) {
   const bool tensor = c->precision == RMAT_C64_3XTF32_IR;
   int st;
   if (c->precision == RMAT_C128)
-    st = lu_factor_dev<double>(c, c->C, c->N, c->ld, c->ipiv, c->nb, false);
+    st = lu_factor_dev<double>(c, c->C, c->N, c->ld, c->ipiv, c->nb, false, c->perm_main);
   else
-    st = lu_factor_dev<float>(c, c->C, c->N, c->ld, c->ipiv, c->nb, tensor);
+    st = lu_factor_dev<float>(c, c->C, c->N, c->ld, c->ipiv, c->nb, tensor, c->perm_main);
   if (st != RMAT_OK) return st;
   record_stage(c, &e1);
   c->factored = true;
@@ -366,8 +391,10 @@ int rmat_factor(rmat_ctx c, int* info) {
 
 static int solve_factors(rmat_ctx c) {
   if (c->precision == RMAT_C128)
-    return lu_solve_dev<double>(c, c->C, c->N, c->ld, c->ipiv, c->nb, c->Bw, c->nrhs, c->nrhs);
-  return lu_solve_dev<float>(c, c->C, c->N, c->ld, c->ipiv, c->nb, c->Bw, c->nrhs, c->nrhs);
+    return lu_solve_dev<double>(c, c->C, c->N, c->ld, c->perm_main, c->nb, c->Bw, c->nrhs,
+                                c->nrhs);
+  return lu_solve_dev<float>(c, c->C, c->N, c->ld, c->perm_main, c->nb, c->Bw, c->nrhs, c->nrhs,
+                             c->precision == RMAT_C64_3XTF32_IR);
 }
 
 int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int* iters,
@@ -385,12 +412,14 @@ int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int
   record_stage(c, &e1);
   int it = 0, status = RMAT_OK;
   double rel = 0.0;
+  c->ir_hist.clear();
   if (max_refine > 0 || tol > 0) {
     double prev = INFINITY;
     int stagn = 0;
     for (;;) {
       RMAT_CHECK(launch_residual(c, nullptr));
       rel = read_red(c) / c->phi_max;
+      c->ir_hist.push_back(rel);
       if (!std::isfinite(rel)) {
         status = RMAT_ENOCONV;
         break;
@@ -475,6 +504,14 @@ int rmat_get_stats(rmat_ctx c, double* out, int n) {
   const int m = n < 13 ? n : 13;
   for (int k = 0; k < m; ++k) out[k] = v[k];
   return m;
+}
+
+int rmat_refine_history(rmat_ctx c, double* hist, int n) {
+  if (!c) return -1;
+  if (!hist && n > 0) return -2;
+  const int cnt = (int)c->ir_hist.size();
+  for (int k = 0; k < std::min(n, cnt); ++k) hist[k] = c->ir_hist[k];
+  return cnt;
 }
 
 int rmat_reset_counters(rmat_ctx c) {

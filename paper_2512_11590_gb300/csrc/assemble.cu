@@ -30,13 +30,15 @@ __global__ void __launch_bounds__(256)
 assemble_kernel(cplx<T>* __restrict__ C, int ld, int N, int nch, int nlag,
                 const double* __restrict__ K, const double* __restrict__ r,
                 const int* __restrict__ l, const double* __restrict__ th,
-                const double2* __restrict__ V, double hm, double E) {
+                const double2* __restrict__ V, double hm, double E,
+                const double* __restrict__ D) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int row = gw; row < N; row += nw) {
     const int al = row / nlag, i = row - al * nlag;
     const double d = chan_diag(hm, l[al], r[i], th[al], E);
+    const double drow = D ? D[row] : 1.0;
     cplx<T>* Crow = C + (size_t)row * ld;
     int alp = lane / nlag, j = lane - alp * nlag;
     const int sq = 32 / nlag, sr = 32 - sq * nlag;  // 32 = sq*nlag + sr
@@ -58,12 +60,31 @@ assemble_kernel(cplx<T>* __restrict__ C, int ld, int N, int nch, int nlag,
           im = v.y;
         }
       }
+      if (D && col < N) {
+        const double s = drow * D[col];
+        re *= s;
+        im *= s;
+      }
       Crow[col] = mkc<T>((T)re, (T)im);
       alp += sq;
       j += sr;
       if (j >= nlag) { j -= nlag; alp += 1; }
     }
   }
+}
+
+// Symmetric equilibration D_(al,i) = |C_(al,i),(al,i)|^-1/2 (1 when the diagonal is 0).
+__global__ void diag_scale_kernel(double* __restrict__ D, int N, int nch, int nlag,
+                                  const double* __restrict__ K, const double* __restrict__ r,
+                                  const int* __restrict__ l, const double* __restrict__ th,
+                                  const double2* __restrict__ V, double hm, double E) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= N) return;
+  const int al = row / nlag, i = row - al * nlag;
+  const double2 v = V[i + (size_t)nlag * (al + (size_t)nch * al)];
+  const double re = K[i * nlag + i] + chan_diag(hm, l[al], r[i], th[al], E) + v.x;
+  const double m = hypot(re, v.y);
+  D[row] = m > 0.0 ? 1.0 / sqrt(m) : 1.0;
 }
 
 // Full coupling matrix at each mesh point for the structured FP64 residual:
@@ -121,14 +142,20 @@ __global__ void load_rhs_kernel(double2* __restrict__ B64, int n, int nrhs,
 
 int launch_assemble(rmat_ctx c, const double2* V, double E) {
   const int blocks = std::max(1, std::min(c->sm_count * 8, ceil_div((long long)c->N * 32, 256)));
+  const double* D = c->equil ? c->Dsc : nullptr;
+  if (D) {
+    diag_scale_kernel<<<ceil_div(c->N, 256), 256, 0, c->stream>>>(
+        c->Dsc, c->N, c->nch, c->nlag, c->Kmat, c->rmesh, c->l_d, c->th_d, V, c->hm, E);
+    c->launches++;
+  }
   if (c->precision == RMAT_C128) {
     assemble_kernel<double><<<blocks, 256, 0, c->stream>>>(
         reinterpret_cast<double2*>(c->C), c->ld, c->N, c->nch, c->nlag, c->Kmat, c->rmesh, c->l_d,
-        c->th_d, V, c->hm, E);
+        c->th_d, V, c->hm, E, D);
   } else {
     assemble_kernel<float><<<blocks, 256, 0, c->stream>>>(
         reinterpret_cast<float2*>(c->C), c->ld, c->N, c->nch, c->nlag, c->Kmat, c->rmesh, c->l_d,
-        c->th_d, V, c->hm, E);
+        c->th_d, V, c->hm, E, D);
   }
   c->launches++;
   RMAT_CU(cudaGetLastError());

@@ -190,8 +190,9 @@ int launch_collision(rmat_ctx c, double2* R_dev, double2* U_dev, int nopen) {
   const double tf = c->tu_flops;
   const size_t tev = c->tu_events.size();
   const int nb = std::min(64, nch);
-  RMAT_CHECK(lu_factor_dev<double>(c, ZO, nch, nch, c->zpiv, nb, false));
-  RMAT_CHECK(lu_solve_dev<double>(c, ZO, nch, nch, c->zpiv, nb, ZI, nopen, nopen));
+  RMAT_CHECK(perm_reserve(c, c->perm_z, nch, nb));
+  RMAT_CHECK(lu_factor_dev<double>(c, ZO, nch, nch, c->zpiv, nb, false, c->perm_z));
+  RMAT_CHECK(lu_solve_dev<double>(c, ZO, nch, nch, c->perm_z, nb, ZI, nopen, nopen));
   c->tu_launches = tl;
   c->tu_flops = tf;
   c->tu_events.resize(tev);

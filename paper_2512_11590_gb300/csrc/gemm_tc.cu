@@ -159,7 +159,8 @@ __device__ __forceinline__ void product(int p, int& qa, int& qb, int& acc, int& 
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_update_kernel(const __grid_constant__ TcMaps maps, float2* __restrict__ C, int ldc, int M,
-                 int Nn, int K, int rowA0, int rowB0, int* __restrict__ err) {
+                 int Nn, int K, int ax0, int rowA0, int bx0, int rowB0, int vec_ok,
+                 int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -211,10 +212,10 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, float2* __restrict__ C, in
           const uint32_t st = smem_u32(stages + s * STAGE_BYTES);
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            tma_load_2d(st + q * A_PLANE_BYTES, &maps.a[q], ks * TC_BK, rowA0 + m0, full);
+            tma_load_2d(st + q * A_PLANE_BYTES, &maps.a[q], ax0 + ks * TC_BK, rowA0 + m0, full);
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            tma_load_2d(st + 4 * A_PLANE_BYTES + q * B_PLANE_BYTES, &maps.b[q], ks * TC_BK,
+            tma_load_2d(st + 4 * A_PLANE_BYTES + q * B_PLANE_BYTES, &maps.b[q], bx0 + ks * TC_BK,
                         rowB0 + n0, full);
         }
       }
@@ -294,7 +295,7 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, float2* __restrict__ C, in
         tmem_wait_ld();
         if (gm < M) {
           const int c0 = ch * 32;
-          if (n0 + c0 + 32 <= Nn) {
+          if (vec_ok && n0 + c0 + 32 <= Nn) {
             float4* p4 = reinterpret_cast<float4*>(Crow + c0);
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -350,11 +351,11 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-int make_plane_map(CUtensorMap* m, float* base, int rows, int box_rows) {
+int make_plane_map(CUtensorMap* m, float* base, int cols, int rows, int row_stride, int box_rows) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return RMAT_ECUDA;
-  cuuint64_t dims[2] = {(cuuint64_t)RMAT_MAX_NB, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)RMAT_MAX_NB * sizeof(float)};
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)row_stride * sizeof(float)};
   cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
@@ -363,58 +364,91 @@ int make_plane_map(CUtensorMap* m, float* base, int rows, int box_rows) {
   return r == CUDA_SUCCESS ? RMAT_OK : RMAT_ECUDA;
 }
 
+// Tensor maps of the three operand sources, rebuilt when a buffer or size changes:
+//   F  full-size split factor planes, row-major [n][ldf]  (A operand)
+//   B  transposed U12 planes [n][256]                      (B operand of the factor update)
+//   Y  transposed right-hand-side block planes [nrhs][256] (B operand of the solve updates)
 struct TcCache {
-  float* apl = nullptr;
-  float* bpl = nullptr;
-  int n = -1;
-  TcMaps maps;
+  const float* f = nullptr;
+  const float* b = nullptr;
+  const float* y = nullptr;
+  int n = -1, ldf = -1, nrhs = -1;
+  TcMaps upd, sol;
   bool attr = false;
 };
 TcCache g_tc;
 
-}  // namespace
-
-int tc_prepare(rmat_ctx c, int n, int) {
-  if (g_tc.apl == c->Apl && g_tc.bpl == c->Bpl && g_tc.n == n) return RMAT_OK;
-  const size_t plane = (size_t)n * RMAT_MAX_NB;
-  for (int q = 0; q < 4; ++q) {
-    RMAT_CHECK(make_plane_map(&g_tc.maps.a[q], c->Apl + q * plane, n, TC_BM));
-    RMAT_CHECK(make_plane_map(&g_tc.maps.b[q], c->Bpl + q * plane, n, TC_BN));
-  }
-  g_tc.apl = c->Apl;
-  g_tc.bpl = c->Bpl;
-  g_tc.n = n;
-  return RMAT_OK;
-}
-
-int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n) {
-  const int rest = n - k0 - jb;
-  if (rest <= 0) return RMAT_OK;
-  if (jb % TC_BK) return RMAT_ESTATE;
-  RMAT_CHECK(tc_prepare(c, n, jb));
+int launch_tc(rmat_ctx c, const TcMaps& maps, float2* C, int ldc, int M, int Nn, int K, int ax0,
+              int ay0, int bx0, int by0, bool count_as_update) {
+  if (M <= 0 || Nn <= 0 || K <= 0) return RMAT_OK;
+  if (K % TC_BK || ax0 % TC_BK || bx0 % TC_BK) return RMAT_ESTATE;
   if (!g_tc.attr) {
     RMAT_CU(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TC_SMEM));
     g_tc.attr = true;
   }
-  const int tiles = ceil_div(rest, TC_BM) * ceil_div(rest, TC_BN);
+  const int tiles = ceil_div(M, TC_BM) * ceil_div(Nn, TC_BN);
   const int grid = std::min(tiles, c->sm_count);
-  float2* C22 = A + (size_t)(k0 + jb) * ld + (k0 + jb);
+  const int vec_ok = (ldc % 2 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c->timing) {
+  if (c->timing && count_as_update) {
     e0 = rmat_event(c);
     e1 = rmat_event(c);
     RMAT_CU(cudaEventRecord(e0, c->stream));
   }
-  tc_update_kernel<<<grid, TC_THREADS, TC_SMEM, c->stream>>>(g_tc.maps, C22, ld, rest, rest, jb,
-                                                             k0 + jb, k0 + jb, c->dstat + ST_TIMEOUT);
+  tc_update_kernel<<<grid, TC_THREADS, TC_SMEM, c->stream>>>(maps, C, ldc, M, Nn, K, ax0, ay0, bx0,
+                                                             by0, vec_ok, c->dstat + ST_TIMEOUT);
   c->launches++;
   RMAT_CU(cudaGetLastError());
-  if (c->timing) {
-    RMAT_CU(cudaEventRecord(e1, c->stream));
-    c->tu_events.push_back({e0, e1});
+  if (count_as_update) {
+    if (c->timing) {
+      RMAT_CU(cudaEventRecord(e1, c->stream));
+      c->tu_events.push_back({e0, e1});
+    }
+    c->tu_launches++;
+    c->tu_flops += 8.0 * M * (double)Nn * K;
   }
-  c->tu_launches++;
-  c->tu_flops += 8.0 * rest * (double)rest * jb;
   return RMAT_OK;
+}
+
+}  // namespace
+
+int tc_prepare(rmat_ctx c, int n, int nrhs) {
+  const int ldf = c->ld;
+  if (g_tc.f == c->Fpl && g_tc.b == c->Bpl && g_tc.y == c->Ypl && g_tc.n == n && g_tc.ldf == ldf &&
+      g_tc.nrhs == nrhs)
+    return RMAT_OK;
+  const size_t fplane = (size_t)n * ldf, bplane = (size_t)n * RMAT_MAX_NB,
+               yplane = (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB;
+  for (int q = 0; q < 4; ++q) {
+    RMAT_CHECK(make_plane_map(&g_tc.upd.a[q], c->Fpl + q * fplane, ldf, n, ldf, TC_BM));
+    RMAT_CHECK(make_plane_map(&g_tc.upd.b[q], c->Bpl + q * bplane, RMAT_MAX_NB, n, RMAT_MAX_NB,
+                              TC_BN));
+    g_tc.sol.a[q] = g_tc.upd.a[q];
+    RMAT_CHECK(make_plane_map(&g_tc.sol.b[q], c->Ypl + q * yplane, RMAT_MAX_NB,
+                              std::max(1, nrhs), RMAT_MAX_NB, TC_BN));
+  }
+  g_tc.f = c->Fpl;
+  g_tc.b = c->Bpl;
+  g_tc.y = c->Ypl;
+  g_tc.n = n;
+  g_tc.ldf = ldf;
+  g_tc.nrhs = nrhs;
+  return RMAT_OK;
+}
+
+// Factor update: C22 -= L21 U12, A = F planes at (x = k0, y = k0+jb), B = U12^T planes.
+int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n) {
+  const int rest = n - k0 - jb;
+  if (rest <= 0) return RMAT_OK;
+  RMAT_CHECK(tc_prepare(c, n, c->nrhs));
+  float2* C22 = A + (size_t)(k0 + jb) * ld + (k0 + jb);
+  return launch_tc(c, g_tc.upd, C22, ld, rest, rest, jb, k0, k0 + jb, 0, k0 + jb, true);
+}
+
+// Solve update: Bsub[M x nrhs] -= F[rows ay0.., cols k0..k0+jb] * Y, Y^T planes in Ypl.
+int launch_solve_tc(rmat_ctx c, float2* Bsub, int ldb, int M, int nrhs, int k0, int jb, int ay0,
+                    int n) {
+  RMAT_CHECK(tc_prepare(c, n, nrhs));
+  return launch_tc(c, g_tc.sol, Bsub, ldb, M, nrhs, jb, k0, ay0, 0, 0, false);
 }

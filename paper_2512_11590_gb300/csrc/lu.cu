@@ -29,7 +29,10 @@ namespace {
 constexpr int PANEL_THREADS = 256;
 constexpr int MAX_RPC = 4096;  // rows per panel CTA
 
-template <class T>
+// SMEM: the CTA's panel rows live in shared memory for the whole column loop
+// (loaded once, written back at the end); otherwise they are read and written
+// in place in global memory (L2-resident), for panels too tall to stage.
+template <class T, bool SMEM>
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __restrict__ ipiv,
              int* __restrict__ stat, PanelScratch ps, int rpc, long long spin_limit) {
@@ -44,12 +47,23 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
 
   __shared__ T s_v[32];
   __shared__ int s_i[32];
-  __shared__ int s_c[32];
   __shared__ int s_win, s_wcta, s_zero, s_abort;
   extern __shared__ unsigned char smem_raw[];
   C2* s_prow = reinterpret_cast<C2*>(smem_raw);  // [RMAT_MAX_NB]
   C2* s_l = s_prow + RMAT_MAX_NB;                // [rpc]
+  C2* s_rows = s_l + rpc;                        // [rpc][jb] when SMEM
+  // own row r, panel-local column c
+  auto at = [&](int r) -> C2* {
+    return SMEM ? s_rows + (size_t)(r - r_lo) * jb : A + (size_t)r * ld + k0;
+  };
   if (tid == 0) s_abort = 0;
+  if (SMEM) {
+    for (int e = tid; e < (r_hi - r_lo) * jb; e += PANEL_THREADS) {
+      const int rr = e / jb, cc = e - rr * jb;
+      s_rows[e] = A[(size_t)(r_lo + rr) * ld + k0 + cc];
+    }
+  }
+  __syncthreads();
 
   for (int j = 0; j < jb; ++j) {
     const int gj = k0 + j;
@@ -58,7 +72,7 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
     T best = (T)-1;
     int bidx = INT_MAX;
     for (int r = max(r_lo, gj) + tid; r < r_hi; r += PANEL_THREADS) {
-      T m = cabs1<T>(A[(size_t)r * ld + gj]);
+      T m = cabs1<T>(at(r)[j]);
       if (m > best) { best = m; bidx = r; }
     }
 #pragma unroll
@@ -88,11 +102,14 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
     {
       const int cr = s_win;
       C2* slot = crow + ((size_t)par * RMAT_MAX_PANEL_CTAS + cta) * RMAT_MAX_NB;
-      if (cr != INT_MAX)
-        for (int c = tid; c < jb; c += PANEL_THREADS) slot[c] = A[(size_t)cr * ld + k0 + c];
-      if (gj >= r_lo && gj < r_hi)
-        for (int c = tid; c < jb; c += PANEL_THREADS)
-          trow[(size_t)par * RMAT_MAX_NB + c] = A[(size_t)gj * ld + k0 + c];
+      if (cr != INT_MAX) {
+        const C2* src = at(cr);
+        for (int c = tid; c < jb; c += PANEL_THREADS) slot[c] = src[c];
+      }
+      if (gj >= r_lo && gj < r_hi) {
+        const C2* src = at(gj);
+        for (int c = tid; c < jb; c += PANEL_THREADS) trow[(size_t)par * RMAT_MAX_NB + c] = src[c];
+      }
     }
     // ---- grid barrier (bounded spin) ----
     __syncthreads();
@@ -145,40 +162,63 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
     }
     __syncthreads();
     if (p != gj) {
-      if (gj >= r_lo && gj < r_hi)
-        for (int c = tid; c < jb; c += PANEL_THREADS) A[(size_t)gj * ld + k0 + c] = s_prow[c];
-      if (p >= r_lo && p < r_hi)
+      if (gj >= r_lo && gj < r_hi) {
+        C2* dst = at(gj);
+        for (int c = tid; c < jb; c += PANEL_THREADS) dst[c] = s_prow[c];
+      }
+      if (p >= r_lo && p < r_hi) {
+        C2* dst = at(p);
         for (int c = tid; c < jb; c += PANEL_THREADS)
-          A[(size_t)p * ld + k0 + c] = ld_cg(trow + (size_t)par * RMAT_MAX_NB + c);
+          dst[c] = ld_cg(trow + (size_t)par * RMAT_MAX_NB + c);
+      }
     }
     __syncthreads();
     if (s_zero) continue;  // exactly zero column: no scaling, no update (LAPACK)
     const C2 piv = s_prow[j];
     const int r_first = max(r_lo, gj + 1);
     for (int r = r_first + tid; r < r_hi; r += PANEL_THREADS) {
-      C2 lm = cdiv<T>(A[(size_t)r * ld + gj], piv);
-      A[(size_t)r * ld + gj] = lm;
+      C2* ar = at(r);
+      C2 lm = cdiv<T>(ar[j], piv);
+      ar[j] = lm;
       s_l[r - r_lo] = lm;
     }
     __syncthreads();
     if (j + 1 < jb) {
-      for (int r = r_first + warp; r < r_hi; r += nwarp) {
-        const C2 lm = s_l[r - r_lo];
-        C2* Ar = A + (size_t)r * ld + k0;
-        for (int c = j + 1 + lane; c < jb; c += 32) {
-          C2 x = Ar[c];
-          csub_mul<T>(x, lm, s_prow[c]);
-          Ar[c] = x;
+      if (SMEM) {
+        // rank-1 update of the rows' remaining columns, one element per thread step
+        const int ncol = jb - j - 1, nrow = r_hi - r_first;
+        for (int e = tid; e < nrow * ncol; e += PANEL_THREADS) {
+          const int rr = e / ncol, cc = j + 1 + (e - rr * ncol);
+          C2* ar = at(r_first + rr);
+          C2 x = ar[cc];
+          csub_mul<T>(x, s_l[r_first + rr - r_lo], s_prow[cc]);
+          ar[cc] = x;
+        }
+      } else {
+        for (int r = r_first + warp; r < r_hi; r += nwarp) {
+          const C2 lm = s_l[r - r_lo];
+          C2* Ar = at(r);
+          for (int c = j + 1 + lane; c < jb; c += 32) {
+            C2 x = Ar[c];
+            csub_mul<T>(x, lm, s_prow[c]);
+            Ar[c] = x;
+          }
         }
       }
     }
     __syncthreads();
   }
+  if (SMEM) {
+    for (int e = tid; e < (r_hi - r_lo) * jb; e += PANEL_THREADS) {
+      const int rr = e / jb, cc = e - rr * jb;
+      A[(size_t)(r_lo + rr) * ld + k0 + cc] = s_rows[e];
+    }
+  }
 }
 
 // ---- G3: row interchanges on the trailing columns + U12 = L11^-1 A12 ------
-// (the interchanges use rhs_swap_kernel and the solve trsm_block_rhs_kernel,
-// both below, on the trailing columns viewed as right-hand sides)
+// (apply_perm_kernel and trsm_block_rhs_kernel below, on the trailing columns
+// viewed as right-hand sides)
 
 __device__ __forceinline__ float tf32_round(float x) {
   unsigned r;
@@ -186,55 +226,53 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// B operand planes of the tensor update: U12^T split into tf32 hi/lo planes.
-// Plane row = trailing column c, K index t (plane row stride RMAT_MAX_NB floats):
-// [re_hi | re_lo | im_hi | im_lo].  K indices jb..round_up(jb,32)-1 are zeroed.
-// 32 x 32 tiles transposed through shared memory (coalesced on both sides).
-__global__ void __launch_bounds__(256)
-split_u12_kernel(const float2* __restrict__ A, int ld, int k0, int jb, int n,
-                 float* __restrict__ Bpl, size_t plane) {
-  __shared__ float2 tile[32][33];
-  const int c0 = k0 + jb + blockIdx.x * 32;
-  const int t0 = blockIdx.y * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  for (int i = ty; i < 32; i += 8) {
-    const int t = t0 + i, c = c0 + tx;
-    tile[i][tx] = (t < jb && c < n) ? A[(size_t)(k0 + t) * ld + c] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  for (int i = ty; i < 32; i += 8) {
-    const int c = c0 + i, t = t0 + tx;
-    if (c >= n) continue;
-    const float2 z = tile[tx][i];
-    const float rh = tf32_round(z.x), ih = tf32_round(z.y);
-    const size_t o = (size_t)c * RMAT_MAX_NB + t;
-    Bpl[o] = rh;
-    Bpl[plane + o] = z.x - rh;
-    Bpl[2 * plane + o] = ih;
-    Bpl[3 * plane + o] = z.y - ih;
-  }
+// TF32 hi/lo split planes (tensor path).  Four planes [re_hi | re_lo | im_hi | im_lo].
+//   F: the whole factor, row-major [n][ldf] — L21 blocks and U12 rows as they are
+//      produced; the A operand of the trailing update and of the solve updates.
+//   B: U12^T of the current block, [c][256] (K-major B operand of the trailing update).
+//   Y: a solved right-hand-side block transposed, [rhs][256] (B operand of the solve updates).
+__device__ __forceinline__ void put_split(float* base, size_t plane, size_t o, float2 z) {
+  const float rh = tf32_round(z.x), ih = tf32_round(z.y);
+  base[o] = rh;
+  base[plane + o] = z.x - rh;
+  base[2 * plane + o] = ih;
+  base[3 * plane + o] = z.y - ih;
 }
 
-// A operand planes of the tensor update: L21 rows r in [k0+jb, n), K index t.
+// L21 rows r in [k0+jb, n), columns k0..k0+jb-1 -> F (warp per row, lanes over columns).
 __global__ void split_l21_kernel(const float2* __restrict__ A, int ld, int k0, int jb, int n,
-                                 float* __restrict__ Apl, size_t plane) {
+                                 float* __restrict__ F, int ldf, size_t fplane) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int r = k0 + jb + warp;
   if (r >= n) return;
-  for (int t = lane; t < RMAT_MAX_NB; t += 32) {
-    float re = 0.f, im = 0.f;
-    if (t < jb) {
-      float2 z = A[(size_t)r * ld + k0 + t];
-      re = z.x;
-      im = z.y;
+  for (int t = lane; t < jb; t += 32)
+    put_split(F, fplane, (size_t)r * ldf + k0 + t, A[(size_t)r * ld + k0 + t]);
+}
+
+// 32 x 32 tile of a jb x ncols block S (rows t, columns c; row stride lds):
+// optional row-major copy into F (rows frow0 + t, columns fcol0 + c) and the
+// transposed planes T[trow0 + c][t], zero-filled for jb <= t < round_up(jb, 32).
+__global__ void __launch_bounds__(256)
+split_block_kernel(const float2* __restrict__ S, int lds, int jb, int ncols, float* __restrict__ F,
+                   int ldf, size_t fplane, int frow0, int fcol0, float* __restrict__ T,
+                   size_t tplane, int trow0) {
+  __shared__ float2 tile[32][33];
+  const int c0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int i = ty; i < 32; i += 8) {
+    const int t = t0 + i, c = c0 + tx;
+    float2 z = make_float2(0.f, 0.f);
+    if (t < jb && c < ncols) {
+      z = S[(size_t)t * lds + c];
+      if (F) put_split(F, fplane, (size_t)(frow0 + t) * ldf + fcol0 + c, z);
     }
-    float rh = tf32_round(re), ih = tf32_round(im);
-    size_t o = (size_t)r * RMAT_MAX_NB + t;
-    Apl[o] = rh;
-    Apl[plane + o] = re - rh;
-    Apl[2 * plane + o] = ih;
-    Apl[3 * plane + o] = im - ih;
+    tile[i][tx] = z;
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int c = c0 + i, t = t0 + tx;
+    if (c < ncols) put_split(T, tplane, (size_t)(trow0 + c) * RMAT_MAX_NB + t, tile[tx][i]);
   }
 }
 
@@ -301,32 +339,12 @@ cgemm_sub_kernel(int M, int N, int K, const cplx<T>* __restrict__ A, int lda,
 }
 
 // ---- solve kernels (right-hand sides row-major, ldb) -------------------------
-// Row interchanges of one panel applied to nrhs columns.  Pivot indices are
-// checked against [k0+t, n): an index outside it (only possible after a panel
-// that gave up on a bounded wait) is skipped and flagged, never dereferenced.
-template <class T>
-__global__ void rhs_swap_kernel(cplx<T>* __restrict__ B, int ldb, int nrhs, int k0, int jb, int n,
-                                const int* __restrict__ ipiv, int* __restrict__ stat) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= nrhs) return;
-  for (int t = 0; t < jb; ++t) {
-    const int p = __ldg(ipiv + k0 + t);
-    if (p < k0 + t || p >= n) {
-      if (col == 0) atomicExch(&stat[ST_BADARG], 1);
-      continue;
-    }
-    if (p != k0 + t) {
-      cplx<T> u = B[(size_t)(k0 + t) * ldb + col];
-      B[(size_t)(k0 + t) * ldb + col] = B[(size_t)p * ldb + col];
-      B[(size_t)p * ldb + col] = u;
-    }
-  }
-}
-
 // Triangular solve on a jb x jb diagonal block for 32 right-hand-side columns
-// per CTA (lane = column).  Rows are processed in groups of 8 (one per warp):
-// each warp first accumulates the contributions of all rows solved before its
-// group in parallel, then warp 0 finishes the 8 x 8 triangle sequentially.
+// per CTA (lane = column).  The diagonal block is first staged in shared memory
+// (coalesced), so the dependent inner products read shared memory only.  Rows
+// are processed in groups of 8 (one per warp): each warp accumulates the
+// contributions of all rows solved before its group in parallel, then warp 0
+// finishes the 8 x 8 triangle sequentially.
 // LOWER: unit lower, rows top-down; else upper (divide by the diagonal), bottom-up.
 template <class T, bool LOWER>
 __global__ void __launch_bounds__(256)
@@ -335,21 +353,27 @@ trsm_block_rhs_kernel(const cplx<T>* __restrict__ A, int ld, int k0, int jb,
   using C2 = cplx<T>;
   extern __shared__ unsigned char smem_raw[];
   C2* xs = reinterpret_cast<C2*>(smem_raw);  // [jb][32]
+  C2* Ls = xs + (size_t)jb * 32;               // [jb][jb + 1]
+  const int lds = jb + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.x * 32 + lane;
   const bool act = col < nrhs;
+  for (int e = threadIdx.x; e < jb * jb; e += 256) {
+    const int i = e / jb, t = e - i * jb;
+    Ls[i * lds + t] = A[(size_t)(k0 + i) * ld + k0 + t];
+  }
+  __syncthreads();
   const int ngroups = (jb + 7) / 8;
   for (int g = 0; g < ngroups; ++g) {
-    // local row index (within the block) handled by this warp
     const int li = LOWER ? g * 8 + warp : jb - 1 - (g * 8 + warp);
     const bool rowok = (g * 8 + warp) < jb;
     if (rowok) {
       C2 acc = act ? B[(size_t)(k0 + li) * ldb + col] : mkc<T>(0, 0);
-      const C2* Ar = A + (size_t)(k0 + li) * ld + k0;
+      const C2* Lr = Ls + li * lds;
       if (LOWER) {
-        for (int t = 0; t < g * 8; ++t) csub_mul<T>(acc, __ldg(Ar + t), xs[t * 32 + lane]);
+        for (int t = 0; t < g * 8; ++t) csub_mul<T>(acc, Lr[t], xs[t * 32 + lane]);
       } else {
-        for (int t = jb - g * 8; t < jb; ++t) csub_mul<T>(acc, __ldg(Ar + t), xs[t * 32 + lane]);
+        for (int t = jb - g * 8; t < jb; ++t) csub_mul<T>(acc, Lr[t], xs[t * 32 + lane]);
       }
       xs[li * 32 + lane] = acc;
     }
@@ -357,13 +381,13 @@ trsm_block_rhs_kernel(const cplx<T>* __restrict__ A, int ld, int k0, int jb,
     if (warp == 0) {
       for (int w = 0; w < 8 && g * 8 + w < jb; ++w) {
         const int ri = LOWER ? g * 8 + w : jb - 1 - (g * 8 + w);
-        const C2* Ar = A + (size_t)(k0 + ri) * ld + k0;
+        const C2* Lr = Ls + ri * lds;
         C2 acc = xs[ri * 32 + lane];
         for (int w2 = 0; w2 < w; ++w2) {
           const int tj = LOWER ? g * 8 + w2 : jb - 1 - (g * 8 + w2);
-          csub_mul<T>(acc, __ldg(Ar + tj), xs[tj * 32 + lane]);
+          csub_mul<T>(acc, Lr[tj], xs[tj * 32 + lane]);
         }
-        if (!LOWER) acc = cdiv<T>(acc, __ldg(Ar + ri));
+        if (!LOWER) acc = cdiv<T>(acc, Lr[ri]);
         xs[ri * 32 + lane] = acc;
       }
     }
@@ -371,6 +395,102 @@ trsm_block_rhs_kernel(const cplx<T>* __restrict__ A, int ld, int k0, int jb,
   }
   if (act)
     for (int i = warp; i < jb; i += 8) B[(size_t)(k0 + i) * ldb + col] = xs[i * 32 + lane];
+}
+
+template <class T>
+size_t trsm_smem(int jb) {
+  return (size_t)jb * 32 * sizeof(cplx<T>) + (size_t)jb * (jb + 1) * sizeof(cplx<T>);
+}
+
+// ---- row interchanges as one permutation per block -----------------------------
+// perm_prep_kernel (one warp per block of jb pivots): the jb sequential swaps
+// rows (k0+t) <-> ipiv[k0+t] touch the block rows k0..k0+jb-1 and at most jb
+// rows below.  The involved rows are listed once (block rows first, then the
+// distinct rows below in first-use order) with, for each step t, the list slot
+// of its pivot row; the list serves the trailing columns of the factorisation
+// and every forward solve.  Out-of-range pivots (only after a panel that gave
+// up on a bounded wait) become no-ops and raise the status word.
+__global__ void perm_prep_kernel(const int* __restrict__ ipiv, int n, int nb, int k0_first,
+                                 int* __restrict__ prow, int* __restrict__ pidx,
+                                 int* __restrict__ pcnt, int* __restrict__ stat) {
+  const int blk = blockIdx.x;
+  const int k0 = k0_first + blk * nb;
+  if (k0 >= n) return;
+  const int jb = min(nb, n - k0);
+  const int lane = threadIdx.x;
+  int* rows = prow + (size_t)(k0 / nb) * 2 * nb;
+  int* idx = pidx + (size_t)(k0 / nb) * nb;
+  for (int t = lane; t < jb; t += 32) rows[t] = k0 + t;
+  int nout = 0;
+  for (int t = 0; t < jb; ++t) {
+    int p = ipiv[k0 + t];
+    int slot;
+    if (p < k0 + t || p >= n) {
+      if (lane == 0) atomicExch(&stat[ST_BADARG], 1);
+      slot = t;
+    } else if (p < k0 + jb) {
+      slot = p - k0;
+    } else {
+      slot = -1;
+      for (int q0 = 0; q0 < nout && slot < 0; q0 += 32) {
+        const int q = q0 + lane;
+        const bool hit = q < nout && rows[jb + q] == p;
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m) slot = jb + q0 + __ffs(m) - 1;
+      }
+      if (slot < 0) {
+        slot = jb + nout;
+        if (lane == 0) rows[slot] = p;
+        ++nout;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) idx[t] = slot;
+  }
+  if (lane == 0) pcnt[k0 / nb] = jb + nout;
+}
+
+// Apply block k0's permutation to ncols columns of B (rows of B are matrix rows):
+// gather the involved rows into shared memory, replay the swaps there, write back.
+template <class T>
+__global__ void __launch_bounds__(256)
+apply_perm_kernel(cplx<T>* __restrict__ B, int ldb, int ncols, int k0, int nb, int jb,
+                  const int* __restrict__ prow, const int* __restrict__ pidx,
+                  const int* __restrict__ pcnt) {
+  using C2 = cplx<T>;
+  extern __shared__ unsigned char smem_raw[];
+  C2* vals = reinterpret_cast<C2*>(smem_raw);                      // [2*nb][32]
+  int* rows = reinterpret_cast<int*>(vals + (size_t)2 * nb * 32);  // [2*nb]
+  int* idx = rows + 2 * nb;                                        // [nb]
+  const int blk = k0 / nb;
+  const int cnt = pcnt[blk];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = threadIdx.x; q < cnt; q += 256) rows[q] = prow[(size_t)blk * 2 * nb + q];
+  for (int q = threadIdx.x; q < jb; q += 256) idx[q] = pidx[(size_t)blk * nb + q];
+  __syncthreads();
+  const int col = blockIdx.x * 32 + lane;
+  const bool act = col < ncols;
+  for (int q = warp; q < cnt; q += 8)
+    if (act) vals[q * 32 + lane] = B[(size_t)rows[q] * ldb + col];
+  __syncthreads();
+  if (warp == 0) {
+    for (int t = 0; t < jb; ++t) {
+      const int s = idx[t];
+      if (s != t) {
+        const C2 u = vals[t * 32 + lane];
+        vals[t * 32 + lane] = vals[s * 32 + lane];
+        vals[s * 32 + lane] = u;
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = warp; q < cnt; q += 8)
+    if (act) B[(size_t)rows[q] * ldb + col] = vals[q * 32 + lane];
+}
+
+template <class T>
+size_t perm_smem(int nb) {
+  return (size_t)2 * nb * 32 * sizeof(cplx<T>) + (size_t)3 * nb * sizeof(int);
 }
 
 template <class T>
@@ -395,17 +515,28 @@ int panel_ctas_for(rmat_ctx c, int M) {
   return P;
 }
 
+constexpr size_t PANEL_SMEM_LIMIT = 220 * 1024;
+
+template <class T>
+size_t panel_smem(int rpc, int jb, bool in_smem) {
+  return (size_t)(RMAT_MAX_NB + rpc) * sizeof(cplx<T>) +
+         (in_smem ? (size_t)rpc * jb * sizeof(cplx<T>) : 0);
+}
+
 template <class T>
 int launch_panel(rmat_ctx c, cplx<T>* A, int ld, int k0, int n, int jb, int* ipiv) {
   const int M = n - k0;
   const int P = panel_ctas_for(c, M);
   const int rpc = ceil_div(M, P);
-  const size_t smem = (size_t)(RMAT_MAX_NB + rpc) * sizeof(cplx<T>);
+  const bool in_smem = panel_smem<T>(rpc, jb, true) <= PANEL_SMEM_LIMIT;
+  const size_t smem = panel_smem<T>(rpc, jb, in_smem);
   static bool attr_set[2] = {false, false};
-  auto kern = panel_kernel<T>;
   if (!attr_set[sizeof(T) == 8]) {
-    RMAT_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((RMAT_MAX_NB + MAX_RPC) * sizeof(cplx<T>))));
+    RMAT_CU(cudaFuncSetAttribute(panel_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)PANEL_SMEM_LIMIT));
+    RMAT_CU(cudaFuncSetAttribute(panel_kernel<T, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)panel_smem<T>(MAX_RPC, 0, false)));
     attr_set[sizeof(T) == 8] = true;
   }
   RMAT_CU(cudaMemsetAsync(c->ps.bar, 0, sizeof(unsigned), c->stream));
@@ -413,51 +544,74 @@ int launch_panel(rmat_ctx c, cplx<T>* A, int ld, int k0, int n, int jb, int* ipi
   long long spin = c->spin_limit;
   int* stat = c->dstat;
   void* args[] = {&A, &ld, (void*)&k0, (void*)&n, (void*)&jb, &ipiv, &stat, &ps, (void*)&rpc, &spin};
-  RMAT_CU(cudaLaunchCooperativeKernel((const void*)kern, dim3(P), dim3(PANEL_THREADS), args, smem,
-                                      c->stream));
+  const void* kern = in_smem ? (const void*)panel_kernel<T, true> : (const void*)panel_kernel<T, false>;
+  RMAT_CU(cudaLaunchCooperativeKernel(kern, dim3(P), dim3(PANEL_THREADS), args, smem, c->stream));
   c->launches++;
   return RMAT_OK;
 }
+
+// Largest block width whose diagonal block fits the TRSM's shared memory.
+template <class T> constexpr int max_nb() { return sizeof(T) == 4 ? 128 : 64; }
 
 template <class T>
 int set_trsm_attrs() {
   static bool done = false;
   if (done) return RMAT_OK;
-  const int smem_max = (int)((size_t)RMAT_MAX_NB * 32 * sizeof(cplx<T>));
+  const int smem_max = (int)trsm_smem<T>(max_nb<T>());
   RMAT_CU(cudaFuncSetAttribute(trsm_block_rhs_kernel<T, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   RMAT_CU(cudaFuncSetAttribute(trsm_block_rhs_kernel<T, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  RMAT_CU(cudaFuncSetAttribute(apply_perm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)perm_smem<T>(max_nb<T>())));
   done = true;
   return RMAT_OK;
 }
 
 template <class T>
-int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool tensor) {
+int apply_perm(rmat_ctx c, const LUPerm& pm, cplx<T>* B, int ldb, int ncols, int k0, int nb, int jb) {
+  apply_perm_kernel<T><<<ceil_div(ncols, 32), 256, perm_smem<T>(nb), c->stream>>>(
+      B, ldb, ncols, k0, nb, jb, pm.rows, pm.idx, pm.cnt);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+template <class T>
+int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool tensor,
+                  const LUPerm& pm) {
   using C2 = cplx<T>;
   C2* A = reinterpret_cast<C2*>(Av);
-  if (nb < 1 || nb > RMAT_MAX_NB || (sizeof(T) == 8 && nb > 128)) return RMAT_ESTATE;
+  if (nb < 1 || nb > max_nb<T>()) return RMAT_ESTATE;
   RMAT_CHECK(set_trsm_attrs<T>());
   RMAT_CU(cudaMemsetAsync(ipiv, 0xff, (size_t)n * sizeof(int), c->stream));  // -1: "not pivoted"
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int jb = std::min(nb, n - k0);
     RMAT_CHECK(launch_panel<T>(c, A, ld, k0, n, jb, ipiv));
     const int rest = n - k0 - jb;
-    if (rest <= 0) continue;
+    if (rest <= 0) {
+      perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt,
+                                                c->dstat);
+      c->launches++;
+      continue;
+    }
     // G3: interchanges on the trailing columns, then U12 = L11^-1 A12
-    rhs_swap_kernel<T><<<ceil_div(rest, 128), 128, 0, c->stream>>>(A + k0 + jb, ld, rest, k0, jb,
-                                                                     n, ipiv, c->dstat);
-    trsm_block_rhs_kernel<T, true><<<ceil_div(rest, 32), 256, (size_t)jb * 32 * sizeof(C2),
-                                     c->stream>>>(A, ld, k0, jb, A + k0 + jb, ld, rest);
-    c->launches += 2;
+    perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt, c->dstat);
+    c->launches++;
+    RMAT_CHECK(apply_perm<T>(c, pm, A + k0 + jb, ld, rest, k0, nb, jb));
+    trsm_block_rhs_kernel<T, true><<<ceil_div(rest, 32), 256, trsm_smem<T>(jb), c->stream>>>(
+        A, ld, k0, jb, A + k0 + jb, ld, rest);
+    c->launches++;
     RMAT_CU(cudaGetLastError());
     if (tensor && sizeof(T) == 4) {
-      const size_t plane = (size_t)n * RMAT_MAX_NB;
+      const size_t fplane = (size_t)n * ld, bplane = (size_t)n * RMAT_MAX_NB;
+      const float2* Af = reinterpret_cast<const float2*>(A);
       const int kpad = (int)round_up(jb, 32);
-      split_u12_kernel<<<dim3(ceil_div(rest, 32), kpad / 32), 256, 0, c->stream>>>(
-          reinterpret_cast<const float2*>(A), ld, k0, jb, n, c->Bpl, plane);
+      split_block_kernel<<<dim3(ceil_div(rest, 32), kpad / 32), 256, 0, c->stream>>>(
+          Af + (size_t)k0 * ld + k0 + jb, ld, jb, rest, c->Fpl, ld, fplane, k0, k0 + jb, c->Bpl,
+          bplane, k0 + jb);
       split_l21_kernel<<<ceil_div((long long)rest * 32, 256), 256, 0, c->stream>>>(
-          reinterpret_cast<const float2*>(A), ld, k0, jb, n, c->Apl, plane);
+          Af, ld, k0, jb, n, c->Fpl, ld, fplane);
       c->launches += 2;
       RMAT_CU(cudaGetLastError());
       RMAT_CHECK(launch_trailing_tc(c, reinterpret_cast<float2*>(A), ld, k0, jb, n));
@@ -483,42 +637,67 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
 }
 
 template <class T>
-int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const int* ipiv, int nb, void* Bv,
-                 int ldb, int nrhs) {
+int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, int nb, void* Bv,
+                 int ldb, int nrhs, bool tensor) {
   using C2 = cplx<T>;
   const C2* A = reinterpret_cast<const C2*>(Av);
   C2* B = reinterpret_cast<C2*>(Bv);
   RMAT_CHECK(set_trsm_attrs<T>());
   const int gx = ceil_div(nrhs, 32);
+  // tensor-core block updates need the factor's split planes (written by a
+  // tensor-path factorisation), an even row stride and at most RMAT_YPL_ROWS columns
+  const bool tc = tensor && sizeof(T) == 4 && c->Fpl && nrhs % 2 == 0 && nrhs <= RMAT_YPL_ROWS &&
+                  ldb == nrhs;
+  const size_t yplane = (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB;
+  auto split_y = [&](int row0, int jb) -> int {
+    split_block_kernel<<<dim3(ceil_div(nrhs, 32), (int)round_up(jb, 32) / 32), 256, 0, c->stream>>>(
+        reinterpret_cast<const float2*>(B) + (size_t)row0 * ldb, ldb, jb, nrhs, nullptr, 0, 0, 0, 0,
+        c->Ypl, yplane, 0);
+    c->launches++;
+    RMAT_CU(cudaGetLastError());
+    return RMAT_OK;
+  };
   // forward: replay each panel's interchanges, then L11 solve and update below
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int jb = std::min(nb, n - k0);
-    rhs_swap_kernel<T><<<ceil_div(nrhs, 128), 128, 0, c->stream>>>(B, ldb, nrhs, k0, jb, n, ipiv,
-                                                                     c->dstat);
-    trsm_block_rhs_kernel<T, true><<<gx, 256, (size_t)jb * 32 * sizeof(C2), c->stream>>>(
-        A, ld, k0, jb, B, ldb, nrhs);
-    c->launches += 2;
+    RMAT_CHECK(apply_perm<T>(c, pm, B, ldb, nrhs, k0, nb, jb));
+    trsm_block_rhs_kernel<T, true><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B, ldb,
+                                                                            nrhs);
+    c->launches++;
     RMAT_CU(cudaGetLastError());
-    RMAT_CHECK(gemm_sub<T>(c, n - k0 - jb, nrhs, jb, A + (size_t)(k0 + jb) * ld + k0, ld,
-                           B + (size_t)k0 * ldb, ldb, B + (size_t)(k0 + jb) * ldb, ldb));
+    if (tc && n - k0 - jb > 0) {
+      RMAT_CHECK(split_y(k0, jb));
+      RMAT_CHECK(launch_solve_tc(c, reinterpret_cast<float2*>(B) + (size_t)(k0 + jb) * ldb, ldb,
+                                 n - k0 - jb, nrhs, k0, jb, k0 + jb, n));
+    } else {
+      RMAT_CHECK(gemm_sub<T>(c, n - k0 - jb, nrhs, jb, A + (size_t)(k0 + jb) * ld + k0, ld,
+                             B + (size_t)k0 * ldb, ldb, B + (size_t)(k0 + jb) * ldb, ldb));
+    }
   }
   // backward: U11 solve, then update the rows above (right-looking)
   const int last = ((n - 1) / nb) * nb;
   for (int k0 = last; k0 >= 0; k0 -= nb) {
     const int jb = std::min(nb, n - k0);
-    trsm_block_rhs_kernel<T, false><<<gx, 256, (size_t)jb * 32 * sizeof(C2), c->stream>>>(
-        A, ld, k0, jb, B, ldb, nrhs);
+    trsm_block_rhs_kernel<T, false><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B,
+                                                                             ldb, nrhs);
     c->launches++;
     RMAT_CU(cudaGetLastError());
-    RMAT_CHECK(gemm_sub<T>(c, k0, nrhs, jb, A + k0, ld, B + (size_t)k0 * ldb, ldb, B, ldb));
+    if (tc && k0 > 0) {
+      RMAT_CHECK(split_y(k0, jb));
+      RMAT_CHECK(launch_solve_tc(c, reinterpret_cast<float2*>(B), ldb, k0, nrhs, k0, jb, 0, n));
+    } else {
+      RMAT_CHECK(gemm_sub<T>(c, k0, nrhs, jb, A + k0, ld, B + (size_t)k0 * ldb, ldb, B, ldb));
+    }
   }
   return RMAT_OK;
 }
 
-template int lu_factor_dev<float>(rmat_ctx, void*, int, int, int*, int, bool);
-template int lu_factor_dev<double>(rmat_ctx, void*, int, int, int*, int, bool);
-template int lu_solve_dev<float>(rmat_ctx, const void*, int, int, const int*, int, void*, int, int);
-template int lu_solve_dev<double>(rmat_ctx, const void*, int, int, const int*, int, void*, int, int);
+template int lu_factor_dev<float>(rmat_ctx, void*, int, int, int*, int, bool, const LUPerm&);
+template int lu_factor_dev<double>(rmat_ctx, void*, int, int, int*, int, bool, const LUPerm&);
+template int lu_solve_dev<float>(rmat_ctx, const void*, int, int, const LUPerm&, int, void*, int,
+                                  int, bool);
+template int lu_solve_dev<double>(rmat_ctx, const void*, int, int, const LUPerm&, int, void*, int,
+                                   int, bool);
 
 int gemm_sub_c128(rmat_ctx c, int M, int N, int K, const double2* A, int lda, const double2* B,
                   int ldb, double2* C, int ldc) {

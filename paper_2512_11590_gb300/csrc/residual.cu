@@ -96,14 +96,19 @@ resid_coupling_kernel(double2* __restrict__ R, const double2* __restrict__ X, in
 
 // max |r| (bit pattern of a non-negative double is monotone) and r -> solve precision
 template <class T>
-__global__ void resid_norm_convert_kernel(const double2* __restrict__ R, size_t total,
-                                          cplx<T>* __restrict__ Bw,
+__global__ void resid_norm_convert_kernel(const double2* __restrict__ R, size_t total, int nrhs,
+                                          const double* __restrict__ D, cplx<T>* __restrict__ Bw,
                                           unsigned long long* __restrict__ red) {
   double m = 0.0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
-    const double2 z = R[e];
+    double2 z = R[e];
     m = fmax(m, hypot(z.x, z.y));
+    if (D) {
+      const double s = D[e / nrhs];
+      z.x *= s;
+      z.y *= s;
+    }
     Bw[e] = to_c(z, T());
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -135,30 +140,39 @@ __global__ void absmax_kernel(const double2* __restrict__ v, size_t total,
 }
 
 template <class T>
-__global__ void x_update_kernel(double2* __restrict__ X, const cplx<T>* __restrict__ D,
-                                size_t total) {
+__global__ void x_update_kernel(double2* __restrict__ X, const cplx<T>* __restrict__ W,
+                                size_t total, int nrhs, const double* __restrict__ D) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
-    const double2 d = to_d(D[e]);
+    const double2 d = to_d(W[e]);
+    const double s = D ? D[e / nrhs] : 1.0;
     double2 x = X[e];
-    x.x += d.x;
-    x.y += d.y;
+    x.x += s * d.x;
+    x.y += s * d.y;
     X[e] = x;
   }
 }
 
 template <class T>
-__global__ void x_from_w_kernel(double2* __restrict__ X, const cplx<T>* __restrict__ D,
-                                size_t total) {
+__global__ void x_from_w_kernel(double2* __restrict__ X, const cplx<T>* __restrict__ W,
+                                size_t total, int nrhs, const double* __restrict__ D) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x)
-    X[e] = to_d(D[e]);
+       e += (size_t)gridDim.x * blockDim.x) {
+    double2 x = to_d(W[e]);
+    if (D) {
+      const double s = D[e / nrhs];
+      x.x *= s;
+      x.y *= s;
+    }
+    X[e] = x;
+  }
 }
 
 // right-hand sides into the solve buffer: surface terms (assembled) or B (dense)
 template <class T>
 __global__ void w_from_phi_kernel(cplx<T>* __restrict__ Bw, int N, int nrhs, int nlag,
-                                  const double* __restrict__ fa, const double2* __restrict__ B64) {
+                                  const double* __restrict__ fa, const double2* __restrict__ B64,
+                                  const double* __restrict__ D) {
   const size_t total = (size_t)N * nrhs;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -169,6 +183,10 @@ __global__ void w_from_phi_kernel(cplx<T>* __restrict__ Bw, int N, int nrhs, int
     } else {
       const int al = row / nlag, i = row - al * nlag;
       z = make_double2(al == be ? fa[i] : 0.0, 0.0);
+    }
+    if (D) {
+      z.x *= D[row];
+      z.y *= D[row];
     }
     Bw[e] = to_c(z, T());
   }
@@ -215,12 +233,13 @@ int launch_residual(rmat_ctx c, double*) {
     RMAT_CHECK(gemm_sub_c128(c, N, nrhs, N, c->A64, N, c->X, nrhs, c->Rres, nrhs));
   }
   RMAT_CU(cudaGetLastError());
+  const double* D = c->equil ? c->Dsc : nullptr;
   if (c->precision == RMAT_C128)
     resid_norm_convert_kernel<double><<<grid_for(c, total), 256, 0, c->stream>>>(
-        c->Rres, total, reinterpret_cast<double2*>(c->Bw), c->red);
+        c->Rres, total, nrhs, D, reinterpret_cast<double2*>(c->Bw), c->red);
   else
     resid_norm_convert_kernel<float><<<grid_for(c, total), 256, 0, c->stream>>>(
-        c->Rres, total, reinterpret_cast<float2*>(c->Bw), c->red);
+        c->Rres, total, nrhs, D, reinterpret_cast<float2*>(c->Bw), c->red);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;
@@ -228,12 +247,13 @@ int launch_residual(rmat_ctx c, double*) {
 
 int launch_update(rmat_ctx c) {
   const size_t total = (size_t)c->N * c->nrhs;
+  const double* D = c->equil ? c->Dsc : nullptr;
   if (c->precision == RMAT_C128)
     x_update_kernel<double><<<grid_for(c, total), 256, 0, c->stream>>>(
-        c->X, reinterpret_cast<const double2*>(c->Bw), total);
+        c->X, reinterpret_cast<const double2*>(c->Bw), total, c->nrhs, D);
   else
     x_update_kernel<float><<<grid_for(c, total), 256, 0, c->stream>>>(
-        c->X, reinterpret_cast<const float2*>(c->Bw), total);
+        c->X, reinterpret_cast<const float2*>(c->Bw), total, c->nrhs, D);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;
@@ -241,12 +261,13 @@ int launch_update(rmat_ctx c) {
 
 int launch_x_from_w(rmat_ctx c) {
   const size_t total = (size_t)c->N * c->nrhs;
+  const double* D = c->equil ? c->Dsc : nullptr;
   if (c->precision == RMAT_C128)
     x_from_w_kernel<double><<<grid_for(c, total), 256, 0, c->stream>>>(
-        c->X, reinterpret_cast<const double2*>(c->Bw), total);
+        c->X, reinterpret_cast<const double2*>(c->Bw), total, c->nrhs, D);
   else
     x_from_w_kernel<float><<<grid_for(c, total), 256, 0, c->stream>>>(
-        c->X, reinterpret_cast<const float2*>(c->Bw), total);
+        c->X, reinterpret_cast<const float2*>(c->Bw), total, c->nrhs, D);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;
@@ -255,12 +276,13 @@ int launch_x_from_w(rmat_ctx c) {
 int launch_w_from_phi(rmat_ctx c) {
   const size_t total = (size_t)c->N * c->nrhs;
   const double2* B64 = (c->kind == 2) ? c->B64 : nullptr;
+  const double* D = c->equil ? c->Dsc : nullptr;
   if (c->precision == RMAT_C128)
     w_from_phi_kernel<double><<<grid_for(c, total), 256, 0, c->stream>>>(
-        reinterpret_cast<double2*>(c->Bw), c->N, c->nrhs, c->nlag, c->fa, B64);
+        reinterpret_cast<double2*>(c->Bw), c->N, c->nrhs, c->nlag, c->fa, B64, D);
   else
     w_from_phi_kernel<float><<<grid_for(c, total), 256, 0, c->stream>>>(
-        reinterpret_cast<float2*>(c->Bw), c->N, c->nrhs, c->nlag, c->fa, B64);
+        reinterpret_cast<float2*>(c->Bw), c->N, c->nrhs, c->nlag, c->fa, B64, D);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;

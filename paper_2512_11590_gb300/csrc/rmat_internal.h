@@ -14,6 +14,8 @@
 #define RMAT_MAX_PANEL_CTAS 256
 // Largest LU block width supported by the panel/TRSM kernels.
 #define RMAT_MAX_NB 256
+// Rows of the right-hand-side plane buffer (max nrhs on the tensor solve path).
+#define RMAT_YPL_ROWS 1024
 
 struct PanelScratch {
   // barrier counter + candidate slots of the one-barrier-per-column panel
@@ -22,6 +24,15 @@ struct PanelScratch {
   int* cidx;           // [2][RMAT_MAX_PANEL_CTAS]
   void* crow;          // [2][RMAT_MAX_PANEL_CTAS][RMAT_MAX_NB] of complex T
   void* trow;          // [2][RMAT_MAX_NB] of complex T
+};
+
+// Net row permutation of each LU block (built once per factorisation, reused
+// by every solve): rows [nblocks][2*nb], idx [nblocks][nb], cnt [nblocks].
+struct LUPerm {
+  int* rows = nullptr;
+  int* idx = nullptr;
+  int* cnt = nullptr;
+  size_t cap = 0;  // bytes
 };
 
 // Device status words written by kernels (read back by the host).
@@ -36,6 +47,8 @@ struct rmat_ctx_s {
   int panel_ctas_param = 0;
   long long spin_limit = 20000000LL;   // ~ seconds of polling
   int timing = 0;
+  int equil_param = -1;   // -1: default (on for complex64 paths), 0 off, 1 on
+  bool equil = false;     // symmetric diagonal equilibration active for this problem
 
   // problem description
   int kind = 0;          // 0 none, 1 assembled, 2 dense
@@ -54,6 +67,7 @@ struct rmat_ctx_s {
   double2* A64 = nullptr;  size_t A64_cap = 0;      // dense loaded system in complex128 (row-major)
   double2* B64 = nullptr;  size_t B64_cap = 0;      // dense loaded right-hand sides (row-major N x nrhs)
   int* ipiv = nullptr;     size_t ipiv_cap = 0;
+  LUPerm perm_main, perm_z;                         // main factor / matching-system factor
   double* Kmat = nullptr;  size_t Kmat_cap = 0;     // hm*T0 - hm*(B/a) f f^T  [nlag*nlag]
   double* T0 = nullptr;    size_t T0_cap = 0;       // T0 [nlag*nlag]
   double* rmesh = nullptr; size_t rmesh_cap = 0;    // r_i
@@ -64,8 +78,11 @@ struct rmat_ctx_s {
   double2* X = nullptr;    size_t X_cap = 0;        // FP64 solution, row-major N x nrhs
   double2* Rres = nullptr; size_t Rres_cap = 0;     // FP64 residual, row-major N x nrhs
   void* Bw = nullptr;      size_t Bw_cap = 0;       // solve work in the factor precision
-  float* Apl = nullptr;    size_t Apl_cap = 0;      // tensor A operand planes (L21 split)
+  float* Fpl = nullptr;    size_t Fpl_cap = 0;      // full-size split factor planes [4][N][ld] (A operand)
+  float* Ypl = nullptr;    size_t Ypl_cap = 0;      // right-hand-side block planes [4][RMAT_YPL_ROWS][256]
   float* Bpl = nullptr;    size_t Bpl_cap = 0;      // tensor B operand planes (U12^T split)
+  double* Dsc = nullptr;   size_t Dsc_cap = 0;      // equilibration scale per row
+  std::vector<double> ir_hist;                      // refinement history of the last solve
   double2* Rint = nullptr; size_t Rint_cap = 0;     // R-matrix (row-major nch x nch)
   double2* Zbuf = nullptr; size_t Zbuf_cap = 0;     // matching system (nch x nch + nch x nopen)
   int* zpiv = nullptr;     size_t zpiv_cap = 0;
@@ -103,13 +120,17 @@ int launch_point_coupling(rmat_ctx c, const double2* V, double E);
 int launch_load_dense(rmat_ctx c, const double2* A, int lda, const double2* B, int ldb);
 // lu.cu
 template <class T>
-int lu_factor_dev(rmat_ctx c, void* A, int n, int ld, int* ipiv, int nb, bool tensor);
+int lu_factor_dev(rmat_ctx c, void* A, int n, int ld, int* ipiv, int nb, bool tensor,
+                  const LUPerm& pm);
 template <class T>
-int lu_solve_dev(rmat_ctx c, const void* A, int n, int ld, const int* ipiv, int nb,
-                 void* B, int ldb, int nrhs);
+int lu_solve_dev(rmat_ctx c, const void* A, int n, int ld, const LUPerm& pm, int nb,
+                 void* B, int ldb, int nrhs, bool tensor = false);
+int perm_reserve(rmat_ctx c, LUPerm& pm, int n, int nb);
 // gemm_tc.cu
 int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n);
-int tc_prepare(rmat_ctx c, int n, int nb);
+int launch_solve_tc(rmat_ctx c, float2* Bsub, int ldb, int M, int nrhs, int k0, int jb, int ay0,
+                    int n);
+int tc_prepare(rmat_ctx c, int n, int nrhs);
 // lu.cu (SIMT complex GEMM C -= A B, row-major)
 int gemm_sub_c128(rmat_ctx c, int M, int N, int K, const double2* A, int lda, const double2* B,
                   int ldb, double2* C, int ldc);

@@ -139,3 +139,25 @@ def test_bounded_panel_wait_times_out_cleanly(g, ctx):
         g.rmat_set_param(ctx, g.RMAT_PARAM_PANEL_CTAS, 0)
     out = run_dense(ctx, A[:200, :200], B[:200], 0)
     assert relerr(out["X"], np.linalg.solve(A[:200, :200], B[:200])) < 1e-12
+
+
+@pytest.mark.parametrize("prec,nb", [(1, 32), (1, 128), (2, 128), (0, 32), (0, 64)])
+def test_block_widths(g, ctx, prec, nb):
+    p = cp.config2(16)
+    ref = truth(p, "c2-16")
+    out = run_problem(ctx, p, prec, max_refine=30, tol=1e-14, nb=nb)
+    assert relerr(out["U"], ref["U"]) < TOL[prec]
+
+
+@pytest.mark.parametrize("equil", [0, 1])
+def test_equilibration_switch(g, ctx, equil):
+    p = cp.config3(16, W=-1.0)               # config 3b: weaker absorption, worse conditioned
+    ref = truth(p, "c3b-16")
+    g.rmat_set_param(ctx, g.RMAT_PARAM_EQUILIBRATE, equil)
+    try:
+        out = run_problem(ctx, p, 1, max_refine=40, tol=1e-14)
+        hist = g.rmat_refine_history(ctx)
+    finally:
+        g.rmat_set_param(ctx, g.RMAT_PARAM_EQUILIBRATE, -1)
+    assert relerr(out["U"], ref["U"]) < TOL[1]
+    assert len(hist) == out["iters"] + 1 and hist[-1] < 1e-11
