@@ -151,9 +151,10 @@ int rmat_factor(rmat_ctx ctx, int* info);
 
 /* Solve C X = Phi (or A X = B) with the factors, then refine:
  *   loop: r = Phi - C X in FP64 (structured for assembled problems, dense for
- *   loaded ones); stop when max|r|/max|Phi| < tol, when the ratio fails to
- *   drop below 0.5x the previous one twice in a row (stagnation), or after
- *   max_refine steps; else solve C d = r with the factors and X += d (FP64).
+ *   loaded ones); stop when max|r|/max|Phi| < tol, when it fails to drop below
+ *   half of the previous step's value (stagnation at the FP64 floor, or
+ *   divergence), or after max_refine steps; else solve C d = r with the
+ *   factors and X += d (FP64).
  * X_dev: device complex128 N x nrhs column-major, ldx >= N (caller-owned).
  * iters (may be NULL): refinement steps taken.  rel_resid (may be NULL): the
  * last max|r|/max|Phi| measured (0 when max_refine == 0 and tol <= 0, in

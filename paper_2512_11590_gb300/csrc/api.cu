@@ -415,7 +415,6 @@ int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int
   c->ir_hist.clear();
   if (max_refine > 0 || tol > 0) {
     double prev = INFINITY;
-    int stagn = 0;
     for (;;) {
       RMAT_CHECK(launch_residual(c, nullptr));
       rel = read_red(c) / c->phi_max;
@@ -429,13 +428,9 @@ int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int
         status = tol > 0 ? RMAT_ENOCONV : RMAT_OK;
         break;
       }
-      if (rel > 0.5 * prev) {
-        if (++stagn >= 2) {
-          status = RMAT_ENOCONV;
-          break;
-        }
-      } else {
-        stagn = 0;
+      if (rel > 0.5 * prev) {  // no longer contracting: the FP64 floor (or divergence)
+        status = RMAT_ENOCONV;
+        break;
       }
       prev = rel;
       RMAT_CHECK(solve_factors(c));

@@ -34,12 +34,14 @@ constexpr int TC_THREADS = 192;
 constexpr uint32_t A_PLANE_BYTES = TC_BM * TC_BK * 4;                              // 4 KB
 constexpr uint32_t B_PLANE_BYTES = TC_BN * TC_BK * 4;                              // 8 KB
 constexpr uint32_t STAGE_BYTES = 4 * A_PLANE_BYTES + 4 * B_PLANE_BYTES;            // 48 KB
-constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t STAGING_BYTES = TC_BM * 32 * 4;  // 16 complex columns x 128 rows, 128B swizzle
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + 2 * STAGING_BYTES + 1024 + 256;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
 
 struct TcMaps {
-  CUtensorMap a[4];  // L21 planes: re_hi, re_lo, im_hi, im_lo
-  CUtensorMap b[4];  // U12^T planes
+  CUtensorMap a[4];  // A operand planes: re_hi, re_lo, im_hi, im_lo
+  CUtensorMap b[4];  // B operand planes
+  CUtensorMap c;     // output C viewed as fp32 [rows][2*cols], reduce-add target
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -141,6 +143,36 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 #pragma unroll
   for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::
+          "l"(reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(src)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void epi_bar() {  // the 128 epilogue threads only
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -158,17 +190,18 @@ __device__ __forceinline__ void product(int p, int& qa, int& qb, int& acc, int& 
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-tc_update_kernel(const __grid_constant__ TcMaps maps, float2* __restrict__ C, int ldc, int M,
-                 int Nn, int K, int ax0, int rowA0, int bx0, int rowB0, int vec_ok,
-                 int* __restrict__ err) {
+tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, int Nn, int K,
+                 int ax0, int rowA0, int bx0, int rowB0, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   unsigned char* stages = smem;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + TC_STAGES * STAGE_BYTES);
+  unsigned char* staging = stages + TC_STAGES * STAGE_BYTES;  // 2 x 16 KB, 1024-aligned
+  uint64_t* bars = reinterpret_cast<uint64_t*>(staging + 2 * STAGING_BYTES);
   // bars[0..3] full, [4..7] empty, [8] tmem_full, [9] tmem_empty
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* epi_abort = abort_flag + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mt = (M + TC_BM - 1) / TC_BM;
@@ -273,56 +306,59 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, float2* __restrict__ C, in
     }
   } else {
     // -------------------------------- epilogue --------------------------------
+    // TMEM row -> registers -> (negated) swizzled shared staging tile -> TMA
+    // reduce-add into C.  The L2 performs C += (-acc); no load of C sits on this
+    // path, and TMEM is handed back to the MMA warp as soon as it has been read.
     const int quad = warp & 3;               // TMEM lane quadrant this warp may access
     const int row = quad * 32 + lane;
-    uint32_t tcount = 0;
+    const bool leader = (warp == 2 && lane == 0);
+    uint32_t tcount = 0, chunk = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
       const int m0 = (tile % mt) * TC_BM, n0 = (tile / mt) * TC_BN;
+      // The four epilogue warps leave together (they share named barriers): each
+      // waits (bounded), then one thread snapshots the abort flag for all.
       if (!mbar_wait(smem_u32(&bars[8]), tcount & 1, abort_flag)) {
         *abort_flag = 1;
         atomicExch(err, 2);
-        break;
       }
+      epi_bar();
+      if (threadIdx.x == 64) *epi_abort = *abort_flag;
+      epi_bar();
+      if (*epi_abort) break;
       fence_after();
-      const int gm = m0 + row;
-      float2* Crow = C + (size_t)gm * ldc + n0;
+      const bool rowvalid = (m0 + row) < M;
 #pragma unroll 1
-      for (int ch = 0; ch < TC_BN / 32; ++ch) {
-        float re[32], im[32];
-        const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + ch * 32;
-        tmem_ld32(ta, re);
-        tmem_ld32(ta + TC_BN, im);
+      for (int ch = 0; ch < TC_BN / 16; ++ch, ++chunk) {
+        float re[16], im[16];
+        const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + ch * 16;
+        tmem_ld16(ta, re);
+        tmem_ld16(ta + TC_BN, im);
         tmem_wait_ld();
-        if (gm < M) {
-          const int c0 = ch * 32;
-          if (vec_ok && n0 + c0 + 32 <= Nn) {
-            float4* p4 = reinterpret_cast<float4*>(Crow + c0);
+        if (ch == TC_BN / 16 - 1) {          // accumulators fully read: release TMEM
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&bars[9]));
+        }
+        unsigned char* buf = staging + (chunk & 1) * STAGING_BYTES;
+        if (leader) bulk_wait_read1();       // the reduce that used this buffer has read it
+        epi_bar();
+        float4* rowp = reinterpret_cast<float4*>(buf + row * 128);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              float4 v = p4[k];
-              v.x -= re[2 * k];
-              v.y -= im[2 * k];
-              v.z -= re[2 * k + 1];
-              v.w -= im[2 * k + 1];
-              p4[k] = v;
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-              if (n0 + c0 + k < Nn) {
-                float2 v = Crow[c0 + k];
-                v.x -= re[k];
-                v.y -= im[k];
-                Crow[c0 + k] = v;
-              }
-            }
-          }
+        for (int k = 0; k < 8; ++k) {
+          const float4 v = rowvalid ? make_float4(-re[2 * k], -im[2 * k], -re[2 * k + 1],
+                                                  -im[2 * k + 1])
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+          rowp[k ^ (row & 7)] = v;
+        }
+        fence_proxy_async_smem();
+        epi_bar();
+        if (leader) {
+          tma_reduce_add_2d(&maps.c, smem_u32(buf), 2 * (cx0 + n0 + ch * 16), cy0 + m0);
+          bulk_commit();
         }
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bars[9]));
     }
+    if (leader) bulk_wait_all();
   }
   fence_before();
   __syncthreads();
@@ -351,6 +387,20 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
+// C viewed as fp32 [rows][2*cols] (interleaved complex), 16 complex columns x 128 rows per box.
+int make_out_map(CUtensorMap* m, void* base, int cols, int rows, int ld_complex) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return RMAT_ECUDA;
+  cuuint64_t dims[2] = {(cuuint64_t)2 * cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld_complex * 2 * sizeof(float)};
+  cuuint32_t box[2] = {32, (cuuint32_t)TC_BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RMAT_OK : RMAT_ECUDA;
+}
+
 int make_plane_map(CUtensorMap* m, float* base, int cols, int rows, int row_stride, int box_rows) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return RMAT_ECUDA;
@@ -372,13 +422,15 @@ struct TcCache {
   const float* f = nullptr;
   const float* b = nullptr;
   const float* y = nullptr;
+  const void* cmat = nullptr;
+  const void* bw = nullptr;
   int n = -1, ldf = -1, nrhs = -1;
   TcMaps upd, sol;
   bool attr = false;
 };
 TcCache g_tc;
 
-int launch_tc(rmat_ctx c, const TcMaps& maps, float2* C, int ldc, int M, int Nn, int K, int ax0,
+int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, int K, int ax0,
               int ay0, int bx0, int by0, bool count_as_update) {
   if (M <= 0 || Nn <= 0 || K <= 0) return RMAT_OK;
   if (K % TC_BK || ax0 % TC_BK || bx0 % TC_BK) return RMAT_ESTATE;
@@ -389,15 +441,14 @@ int launch_tc(rmat_ctx c, const TcMaps& maps, float2* C, int ldc, int M, int Nn,
   }
   const int tiles = ceil_div(M, TC_BM) * ceil_div(Nn, TC_BN);
   const int grid = std::min(tiles, c->sm_count);
-  const int vec_ok = (ldc % 2 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing && count_as_update) {
     e0 = rmat_event(c);
     e1 = rmat_event(c);
     RMAT_CU(cudaEventRecord(e0, c->stream));
   }
-  tc_update_kernel<<<grid, TC_THREADS, TC_SMEM, c->stream>>>(maps, C, ldc, M, Nn, K, ax0, ay0, bx0,
-                                                             by0, vec_ok, c->dstat + ST_TIMEOUT);
+  tc_update_kernel<<<grid, TC_THREADS, TC_SMEM, c->stream>>>(maps, cx0, cy0, M, Nn, K, ax0, ay0,
+                                                             bx0, by0, c->dstat + ST_TIMEOUT);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   if (count_as_update) {
@@ -415,9 +466,10 @@ int launch_tc(rmat_ctx c, const TcMaps& maps, float2* C, int ldc, int M, int Nn,
 
 int tc_prepare(rmat_ctx c, int n, int nrhs) {
   const int ldf = c->ld;
-  if (g_tc.f == c->Fpl && g_tc.b == c->Bpl && g_tc.y == c->Ypl && g_tc.n == n && g_tc.ldf == ldf &&
-      g_tc.nrhs == nrhs)
+  if (g_tc.f == c->Fpl && g_tc.b == c->Bpl && g_tc.y == c->Ypl && g_tc.cmat == c->C &&
+      g_tc.bw == c->Bw && g_tc.n == n && g_tc.ldf == ldf && g_tc.nrhs == nrhs)
     return RMAT_OK;
+  if (nrhs % 2) return RMAT_ESTATE;
   const size_t fplane = (size_t)n * ldf, bplane = (size_t)n * RMAT_MAX_NB,
                yplane = (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB;
   for (int q = 0; q < 4; ++q) {
@@ -428,9 +480,13 @@ int tc_prepare(rmat_ctx c, int n, int nrhs) {
     RMAT_CHECK(make_plane_map(&g_tc.sol.b[q], c->Ypl + q * yplane, RMAT_MAX_NB,
                               std::max(1, nrhs), RMAT_MAX_NB, TC_BN));
   }
+  RMAT_CHECK(make_out_map(&g_tc.upd.c, c->C, n, n, c->ld));
+  RMAT_CHECK(make_out_map(&g_tc.sol.c, c->Bw, std::max(2, nrhs), n, std::max(2, nrhs)));
   g_tc.f = c->Fpl;
   g_tc.b = c->Bpl;
   g_tc.y = c->Ypl;
+  g_tc.cmat = c->C;
+  g_tc.bw = c->Bw;
   g_tc.n = n;
   g_tc.ldf = ldf;
   g_tc.nrhs = nrhs;
@@ -441,14 +497,13 @@ int tc_prepare(rmat_ctx c, int n, int nrhs) {
 int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n) {
   const int rest = n - k0 - jb;
   if (rest <= 0) return RMAT_OK;
-  RMAT_CHECK(tc_prepare(c, n, c->nrhs));
-  float2* C22 = A + (size_t)(k0 + jb) * ld + (k0 + jb);
-  return launch_tc(c, g_tc.upd, C22, ld, rest, rest, jb, k0, k0 + jb, 0, k0 + jb, true);
+  if (reinterpret_cast<void*>(A) != c->C || ld != c->ld) return RMAT_ESTATE;
+  RMAT_CHECK(tc_prepare(c, n, c->nrhs + (c->nrhs & 1)));
+  return launch_tc(c, g_tc.upd, k0 + jb, k0 + jb, rest, rest, jb, k0, k0 + jb, 0, k0 + jb, true);
 }
 
 // Solve update: Bsub[M x nrhs] -= F[rows ay0.., cols k0..k0+jb] * Y, Y^T planes in Ypl.
-int launch_solve_tc(rmat_ctx c, float2* Bsub, int ldb, int M, int nrhs, int k0, int jb, int ay0,
-                    int n) {
+int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n) {
   RMAT_CHECK(tc_prepare(c, n, nrhs));
-  return launch_tc(c, g_tc.sol, Bsub, ldb, M, nrhs, jb, k0, ay0, 0, 0, false);
+  return launch_tc(c, g_tc.sol, 0, row0, M, nrhs, jb, k0, ay0, 0, 0, false);
 }

@@ -358,9 +358,25 @@ trsm_block_rhs_kernel(const cplx<T>* __restrict__ A, int ld, int k0, int jb,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.x * 32 + lane;
   const bool act = col < nrhs;
-  for (int e = threadIdx.x; e < jb * jb; e += 256) {
-    const int i = e / jb, t = e - i * jb;
-    Ls[i * lds + t] = A[(size_t)(k0 + i) * ld + k0 + t];
+  // stage the diagonal block: 8 independent loads in flight per thread
+  for (int e0 = threadIdx.x; e0 < jb * jb; e0 += 256 * 8) {
+    C2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 256;
+      if (e < jb * jb) {
+        const int i = e / jb, t = e - i * jb;
+        v[u] = A[(size_t)(k0 + i) * ld + k0 + t];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 256;
+      if (e < jb * jb) {
+        const int i = e / jb, t = e - i * jb;
+        Ls[i * lds + t] = v[u];
+      }
+    }
   }
   __syncthreads();
   const int ngroups = (jb + 7) / 8;
@@ -647,7 +663,7 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
   // tensor-core block updates need the factor's split planes (written by a
   // tensor-path factorisation), an even row stride and at most RMAT_YPL_ROWS columns
   const bool tc = tensor && sizeof(T) == 4 && c->Fpl && nrhs % 2 == 0 && nrhs <= RMAT_YPL_ROWS &&
-                  ldb == nrhs;
+                  ldb == nrhs && Bv == c->Bw;
   const size_t yplane = (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB;
   auto split_y = [&](int row0, int jb) -> int {
     split_block_kernel<<<dim3(ceil_div(nrhs, 32), (int)round_up(jb, 32) / 32), 256, 0, c->stream>>>(
@@ -667,8 +683,7 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     RMAT_CU(cudaGetLastError());
     if (tc && n - k0 - jb > 0) {
       RMAT_CHECK(split_y(k0, jb));
-      RMAT_CHECK(launch_solve_tc(c, reinterpret_cast<float2*>(B) + (size_t)(k0 + jb) * ldb, ldb,
-                                 n - k0 - jb, nrhs, k0, jb, k0 + jb, n));
+      RMAT_CHECK(launch_solve_tc(c, k0 + jb, n - k0 - jb, nrhs, k0, jb, k0 + jb, n));
     } else {
       RMAT_CHECK(gemm_sub<T>(c, n - k0 - jb, nrhs, jb, A + (size_t)(k0 + jb) * ld + k0, ld,
                              B + (size_t)k0 * ldb, ldb, B + (size_t)(k0 + jb) * ldb, ldb));
@@ -684,7 +699,7 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     RMAT_CU(cudaGetLastError());
     if (tc && k0 > 0) {
       RMAT_CHECK(split_y(k0, jb));
-      RMAT_CHECK(launch_solve_tc(c, reinterpret_cast<float2*>(B), ldb, k0, nrhs, k0, jb, 0, n));
+      RMAT_CHECK(launch_solve_tc(c, 0, k0, nrhs, k0, jb, 0, n));
     } else {
       RMAT_CHECK(gemm_sub<T>(c, k0, nrhs, jb, A + k0, ld, B + (size_t)k0 * ldb, ldb, B, ldb));
     }

@@ -128,8 +128,8 @@ int lu_solve_dev(rmat_ctx c, const void* A, int n, int ld, const LUPerm& pm, int
 int perm_reserve(rmat_ctx c, LUPerm& pm, int n, int nb);
 // gemm_tc.cu
 int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n);
-int launch_solve_tc(rmat_ctx c, float2* Bsub, int ldb, int M, int nrhs, int k0, int jb, int ay0,
-                    int n);
+// solve update: rows [row0, row0+M) of the solve buffer Bw (ld = nrhs) -= F(ay0.., k0..k0+jb) * Y
+int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n);
 int tc_prepare(rmat_ctx c, int n, int nrhs);
 // lu.cu (SIMT complex GEMM C -= A B, row-major)
 int gemm_sub_c128(rmat_ctx c, int M, int N, int K, const double2* A, int lda, const double2* B,
