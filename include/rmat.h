@@ -153,7 +153,8 @@ int rmat_factor(rmat_ctx ctx, int* info);
  *   loop: r = Phi - C X in FP64 (structured for assembled problems, dense for
  *   loaded ones); stop when max|r|/max|Phi| < tol, when it fails to drop below
  *   half of the previous step's value (stagnation at the FP64 floor, or
- *   divergence), or after max_refine steps; else solve C d = r with the
+ *   divergence: once for the complex64 precisions, twice in a row for
+ *   RMAT_C128), or after max_refine steps; else solve C d = r with the
  *   factors and X += d (FP64).
  * X_dev: device complex128 N x nrhs column-major, ldx >= N (caller-owned).
  * iters (may be NULL): refinement steps taken.  rel_resid (may be NULL): the

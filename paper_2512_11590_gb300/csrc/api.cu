@@ -415,6 +415,11 @@ int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int
   c->ir_hist.clear();
   if (max_refine > 0 || tol > 0) {
     double prev = INFINITY;
+    // complex64 factors: one non-halving step ends the refinement (each extra
+    // correction costs a full solve); complex128: two, one more FP64 correction
+    // past the floor still sharpens X, R and U at the 1e-12 level
+    const int patience = c->precision == RMAT_C128 ? 2 : 1;
+    int stagn = 0;
     for (;;) {
       RMAT_CHECK(launch_residual(c, nullptr));
       rel = read_red(c) / c->phi_max;
@@ -429,8 +434,12 @@ int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int
         break;
       }
       if (rel > 0.5 * prev) {  // no longer contracting: the FP64 floor (or divergence)
-        status = RMAT_ENOCONV;
-        break;
+        if (++stagn >= patience) {
+          status = RMAT_ENOCONV;
+          break;
+        }
+      } else {
+        stagn = 0;
       }
       prev = rel;
       RMAT_CHECK(solve_factors(c));
