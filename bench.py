@@ -242,6 +242,25 @@ def reference_main(args):
     return 0
 
 
+def profile_step(nch):
+    """Launch sequence for ncu: the warm-up step uses the SIMT precision, so the
+    first tensor-core launch of the run is the first trailing update at N = nch*100."""
+    import torch
+
+    import cc_problems as cp
+    import paper_2512_11590_gb300 as g
+    torch.cuda.set_device(0)
+    warm = Runner(cp.config3(16), g.RMAT_C64_SIMT_IR, 0)
+    warm.step()
+    warm.close()
+    run = Runner(cp.config3(nch), g.RMAT_C64_3XTF32_IR, 0)
+    run.step()
+    torch.cuda.synchronize()
+    print("profile step", nch, run.last)
+    run.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -252,12 +271,18 @@ def main():
     ap.add_argument("--small", action="store_true", help="N=1600 instead of N=25600")
     ap.add_argument("--no-fp64", action="store_true", help="skip the complex128 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="for ncu: one untimed SIMT warm-up step at N=1600, then one FP32+IR "
+                         "tensor step at N = nch*100; no timing, no JSON")
+    ap.add_argument("--nch", type=int, default=256, help="channels of the --profile-step system")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warmup must be >= 3", file=sys.stderr)
         return 2
     if args.impl == "reference":
         return reference_main(args)
+    if args.profile_step:
+        return profile_step(args.nch)
 
     import torch
     import paper_2512_11590_gb300 as g

@@ -413,6 +413,131 @@ trsm_block_rhs_kernel(const cplx<T>* __restrict__ A, int ld, int k0, int jb,
     for (int i = warp; i < jb; i += 8) B[(size_t)(k0 + i) * ldb + col] = xs[i * 32 + lane];
 }
 
+// Fused block solve for a block of exactly JB rows (JB in {32, 64, 128}),
+// 32 right-hand-side columns per CTA (lane = column), 8 warps:
+//   1. stage the diagonal block (L11 unit lower, or U11) in shared memory;
+//   2. LOWER with a permutation list: gather the involved rows, replay the
+//      block's interchanges in shared memory, write the rows below the block back;
+//   3. right-looking substitution with the block's rows in registers (warp w
+//      owns solve positions w, w+8, ...): per step the owner publishes x_s,
+//      then every warp subtracts L[i][s] x_s from its remaining rows;
+//   4. write the solved rows, and (float, Y != nullptr) their TF32 split
+//      planes transposed, the B operand of the tensor-core block update.
+template <class T, bool LOWER, int JB>
+__global__ void __launch_bounds__(256)
+solve_block_kernel(const cplx<T>* __restrict__ A, int ld, int k0, cplx<T>* __restrict__ B,
+                   int ldb, int ncols, int nbp, const int* __restrict__ prow,
+                   const int* __restrict__ pidx, const int* __restrict__ pcnt,
+                   float* __restrict__ Y, size_t yplane) {
+  using C2 = cplx<T>;
+  constexpr int RPW = JB / 8;
+  constexpr int LDS = JB + 1;
+  extern __shared__ unsigned char smem_raw[];
+  C2* Ls = reinterpret_cast<C2*>(smem_raw);  // [JB][LDS]
+  C2* vals = Ls + JB * LDS;                  // [2*JB][32] gather; reused as xs [JB][33]
+  C2* xs = vals;
+  C2* dinv = vals + 2 * JB * 32;             // [JB]
+  int* rows = reinterpret_cast<int*>(dinv + JB);  // [2*JB]
+  int* idx = rows + 2 * JB;                  // [JB]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.x * 32 + lane;
+  const bool act = col < ncols;
+
+  for (int e0 = threadIdx.x; e0 < JB * JB; e0 += 256 * 8) {
+    C2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 256;
+      if (e < JB * JB) v[u] = A[(size_t)(k0 + e / JB) * ld + k0 + e % JB];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 256;
+      if (e < JB * JB) Ls[(e / JB) * LDS + e % JB] = v[u];
+    }
+  }
+  int cnt = JB;
+  if (prow) {
+    const int blk = k0 / nbp;
+    cnt = pcnt[blk];
+    for (int q = threadIdx.x; q < cnt; q += 256) rows[q] = prow[(size_t)blk * 2 * nbp + q];
+    for (int q = threadIdx.x; q < JB; q += 256) idx[q] = pidx[(size_t)blk * nbp + q];
+  } else {
+    for (int q = threadIdx.x; q < JB; q += 256) rows[q] = k0 + q;
+  }
+  __syncthreads();
+  if (!LOWER)
+    for (int q = threadIdx.x; q < JB; q += 256) dinv[q] = cdiv<T>(mkc<T>(1, 0), Ls[q * LDS + q]);
+  for (int q = warp; q < cnt; q += 8)
+    vals[q * 32 + lane] = act ? B[(size_t)rows[q] * ldb + col] : mkc<T>(0, 0);
+  __syncthreads();
+  if (prow && warp == 0) {
+    for (int t = 0; t < JB; ++t) {
+      const int sl = idx[t];
+      if (sl != t) {
+        const C2 u = vals[t * 32 + lane];
+        vals[t * 32 + lane] = vals[sl * 32 + lane];
+        vals[sl * 32 + lane] = u;
+      }
+    }
+  }
+  __syncthreads();
+  if (prow)
+    for (int q = JB + warp; q < cnt; q += 8)
+      if (act) B[(size_t)rows[q] * ldb + col] = vals[q * 32 + lane];
+  C2 b[RPW];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int sp = r * 8 + warp;
+    b[r] = vals[(LOWER ? sp : JB - 1 - sp) * 32 + lane];
+  }
+  __syncthreads();  // vals is reused as xs below
+  for (int sp = 0; sp < JB; ++sp) {
+    const int is = LOWER ? sp : JB - 1 - sp;
+    if (warp == (sp & 7)) {
+      const int rs = sp >> 3;
+      C2 x = b[0];
+#pragma unroll
+      for (int r = 1; r < RPW; ++r)
+        if (r == rs) x = b[r];
+      if (!LOWER) x = cmul<T>(x, dinv[is]);
+      xs[is * 33 + lane] = x;
+    }
+    __syncthreads();
+    const C2 xv = xs[is * 33 + lane];
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const int s2 = r * 8 + warp;
+      if (s2 > sp) csub_mul<T>(b[r], Ls[(LOWER ? s2 : JB - 1 - s2) * LDS + is], xv);
+    }
+  }
+  __syncthreads();
+  if (act)
+    for (int i = warp; i < JB; i += 8) B[(size_t)(k0 + i) * ldb + col] = xs[i * 33 + lane];
+  if (Y) {
+    for (int cc = warp; cc < 32; cc += 8) {
+      const int gc = blockIdx.x * 32 + cc;
+      if (gc >= ncols) continue;
+      for (int i = lane; i < JB; i += 32) {
+        const C2 z = xs[i * 33 + cc];
+        const float re = (float)z.x, im = (float)z.y;
+        const float rh = tf32_round(re), ih = tf32_round(im);
+        const size_t o = (size_t)gc * RMAT_MAX_NB + i;
+        Y[o] = rh;
+        Y[yplane + o] = re - rh;
+        Y[2 * yplane + o] = ih;
+        Y[3 * yplane + o] = im - ih;
+      }
+    }
+  }
+}
+
+template <class T, int JB>
+size_t solve_block_smem() {
+  return (size_t)JB * (JB + 1) * sizeof(cplx<T>) + (size_t)2 * JB * 32 * sizeof(cplx<T>) +
+         (size_t)JB * sizeof(cplx<T>) + (size_t)3 * JB * sizeof(int);
+}
+
 template <class T>
 size_t trsm_smem(int jb) {
   return (size_t)jb * 32 * sizeof(cplx<T>) + (size_t)jb * (jb + 1) * sizeof(cplx<T>);
@@ -593,6 +718,37 @@ int apply_perm(rmat_ctx c, const LUPerm& pm, cplx<T>* B, int ldb, int ncols, int
   return RMAT_OK;
 }
 
+// Fused block solve when jb is a supported width; *done = false otherwise.
+template <class T, bool LOWER, int JB>
+int launch_solve_block(rmat_ctx c, const LUPerm* pm, const cplx<T>* A, int ld, int k0, int nb,
+                       cplx<T>* B, int ldb, int ncols, float* Y) {
+  static bool attr = false;
+  const size_t smem = solve_block_smem<T, JB>();
+  if (!attr) {
+    RMAT_CU(cudaFuncSetAttribute(solve_block_kernel<T, LOWER, JB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  solve_block_kernel<T, LOWER, JB><<<ceil_div(ncols, 32), 256, smem, c->stream>>>(
+      A, ld, k0, B, ldb, ncols, nb, pm ? pm->rows : nullptr, pm ? pm->idx : nullptr,
+      pm ? pm->cnt : nullptr, Y, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+template <class T, bool LOWER>
+int solve_block(rmat_ctx c, const LUPerm* pm, const cplx<T>* A, int ld, int k0, int nb, int jb,
+                cplx<T>* B, int ldb, int ncols, float* Y, bool* done) {
+  *done = true;
+  if (jb == 32) return launch_solve_block<T, LOWER, 32>(c, pm, A, ld, k0, nb, B, ldb, ncols, Y);
+  if (jb == 64) return launch_solve_block<T, LOWER, 64>(c, pm, A, ld, k0, nb, B, ldb, ncols, Y);
+  if constexpr (sizeof(T) == 4)
+    if (jb == 128) return launch_solve_block<T, LOWER, 128>(c, pm, A, ld, k0, nb, B, ldb, ncols, Y);
+  *done = false;
+  return RMAT_OK;
+}
+
 template <class T>
 int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool tensor,
                   const LUPerm& pm) {
@@ -614,10 +770,15 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
     // G3: interchanges on the trailing columns, then U12 = L11^-1 A12
     perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt, c->dstat);
     c->launches++;
-    RMAT_CHECK(apply_perm<T>(c, pm, A + k0 + jb, ld, rest, k0, nb, jb));
-    trsm_block_rhs_kernel<T, true><<<ceil_div(rest, 32), 256, trsm_smem<T>(jb), c->stream>>>(
-        A, ld, k0, jb, A + k0 + jb, ld, rest);
-    c->launches++;
+    bool fused = false;
+    RMAT_CHECK(solve_block<T, true>(c, &pm, A, ld, k0, nb, jb, A + k0 + jb, ld, rest, nullptr,
+                                    &fused));
+    if (!fused) {
+      RMAT_CHECK(apply_perm<T>(c, pm, A + k0 + jb, ld, rest, k0, nb, jb));
+      trsm_block_rhs_kernel<T, true><<<ceil_div(rest, 32), 256, trsm_smem<T>(jb), c->stream>>>(
+          A, ld, k0, jb, A + k0 + jb, ld, rest);
+      c->launches++;
+    }
     RMAT_CU(cudaGetLastError());
     if (tensor && sizeof(T) == 4) {
       const size_t fplane = (size_t)n * ld, bplane = (size_t)n * RMAT_MAX_NB;
@@ -676,13 +837,19 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
   // forward: replay each panel's interchanges, then L11 solve and update below
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int jb = std::min(nb, n - k0);
-    RMAT_CHECK(apply_perm<T>(c, pm, B, ldb, nrhs, k0, nb, jb));
-    trsm_block_rhs_kernel<T, true><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B, ldb,
-                                                                            nrhs);
-    c->launches++;
-    RMAT_CU(cudaGetLastError());
-    if (tc && n - k0 - jb > 0) {
-      RMAT_CHECK(split_y(k0, jb));
+    const bool need_y = tc && n - k0 - jb > 0;
+    bool fused = false;
+    RMAT_CHECK(solve_block<T, true>(c, &pm, A, ld, k0, nb, jb, B, ldb, nrhs,
+                                    need_y ? c->Ypl : nullptr, &fused));
+    if (!fused) {
+      RMAT_CHECK(apply_perm<T>(c, pm, B, ldb, nrhs, k0, nb, jb));
+      trsm_block_rhs_kernel<T, true><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B,
+                                                                              ldb, nrhs);
+      c->launches++;
+      RMAT_CU(cudaGetLastError());
+      if (need_y) RMAT_CHECK(split_y(k0, jb));
+    }
+    if (need_y) {
       RMAT_CHECK(launch_solve_tc(c, k0 + jb, n - k0 - jb, nrhs, k0, jb, k0 + jb, n));
     } else {
       RMAT_CHECK(gemm_sub<T>(c, n - k0 - jb, nrhs, jb, A + (size_t)(k0 + jb) * ld + k0, ld,
@@ -693,12 +860,18 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
   const int last = ((n - 1) / nb) * nb;
   for (int k0 = last; k0 >= 0; k0 -= nb) {
     const int jb = std::min(nb, n - k0);
-    trsm_block_rhs_kernel<T, false><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B,
-                                                                             ldb, nrhs);
-    c->launches++;
-    RMAT_CU(cudaGetLastError());
-    if (tc && k0 > 0) {
-      RMAT_CHECK(split_y(k0, jb));
+    const bool need_y = tc && k0 > 0;
+    bool fused = false;
+    RMAT_CHECK(solve_block<T, false>(c, nullptr, A, ld, k0, nb, jb, B, ldb, nrhs,
+                                     need_y ? c->Ypl : nullptr, &fused));
+    if (!fused) {
+      trsm_block_rhs_kernel<T, false><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B,
+                                                                               ldb, nrhs);
+      c->launches++;
+      RMAT_CU(cudaGetLastError());
+      if (need_y) RMAT_CHECK(split_y(k0, jb));
+    }
+    if (need_y) {
       RMAT_CHECK(launch_solve_tc(c, 0, k0, nrhs, k0, jb, 0, n));
     } else {
       RMAT_CHECK(gemm_sub<T>(c, k0, nrhs, jb, A + k0, ld, B + (size_t)k0 * ldb, ldb, B, ldb));

@@ -154,9 +154,9 @@ void rmat_kinetic_table(int nlag, double hm, double s1, const double* T0, const 
     if (e__ != cudaSuccess) return RMAT_ECUDA;      \
   } while (0)
 
-#define RMAT_CHECK(x)                               \
+#define RMAT_CHECK(...)                             \
   do {                                              \
-    int s__ = (x);                                  \
+    int s__ = (__VA_ARGS__);                        \
     if (s__ != RMAT_OK) return s__;                 \
   } while (0)
 
