@@ -222,7 +222,7 @@ int rmat_destroy(rmat_ctx c) {
   void* bufs[] = {c->C,    c->A64,  c->B64, c->ipiv, c->Kmat, c->T0,  c->rmesh,
                   c->fa,   c->l_d,  c->th_d, c->Wpt, c->X,    c->Rres, c->Bw,
                   c->Fpl,  c->Bpl, c->Ypl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
-                  c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows};
+                  c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows, c->Dinv};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->hstat) cudaFreeHost(c->hstat);

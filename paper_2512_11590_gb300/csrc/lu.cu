@@ -428,8 +428,12 @@ __global__ void __launch_bounds__(256)
 solve_block_kernel(const cplx<T>* __restrict__ A, int ld, int k0, cplx<T>* __restrict__ B,
                    int ldb, int ncols, int nbp, const int* __restrict__ prow,
                    const int* __restrict__ pidx, const int* __restrict__ pcnt,
-                   float* __restrict__ Y, size_t yplane) {
+                   float* __restrict__ Y, size_t yplane, size_t bstride) {
   using C2 = cplx<T>;
+  if (bstride) {  // batched over diagonal blocks (inversion): block blockIdx.y, B rows 0..JB-1
+    k0 = blockIdx.y * nbp;
+    B += (size_t)blockIdx.y * bstride - (size_t)k0 * ldb;
+  }
   constexpr int RPW = JB / 8;
   constexpr int LDS = JB + 1;
   extern __shared__ unsigned char smem_raw[];
@@ -530,6 +534,108 @@ solve_block_kernel(const cplx<T>* __restrict__ A, int ld, int k0, cplx<T>* __res
       }
     }
   }
+}
+
+template <class T>
+__global__ void identity_blocks_kernel(cplx<T>* __restrict__ D, int JB, size_t total) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)((e / JB) % JB), j = (int)(e % JB);
+    D[e] = mkc<T>(i == j ? (T)1 : (T)0, (T)0);
+  }
+}
+
+// Solve-path block application with an inverted diagonal block:
+//   Y = Dinv * B_k   (B_k = rows k0..k0+JB-1 of B, after the block's interchanges
+//                     when a permutation list is given),
+// Y written back over B_k and, when Y planes are requested, as TF32 split planes
+// transposed (B operand of the tensor-core block update).  One CTA owns 16
+// right-hand-side columns and all JB rows, so no CTA reads what another writes.
+template <class T, int JB>
+__global__ void __launch_bounds__(256)
+apply_inv_kernel(const cplx<T>* __restrict__ Dinv, int k0, int nbp, cplx<T>* __restrict__ B,
+                 int ldb, int ncols, const int* __restrict__ prow, const int* __restrict__ pidx,
+                 const int* __restrict__ pcnt, float* __restrict__ Yp, size_t yplane) {
+  using C2 = cplx<T>;
+  constexpr int CW = 16;                     // columns per CTA
+  constexpr int RPT = JB / 16;               // output rows per thread
+  extern __shared__ unsigned char smem_raw[];
+  C2* vals = reinterpret_cast<C2*>(smem_raw);  // [2*JB][CW] gathered rows; [JB][CW+1] Y after
+  int* rows = reinterpret_cast<int*>(vals + 2 * JB * (CW + 1));  // [2*JB]
+  int* idx = rows + 2 * JB;                                      // [JB]
+  const int tid = threadIdx.x;
+  const int cl = tid & (CW - 1), rg = tid >> 4;  // column lane, row group 0..15
+  const int col = blockIdx.x * CW + cl;
+  const bool act = col < ncols;
+  int cnt = JB;
+  const int blk = k0 / nbp;
+  if (prow) {
+    cnt = pcnt[blk];
+    for (int q = tid; q < cnt; q += 256) rows[q] = prow[(size_t)blk * 2 * nbp + q];
+    for (int q = tid; q < JB; q += 256) idx[q] = pidx[(size_t)blk * nbp + q];
+  } else {
+    for (int q = tid; q < JB; q += 256) rows[q] = k0 + q;
+  }
+  __syncthreads();
+  for (int q = rg; q < cnt; q += 16)
+    vals[q * CW + cl] = act ? B[(size_t)rows[q] * ldb + col] : mkc<T>(0, 0);
+  __syncthreads();
+  if (prow) {
+    if (tid < CW) {
+      for (int t = 0; t < JB; ++t) {
+        const int sl = idx[t];
+        if (sl != t) {
+          const C2 u = vals[t * CW + tid];
+          vals[t * CW + tid] = vals[sl * CW + tid];
+          vals[sl * CW + tid] = u;
+        }
+      }
+    }
+    __syncthreads();
+    for (int q = JB + rg; q < cnt; q += 16)
+      if (act) B[(size_t)rows[q] * ldb + col] = vals[q * CW + cl];
+  }
+  // Y rows rg, rg+16, ... for column cl
+  const C2* D = Dinv + (size_t)blk * JB * JB;
+  C2 acc[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) acc[r] = mkc<T>(0, 0);
+  for (int t = 0; t < JB; ++t) {
+    const C2 bv = vals[t * CW + cl];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) cadd_mul<T>(acc[r], __ldg(D + (size_t)(rg + 16 * r) * JB + t), bv);
+  }
+  __syncthreads();
+  C2* ys = vals;  // [JB][CW+1]
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int i = rg + 16 * r;
+    ys[i * (CW + 1) + cl] = acc[r];
+    if (act) B[(size_t)(k0 + i) * ldb + col] = acc[r];
+  }
+  if (Yp) {
+    __syncthreads();
+    // transposed planes: plane row = column, K index = i (coalesced over i)
+    for (int cc = tid >> 5; cc < CW; cc += 8) {
+      const int gc = blockIdx.x * CW + cc;
+      if (gc >= ncols) continue;
+      for (int i = tid & 31; i < JB; i += 32) {
+        const C2 z = ys[i * (CW + 1) + cc];
+        const float re = (float)z.x, im = (float)z.y;
+        const float rh = tf32_round(re), ih = tf32_round(im);
+        const size_t o = (size_t)gc * RMAT_MAX_NB + i;
+        Yp[o] = rh;
+        Yp[yplane + o] = re - rh;
+        Yp[2 * yplane + o] = ih;
+        Yp[3 * yplane + o] = im - ih;
+      }
+    }
+  }
+}
+
+template <class T, int JB>
+size_t apply_inv_smem() {
+  return (size_t)2 * JB * 17 * sizeof(cplx<T>) + (size_t)3 * JB * sizeof(int);
 }
 
 template <class T, int JB>
@@ -731,7 +837,7 @@ int launch_solve_block(rmat_ctx c, const LUPerm* pm, const cplx<T>* A, int ld, i
   }
   solve_block_kernel<T, LOWER, JB><<<ceil_div(ncols, 32), 256, smem, c->stream>>>(
       A, ld, k0, B, ldb, ncols, nb, pm ? pm->rows : nullptr, pm ? pm->idx : nullptr,
-      pm ? pm->cnt : nullptr, Y, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB);
+      pm ? pm->cnt : nullptr, Y, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB, (size_t)0);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;
@@ -746,6 +852,61 @@ int solve_block(rmat_ctx c, const LUPerm* pm, const cplx<T>* A, int ld, int k0, 
   if constexpr (sizeof(T) == 4)
     if (jb == 128) return launch_solve_block<T, LOWER, 128>(c, pm, A, ld, k0, nb, B, ldb, ncols, Y);
   *done = false;
+  return RMAT_OK;
+}
+
+// Inverses of all full-width diagonal blocks (L11^-1 unit lower, U11^-1 upper) of a
+// complex64 factor, for the solve path: identity, then the batched block solve.
+template <int JB>
+int invert_diag_blocks(rmat_ctx c, const float2* A, int ld, int n, int nb) {
+  const int nfull = n / nb;
+  c->inv_blocks = 0;
+  if (nfull == 0) return RMAT_OK;
+  const size_t per = (size_t)JB * JB, total = per * nfull;
+  RMAT_CHECK(rmat_grow(c, &c->Dinv, &c->Dinv_cap, 2 * total * sizeof(float2)));
+  float2* Linv = reinterpret_cast<float2*>(c->Dinv);
+  float2* Uinv = Linv + total;
+  identity_blocks_kernel<float><<<std::min(c->sm_count * 4, ceil_div((long long)2 * total, 256)), 256,
+                                  0, c->stream>>>(Linv, JB, 2 * total);
+  c->launches++;
+  static bool attr[2] = {false, false};
+  const size_t smem = solve_block_smem<float, JB>();
+  if (!attr[JB == 128]) {
+    RMAT_CU(cudaFuncSetAttribute(solve_block_kernel<float, true, JB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RMAT_CU(cudaFuncSetAttribute(solve_block_kernel<float, false, JB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr[JB == 128] = true;
+  }
+  const dim3 grid(JB / 32, nfull);
+  solve_block_kernel<float, true, JB><<<grid, 256, smem, c->stream>>>(
+      A, ld, 0, Linv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per);
+  solve_block_kernel<float, false, JB><<<grid, 256, smem, c->stream>>>(
+      A, ld, 0, Uinv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per);
+  c->launches += 2;
+  RMAT_CU(cudaGetLastError());
+  c->inv_blocks = nfull;
+  c->inv_nb = nb;
+  return RMAT_OK;
+}
+
+template <int JB>
+int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb, int ncols,
+                     const LUPerm* pm, float* Yp) {
+  static bool attr = false;
+  const size_t smem = apply_inv_smem<float, JB>();
+  if (!attr) {
+    RMAT_CU(cudaFuncSetAttribute(apply_inv_kernel<float, JB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const size_t total = (size_t)JB * JB * c->inv_blocks;
+  const float2* D = reinterpret_cast<const float2*>(c->Dinv) + (upper ? total : 0);
+  apply_inv_kernel<float, JB><<<ceil_div(ncols, 16), 256, smem, c->stream>>>(
+      D, k0, nb, B, ldb, ncols, pm ? pm->rows : nullptr, pm ? pm->idx : nullptr,
+      pm ? pm->cnt : nullptr, Yp, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
   return RMAT_OK;
 }
 
@@ -810,6 +971,12 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
       c->tu_flops += 8.0 * rest * (double)rest * jb;
     }
   }
+  c->inv_blocks = 0;
+  if (tensor && sizeof(T) == 4) {
+    const float2* Af = reinterpret_cast<const float2*>(A);
+    if (nb == 128) RMAT_CHECK(invert_diag_blocks<128>(c, Af, ld, n, nb));
+    if (nb == 64) RMAT_CHECK(invert_diag_blocks<64>(c, Af, ld, n, nb));
+  }
   return RMAT_OK;
 }
 
@@ -839,8 +1006,16 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     const int jb = std::min(nb, n - k0);
     const bool need_y = tc && n - k0 - jb > 0;
     bool fused = false;
-    RMAT_CHECK(solve_block<T, true>(c, &pm, A, ld, k0, nb, jb, B, ldb, nrhs,
-                                    need_y ? c->Ypl : nullptr, &fused));
+    if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
+      float2* Bf = reinterpret_cast<float2*>(B);
+      float* Yp = need_y ? c->Ypl : nullptr;
+      if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, false, k0, nb, Bf, ldb, nrhs, &pm, Yp));
+      else RMAT_CHECK(launch_apply_inv<64>(c, false, k0, nb, Bf, ldb, nrhs, &pm, Yp));
+      fused = true;
+    } else {
+      RMAT_CHECK(solve_block<T, true>(c, &pm, A, ld, k0, nb, jb, B, ldb, nrhs,
+                                      need_y ? c->Ypl : nullptr, &fused));
+    }
     if (!fused) {
       RMAT_CHECK(apply_perm<T>(c, pm, B, ldb, nrhs, k0, nb, jb));
       trsm_block_rhs_kernel<T, true><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B,
@@ -862,8 +1037,16 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     const int jb = std::min(nb, n - k0);
     const bool need_y = tc && k0 > 0;
     bool fused = false;
-    RMAT_CHECK(solve_block<T, false>(c, nullptr, A, ld, k0, nb, jb, B, ldb, nrhs,
-                                     need_y ? c->Ypl : nullptr, &fused));
+    if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
+      float2* Bf = reinterpret_cast<float2*>(B);
+      float* Yp = need_y ? c->Ypl : nullptr;
+      if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, true, k0, nb, Bf, ldb, nrhs, nullptr, Yp));
+      else RMAT_CHECK(launch_apply_inv<64>(c, true, k0, nb, Bf, ldb, nrhs, nullptr, Yp));
+      fused = true;
+    } else {
+      RMAT_CHECK(solve_block<T, false>(c, nullptr, A, ld, k0, nb, jb, B, ldb, nrhs,
+                                       need_y ? c->Ypl : nullptr, &fused));
+    }
     if (!fused) {
       trsm_block_rhs_kernel<T, false><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B,
                                                                                ldb, nrhs);

@@ -79,7 +79,9 @@ struct rmat_ctx_s {
   double2* Rres = nullptr; size_t Rres_cap = 0;     // FP64 residual, row-major N x nrhs
   void* Bw = nullptr;      size_t Bw_cap = 0;       // solve work in the factor precision
   float* Fpl = nullptr;    size_t Fpl_cap = 0;      // full-size split factor planes [4][N][ld] (A operand)
-  float* Ypl = nullptr;    size_t Ypl_cap = 0;      // right-hand-side block planes [4][RMAT_YPL_ROWS][256]
+  float* Ypl = nullptr;    size_t Ypl_cap = 0;
+  void* Dinv = nullptr;    size_t Dinv_cap = 0;     // inverted diagonal blocks (tensor solve path)
+  int inv_blocks = 0, inv_nb = 0;      // right-hand-side block planes [4][RMAT_YPL_ROWS][256]
   float* Bpl = nullptr;    size_t Bpl_cap = 0;      // tensor B operand planes (U12^T split)
   double* Dsc = nullptr;   size_t Dsc_cap = 0;      // equilibration scale per row
   std::vector<double> ir_hist;                      // refinement history of the last solve
