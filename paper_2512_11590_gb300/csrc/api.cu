@@ -109,7 +109,7 @@ double elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 int perm_reserve(rmat_ctx c, LUPerm& pm, int n, int nb) {
   const size_t nblk = (size_t)(n + nb - 1) / nb;
-  const size_t bytes = nblk * (3 * (size_t)nb + 1) * sizeof(int);
+  const size_t bytes = nblk * (5 * (size_t)nb + 1) * sizeof(int);
   if (bytes > pm.cap || !pm.rows) {
     void* p = pm.rows;
     size_t cap = pm.cap;
@@ -118,7 +118,8 @@ int perm_reserve(rmat_ctx c, LUPerm& pm, int n, int nb) {
     pm.cap = cap;
   }
   pm.idx = pm.rows + nblk * 2 * nb;
-  pm.cnt = pm.idx + nblk * nb;
+  pm.src = pm.idx + nblk * nb;
+  pm.cnt = pm.src + nblk * 2 * nb;
   return RMAT_OK;
 }
 

@@ -416,8 +416,8 @@ trsm_block_rhs_kernel(const cplx<T>* __restrict__ A, int ld, int k0, int jb,
 // Fused block solve for a block of exactly JB rows (JB in {32, 64, 128}),
 // 32 right-hand-side columns per CTA (lane = column), 8 warps:
 //   1. stage the diagonal block (L11 unit lower, or U11) in shared memory;
-//   2. LOWER with a permutation list: gather the involved rows, replay the
-//      block's interchanges in shared memory, write the rows below the block back;
+//   2. with a permutation list: gather the involved rows through the block's net
+//      source map (the interchanges applied), write the rows below the block back;
 //   3. right-looking substitution with the block's rows in registers (warp w
 //      owns solve positions w, w+8, ...): per step the owner publishes x_s,
 //      then every warp subtracts L[i][s] x_s from its remaining rows;
@@ -427,7 +427,7 @@ template <class T, bool LOWER, int JB>
 __global__ void __launch_bounds__(256)
 solve_block_kernel(const cplx<T>* __restrict__ A, int ld, int k0, cplx<T>* __restrict__ B,
                    int ldb, int ncols, int nbp, const int* __restrict__ prow,
-                   const int* __restrict__ pidx, const int* __restrict__ pcnt,
+                   const int* __restrict__ psrc, const int* __restrict__ pcnt,
                    float* __restrict__ Y, size_t yplane, size_t bstride) {
   using C2 = cplx<T>;
   if (bstride) {  // batched over diagonal blocks (inversion): block blockIdx.y, B rows 0..JB-1
@@ -442,7 +442,7 @@ solve_block_kernel(const cplx<T>* __restrict__ A, int ld, int k0, cplx<T>* __res
   C2* xs = vals;
   C2* dinv = vals + 2 * JB * 32;             // [JB]
   int* rows = reinterpret_cast<int*>(dinv + JB);  // [2*JB]
-  int* idx = rows + 2 * JB;                  // [JB]
+  int* idx = rows + 2 * JB;                  // [2*JB] net source slots
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.x * 32 + lane;
   const bool act = col < ncols;
@@ -464,27 +464,22 @@ solve_block_kernel(const cplx<T>* __restrict__ A, int ld, int k0, cplx<T>* __res
   if (prow) {
     const int blk = k0 / nbp;
     cnt = pcnt[blk];
-    for (int q = threadIdx.x; q < cnt; q += 256) rows[q] = prow[(size_t)blk * 2 * nbp + q];
-    for (int q = threadIdx.x; q < JB; q += 256) idx[q] = pidx[(size_t)blk * nbp + q];
+    for (int q = threadIdx.x; q < cnt; q += 256) {
+      rows[q] = prow[(size_t)blk * 2 * nbp + q];
+      idx[q] = psrc[(size_t)blk * 2 * nbp + q];  // net source slot of slot q
+    }
   } else {
-    for (int q = threadIdx.x; q < JB; q += 256) rows[q] = k0 + q;
+    for (int q = threadIdx.x; q < JB; q += 256) {
+      rows[q] = k0 + q;
+      idx[q] = q;
+    }
   }
   __syncthreads();
   if (!LOWER)
     for (int q = threadIdx.x; q < JB; q += 256) dinv[q] = cdiv<T>(mkc<T>(1, 0), Ls[q * LDS + q]);
+  // permuted gather: slot q receives the original content of slot idx[q]
   for (int q = warp; q < cnt; q += 8)
-    vals[q * 32 + lane] = act ? B[(size_t)rows[q] * ldb + col] : mkc<T>(0, 0);
-  __syncthreads();
-  if (prow && warp == 0) {
-    for (int t = 0; t < JB; ++t) {
-      const int sl = idx[t];
-      if (sl != t) {
-        const C2 u = vals[t * 32 + lane];
-        vals[t * 32 + lane] = vals[sl * 32 + lane];
-        vals[sl * 32 + lane] = u;
-      }
-    }
-  }
+    vals[q * 32 + lane] = act ? B[(size_t)rows[idx[q]] * ldb + col] : mkc<T>(0, 0);
   __syncthreads();
   if (prow)
     for (int q = JB + warp; q < cnt; q += 8)
@@ -546,64 +541,72 @@ __global__ void identity_blocks_kernel(cplx<T>* __restrict__ D, int JB, size_t t
 }
 
 // Solve-path block application with an inverted diagonal block:
-//   Y = Dinv * B_k   (B_k = rows k0..k0+JB-1 of B, after the block's interchanges
-//                     when a permutation list is given),
+//   Y = Dinv * B_k   (B_k = rows k0..k0+JB-1 of B after the block's interchanges,
+//                     gathered through the net source map when one is given),
 // Y written back over B_k and, when Y planes are requested, as TF32 split planes
-// transposed (B operand of the tensor-core block update).  One CTA owns 16
-// right-hand-side columns and all JB rows, so no CTA reads what another writes.
+// transposed (B operand of the tensor-core block update).  The inverse block is
+// staged in shared memory; one CTA owns 16 right-hand-side columns and all JB
+// rows, so no CTA reads what another writes.
 template <class T, int JB>
 __global__ void __launch_bounds__(256)
 apply_inv_kernel(const cplx<T>* __restrict__ Dinv, int k0, int nbp, cplx<T>* __restrict__ B,
-                 int ldb, int ncols, const int* __restrict__ prow, const int* __restrict__ pidx,
+                 int ldb, int ncols, const int* __restrict__ prow, const int* __restrict__ psrc,
                  const int* __restrict__ pcnt, float* __restrict__ Yp, size_t yplane) {
   using C2 = cplx<T>;
   constexpr int CW = 16;                     // columns per CTA
   constexpr int RPT = JB / 16;               // output rows per thread
+  constexpr int LDD = JB + 1;
   extern __shared__ unsigned char smem_raw[];
-  C2* vals = reinterpret_cast<C2*>(smem_raw);  // [2*JB][CW] gathered rows; [JB][CW+1] Y after
+  C2* Ds = reinterpret_cast<C2*>(smem_raw);        // [JB][LDD] inverse block
+  C2* vals = Ds + JB * LDD;                        // [2*JB][CW] gathered rows; [JB][CW+1] Y after
   int* rows = reinterpret_cast<int*>(vals + 2 * JB * (CW + 1));  // [2*JB]
-  int* idx = rows + 2 * JB;                                      // [JB]
+  int* src = rows + 2 * JB;                                      // [2*JB]
   const int tid = threadIdx.x;
   const int cl = tid & (CW - 1), rg = tid >> 4;  // column lane, row group 0..15
   const int col = blockIdx.x * CW + cl;
   const bool act = col < ncols;
-  int cnt = JB;
   const int blk = k0 / nbp;
+  const C2* D = Dinv + (size_t)blk * JB * JB;
+  for (int e0 = tid; e0 < JB * JB; e0 += 256 * 8) {
+    C2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (e0 + u * 256 < JB * JB) v[u] = D[e0 + u * 256];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 256;
+      if (e < JB * JB) Ds[(e / JB) * LDD + e % JB] = v[u];
+    }
+  }
+  int cnt = JB;
   if (prow) {
     cnt = pcnt[blk];
-    for (int q = tid; q < cnt; q += 256) rows[q] = prow[(size_t)blk * 2 * nbp + q];
-    for (int q = tid; q < JB; q += 256) idx[q] = pidx[(size_t)blk * nbp + q];
+    for (int q = tid; q < cnt; q += 256) {
+      rows[q] = prow[(size_t)blk * 2 * nbp + q];
+      src[q] = psrc[(size_t)blk * 2 * nbp + q];
+    }
   } else {
-    for (int q = tid; q < JB; q += 256) rows[q] = k0 + q;
+    for (int q = tid; q < JB; q += 256) {
+      rows[q] = k0 + q;
+      src[q] = q;
+    }
   }
   __syncthreads();
+  // permuted gather: slot q receives the original content of slot src[q]
   for (int q = rg; q < cnt; q += 16)
-    vals[q * CW + cl] = act ? B[(size_t)rows[q] * ldb + col] : mkc<T>(0, 0);
+    vals[q * CW + cl] = act ? B[(size_t)rows[src[q]] * ldb + col] : mkc<T>(0, 0);
   __syncthreads();
-  if (prow) {
-    if (tid < CW) {
-      for (int t = 0; t < JB; ++t) {
-        const int sl = idx[t];
-        if (sl != t) {
-          const C2 u = vals[t * CW + tid];
-          vals[t * CW + tid] = vals[sl * CW + tid];
-          vals[sl * CW + tid] = u;
-        }
-      }
-    }
-    __syncthreads();
+  if (prow)
     for (int q = JB + rg; q < cnt; q += 16)
       if (act) B[(size_t)rows[q] * ldb + col] = vals[q * CW + cl];
-  }
-  // Y rows rg, rg+16, ... for column cl
-  const C2* D = Dinv + (size_t)blk * JB * JB;
   C2 acc[RPT];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) acc[r] = mkc<T>(0, 0);
+#pragma unroll 4
   for (int t = 0; t < JB; ++t) {
     const C2 bv = vals[t * CW + cl];
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) cadd_mul<T>(acc[r], __ldg(D + (size_t)(rg + 16 * r) * JB + t), bv);
+    for (int r = 0; r < RPT; ++r) cadd_mul<T>(acc[r], Ds[(rg + 16 * r) * LDD + t], bv);
   }
   __syncthreads();
   C2* ys = vals;  // [JB][CW+1]
@@ -635,13 +638,14 @@ apply_inv_kernel(const cplx<T>* __restrict__ Dinv, int k0, int nbp, cplx<T>* __r
 
 template <class T, int JB>
 size_t apply_inv_smem() {
-  return (size_t)2 * JB * 17 * sizeof(cplx<T>) + (size_t)3 * JB * sizeof(int);
+  return (size_t)JB * (JB + 1) * sizeof(cplx<T>) + (size_t)2 * JB * 17 * sizeof(cplx<T>) +
+         (size_t)4 * JB * sizeof(int);
 }
 
 template <class T, int JB>
 size_t solve_block_smem() {
   return (size_t)JB * (JB + 1) * sizeof(cplx<T>) + (size_t)2 * JB * 32 * sizeof(cplx<T>) +
-         (size_t)JB * sizeof(cplx<T>) + (size_t)3 * JB * sizeof(int);
+         (size_t)JB * sizeof(cplx<T>) + (size_t)4 * JB * sizeof(int);
 }
 
 template <class T>
@@ -659,7 +663,8 @@ size_t trsm_smem(int jb) {
 // up on a bounded wait) become no-ops and raise the status word.
 __global__ void perm_prep_kernel(const int* __restrict__ ipiv, int n, int nb, int k0_first,
                                  int* __restrict__ prow, int* __restrict__ pidx,
-                                 int* __restrict__ pcnt, int* __restrict__ stat) {
+                                 int* __restrict__ pcnt, int* __restrict__ psrc,
+                                 int* __restrict__ stat) {
   const int blk = blockIdx.x;
   const int k0 = k0_first + blk * nb;
   if (k0 >= n) return;
@@ -695,6 +700,24 @@ __global__ void perm_prep_kernel(const int* __restrict__ ipiv, int n, int nb, in
     if (lane == 0) idx[t] = slot;
   }
   if (lane == 0) pcnt[k0 / nb] = jb + nout;
+  // net effect of the sequential swaps: slot q ends up holding the original
+  // content of slot src[q] (simulated once here, so gathers need no replay)
+  __syncwarp();
+  int* src = psrc + (size_t)(k0 / nb) * 2 * nb;
+  const int cnt = jb + nout;
+  for (int q = lane; q < cnt; q += 32) src[q] = q;
+  __syncwarp();
+  if (lane == 0) {
+    for (int t = 0; t < jb; ++t) {
+      const int sl = idx[t];
+      if (sl != t) {
+        const int u = src[t];
+        src[t] = src[sl];
+        src[sl] = u;
+      }
+    }
+  }
+  __syncwarp();
 }
 
 // Apply block k0's permutation to ncols columns of B (rows of B are matrix rows):
@@ -836,7 +859,7 @@ int launch_solve_block(rmat_ctx c, const LUPerm* pm, const cplx<T>* A, int ld, i
     attr = true;
   }
   solve_block_kernel<T, LOWER, JB><<<ceil_div(ncols, 32), 256, smem, c->stream>>>(
-      A, ld, k0, B, ldb, ncols, nb, pm ? pm->rows : nullptr, pm ? pm->idx : nullptr,
+      A, ld, k0, B, ldb, ncols, nb, pm ? pm->rows : nullptr, pm ? pm->src : nullptr,
       pm ? pm->cnt : nullptr, Y, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB, (size_t)0);
   c->launches++;
   RMAT_CU(cudaGetLastError());
@@ -903,7 +926,7 @@ int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb,
   const size_t total = (size_t)JB * JB * c->inv_blocks;
   const float2* D = reinterpret_cast<const float2*>(c->Dinv) + (upper ? total : 0);
   apply_inv_kernel<float, JB><<<ceil_div(ncols, 16), 256, smem, c->stream>>>(
-      D, k0, nb, B, ldb, ncols, pm ? pm->rows : nullptr, pm ? pm->idx : nullptr,
+      D, k0, nb, B, ldb, ncols, pm ? pm->rows : nullptr, pm ? pm->src : nullptr,
       pm ? pm->cnt : nullptr, Yp, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB);
   c->launches++;
   RMAT_CU(cudaGetLastError());
@@ -923,13 +946,14 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
     RMAT_CHECK(launch_panel<T>(c, A, ld, k0, n, jb, ipiv));
     const int rest = n - k0 - jb;
     if (rest <= 0) {
-      perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt,
+      perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt, pm.src,
                                                 c->dstat);
       c->launches++;
       continue;
     }
     // G3: interchanges on the trailing columns, then U12 = L11^-1 A12
-    perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt, c->dstat);
+    perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt, pm.src,
+                                              c->dstat);
     c->launches++;
     bool fused = false;
     RMAT_CHECK(solve_block<T, true>(c, &pm, A, ld, k0, nb, jb, A + k0 + jb, ld, rest, nullptr,

@@ -27,11 +27,14 @@ struct PanelScratch {
 };
 
 // Net row permutation of each LU block (built once per factorisation, reused
-// by every solve): rows [nblocks][2*nb], idx [nblocks][nb], cnt [nblocks].
+// by every solve): rows [nblocks][2*nb] involved rows, idx [nblocks][nb] slot of
+// each step's pivot row, src [nblocks][2*nb] net source slot of every involved
+// slot, cnt [nblocks] involved-row count.
 struct LUPerm {
   int* rows = nullptr;
   int* idx = nullptr;
   int* cnt = nullptr;
+  int* src = nullptr;
   size_t cap = 0;  // bytes
 };
 
