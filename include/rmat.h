@@ -198,6 +198,40 @@ int rmat_reset_counters(rmat_ctx ctx);
  * Errors: -1 ctx, -2 hist NULL with n > 0. */
 int rmat_refine_history(rmat_ctx ctx, double* hist, int n);
 
+/* ---- allocation-free collision step ---------------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers that
+ * cannot allocate device memory at the point where they need U: code whose
+ * device memory is owned by a pool or caching allocator of another framework
+ * (a cudaMalloc there fails or fragments the pool), code that must not
+ * synchronise the device (cudaMalloc and cudaFree can), and loops with a fixed
+ * memory budget.
+ *
+ * Computes the same R and U as rmat_collision, from a solution X the caller
+ * already holds, in one kernel launch on `stream`, allocating nothing.  Its
+ * scratch (the nch x nch matching system, channel functions, a status word)
+ * is a fixed array in device memory, sized for nch <= RMAT_NOALLOC_MAX_NCH; every
+ * GPU that loads the library holds it (about 200 KB) until the process exits.
+ *   prob      problem description (nch 1..RMAT_NOALLOC_MAX_NCH; precision ignored)
+ *   E         energy (MeV)
+ *   f_a_dev   device double[nlag]: f_i(a), as returned by rmat_mesh
+ *   X_dev     device complex128 N x nch column-major solution (ld = ldx >= N)
+ *   R_dev     device complex128 nch x nch column-major output (may be NULL)
+ *   U_dev     device complex128 nopen x nopen column-major output
+ *   nopen     host int output (may be NULL)
+ * The first call on a device looks up the scratch array's device address; make
+ * that first call before any stream capture.  All calls share the one scratch
+ * array and it keeps the last call's contents (the kernel rewrites everything
+ * it reads, and clears its status word, on every call): calls that overlap on
+ * the GPU, from any stream or thread, race.  Synchronises `stream`.
+ * Errors: -1 prob invalid or nch > RMAT_NOALLOC_MAX_NCH, -2 E invalid or a channel
+ * exactly at threshold, -3 f_a_dev NULL, -4 X_dev NULL, -5 ldx < N, -7 U_dev NULL
+ * with open channels, RMAT_ESINGULAR for an exactly singular matching system,
+ * RMAT_ECUDA. */
+#define RMAT_NOALLOC_MAX_NCH 64
+int rmat_collision_noalloc(const rmat_problem* prob, double E, const void* f_a_dev,
+                           const void* X_dev, int ldx, void* R_dev, void* U_dev, int* nopen,
+                           void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* rmat_status_string(int status);
 

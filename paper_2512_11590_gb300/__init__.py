@@ -38,7 +38,8 @@ RMAT_PARAM_EQUILIBRATE = 5
 
 EXPORTED = ("rmat_create", "rmat_destroy", "rmat_set_param", "rmat_mesh", "rmat_assemble",
             "rmat_load_dense", "rmat_factor", "rmat_solve", "rmat_collision", "rmat_get_stats",
-            "rmat_reset_counters", "rmat_refine_history", "rmat_status_string")
+            "rmat_reset_counters", "rmat_refine_history", "rmat_collision_noalloc",
+            "rmat_status_string")
 
 
 class rmat_problem(ct.Structure):
@@ -79,6 +80,7 @@ def lib():
             "rmat_get_stats": (i, [vp, pd, i]),
             "rmat_reset_counters": (i, [vp]),
             "rmat_refine_history": (i, [vp, pd, i]),
+            "rmat_collision_noalloc": (i, [ct.POINTER(rmat_problem), d, vp, vp, i, vp, vp, pi, vp]),
             "rmat_status_string": (ct.c_char_p, [i]),
         }
         for name, (res, args) in sig.items():
@@ -195,3 +197,14 @@ def rmat_refine_history(ctx) -> list:
     buf = (ct.c_double * max(n, 1))()
     lib().rmat_refine_history(ct.c_void_p(ctx), buf, n)
     return [buf[k] for k in range(n)]
+
+
+def rmat_collision_noalloc(prob, E, f_a_dev, X_dev, ldx, R_dev, U_dev, stream=0) -> int:
+    """R and U from a solved X without allocating (see include/rmat.h). Returns nopen."""
+    nopen = ct.c_int(0)
+    _check("rmat_collision_noalloc",
+           lib().rmat_collision_noalloc(ct.byref(prob), float(E), ct.c_void_p(f_a_dev),
+                                        ct.c_void_p(X_dev), int(ldx), ct.c_void_p(R_dev or None),
+                                        ct.c_void_p(U_dev or None), ct.byref(nopen),
+                                        ct.c_void_p(stream or None)))
+    return nopen.value

@@ -1,0 +1,246 @@
+// rmat_collision_noalloc: the R-matrix and collision matrix of a solved system in
+// ONE kernel launch that allocates nothing.
+//
+// Some callers cannot allocate device memory when they need U: code running
+// under a memory pool or caching allocator that owns the whole device (so a
+// cudaMalloc would fail or fragment it), code that must not synchronise the
+// device (cudaMalloc/cudaFree can), and real-time loops with a fixed memory
+// budget.  This entry point takes the solution X and the boundary values f_i(a)
+// from the caller, writes R and U into caller buffers, and keeps its scratch
+// (the nch x nch matching system, channel functions, status word) in the
+// file-scope device array below, of fixed size for nch <= RMAT_NOALLOC_MAX_NCH.
+//
+// It computes the same quantities as rmat_collision (see include/rmat.h):
+//   R = (hm/a) Phi^T X;  R~ = a sqrt(k) R sqrt(k);
+//   U = (diag O - R~ diag O')^-1 (diag I - R~ diag I'), open x open block,
+// but in a single CTA: R contraction, channel functions, the matching system,
+// Gaussian elimination with partial pivoting (largest |Re|+|Im|, first row on
+// ties) carrying the right-hand sides, and back substitution.
+#include <cstring>
+
+#include "cplx.cuh"
+#include "rmat_internal.h"
+#include "special.cuh"
+
+namespace {
+
+constexpr int MAXC = RMAT_NOALLOC_MAX_NCH;
+constexpr int NA_THREADS = 256;
+
+struct NoallocScratch {
+  double2 R[MAXC * MAXC];   // R-matrix, row-major
+  double2 ZO[MAXC * MAXC];  // matching matrix diag O - R~ diag O'
+  double2 ZI[MAXC * MAXC];  // right-hand sides diag I - R~ diag I' (open columns)
+  double2 I[MAXC], O[MAXC], dI[MAXC], dO[MAXC];
+  double k[MAXC];
+  int status;               // 0 ok, 1 + column of an exactly zero pivot
+};
+
+// Scratch shared by every call on this device (contents persist between calls).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
+
+struct NoallocParams {
+  int nch, nlag, nopen, ldx;
+  double a, hm, B, E;
+  int l[MAXC];
+  double thresh[MAXC];
+  int open[MAXC];
+};
+
+__global__ void __launch_bounds__(NA_THREADS)
+collision_noalloc_kernel(const NoallocParams p, const double* __restrict__ fa,
+                         const double2* __restrict__ X, double2* __restrict__ Rout,
+                         double2* __restrict__ Uout, NoallocScratch* __restrict__ S) {
+  const int tid = threadIdx.x;
+  const int nch = p.nch, no = p.nopen;
+  __shared__ int s_piv;
+  if (tid == 0) S->status = 0;  // must start at zero on every call
+  // R[al][be] = (hm/a) sum_i f_i(a) X[(al,i), be]   (X column-major, ld = ldx)
+  for (int e = tid; e < nch * nch; e += NA_THREADS) {
+    const int al = e / nch, be = e % nch;
+    double sr = 0.0, si = 0.0;
+    for (int i = 0; i < p.nlag; ++i) {
+      const double2 x = X[(size_t)al * p.nlag + i + (size_t)p.ldx * be];
+      sr = fma(fa[i], x.x, sr);
+      si = fma(fa[i], x.y, si);
+    }
+    const double2 r = make_double2(p.hm / p.a * sr, p.hm / p.a * si);
+    S->R[e] = r;
+    if (Rout) Rout[al + (size_t)nch * be] = r;
+  }
+  // channel functions at rho = k a
+  for (int ch = tid; ch < nch; ch += NA_THREADS) {
+    const double ecm = p.E - p.thresh[ch];
+    const double k = sqrt(fabs(ecm) / p.hm), rho = k * p.a;
+    double2 I, O, dI, dO;
+    if (ecm > 0) {
+      double F, G, dF, dG;
+      riccati_fg(p.l[ch], rho, &F, &G, &dF, &dG);
+      I = make_double2(G, -F);
+      O = make_double2(G, F);
+      dI = make_double2(dG, -dF);
+      dO = make_double2(dG, dF);
+    } else {
+      double W, dW;
+      whittaker_w(p.l[ch], rho, &W, &dW);
+      I = dI = make_double2(0, 0);
+      O = make_double2(W, 0);
+      dO = make_double2(dW, 0);
+    }
+    dI.x -= p.B / rho * I.x;
+    dI.y -= p.B / rho * I.y;
+    dO.x -= p.B / rho * O.x;
+    dO.y -= p.B / rho * O.y;
+    S->I[ch] = I;
+    S->O[ch] = O;
+    S->dI[ch] = dI;
+    S->dO[ch] = dO;
+    S->k[ch] = k;
+  }
+  __syncthreads();
+  // matching system (every entry written, nothing relies on earlier contents)
+  for (int e = tid; e < nch * (nch + no); e += NA_THREADS) {
+    const int row = e / (nch + no), col = e % (nch + no);
+    const int cp = col < nch ? col : p.open[col - nch];
+    const double2 R = S->R[row * nch + cp];
+    const double s = p.a * sqrt(S->k[row]) * sqrt(S->k[cp]);
+    const double2 Rt = make_double2(s * R.x, s * R.y);
+    const double2 f = col < nch ? S->dO[cp] : S->dI[cp];
+    double2 z = cmul<double>(Rt, f);
+    z.x = -z.x;
+    z.y = -z.y;
+    if (row == cp) {
+      const double2 d = col < nch ? S->O[row] : S->I[row];
+      z.x += d.x;
+      z.y += d.y;
+    }
+    if (col < nch) S->ZO[row * nch + col] = z;
+    else S->ZI[row * no + (col - nch)] = z;
+  }
+  __syncthreads();
+  // Gaussian elimination with partial pivoting, right-hand sides carried along
+  for (int j = 0; j < nch; ++j) {
+    if (tid < 32) {
+      double best = -1.0;
+      int bi = nch;
+      for (int r = j + tid; r < nch; r += 32) {
+        const double m = cabs1<double>(S->ZO[r * nch + j]);
+        if (m > best) { best = m; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) {
+        s_piv = bi;
+        if (!(best > 0.0) && S->status == 0) S->status = j + 1;
+      }
+    }
+    __syncthreads();
+    const int pv = s_piv;
+    if (pv != j && pv < nch) {
+      for (int c = tid; c < nch + no; c += NA_THREADS) {
+        double2* a = c < nch ? &S->ZO[j * nch + c] : &S->ZI[j * no + (c - nch)];
+        double2* b = c < nch ? &S->ZO[pv * nch + c] : &S->ZI[pv * no + (c - nch)];
+        const double2 t = *a;
+        *a = *b;
+        *b = t;
+      }
+    }
+    __syncthreads();
+    const double2 piv = S->ZO[j * nch + j];
+    if (piv.x != 0.0 || piv.y != 0.0) {
+      const int rows = nch - j - 1, cols = nch - j - 1 + no;
+      for (int e = tid; e < rows * cols; e += NA_THREADS) {
+        const int r = j + 1 + e / cols, cc = e % cols;
+        const double2 lm = cdiv<double>(S->ZO[r * nch + j], piv);
+        if (cc < nch - j - 1) {
+          const int c = j + 1 + cc;
+          csub_mul<double>(S->ZO[r * nch + c], lm, S->ZO[j * nch + c]);
+        } else {
+          const int c = cc - (nch - j - 1);
+          csub_mul<double>(S->ZI[r * no + c], lm, S->ZI[j * no + c]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // back substitution on the open columns
+  for (int j = nch - 1; j >= 0; --j) {
+    const double2 d = S->ZO[j * nch + j];
+    for (int c = tid; c < no; c += NA_THREADS)
+      if (d.x != 0.0 || d.y != 0.0) S->ZI[j * no + c] = cdiv<double>(S->ZI[j * no + c], d);
+    __syncthreads();
+    for (int e = tid; e < j * no; e += NA_THREADS) {
+      const int r = e / no, c = e % no;
+      csub_mul<double>(S->ZI[r * no + c], S->ZO[r * nch + j], S->ZI[j * no + c]);
+    }
+    __syncthreads();
+  }
+  // U(q, q2) = Ufull[open[q]][q2], column-major nopen x nopen
+  for (int e = tid; e < no * no; e += NA_THREADS) {
+    const int q = e % no, q2 = e / no;
+    Uout[e] = S->ZI[p.open[q] * no + q2];
+  }
+}
+
+// Device address of the scratch array, looked up once per device.
+void* g_scratch_ptr[64] = {nullptr};
+
+}  // namespace
+
+extern "C" int rmat_collision_noalloc(const rmat_problem* prob, double E, const void* f_a_dev,
+                                      const void* X_dev, int ldx, void* R_dev, void* U_dev,
+                                      int* nopen, void* stream) {
+  if (!prob || prob->nch < 1 || prob->nch > RMAT_NOALLOC_MAX_NCH || prob->nlag < 1 ||
+      !(prob->a > 0) || !(prob->hm > 0) || !prob->l || !prob->thresh)
+    return -1;
+  if (!(E == E)) return -2;
+  if (!f_a_dev) return -3;
+  if (!X_dev) return -4;
+  if (ldx < prob->nch * prob->nlag) return -5;
+  NoallocParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.nch = prob->nch;
+  p.nlag = prob->nlag;
+  p.ldx = ldx;
+  p.a = prob->a;
+  p.hm = prob->hm;
+  p.B = prob->bloch_B;
+  p.E = E;
+  int no = 0;
+  for (int c = 0; c < prob->nch; ++c) {
+    if (prob->l[c] < 0 || prob->l[c] > 64) return -1;
+    p.l[c] = prob->l[c];
+    p.thresh[c] = prob->thresh[c];
+    if (E - prob->thresh[c] == 0.0) return -2;  // a channel exactly at threshold
+    if (E - prob->thresh[c] > 0) p.open[no++] = c;
+  }
+  p.nopen = no;
+  if (nopen) *nopen = no;
+  if (no > 0 && !U_dev) return -7;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RMAT_ECUDA;
+  if (!g_scratch_ptr[dev]) {
+    // first call on this device: resolve the scratch array's device address
+    // (the host-side symbol is only a stand-in and must not reach a kernel)
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return RMAT_ECUDA;
+    }
+    g_scratch_ptr[dev] = ptr;
+  }
+  NoallocScratch* S = reinterpret_cast<NoallocScratch*>(g_scratch_ptr[dev]);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  collision_noalloc_kernel<<<1, NA_THREADS, 0, st>>>(
+      p, reinterpret_cast<const double*>(f_a_dev), reinterpret_cast<const double2*>(X_dev),
+      reinterpret_cast<double2*>(R_dev), reinterpret_cast<double2*>(U_dev), S);
+  if (cudaGetLastError() != cudaSuccess) return RMAT_ECUDA;
+  int status = 0;
+  if (cudaMemcpyAsync(&status, &S->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return RMAT_ECUDA;
+  return status ? RMAT_ESINGULAR : RMAT_OK;
+}
