@@ -261,6 +261,90 @@ def profile_step(nch):
     return 0
 
 
+def batch_main(args):
+    """Config 4: 512 independent systems of uneven size (N = 80 .. 6400) through
+    the batch driver (tuned lanes + CUDA graph), against a loop of single-system
+    calls on the same inputs.  Prints one JSON line (systems/s)."""
+    import torch
+
+    import cc_problems as cp
+    import paper_2512_11590_gb300 as g
+    torch.cuda.set_device(0)
+    probs = cp.batch_problems(args.batch)
+    prec = g.RMAT_C64_3XTF32_IR if args.precision == "tf32" else g.RMAT_C64_SIMT_IR
+    stream = torch.cuda.current_stream()
+    ctx = g.rmat_create(0, stream.cuda_stream)
+    Vs, structs, keep = [], [], []
+    for p in probs:
+        m = g.rmat_mesh(p.nlag, p.a)
+        Vs.append(torch.from_numpy(cp.potential_at(p, m["r"]).ravel()).cuda())
+        s, k = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh, prec)
+        structs.append(s)
+        keep.append(k)
+    b = g.rmat_batch_create(ctx, structs, [p.E for p in probs], [v.data_ptr() for v in Vs],
+                            max_refine=args.batch_refine, tol=1e-13)
+    nopen = g.rmat_batch_nopen(b, len(probs))
+    Us = [torch.zeros(max(1, n) ** 2, dtype=torch.complex128, device="cuda") for n in nopen]
+    Uptr = [u.data_ptr() for u in Us]
+    t0 = time.perf_counter()
+    lanes, split = g.rmat_batch_tune(b, Uptr)
+    tune_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        g.rmat_batch_run(b, Uptr)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            st, it = g.rmat_batch_run(b, Uptr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    info = g.rmat_batch_info(b)
+    Ub = [u.cpu().numpy() for u in Us]
+    g.rmat_batch_destroy(b)
+    # the same systems one at a time through the single-system calls
+    Xs = [torch.zeros((p.nch, p.N), dtype=torch.complex128, device="cuda") for p in probs]
+    Ul = [torch.zeros_like(u) for u in Us]
+
+    def loop():
+        for p, s, v, X, U in zip(probs, structs, Vs, Xs, Ul):
+            g.rmat_assemble(ctx, s, p.E, v.data_ptr())
+            g.rmat_factor(ctx, want_info=False)
+            g.rmat_solve(ctx, X.data_ptr(), p.N, max_refine=30, tol=1e-13)
+            g.rmat_collision(ctx, 0, U.data_ptr())
+    loop()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    loop()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_loop = e0.elapsed_time(e1)
+    diff = max(float(np.max(np.abs(u - w.cpu().numpy())) / max(1e-300, np.max(np.abs(w.cpu().numpy()))))
+               for u, w, n in zip(Ub, Ul, nopen) if n > 0)
+    g.rmat_destroy(ctx)
+    Ns = np.array([p.N for p in probs])
+    flops = float(sum(lu_flops(p.N, p.nch) for p in probs))
+    line = {"metric": "batched systems/s (config 4: %d uneven systems)" % len(probs),
+            "value": len(probs) / (ms * 1e-3), "unit": "systems/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64+3xtf32 factor / f64 refinement" if prec == 1 else "c64 simt / f64",
+            "data": "synthetic",
+            "config": {"workload": "config4 batch_problems(%d) seed 11593, N %d..%d, median %d"
+                       % (len(probs), Ns.min(), Ns.max(), int(np.median(Ns))),
+                       "lanes": lanes, "split_n": split, "graph": info.get("graph"),
+                       "tune_s": tune_s, "max_refine": args.batch_refine},
+            "tflops": flops / (ms * 1e-3) / 1e12,
+            "loop": {"ms_per_step": ms_loop, "systems_per_s": len(probs) / (ms_loop * 1e-3),
+                     "speedup_batch_over_loop": ms_loop / ms, "u_rel_diff_batch_vs_loop": diff},
+            "statuses": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
+            "refine_steps_max": int(max(it)), "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -275,6 +359,10 @@ def main():
                     help="for ncu: one untimed SIMT warm-up step at N=1600, then one FP32+IR "
                          "tensor step at N = nch*100; no timing, no JSON")
     ap.add_argument("--nch", type=int, default=256, help="channels of the --profile-step system")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="time the batch driver on this many config-4 systems instead")
+    ap.add_argument("--batch-refine", type=int, default=10,
+                    help="refinement-step budget of the batch (stopping decided on the device)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warmup must be >= 3", file=sys.stderr)
@@ -283,6 +371,8 @@ def main():
         return reference_main(args)
     if args.profile_step:
         return profile_step(args.nch)
+    if args.batch:
+        return batch_main(args)
 
     import torch
     import paper_2512_11590_gb300 as g

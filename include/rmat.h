@@ -198,6 +198,47 @@ int rmat_reset_counters(rmat_ctx ctx);
  * Errors: -1 ctx, -2 hist NULL with n > 0. */
 int rmat_refine_history(rmat_ctx ctx, double* hist, int n);
 
+/* ---- batches of independent systems ------------------------------------------
+ * Many energies and partial waves of uneven size (the persistent-buffer energy
+ * scan of Sec. 3.4 step 1, generalised).  All systems of a batch share one
+ * precision.  The whole batch (assembly, factorisation, refined solve, R and U
+ * for every system) is enqueued without host synchronisation and captured into
+ * one CUDA graph that later runs replay; refinement uses max_refine steps with
+ * the stopping rule of rmat_solve evaluated on the device.  Systems with
+ * N > split_n run one after another with the full-device path; smaller ones are
+ * spread over `lanes` concurrent streams (single-CTA panels; at most N = 832 for
+ * the complex64 precisions and 416 for RMAT_C128, whatever split_n says).  rmat_batch_tune
+ * times candidate (lanes, split_n) plans on the batch and keeps the fastest,
+ * cached in the JSON-lines file named by the environment variable
+ * RMAT_TUNE_CACHE when it is set. */
+typedef struct rmat_batch_s* rmat_batch;
+#define RMAT_BATCH_LANES   1  /* concurrent streams for small systems (0..16)   */
+#define RMAT_BATCH_SPLIT_N 2  /* systems with N <= split_n go to the lanes      */
+#define RMAT_BATCH_GRAPH   3  /* 1 = capture and replay a CUDA graph (default)  */
+
+/* probs[s], E[s], V_dev[s] (device complex128 cpot(nlag,nch,nch) of system s, as
+ * in rmat_assemble) for s < nsys; the arrays are copied, V_dev must stay valid
+ * while the batch is used.  Reserves all workspace.  Errors: -1 ctx, -2 nsys,
+ * -3 a problem invalid or precisions differ, -4 E, -5 V_dev, -6 max_refine,
+ * -8 out; RMAT_ENOMEM. */
+int rmat_batch_create(rmat_ctx ctx, int nsys, const rmat_problem* probs, const double* E,
+                      const void* const* V_dev, int max_refine, double tol, rmat_batch* out);
+/* Open channels of every system (host int[nsys]). */
+int rmat_batch_nopen(rmat_batch b, int* nopen);
+int rmat_batch_set(rmat_batch b, int key, long long value);
+/* Choose lanes and split_n by timing candidate plans with the outputs U_dev. */
+int rmat_batch_tune(rmat_batch b, void* const* U_dev, int* lanes, int* split_n);
+/* Run the batch: U_dev[s] = device complex128 nopen_s x nopen_s column-major
+ * collision matrix of system s (may be NULL when nopen_s = 0).  status[s] and
+ * iters[s] (host, may be NULL) receive each system's status (as rmat_solve /
+ * rmat_collision) and refinement steps.  Synchronises.  Returns the most severe
+ * negative status, else RMAT_OK (per-system numerical outcomes in status). */
+int rmat_batch_run(rmat_batch b, void* const* U_dev, int* status, int* iters);
+/* out[0] systems, out[1] lanes, out[2] split_n, out[3] graph (1 used, -1 capture
+ * unavailable, 0 not yet), out[4] kernel launches enqueued so far. */
+int rmat_batch_info(rmat_batch b, long long* out, int n);
+int rmat_batch_destroy(rmat_batch b);
+
 /* ---- allocation-free collision step ---------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers that
  * cannot allocate device memory at the point where they need U: code whose

@@ -36,10 +36,15 @@ RMAT_PARAM_SPIN_LIMIT = 3
 RMAT_PARAM_TIMING = 4
 RMAT_PARAM_EQUILIBRATE = 5
 
+RMAT_BATCH_LANES = 1
+RMAT_BATCH_SPLIT_N = 2
+RMAT_BATCH_GRAPH = 3
+
 EXPORTED = ("rmat_create", "rmat_destroy", "rmat_set_param", "rmat_mesh", "rmat_assemble",
             "rmat_load_dense", "rmat_factor", "rmat_solve", "rmat_collision", "rmat_get_stats",
             "rmat_reset_counters", "rmat_refine_history", "rmat_collision_noalloc",
-            "rmat_status_string")
+            "rmat_batch_create", "rmat_batch_nopen", "rmat_batch_set", "rmat_batch_tune",
+            "rmat_batch_run", "rmat_batch_info", "rmat_batch_destroy", "rmat_status_string")
 
 
 class rmat_problem(ct.Structure):
@@ -81,6 +86,14 @@ def lib():
             "rmat_reset_counters": (i, [vp]),
             "rmat_refine_history": (i, [vp, pd, i]),
             "rmat_collision_noalloc": (i, [ct.POINTER(rmat_problem), d, vp, vp, i, vp, vp, pi, vp]),
+            "rmat_batch_create": (i, [vp, i, ct.POINTER(rmat_problem), pd, ct.POINTER(vp), i, d,
+                                      ct.POINTER(vp)]),
+            "rmat_batch_nopen": (i, [vp, pi]),
+            "rmat_batch_set": (i, [vp, i, ct.c_longlong]),
+            "rmat_batch_tune": (i, [vp, ct.POINTER(vp), pi, pi]),
+            "rmat_batch_run": (i, [vp, ct.POINTER(vp), pi, pi]),
+            "rmat_batch_info": (i, [vp, ct.POINTER(ct.c_longlong), i]),
+            "rmat_batch_destroy": (i, [vp]),
             "rmat_status_string": (ct.c_char_p, [i]),
         }
         for name, (res, args) in sig.items():
@@ -208,3 +221,56 @@ def rmat_collision_noalloc(prob, E, f_a_dev, X_dev, ldx, R_dev, U_dev, stream=0)
                                         ct.c_void_p(U_dev or None), ct.byref(nopen),
                                         ct.c_void_p(stream or None)))
     return nopen.value
+
+
+# ---- batches -------------------------------------------------------------------
+
+def _ptrs(seq):
+    return (ct.c_void_p * len(seq))(*[ct.c_void_p(int(p) or None) for p in seq])
+
+
+def rmat_batch_create(ctx, probs, energies, V_ptrs, max_refine=30, tol=1e-13) -> int:
+    """probs: list of rmat_problem (all one precision); returns the batch handle."""
+    n = len(probs)
+    arr = (rmat_problem * n)(*probs)
+    E = (ct.c_double * n)(*[float(e) for e in energies])
+    h = ct.c_void_p()
+    _check("rmat_batch_create", lib().rmat_batch_create(ct.c_void_p(ctx), n, arr, E, _ptrs(V_ptrs),
+                                                        int(max_refine), float(tol), ct.byref(h)))
+    return h.value
+
+
+def rmat_batch_nopen(b, n) -> list:
+    out = (ct.c_int * n)()
+    _check("rmat_batch_nopen", lib().rmat_batch_nopen(ct.c_void_p(b), out))
+    return list(out)
+
+
+def rmat_batch_set(b, key, value) -> None:
+    _check("rmat_batch_set", lib().rmat_batch_set(ct.c_void_p(b), int(key), int(value)))
+
+
+def rmat_batch_tune(b, U_ptrs):
+    lanes, split = ct.c_int(0), ct.c_int(0)
+    _check("rmat_batch_tune", lib().rmat_batch_tune(ct.c_void_p(b), _ptrs(U_ptrs), ct.byref(lanes),
+                                                    ct.byref(split)))
+    return lanes.value, split.value
+
+
+def rmat_batch_run(b, U_ptrs):
+    """Returns (status list, refinement-step list)."""
+    n = len(U_ptrs)
+    st = (ct.c_int * n)()
+    it = (ct.c_int * n)()
+    _check("rmat_batch_run", lib().rmat_batch_run(ct.c_void_p(b), _ptrs(U_ptrs), st, it))
+    return list(st), list(it)
+
+
+def rmat_batch_info(b) -> dict:
+    out = (ct.c_longlong * 5)()
+    n = lib().rmat_batch_info(ct.c_void_p(b), out, 5)
+    return dict(zip(("systems", "lanes", "split_n", "graph", "launches"), list(out)[:n]))
+
+
+def rmat_batch_destroy(b) -> None:
+    _check("rmat_batch_destroy", lib().rmat_batch_destroy(ct.c_void_p(b)))

@@ -47,8 +47,10 @@ double read_red(rmat_ctx c) {
   return v;
 }
 
+}  // namespace
+
 // Reserve device memory for the problem; RMAT_ENOMEM when it cannot fit.
-int reserve(rmat_ctx c, bool dense) {
+int ctx_reserve(rmat_ctx c, bool dense) {
   const size_t N = c->N, ld = c->ld, nrhs = c->nrhs;
   const size_t eb = elem_bytes(c->precision);
   const bool tensor = c->precision == RMAT_C64_3XTF32_IR;
@@ -87,6 +89,10 @@ int reserve(rmat_ctx c, bool dense) {
   }
   return RMAT_OK;
 }
+
+namespace {
+
+int reserve(rmat_ctx c, bool dense) { return ctx_reserve(c, dense); }
 
 void record_stage(rmat_ctx c, cudaEvent_t* ev) {
   if (c->timing) {
@@ -220,6 +226,9 @@ int rmat_destroy(rmat_ctx c) {
   if (!c) return RMAT_OK;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->borrowed_tables) c->Kmat = c->T0 = c->rmesh = c->fa = nullptr, c->l_d = nullptr,
+                          c->th_d = nullptr, c->open_d = nullptr;
+  tc_release(c);
   void* bufs[] = {c->C,    c->A64,  c->B64, c->ipiv, c->Kmat, c->T0,  c->rmesh,
                   c->fa,   c->l_d,  c->th_d, c->Wpt, c->X,    c->Rres, c->Bw,
                   c->Fpl,  c->Bpl, c->Ypl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
@@ -397,6 +406,26 @@ static int solve_factors(rmat_ctx c) {
   return lu_solve_dev<float>(c, c->C, c->N, c->ld, c->perm_main, c->nb, c->Bw, c->nrhs, c->nrhs,
                              c->precision == RMAT_C64_3XTF32_IR);
 }
+
+}  // extern "C"
+
+int enqueue_solve_refine(rmat_ctx c, int max_refine, double tol, IrState* st) {
+  RMAT_CHECK(launch_w_from_phi(c));
+  RMAT_CHECK(solve_factors(c));
+  RMAT_CHECK(launch_x_from_w(c));
+  RMAT_CHECK(launch_ir_init(c, st));
+  const int patience = c->precision == RMAT_C128 ? 2 : 1;
+  for (int it = 0; it <= max_refine; ++it) {
+    RMAT_CHECK(launch_residual(c, nullptr));
+    RMAT_CHECK(launch_ir_state(c, tol, patience, it == max_refine, st));
+    if (it == max_refine) break;
+    RMAT_CHECK(solve_factors(c));
+    RMAT_CHECK(launch_update(c, st));
+  }
+  return RMAT_OK;
+}
+
+extern "C" {
 
 int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int* iters,
                double* rel_resid) {

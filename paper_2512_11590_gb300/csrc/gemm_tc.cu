@@ -426,18 +426,23 @@ struct TcCache {
   const void* bw = nullptr;
   int n = -1, ldf = -1, nrhs = -1;
   TcMaps upd, sol;
-  bool attr = false;
 };
-TcCache g_tc;
+bool g_tc_attr = false;
+
+// The cache lives with its context (contexts may run concurrently on separate streams).
+TcCache& tc_cache(rmat_ctx c) {
+  if (!c->tc) c->tc = new TcCache();
+  return *reinterpret_cast<TcCache*>(c->tc);
+}
 
 int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, int K, int ax0,
               int ay0, int bx0, int by0, bool count_as_update) {
   if (M <= 0 || Nn <= 0 || K <= 0) return RMAT_OK;
   if (K % TC_BK || ax0 % TC_BK || bx0 % TC_BK) return RMAT_ESTATE;
-  if (!g_tc.attr) {
+  if (!g_tc_attr) {
     RMAT_CU(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TC_SMEM));
-    g_tc.attr = true;
+    g_tc_attr = true;
   }
   const int tiles = ceil_div(M, TC_BM) * ceil_div(Nn, TC_BN);
   const int grid = std::min(tiles, c->sm_count);
@@ -465,6 +470,7 @@ int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, i
 }  // namespace
 
 int tc_prepare(rmat_ctx c, int n, int nrhs) {
+  TcCache& g_tc = tc_cache(c);
   const int ldf = c->ld;
   if (g_tc.f == c->Fpl && g_tc.b == c->Bpl && g_tc.y == c->Ypl && g_tc.cmat == c->C &&
       g_tc.bw == c->Bw && g_tc.n == n && g_tc.ldf == ldf && g_tc.nrhs == nrhs)
@@ -499,11 +505,18 @@ int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n) {
   if (rest <= 0) return RMAT_OK;
   if (reinterpret_cast<void*>(A) != c->C || ld != c->ld) return RMAT_ESTATE;
   RMAT_CHECK(tc_prepare(c, n, c->nrhs + (c->nrhs & 1)));
+  TcCache& g_tc = tc_cache(c);
   return launch_tc(c, g_tc.upd, k0 + jb, k0 + jb, rest, rest, jb, k0, k0 + jb, 0, k0 + jb, true);
 }
 
 // Solve update: Bsub[M x nrhs] -= F[rows ay0.., cols k0..k0+jb] * Y, Y^T planes in Ypl.
 int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n) {
   RMAT_CHECK(tc_prepare(c, n, nrhs));
+  TcCache& g_tc = tc_cache(c);
   return launch_tc(c, g_tc.sol, 0, row0, M, nrhs, jb, k0, ay0, 0, 0, false);
+}
+
+void tc_release(rmat_ctx c) {
+  delete reinterpret_cast<TcCache*>(c->tc);
+  c->tc = nullptr;
 }

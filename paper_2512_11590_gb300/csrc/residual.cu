@@ -141,7 +141,9 @@ __global__ void absmax_kernel(const double2* __restrict__ v, size_t total,
 
 template <class T>
 __global__ void x_update_kernel(double2* __restrict__ X, const cplx<T>* __restrict__ W,
-                                size_t total, int nrhs, const double* __restrict__ D) {
+                                size_t total, int nrhs, const double* __restrict__ D,
+                                const IrState* __restrict__ st) {
+  if (st && st->done) return;  // device-driven refinement: already stopped
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     const double2 d = to_d(W[e]);
@@ -209,6 +211,43 @@ __global__ void x_to_colmajor_kernel(const double2* __restrict__ X, int N, int n
   }
 }
 
+// Device-side stopping rule of the graph-capturable refinement (same rule as the
+// host loop of rmat_solve): tol reached, non-halving residual `patience` times in
+// a row, non-finite residual, or the last allowed step.
+__global__ void ir_init_kernel(IrState* st) {
+  st->prev = INFINITY;
+  st->rel = 0.0;
+  st->stagn = 0;
+  st->done = 0;
+  st->status = RMAT_OK;
+  st->iters = 0;
+}
+
+__global__ void ir_state_kernel(const unsigned long long* __restrict__ red, double phi_max,
+                                double tol, int patience, int last, IrState* st) {
+  if (st->done) return;
+  const double r = __longlong_as_double((long long)*red) / phi_max;
+  st->rel = r;
+  if (!isfinite(r)) {
+    st->done = 1;
+    st->status = RMAT_ENOCONV;
+  } else if (r < tol) {
+    st->done = 1;
+  } else if (last) {
+    st->done = 1;
+    st->status = tol > 0 ? RMAT_ENOCONV : RMAT_OK;
+  } else if (r > 0.5 * st->prev) {
+    if (++st->stagn >= patience) {
+      st->done = 1;
+      st->status = RMAT_ENOCONV;
+    }
+  } else {
+    st->stagn = 0;
+  }
+  st->prev = r;
+  if (!st->done) st->iters++;
+}
+
 int grid_for(rmat_ctx c, size_t total) {
   return std::max(1, (int)std::min<size_t>((size_t)c->sm_count * 8, (total + 255) / 256));
 }
@@ -245,15 +284,15 @@ int launch_residual(rmat_ctx c, double*) {
   return RMAT_OK;
 }
 
-int launch_update(rmat_ctx c) {
+int launch_update(rmat_ctx c, const IrState* st) {
   const size_t total = (size_t)c->N * c->nrhs;
   const double* D = c->equil ? c->Dsc : nullptr;
   if (c->precision == RMAT_C128)
     x_update_kernel<double><<<grid_for(c, total), 256, 0, c->stream>>>(
-        c->X, reinterpret_cast<const double2*>(c->Bw), total, c->nrhs, D);
+        c->X, reinterpret_cast<const double2*>(c->Bw), total, c->nrhs, D, st);
   else
     x_update_kernel<float><<<grid_for(c, total), 256, 0, c->stream>>>(
-        c->X, reinterpret_cast<const float2*>(c->Bw), total, c->nrhs, D);
+        c->X, reinterpret_cast<const float2*>(c->Bw), total, c->nrhs, D, st);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;
@@ -299,6 +338,20 @@ int launch_x_out(rmat_ctx c, double2* Xo, int ldx) {
 int launch_absmax(rmat_ctx c, const double2* v, size_t n) {
   RMAT_CU(cudaMemsetAsync(c->red, 0, sizeof(unsigned long long), c->stream));
   absmax_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(v, n, c->red);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+int launch_ir_init(rmat_ctx c, IrState* st) {
+  ir_init_kernel<<<1, 1, 0, c->stream>>>(st);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+int launch_ir_state(rmat_ctx c, double tol, int patience, int last, IrState* st) {
+  ir_state_kernel<<<1, 1, 0, c->stream>>>(c->red, c->phi_max, tol, patience, last, st);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;

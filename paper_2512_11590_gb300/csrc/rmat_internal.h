@@ -38,6 +38,12 @@ struct LUPerm {
   size_t cap = 0;  // bytes
 };
 
+// State of a device-driven refinement loop (graph-capturable solve).
+struct IrState {
+  double prev, rel;
+  int stagn, done, status, iters;
+};
+
 // Device status words written by kernels (read back by the host).
 enum { ST_INFO = 0, ST_TIMEOUT = 1, ST_BADARG = 2, ST_COUNT = 8 };
 
@@ -99,6 +105,8 @@ struct rmat_ctx_s {
   int* hstat = nullptr;    // pinned mirror
 
   bool assembled = false, factored = false, solved = false;
+  void* tc = nullptr;      // tensor-map cache of this context (gemm_tc.cu)
+  bool borrowed_tables = false;  // mesh/channel tables owned by a batch, not freed here
 
   // statistics
   long long launches = 0, tu_launches = 0;
@@ -136,6 +144,7 @@ int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n);
 // solve update: rows [row0, row0+M) of the solve buffer Bw (ld = nrhs) -= F(ay0.., k0..k0+jb) * Y
 int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n);
 int tc_prepare(rmat_ctx c, int n, int nrhs);
+void tc_release(rmat_ctx c);
 // lu.cu (SIMT complex GEMM C -= A B, row-major)
 int gemm_sub_c128(rmat_ctx c, int M, int N, int K, const double2* A, int lda, const double2* B,
                   int ldb, double2* C, int ldc);
@@ -144,7 +153,13 @@ int panel_ctas_for(rmat_ctx c, int M);
 int launch_residual(rmat_ctx c, double* relres_dev_unused);
 int launch_x_out(rmat_ctx c, double2* Xo, int ldx);
 int launch_absmax(rmat_ctx c, const double2* v, size_t n);
-int launch_update(rmat_ctx c);
+int launch_update(rmat_ctx c, const IrState* st = nullptr);
+int launch_ir_init(rmat_ctx c, IrState* st);
+int launch_ir_state(rmat_ctx c, double tol, int patience, int last, IrState* st);
+// api.cu: solve + refinement enqueued without host synchronisation (fixed step
+// budget, device-side stopping rule); X stays in the context's FP64 buffer.
+int enqueue_solve_refine(rmat_ctx c, int max_refine, double tol, IrState* st);
+int ctx_reserve(rmat_ctx c, bool dense);
 int launch_x_from_w(rmat_ctx c);
 int launch_w_from_phi(rmat_ctx c);
 // collision.cu
