@@ -272,7 +272,7 @@ def batch_main(args):
     torch.cuda.set_device(0)
     probs = cp.batch_problems(args.batch)
     prec = g.RMAT_C64_3XTF32_IR if args.precision == "tf32" else g.RMAT_C64_SIMT_IR
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()                 # capturable stream for the batch's CUDA graph
     ctx = g.rmat_create(0, stream.cuda_stream)
     Vs, structs, keep = [], [], []
     for p in probs:
@@ -286,6 +286,7 @@ def batch_main(args):
     nopen = g.rmat_batch_nopen(b, len(probs))
     Us = [torch.zeros(max(1, n) ** 2, dtype=torch.complex128, device="cuda") for n in nopen]
     Uptr = [u.data_ptr() for u in Us]
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     lanes, split = g.rmat_batch_tune(b, Uptr)
     tune_s = time.perf_counter() - t0

@@ -276,6 +276,11 @@ int rmat_collision_noalloc(const rmat_problem* prob, double E, const void* f_a_d
 /* Human-readable name of a status code (static storage). */
 const char* rmat_status_string(int status);
 
+/* The CUDA runtime error behind the calling thread's most recent RMAT_ECUDA
+ * (0 if none yet); writes "file:line cudaErrorName: description" into buf
+ * (NUL-terminated, truncated to len bytes; buf may be NULL). */
+int rmat_last_error(char* buf, int len);
+
 #ifdef __cplusplus
 }
 #endif

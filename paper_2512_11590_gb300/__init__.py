@@ -54,9 +54,10 @@ class rmat_problem(ct.Structure):
 
 
 class RmatError(RuntimeError):
-    def __init__(self, name, status):
+    def __init__(self, name, status, detail=""):
         self.status = status
-        super().__init__(f"{name} -> {status} ({status_string(status)})")
+        super().__init__(f"{name} -> {status} ({status_string(status)})"
+                         + (f" at {detail}" if detail else ""))
 
 
 _lib = None
@@ -95,6 +96,7 @@ def lib():
             "rmat_batch_info": (i, [vp, ct.POINTER(ct.c_longlong), i]),
             "rmat_batch_destroy": (i, [vp]),
             "rmat_status_string": (ct.c_char_p, [i]),
+            "rmat_last_error": (i, [ct.c_char_p, i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -107,8 +109,17 @@ def status_string(s: int) -> str:
     return lib().rmat_status_string(int(s)).decode()
 
 
+def rmat_last_error() -> tuple:
+    """(CUDA error code, "file:line name: description") of the last RMAT_ECUDA."""
+    buf = ct.create_string_buffer(256)
+    e = lib().rmat_last_error(buf, 256)
+    return e, buf.value.decode()
+
+
 def _check(name, s, ok=(RMAT_OK,)):
     if s not in ok:
+        if s == RMAT_ECUDA:
+            raise RmatError(name, s, rmat_last_error()[1])
         raise RmatError(name, s)
     return s
 

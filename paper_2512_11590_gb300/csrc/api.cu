@@ -1,6 +1,7 @@
 // C ABI entry points (include/rmat.h): context, workspace, orchestration of
 // assemble -> factor -> solve/refine -> collision on one stream.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 
@@ -113,6 +114,18 @@ double elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 }  // namespace
 
+namespace {
+thread_local int g_last_err = 0;
+thread_local char g_last_where[192] = "";
+}  // namespace
+
+void rmat_note_cuda_error(int err, const char* file, int line) {
+  g_last_err = err;
+  const char* base = std::strrchr(file, '/');
+  std::snprintf(g_last_where, sizeof(g_last_where), "%s:%d %s: %s", base ? base + 1 : file, line,
+                cudaGetErrorName((cudaError_t)err), cudaGetErrorString((cudaError_t)err));
+}
+
 int perm_reserve(rmat_ctx c, LUPerm& pm, int n, int nb) {
   const size_t nblk = (size_t)(n + nb - 1) / nb;
   const size_t bytes = nblk * (5 * (size_t)nb + 1) * sizeof(int);
@@ -157,6 +170,14 @@ cudaEvent_t rmat_event(rmat_ctx c) {
 }
 
 extern "C" {
+
+int rmat_last_error(char* buf, int len) {
+  if (buf && len > 0) {
+    std::strncpy(buf, g_last_where, (size_t)len - 1);
+    buf[len - 1] = 0;
+  }
+  return g_last_err;
+}
 
 const char* rmat_status_string(int s) {
   switch (s) {

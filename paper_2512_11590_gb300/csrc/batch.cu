@@ -85,6 +85,14 @@ struct rmat_batch_s {
 
 namespace {
 
+// LU block width of a system: 32 in a lane (a single-CTA panel keeps its rows x
+// 32 columns in shared memory), the single-system default otherwise.
+int sys_nb(rmat_batch b, const BatchSys& y) {
+  if (y.lane > 0) return 32;
+  if (b->precision == RMAT_C128) return y.N >= 2048 ? 64 : 32;
+  return y.N >= 4096 ? 128 : 64;
+}
+
 template <class T>
 int enqueue_system(rmat_batch b, int s, void* U) {
   BatchSys& y = b->sys[s];
@@ -101,10 +109,7 @@ int enqueue_system(rmat_batch b, int s, void* U) {
   c->hm = y.hm;
   c->bloch_B = y.B;
   c->E = y.E;
-  if (y.lane > 0)
-    c->nb = 32;  // single-CTA panel: rows x 32 columns stay in shared memory
-  else
-    c->nb = b->precision == RMAT_C128 ? (y.N >= 2048 ? 64 : 32) : (y.N >= 4096 ? 128 : 64);
+  c->nb = sys_nb(b, y);
   c->panel_ctas_param = y.lane > 0 ? 1 : 0;
   c->Kmat = m.K;
   c->rmesh = m.r;
@@ -115,6 +120,7 @@ int enqueue_system(rmat_batch b, int s, void* U) {
   c->open_d = b->open_all + y.off_open;
   c->borrowed_tables = true;
   c->equil = c->equil_param == -1 ? b->precision != RMAT_C128 : c->equil_param == 1;
+  RMAT_CHECK(perm_reserve(c, c->perm_main, y.N, c->nb));  // lay out, no growth (plan sized it)
   RMAT_CU(cudaMemsetAsync(c->dstat, 0, ST_COUNT * sizeof(int), c->stream));
   RMAT_CHECK(launch_assemble(c, y.V, y.E));
   RMAT_CHECK(launch_point_coupling(c, y.V, y.E));
@@ -190,7 +196,8 @@ int plan(rmat_batch b) {
     c->kind = 1;
     c->nb = 32;
     RMAT_CHECK(ctx_reserve(c, false));
-    RMAT_CHECK(perm_reserve(c, c->perm_main, maxN, 32));
+    for (const BatchSys& y : b->sys)
+      if (y.lane == l) RMAT_CHECK(perm_reserve(c, c->perm_main, y.N, sys_nb(b, y)));
     RMAT_CHECK(perm_reserve(c, c->perm_z, maxc, 32));
     RMAT_CHECK(rmat_grow(c, (void**)&c->Wpt, &c->Wpt_cap, (size_t)maxlag * maxc * maxc * 16));
     RMAT_CHECK(rmat_grow(c, (void**)&c->Rint, &c->Rint_cap, (size_t)maxc * maxc * 16));
@@ -200,6 +207,7 @@ int plan(rmat_batch b) {
   }
   b->planned = true;
   b->warm = false;
+  b->graph_ok = 0;
   return RMAT_OK;
 }
 
@@ -213,13 +221,19 @@ int run_once(rmat_batch b, void* const* U, bool allow_graph) {
   }
   const bool same_U = b->gexec && b->graph_U.size() == b->sys.size() &&
                       std::equal(b->graph_U.begin(), b->graph_U.end(), U);
-  if (allow_graph && b->use_graph && !same_U) {
+  if (allow_graph && b->use_graph && b->graph_ok >= 0 && !same_U) {
     if (b->gexec) {
       cudaGraphExecDestroy(b->gexec);
       b->gexec = nullptr;
     }
     cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(main, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+    // the legacy default stream cannot be captured: run without a graph there
+    if (main == nullptr) {
+      b->graph_ok = -1;
+    } else if (cudaStreamBeginCapture(main, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      b->graph_ok = -1;
+    } else {
       const int st = enqueue_all(b, U);
       const cudaError_t e = cudaStreamEndCapture(main, &g);
       if (st == RMAT_OK && e == cudaSuccess && g &&

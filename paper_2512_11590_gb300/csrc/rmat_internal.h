@@ -168,10 +168,17 @@ size_t collision_workspace_bytes(int nch);
 // mesh.cpp: K = hm*T0 - (hm*(B/a)) * (f_i*f_j) in IEEE double, no contraction
 void rmat_kinetic_table(int nlag, double hm, double s1, const double* T0, const double* fa, double* K);
 
-#define RMAT_CU(x)                                  \
-  do {                                              \
-    cudaError_t e__ = (x);                          \
-    if (e__ != cudaSuccess) return RMAT_ECUDA;      \
+// Records the failing call's CUDA error and source location (read back with
+// rmat_last_error) before returning RMAT_ECUDA.
+void rmat_note_cuda_error(int err, const char* file, int line);
+
+#define RMAT_CU(x)                                        \
+  do {                                                    \
+    cudaError_t e__ = (x);                                \
+    if (e__ != cudaSuccess) {                             \
+      rmat_note_cuda_error((int)e__, __FILE__, __LINE__); \
+      return RMAT_ECUDA;                                  \
+    }                                                     \
   } while (0)
 
 #define RMAT_CHECK(...)                             \

@@ -41,7 +41,8 @@ def test_batch_matches_oracle(g, cases, prec, lanes, split, graph):
     import torch
     torch.cuda.set_device(0)
     probs, refs = cases
-    ctx = g.rmat_create(0, torch.cuda.current_stream().cuda_stream)
+    stream = torch.cuda.Stream()                 # a capturable (non-default) stream
+    ctx = g.rmat_create(0, stream.cuda_stream)
     try:
         Vs, structs, keep = [], [], []
         for p in probs:
@@ -59,6 +60,7 @@ def test_batch_matches_oracle(g, cases, prec, lanes, split, graph):
             g.rmat_batch_set(b, g.RMAT_BATCH_GRAPH, graph)
             nopen = g.rmat_batch_nopen(b, len(probs))
             Us = [torch.zeros(max(1, n) ** 2, dtype=torch.complex128, device="cuda") for n in nopen]
+            torch.cuda.synchronize()
             for rep in range(2):                   # second run replays the graph
                 st, it = g.rmat_batch_run(b, [u.data_ptr() for u in Us])
                 torch.cuda.synchronize()
@@ -72,6 +74,7 @@ def test_batch_matches_oracle(g, cases, prec, lanes, split, graph):
                     assert relerr(U, ref["U"]) < TOL[prec], (rep, k, relerr(U, ref["U"]))
             info = g.rmat_batch_info(b)
             assert info["systems"] == len(probs)
+            assert info["graph"] == (1 if graph else 0)
         finally:
             g.rmat_batch_destroy(b)
     finally:
