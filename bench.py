@@ -437,6 +437,18 @@ def main():
         peak = 152 * 128 * 2 * 2070e6 / 1e12
         bound, unit, pname = "alu", "TFLOP/s", "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"
     achieved = tu_flops / (tu_ms * 1e-3) / 1e12 if tu_ms and tu_ms > 0 else None
+    traffic, tsrc = None, None
+    if prec == g.RMAT_C64_3XTF32_IR:
+        # DRAM bytes per launch: the ncu capture of the same kernel at N = 6400 (first
+        # update, 6272^2 x 128) read + wrote 596.8 MB for 655 MB of algorithmic bytes
+        # (C22 read + write, 4 operand planes per side); scaled by the algorithmic
+        # bytes of this run's average launch
+        nb = int(stats["nb"])
+        rests = [p.N - (k + 1) * nb for k in range(p.N // nb) if p.N - (k + 1) * nb > 0]
+        alg = [r * r * 16.0 + 2 * r * nb * 16.0 for r in rests]
+        traffic = 596.8e6 / 655.0e6 * (sum(alg) / len(alg))
+        tsrc = ("ncu dram__bytes_read+write of the N=6400 first-update capture "
+                "(profiles/trailing_update_tc_n6400.md), scaled by algorithmic bytes per launch")
     line = {
         "metric": "N=25600 complex solve time & TFLOP/s: FP32+IR vs FP64 at equal U error",
         "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -447,14 +459,17 @@ def main():
                    "refinement": ir, "l2": "inputs larger than L2 (C is %.1f GB)" % (p.N * p.N * 8 / 1e9),
                    "lu_block": stats["nb"], "panel_ctas": stats["panel_ctas"],
                    "stage_ms": {k: stats[k] for k in ("assemble_ms", "factor_ms", "solve_ms",
-                                                       "refine_ms", "collision_ms")}},
+                                                       "refine_ms", "collision_ms")},
+                   "kernel_ms": {k: [stats.get(k + "_ms"), stats.get(k + "_launches")]
+                                 for k in ("panel", "apply_inv", "solve_tc", "resid")}},
         "fp64_path": fp64,
         "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": {"kernel": "trailing update C22 -= L21 U12", "bound": bound,
                      "achieved": achieved, "peak": peak, "peak_source": pname, "unit": unit,
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_source": tsrc,
                      "launches": tu_n, "kernel_ms_per_step": tu_ms,
                      "share_of_step": (tu_ms / ms) if tu_ms and tu_ms > 0 else None},
         "clocks": clk.summary(),

@@ -186,9 +186,13 @@ int rmat_collision(rmat_ctx ctx, void* R_dev, void* U_dev, int* nopen);
  *   out[5] trailing-update launches, out[6] trailing-update time (ms, events),
  *   out[7] trailing-update algorithmic flops (8 M N K per launch),
  *   out[8] assemble ms, out[9] factor ms, out[10] first solve ms,
- *   out[11] refinement ms, out[12] collision ms  (timers need RMAT_PARAM_TIMING=1;
- *   a stage's time is -1 when it was not timed).
- * n: capacity of out; returns the number of values written (<= 13). */
+ *   out[11] refinement ms, out[12] collision ms,
+ *   out[13] / out[14] panel kernel ms / launches,
+ *   out[15] / out[16] solve-path diagonal-block application ms / launches,
+ *   out[17] / out[18] solve-path tensor-core block update ms / launches,
+ *   out[19] / out[20] FP64 residual ms / launches
+ *   (timers need RMAT_PARAM_TIMING=1; a time is -1 when it was not timed).
+ * n: capacity of out; returns the number of values written (<= 21). */
 int rmat_get_stats(rmat_ctx ctx, double* out, int n);
 int rmat_reset_counters(rmat_ctx ctx);
 

@@ -203,12 +203,14 @@ def rmat_collision(ctx, R_dev=0, U_dev=0) -> int:
 
 
 STAT_KEYS = ("N", "nrhs", "nb", "panel_ctas", "launches", "tu_launches", "tu_ms", "tu_flops",
-             "assemble_ms", "factor_ms", "solve_ms", "refine_ms", "collision_ms")
+             "assemble_ms", "factor_ms", "solve_ms", "refine_ms", "collision_ms",
+             "panel_ms", "panel_launches", "apply_inv_ms", "apply_inv_launches",
+             "solve_tc_ms", "solve_tc_launches", "resid_ms", "resid_launches")
 
 
 def rmat_get_stats(ctx) -> dict:
-    buf = (ct.c_double * 13)()
-    n = lib().rmat_get_stats(ct.c_void_p(ctx), buf, 13)
+    buf = (ct.c_double * len(STAT_KEYS))()
+    n = lib().rmat_get_stats(ct.c_void_p(ctx), buf, len(STAT_KEYS))
     return {k: buf[i] for i, k in enumerate(STAT_KEYS[:n])}
 
 

@@ -169,6 +169,24 @@ cudaEvent_t rmat_event(rmat_ctx c) {
   return c->ev_pool[c->ev_next++];
 }
 
+KTimer::KTimer(rmat_ctx c_, int k_) : c(c_), k(k_) {
+  if (c->timing) {
+    e0 = rmat_event(c);
+    if (e0) cudaEventRecord(e0, c->stream);
+  }
+}
+
+void KTimer::end() {
+  c->kt_launches[k]++;
+  if (e0) {
+    cudaEvent_t e1 = rmat_event(c);
+    if (e1) {
+      cudaEventRecord(e1, c->stream);
+      c->kt_events[k].push_back({e0, e1});
+    }
+  }
+}
+
 extern "C" {
 
 int rmat_last_error(char* buf, int len) {
@@ -542,21 +560,27 @@ int rmat_collision(rmat_ctx c, void* R_dev, void* U_dev, int* nopen) {
 int rmat_get_stats(rmat_ctx c, double* out, int n) {
   if (!c) return -1;
   if (!out || n < 0) return -2;
-  double tu = 0;
-  bool ok = true;
-  for (auto& pr : c->tu_events) {
-    double ms = elapsed(pr.first, pr.second);
-    if (ms < 0) ok = false;
-    tu += ms;
-  }
+  auto sum = [](const std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& evs) {
+    if (evs.empty()) return -1.0;
+    double t = 0;
+    for (auto& pr : evs) {
+      const double ms = elapsed(pr.first, pr.second);
+      if (ms < 0) return -1.0;
+      t += ms;
+    }
+    return t;
+  };
   for (int k = 0; k < 5; ++k)
     c->stage_ms[k] = elapsed(c->stage_ev[k][0], c->stage_ev[k][1]);
-  const double v[13] = {(double)c->N, (double)c->nrhs, (double)c->nb,
+  const double v[21] = {(double)c->N, (double)c->nrhs, (double)c->nb,
                         (double)panel_ctas_for(c, c->N > 0 ? c->N : 1), (double)c->launches,
-                        (double)c->tu_launches, (ok && !c->tu_events.empty()) ? tu : -1.0,
-                        c->tu_flops, c->stage_ms[0], c->stage_ms[1], c->stage_ms[2],
-                        c->stage_ms[3], c->stage_ms[4]};
-  const int m = n < 13 ? n : 13;
+                        (double)c->tu_launches, sum(c->tu_events), c->tu_flops, c->stage_ms[0],
+                        c->stage_ms[1], c->stage_ms[2], c->stage_ms[3], c->stage_ms[4],
+                        sum(c->kt_events[KT_PANEL]), (double)c->kt_launches[KT_PANEL],
+                        sum(c->kt_events[KT_APPLY_INV]), (double)c->kt_launches[KT_APPLY_INV],
+                        sum(c->kt_events[KT_SOLVE_TC]), (double)c->kt_launches[KT_SOLVE_TC],
+                        sum(c->kt_events[KT_RESID]), (double)c->kt_launches[KT_RESID]};
+  const int m = n < 21 ? n : 21;
   for (int k = 0; k < m; ++k) out[k] = v[k];
   return m;
 }
@@ -574,6 +598,10 @@ int rmat_reset_counters(rmat_ctx c) {
   c->launches = c->tu_launches = 0;
   c->tu_flops = 0;
   c->tu_events.clear();
+  for (int k = 0; k < 4; ++k) {
+    c->kt_events[k].clear();
+    c->kt_launches[k] = 0;
+  }
   c->ev_next = 0;
   for (double& s : c->stage_ms) s = -1;
   for (auto& pr : c->stage_ev) pr[0] = pr[1] = nullptr;

@@ -32,10 +32,18 @@ namespace {
 constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 8, TC_STAGES = 4;
 constexpr int TC_THREADS = 192;
 constexpr uint32_t A_PLANE_BYTES = TC_BM * TC_BK * 4;                              // 4 KB
-constexpr uint32_t B_PLANE_BYTES = TC_BN * TC_BK * 4;                              // 8 KB
-constexpr uint32_t STAGE_BYTES = 4 * A_PLANE_BYTES + 4 * B_PLANE_BYTES;            // 48 KB
 constexpr uint32_t STAGING_BYTES = TC_BM * 32 * 4;  // 16 complex columns x 128 rows, 128B swizzle
-constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + 2 * STAGING_BYTES + 1024 + 256;
+
+// Tile width BN = 256 (trailing updates) or 128 (solve updates: twice the tiles for
+// the same rows, and two accumulator sets in the 512 TMEM columns, so the epilogue
+// of one tile overlaps the MMAs of the next).
+template <int BN>
+struct TcCfg {
+  static constexpr uint32_t B_PLANE = BN * TC_BK * 4;                 // 8 / 4 KB
+  static constexpr uint32_t STAGE = 4 * A_PLANE_BYTES + 4 * B_PLANE;  // 48 / 32 KB
+  static constexpr int NBUF = 512 / (2 * BN);                         // accumulator sets
+  static constexpr size_t SMEM = (size_t)TC_STAGES * STAGE + 2 * STAGING_BYTES + 1024 + 256;
+};
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
 
 struct TcMaps {
@@ -102,13 +110,14 @@ __device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
   d |= (uint64_t)6 << 61;                   // layout: SWIZZLE_32B
   return d;
 }
-// kind::tf32 instruction descriptor: D f32, A/B tf32, K-major, N = 256, M = 128.
+// kind::tf32 instruction descriptor: D f32, A/B tf32, K-major, N = BN, M = 128.
+template <int BN>
 __host__ __device__ constexpr uint32_t idesc_tf32(bool negA) {
   return (1u << 4)               // D format f32
          | (2u << 7)             // A format tf32
          | (2u << 10)            // B format tf32
          | ((negA ? 1u : 0u) << 13)
-         | ((uint32_t)(TC_BN >> 3) << 17)
+         | ((uint32_t)(BN >> 3) << 17)
          | ((uint32_t)(TC_BM >> 4) << 24);
 }
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
@@ -189,23 +198,27 @@ __device__ __forceinline__ void product(int p, int& qa, int& qb, int& acc, int& 
   neg = (acc == 0 && part == 1);
 }
 
+template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, int Nn, int K,
                  int ax0, int rowA0, int bx0, int rowB0, int* __restrict__ err) {
+  using Cfg = TcCfg<BN>;
+  constexpr uint32_t B_PLANE_BYTES = Cfg::B_PLANE, STAGE_BYTES = Cfg::STAGE;
+  constexpr int NBUF = Cfg::NBUF;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   unsigned char* stages = smem;
   unsigned char* staging = stages + TC_STAGES * STAGE_BYTES;  // 2 x 16 KB, 1024-aligned
   uint64_t* bars = reinterpret_cast<uint64_t*>(staging + 2 * STAGING_BYTES);
-  // bars[0..3] full, [4..7] empty, [8] tmem_full, [9] tmem_empty
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  // bars[0..3] full, [4..7] empty, [8 + 2b] tmem_full of set b, [9 + 2b] tmem_empty
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* epi_abort = abort_flag + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mt = (M + TC_BM - 1) / TC_BM;
-  const int nt = (Nn + TC_BN - 1) / TC_BN;
+  const int nt = (Nn + BN - 1) / BN;
   const int ntiles = mt * nt;
   const int ksteps = K / TC_BK;
 
@@ -214,8 +227,10 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
       mbar_init(smem_u32(&bars[s]), 1);
       mbar_init(smem_u32(&bars[4 + s]), 1);
     }
-    mbar_init(smem_u32(&bars[8]), 1);
-    mbar_init(smem_u32(&bars[9]), 4);
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(smem_u32(&bars[8 + 2 * b]), 1);
+      mbar_init(smem_u32(&bars[9 + 2 * b]), 4);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -236,7 +251,7 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
       uint32_t it = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int m0 = (tile % mt) * TC_BM, n0 = (tile / mt) * TC_BN;
+        const int m0 = (tile % mt) * TC_BM, n0 = (tile / mt) * BN;
         for (int ks = 0; ks < ksteps; ++ks, ++it) {
           const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
           if (!mbar_wait(smem_u32(&bars[4 + s]), ph ^ 1, abort_flag)) { ok = false; break; }
@@ -268,9 +283,12 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
     if (lane == 0) {
       uint32_t it = 0, tcount = 0;
       bool ok = true;
-      uint32_t idesc[2] = {idesc_tf32(false), idesc_tf32(true)};
+      uint32_t idesc[2] = {idesc_tf32<BN>(false), idesc_tf32<BN>(true)};
+      uint32_t buf = 0, use = 0;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tcount) {
-        if (tcount > 0 && !mbar_wait(smem_u32(&bars[9]), (tcount - 1) & 1, abort_flag)) {
+        buf = tcount % NBUF;
+        use = tcount / NBUF;  // earlier tiles that used this accumulator set
+        if (use > 0 && !mbar_wait(smem_u32(&bars[9 + 2 * buf]), (use - 1) & 1, abort_flag)) {
           ok = false;
           break;
         }
@@ -287,20 +305,22 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
             const uint64_t ad = sdesc_sw32(st + qa * A_PLANE_BYTES);
             const uint64_t bd = sdesc_sw32(st + 4 * A_PLANE_BYTES + qb * B_PLANE_BYTES);
             const uint32_t first = (ks == 0) && (p == 0 || p == 6);
-            mma_tf32(tmem + acc * TC_BN, ad, bd, idesc[neg], first ? 0u : 1u);
+            mma_tf32(tmem + buf * 2 * BN + acc * BN, ad, bd, idesc[neg], first ? 0u : 1u);
           }
           mma_commit(smem_u32(&bars[4 + s]));  // frees the stage once these MMAs have read it
         }
         if (!ok) break;
-        mma_commit(smem_u32(&bars[8]));        // accumulators ready for the epilogue
+        mma_commit(smem_u32(&bars[8 + 2 * buf]));  // accumulator set ready for the epilogue
       }
       if (!ok) {
         *abort_flag = 1;
         atomicExch(err, 2);
         // let every MMA issued so far finish before TMEM is released
-        mma_commit(smem_u32(&bars[8]));
+        buf = tcount % NBUF;
+        use = tcount / NBUF;
+        mma_commit(smem_u32(&bars[8 + 2 * buf]));
         const unsigned long long t0 = gtimer();
-        while (!mbar_try(smem_u32(&bars[8]), tcount & 1))
+        while (!mbar_try(smem_u32(&bars[8 + 2 * buf]), use & 1))
           if (gtimer() - t0 > TC_WAIT_NS) break;
       }
     }
@@ -314,10 +334,11 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
     const bool leader = (warp == 2 && lane == 0);
     uint32_t tcount = 0, chunk = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
-      const int m0 = (tile % mt) * TC_BM, n0 = (tile / mt) * TC_BN;
+      const int m0 = (tile % mt) * TC_BM, n0 = (tile / mt) * BN;
+      const uint32_t buf = tcount % NBUF, use = tcount / NBUF;
       // The four epilogue warps leave together (they share named barriers): each
       // waits (bounded), then one thread snapshots the abort flag for all.
-      if (!mbar_wait(smem_u32(&bars[8]), tcount & 1, abort_flag)) {
+      if (!mbar_wait(smem_u32(&bars[8 + 2 * buf]), use & 1, abort_flag)) {
         *abort_flag = 1;
         atomicExch(err, 2);
       }
@@ -328,16 +349,16 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
       fence_after();
       const bool rowvalid = (m0 + row) < M;
 #pragma unroll 1
-      for (int ch = 0; ch < TC_BN / 16; ++ch, ++chunk) {
+      for (int ch = 0; ch < BN / 16; ++ch, ++chunk) {
         float re[16], im[16];
-        const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + ch * 16;
+        const uint32_t ta = tmem + buf * 2 * BN + ((uint32_t)(quad * 32) << 16) + ch * 16;
         tmem_ld16(ta, re);
-        tmem_ld16(ta + TC_BN, im);
+        tmem_ld16(ta + BN, im);
         tmem_wait_ld();
-        if (ch == TC_BN / 16 - 1) {          // accumulators fully read: release TMEM
+        if (ch == BN / 16 - 1) {             // accumulator set fully read: release it
           fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(&bars[9]));
+          if (lane == 0) mbar_arrive(smem_u32(&bars[9 + 2 * buf]));
         }
         unsigned char* buf = staging + (chunk & 1) * STAGING_BYTES;
         if (leader) bulk_wait_read1();       // the reduce that used this buffer has read it
@@ -425,9 +446,9 @@ struct TcCache {
   const void* cmat = nullptr;
   const void* bw = nullptr;
   int n = -1, ldf = -1, nrhs = -1;
-  TcMaps upd, sol;
+  TcMaps upd, sol;  // trailing update (BN = 256), solve update (BN = 128)
 };
-bool g_tc_attr = false;
+bool g_tc_attr[2] = {false, false};
 
 // The cache lives with its context (contexts may run concurrently on separate streams).
 TcCache& tc_cache(rmat_ctx c) {
@@ -435,16 +456,18 @@ TcCache& tc_cache(rmat_ctx c) {
   return *reinterpret_cast<TcCache*>(c->tc);
 }
 
+template <int BN>
 int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, int K, int ax0,
               int ay0, int bx0, int by0, bool count_as_update) {
   if (M <= 0 || Nn <= 0 || K <= 0) return RMAT_OK;
   if (K % TC_BK || ax0 % TC_BK || bx0 % TC_BK) return RMAT_ESTATE;
-  if (!g_tc_attr) {
-    RMAT_CU(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  constexpr size_t TC_SMEM = TcCfg<BN>::SMEM;
+  if (!g_tc_attr[BN == 128]) {
+    RMAT_CU(cudaFuncSetAttribute(tc_update_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TC_SMEM));
-    g_tc_attr = true;
+    g_tc_attr[BN == 128] = true;
   }
-  const int tiles = ceil_div(M, TC_BM) * ceil_div(Nn, TC_BN);
+  const int tiles = ceil_div(M, TC_BM) * ceil_div(Nn, BN);
   const int grid = std::min(tiles, c->sm_count);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing && count_as_update) {
@@ -452,8 +475,8 @@ int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, i
     e1 = rmat_event(c);
     RMAT_CU(cudaEventRecord(e0, c->stream));
   }
-  tc_update_kernel<<<grid, TC_THREADS, TC_SMEM, c->stream>>>(maps, cx0, cy0, M, Nn, K, ax0, ay0,
-                                                             bx0, by0, c->dstat + ST_TIMEOUT);
+  tc_update_kernel<BN><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(
+      maps, cx0, cy0, M, Nn, K, ax0, ay0, bx0, by0, c->dstat + ST_TIMEOUT);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   if (count_as_update) {
@@ -484,7 +507,7 @@ int tc_prepare(rmat_ctx c, int n, int nrhs) {
                               TC_BN));
     g_tc.sol.a[q] = g_tc.upd.a[q];
     RMAT_CHECK(make_plane_map(&g_tc.sol.b[q], c->Ypl + q * yplane, RMAT_MAX_NB,
-                              std::max(1, nrhs), RMAT_MAX_NB, TC_BN));
+                              std::max(1, nrhs), RMAT_MAX_NB, 128));
   }
   RMAT_CHECK(make_out_map(&g_tc.upd.c, c->C, n, n, c->ld));
   RMAT_CHECK(make_out_map(&g_tc.sol.c, c->Bw, std::max(2, nrhs), n, std::max(2, nrhs)));
@@ -506,14 +529,18 @@ int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n) {
   if (reinterpret_cast<void*>(A) != c->C || ld != c->ld) return RMAT_ESTATE;
   RMAT_CHECK(tc_prepare(c, n, c->nrhs + (c->nrhs & 1)));
   TcCache& g_tc = tc_cache(c);
-  return launch_tc(c, g_tc.upd, k0 + jb, k0 + jb, rest, rest, jb, k0, k0 + jb, 0, k0 + jb, true);
+  return launch_tc<TC_BN>(c, g_tc.upd, k0 + jb, k0 + jb, rest, rest, jb, k0, k0 + jb, 0, k0 + jb,
+                          true);
 }
 
 // Solve update: Bsub[M x nrhs] -= F[rows ay0.., cols k0..k0+jb] * Y, Y^T planes in Ypl.
 int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n) {
   RMAT_CHECK(tc_prepare(c, n, nrhs));
   TcCache& g_tc = tc_cache(c);
-  return launch_tc(c, g_tc.sol, 0, row0, M, nrhs, jb, k0, ay0, 0, 0, false);
+  KTimer kt(c, KT_SOLVE_TC);
+  RMAT_CHECK(launch_tc<128>(c, g_tc.sol, 0, row0, M, nrhs, jb, k0, ay0, 0, 0, false));
+  kt.end();
+  return RMAT_OK;
 }
 
 void tc_release(rmat_ctx c) {

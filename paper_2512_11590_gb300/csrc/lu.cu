@@ -21,6 +21,8 @@
 #include <algorithm>
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "cplx.cuh"
 #include "rmat_internal.h"
 
@@ -133,11 +135,23 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
       best = (T)-1;
       bidx = INT_MAX;
       int bc = -1;
-      for (int q = lane; q < P; q += 32) {
-        T v = ld_cg(cval + par * RMAT_MAX_PANEL_CTAS + q);
-        int ix = ld_cg(ps.cidx + par * RMAT_MAX_PANEL_CTAS + q);
-        if (v > best || (v == best && ix < bidx)) { best = v; bidx = ix; bc = q; }
+      // all candidates requested before any is compared: one L2 round trip
+      constexpr int QPL = RMAT_MAX_PANEL_CTAS / 32;
+      T cv[QPL];
+      int ci[QPL];
+#pragma unroll
+      for (int u = 0; u < QPL; ++u) {
+        const int q = lane + 32 * u;
+        cv[u] = q < P ? ld_cg(cval + par * RMAT_MAX_PANEL_CTAS + q) : (T)-1;
+        ci[u] = q < P ? ld_cg(ps.cidx + par * RMAT_MAX_PANEL_CTAS + q) : INT_MAX;
       }
+#pragma unroll
+      for (int u = 0; u < QPL; ++u)
+        if (cv[u] > best || (cv[u] == best && ci[u] < bidx)) {
+          best = cv[u];
+          bidx = ci[u];
+          bc = lane + 32 * u;
+        }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         T ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -544,40 +558,44 @@ __global__ void identity_blocks_kernel(cplx<T>* __restrict__ D, int JB, size_t t
 //   Y = Dinv * B_k   (B_k = rows k0..k0+JB-1 of B after the block's interchanges,
 //                     gathered through the net source map when one is given),
 // Y written back over B_k and, when Y planes are requested, as TF32 split planes
-// transposed (B operand of the tensor-core block update).  The inverse block is
-// staged in shared memory; one CTA owns 16 right-hand-side columns and all JB
-// rows, so no CTA reads what another writes.
-template <class T, int JB>
-__global__ void __launch_bounds__(256)
-apply_inv_kernel(const cplx<T>* __restrict__ Dinv, int k0, int nbp, cplx<T>* __restrict__ B,
+// transposed (B operand of the tensor-core block update).
+// One cluster of JB/16 CTAs owns 16 right-hand-side columns; CTA s of the cluster
+// gathers permutation slots 32s..32s+31 and computes output rows 16s..16s+15.
+// Every read of B happens before the first cluster barrier and every write after
+// the second, and no two clusters touch the same column, so the in-place update
+// has no race.
+template <int JB>
+__global__ void __cluster_dims__(1, JB / 16, 1) __launch_bounds__(256)
+apply_inv_kernel(const float2* __restrict__ Dinv, int k0, int nbp, float2* __restrict__ B,
                  int ldb, int ncols, const int* __restrict__ prow, const int* __restrict__ psrc,
                  const int* __restrict__ pcnt, float* __restrict__ Yp, size_t yplane) {
-  using C2 = cplx<T>;
-  constexpr int CW = 16;                     // columns per CTA
-  constexpr int RPT = JB / 16;               // output rows per thread
-  constexpr int LDD = JB + 1;
-  extern __shared__ unsigned char smem_raw[];
-  C2* Ds = reinterpret_cast<C2*>(smem_raw);        // [JB][LDD] inverse block
-  C2* vals = Ds + JB * LDD;                        // [2*JB][CW] gathered rows; [JB][CW+1] Y after
-  int* rows = reinterpret_cast<int*>(vals + 2 * JB * (CW + 1));  // [2*JB]
-  int* src = rows + 2 * JB;                                      // [2*JB]
-  const int tid = threadIdx.x;
-  const int cl = tid & (CW - 1), rg = tid >> 4;  // column lane, row group 0..15
+  namespace cg = cooperative_groups;
+  constexpr int CW = 16;          // columns per cluster
+  constexpr int SL = 32;          // permutation slots gathered per CTA (2*JB over JB/16 CTAs)
+  constexpr int LDD = JB + 2;     // 16-byte aligned rows; the two rows a warp reads use different banks
+  constexpr int CPR = JB * 8 / 16;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Ds = reinterpret_cast<float2*>(smem_raw);  // [16][LDD] rows 16s.. of the inverse
+  float2* vloc = Ds + 16 * LDD;                     // [SL][CW] own gathered slots
+  float2* vk = vloc + SL * CW;                      // [JB][CW] permuted B_k (all slots < JB)
+  float2* ys = vk + JB * CW;                        // [16][CW+1] output rows
+  int* rows = reinterpret_cast<int*>(ys + 16 * (CW + 1));  // [2*JB]
+  int* src = rows + 2 * JB;                                // [2*JB]
+  const int tid = threadIdx.x, s = blockIdx.y;
+  const int cl = tid & (CW - 1), qq = tid >> 4;
   const int col = blockIdx.x * CW + cl;
   const bool act = col < ncols;
   const int blk = k0 / nbp;
-  const C2* D = Dinv + (size_t)blk * JB * JB;
-  for (int e0 = tid; e0 < JB * JB; e0 += 256 * 8) {
-    C2 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (e0 + u * 256 < JB * JB) v[u] = D[e0 + u * 256];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * 256;
-      if (e < JB * JB) Ds[(e / JB) * LDD + e % JB] = v[u];
-    }
+  const float2* D = Dinv + ((size_t)blk * JB + 16 * s) * JB;
+  for (int q = tid; q < 16 * CPR; q += 256) {
+    const int r = q / CPR, h = q - r * CPR;
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(
+        reinterpret_cast<unsigned char*>(Ds + (size_t)r * LDD) + 16 * h);
+    const unsigned char* sp = reinterpret_cast<const unsigned char*>(D + (size_t)r * JB) + 16 * h;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(sp) : "memory");
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
   int cnt = JB;
   if (prow) {
     cnt = pcnt[blk];
@@ -592,53 +610,55 @@ apply_inv_kernel(const cplx<T>* __restrict__ Dinv, int k0, int nbp, cplx<T>* __r
     }
   }
   __syncthreads();
-  // permuted gather: slot q receives the original content of slot src[q]
-  for (int q = rg; q < cnt; q += 16)
-    vals[q * CW + cl] = act ? B[(size_t)rows[src[q]] * ldb + col] : mkc<T>(0, 0);
-  __syncthreads();
-  if (prow)
-    for (int q = JB + rg; q < cnt; q += 16)
-      if (act) B[(size_t)rows[q] * ldb + col] = vals[q * CW + cl];
-  C2 acc[RPT];
+  // gather: slot q receives the original content of slot src[q]
 #pragma unroll
-  for (int r = 0; r < RPT; ++r) acc[r] = mkc<T>(0, 0);
-#pragma unroll 4
-  for (int t = 0; t < JB; ++t) {
-    const C2 bv = vals[t * CW + cl];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) cadd_mul<T>(acc[r], Ds[(rg + 16 * r) * LDD + t], bv);
+  for (int u = 0; u < SL / 16; ++u) {
+    const int q = SL * s + qq + 16 * u;
+    if (q < cnt)
+      vloc[(qq + 16 * u) * CW + cl] = act ? B[(size_t)rows[src[q]] * ldb + col] : make_float2(0.f, 0.f);
   }
-  __syncthreads();
-  C2* ys = vals;  // [JB][CW+1]
-#pragma unroll
-  for (int r = 0; r < RPT; ++r) {
-    const int i = rg + 16 * r;
-    ys[i * (CW + 1) + cl] = acc[r];
-    if (act) B[(size_t)(k0 + i) * ldb + col] = acc[r];
+  cluster.sync();  // every gather (read of B) of the cluster is done
+  for (int e = tid; e < JB * CW; e += 256) {
+    const int t = e / CW;
+    const float2* peer = cluster.map_shared_rank(vloc, t / SL);
+    vk[e] = peer[(t % SL) * CW + (e % CW)];
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  cluster.sync();  // peers may now overwrite B and exit
+  if (prow && act) {
+#pragma unroll
+    for (int u = 0; u < SL / 16; ++u) {
+      const int q = SL * s + qq + 16 * u;
+      if (q >= JB && q < cnt) B[(size_t)rows[q] * ldb + col] = vloc[(qq + 16 * u) * CW + cl];
+    }
+  }
+  const int ri = qq;  // output row 16s + ri, column cl
+  float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 8
+  for (int t = 0; t < JB; ++t) cadd_mul<float>(acc, Ds[ri * LDD + t], vk[t * CW + cl]);
+  const int i = 16 * s + ri;
+  if (act) B[(size_t)(k0 + i) * ldb + col] = acc;
   if (Yp) {
+    ys[ri * (CW + 1) + cl] = acc;
     __syncthreads();
-    // transposed planes: plane row = column, K index = i (coalesced over i)
-    for (int cc = tid >> 5; cc < CW; cc += 8) {
-      const int gc = blockIdx.x * CW + cc;
-      if (gc >= ncols) continue;
-      for (int i = tid & 31; i < JB; i += 32) {
-        const C2 z = ys[i * (CW + 1) + cc];
-        const float re = (float)z.x, im = (float)z.y;
-        const float rh = tf32_round(re), ih = tf32_round(im);
-        const size_t o = (size_t)gc * RMAT_MAX_NB + i;
-        Yp[o] = rh;
-        Yp[yplane + o] = re - rh;
-        Yp[2 * yplane + o] = ih;
-        Yp[3 * yplane + o] = im - ih;
-      }
+    // transposed planes: plane row = column, K index = i (16 consecutive i per column)
+    const int cc = tid >> 4, ii = tid & 15;
+    const int gc = blockIdx.x * CW + cc;
+    if (gc < ncols) {
+      const float2 z = ys[ii * (CW + 1) + cc];
+      const float rh = tf32_round(z.x), ih = tf32_round(z.y);
+      const size_t o = (size_t)gc * RMAT_MAX_NB + 16 * s + ii;
+      Yp[o] = rh;
+      Yp[yplane + o] = z.x - rh;
+      Yp[2 * yplane + o] = ih;
+      Yp[3 * yplane + o] = z.y - ih;
     }
   }
 }
 
-template <class T, int JB>
+template <int JB>
 size_t apply_inv_smem() {
-  return (size_t)JB * (JB + 1) * sizeof(cplx<T>) + (size_t)2 * JB * 17 * sizeof(cplx<T>) +
+  return (size_t)(16 * (JB + 2) + 32 * 16 + JB * 16 + 16 * 17) * sizeof(float2) +
          (size_t)4 * JB * sizeof(int);
 }
 
@@ -815,7 +835,9 @@ int launch_panel(rmat_ctx c, cplx<T>* A, int ld, int k0, int n, int jb, int* ipi
   int* stat = c->dstat;
   void* args[] = {&A, &ld, (void*)&k0, (void*)&n, (void*)&jb, &ipiv, &stat, &ps, (void*)&rpc, &spin};
   const void* kern = in_smem ? (const void*)panel_kernel<T, true> : (const void*)panel_kernel<T, false>;
+  KTimer kt(c, KT_PANEL);
   RMAT_CU(cudaLaunchCooperativeKernel(kern, dim3(P), dim3(PANEL_THREADS), args, smem, c->stream));
+  kt.end();
   c->launches++;
   return RMAT_OK;
 }
@@ -917,17 +939,19 @@ template <int JB>
 int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb, int ncols,
                      const LUPerm* pm, float* Yp) {
   static bool attr = false;
-  const size_t smem = apply_inv_smem<float, JB>();
+  const size_t smem = apply_inv_smem<JB>();
   if (!attr) {
-    RMAT_CU(cudaFuncSetAttribute(apply_inv_kernel<float, JB>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RMAT_CU(cudaFuncSetAttribute(apply_inv_kernel<JB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
     attr = true;
   }
   const size_t total = (size_t)JB * JB * c->inv_blocks;
   const float2* D = reinterpret_cast<const float2*>(c->Dinv) + (upper ? total : 0);
-  apply_inv_kernel<float, JB><<<ceil_div(ncols, 16), 256, smem, c->stream>>>(
+  KTimer kt(c, KT_APPLY_INV);
+  apply_inv_kernel<JB><<<dim3(ceil_div(ncols, 16), JB / 16), 256, smem, c->stream>>>(
       D, k0, nb, B, ldb, ncols, pm ? pm->rows : nullptr, pm ? pm->src : nullptr,
       pm ? pm->cnt : nullptr, Yp, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB);
+  kt.end();
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;

@@ -259,6 +259,7 @@ int grid_for(rmat_ctx c, size_t total) {
 int launch_residual(rmat_ctx c, double*) {
   const int N = c->N, nrhs = c->nrhs;
   const size_t total = (size_t)N * nrhs;
+  KTimer kt(c, KT_RESID);
   RMAT_CU(cudaMemsetAsync(c->red, 0, sizeof(unsigned long long), c->stream));
   if (c->kind == 1) {
     dim3 gk(ceil_div(nrhs, 32), c->nch);
@@ -281,6 +282,7 @@ int launch_residual(rmat_ctx c, double*) {
         c->Rres, total, nrhs, D, reinterpret_cast<float2*>(c->Bw), c->red);
   c->launches++;
   RMAT_CU(cudaGetLastError());
+  kt.end();
   return RMAT_OK;
 }
 

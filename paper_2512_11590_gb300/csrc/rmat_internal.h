@@ -115,6 +115,9 @@ struct rmat_ctx_s {
   cudaEvent_t stage_ev[5][2] = {};
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tu_events;
+  // per kernel class (KT_*): event pairs (timing on) and launch counts
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> kt_events[4];
+  long long kt_launches[4] = {0, 0, 0, 0};
   size_t ev_next = 0;
 };
 
@@ -186,6 +189,18 @@ void rmat_note_cuda_error(int err, const char* file, int line);
     int s__ = (__VA_ARGS__);                        \
     if (s__ != RMAT_OK) return s__;                 \
   } while (0)
+
+// Kernel classes timed separately when timing is on (rmat_get_stats).
+enum { KT_PANEL = 0, KT_APPLY_INV = 1, KT_SOLVE_TC = 2, KT_RESID = 3 };
+
+// Brackets the launches of one kernel class with events on the context's stream.
+struct KTimer {
+  struct rmat_ctx_s* c;
+  int k;
+  cudaEvent_t e0 = nullptr;
+  KTimer(struct rmat_ctx_s* c_, int k_);
+  void end();
+};
 
 static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 static inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
