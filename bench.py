@@ -37,6 +37,9 @@ sys.path.insert(0, ROOT)
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 TF32_PER_BF16 = 0.5          # nominal dense tf32 : bf16 tensor rate on GB300 (1.1 : 2.25 PF)
+DTYPES = {1: "c64 factor with 3xTF32 tensor updates / f64 refinement",
+          2: "c64 factor with FP32 CUDA-core updates / f64 refinement",
+          3: "c64 factor with 3xFP16 (scaled split) tensor updates / f64 refinement"}
 
 
 def peaks():
@@ -242,7 +245,7 @@ def reference_main(args):
     return 0
 
 
-def profile_step(nch):
+def profile_step(nch, precision, warm=True):
     """Launch sequence for ncu: the warm-up step uses the SIMT precision, so the
     first tensor-core launch of the run is the first trailing update at N = nch*100."""
     import torch
@@ -250,10 +253,11 @@ def profile_step(nch):
     import cc_problems as cp
     import paper_2512_11590_gb300 as g
     torch.cuda.set_device(0)
-    warm = Runner(cp.config3(16), g.RMAT_C64_SIMT_IR, 0)
-    warm.step()
-    warm.close()
-    run = Runner(cp.config3(nch), g.RMAT_C64_3XTF32_IR, 0)
+    if warm:
+        w = Runner(cp.config3(16), g.RMAT_C64_SIMT_IR, 0)
+        w.step()
+        w.close()
+    run = Runner(cp.config3(nch), precision, 0)
     run.step()
     torch.cuda.synchronize()
     print("profile step", nch, run.last)
@@ -271,7 +275,8 @@ def batch_main(args):
     import paper_2512_11590_gb300 as g
     torch.cuda.set_device(0)
     probs = cp.batch_problems(args.batch)
-    prec = g.RMAT_C64_3XTF32_IR if args.precision == "tf32" else g.RMAT_C64_SIMT_IR
+    prec = {"tf32": g.RMAT_C64_3XTF32_IR, "f16": g.RMAT_C64_3XF16_IR,
+            "simt": g.RMAT_C64_SIMT_IR}[args.precision]
     stream = torch.cuda.Stream()                 # capturable stream for the batch's CUDA graph
     ctx = g.rmat_create(0, stream.cuda_stream)
     Vs, structs, keep = [], [], []
@@ -331,7 +336,7 @@ def batch_main(args):
             "value": len(probs) / (ms * 1e-3), "unit": "systems/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "c64+3xtf32 factor / f64 refinement" if prec == 1 else "c64 simt / f64",
+            "dtype": DTYPES[prec],
             "data": "synthetic",
             "config": {"workload": "config4 batch_problems(%d) seed 11593, N %d..%d, median %d"
                        % (len(probs), Ns.min(), Ns.max(), int(np.median(Ns))),
@@ -352,7 +357,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32", choices=["tf32", "simt"])
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "f16", "simt"])
     ap.add_argument("--small", action="store_true", help="N=1600 instead of N=25600")
     ap.add_argument("--no-fp64", action="store_true", help="skip the complex128 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -360,6 +365,7 @@ def main():
                     help="for ncu: one untimed SIMT warm-up step at N=1600, then one FP32+IR "
                          "tensor step at N = nch*100; no timing, no JSON")
     ap.add_argument("--nch", type=int, default=256, help="channels of the --profile-step system")
+    ap.add_argument("--no-warm", action="store_true", help="--profile-step without the warm-up step")
     ap.add_argument("--batch", type=int, default=0,
                     help="time the batch driver on this many config-4 systems instead")
     ap.add_argument("--batch-refine", type=int, default=10,
@@ -371,7 +377,10 @@ def main():
     if args.impl == "reference":
         return reference_main(args)
     if args.profile_step:
-        return profile_step(args.nch)
+        import paper_2512_11590_gb300 as g
+        return profile_step(args.nch, {"tf32": g.RMAT_C64_3XTF32_IR, "f16": g.RMAT_C64_3XF16_IR,
+                                       "simt": g.RMAT_C64_SIMT_IR}[args.precision],
+                            warm=not args.no_warm)
     if args.batch:
         return batch_main(args)
 
@@ -392,7 +401,8 @@ def main():
             dist.barrier()
 
     p, desc = workload(args)
-    prec = g.RMAT_C64_3XTF32_IR if args.precision == "tf32" else g.RMAT_C64_SIMT_IR
+    prec = {"tf32": g.RMAT_C64_3XTF32_IR, "f16": g.RMAT_C64_3XF16_IR,
+            "simt": g.RMAT_C64_SIMT_IR}[args.precision]
     run = Runner(p, prec, local)
     with ClockSampler(local) as clk:
         ms, stats, launches = time_steps(run, args.steps, args.warmup, sync_all)
@@ -433,6 +443,11 @@ def main():
         peak = pk["bf16_tflops_sustained"] * TF32_PER_BF16 / 3.0
         bound, unit, pname = "tensor", "TFLOP/s", ("bf16 sustained (%s) x 0.5 (tf32/bf16 nominal) / 3 "
                                                     "(tf32 split products per fp32 product)" % src)
+    elif prec == g.RMAT_C64_3XF16_IR:
+        # 4 real GEMMs x 3 fp16 split products; fp16 and bf16 share the tensor rate
+        peak = pk["bf16_tflops_sustained"] / 3.0
+        bound, unit, pname = "tensor", "TFLOP/s", ("bf16 sustained (%s) / 3 (fp16 split products "
+                                                    "per fp32 product; fp16 rate = bf16 rate)" % src)
     else:
         peak = 152 * 128 * 2 * 2070e6 / 1e12
         bound, unit, pname = "alu", "TFLOP/s", "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"
@@ -453,7 +468,7 @@ def main():
         "metric": "N=25600 complex solve time & TFLOP/s: FP32+IR vs FP64 at equal U error",
         "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64+3xtf32 factor / f64 refinement" if prec == 1 else "c64 simt / f64",
+        "vs_baseline": None, "dtype": DTYPES[prec],
         "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "nrhs": p.nch,
                    "refinement": ir, "l2": "inputs larger than L2 (C is %.1f GB)" % (p.N * p.N * 8 / 1e9),

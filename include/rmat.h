@@ -60,6 +60,11 @@ extern "C" {
 #define RMAT_C64_3XTF32_IR   1
 /* complex64 matrix and LU with FP32 CUDA-core trailing updates; FP64 refinement. */
 #define RMAT_C64_SIMT_IR     2
+/* complex64 matrix and LU; tensor-core updates as three FP16 products of a hi/lo
+ * split (the same 22-bit operand precision as the TF32 split at twice the tensor
+ * rate), with power-of-two scaling per U block and per right-hand-side column so
+ * every operand stays in FP16 range; FP32 accumulation; FP64 residual refinement. */
+#define RMAT_C64_3XF16_IR    3
 
 /* ---- tunable parameters (rmat_set_param) -------------------------------- */
 #define RMAT_PARAM_NB          1  /* LU block width (multiple of 32; 0 = tuned) */
@@ -85,7 +90,7 @@ typedef struct {
   double bloch_B;        /* Bloch boundary constant B of L(B) (0 in the paper) */
   const int* l;          /* host [nch]: orbital momentum of each channel, >= 0 */
   const double* thresh;  /* host [nch]: channel threshold energies (MeV)       */
-  int precision;         /* RMAT_C128, RMAT_C64_3XTF32_IR or RMAT_C64_SIMT_IR  */
+  int precision;         /* one of the RMAT_C128 / RMAT_C64_* precisions above */
 } rmat_problem;
 
 /* Create a context bound to CUDA device `device` and stream `stream` (a

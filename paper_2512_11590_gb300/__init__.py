@@ -29,6 +29,7 @@ RMAT_ENOCONV = 2
 RMAT_C128 = 0
 RMAT_C64_3XTF32_IR = 1
 RMAT_C64_SIMT_IR = 2
+RMAT_C64_3XF16_IR = 3
 
 RMAT_PARAM_NB = 1
 RMAT_PARAM_PANEL_CTAS = 2

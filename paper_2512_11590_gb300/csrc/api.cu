@@ -20,7 +20,8 @@ int default_nb(int precision, int N) {
 int clamp_nb(int precision, int nb) { return std::min(nb, precision == RMAT_C128 ? 64 : 128); }
 
 bool valid_precision(int p) {
-  return p == RMAT_C128 || p == RMAT_C64_3XTF32_IR || p == RMAT_C64_SIMT_IR;
+  return p == RMAT_C128 || p == RMAT_C64_3XTF32_IR || p == RMAT_C64_SIMT_IR ||
+         p == RMAT_C64_3XF16_IR;
 }
 
 int begin(rmat_ctx c) {
@@ -54,7 +55,8 @@ double read_red(rmat_ctx c) {
 int ctx_reserve(rmat_ctx c, bool dense) {
   const size_t N = c->N, ld = c->ld, nrhs = c->nrhs;
   const size_t eb = elem_bytes(c->precision);
-  const bool tensor = c->precision == RMAT_C64_3XTF32_IR;
+  const bool tensor = rmat_tensor_prec(c->precision);
+  const size_t pe = rmat_plane_esz(c->precision);
   size_t need = 0;
   auto want = [&](size_t cap, size_t bytes) { need += bytes > cap ? bytes - cap : 0; };
   want(c->C_cap, N * ld * eb);
@@ -62,9 +64,9 @@ int ctx_reserve(rmat_ctx c, bool dense) {
   want(c->Rres_cap, N * nrhs * 16);
   want(c->Bw_cap, N * nrhs * eb);
   if (tensor) {
-    want(c->Fpl_cap, 4 * N * ld * 4);
-    want(c->Bpl_cap, 4 * N * RMAT_MAX_NB * 4);
-    want(c->Ypl_cap, (size_t)4 * RMAT_YPL_ROWS * RMAT_MAX_NB * 4);
+    want(c->Fpl_cap, 4 * N * ld * pe);
+    want(c->Bpl_cap, 4 * N * RMAT_MAX_NB * pe);
+    want(c->Ypl_cap, (size_t)4 * RMAT_YPL_ROWS * RMAT_MAX_NB * pe);
   }
   if (dense) {
     want(c->A64_cap, N * N * 16);
@@ -80,9 +82,13 @@ int ctx_reserve(rmat_ctx c, bool dense) {
   RMAT_CHECK(rmat_grow(c, (void**)&c->ipiv, &c->ipiv_cap, N * sizeof(int)));
   RMAT_CHECK(perm_reserve(c, c->perm_main, (int)N, c->nb));
   if (tensor) {
-    RMAT_CHECK(rmat_grow(c, (void**)&c->Fpl, &c->Fpl_cap, 4 * N * ld * 4));
-    RMAT_CHECK(rmat_grow(c, (void**)&c->Bpl, &c->Bpl_cap, 4 * N * RMAT_MAX_NB * 4));
-    RMAT_CHECK(rmat_grow(c, (void**)&c->Ypl, &c->Ypl_cap, (size_t)4 * RMAT_YPL_ROWS * RMAT_MAX_NB * 4));
+    RMAT_CHECK(rmat_grow(c, &c->Fpl, &c->Fpl_cap, 4 * N * ld * pe));
+    RMAT_CHECK(rmat_grow(c, &c->Bpl, &c->Bpl_cap, 4 * N * RMAT_MAX_NB * pe));
+    RMAT_CHECK(rmat_grow(c, &c->Ypl, &c->Ypl_cap, (size_t)4 * RMAT_YPL_ROWS * RMAT_MAX_NB * pe));
+    const size_t nblk = N / 32 + 2;
+    RMAT_CHECK(rmat_grow(c, (void**)&c->umax, &c->umax_cap, nblk * sizeof(unsigned)));
+    RMAT_CHECK(rmat_grow(c, (void**)&c->uscale, &c->uscale_cap, nblk * sizeof(float)));
+    RMAT_CHECK(rmat_grow(c, (void**)&c->ycs, &c->ycs_cap, (size_t)RMAT_YPL_ROWS * sizeof(float)));
   }
   if (dense) {
     RMAT_CHECK(rmat_grow(c, (void**)&c->A64, &c->A64_cap, N * N * 16));
@@ -271,7 +277,8 @@ int rmat_destroy(rmat_ctx c) {
   void* bufs[] = {c->C,    c->A64,  c->B64, c->ipiv, c->Kmat, c->T0,  c->rmesh,
                   c->fa,   c->l_d,  c->th_d, c->Wpt, c->X,    c->Rres, c->Bw,
                   c->Fpl,  c->Bpl, c->Ypl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
-                  c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows, c->Dinv};
+                  c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows, c->Dinv,
+                  c->umax, c->uscale, c->ycs};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->hstat) cudaFreeHost(c->hstat);
@@ -417,7 +424,7 @@ int rmat_factor(rmat_ctx c, int* info) {
   RMAT_CU(cudaMemsetAsync(c->dstat, 0, ST_COUNT * sizeof(int), c->stream));
   cudaEvent_t e0, e1;
   record_stage(c, &e0);
-  const bool tensor = c->precision == RMAT_C64_3XTF32_IR;
+  const bool tensor = rmat_tensor_prec(c->precision);
   int st;
   if (c->precision == RMAT_C128)
     st = lu_factor_dev<double>(c, c->C, c->N, c->ld, c->ipiv, c->nb, false, c->perm_main);
@@ -443,7 +450,7 @@ static int solve_factors(rmat_ctx c) {
     return lu_solve_dev<double>(c, c->C, c->N, c->ld, c->perm_main, c->nb, c->Bw, c->nrhs,
                                 c->nrhs);
   return lu_solve_dev<float>(c, c->C, c->N, c->ld, c->perm_main, c->nb, c->Bw, c->nrhs, c->nrhs,
-                             c->precision == RMAT_C64_3XTF32_IR);
+                             rmat_tensor_prec(c->precision));
 }
 
 }  // extern "C"

@@ -125,7 +125,7 @@ int enqueue_system(rmat_batch b, int s, void* U) {
   RMAT_CHECK(launch_assemble(c, y.V, y.E));
   RMAT_CHECK(launch_point_coupling(c, y.V, y.E));
   RMAT_CHECK(lu_factor_dev<T>(c, c->C, c->N, c->ld, c->ipiv, c->nb,
-                              b->precision == RMAT_C64_3XTF32_IR, c->perm_main));
+                              rmat_tensor_prec(b->precision), c->perm_main));
   RMAT_CHECK(enqueue_solve_refine(c, b->max_refine, b->tol, b->ir + s));
   RMAT_CHECK(launch_collision(c, nullptr, reinterpret_cast<double2*>(U), y.nopen));
   RMAT_CU(cudaMemcpyAsync(b->st_dev + (size_t)s * ST_COUNT, c->dstat, ST_COUNT * sizeof(int),
@@ -322,7 +322,9 @@ int rmat_batch_create(rmat_ctx ctx, int nsys, const rmat_problem* probs, const d
         !p.thresh || p.precision != prec || (long long)p.nch * p.nlag > 200000 ||
         !std::isfinite(E[s]) || !V_dev[s])
       return -3;
-    if (prec != RMAT_C128 && prec != RMAT_C64_3XTF32_IR && prec != RMAT_C64_SIMT_IR) return -3;
+    if (prec != RMAT_C128 && prec != RMAT_C64_3XTF32_IR && prec != RMAT_C64_SIMT_IR &&
+        prec != RMAT_C64_3XF16_IR)
+      return -3;
   }
   rmat_batch b = new (std::nothrow) rmat_batch_s();
   if (!b) return RMAT_ENOMEM;

@@ -110,22 +110,30 @@ __device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
   d |= (uint64_t)6 << 61;                   // layout: SWIZZLE_32B
   return d;
 }
-// kind::tf32 instruction descriptor: D f32, A/B tf32, K-major, N = BN, M = 128.
-template <int BN>
-__host__ __device__ constexpr uint32_t idesc_tf32(bool negA) {
-  return (1u << 4)               // D format f32
-         | (2u << 7)             // A format tf32
-         | (2u << 10)            // B format tf32
+// Instruction descriptor: D f32, A/B K-major, N = BN, M = 128; operand format
+// TF32 (code 2, kind::tf32) or F16 (code 0, kind::f16).
+template <int BN, int KIND>
+__host__ __device__ constexpr uint32_t idesc_mma(bool negA) {
+  return (1u << 4)                                 // D format f32
+         | ((KIND == 0 ? 2u : 0u) << 7)            // A format
+         | ((KIND == 0 ? 2u : 0u) << 10)           // B format
          | ((negA ? 1u : 0u) << 13)
          | ((uint32_t)(BN >> 3) << 17)
          | ((uint32_t)(TC_BM >> 4) << 24);
 }
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+template <int KIND>
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                          uint32_t accumulate) {
+  if constexpr (KIND == 0)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -198,11 +206,21 @@ __device__ __forceinline__ void product(int p, int& qa, int& qb, int& acc, int& 
   neg = (acc == 0 && part == 1);
 }
 
-template <int BN>
+// Epilogue scales (power-of-two factors of the FP16 planes; all null for TF32):
+// out[r][c] -= acc[r][c] * rowscale[(rowA0 + r) / rs_div] * colscale[rowB0 + c] * (*cscal).
+struct TcScales {
+  const float* rowscale;
+  int rs_div;
+  const float* colscale;
+  const float* cscal;
+};
+
+template <int BN, int KIND>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, int Nn, int K,
-                 int ax0, int rowA0, int bx0, int rowB0, int* __restrict__ err) {
+                 int ax0, int rowA0, int bx0, int rowB0, TcScales sc, int* __restrict__ err) {
   using Cfg = TcCfg<BN>;
+  constexpr int KSTEP = KIND == 0 ? 8 : 16;  // K elements per 32-byte operand row
   constexpr uint32_t B_PLANE_BYTES = Cfg::B_PLANE, STAGE_BYTES = Cfg::STAGE;
   constexpr int NBUF = Cfg::NBUF;
   extern __shared__ unsigned char smem_raw[];
@@ -220,7 +238,7 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
   const int mt = (M + TC_BM - 1) / TC_BM;
   const int nt = (Nn + BN - 1) / BN;
   const int ntiles = mt * nt;
-  const int ksteps = K / TC_BK;
+  const int ksteps = K / KSTEP;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -260,10 +278,10 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
           const uint32_t st = smem_u32(stages + s * STAGE_BYTES);
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            tma_load_2d(st + q * A_PLANE_BYTES, &maps.a[q], ax0 + ks * TC_BK, rowA0 + m0, full);
+            tma_load_2d(st + q * A_PLANE_BYTES, &maps.a[q], ax0 + ks * KSTEP, rowA0 + m0, full);
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            tma_load_2d(st + 4 * A_PLANE_BYTES + q * B_PLANE_BYTES, &maps.b[q], bx0 + ks * TC_BK,
+            tma_load_2d(st + 4 * A_PLANE_BYTES + q * B_PLANE_BYTES, &maps.b[q], bx0 + ks * KSTEP,
                         rowB0 + n0, full);
         }
       }
@@ -283,7 +301,7 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
     if (lane == 0) {
       uint32_t it = 0, tcount = 0;
       bool ok = true;
-      uint32_t idesc[2] = {idesc_tf32<BN>(false), idesc_tf32<BN>(true)};
+      uint32_t idesc[2] = {idesc_mma<BN, KIND>(false), idesc_mma<BN, KIND>(true)};
       uint32_t buf = 0, use = 0;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tcount) {
         buf = tcount % NBUF;
@@ -305,7 +323,7 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
             const uint64_t ad = sdesc_sw32(st + qa * A_PLANE_BYTES);
             const uint64_t bd = sdesc_sw32(st + 4 * A_PLANE_BYTES + qb * B_PLANE_BYTES);
             const uint32_t first = (ks == 0) && (p == 0 || p == 6);
-            mma_tf32(tmem + buf * 2 * BN + acc * BN, ad, bd, idesc[neg], first ? 0u : 1u);
+            mma_issue<KIND>(tmem + buf * 2 * BN + acc * BN, ad, bd, idesc[neg], first ? 0u : 1u);
           }
           mma_commit(smem_u32(&bars[4 + s]));  // frees the stage once these MMAs have read it
         }
@@ -348,6 +366,8 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
       if (*epi_abort) break;
       fence_after();
       const bool rowvalid = (m0 + row) < M;
+      float rsc = sc.cscal ? *sc.cscal : 1.f;
+      if (sc.rowscale && rowvalid) rsc *= sc.rowscale[(rowA0 + m0 + row) / sc.rs_div];
 #pragma unroll 1
       for (int ch = 0; ch < BN / 16; ++ch, ++chunk) {
         float re[16], im[16];
@@ -360,21 +380,28 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(&bars[9 + 2 * buf]));
         }
-        unsigned char* buf = staging + (chunk & 1) * STAGING_BYTES;
+        unsigned char* sbuf = staging + (chunk & 1) * STAGING_BYTES;
         if (leader) bulk_wait_read1();       // the reduce that used this buffer has read it
         epi_bar();
-        float4* rowp = reinterpret_cast<float4*>(buf + row * 128);
+        float4* rowp = reinterpret_cast<float4*>(sbuf + row * 128);
+        float cs[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int col = n0 + ch * 16 + k;
+          cs[k] = -rsc * ((sc.colscale && col < Nn) ? sc.colscale[rowB0 + col] : 1.f);
+        }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const float4 v = rowvalid ? make_float4(-re[2 * k], -im[2 * k], -re[2 * k + 1],
-                                                  -im[2 * k + 1])
+          const float4 v = rowvalid ? make_float4(cs[2 * k] * re[2 * k], cs[2 * k] * im[2 * k],
+                                                  cs[2 * k + 1] * re[2 * k + 1],
+                                                  cs[2 * k + 1] * im[2 * k + 1])
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
           rowp[k ^ (row & 7)] = v;
         }
         fence_proxy_async_smem();
         epi_bar();
         if (leader) {
-          tma_reduce_add_2d(&maps.c, smem_u32(buf), 2 * (cx0 + n0 + ch * 16), cy0 + m0);
+          tma_reduce_add_2d(&maps.c, smem_u32(sbuf), 2 * (cx0 + n0 + ch * 16), cy0 + m0);
           bulk_commit();
         }
       }
@@ -422,33 +449,39 @@ int make_out_map(CUtensorMap* m, void* base, int cols, int rows, int ld_complex)
   return r == CUDA_SUCCESS ? RMAT_OK : RMAT_ECUDA;
 }
 
-int make_plane_map(CUtensorMap* m, float* base, int cols, int rows, int row_stride, int box_rows) {
+// One operand plane, K-major [rows][row_stride] of fmt 0 (fp32 words holding TF32)
+// or fmt 1 (fp16); boxes are 32 bytes of K (8 or 16 elements) by box_rows rows.
+int make_plane_map(CUtensorMap* m, void* base, int fmt, int cols, int rows, int row_stride,
+                   int box_rows) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return RMAT_ECUDA;
+  const size_t esz = fmt == 1 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)row_stride * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)row_stride * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(32 / esz), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(m, fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                   2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? RMAT_OK : RMAT_ECUDA;
 }
 
 // Tensor maps of the three operand sources, rebuilt when a buffer or size changes:
-//   F  full-size split factor planes, row-major [n][ldf]  (A operand)
+//   F  full-size split factor planes, row-major [n][ldf]  (A operand; columns
+//      limited to n, so K padding beyond the matrix reads zeros)
 //   B  transposed U12 planes [n][256]                      (B operand of the factor update)
 //   Y  transposed right-hand-side block planes [nrhs][256] (B operand of the solve updates)
 struct TcCache {
-  const float* f = nullptr;
-  const float* b = nullptr;
-  const float* y = nullptr;
+  const void* f = nullptr;
+  const void* b = nullptr;
+  const void* y = nullptr;
   const void* cmat = nullptr;
   const void* bw = nullptr;
-  int n = -1, ldf = -1, nrhs = -1;
+  int n = -1, ldf = -1, nrhs = -1, fmt = -1;
   TcMaps upd, sol;  // trailing update (BN = 256), solve update (BN = 128)
 };
-bool g_tc_attr[2] = {false, false};
+bool g_tc_attr[2][2] = {{false, false}, {false, false}};
 
 // The cache lives with its context (contexts may run concurrently on separate streams).
 TcCache& tc_cache(rmat_ctx c) {
@@ -456,16 +489,17 @@ TcCache& tc_cache(rmat_ctx c) {
   return *reinterpret_cast<TcCache*>(c->tc);
 }
 
-template <int BN>
-int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, int K, int ax0,
-              int ay0, int bx0, int by0, bool count_as_update) {
+template <int BN, int KIND>
+int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, int K, int ax0,
+                int ay0, int bx0, int by0, const TcScales& sc, bool count_as_update) {
+  constexpr int KSTEP = KIND == 0 ? 8 : 16;
   if (M <= 0 || Nn <= 0 || K <= 0) return RMAT_OK;
-  if (K % TC_BK || ax0 % TC_BK || bx0 % TC_BK) return RMAT_ESTATE;
+  if (K % KSTEP || ax0 % KSTEP || bx0 % KSTEP) return RMAT_ESTATE;
   constexpr size_t TC_SMEM = TcCfg<BN>::SMEM;
-  if (!g_tc_attr[BN == 128]) {
-    RMAT_CU(cudaFuncSetAttribute(tc_update_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)TC_SMEM));
-    g_tc_attr[BN == 128] = true;
+  if (!g_tc_attr[BN == 128][KIND]) {
+    RMAT_CU(cudaFuncSetAttribute(tc_update_kernel<BN, KIND>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    g_tc_attr[BN == 128][KIND] = true;
   }
   const int tiles = ceil_div(M, TC_BM) * ceil_div(Nn, BN);
   const int grid = std::min(tiles, c->sm_count);
@@ -475,8 +509,8 @@ int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, i
     e1 = rmat_event(c);
     RMAT_CU(cudaEventRecord(e0, c->stream));
   }
-  tc_update_kernel<BN><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(
-      maps, cx0, cy0, M, Nn, K, ax0, ay0, bx0, by0, c->dstat + ST_TIMEOUT);
+  tc_update_kernel<BN, KIND><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(
+      maps, cx0, cy0, M, Nn, K, ax0, ay0, bx0, by0, sc, c->dstat + ST_TIMEOUT);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   if (count_as_update) {
@@ -490,24 +524,40 @@ int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, i
   return RMAT_OK;
 }
 
+template <int BN>
+int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, int K, int ax0,
+              int ay0, int bx0, int by0, const TcScales& sc, bool count_as_update) {
+  // K beyond the block reads zeros: F columns past n are outside the tensor map and
+  // the Y / B planes are zero-filled up to a multiple of 32
+  if (rmat_plane_fmt(c->precision) == 1)
+    return launch_tc_k<BN, 1>(c, maps, cx0, cy0, M, Nn, round_up(K, 16), ax0, ay0, bx0, by0, sc,
+                              count_as_update);
+  return launch_tc_k<BN, 0>(c, maps, cx0, cy0, M, Nn, round_up(K, 8), ax0, ay0, bx0, by0, sc,
+                            count_as_update);
+}
+
 }  // namespace
 
 int tc_prepare(rmat_ctx c, int n, int nrhs) {
   TcCache& g_tc = tc_cache(c);
-  const int ldf = c->ld;
+  const int ldf = c->ld, fmt = rmat_plane_fmt(c->precision);
   if (g_tc.f == c->Fpl && g_tc.b == c->Bpl && g_tc.y == c->Ypl && g_tc.cmat == c->C &&
-      g_tc.bw == c->Bw && g_tc.n == n && g_tc.ldf == ldf && g_tc.nrhs == nrhs)
+      g_tc.bw == c->Bw && g_tc.n == n && g_tc.ldf == ldf && g_tc.nrhs == nrhs && g_tc.fmt == fmt)
     return RMAT_OK;
   if (nrhs % 2) return RMAT_ESTATE;
-  const size_t fplane = (size_t)n * ldf, bplane = (size_t)n * RMAT_MAX_NB,
-               yplane = (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB;
+  const size_t esz = rmat_plane_esz(c->precision);
+  const size_t fplane = (size_t)n * ldf * esz, bplane = (size_t)n * RMAT_MAX_NB * esz,
+               yplane = (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB * esz;
+  char* F = reinterpret_cast<char*>(c->Fpl);
+  char* Bp = reinterpret_cast<char*>(c->Bpl);
+  char* Y = reinterpret_cast<char*>(c->Ypl);
   for (int q = 0; q < 4; ++q) {
-    RMAT_CHECK(make_plane_map(&g_tc.upd.a[q], c->Fpl + q * fplane, ldf, n, ldf, TC_BM));
-    RMAT_CHECK(make_plane_map(&g_tc.upd.b[q], c->Bpl + q * bplane, RMAT_MAX_NB, n, RMAT_MAX_NB,
+    RMAT_CHECK(make_plane_map(&g_tc.upd.a[q], F + q * fplane, fmt, n, n, ldf, TC_BM));
+    RMAT_CHECK(make_plane_map(&g_tc.upd.b[q], Bp + q * bplane, fmt, RMAT_MAX_NB, n, RMAT_MAX_NB,
                               TC_BN));
     g_tc.sol.a[q] = g_tc.upd.a[q];
-    RMAT_CHECK(make_plane_map(&g_tc.sol.b[q], c->Ypl + q * yplane, RMAT_MAX_NB,
-                              std::max(1, nrhs), RMAT_MAX_NB, 128));
+    RMAT_CHECK(make_plane_map(&g_tc.sol.b[q], Y + q * yplane, fmt, RMAT_MAX_NB, std::max(1, nrhs),
+                              RMAT_MAX_NB, 128));
   }
   RMAT_CHECK(make_out_map(&g_tc.upd.c, c->C, n, n, c->ld));
   RMAT_CHECK(make_out_map(&g_tc.sol.c, c->Bw, std::max(2, nrhs), n, std::max(2, nrhs)));
@@ -519,6 +569,7 @@ int tc_prepare(rmat_ctx c, int n, int nrhs) {
   g_tc.n = n;
   g_tc.ldf = ldf;
   g_tc.nrhs = nrhs;
+  g_tc.fmt = fmt;
   return RMAT_OK;
 }
 
@@ -529,16 +580,26 @@ int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n) {
   if (reinterpret_cast<void*>(A) != c->C || ld != c->ld) return RMAT_ESTATE;
   RMAT_CHECK(tc_prepare(c, n, c->nrhs + (c->nrhs & 1)));
   TcCache& g_tc = tc_cache(c);
+  TcScales sc{nullptr, 1, nullptr, nullptr};
+  if (rmat_plane_fmt(c->precision) == 1) sc.cscal = c->uscale + k0 / jb;  // jb = nb here
   return launch_tc<TC_BN>(c, g_tc.upd, k0 + jb, k0 + jb, rest, rest, jb, k0, k0 + jb, 0, k0 + jb,
-                          true);
+                          sc, true);
 }
 
 // Solve update: Bsub[M x nrhs] -= F[rows ay0.., cols k0..k0+jb] * Y, Y^T planes in Ypl.
-int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n) {
+// rowscale (FP16 planes): inverse scale per rs_div rows of F (the U blocks).
+int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n,
+                    const float* rowscale, int rs_div) {
   RMAT_CHECK(tc_prepare(c, n, nrhs));
   TcCache& g_tc = tc_cache(c);
+  TcScales sc{nullptr, 1, nullptr, nullptr};
+  if (rmat_plane_fmt(c->precision) == 1) {
+    sc.rowscale = rowscale;
+    sc.rs_div = rs_div;
+    sc.colscale = c->ycs;
+  }
   KTimer kt(c, KT_SOLVE_TC);
-  RMAT_CHECK(launch_tc<128>(c, g_tc.sol, 0, row0, M, nrhs, jb, k0, ay0, 0, 0, false));
+  RMAT_CHECK(launch_tc<128>(c, g_tc.sol, 0, row0, M, nrhs, jb, k0, ay0, 0, 0, sc, false));
   kt.end();
   return RMAT_OK;
 }

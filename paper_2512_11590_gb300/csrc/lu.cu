@@ -22,6 +22,7 @@
 #include <climits>
 
 #include <cooperative_groups.h>
+#include <cuda_fp16.h>
 
 #include "cplx.cuh"
 #include "rmat_internal.h"
@@ -240,38 +241,89 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// TF32 hi/lo split planes (tensor path).  Four planes [re_hi | re_lo | im_hi | im_lo].
+// Tensor operand planes, four per operand: [re_hi | re_lo | im_hi | im_lo].
+//   fmt 0: TF32 hi/lo in fp32 words (hi = TF32 rounding, lo = exact remainder);
+//   fmt 1: FP16 hi/lo of s*z, s a power of two chosen so that |s*z| <= 1.
 //   F: the whole factor, row-major [n][ldf] — L21 blocks and U12 rows as they are
 //      produced; the A operand of the trailing update and of the solve updates.
 //   B: U12^T of the current block, [c][256] (K-major B operand of the trailing update).
 //   Y: a solved right-hand-side block transposed, [rhs][256] (B operand of the solve updates).
-__device__ __forceinline__ void put_split(float* base, size_t plane, size_t o, float2 z) {
-  const float rh = tf32_round(z.x), ih = tf32_round(z.y);
-  base[o] = rh;
-  base[plane + o] = z.x - rh;
-  base[2 * plane + o] = ih;
-  base[3 * plane + o] = z.y - ih;
+// With fmt 1, L21 is stored unscaled (|l| <= sqrt(2) under |Re|+|Im| pivoting), each
+// U12 block with one scale (inverse kept in uscale[block]), each Y column with its
+// own (inverse in ycs[column]); the tensor-core epilogue multiplies the scales back.
+__device__ __forceinline__ void put4(void* base, size_t plane, size_t o, float2 z, int fmt,
+                                     float sc) {
+  if (fmt == 0) {
+    float* b = reinterpret_cast<float*>(base);
+    const float rh = tf32_round(z.x), ih = tf32_round(z.y);
+    b[o] = rh;
+    b[plane + o] = z.x - rh;
+    b[2 * plane + o] = ih;
+    b[3 * plane + o] = z.y - ih;
+  } else {
+    __half* b = reinterpret_cast<__half*>(base);
+    const float xr = z.x * sc, xi = z.y * sc;
+    const __half hr = __float2half_rn(xr), hi = __float2half_rn(xi);
+    b[o] = hr;
+    b[plane + o] = __float2half_rn(xr - __half2float(hr));
+    b[2 * plane + o] = hi;
+    b[3 * plane + o] = __float2half_rn(xi - __half2float(hi));
+  }
 }
+
+// Power-of-two s with m*s in [0.5, 1) (1 for m = 0 or non-finite m).
+__device__ __forceinline__ float pow2_scale(float m) {
+  if (!(m > 0.f) || !(m < INFINITY)) return 1.f;
+  int e;
+  frexpf(m, &e);
+  e = max(-126, min(126, e));
+  return ldexpf(1.f, -e);
+}
+
+__device__ __forceinline__ float cmaxabs(float2 z) { return fmaxf(fabsf(z.x), fabsf(z.y)); }
 
 // L21 rows r in [k0+jb, n), columns k0..k0+jb-1 -> F (warp per row, lanes over columns).
 __global__ void split_l21_kernel(const float2* __restrict__ A, int ld, int k0, int jb, int n,
-                                 float* __restrict__ F, int ldf, size_t fplane) {
+                                 void* __restrict__ F, int ldf, size_t fplane, int fmt) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int r = k0 + jb + warp;
   if (r >= n) return;
   for (int t = lane; t < jb; t += 32)
-    put_split(F, fplane, (size_t)r * ldf + k0 + t, A[(size_t)r * ld + k0 + t]);
+    put4(F, fplane, (size_t)r * ldf + k0 + t, A[(size_t)r * ld + k0 + t], fmt, 1.f);
+}
+
+// max(|Re|, |Im|) over rows k0..k0+jb-1, columns c0..c0+ncols-1 of A -> atomicMax on
+// the float bits in *out (non-negative floats order like their bit patterns).
+__global__ void __launch_bounds__(256)
+block_absmax_kernel(const float2* __restrict__ A, int ld, int k0, int jb, int c0, int ncols,
+                    unsigned* __restrict__ out) {
+  float m = 0.f;
+  const long long total = (long long)jb * ncols;
+  for (long long e = blockIdx.x * 256ll + threadIdx.x; e < total; e += (long long)gridDim.x * 256)
+    m = fmaxf(m, cmaxabs(A[(size_t)(k0 + e / ncols) * ld + c0 + e % ncols]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float sm[8];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) m = fmaxf(m, sm[w]);
+    atomicMax(out, __float_as_uint(m));
+  }
 }
 
 // 32 x 32 tile of a jb x ncols block S (rows t, columns c; row stride lds):
 // optional row-major copy into F (rows frow0 + t, columns fcol0 + c) and the
 // transposed planes T[trow0 + c][t], zero-filled for jb <= t < round_up(jb, 32).
+// fmt 1: the block's scale comes from its max in *smax; CTA (0, 0) records 1/s.
 __global__ void __launch_bounds__(256)
-split_block_kernel(const float2* __restrict__ S, int lds, int jb, int ncols, float* __restrict__ F,
-                   int ldf, size_t fplane, int frow0, int fcol0, float* __restrict__ T,
-                   size_t tplane, int trow0) {
+split_block_kernel(const float2* __restrict__ S, int lds, int jb, int ncols, void* __restrict__ F,
+                   int ldf, size_t fplane, int frow0, int fcol0, void* __restrict__ T,
+                   size_t tplane, int trow0, int fmt, const unsigned* __restrict__ smax,
+                   float* __restrict__ sinv) {
   __shared__ float2 tile[32][33];
+  const float sc = (fmt == 1 && smax) ? pow2_scale(__uint_as_float(*smax)) : 1.f;
+  if (sinv && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *sinv = 1.f / sc;
   const int c0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   for (int i = ty; i < 32; i += 8) {
@@ -279,14 +331,34 @@ split_block_kernel(const float2* __restrict__ S, int lds, int jb, int ncols, flo
     float2 z = make_float2(0.f, 0.f);
     if (t < jb && c < ncols) {
       z = S[(size_t)t * lds + c];
-      if (F) put_split(F, fplane, (size_t)(frow0 + t) * ldf + fcol0 + c, z);
+      if (F) put4(F, fplane, (size_t)(frow0 + t) * ldf + fcol0 + c, z, fmt, sc);
     }
     tile[i][tx] = z;
   }
   __syncthreads();
   for (int i = ty; i < 32; i += 8) {
     const int c = c0 + i, t = t0 + tx;
-    if (c < ncols) put_split(T, tplane, (size_t)(trow0 + c) * RMAT_MAX_NB + t, tile[tx][i]);
+    if (c < ncols) put4(T, tplane, (size_t)(trow0 + c) * RMAT_MAX_NB + t, tile[tx][i], fmt, sc);
+  }
+}
+
+// A solved right-hand-side block (jb rows of S, ncols columns) -> transposed planes
+// Y[c][t], zero-filled for jb <= t < round_up(jb, 32); one warp per column, so the
+// column's scale (fmt 1) is a warp reduction; ycs[c] = 1/s.
+__global__ void __launch_bounds__(256)
+split_y_kernel(const float2* __restrict__ S, int lds, int jb, int ncols, void* __restrict__ Y,
+               size_t yplane, int fmt, float* __restrict__ ycs) {
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (c >= ncols) return;
+  const int kpad = (jb + 31) / 32 * 32;
+  float m = 0.f;
+  for (int t = lane; t < jb; t += 32) m = fmaxf(m, cmaxabs(S[(size_t)t * lds + c]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const float sc = fmt == 1 ? pow2_scale(m) : 1.f;
+  if (ycs && lane == 0) ycs[c] = 1.f / sc;
+  for (int t = lane; t < kpad; t += 32) {
+    const float2 z = t < jb ? S[(size_t)t * lds + c] : make_float2(0.f, 0.f);
+    put4(Y, yplane, (size_t)c * RMAT_MAX_NB + t, z, fmt, sc);
   }
 }
 
@@ -442,7 +514,8 @@ __global__ void __launch_bounds__(256)
 solve_block_kernel(const cplx<T>* __restrict__ A, int ld, int k0, cplx<T>* __restrict__ B,
                    int ldb, int ncols, int nbp, const int* __restrict__ prow,
                    const int* __restrict__ psrc, const int* __restrict__ pcnt,
-                   float* __restrict__ Y, size_t yplane, size_t bstride) {
+                   void* __restrict__ Y, size_t yplane, size_t bstride, int fmt,
+                   float* __restrict__ ycs) {
   using C2 = cplx<T>;
   if (bstride) {  // batched over diagonal blocks (inversion): block blockIdx.y, B rows 0..JB-1
     k0 = blockIdx.y * nbp;
@@ -531,15 +604,17 @@ solve_block_kernel(const cplx<T>* __restrict__ A, int ld, int k0, cplx<T>* __res
     for (int cc = warp; cc < 32; cc += 8) {
       const int gc = blockIdx.x * 32 + cc;
       if (gc >= ncols) continue;
+      float m = 0.f;
       for (int i = lane; i < JB; i += 32) {
         const C2 z = xs[i * 33 + cc];
-        const float re = (float)z.x, im = (float)z.y;
-        const float rh = tf32_round(re), ih = tf32_round(im);
-        const size_t o = (size_t)gc * RMAT_MAX_NB + i;
-        Y[o] = rh;
-        Y[yplane + o] = re - rh;
-        Y[2 * yplane + o] = ih;
-        Y[3 * yplane + o] = im - ih;
+        m = fmaxf(m, fmaxf(fabsf((float)z.x), fabsf((float)z.y)));
+      }
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      const float sc = fmt == 1 ? pow2_scale(m) : 1.f;
+      if (ycs && lane == 0) ycs[gc] = 1.f / sc;
+      for (int i = lane; i < JB; i += 32) {
+        const C2 z = xs[i * 33 + cc];
+        put4(Y, yplane, (size_t)gc * RMAT_MAX_NB + i, make_float2((float)z.x, (float)z.y), fmt, sc);
       }
     }
   }
@@ -568,7 +643,8 @@ template <int JB>
 __global__ void __cluster_dims__(1, JB / 16, 1) __launch_bounds__(256)
 apply_inv_kernel(const float2* __restrict__ Dinv, int k0, int nbp, float2* __restrict__ B,
                  int ldb, int ncols, const int* __restrict__ prow, const int* __restrict__ psrc,
-                 const int* __restrict__ pcnt, float* __restrict__ Yp, size_t yplane) {
+                 const int* __restrict__ pcnt, void* __restrict__ Yp, size_t yplane, int fmt,
+                 float* __restrict__ ycs) {
   namespace cg = cooperative_groups;
   constexpr int CW = 16;          // columns per cluster
   constexpr int SL = 32;          // permutation slots gathered per CTA (2*JB over JB/16 CTAs)
@@ -639,20 +715,29 @@ apply_inv_kernel(const float2* __restrict__ Dinv, int k0, int nbp, float2* __res
   const int i = 16 * s + ri;
   if (act) B[(size_t)(k0 + i) * ldb + col] = acc;
   if (Yp) {
+    __shared__ float cmax[CW];
     ys[ri * (CW + 1) + cl] = acc;
     __syncthreads();
-    // transposed planes: plane row = column, K index = i (16 consecutive i per column)
     const int cc = tid >> 4, ii = tid & 15;
-    const int gc = blockIdx.x * CW + cc;
-    if (gc < ncols) {
-      const float2 z = ys[ii * (CW + 1) + cc];
-      const float rh = tf32_round(z.x), ih = tf32_round(z.y);
-      const size_t o = (size_t)gc * RMAT_MAX_NB + 16 * s + ii;
-      Yp[o] = rh;
-      Yp[yplane + o] = z.x - rh;
-      Yp[2 * yplane + o] = ih;
-      Yp[3 * yplane + o] = z.y - ih;
+    float sc = 1.f;
+    if (fmt == 1) {
+      // column scale: max over the cluster's JB rows (16 per CTA, exchanged via DSMEM)
+      if (tid < CW) {
+        float m = 0.f;
+        for (int r = 0; r < 16; ++r) m = fmaxf(m, cmaxabs(ys[r * (CW + 1) + tid]));
+        cmax[tid] = m;
+      }
+      cluster.sync();
+      float m = 0.f;
+      for (int q = 0; q < JB / 16; ++q) m = fmaxf(m, *cluster.map_shared_rank(&cmax[cc], q));
+      sc = pow2_scale(m);
+      if (s == 0 && ii == 0 && blockIdx.x * CW + cc < ncols) ycs[blockIdx.x * CW + cc] = 1.f / sc;
+      cluster.sync();  // peers' cmax reads are done
     }
+    // transposed planes: plane row = column, K index = i (16 consecutive i per column)
+    const int gc = blockIdx.x * CW + cc;
+    if (gc < ncols)
+      put4(Yp, yplane, (size_t)gc * RMAT_MAX_NB + 16 * s + ii, ys[ii * (CW + 1) + cc], fmt, sc);
   }
 }
 
@@ -872,7 +957,7 @@ int apply_perm(rmat_ctx c, const LUPerm& pm, cplx<T>* B, int ldb, int ncols, int
 // Fused block solve when jb is a supported width; *done = false otherwise.
 template <class T, bool LOWER, int JB>
 int launch_solve_block(rmat_ctx c, const LUPerm* pm, const cplx<T>* A, int ld, int k0, int nb,
-                       cplx<T>* B, int ldb, int ncols, float* Y) {
+                       cplx<T>* B, int ldb, int ncols, void* Y) {
   static bool attr = false;
   const size_t smem = solve_block_smem<T, JB>();
   if (!attr) {
@@ -882,7 +967,8 @@ int launch_solve_block(rmat_ctx c, const LUPerm* pm, const cplx<T>* A, int ld, i
   }
   solve_block_kernel<T, LOWER, JB><<<ceil_div(ncols, 32), 256, smem, c->stream>>>(
       A, ld, k0, B, ldb, ncols, nb, pm ? pm->rows : nullptr, pm ? pm->src : nullptr,
-      pm ? pm->cnt : nullptr, Y, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB, (size_t)0);
+      pm ? pm->cnt : nullptr, Y, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB, (size_t)0,
+      rmat_plane_fmt(c->precision), Y ? c->ycs : nullptr);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;
@@ -890,7 +976,7 @@ int launch_solve_block(rmat_ctx c, const LUPerm* pm, const cplx<T>* A, int ld, i
 
 template <class T, bool LOWER>
 int solve_block(rmat_ctx c, const LUPerm* pm, const cplx<T>* A, int ld, int k0, int nb, int jb,
-                cplx<T>* B, int ldb, int ncols, float* Y, bool* done) {
+                cplx<T>* B, int ldb, int ncols, void* Y, bool* done) {
   *done = true;
   if (jb == 32) return launch_solve_block<T, LOWER, 32>(c, pm, A, ld, k0, nb, B, ldb, ncols, Y);
   if (jb == 64) return launch_solve_block<T, LOWER, 64>(c, pm, A, ld, k0, nb, B, ldb, ncols, Y);
@@ -925,9 +1011,9 @@ int invert_diag_blocks(rmat_ctx c, const float2* A, int ld, int n, int nb) {
   }
   const dim3 grid(JB / 32, nfull);
   solve_block_kernel<float, true, JB><<<grid, 256, smem, c->stream>>>(
-      A, ld, 0, Linv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per);
+      A, ld, 0, Linv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per, 0, nullptr);
   solve_block_kernel<float, false, JB><<<grid, 256, smem, c->stream>>>(
-      A, ld, 0, Uinv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per);
+      A, ld, 0, Uinv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per, 0, nullptr);
   c->launches += 2;
   RMAT_CU(cudaGetLastError());
   c->inv_blocks = nfull;
@@ -937,7 +1023,7 @@ int invert_diag_blocks(rmat_ctx c, const float2* A, int ld, int n, int nb) {
 
 template <int JB>
 int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb, int ncols,
-                     const LUPerm* pm, float* Yp) {
+                     const LUPerm* pm, void* Yp) {
   static bool attr = false;
   const size_t smem = apply_inv_smem<JB>();
   if (!attr) {
@@ -950,7 +1036,8 @@ int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb,
   KTimer kt(c, KT_APPLY_INV);
   apply_inv_kernel<JB><<<dim3(ceil_div(ncols, 16), JB / 16), 256, smem, c->stream>>>(
       D, k0, nb, B, ldb, ncols, pm ? pm->rows : nullptr, pm ? pm->src : nullptr,
-      pm ? pm->cnt : nullptr, Yp, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB);
+      pm ? pm->cnt : nullptr, Yp, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB, rmat_plane_fmt(c->precision),
+      c->ycs);
   kt.end();
   c->launches++;
   RMAT_CU(cudaGetLastError());
@@ -965,6 +1052,9 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
   if (nb < 1 || nb > max_nb<T>()) return RMAT_ESTATE;
   RMAT_CHECK(set_trsm_attrs<T>());
   RMAT_CU(cudaMemsetAsync(ipiv, 0xff, (size_t)n * sizeof(int), c->stream));  // -1: "not pivoted"
+  const int fmt = rmat_plane_fmt(c->precision);
+  if (tensor && fmt == 1)
+    RMAT_CU(cudaMemsetAsync(c->umax, 0, (size_t)ceil_div(n, nb) * sizeof(unsigned), c->stream));
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int jb = std::min(nb, n - k0);
     RMAT_CHECK(launch_panel<T>(c, A, ld, k0, n, jb, ipiv));
@@ -993,11 +1083,18 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
       const size_t fplane = (size_t)n * ld, bplane = (size_t)n * RMAT_MAX_NB;
       const float2* Af = reinterpret_cast<const float2*>(A);
       const int kpad = (int)round_up(jb, 32);
+      const int blk = k0 / nb;
+      if (fmt == 1) {  // the U12 block's scale: max over its entries first
+        block_absmax_kernel<<<std::min(c->sm_count * 2, ceil_div((long long)jb * rest, 256)), 256, 0,
+                              c->stream>>>(Af, ld, k0, jb, k0 + jb, rest, c->umax + blk);
+        c->launches++;
+      }
       split_block_kernel<<<dim3(ceil_div(rest, 32), kpad / 32), 256, 0, c->stream>>>(
           Af + (size_t)k0 * ld + k0 + jb, ld, jb, rest, c->Fpl, ld, fplane, k0, k0 + jb, c->Bpl,
-          bplane, k0 + jb);
+          bplane, k0 + jb, fmt, fmt == 1 ? c->umax + blk : nullptr,
+          fmt == 1 ? c->uscale + blk : nullptr);
       split_l21_kernel<<<ceil_div((long long)rest * 32, 256), 256, 0, c->stream>>>(
-          Af, ld, k0, jb, n, c->Fpl, ld, fplane);
+          Af, ld, k0, jb, n, c->Fpl, ld, fplane, fmt);
       c->launches += 2;
       RMAT_CU(cudaGetLastError());
       RMAT_CHECK(launch_trailing_tc(c, reinterpret_cast<float2*>(A), ld, k0, jb, n));
@@ -1041,10 +1138,11 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
   const bool tc = tensor && sizeof(T) == 4 && c->Fpl && nrhs % 2 == 0 && nrhs <= RMAT_YPL_ROWS &&
                   ldb == nrhs && Bv == c->Bw;
   const size_t yplane = (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB;
+  const int fmt = rmat_plane_fmt(c->precision);
   auto split_y = [&](int row0, int jb) -> int {
-    split_block_kernel<<<dim3(ceil_div(nrhs, 32), (int)round_up(jb, 32) / 32), 256, 0, c->stream>>>(
-        reinterpret_cast<const float2*>(B) + (size_t)row0 * ldb, ldb, jb, nrhs, nullptr, 0, 0, 0, 0,
-        c->Ypl, yplane, 0);
+    split_y_kernel<<<ceil_div(nrhs, 8), 256, 0, c->stream>>>(
+        reinterpret_cast<const float2*>(B) + (size_t)row0 * ldb, ldb, jb, nrhs, c->Ypl, yplane, fmt,
+        c->ycs);
     c->launches++;
     RMAT_CU(cudaGetLastError());
     return RMAT_OK;
@@ -1056,7 +1154,7 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     bool fused = false;
     if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
       float2* Bf = reinterpret_cast<float2*>(B);
-      float* Yp = need_y ? c->Ypl : nullptr;
+      void* Yp = need_y ? c->Ypl : nullptr;
       if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, false, k0, nb, Bf, ldb, nrhs, &pm, Yp));
       else RMAT_CHECK(launch_apply_inv<64>(c, false, k0, nb, Bf, ldb, nrhs, &pm, Yp));
       fused = true;
@@ -1073,7 +1171,7 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
       if (need_y) RMAT_CHECK(split_y(k0, jb));
     }
     if (need_y) {
-      RMAT_CHECK(launch_solve_tc(c, k0 + jb, n - k0 - jb, nrhs, k0, jb, k0 + jb, n));
+      RMAT_CHECK(launch_solve_tc(c, k0 + jb, n - k0 - jb, nrhs, k0, jb, k0 + jb, n, nullptr, nb));
     } else {
       RMAT_CHECK(gemm_sub<T>(c, n - k0 - jb, nrhs, jb, A + (size_t)(k0 + jb) * ld + k0, ld,
                              B + (size_t)k0 * ldb, ldb, B + (size_t)(k0 + jb) * ldb, ldb));
@@ -1087,7 +1185,7 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     bool fused = false;
     if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
       float2* Bf = reinterpret_cast<float2*>(B);
-      float* Yp = need_y ? c->Ypl : nullptr;
+      void* Yp = need_y ? c->Ypl : nullptr;
       if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, true, k0, nb, Bf, ldb, nrhs, nullptr, Yp));
       else RMAT_CHECK(launch_apply_inv<64>(c, true, k0, nb, Bf, ldb, nrhs, nullptr, Yp));
       fused = true;
@@ -1103,7 +1201,8 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
       if (need_y) RMAT_CHECK(split_y(k0, jb));
     }
     if (need_y) {
-      RMAT_CHECK(launch_solve_tc(c, 0, k0, nrhs, k0, jb, 0, n));
+      // A = U rows of earlier row blocks: their per-block scales apply row-wise
+      RMAT_CHECK(launch_solve_tc(c, 0, k0, nrhs, k0, jb, 0, n, fmt == 1 ? c->uscale : nullptr, nb));
     } else {
       RMAT_CHECK(gemm_sub<T>(c, k0, nrhs, jb, A + k0, ld, B + (size_t)k0 * ldb, ldb, B, ldb));
     }

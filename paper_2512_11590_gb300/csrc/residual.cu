@@ -41,56 +41,95 @@ resid_kinetic_kernel(double2* __restrict__ R, const double2* __restrict__ X, int
 }
 
 // r -= W_i X_i at every mesh point: complex FP64 GEMM (nch x nch) x (nch x nrhs)
-// per point; 32 x 32 output tile per CTA, 16-deep K chunks in shared memory.
+// per point on the FP64 tensor path (mma.m8n8k4.f64; the complex product as four
+// real products, -Wi*Xi through a negated copy of the Wi fragment).  64 x 64
+// output tile per CTA, 16-deep K chunks staged in shared memory as separate real
+// and imaginary [k][64] planes (row pitch 72 doubles: the 4 k-rows x 8 entries a
+// fragment load touches fall in distinct 8-byte bank slots, two wavefronts).
+// Each of the 8 warps owns a 32 x 16 sub-tile: 4 x 2 tiles of 8 x 8.
+constexpr int RC_T = 64, RC_K = 16, RC_LD = 72;
+
+__device__ __forceinline__ void dmma(double& d0, double& d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
 __global__ void __launch_bounds__(256)
 resid_coupling_kernel(double2* __restrict__ R, const double2* __restrict__ X, int nrhs, int nlag,
                       int nch, const double2* __restrict__ W) {
-  __shared__ double2 Ws[16][33];
-  __shared__ double2 Xs[16][32];
+  __shared__ double Wr[RC_K][RC_LD], Wm[RC_K][RC_LD];  // W[a0 + a][k0 + k] -> [k][a]
+  __shared__ double Xr[RC_K][RC_LD], Xm[RC_K][RC_LD];  // X[(k0 + k, i)][b0 + b] -> [k][b]
   const int i = blockIdx.z;
-  const int a0 = blockIdx.y * 32, b0 = blockIdx.x * 32;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int a0 = blockIdx.y * RC_T, b0 = blockIdx.x * RC_T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wa = (warp >> 2) * 32, wb = (warp & 3) * 16;  // warp sub-tile origin
+  const int g = lane >> 2, t = lane & 3;                   // fragment group / thread in group
   const double2* Wi = W + (size_t)i * nch * nch;
-  double2 acc[2][2];
-  for (int p = 0; p < 2; ++p)
-    for (int q = 0; q < 2; ++q) acc[p][q] = make_double2(0, 0);
-  for (int k0 = 0; k0 < nch; k0 += 16) {
-    for (int e = threadIdx.x; e < 16 * 32; e += 256) {
-      const int kk = e & 15, aa = e >> 4;  // W row a0+aa, column k0+kk
+  double accr[4][2][2], acci[4][2][2];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) accr[p][q][0] = accr[p][q][1] = acci[p][q][0] = acci[p][q][1] = 0.0;
+  for (int k0 = 0; k0 < nch; k0 += RC_K) {
+    // W tile: 64 rows x 16 k (coalesced along k); X tile: 16 k x 64 columns
+    for (int e = threadIdx.x; e < RC_T * RC_K; e += 256) {
+      const int kk = e & (RC_K - 1), aa = e >> 4;
       const int ga = a0 + aa, gk = k0 + kk;
-      Ws[kk][aa] = (ga < nch && gk < nch) ? Wi[(size_t)ga * nch + gk] : make_double2(0, 0);
-      const int kb = e >> 5, bb = e & 31;  // X row (k0+kb, i), column b0+bb
+      const double2 w = (ga < nch && gk < nch) ? Wi[(size_t)ga * nch + gk] : make_double2(0, 0);
+      Wr[kk][aa] = w.x;
+      Wm[kk][aa] = w.y;
+      const int kb = e >> 6, bb = e & (RC_T - 1);
       const int gk2 = k0 + kb, gb = b0 + bb;
-      Xs[kb][bb] = (gk2 < nch && gb < nrhs) ? X[((size_t)gk2 * nlag + i) * nrhs + gb]
-                                           : make_double2(0, 0);
+      const double2 x = (gk2 < nch && gb < nrhs) ? X[((size_t)gk2 * nlag + i) * nrhs + gb]
+                                                : make_double2(0, 0);
+      Xr[kb][bb] = x.x;
+      Xm[kb][bb] = x.y;
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      double2 w[2], x[2];
-      w[0] = Ws[kk][ty];
-      w[1] = Ws[kk][ty + 16];
-      x[0] = Xs[kk][tx];
-      x[1] = Xs[kk][tx + 16];
+    for (int k4 = 0; k4 < RC_K; k4 += 4) {
+      double ar[4], ai[4], an[4], br[2], bi[2];
 #pragma unroll
-      for (int p = 0; p < 2; ++p)
+      for (int p = 0; p < 4; ++p) {
+        ar[p] = Wr[k4 + t][wa + 8 * p + g];
+        ai[p] = Wm[k4 + t][wa + 8 * p + g];
+        an[p] = -ai[p];
+      }
 #pragma unroll
-        for (int q = 0; q < 2; ++q) cadd_mul<double>(acc[p][q], w[p], x[q]);
+      for (int q = 0; q < 2; ++q) {
+        br[q] = Xr[k4 + t][wb + 8 * q + g];
+        bi[q] = Xm[k4 + t][wb + 8 * q + g];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          dmma(accr[p][q][0], accr[p][q][1], ar[p], br[q]);
+          dmma(accr[p][q][0], accr[p][q][1], an[p], bi[q]);
+          dmma(acci[p][q][0], acci[p][q][1], ar[p], bi[q]);
+          dmma(acci[p][q][0], acci[p][q][1], ai[p], br[q]);
+        }
     }
     __syncthreads();
   }
-  for (int p = 0; p < 2; ++p) {
-    const int ga = a0 + ty + 16 * p;
+  // accumulator element (row g, columns 2t, 2t+1) of each 8 x 8 tile
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int ga = a0 + wa + 8 * p + g;
     if (ga >= nch) continue;
-    for (int q = 0; q < 2; ++q) {
-      const int gb = b0 + tx + 16 * q;
-      if (gb >= nrhs) continue;
-      double2* r = R + ((size_t)ga * nlag + i) * nrhs + gb;
-      double2 v = *r;
-      v.x -= acc[p][q].x;
-      v.y -= acc[p][q].y;
-      *r = v;
-    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gb = b0 + wb + 8 * q + 2 * t + h;
+        if (gb >= nrhs) continue;
+        double2* r = R + ((size_t)ga * nlag + i) * nrhs + gb;
+        double2 v = *r;
+        v.x -= accr[p][q][h];
+        v.y -= acci[p][q][h];
+        *r = v;
+      }
   }
 }
 
@@ -264,7 +303,7 @@ int launch_residual(rmat_ctx c, double*) {
   if (c->kind == 1) {
     dim3 gk(ceil_div(nrhs, 32), c->nch);
     resid_kinetic_kernel<<<gk, 256, 0, c->stream>>>(c->Rres, c->X, nrhs, c->nlag, c->Kmat, c->fa);
-    dim3 gc(ceil_div(nrhs, 32), ceil_div(c->nch, 32), c->nlag);
+    dim3 gc(ceil_div(nrhs, RC_T), ceil_div(c->nch, RC_T), c->nlag);
     resid_coupling_kernel<<<gc, 256, 0, c->stream>>>(c->Rres, c->X, nrhs, c->nlag, c->nch, c->Wpt);
     c->launches += 2;
   } else {

@@ -87,11 +87,16 @@ struct rmat_ctx_s {
   double2* X = nullptr;    size_t X_cap = 0;        // FP64 solution, row-major N x nrhs
   double2* Rres = nullptr; size_t Rres_cap = 0;     // FP64 residual, row-major N x nrhs
   void* Bw = nullptr;      size_t Bw_cap = 0;       // solve work in the factor precision
-  float* Fpl = nullptr;    size_t Fpl_cap = 0;      // full-size split factor planes [4][N][ld] (A operand)
-  float* Ypl = nullptr;    size_t Ypl_cap = 0;
+  void* Fpl = nullptr;     size_t Fpl_cap = 0;      // full-size split factor planes [4][N][ld] (A operand)
+  void* Ypl = nullptr;     size_t Ypl_cap = 0;
   void* Dinv = nullptr;    size_t Dinv_cap = 0;     // inverted diagonal blocks (tensor solve path)
   int inv_blocks = 0, inv_nb = 0;      // right-hand-side block planes [4][RMAT_YPL_ROWS][256]
-  float* Bpl = nullptr;    size_t Bpl_cap = 0;      // tensor B operand planes (U12^T split)
+  void* Bpl = nullptr;     size_t Bpl_cap = 0;      // tensor B operand planes (U12^T split)
+  // FP16 planes: per U block max bits and inverse scale 2^e, per right-hand-side
+  // column inverse scale of the current solved block
+  unsigned* umax = nullptr; size_t umax_cap = 0;
+  float* uscale = nullptr; size_t uscale_cap = 0;
+  float* ycs = nullptr;    size_t ycs_cap = 0;
   double* Dsc = nullptr;   size_t Dsc_cap = 0;      // equilibration scale per row
   std::vector<double> ir_hist;                      // refinement history of the last solve
   double2* Rint = nullptr; size_t Rint_cap = 0;     // R-matrix (row-major nch x nch)
@@ -145,7 +150,8 @@ int perm_reserve(rmat_ctx c, LUPerm& pm, int n, int nb);
 // gemm_tc.cu
 int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n);
 // solve update: rows [row0, row0+M) of the solve buffer Bw (ld = nrhs) -= F(ay0.., k0..k0+jb) * Y
-int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n);
+int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n,
+                    const float* rowscale, int rs_div);
 int tc_prepare(rmat_ctx c, int n, int nrhs);
 void tc_release(rmat_ctx c);
 // lu.cu (SIMT complex GEMM C -= A B, row-major)
@@ -201,6 +207,11 @@ struct KTimer {
   KTimer(struct rmat_ctx_s* c_, int k_);
   void end();
 };
+
+// Tensor-core operand planes: format 0 = TF32 hi/lo held in fp32 words, 1 = FP16 hi/lo.
+static inline bool rmat_tensor_prec(int p) { return p == RMAT_C64_3XTF32_IR || p == RMAT_C64_3XF16_IR; }
+static inline int rmat_plane_fmt(int p) { return p == RMAT_C64_3XF16_IR ? 1 : 0; }
+static inline size_t rmat_plane_esz(int p) { return p == RMAT_C64_3XF16_IR ? 2 : 4; }
 
 static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 static inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }

@@ -14,7 +14,7 @@ from rmat_gpu import relerr, run_dense, run_problem
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 1e-10, 2: 1e-10}
+TOL = {0: 1e-12, 1: 1e-10, 2: 1e-10, 3: 1e-10}
 
 
 @pytest.fixture(scope="module")
@@ -42,7 +42,7 @@ def truth(p, key):
     return _TRUTH[key]
 
 
-PRECS = [0, 1, 2]
+PRECS = [0, 1, 2, 3]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -141,7 +141,8 @@ def test_bounded_panel_wait_times_out_cleanly(g, ctx):
     assert relerr(out["X"], np.linalg.solve(A[:200, :200], B[:200])) < 1e-12
 
 
-@pytest.mark.parametrize("prec,nb", [(1, 32), (1, 128), (2, 128), (0, 32), (0, 64)])
+@pytest.mark.parametrize("prec,nb", [(1, 32), (1, 128), (2, 128), (0, 32), (0, 64), (3, 64),
+                                     (3, 128)])
 def test_block_widths(g, ctx, prec, nb):
     p = cp.config2(16)
     ref = truth(p, "c2-16")
@@ -149,15 +150,30 @@ def test_block_widths(g, ctx, prec, nb):
     assert relerr(out["U"], ref["U"]) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", [1, 3])
 @pytest.mark.parametrize("equil", [0, 1])
-def test_equilibration_switch(g, ctx, equil):
+def test_equilibration_switch(g, ctx, equil, prec):
     p = cp.config3(16, W=-1.0)               # config 3b: weaker absorption, worse conditioned
     ref = truth(p, "c3b-16")
     g.rmat_set_param(ctx, g.RMAT_PARAM_EQUILIBRATE, equil)
     try:
-        out = run_problem(ctx, p, 1, max_refine=40, tol=1e-14)
+        out = run_problem(ctx, p, prec, max_refine=40, tol=1e-14)
         hist = g.rmat_refine_history(ctx)
     finally:
         g.rmat_set_param(ctx, g.RMAT_PARAM_EQUILIBRATE, -1)
-    assert relerr(out["U"], ref["U"]) < TOL[1]
+    assert relerr(out["U"], ref["U"]) < TOL[prec]
     assert len(hist) == out["iters"] + 1 and hist[-1] < 1e-11
+
+
+@pytest.mark.parametrize("scale_a,scale_b", [(1e7, 1e-12), (1e-6, 1e9)])
+def test_fp16_planes_far_outside_fp16_range(g, ctx, scale_a, scale_b):
+    """Split-FP16 tensor path on a dense system whose entries (scale_a) and right-hand
+    sides (scale_b) lie far outside the FP16 range: the per-block and per-column
+    power-of-two scales keep every operand representable, and refinement reaches
+    the FP64 level (checked against LAPACK)."""
+    A, B = cp.random_dense(31, 640, nrhs=4)
+    A, B = A * scale_a, B * scale_b
+    Xe = np.linalg.solve(A, B)
+    out = run_dense(ctx, A, B, 3, max_refine=30, tol=1e-15, nb=128)
+    assert out["iters"] >= 1
+    assert relerr(out["X"], Xe) < 1e-12
