@@ -151,7 +151,7 @@ int enqueue_all(rmat_batch b, void* const* U) {
 }
 
 // Largest system a lane takes: a single panel CTA keeps N rows x 32 columns in
-// shared memory (panel_kernel's staged variant, 220 KB).
+// shared memory (panel_kernel's staged variant, within the 227 KB opt-in limit).
 int lane_cap(rmat_batch b) { return b->precision == RMAT_C128 ? 416 : 832; }
 
 // Assign systems to the serial phase or to lanes (longest first onto the least

@@ -38,7 +38,7 @@ constexpr int MAX_RPC = 4096;  // rows per panel CTA
 template <class T, bool SMEM>
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __restrict__ ipiv,
-             int* __restrict__ stat, PanelScratch ps, int rpc, long long spin_limit) {
+             int* __restrict__ stat, PanelScratch ps, int rpc, int ldr, long long spin_limit) {
   using C2 = cplx<T>;
   const int P = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = PANEL_THREADS / 32;
@@ -50,20 +50,22 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
 
   __shared__ T s_v[32];
   __shared__ int s_i[32];
-  __shared__ int s_win, s_wcta, s_zero, s_abort;
+  __shared__ int s_win, s_zero, s_abort;
   extern __shared__ unsigned char smem_raw[];
-  C2* s_prow = reinterpret_cast<C2*>(smem_raw);  // [RMAT_MAX_NB]
-  C2* s_l = s_prow + RMAT_MAX_NB;                // [rpc]
-  C2* s_rows = s_l + rpc;                        // [rpc][jb] when SMEM
-  // own row r, panel-local column c
+  C2* s_prow = reinterpret_cast<C2*>(smem_raw);  // [RMAT_MAX_NB] pivot row
+  C2* s_trow = s_prow + RMAT_MAX_NB;             // [RMAT_MAX_NB] old row gj
+  C2* s_l = s_trow + RMAT_MAX_NB;                // [rpc]
+  C2* s_rows = s_l + rpc;                        // [rpc][ldr] when SMEM
+  // own row r, panel-local column c (shared-memory rows padded to ldr = jb + 1 when
+  // that fits, so a column read by consecutive rows spreads over the banks)
   auto at = [&](int r) -> C2* {
-    return SMEM ? s_rows + (size_t)(r - r_lo) * jb : A + (size_t)r * ld + k0;
+    return SMEM ? s_rows + (size_t)(r - r_lo) * ldr : A + (size_t)r * ld + k0;
   };
   if (tid == 0) s_abort = 0;
   if (SMEM) {
     for (int e = tid; e < (r_hi - r_lo) * jb; e += PANEL_THREADS) {
       const int rr = e / jb, cc = e - rr * jb;
-      s_rows[e] = A[(size_t)(r_lo + rr) * ld + k0 + cc];
+      s_rows[(size_t)rr * ldr + cc] = A[(size_t)(r_lo + rr) * ld + k0 + cc];
     }
   }
   __syncthreads();
@@ -85,6 +87,11 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
       if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
     }
     if (lane == 0) { s_v[warp] = best; s_i[warp] = bidx; }
+    // the current row gj travels to the pivot row's owner through trow
+    if (gj >= r_lo && gj < r_hi && warp > 0) {
+      const C2* src = at(gj);
+      for (int c = tid - 32; c < jb; c += PANEL_THREADS - 32) trow[(size_t)par * RMAT_MAX_NB + c] = src[c];
+    }
     __syncthreads();
     if (warp == 0) {
       best = lane < nwarp ? s_v[lane] : (T)-1;
@@ -96,29 +103,20 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
         if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
       }
       if (lane == 0) {
-        s_win = bidx;
         cval[par * RMAT_MAX_PANEL_CTAS + cta] = best;
         ps.cidx[par * RMAT_MAX_PANEL_CTAS + cta] = bidx;
       }
-    }
-    __syncthreads();
-    {
-      const int cr = s_win;
-      C2* slot = crow + ((size_t)par * RMAT_MAX_PANEL_CTAS + cta) * RMAT_MAX_NB;
-      if (cr != INT_MAX) {
-        const C2* src = at(cr);
-        for (int c = tid; c < jb; c += PANEL_THREADS) slot[c] = src[c];
-      }
-      if (gj >= r_lo && gj < r_hi) {
-        const C2* src = at(gj);
-        for (int c = tid; c < jb; c += PANEL_THREADS) trow[(size_t)par * RMAT_MAX_NB + c] = src[c];
+      // the CTA's candidate row, published for whichever CTA's row wins
+      if (bidx != INT_MAX) {
+        C2* slot = crow + ((size_t)par * RMAT_MAX_PANEL_CTAS + cta) * RMAT_MAX_NB;
+        const C2* src = at(bidx);
+        for (int c = lane; c < jb; c += 32) slot[c] = src[c];
       }
     }
-    // ---- grid barrier (bounded spin) ----
+    // ---- grid barrier (bounded spin): release-add, acquire-poll ----
     __syncthreads();
     if (tid == 0) {
-      __threadfence();
-      atomicAdd(ps.bar, 1u);
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ps.bar) : "memory");
       const unsigned target = (unsigned)(j + 1) * (unsigned)P;
       long long polls = 0;
       while (ld_acquire_gpu(ps.bar) < target) {
@@ -131,7 +129,7 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
     }
     __syncthreads();
     if (s_abort) return;
-    // ---- phase B: global winner ----
+    // ---- phase B: global winner (warp 0), old row gj prefetched (other warps) ----
     if (warp == 0) {
       best = (T)-1;
       bidx = INT_MAX;
@@ -160,22 +158,24 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
         int oc = __shfl_xor_sync(0xffffffffu, bc, o);
         if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; bc = oc; }
       }
+      // winner's row into shared memory (same warp: no barrier in between)
+      const int wc = (bc >= 0 && bc < P) ? bc : 0;
+      const C2* wslot = crow + ((size_t)par * RMAT_MAX_PANEL_CTAS + wc) * RMAT_MAX_NB;
+      for (int c = lane; c < jb; c += 32) s_prow[c] = ld_cg(wslot + c);
       if (lane == 0) {
         s_win = bidx;
-        s_wcta = bc;
         s_zero = !(best > (T)0);
       }
+    } else {
+      for (int c = tid - 32; c < jb; c += PANEL_THREADS - 32)
+        s_trow[c] = ld_cg(trow + (size_t)par * RMAT_MAX_NB + c);
     }
     __syncthreads();
     const int p = (s_win >= gj && s_win < n) ? s_win : gj;
-    const int wc = (s_wcta >= 0 && s_wcta < P) ? s_wcta : 0;
-    const C2* wslot = crow + ((size_t)par * RMAT_MAX_PANEL_CTAS + wc) * RMAT_MAX_NB;
-    for (int c = tid; c < jb; c += PANEL_THREADS) s_prow[c] = ld_cg(wslot + c);
     if (cta == 0 && tid == 0) {
       ipiv[gj] = p;
       if (s_zero) atomicCAS(&stat[ST_INFO], 0, gj + 1);
     }
-    __syncthreads();
     if (p != gj) {
       if (gj >= r_lo && gj < r_hi) {
         C2* dst = at(gj);
@@ -183,8 +183,7 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
       }
       if (p >= r_lo && p < r_hi) {
         C2* dst = at(p);
-        for (int c = tid; c < jb; c += PANEL_THREADS)
-          dst[c] = ld_cg(trow + (size_t)par * RMAT_MAX_NB + c);
+        for (int c = tid; c < jb; c += PANEL_THREADS) dst[c] = s_trow[c];
       }
     }
     __syncthreads();
@@ -199,25 +198,14 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
     }
     __syncthreads();
     if (j + 1 < jb) {
-      if (SMEM) {
-        // rank-1 update of the rows' remaining columns, one element per thread step
-        const int ncol = jb - j - 1, nrow = r_hi - r_first;
-        for (int e = tid; e < nrow * ncol; e += PANEL_THREADS) {
-          const int rr = e / ncol, cc = j + 1 + (e - rr * ncol);
-          C2* ar = at(r_first + rr);
-          C2 x = ar[cc];
-          csub_mul<T>(x, s_l[r_first + rr - r_lo], s_prow[cc]);
-          ar[cc] = x;
-        }
-      } else {
-        for (int r = r_first + warp; r < r_hi; r += nwarp) {
-          const C2 lm = s_l[r - r_lo];
-          C2* Ar = at(r);
-          for (int c = j + 1 + lane; c < jb; c += 32) {
-            C2 x = Ar[c];
-            csub_mul<T>(x, lm, s_prow[c]);
-            Ar[c] = x;
-          }
+      // rank-1 update of the remaining columns: warp per row, lanes over columns
+      for (int r = r_first + warp; r < r_hi; r += nwarp) {
+        const C2 lm = s_l[r - r_lo];
+        C2* Ar = at(r);
+        for (int c = j + 1 + lane; c < jb; c += 32) {
+          C2 x = Ar[c];
+          csub_mul<T>(x, lm, s_prow[c]);
+          Ar[c] = x;
         }
       }
     }
@@ -226,7 +214,7 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
   if (SMEM) {
     for (int e = tid; e < (r_hi - r_lo) * jb; e += PANEL_THREADS) {
       const int rr = e / jb, cc = e - rr * jb;
-      A[(size_t)(r_lo + rr) * ld + k0 + cc] = s_rows[e];
+      A[(size_t)(r_lo + rr) * ld + k0 + cc] = s_rows[(size_t)rr * ldr + cc];
     }
   }
 }
@@ -522,8 +510,9 @@ solve_block_kernel(const cplx<T>* __restrict__ A, int ld, int k0, cplx<T>* __res
     B += (size_t)blockIdx.y * bstride - (size_t)k0 * ldb;
   }
   constexpr int RPW = JB / 8;
-  constexpr int LDS = JB + 1;
-  extern __shared__ unsigned char smem_raw[];
+  constexpr int LDS = JB + 2;  // 16-byte aligned rows for the asynchronous copy
+  constexpr int CPR = JB * (int)sizeof(C2) / 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* Ls = reinterpret_cast<C2*>(smem_raw);  // [JB][LDS]
   C2* vals = Ls + JB * LDS;                  // [2*JB][32] gather; reused as xs [JB][33]
   C2* xs = vals;
@@ -534,19 +523,15 @@ solve_block_kernel(const cplx<T>* __restrict__ A, int ld, int k0, cplx<T>* __res
   const int col = blockIdx.x * 32 + lane;
   const bool act = col < ncols;
 
-  for (int e0 = threadIdx.x; e0 < JB * JB; e0 += 256 * 8) {
-    C2 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * 256;
-      if (e < JB * JB) v[u] = A[(size_t)(k0 + e / JB) * ld + k0 + e % JB];
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * 256;
-      if (e < JB * JB) Ls[(e / JB) * LDS + e % JB] = v[u];
-    }
+  // diagonal block -> shared memory, every 16-byte copy in flight at once
+  for (int q = threadIdx.x; q < JB * CPR; q += 256) {
+    const int r = q / CPR, h = q - r * CPR;
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(
+        reinterpret_cast<unsigned char*>(Ls + (size_t)r * LDS) + 16 * h);
+    const unsigned char* sp = reinterpret_cast<const unsigned char*>(A + (size_t)(k0 + r) * ld + k0) + 16 * h;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(sp) : "memory");
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
   int cnt = JB;
   if (prow) {
     const int blk = k0 / nbp;
@@ -562,12 +547,16 @@ solve_block_kernel(const cplx<T>* __restrict__ A, int ld, int k0, cplx<T>* __res
     }
   }
   __syncthreads();
-  if (!LOWER)
-    for (int q = threadIdx.x; q < JB; q += 256) dinv[q] = cdiv<T>(mkc<T>(1, 0), Ls[q * LDS + q]);
   // permuted gather: slot q receives the original content of slot idx[q]
+#pragma unroll 4
   for (int q = warp; q < cnt; q += 8)
     vals[q * 32 + lane] = act ? B[(size_t)rows[idx[q]] * ldb + col] : mkc<T>(0, 0);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
+  if (!LOWER) {
+    for (int q = threadIdx.x; q < JB; q += 256) dinv[q] = cdiv<T>(mkc<T>(1, 0), Ls[q * LDS + q]);
+    __syncthreads();
+  }
   if (prow)
     for (int q = JB + warp; q < cnt; q += 8)
       if (act) B[(size_t)rows[q] * ldb + col] = vals[q * 32 + lane];
@@ -749,7 +738,7 @@ size_t apply_inv_smem() {
 
 template <class T, int JB>
 size_t solve_block_smem() {
-  return (size_t)JB * (JB + 1) * sizeof(cplx<T>) + (size_t)2 * JB * 32 * sizeof(cplx<T>) +
+  return (size_t)JB * (JB + 2) * sizeof(cplx<T>) + (size_t)2 * JB * 32 * sizeof(cplx<T>) +
          (size_t)JB * sizeof(cplx<T>) + (size_t)4 * JB * sizeof(int);
 }
 
@@ -890,12 +879,14 @@ int panel_ctas_for(rmat_ctx c, int M) {
   return P;
 }
 
-constexpr size_t PANEL_SMEM_LIMIT = 220 * 1024;
+// Dynamic shared memory a panel CTA may stage: the device's opt-in maximum per
+// block less 1 KB for the kernel's static shared variables.
+size_t panel_smem_limit(rmat_ctx c) { return (size_t)c->smem_optin - 1024; }
 
 template <class T>
-size_t panel_smem(int rpc, int jb, bool in_smem) {
-  return (size_t)(RMAT_MAX_NB + rpc) * sizeof(cplx<T>) +
-         (in_smem ? (size_t)rpc * jb * sizeof(cplx<T>) : 0);
+size_t panel_smem(int rpc, int ldr, bool in_smem) {
+  return (size_t)(2 * RMAT_MAX_NB + rpc) * sizeof(cplx<T>) +
+         (in_smem ? (size_t)rpc * ldr * sizeof(cplx<T>) : 0);
 }
 
 template <class T>
@@ -903,12 +894,15 @@ int launch_panel(rmat_ctx c, cplx<T>* A, int ld, int k0, int n, int jb, int* ipi
   const int M = n - k0;
   const int P = panel_ctas_for(c, M);
   const int rpc = ceil_div(M, P);
-  const bool in_smem = panel_smem<T>(rpc, jb, true) <= PANEL_SMEM_LIMIT;
-  const size_t smem = panel_smem<T>(rpc, jb, in_smem);
+  int ldr = jb + 1;
+  const size_t limit = panel_smem_limit(c);
+  if (panel_smem<T>(rpc, ldr, true) > limit) ldr = jb;
+  const bool in_smem = panel_smem<T>(rpc, ldr, true) <= limit;
+  const size_t smem = panel_smem<T>(rpc, ldr, in_smem);
   static bool attr_set[2] = {false, false};
   if (!attr_set[sizeof(T) == 8]) {
     RMAT_CU(cudaFuncSetAttribute(panel_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)PANEL_SMEM_LIMIT));
+                                 (int)limit));
     RMAT_CU(cudaFuncSetAttribute(panel_kernel<T, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)panel_smem<T>(MAX_RPC, 0, false)));
@@ -918,7 +912,8 @@ int launch_panel(rmat_ctx c, cplx<T>* A, int ld, int k0, int n, int jb, int* ipi
   PanelScratch ps = c->ps;
   long long spin = c->spin_limit;
   int* stat = c->dstat;
-  void* args[] = {&A, &ld, (void*)&k0, (void*)&n, (void*)&jb, &ipiv, &stat, &ps, (void*)&rpc, &spin};
+  void* args[] = {&A,   &ld,   (void*)&k0,  (void*)&n, (void*)&jb, &ipiv,
+                  &stat, &ps,   (void*)&rpc, &ldr,      &spin};
   const void* kern = in_smem ? (const void*)panel_kernel<T, true> : (const void*)panel_kernel<T, false>;
   KTimer kt(c, KT_PANEL);
   RMAT_CU(cudaLaunchCooperativeKernel(kern, dim3(P), dim3(PANEL_THREADS), args, smem, c->stream));

@@ -56,6 +56,7 @@ struct rmat_ctx_s {
   int panel_ctas_param = 0;
   long long spin_limit = 20000000LL;   // ~ seconds of polling
   int timing = 0;
+  int smem_optin = 232448;  // cudaDeviceProp::sharedMemPerBlockOptin
   int equil_param = -1;   // -1: default (on for complex64 paths), 0 off, 1 on
   bool equil = false;     // symmetric diagonal equilibration active for this problem
 
