@@ -215,8 +215,10 @@ int rmat_refine_history(rmat_ctx ctx, double* hist, int n);
  * one CUDA graph that later runs replay; refinement uses max_refine steps with
  * the stopping rule of rmat_solve evaluated on the device.  Systems with
  * N > split_n run one after another with the full-device path; smaller ones are
- * spread over `lanes` concurrent streams (single-CTA panels; at most N = 832 for
- * the complex64 precisions and 416 for RMAT_C128, whatever split_n says).  rmat_batch_tune
+ * spread over `lanes` concurrent streams, provided their panels fit the shared
+ * memory of one thread block cluster (up to 16 CTAs: N <= ~6900 in complex64,
+ * ~3400 in complex128), whatever split_n says.  Refinement steps after a system
+ * has stopped return at once on the device.  rmat_batch_tune
  * times candidate (lanes, split_n) plans on the batch and keeps the fastest,
  * cached in the JSON-lines file named by the environment variable
  * RMAT_TUNE_CACHE when it is set. */

@@ -462,14 +462,18 @@ int enqueue_solve_refine(rmat_ctx c, int max_refine, double tol, IrState* st) {
   RMAT_CHECK(launch_x_from_w(c));
   RMAT_CHECK(launch_ir_init(c, st));
   const int patience = c->precision == RMAT_C128 ? 2 : 1;
-  for (int it = 0; it <= max_refine; ++it) {
-    RMAT_CHECK(launch_residual(c, nullptr));
-    RMAT_CHECK(launch_ir_state(c, tol, patience, it == max_refine, st));
-    if (it == max_refine) break;
-    RMAT_CHECK(solve_factors(c));
-    RMAT_CHECK(launch_update(c, st));
+  // once the stopping rule has fired, every later kernel of the loop returns at once
+  c->skip = &st->done;
+  int rc = RMAT_OK;
+  for (int it = 0; it <= max_refine && rc == RMAT_OK; ++it) {
+    rc = launch_residual(c, nullptr);
+    if (rc == RMAT_OK) rc = launch_ir_state(c, tol, patience, it == max_refine, st);
+    if (rc != RMAT_OK || it == max_refine) break;
+    rc = solve_factors(c);
+    if (rc == RMAT_OK) rc = launch_update(c, st);
   }
-  return RMAT_OK;
+  c->skip = nullptr;
+  return rc;
 }
 
 extern "C" {

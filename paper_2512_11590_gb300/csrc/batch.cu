@@ -8,9 +8,10 @@
 //     with the full-device path (cooperative panels across all SMs, tcgen05
 //     updates); they are the bulk of the flops;
 //   * the other systems are spread over `lanes` concurrent streams (longest job
-//     first onto the least-loaded lane), each with single-CTA panels, so no
-//     kernel of a lane ever waits for another CTA and lanes can share the GPU with
-//     the large systems without any co-residency requirement;
+//     first onto the least-loaded lane), each with cluster panels (one thread
+//     block cluster, distributed shared memory), so no kernel of a lane waits for
+//     CTAs outside its own cluster and lanes share the GPU with the large systems
+//     without any grid-wide co-residency requirement;
 //   * refinement runs a fixed step budget with the stopping rule evaluated on the
 //     device (converged systems skip their updates);
 //   * per-system statuses and refinement counts are read once at the end.
@@ -75,7 +76,7 @@ struct rmat_batch_s {
   int max_refine = 30;
   double tol = 1e-13;
   int lanes = 8;
-  int split_n = 832;
+  int split_n = 8192;
   bool use_graph = true;
   bool planned = false, warm = false;
   cudaGraphExec_t gexec = nullptr;
@@ -85,10 +86,10 @@ struct rmat_batch_s {
 
 namespace {
 
-// LU block width of a system: 32 in a lane (a single-CTA panel keeps its rows x
-// 32 columns in shared memory), the single-system default otherwise.
+// LU block width of a system: in a lane 32 up to N = 1024 and 64 above (its panel
+// runs as one thread block cluster), the single-system default otherwise.
 int sys_nb(rmat_batch b, const BatchSys& y) {
-  if (y.lane > 0) return 32;
+  if (y.lane > 0) return y.N <= 1024 ? 32 : 64;
   if (b->precision == RMAT_C128) return y.N >= 2048 ? 64 : 32;
   return y.N >= 4096 ? 128 : 64;
 }
@@ -110,7 +111,7 @@ int enqueue_system(rmat_batch b, int s, void* U) {
   c->bloch_B = y.B;
   c->E = y.E;
   c->nb = sys_nb(b, y);
-  c->panel_ctas_param = y.lane > 0 ? 1 : 0;
+  c->panel_ctas_param = 0;
   c->Kmat = m.K;
   c->rmesh = m.r;
   c->fa = m.fa;
@@ -150,9 +151,13 @@ int enqueue_all(rmat_batch b, void* const* U) {
   return RMAT_OK;
 }
 
-// Largest system a lane takes: a single panel CTA keeps N rows x 32 columns in
-// shared memory (panel_kernel's staged variant, within the 227 KB opt-in limit).
-int lane_cap(rmat_batch b) { return b->precision == RMAT_C128 ? 416 : 832; }
+// A lane takes a system whose panels fit one thread block cluster's shared memory
+// (the cluster panel), so no kernel of a lane waits on CTAs it cannot see.
+bool lane_fits(rmat_batch b, const BatchSys& y) {
+  BatchSys t = y;
+  t.lane = 1;
+  return panel_cluster_fits(b->parent, b->precision, y.N, sys_nb(b, t)) > 0;
+}
 
 // Assign systems to the serial phase or to lanes (longest first onto the least
 // loaded lane) and size every lane context for its largest system.
@@ -168,8 +173,8 @@ int plan(rmat_batch b) {
   std::vector<double> load(b->lanes + 1, 0.0);
   for (int s : order) {
     BatchSys& y = b->sys[s];
-    // lanes hold single-CTA panels whose rows x 32 columns fit in shared memory
-    if (y.N > std::min(b->split_n, lane_cap(b)) || b->lanes == 0) {
+    // lanes hold systems whose panels fit one cluster
+    if (y.N > b->split_n || b->lanes == 0 || !lane_fits(b, y)) {
       y.lane = 0;
     } else {
       int best = 1;
@@ -194,7 +199,7 @@ int plan(rmat_batch b) {
     c->ld = (int)round_up(maxN, 32);
     c->nrhs = maxc;
     c->kind = 1;
-    c->nb = 32;
+    c->nb = 64;
     RMAT_CHECK(ctx_reserve(c, false));
     for (const BatchSys& y : b->sys)
       if (y.lane == l) RMAT_CHECK(perm_reserve(c, c->perm_main, y.N, sys_nb(b, y)));
@@ -461,7 +466,7 @@ int rmat_batch_tune(rmat_batch b, void* const* U_dev, int* lanes, int* split_n) 
   const std::string key = tune_key(b);
   int bl = b->lanes, bs = b->split_n;
   if (!cache_lookup(key, &bl, &bs)) {
-    const int cand[][2] = {{0, 0}, {4, 416}, {8, 416}, {8, 832}, {16, 832}};
+    const int cand[][2] = {{0, 0}, {8, 1024}, {8, 8192}, {16, 1024}, {16, 8192}};
     double best = INFINITY;
     for (const auto& cd : cand) {
       b->lanes = cd[0];

@@ -213,6 +213,7 @@ struct TcScales {
   int rs_div;
   const float* colscale;
   const float* cscal;
+  const int* skip;  // nonzero *skip: the launch does nothing (a stopped refinement)
 };
 
 template <int BN, int KIND>
@@ -221,6 +222,7 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
                  int ax0, int rowA0, int bx0, int rowB0, TcScales sc, int* __restrict__ err) {
   using Cfg = TcCfg<BN>;
   constexpr int KSTEP = KIND == 0 ? 8 : 16;  // K elements per 32-byte operand row
+  if (sc.skip && *sc.skip) return;           // before any barrier or TMEM allocation
   constexpr uint32_t B_PLANE_BYTES = Cfg::B_PLANE, STAGE_BYTES = Cfg::STAGE;
   constexpr int NBUF = Cfg::NBUF;
   extern __shared__ unsigned char smem_raw[];
@@ -580,7 +582,7 @@ int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n) {
   if (reinterpret_cast<void*>(A) != c->C || ld != c->ld) return RMAT_ESTATE;
   RMAT_CHECK(tc_prepare(c, n, c->nrhs + (c->nrhs & 1)));
   TcCache& g_tc = tc_cache(c);
-  TcScales sc{nullptr, 1, nullptr, nullptr};
+  TcScales sc{nullptr, 1, nullptr, nullptr, nullptr};
   if (rmat_plane_fmt(c->precision) == 1) sc.cscal = c->uscale + k0 / jb;  // jb = nb here
   return launch_tc<TC_BN>(c, g_tc.upd, k0 + jb, k0 + jb, rest, rest, jb, k0, k0 + jb, 0, k0 + jb,
                           sc, true);
@@ -592,7 +594,7 @@ int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int a
                     const float* rowscale, int rs_div) {
   RMAT_CHECK(tc_prepare(c, n, nrhs));
   TcCache& g_tc = tc_cache(c);
-  TcScales sc{nullptr, 1, nullptr, nullptr};
+  TcScales sc{nullptr, 1, nullptr, nullptr, c->skip};
   if (rmat_plane_fmt(c->precision) == 1) {
     sc.rowscale = rowscale;
     sc.rs_div = rs_div;

@@ -219,6 +219,145 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
   }
 }
 
+// Cluster variant of the panel for M rows that fit the shared memory of one thread
+// block cluster (up to 16 CTAs): the same partial pivoting (largest |Re|+|Im|, first
+// row on ties), with the per-column exchange through distributed shared memory and
+// the hardware cluster barrier instead of a grid barrier in global memory.  Each CTA
+// publishes its candidate (value, row, row contents) and, if it holds row gj, that
+// row, in parity-double-buffered shared slots; one cluster barrier per column.
+template <class T>
+__global__ void __launch_bounds__(PANEL_THREADS)
+panel_cluster_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb,
+                     int* __restrict__ ipiv, int* __restrict__ stat, int rpc, int ldr) {
+  namespace cg = cooperative_groups;
+  using C2 = cplx<T>;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks(), rank = (int)cluster.block_rank(), tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = PANEL_THREADS / 32;
+  const int r_lo = k0 + rank * rpc;
+  const int r_hi = min(k0 + (rank + 1) * rpc, n);
+  __shared__ T s_v[32];
+  __shared__ int s_i[32];
+  __shared__ int s_win, s_zero;
+  __shared__ T c_v[2];    // published candidate value (parity buffers)
+  __shared__ int c_i[2];  // published candidate row
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* s_prow = reinterpret_cast<C2*>(smem_raw);  // [jb] pivot row
+  C2* s_trow = s_prow + jb;                      // [jb] old row gj
+  C2* crow = s_trow + jb;                        // [2][jb] published candidate row
+  C2* trowp = crow + 2 * jb;                     // [2][jb] published row gj (its holder)
+  C2* s_l = trowp + 2 * jb;                      // [rpc]
+  C2* s_rows = s_l + rpc;                        // [rpc][ldr]
+  auto at = [&](int r) -> C2* { return s_rows + (size_t)(r - r_lo) * ldr; };
+  for (int e = tid; e < (r_hi - r_lo) * jb; e += PANEL_THREADS) {
+    const int rr = e / jb, cc = e - rr * jb;
+    s_rows[(size_t)rr * ldr + cc] = A[(size_t)(r_lo + rr) * ld + k0 + cc];
+  }
+  __syncthreads();
+  for (int j = 0; j < jb; ++j) {
+    const int gj = k0 + j, par = j & 1;
+    T best = (T)-1;
+    int bidx = INT_MAX;
+    for (int r = max(r_lo, gj) + tid; r < r_hi; r += PANEL_THREADS) {
+      const T m = cabs1<T>(at(r)[j]);
+      if (m > best) { best = m; bidx = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if (lane == 0) { s_v[warp] = best; s_i[warp] = bidx; }
+    if (gj >= r_lo && gj < r_hi && warp > 0) {
+      const C2* src = at(gj);
+      for (int c = tid - 32; c < jb; c += PANEL_THREADS - 32) trowp[par * jb + c] = src[c];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nwarp ? s_v[lane] : (T)-1;
+      bidx = lane < nwarp ? s_i[lane] : INT_MAX;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+      }
+      if (lane == 0) { c_v[par] = best; c_i[par] = bidx; }
+      if (bidx != INT_MAX)
+        for (int c = lane; c < jb; c += 32) crow[par * jb + c] = at(bidx)[c];
+    }
+    cluster.sync();  // every CTA's candidate and row gj are published
+    if (warp == 0) {
+      best = (T)-1;
+      bidx = INT_MAX;
+      int wr = 0;
+      if (lane < CS) {
+        best = *cluster.map_shared_rank(&c_v[par], lane);
+        bidx = *cluster.map_shared_rank(&c_i[par], lane);
+        wr = lane;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, wr, o);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; wr = orr; }
+      }
+      const C2* wrow = cluster.map_shared_rank(crow + par * jb, wr);
+      for (int c = lane; c < jb; c += 32) s_prow[c] = wrow[c];
+      if (lane == 0) {
+        s_win = bidx;
+        s_zero = !(best > (T)0);
+      }
+    } else {
+      const int hr = min((gj - k0) / rpc, CS - 1);  // the CTA holding row gj
+      const C2* hrow = cluster.map_shared_rank(trowp + par * jb, hr);
+      for (int c = tid - 32; c < jb; c += PANEL_THREADS - 32) s_trow[c] = hrow[c];
+    }
+    __syncthreads();
+    const int p = (s_win >= gj && s_win < n) ? s_win : gj;
+    if (rank == 0 && tid == 0) {
+      ipiv[gj] = p;
+      if (s_zero) atomicCAS(&stat[ST_INFO], 0, gj + 1);
+    }
+    if (p != gj) {
+      if (gj >= r_lo && gj < r_hi)
+        for (int c = tid; c < jb; c += PANEL_THREADS) at(gj)[c] = s_prow[c];
+      if (p >= r_lo && p < r_hi)
+        for (int c = tid; c < jb; c += PANEL_THREADS) at(p)[c] = s_trow[c];
+    }
+    __syncthreads();
+    if (s_zero) continue;  // exactly zero column: no scaling, no update (LAPACK)
+    const C2 piv = s_prow[j];
+    const int r_first = max(r_lo, gj + 1);
+    for (int r = r_first + tid; r < r_hi; r += PANEL_THREADS) {
+      C2* ar = at(r);
+      const C2 lm = cdiv<T>(ar[j], piv);
+      ar[j] = lm;
+      s_l[r - r_lo] = lm;
+    }
+    __syncthreads();
+    if (j + 1 < jb) {
+      for (int r = r_first + warp; r < r_hi; r += nwarp) {
+        const C2 lm = s_l[r - r_lo];
+        C2* Ar = at(r);
+        for (int c = j + 1 + lane; c < jb; c += 32) {
+          C2 x = Ar[c];
+          csub_mul<T>(x, lm, s_prow[c]);
+          Ar[c] = x;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  cluster.sync();  // no CTA leaves while a peer may still read its published slots
+  for (int e = tid; e < (r_hi - r_lo) * jb; e += PANEL_THREADS) {
+    const int rr = e / jb, cc = e - rr * jb;
+    A[(size_t)(r_lo + rr) * ld + k0 + cc] = s_rows[(size_t)rr * ldr + cc];
+  }
+}
+
 // ---- G3: row interchanges on the trailing columns + U12 = L11^-1 A12 ------
 // (apply_perm_kernel and trsm_block_rhs_kernel below, on the trailing columns
 // viewed as right-hand sides)
@@ -335,7 +474,8 @@ split_block_kernel(const float2* __restrict__ S, int lds, int jb, int ncols, voi
 // column's scale (fmt 1) is a warp reduction; ycs[c] = 1/s.
 __global__ void __launch_bounds__(256)
 split_y_kernel(const float2* __restrict__ S, int lds, int jb, int ncols, void* __restrict__ Y,
-               size_t yplane, int fmt, float* __restrict__ ycs) {
+               size_t yplane, int fmt, float* __restrict__ ycs, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   const int c = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (c >= ncols) return;
   const int kpad = (jb + 31) / 32 * 32;
@@ -356,8 +496,10 @@ constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
 template <class T>
 __global__ void __launch_bounds__(256)
 cgemm_sub_kernel(int M, int N, int K, const cplx<T>* __restrict__ A, int lda,
-                 const cplx<T>* __restrict__ B, int ldb, cplx<T>* __restrict__ C, int ldc) {
+                 const cplx<T>* __restrict__ B, int ldb, cplx<T>* __restrict__ C, int ldc,
+                 const int* __restrict__ skip) {
   using C2 = cplx<T>;
+  if (skip && *skip) return;
   __shared__ C2 As[GB_K][GB_M + 1];
   __shared__ C2 Bs[GB_K][GB_N];
   const int tid = threadIdx.x;
@@ -423,8 +565,9 @@ cgemm_sub_kernel(int M, int N, int K, const cplx<T>* __restrict__ A, int lda,
 template <class T, bool LOWER>
 __global__ void __launch_bounds__(256)
 trsm_block_rhs_kernel(const cplx<T>* __restrict__ A, int ld, int k0, int jb,
-                      cplx<T>* __restrict__ B, int ldb, int nrhs) {
+                      cplx<T>* __restrict__ B, int ldb, int nrhs, const int* __restrict__ skip) {
   using C2 = cplx<T>;
+  if (skip && *skip) return;
   extern __shared__ unsigned char smem_raw[];
   C2* xs = reinterpret_cast<C2*>(smem_raw);  // [jb][32]
   C2* Ls = xs + (size_t)jb * 32;               // [jb][jb + 1]
@@ -503,8 +646,9 @@ solve_block_kernel(const cplx<T>* __restrict__ A, int ld, int k0, cplx<T>* __res
                    int ldb, int ncols, int nbp, const int* __restrict__ prow,
                    const int* __restrict__ psrc, const int* __restrict__ pcnt,
                    void* __restrict__ Y, size_t yplane, size_t bstride, int fmt,
-                   float* __restrict__ ycs) {
+                   float* __restrict__ ycs, const int* __restrict__ skip) {
   using C2 = cplx<T>;
+  if (skip && *skip) return;
   if (bstride) {  // batched over diagonal blocks (inversion): block blockIdx.y, B rows 0..JB-1
     k0 = blockIdx.y * nbp;
     B += (size_t)blockIdx.y * bstride - (size_t)k0 * ldb;
@@ -633,8 +777,9 @@ __global__ void __cluster_dims__(1, JB / 16, 1) __launch_bounds__(256)
 apply_inv_kernel(const float2* __restrict__ Dinv, int k0, int nbp, float2* __restrict__ B,
                  int ldb, int ncols, const int* __restrict__ prow, const int* __restrict__ psrc,
                  const int* __restrict__ pcnt, void* __restrict__ Yp, size_t yplane, int fmt,
-                 float* __restrict__ ycs) {
+                 float* __restrict__ ycs, const int* __restrict__ skip) {
   namespace cg = cooperative_groups;
+  if (skip && *skip) return;  // uniform over the cluster: no CTA reaches a cluster barrier
   constexpr int CW = 16;          // columns per cluster
   constexpr int SL = 32;          // permutation slots gathered per CTA (2*JB over JB/16 CTAs)
   constexpr int LDD = JB + 2;     // 16-byte aligned rows; the two rows a warp reads use different banks
@@ -820,8 +965,9 @@ template <class T>
 __global__ void __launch_bounds__(256)
 apply_perm_kernel(cplx<T>* __restrict__ B, int ldb, int ncols, int k0, int nb, int jb,
                   const int* __restrict__ prow, const int* __restrict__ pidx,
-                  const int* __restrict__ pcnt) {
+                  const int* __restrict__ pcnt, const int* __restrict__ skip) {
   using C2 = cplx<T>;
+  if (skip && *skip) return;
   extern __shared__ unsigned char smem_raw[];
   C2* vals = reinterpret_cast<C2*>(smem_raw);                      // [2*nb][32]
   int* rows = reinterpret_cast<int*>(vals + (size_t)2 * nb * 32);  // [2*nb]
@@ -862,7 +1008,7 @@ int gemm_sub(rmat_ctx c, int M, int N, int K, const cplx<T>* A, int lda, const c
              int ldb, cplx<T>* C, int ldc) {
   if (M <= 0 || N <= 0 || K <= 0) return RMAT_OK;
   dim3 grid(ceil_div(N, GB_N), ceil_div(M, GB_M));
-  cgemm_sub_kernel<T><<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, B, ldb, C, ldc);
+  cgemm_sub_kernel<T><<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, B, ldb, C, ldc, c->skip);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;
@@ -890,8 +1036,100 @@ size_t panel_smem(int rpc, int ldr, bool in_smem) {
 }
 
 template <class T>
+size_t panel_cluster_smem(int jb, int rpc, int ldr) {
+  return (size_t)(6 * jb + rpc + (size_t)rpc * ldr) * sizeof(cplx<T>);
+}
+
+// Largest cluster the cluster panel may use on this device (16 needs the
+// non-portable size opt-in; 8 is portable); 0 if cluster launches are unavailable.
+template <class T>
+int panel_cluster_max(rmat_ctx c) {
+  static int cs_max[2] = {-1, -1};
+  int& m = cs_max[sizeof(T) == 8];
+  if (m >= 0) return m;
+  m = 0;
+  const int smem = (int)panel_smem_limit(c);
+  if (cudaFuncSetAttribute(panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem) != cudaSuccess ||
+      cudaFuncSetAttribute(panel_cluster_kernel<T>,
+                           cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return m;
+  }
+  for (int cs = 16; cs >= 1; cs /= 2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(PANEL_THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, panel_cluster_kernel<T>, &cfg) == cudaSuccess &&
+        nclusters > 0) {
+      m = cs;
+      break;
+    }
+    cudaGetLastError();
+  }
+  return m;
+}
+
+// Cluster size for a panel of M rows: about 128 rows per CTA, up to the device's
+// maximum; 0 when the rows do not fit the cluster's shared memory (grid variant).
+template <class T>
+int panel_cluster_size(rmat_ctx c, int M, int jb, int* rpc_out, int* ldr_out) {
+  const int cmax = panel_cluster_max<T>(c);
+  if (cmax == 0) return 0;
+  int cs = 1;
+  while (cs < cmax && ceil_div(M, cs) > 128) cs *= 2;
+  const int rpc = ceil_div(M, cs);
+  const size_t limit = panel_smem_limit(c);
+  int ldr = jb + 1;
+  if (panel_cluster_smem<T>(jb, rpc, ldr) > limit) ldr = jb;
+  if (panel_cluster_smem<T>(jb, rpc, ldr) > limit) return 0;
+  *rpc_out = rpc;
+  *ldr_out = ldr;
+  return cs;
+}
+
+int panel_cluster_fits(rmat_ctx c, int precision, int M, int jb) {
+  int rpc = 0, ldr = 0;
+  return precision == RMAT_C128 ? panel_cluster_size<double>(c, M, jb, &rpc, &ldr)
+                                : panel_cluster_size<float>(c, M, jb, &rpc, &ldr);
+}
+
+template <class T>
 int launch_panel(rmat_ctx c, cplx<T>* A, int ld, int k0, int n, int jb, int* ipiv) {
   const int M = n - k0;
+  if (c->panel_ctas_param <= 0) {  // rows fit one cluster's shared memory: cluster panel
+    int rpc = 0, ldr = 0;
+    const int cs = panel_cluster_size<T>(c, M, jb, &rpc, &ldr);
+    if (cs > 0) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(PANEL_THREADS);
+      cfg.dynamicSmemBytes = panel_cluster_smem<T>(jb, rpc, ldr);
+      cfg.stream = c->stream;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      KTimer kt(c, KT_PANEL);
+      RMAT_CU(cudaLaunchKernelEx(&cfg, panel_cluster_kernel<T>, A, ld, k0, n, jb, ipiv, c->dstat,
+                                 rpc, ldr));
+      kt.end();
+      c->launches++;
+      return RMAT_OK;
+    }
+  }
   const int P = panel_ctas_for(c, M);
   const int rpc = ceil_div(M, P);
   int ldr = jb + 1;
@@ -943,7 +1181,7 @@ int set_trsm_attrs() {
 template <class T>
 int apply_perm(rmat_ctx c, const LUPerm& pm, cplx<T>* B, int ldb, int ncols, int k0, int nb, int jb) {
   apply_perm_kernel<T><<<ceil_div(ncols, 32), 256, perm_smem<T>(nb), c->stream>>>(
-      B, ldb, ncols, k0, nb, jb, pm.rows, pm.idx, pm.cnt);
+      B, ldb, ncols, k0, nb, jb, pm.rows, pm.idx, pm.cnt, c->skip);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;
@@ -963,7 +1201,7 @@ int launch_solve_block(rmat_ctx c, const LUPerm* pm, const cplx<T>* A, int ld, i
   solve_block_kernel<T, LOWER, JB><<<ceil_div(ncols, 32), 256, smem, c->stream>>>(
       A, ld, k0, B, ldb, ncols, nb, pm ? pm->rows : nullptr, pm ? pm->src : nullptr,
       pm ? pm->cnt : nullptr, Y, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB, (size_t)0,
-      rmat_plane_fmt(c->precision), Y ? c->ycs : nullptr);
+      rmat_plane_fmt(c->precision), Y ? c->ycs : nullptr, c->skip);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;
@@ -1006,9 +1244,9 @@ int invert_diag_blocks(rmat_ctx c, const float2* A, int ld, int n, int nb) {
   }
   const dim3 grid(JB / 32, nfull);
   solve_block_kernel<float, true, JB><<<grid, 256, smem, c->stream>>>(
-      A, ld, 0, Linv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per, 0, nullptr);
+      A, ld, 0, Linv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per, 0, nullptr, nullptr);
   solve_block_kernel<float, false, JB><<<grid, 256, smem, c->stream>>>(
-      A, ld, 0, Uinv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per, 0, nullptr);
+      A, ld, 0, Uinv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per, 0, nullptr, nullptr);
   c->launches += 2;
   RMAT_CU(cudaGetLastError());
   c->inv_blocks = nfull;
@@ -1032,7 +1270,7 @@ int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb,
   apply_inv_kernel<JB><<<dim3(ceil_div(ncols, 16), JB / 16), 256, smem, c->stream>>>(
       D, k0, nb, B, ldb, ncols, pm ? pm->rows : nullptr, pm ? pm->src : nullptr,
       pm ? pm->cnt : nullptr, Yp, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB, rmat_plane_fmt(c->precision),
-      c->ycs);
+      c->ycs, c->skip);
   kt.end();
   c->launches++;
   RMAT_CU(cudaGetLastError());
@@ -1070,7 +1308,7 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
     if (!fused) {
       RMAT_CHECK(apply_perm<T>(c, pm, A + k0 + jb, ld, rest, k0, nb, jb));
       trsm_block_rhs_kernel<T, true><<<ceil_div(rest, 32), 256, trsm_smem<T>(jb), c->stream>>>(
-          A, ld, k0, jb, A + k0 + jb, ld, rest);
+          A, ld, k0, jb, A + k0 + jb, ld, rest, nullptr);
       c->launches++;
     }
     RMAT_CU(cudaGetLastError());
@@ -1137,7 +1375,7 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
   auto split_y = [&](int row0, int jb) -> int {
     split_y_kernel<<<ceil_div(nrhs, 8), 256, 0, c->stream>>>(
         reinterpret_cast<const float2*>(B) + (size_t)row0 * ldb, ldb, jb, nrhs, c->Ypl, yplane, fmt,
-        c->ycs);
+        c->ycs, c->skip);
     c->launches++;
     RMAT_CU(cudaGetLastError());
     return RMAT_OK;
@@ -1160,7 +1398,7 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     if (!fused) {
       RMAT_CHECK(apply_perm<T>(c, pm, B, ldb, nrhs, k0, nb, jb));
       trsm_block_rhs_kernel<T, true><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B,
-                                                                              ldb, nrhs);
+                                                                              ldb, nrhs, c->skip);
       c->launches++;
       RMAT_CU(cudaGetLastError());
       if (need_y) RMAT_CHECK(split_y(k0, jb));
@@ -1190,7 +1428,7 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     }
     if (!fused) {
       trsm_block_rhs_kernel<T, false><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B,
-                                                                               ldb, nrhs);
+                                                                               ldb, nrhs, c->skip);
       c->launches++;
       RMAT_CU(cudaGetLastError());
       if (need_y) RMAT_CHECK(split_y(k0, jb));

@@ -20,7 +20,9 @@ namespace {
 // r = Phi - K X  (one CTA per (channel, 32 right-hand sides); warps over mesh rows)
 __global__ void __launch_bounds__(256)
 resid_kinetic_kernel(double2* __restrict__ R, const double2* __restrict__ X, int nrhs, int nlag,
-                     const double* __restrict__ K, const double* __restrict__ fa) {
+                     const double* __restrict__ K, const double* __restrict__ fa,
+                     const int* __restrict__ skip) {
+  if (skip && *skip) return;
   const int al = blockIdx.y;
   const int be = blockIdx.x * 32 + (threadIdx.x & 31);
   const int warp = threadIdx.x >> 5;
@@ -57,7 +59,8 @@ __device__ __forceinline__ void dmma(double& d0, double& d1, double a, double b)
 
 __global__ void __launch_bounds__(256)
 resid_coupling_kernel(double2* __restrict__ R, const double2* __restrict__ X, int nrhs, int nlag,
-                      int nch, const double2* __restrict__ W) {
+                      int nch, const double2* __restrict__ W, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   __shared__ double Wr[RC_K][RC_LD], Wm[RC_K][RC_LD];  // W[a0 + a][k0 + k] -> [k][a]
   __shared__ double Xr[RC_K][RC_LD], Xm[RC_K][RC_LD];  // X[(k0 + k, i)][b0 + b] -> [k][b]
   const int i = blockIdx.z;
@@ -137,7 +140,9 @@ resid_coupling_kernel(double2* __restrict__ R, const double2* __restrict__ X, in
 template <class T>
 __global__ void resid_norm_convert_kernel(const double2* __restrict__ R, size_t total, int nrhs,
                                           const double* __restrict__ D, cplx<T>* __restrict__ Bw,
-                                          unsigned long long* __restrict__ red) {
+                                          unsigned long long* __restrict__ red,
+                                          const int* __restrict__ skip) {
+  if (skip && *skip) return;
   double m = 0.0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -302,9 +307,11 @@ int launch_residual(rmat_ctx c, double*) {
   RMAT_CU(cudaMemsetAsync(c->red, 0, sizeof(unsigned long long), c->stream));
   if (c->kind == 1) {
     dim3 gk(ceil_div(nrhs, 32), c->nch);
-    resid_kinetic_kernel<<<gk, 256, 0, c->stream>>>(c->Rres, c->X, nrhs, c->nlag, c->Kmat, c->fa);
+    resid_kinetic_kernel<<<gk, 256, 0, c->stream>>>(c->Rres, c->X, nrhs, c->nlag, c->Kmat, c->fa,
+                                                    c->skip);
     dim3 gc(ceil_div(nrhs, RC_T), ceil_div(c->nch, RC_T), c->nlag);
-    resid_coupling_kernel<<<gc, 256, 0, c->stream>>>(c->Rres, c->X, nrhs, c->nlag, c->nch, c->Wpt);
+    resid_coupling_kernel<<<gc, 256, 0, c->stream>>>(c->Rres, c->X, nrhs, c->nlag, c->nch, c->Wpt,
+                                                     c->skip);
     c->launches += 2;
   } else {
     RMAT_CU(cudaMemcpyAsync(c->Rres, c->B64, total * sizeof(double2), cudaMemcpyDeviceToDevice,
@@ -315,10 +322,10 @@ int launch_residual(rmat_ctx c, double*) {
   const double* D = c->equil ? c->Dsc : nullptr;
   if (c->precision == RMAT_C128)
     resid_norm_convert_kernel<double><<<grid_for(c, total), 256, 0, c->stream>>>(
-        c->Rres, total, nrhs, D, reinterpret_cast<double2*>(c->Bw), c->red);
+        c->Rres, total, nrhs, D, reinterpret_cast<double2*>(c->Bw), c->red, c->skip);
   else
     resid_norm_convert_kernel<float><<<grid_for(c, total), 256, 0, c->stream>>>(
-        c->Rres, total, nrhs, D, reinterpret_cast<float2*>(c->Bw), c->red);
+        c->Rres, total, nrhs, D, reinterpret_cast<float2*>(c->Bw), c->red, c->skip);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   kt.end();

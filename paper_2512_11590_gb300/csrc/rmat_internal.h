@@ -57,6 +57,9 @@ struct rmat_ctx_s {
   long long spin_limit = 20000000LL;   // ~ seconds of polling
   int timing = 0;
   int smem_optin = 232448;  // cudaDeviceProp::sharedMemPerBlockOptin
+  // device flag read by the refinement-loop kernels: nonzero = this system's
+  // device-side refinement has stopped, so the launch returns at once (null: run)
+  const int* skip = nullptr;
   int equil_param = -1;   // -1: default (on for complex64 paths), 0 off, 1 on
   bool equil = false;     // symmetric diagonal equilibration active for this problem
 
@@ -151,6 +154,8 @@ int perm_reserve(rmat_ctx c, LUPerm& pm, int n, int nb);
 // gemm_tc.cu
 int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n);
 // solve update: rows [row0, row0+M) of the solve buffer Bw (ld = nrhs) -= F(ay0.., k0..k0+jb) * Y
+// Cluster size the cluster panel would use for M rows of width jb (0: does not fit).
+int panel_cluster_fits(rmat_ctx c, int precision, int M, int jb);
 int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n,
                     const float* rowscale, int rs_div);
 int tc_prepare(rmat_ctx c, int n, int nrhs);

@@ -9,7 +9,7 @@ from rmat_gpu import relerr, run_problem
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 1e-10, 2: 1e-10}
+TOL = {0: 1e-12, 1: 1e-10, 2: 1e-10, 3: 1e-10}
 
 
 def mixed_problems():
@@ -35,8 +35,8 @@ def g():
     return mod
 
 
-@pytest.mark.parametrize("prec", [1, 0])
-@pytest.mark.parametrize("lanes,split,graph", [(0, 0, 1), (4, 832, 1), (4, 832, 0)])
+@pytest.mark.parametrize("prec", [3, 1, 0])
+@pytest.mark.parametrize("lanes,split,graph", [(0, 0, 1), (4, 832, 1), (4, 832, 0), (8, 8192, 1)])
 def test_batch_matches_oracle(g, cases, prec, lanes, split, graph):
     import torch
     torch.cuda.set_device(0)

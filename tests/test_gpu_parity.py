@@ -177,3 +177,17 @@ def test_fp16_planes_far_outside_fp16_range(g, ctx, scale_a, scale_b):
     out = run_dense(ctx, A, B, 3, max_refine=30, tol=1e-15, nb=128)
     assert out["iters"] >= 1
     assert relerr(out["X"], Xe) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [3, 0])
+def test_grid_panel_variant(g, ctx, prec):
+    """A fixed panel CTA count selects the cooperative grid-barrier panel (used for
+    panels taller than one cluster's shared memory); same results as the default."""
+    p = cp.config2(16)
+    ref = truth(p, "c2-16")
+    g.rmat_set_param(ctx, g.RMAT_PARAM_PANEL_CTAS, 16)
+    try:
+        out = run_problem(ctx, p, prec, max_refine=30, tol=1e-14)
+    finally:
+        g.rmat_set_param(ctx, g.RMAT_PARAM_PANEL_CTAS, 0)
+    assert relerr(out["U"], ref["U"]) < TOL[prec]
