@@ -70,107 +70,221 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
   }
   __syncthreads();
 
-  for (int j = 0; j < jb; ++j) {
-    const int gj = k0 + j;
-    const int par = j & 1;
-    // ---- phase A: local candidate for column gj among own rows >= gj ----
-    T best = (T)-1;
-    int bidx = INT_MAX;
-    for (int r = max(r_lo, gj) + tid; r < r_hi; r += PANEL_THREADS) {
-      T m = cabs1<T>(at(r)[j]);
-      if (m > best) { best = m; bidx = r; }
-    }
+  // Column lookahead: right after column j's multipliers, only column j+1 of the
+  // rank-1 update is applied and its local candidate found; the two rows published
+  // before the barrier (the candidate and row gj+1) are brought fully up to date,
+  // and the rest of column j's update runs while the grid barrier is in flight.
+  __shared__ T s_cb;
+  __shared__ int s_ci, s_pre0, s_pre1, s_zprev;
+  // block-wide (best, bidx) -> s_cb, s_ci (first row on ties)
+  auto block_cand = [&](T best, int bidx) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      T ob = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
       if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
     }
     if (lane == 0) { s_v[warp] = best; s_i[warp] = bidx; }
-    // the current row gj travels to the pivot row's owner through trow
-    if (gj >= r_lo && gj < r_hi && warp > 0) {
-      const C2* src = at(gj);
-      for (int c = tid - 32; c < jb; c += PANEL_THREADS - 32) trow[(size_t)par * RMAT_MAX_NB + c] = src[c];
-    }
     __syncthreads();
     if (warp == 0) {
       best = lane < nwarp ? s_v[lane] : (T)-1;
       bidx = lane < nwarp ? s_i[lane] : INT_MAX;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
         if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
       }
-      if (lane == 0) {
-        cval[par * RMAT_MAX_PANEL_CTAS + cta] = best;
-        ps.cidx[par * RMAT_MAX_PANEL_CTAS + cta] = bidx;
+      if (lane == 0) { s_cb = best; s_ci = bidx; }
+    }
+    __syncthreads();
+  };
+  // publish column jj's candidate (row s_ci) and row k0+jj, then arrive at barrier jj
+  // complex64: the candidate (value, row, column generation) is one 64-bit record
+  // per CTA and parity, stored with release semantics after the CTA's rows: the
+  // records are the barrier, and the winner is known as soon as all have arrived.
+  // complex128: value/row in cval/cidx and an arrival counter.
+  unsigned long long* rec = reinterpret_cast<unsigned long long*>(ps.cval);
+  auto publish_arrive = [&](int jj) {
+    const int pp = jj & 1, gg = k0 + jj;
+    if (warp == 0) {
+      if (sizeof(T) == 8 && lane == 0) {
+        cval[pp * RMAT_MAX_PANEL_CTAS + cta] = s_cb;
+        ps.cidx[pp * RMAT_MAX_PANEL_CTAS + cta] = s_ci;
       }
-      // the CTA's candidate row, published for whichever CTA's row wins
-      if (bidx != INT_MAX) {
-        C2* slot = crow + ((size_t)par * RMAT_MAX_PANEL_CTAS + cta) * RMAT_MAX_NB;
-        const C2* src = at(bidx);
+      if (s_ci != INT_MAX) {
+        C2* slot = crow + ((size_t)pp * RMAT_MAX_PANEL_CTAS + cta) * RMAT_MAX_NB;
+        const C2* src = at(s_ci);
         for (int c = lane; c < jb; c += 32) slot[c] = src[c];
       }
+    } else if (gg >= r_lo && gg < r_hi) {
+      const C2* src = at(gg);
+      for (int c = tid - 32; c < jb; c += PANEL_THREADS - 32) trow[(size_t)pp * RMAT_MAX_NB + c] = src[c];
     }
-    // ---- grid barrier (bounded spin): release-add, acquire-poll ----
     __syncthreads();
     if (tid == 0) {
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ps.bar) : "memory");
-      const unsigned target = (unsigned)(j + 1) * (unsigned)P;
-      long long polls = 0;
-      while (ld_acquire_gpu(ps.bar) < target) {
-        if (++polls > spin_limit) {
-          atomicExch(&stat[ST_TIMEOUT], 1);
-          s_abort = 1;
-          break;
+      if constexpr (sizeof(T) == 4) {
+        const unsigned long long v =
+            ((unsigned long long)__float_as_uint((float)(s_cb > (T)0 ? s_cb : (T)0)) << 32) |
+            ((unsigned long long)(jj + 1) << 18) | (unsigned long long)(s_ci == INT_MAX ? 0x3FFFF : s_ci);
+        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(rec + pp * RMAT_MAX_PANEL_CTAS + cta),
+                     "l"(v)
+                     : "memory");
+      } else {
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ps.bar) : "memory");
+      }
+    }
+  };
+
+  {  // column 0: nothing pending
+    T best = (T)-1;
+    int bidx = INT_MAX;
+    for (int r = r_lo + tid; r < r_hi; r += PANEL_THREADS) {
+      const T m = cabs1<T>(at(r)[0]);
+      if (m > best) { best = m; bidx = r; }
+    }
+    if (tid == 0) { s_pre0 = -1; s_pre1 = -1; s_zprev = 1; }
+    block_cand(best, bidx);
+    publish_arrive(0);
+  }
+
+  for (int j = 0; j < jb; ++j) {
+    const int gj = k0 + j;
+    const int par = j & 1;
+    // ---- deferred: column j-1's update of columns j+1.. (rows > gj-1, not published) ----
+    if (!s_zprev && j + 1 < jb) {
+      const int p0 = s_pre0, p1 = s_pre1;
+      for (int r = max(r_lo, gj) + warp; r < r_hi; r += nwarp) {
+        if (r == p0 || r == p1) continue;
+        const C2 lm = s_l[r - r_lo];
+        C2* Ar = at(r);
+        for (int c = j + 1 + lane; c < jb; c += 32) {
+          C2 x = Ar[c];
+          csub_mul<T>(x, lm, s_prow[c]);
+          Ar[c] = x;
         }
       }
     }
-    __syncthreads();
-    if (s_abort) return;
-    // ---- phase B: global winner (warp 0), old row gj prefetched (other warps) ----
-    if (warp == 0) {
-      best = (T)-1;
-      bidx = INT_MAX;
-      int bc = -1;
-      // all candidates requested before any is compared: one L2 round trip
-      constexpr int QPL = RMAT_MAX_PANEL_CTAS / 32;
-      T cv[QPL];
-      int ci[QPL];
+    if constexpr (sizeof(T) == 4) {
+      // ---- barrier j = all P records of parity j&1 carry generation j+1 (bounded) ----
+      if (warp == 0) {
+        constexpr int QPL = RMAT_MAX_PANEL_CTAS / 32;
+        unsigned long long r[QPL];
+        long long polls = 0;
+        bool ok = false;
+        for (;;) {
+          bool mine = true;
 #pragma unroll
-      for (int u = 0; u < QPL; ++u) {
-        const int q = lane + 32 * u;
-        cv[u] = q < P ? ld_cg(cval + par * RMAT_MAX_PANEL_CTAS + q) : (T)-1;
-        ci[u] = q < P ? ld_cg(ps.cidx + par * RMAT_MAX_PANEL_CTAS + q) : INT_MAX;
-      }
-#pragma unroll
-      for (int u = 0; u < QPL; ++u)
-        if (cv[u] > best || (cv[u] == best && ci[u] < bidx)) {
-          best = cv[u];
-          bidx = ci[u];
-          bc = lane + 32 * u;
+          for (int u = 0; u < QPL; ++u) {
+            const int q = lane + 32 * u;
+            r[u] = 0ull;
+            if (q < P)
+              asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];"
+                           : "=l"(r[u])
+                           : "l"(rec + par * RMAT_MAX_PANEL_CTAS + q)
+                           : "memory");
+            if (q < P && (int)((r[u] >> 18) & 0x3FFF) != j + 1) mine = false;
+          }
+          if (__all_sync(0xffffffffu, mine)) { ok = true; break; }
+          if (++polls > spin_limit) break;
         }
+        if (!ok) {
+          if (lane == 0) {
+            atomicExch(&stat[ST_TIMEOUT], 1);
+            s_abort = 1;
+          }
+        } else {
+          asm volatile("fence.acq_rel.gpu;" ::: "memory");
+          float best = -1.f;
+          int bidx = INT_MAX, bc = -1;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-        int oc = __shfl_xor_sync(0xffffffffu, bc, o);
-        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; bc = oc; }
+          for (int u = 0; u < QPL; ++u) {
+            const int q = lane + 32 * u;
+            if (q >= P) continue;
+            const float v = __uint_as_float((unsigned)(r[u] >> 32));
+            int ix = (int)(r[u] & 0x3FFFF);
+            if (ix == 0x3FFFF) ix = INT_MAX;
+            if (v > best || (v == best && ix < bidx)) { best = v; bidx = ix; bc = q; }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+            const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+            if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; bc = oc; }
+          }
+          // winner's row and the old row gj in one round trip
+          const int wc = (bc >= 0 && bc < P) ? bc : 0;
+          const C2* wslot = crow + ((size_t)par * RMAT_MAX_PANEL_CTAS + wc) * RMAT_MAX_NB;
+          for (int c = lane; c < jb; c += 32) {
+            s_prow[c] = ld_cg(wslot + c);
+            s_trow[c] = ld_cg(trow + (size_t)par * RMAT_MAX_NB + c);
+          }
+          if (lane == 0) {
+            s_win = bidx;
+            s_zero = !(best > 0.f);
+          }
+        }
       }
-      // winner's row into shared memory (same warp: no barrier in between)
-      const int wc = (bc >= 0 && bc < P) ? bc : 0;
-      const C2* wslot = crow + ((size_t)par * RMAT_MAX_PANEL_CTAS + wc) * RMAT_MAX_NB;
-      for (int c = lane; c < jb; c += 32) s_prow[c] = ld_cg(wslot + c);
-      if (lane == 0) {
-        s_win = bidx;
-        s_zero = !(best > (T)0);
-      }
+      __syncthreads();
+      if (s_abort) return;
     } else {
-      for (int c = tid - 32; c < jb; c += PANEL_THREADS - 32)
-        s_trow[c] = ld_cg(trow + (size_t)par * RMAT_MAX_NB + c);
+      // ---- grid barrier j (bounded spin): acquire-poll ----
+      if (tid == 0) {
+        const unsigned target = (unsigned)(j + 1) * (unsigned)P;
+        long long polls = 0;
+        while (ld_acquire_gpu(ps.bar) < target) {
+          if (++polls > spin_limit) {
+            atomicExch(&stat[ST_TIMEOUT], 1);
+            s_abort = 1;
+            break;
+          }
+        }
+      }
+      __syncthreads();
+      if (s_abort) return;
+      // ---- phase B: global winner (warp 0), old row gj prefetched (other warps) ----
+      if (warp == 0) {
+        T best = (T)-1;
+        int bidx = INT_MAX;
+        int bc = -1;
+        // all candidates requested before any is compared: one L2 round trip
+        constexpr int QPL = RMAT_MAX_PANEL_CTAS / 32;
+        T cv[QPL];
+        int ci[QPL];
+  #pragma unroll
+        for (int u = 0; u < QPL; ++u) {
+          const int q = lane + 32 * u;
+          cv[u] = q < P ? ld_cg(cval + par * RMAT_MAX_PANEL_CTAS + q) : (T)-1;
+          ci[u] = q < P ? ld_cg(ps.cidx + par * RMAT_MAX_PANEL_CTAS + q) : INT_MAX;
+        }
+  #pragma unroll
+        for (int u = 0; u < QPL; ++u)
+          if (cv[u] > best || (cv[u] == best && ci[u] < bidx)) {
+            best = cv[u];
+            bidx = ci[u];
+            bc = lane + 32 * u;
+          }
+  #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+          const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+          if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; bc = oc; }
+        }
+        const int wc = (bc >= 0 && bc < P) ? bc : 0;
+        const C2* wslot = crow + ((size_t)par * RMAT_MAX_PANEL_CTAS + wc) * RMAT_MAX_NB;
+        for (int c = lane; c < jb; c += 32) s_prow[c] = ld_cg(wslot + c);
+        if (lane == 0) {
+          s_win = bidx;
+          s_zero = !(best > (T)0);
+        }
+      } else {
+        for (int c = tid - 32; c < jb; c += PANEL_THREADS - 32)
+          s_trow[c] = ld_cg(trow + (size_t)par * RMAT_MAX_NB + c);
+      }
+      __syncthreads();
     }
-    __syncthreads();
     const int p = (s_win >= gj && s_win < n) ? s_win : gj;
     if (cta == 0 && tid == 0) {
       ipiv[gj] = p;
@@ -187,30 +301,53 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
       }
     }
     __syncthreads();
-    if (s_zero) continue;  // exactly zero column: no scaling, no update (LAPACK)
+    // ---- multipliers of column j (an exactly zero column keeps its entries: LAPACK) ----
+    const bool zero = s_zero;
     const C2 piv = s_prow[j];
     const int r_first = max(r_lo, gj + 1);
+    if (!zero)
+      for (int r = r_first + tid; r < r_hi; r += PANEL_THREADS) {
+        C2* ar = at(r);
+        const C2 lm = cdiv<T>(ar[j], piv);
+        ar[j] = lm;
+        s_l[r - r_lo] = lm;
+      }
+    if (j + 1 == jb) break;
+    __syncthreads();
+    // ---- column j+1: its update, then its local candidate ----
+    T best = (T)-1;
+    int bidx = INT_MAX;
     for (int r = r_first + tid; r < r_hi; r += PANEL_THREADS) {
       C2* ar = at(r);
-      C2 lm = cdiv<T>(ar[j], piv);
-      ar[j] = lm;
-      s_l[r - r_lo] = lm;
+      C2 x = ar[j + 1];
+      if (!zero) {
+        csub_mul<T>(x, s_l[r - r_lo], s_prow[j + 1]);
+        ar[j + 1] = x;
+      }
+      const T m = cabs1<T>(x);
+      if (m > best) { best = m; bidx = r; }
     }
-    __syncthreads();
-    if (j + 1 < jb) {
-      // rank-1 update of the remaining columns: warp per row, lanes over columns
-      for (int r = r_first + warp; r < r_hi; r += nwarp) {
+    block_cand(best, bidx);
+    // rows published before barrier j+1: the candidate and row gj+1, fully updated
+    const int q0 = (s_ci != INT_MAX) ? s_ci : -1;
+    const int q1 = (gj + 1 >= r_lo && gj + 1 < r_hi && gj + 1 != q0) ? gj + 1 : -1;
+    if (!zero && warp < 2) {
+      const int r = warp == 0 ? q0 : q1;
+      if (r >= 0) {
         const C2 lm = s_l[r - r_lo];
         C2* Ar = at(r);
-        for (int c = j + 1 + lane; c < jb; c += 32) {
+        for (int c = j + 2 + lane; c < jb; c += 32) {
           C2 x = Ar[c];
           csub_mul<T>(x, lm, s_prow[c]);
           Ar[c] = x;
         }
       }
     }
+    if (tid == 0) { s_pre0 = q0; s_pre1 = q1; s_zprev = zero; }
     __syncthreads();
+    publish_arrive(j + 1);
   }
+  __syncthreads();
   if (SMEM) {
     for (int e = tid; e < (r_hi - r_lo) * jb; e += PANEL_THREADS) {
       const int rr = e / jb, cc = e - rr * jb;
@@ -1146,7 +1283,8 @@ int launch_panel(rmat_ctx c, cplx<T>* A, int ld, int k0, int n, int jb, int* ipi
                                  (int)panel_smem<T>(MAX_RPC, 0, false)));
     attr_set[sizeof(T) == 8] = true;
   }
-  RMAT_CU(cudaMemsetAsync(c->ps.bar, 0, sizeof(unsigned), c->stream));
+  // arrival counter and the candidate records (generation 0: nothing published)
+  RMAT_CU(cudaMemsetAsync(c->ps.bar, 0, 256 + 2 * RMAT_MAX_PANEL_CTAS * sizeof(double), c->stream));
   PanelScratch ps = c->ps;
   long long spin = c->spin_limit;
   int* stat = c->dstat;
