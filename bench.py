@@ -50,6 +50,28 @@ def peaks():
         return dict(FALLBACK_PEAKS), "fallback"
 
 
+def paired_update_bytes(N, nb, plane_bytes):
+    """Algorithmic bytes of each tensor-core factor update launch with paired panels:
+    C read + write (16 B per complex64 element) plus the operand planes (4 per
+    operand, plane_bytes per element in total)."""
+    out, k0 = [], 0
+    while k0 < N:
+        ja = min(nb, N - k0)
+        ra = N - k0 - ja
+        if ra <= 0:
+            break
+        if ra <= nb:
+            out.append(16.0 * ra * ra + plane_bytes * ja * 2 * ra)
+            k0 += ja
+            continue
+        jb, far = nb, N - k0 - ja - nb
+        out.append(16.0 * ra * jb + plane_bytes * ja * (ra + jb))     # columns of b
+        out.append(16.0 * jb * far + plane_bytes * ja * (jb + far))   # rows of b
+        out.append(16.0 * far * far + plane_bytes * (ja + jb) * 2 * far)
+        k0 += ja + jb
+    return out
+
+
 def lu_flops(N, nrhs):
     return 8.0 / 3.0 * N ** 3 + 8.0 * N ** 2 * nrhs
 
@@ -458,17 +480,17 @@ def main():
     if prec == g.RMAT_C64_3XF16_IR:
         # the fp16 update is bound by C22's read-modify-write in HBM (8-byte complex64,
         # read + written per update) more than by the tensor pipe; report it against HBM.
-        # ncu at N = 6400 (first update): 581.6 MB of DRAM traffic for 642 MB algorithmic
-        alg = [r * r * 16.0 + 2 * r * nbk * 8.0 for r in rests]
+        # Paired updates (default): per pair one narrow update of the next panel's
+        # columns, one of its rows, and one K = 2 nb update of the far block.
+        alg = paired_update_bytes(p.N, nbk, 8.0)
         tflops_achieved, tflops_peak = achieved, peak
-        achieved = (sum(alg) / len(alg)) / (tu_ms * 1e-3 / tu_n) / 1e9 if tu_ms and tu_ms > 0 else None
+        achieved = sum(alg) / (tu_ms * 1e-3) / 1e9 if tu_ms and tu_ms > 0 else None
         peak = pk["hbm_gbs"]
         bound, unit = "hbm", "GB/s"
         pname = "STREAM copy (%s); tensor view: %.1f of %.1f TFLOP/s (bf16 sustained / 3)" % (
             src, tflops_achieved or 0.0, tflops_peak)
-        traffic = 581.6e6 / 642.0e6 * (sum(alg) / len(alg))
-        tsrc = ("ncu dram__bytes_read+write of the N=6400 first-update capture "
-                "(profiles/trailing_update_tc_f16_n6400.md), scaled by algorithmic bytes per launch")
+        traffic = None   # no capture of the paired kernels yet
+        tsrc = None
     if prec == g.RMAT_C64_3XTF32_IR:
         # DRAM bytes per launch: the ncu capture of the same kernel at N = 6400 (first
         # update, 6272^2 x 128) read + wrote 596.8 MB for 655 MB of algorithmic bytes

@@ -68,13 +68,18 @@ extern "C" {
 
 /* ---- tunable parameters (rmat_set_param) -------------------------------- */
 #define RMAT_PARAM_NB          1  /* LU block width (multiple of 32; 0 = tuned) */
-#define RMAT_PARAM_PANEL_CTAS  2  /* CTAs of the cooperative panel (0 = auto)   */
+#define RMAT_PARAM_PANEL_CTAS  2  /* CTAs of the grid panel (0 = auto: cluster panel
+                                     when the rows fit one cluster, else grid) */
 #define RMAT_PARAM_SPIN_LIMIT  3  /* polls before a device wait gives up        */
 #define RMAT_PARAM_TIMING      4  /* 1 = record per-stage CUDA events           */
 /* Symmetric diagonal equilibration of assembled problems: the factor is taken of
  * D C D with D = |diag C|^-1/2 (LAPACK-style scaling; the FP64 residual stays on C).
  * -1 = default (on for the complex64 precisions, off for RMAT_C128), 0 off, 1 on. */
 #define RMAT_PARAM_EQUILIBRATE 5
+/* Complex64 tensor-core precisions: 1 (default) = two panels share one trailing
+ * update of depth 2*nb (half the passes over the trailing matrix), 0 = one update
+ * per panel.  Results agree to rounding. */
+#define RMAT_PARAM_PAIRED      6
 
 typedef struct rmat_ctx_s* rmat_ctx;
 

@@ -36,6 +36,7 @@ RMAT_PARAM_PANEL_CTAS = 2
 RMAT_PARAM_SPIN_LIMIT = 3
 RMAT_PARAM_TIMING = 4
 RMAT_PARAM_EQUILIBRATE = 5
+RMAT_PARAM_PAIRED = 6
 
 RMAT_BATCH_LANES = 1
 RMAT_BATCH_SPLIT_N = 2

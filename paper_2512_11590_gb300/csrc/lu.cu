@@ -561,7 +561,7 @@ __global__ void split_l21_kernel(const float2* __restrict__ A, int ld, int k0, i
 // the float bits in *out (non-negative floats order like their bit patterns).
 __global__ void __launch_bounds__(256)
 block_absmax_kernel(const float2* __restrict__ A, int ld, int k0, int jb, int c0, int ncols,
-                    unsigned* __restrict__ out) {
+                    unsigned* __restrict__ out, unsigned* __restrict__ out2) {
   float m = 0.f;
   const long long total = (long long)jb * ncols;
   for (long long e = blockIdx.x * 256ll + threadIdx.x; e < total; e += (long long)gridDim.x * 256)
@@ -573,21 +573,28 @@ block_absmax_kernel(const float2* __restrict__ A, int ld, int k0, int jb, int c0
   if (threadIdx.x == 0) {
     for (int w = 1; w < 8; ++w) m = fmaxf(m, sm[w]);
     atomicMax(out, __float_as_uint(m));
+    if (out2) atomicMax(out2, __float_as_uint(m));
   }
 }
 
 // 32 x 32 tile of a jb x ncols block S (rows t, columns c; row stride lds):
-// optional row-major copy into F (rows frow0 + t, columns fcol0 + c) and the
-// transposed planes T[trow0 + c][t], zero-filled for jb <= t < round_up(jb, 32).
-// fmt 1: the block's scale comes from its max in *smax; CTA (0, 0) records 1/s.
+// optional row-major copy into F (rows frow0 + t, columns fcol0 + c) and optional
+// transposed planes T[trow0 + c][tk0 + t], zero-filled for jb <= t < round_up(jb, 32).
+// fmt 1: F's scale comes from the max in *smax, T's from *smaxT (default: F's);
+// CTA (0, 0) records the inverse scales.
 __global__ void __launch_bounds__(256)
 split_block_kernel(const float2* __restrict__ S, int lds, int jb, int ncols, void* __restrict__ F,
                    int ldf, size_t fplane, int frow0, int fcol0, void* __restrict__ T,
-                   size_t tplane, int trow0, int fmt, const unsigned* __restrict__ smax,
-                   float* __restrict__ sinv) {
+                   size_t tplane, int trow0, int tk0, int fmt, const unsigned* __restrict__ smax,
+                   float* __restrict__ sinv, const unsigned* __restrict__ smaxT,
+                   float* __restrict__ sinvT) {
   __shared__ float2 tile[32][33];
   const float sc = (fmt == 1 && smax) ? pow2_scale(__uint_as_float(*smax)) : 1.f;
-  if (sinv && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *sinv = 1.f / sc;
+  const float scT = (fmt == 1 && smaxT) ? pow2_scale(__uint_as_float(*smaxT)) : sc;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    if (sinv) *sinv = 1.f / sc;
+    if (sinvT) *sinvT = 1.f / scT;
+  }
   const int c0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   for (int i = ty; i < 32; i += 8) {
@@ -599,11 +606,35 @@ split_block_kernel(const float2* __restrict__ S, int lds, int jb, int ncols, voi
     }
     tile[i][tx] = z;
   }
+  if (!T) return;
   __syncthreads();
   for (int i = ty; i < 32; i += 8) {
     const int c = c0 + i, t = t0 + tx;
-    if (c < ncols) put4(T, tplane, (size_t)(trow0 + c) * RMAT_MAX_NB + t, tile[tx][i], fmt, sc);
+    if (c < ncols) put4(T, tplane, (size_t)(trow0 + c) * RMAT_MAX_NB + tk0 + t, tile[tx][i], fmt, scT);
   }
+}
+
+// Rows of the L21 copy S (columns 0..jba of the paired update's A operand) that the
+// next panel's interchanges moved: S[rows[q]] = F[rows[src[q]]] over K-columns
+// k0..k0+jba of F, four planes (q < cnt; one warp per moved row).
+__global__ void __launch_bounds__(256)
+permute_l21_copy_kernel(const void* __restrict__ F, int ldf, size_t fplane, int k0, int jba,
+                        void* __restrict__ Sp, size_t splane, const int* __restrict__ rows,
+                        const int* __restrict__ src, const int* __restrict__ cnt, int blk, int nbp,
+                        int esz) {
+  const int q = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (q >= cnt[blk]) return;
+  const int* rw = rows + (size_t)blk * 2 * nbp;
+  const int dst = rw[q], from = rw[src[(size_t)blk * 2 * nbp + q]];
+  for (int pl = 0; pl < 4; ++pl)
+    for (int t = lane; t < jba; t += 32) {
+      const size_t fo = pl * fplane + (size_t)from * ldf + k0 + t;
+      const size_t so = pl * splane + (size_t)dst * RMAT_SPL_COLS + t;
+      if (esz == 2)
+        reinterpret_cast<__half*>(Sp)[so] = reinterpret_cast<const __half*>(F)[fo];
+      else
+        reinterpret_cast<float*>(Sp)[so] = reinterpret_cast<const float*>(F)[fo];
+    }
 }
 
 // A solved right-hand-side block (jb rows of S, ncols columns) -> transposed planes
@@ -1415,6 +1446,121 @@ int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb,
   return RMAT_OK;
 }
 
+// Paired tensor-core factorisation (complex64): two panels share one trailing
+// update with K = 2 nb, halving the read-modify-write passes over C22 (the update
+// is bound by that traffic with FP16 operands).  For a pair (a at k0, b at k0b):
+//   panel a; U12_a over all trailing columns; columns of b updated by a (narrow);
+//   panel b; b's interchanges applied to the far columns and to a copy S of L21_a
+//   (F keeps the deferred-interchange layout the solves replay); rows of b updated
+//   by a (strip); U12_b; then C_far -= [S | L21_b] [U12_a ; U12_b] with one common
+//   scale for both U12 halves.
+int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, const LUPerm& pm) {
+  const int fmt = rmat_plane_fmt(c->precision);
+  const size_t esz = rmat_plane_esz(c->precision);
+  const size_t fplane = (size_t)n * ld, bplane = (size_t)n * RMAT_MAX_NB,
+               splane = (size_t)n * RMAT_SPL_COLS;
+  const int pslot = ceil_div(n, nb);  // umax / uscale entry of the pair's common scale
+  auto absmax = [&](int row0, int jb, int col0, int ncols, unsigned* o1, unsigned* o2) {
+    block_absmax_kernel<<<std::min(c->sm_count * 2, ceil_div((long long)jb * ncols, 256)), 256, 0,
+                          c->stream>>>(A, ld, row0, jb, col0, ncols, o1, o2);
+    c->launches++;
+  };
+  auto split = [&](int row0, int jb, int col0, int ncols, bool f, bool t, int tk0,
+                   const unsigned* sm, float* si, const unsigned* smT, float* siT) {
+    split_block_kernel<<<dim3(ceil_div(ncols, 32), (int)round_up(jb, 32) / 32), 256, 0, c->stream>>>(
+        A + (size_t)row0 * ld + col0, ld, jb, ncols, f ? c->Fpl : nullptr, ld, fplane, row0, col0,
+        t ? c->Bpl : nullptr, bplane, col0, tk0, fmt, sm, si, smT, siT);
+    c->launches++;
+  };
+  auto l21 = [&](int k0, int jb) {
+    split_l21_kernel<<<ceil_div((long long)(n - k0 - jb) * 32, 256), 256, 0, c->stream>>>(
+        A, ld, k0, jb, n, c->Fpl, ld, fplane, fmt);
+    c->launches++;
+  };
+  auto prep = [&](int k0) {
+    perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt, pm.src,
+                                              c->dstat);
+    c->launches++;
+  };
+  // U12 = L11^-1 (rows k0.., columns col0..col0+ncols), interchanges applied when perm
+  auto trsm = [&](int k0, int jb, int col0, int ncols, bool perm) -> int {
+    bool fused = false;
+    RMAT_CHECK(solve_block<float, true>(c, perm ? &pm : nullptr, A, ld, k0, nb, jb, A + col0, ld,
+                                        ncols, nullptr, &fused));
+    if (!fused) {
+      if (perm) RMAT_CHECK(apply_perm<float>(c, pm, A + col0, ld, ncols, k0, nb, jb));
+      trsm_block_rhs_kernel<float, true><<<ceil_div(ncols, 32), 256, trsm_smem<float>(jb),
+                                           c->stream>>>(A, ld, k0, jb, A + col0, ld, ncols, nullptr);
+      c->launches++;
+    }
+    RMAT_CU(cudaGetLastError());
+    return RMAT_OK;
+  };
+  unsigned* um = fmt == 1 ? c->umax : nullptr;
+  float* us = fmt == 1 ? c->uscale : nullptr;
+  int k0 = 0;
+  while (k0 < n) {
+    const int jba = std::min(nb, n - k0), blka = k0 / nb;
+    RMAT_CHECK(launch_panel<float>(c, A, ld, k0, n, jba, ipiv));
+    prep(k0);
+    const int resta = n - k0 - jba;
+    if (resta <= 0) break;
+    RMAT_CHECK(trsm(k0, jba, k0 + jba, resta, true));
+    if (resta <= nb) {  // block b is the last one: a single update
+      if (um) absmax(k0, jba, k0 + jba, resta, um + blka, nullptr);
+      split(k0, jba, k0 + jba, resta, true, true, 0, um ? um + blka : nullptr,
+            us ? us + blka : nullptr, nullptr, nullptr);
+      l21(k0, jba);
+      RMAT_CU(cudaGetLastError());
+      RMAT_CHECK(launch_trailing_tc(c, A, ld, k0, jba, n));
+      k0 += jba;
+      continue;
+    }
+    const int k0b = k0 + jba, jbb = nb, blkb = k0b / nb, far0 = k0b + jbb, far = n - far0;
+    if (um) {
+      RMAT_CU(cudaMemsetAsync(um + pslot, 0, sizeof(unsigned), c->stream));
+      absmax(k0, jba, k0b, resta, um + blka, um + pslot);
+    }
+    split(k0, jba, k0b, resta, true, true, 0, um ? um + blka : nullptr, us ? us + blka : nullptr,
+          nullptr, nullptr);
+    l21(k0, jba);
+    RMAT_CU(cudaGetLastError());
+    // columns of b <- a (rows k0b.., deferred row order: panel b has not run yet)
+    RMAT_CHECK(launch_factor_tc(c, n, k0b, n - k0b, k0b, jbb, jba, false, k0, us ? us + blka : nullptr));
+    RMAT_CHECK(launch_panel<float>(c, A, ld, k0b, n, jbb, ipiv));
+    prep(k0b);
+    // b's interchanges on the far columns and on the copy S of L21_a
+    RMAT_CHECK(apply_perm<float>(c, pm, A + far0, ld, far, k0b, nb, jbb));
+    for (int q = 0; q < 4; ++q)
+      RMAT_CU(cudaMemcpy2DAsync(
+          reinterpret_cast<char*>(c->Spl) + (q * splane + (size_t)k0b * RMAT_SPL_COLS) * esz,
+          RMAT_SPL_COLS * esz,
+          reinterpret_cast<const char*>(c->Fpl) + (q * fplane + (size_t)k0b * ld + k0) * esz,
+          (size_t)ld * esz, (size_t)jba * esz, (size_t)(n - k0b), cudaMemcpyDeviceToDevice,
+          c->stream));
+    permute_l21_copy_kernel<<<ceil_div(2 * nb, 8), 256, 0, c->stream>>>(
+        c->Fpl, ld, fplane, k0, jba, c->Spl, splane, pm.rows, pm.src, pm.cnt, blkb, nb, (int)esz);
+    c->launches++;
+    RMAT_CU(cudaGetLastError());
+    // rows of b <- a in the far columns, then U12_b
+    RMAT_CHECK(launch_factor_tc(c, n, k0b, jbb, far0, far, jba, true, 0, us ? us + blka : nullptr));
+    RMAT_CHECK(trsm(k0b, jbb, far0, far, false));
+    if (um) absmax(k0b, jbb, far0, far, um + blkb, um + pslot);
+    // F rows of b (own scale); U12^T planes of both halves with the pair's common scale
+    split(k0b, jbb, far0, far, true, true, jba, um ? um + blkb : nullptr, us ? us + blkb : nullptr,
+          um ? um + pslot : nullptr, us ? us + pslot : nullptr);
+    split(k0, jba, far0, far, false, true, 0, um ? um + pslot : nullptr, nullptr, nullptr, nullptr);
+    l21(k0b, jbb);
+    RMAT_CU(cudaGetLastError());
+    RMAT_CHECK(launch_pair_tc(c, n, far0, jba, k0b, jbb, us ? us + pslot : nullptr));
+    k0 = far0;
+  }
+  c->inv_blocks = 0;
+  if (nb == 128) RMAT_CHECK(invert_diag_blocks<128>(c, A, ld, n, nb));
+  if (nb == 64) RMAT_CHECK(invert_diag_blocks<64>(c, A, ld, n, nb));
+  return RMAT_OK;
+}
+
 template <class T>
 int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool tensor,
                   const LUPerm& pm) {
@@ -1426,6 +1572,9 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
   const int fmt = rmat_plane_fmt(c->precision);
   if (tensor && fmt == 1)
     RMAT_CU(cudaMemsetAsync(c->umax, 0, (size_t)ceil_div(n, nb) * sizeof(unsigned), c->stream));
+  if constexpr (sizeof(T) == 4)
+    if (tensor && c->paired && c->Spl && 2 * nb <= RMAT_MAX_NB && nb <= RMAT_SPL_COLS)
+      return factor_pairs_tc(c, reinterpret_cast<float2*>(A), n, ld, ipiv, nb, pm);
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int jb = std::min(nb, n - k0);
     RMAT_CHECK(launch_panel<T>(c, A, ld, k0, n, jb, ipiv));
@@ -1457,13 +1606,13 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
       const int blk = k0 / nb;
       if (fmt == 1) {  // the U12 block's scale: max over its entries first
         block_absmax_kernel<<<std::min(c->sm_count * 2, ceil_div((long long)jb * rest, 256)), 256, 0,
-                              c->stream>>>(Af, ld, k0, jb, k0 + jb, rest, c->umax + blk);
+                              c->stream>>>(Af, ld, k0, jb, k0 + jb, rest, c->umax + blk, nullptr);
         c->launches++;
       }
       split_block_kernel<<<dim3(ceil_div(rest, 32), kpad / 32), 256, 0, c->stream>>>(
           Af + (size_t)k0 * ld + k0 + jb, ld, jb, rest, c->Fpl, ld, fplane, k0, k0 + jb, c->Bpl,
-          bplane, k0 + jb, fmt, fmt == 1 ? c->umax + blk : nullptr,
-          fmt == 1 ? c->uscale + blk : nullptr);
+          bplane, k0 + jb, 0, fmt, fmt == 1 ? c->umax + blk : nullptr,
+          fmt == 1 ? c->uscale + blk : nullptr, nullptr, nullptr);
       split_l21_kernel<<<ceil_div((long long)rest * 32, 256), 256, 0, c->stream>>>(
           Af, ld, k0, jb, n, c->Fpl, ld, fplane, fmt);
       c->launches += 2;

@@ -191,3 +191,20 @@ def test_grid_panel_variant(g, ctx, prec):
     finally:
         g.rmat_set_param(ctx, g.RMAT_PARAM_PANEL_CTAS, 0)
     assert relerr(out["U"], ref["U"]) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("paired,nb", [(0, 64), (1, 64), (1, 128)])
+def test_paired_trailing_updates(g, ctx, prec, paired, nb):
+    """Two panels per tensor-core trailing update (K = 2 nb, interchanges of the
+    second panel applied to a copy of the first panel's L21) and one update per
+    panel both reach the oracle's U."""
+    p = cp.config2(16)
+    ref = truth(p, "c2-16")
+    g.rmat_set_param(ctx, g.RMAT_PARAM_PAIRED, paired)
+    try:
+        out = run_problem(ctx, p, prec, max_refine=30, tol=1e-14, nb=nb)
+    finally:
+        g.rmat_set_param(ctx, g.RMAT_PARAM_PAIRED, 1)
+    assert relerr(out["U"], ref["U"]) < TOL[prec]
+    assert relerr(out["X"], ref["X"]) < TOL[prec]
