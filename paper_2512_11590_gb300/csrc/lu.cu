@@ -1391,7 +1391,7 @@ int solve_block(rmat_ctx c, const LUPerm* pm, const cplx<T>* A, int ld, int k0, 
 // Inverses of all full-width diagonal blocks (L11^-1 unit lower, U11^-1 upper) of a
 // complex64 factor, for the solve path: identity, then the batched block solve.
 template <int JB>
-int invert_diag_blocks(rmat_ctx c, const float2* A, int ld, int n, int nb) {
+int invert_diag_blocks(rmat_ctx c, const float2* A, int ld, int n, int nb, bool lower_done = false) {
   const int nfull = n / nb;
   c->inv_blocks = 0;
   if (nfull == 0) return RMAT_OK;
@@ -1399,8 +1399,11 @@ int invert_diag_blocks(rmat_ctx c, const float2* A, int ld, int n, int nb) {
   RMAT_CHECK(rmat_grow(c, &c->Dinv, &c->Dinv_cap, 2 * total * sizeof(float2)));
   float2* Linv = reinterpret_cast<float2*>(c->Dinv);
   float2* Uinv = Linv + total;
-  identity_blocks_kernel<float><<<std::min(c->sm_count * 4, ceil_div((long long)2 * total, 256)), 256,
-                                  0, c->stream>>>(Linv, JB, 2 * total);
+  // lower_done: the L11^-1 blocks were formed during the factorisation (U12 products)
+  float2* first = lower_done ? Uinv : Linv;
+  const size_t cnt = lower_done ? total : 2 * total;
+  identity_blocks_kernel<float><<<std::min(c->sm_count * 4, ceil_div((long long)cnt, 256)), 256,
+                                  0, c->stream>>>(first, JB, cnt);
   c->launches++;
   static bool attr[2] = {false, false};
   const size_t smem = solve_block_smem<float, JB>();
@@ -1412,11 +1415,14 @@ int invert_diag_blocks(rmat_ctx c, const float2* A, int ld, int n, int nb) {
     attr[JB == 128] = true;
   }
   const dim3 grid(JB / 32, nfull);
-  solve_block_kernel<float, true, JB><<<grid, 256, smem, c->stream>>>(
-      A, ld, 0, Linv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per, 0, nullptr, nullptr);
+  if (!lower_done) {
+    solve_block_kernel<float, true, JB><<<grid, 256, smem, c->stream>>>(
+        A, ld, 0, Linv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per, 0, nullptr, nullptr);
+    c->launches++;
+  }
   solve_block_kernel<float, false, JB><<<grid, 256, smem, c->stream>>>(
       A, ld, 0, Uinv, JB, JB, nb, nullptr, nullptr, nullptr, nullptr, 0, per, 0, nullptr, nullptr);
-  c->launches += 2;
+  c->launches++;
   RMAT_CU(cudaGetLastError());
   c->inv_blocks = nfull;
   c->inv_nb = nb;
@@ -1443,6 +1449,44 @@ int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb,
   kt.end();
   c->launches++;
   RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+// U12 = L11^-1 (P A12) for a full complex64 block through its inverse: L11^-1 is formed
+// right after the panel (identity + the register-blocked block solve, one block) into
+// its slot of the solve-path inverse table, then applied to all trailing columns by
+// the cluster kernel of the solve path (gather of the interchanged rows included).
+// Block widths 64 and 128; returns false when it does not apply.
+template <int JB>
+int u12_by_inverse_jb(rmat_ctx c, float2* A, int ld, int n, int k0, const LUPerm* pm, int col0,
+                      int ncols) {
+  const int nfull = n / JB;
+  const size_t per = (size_t)JB * JB;
+  RMAT_CHECK(rmat_grow(c, &c->Dinv, &c->Dinv_cap, 2 * per * nfull * sizeof(float2)));
+  float2* Lk = reinterpret_cast<float2*>(c->Dinv) + (size_t)(k0 / JB) * per;
+  identity_blocks_kernel<float><<<ceil_div((long long)per, 256), 256, 0, c->stream>>>(Lk, JB, per);
+  static bool attr = false;
+  const size_t smem = solve_block_smem<float, JB>();
+  if (!attr) {
+    RMAT_CU(cudaFuncSetAttribute(solve_block_kernel<float, true, JB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  solve_block_kernel<float, true, JB><<<dim3(JB / 32, 1), 256, smem, c->stream>>>(
+      A + (size_t)k0 * ld + k0, ld, 0, Lk, JB, JB, JB, nullptr, nullptr, nullptr, nullptr, 0, per, 0,
+      nullptr, nullptr);
+  c->launches += 2;
+  RMAT_CU(cudaGetLastError());
+  if (ncols <= 0) return RMAT_OK;
+  return launch_apply_inv<JB>(c, false, k0, JB, A + col0, ld, ncols, pm, nullptr);
+}
+
+int u12_by_inverse(rmat_ctx c, float2* A, int ld, int n, int k0, int nb, const LUPerm* pm,
+                   int col0, int ncols, bool* done) {
+  *done = true;
+  if (nb == 128) return u12_by_inverse_jb<128>(c, A, ld, n, k0, pm, col0, ncols);
+  if (nb == 64) return u12_by_inverse_jb<64>(c, A, ld, n, k0, pm, col0, ncols);
+  *done = false;
   return RMAT_OK;
 }
 
@@ -1485,8 +1529,11 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
   // U12 = L11^-1 (rows k0.., columns col0..col0+ncols), interchanges applied when perm
   auto trsm = [&](int k0, int jb, int col0, int ncols, bool perm) -> int {
     bool fused = false;
-    RMAT_CHECK(solve_block<float, true>(c, perm ? &pm : nullptr, A, ld, k0, nb, jb, A + col0, ld,
-                                        ncols, nullptr, &fused));
+    if (jb == nb) RMAT_CHECK(u12_by_inverse(c, A, ld, n, k0, nb, perm ? &pm : nullptr, col0, ncols,
+                                            &fused));
+    if (!fused)
+      RMAT_CHECK(solve_block<float, true>(c, perm ? &pm : nullptr, A, ld, k0, nb, jb, A + col0, ld,
+                                          ncols, nullptr, &fused));
     if (!fused) {
       if (perm) RMAT_CHECK(apply_perm<float>(c, pm, A + col0, ld, ncols, k0, nb, jb));
       trsm_block_rhs_kernel<float, true><<<ceil_div(ncols, 32), 256, trsm_smem<float>(jb),
@@ -1556,8 +1603,15 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
     k0 = far0;
   }
   c->inv_blocks = 0;
-  if (nb == 128) RMAT_CHECK(invert_diag_blocks<128>(c, A, ld, n, nb));
-  if (nb == 64) RMAT_CHECK(invert_diag_blocks<64>(c, A, ld, n, nb));
+  // L11^-1 of every full block is already in place (formed for its U12), except the
+  // last block when it has no trailing columns: form it here
+  const int nfull = n / nb;
+  if (nfull > 0 && nfull * nb == n) {
+    bool done = false;
+    RMAT_CHECK(u12_by_inverse(c, A, ld, n, (nfull - 1) * nb, nb, nullptr, n, 0, &done));
+  }
+  if (nb == 128) RMAT_CHECK(invert_diag_blocks<128>(c, A, ld, n, nb, true));
+  if (nb == 64) RMAT_CHECK(invert_diag_blocks<64>(c, A, ld, n, nb, true));
   return RMAT_OK;
 }
 
