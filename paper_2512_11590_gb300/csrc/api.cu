@@ -67,7 +67,6 @@ int ctx_reserve(rmat_ctx c, bool dense) {
     want(c->Fpl_cap, 4 * N * ld * pe);
     want(c->Bpl_cap, 4 * N * RMAT_MAX_NB * pe);
     want(c->Ypl_cap, (size_t)4 * RMAT_YPL_ROWS * RMAT_MAX_NB * pe);
-    want(c->Spl_cap, 4 * N * RMAT_SPL_COLS * pe);
   }
   if (dense) {
     want(c->A64_cap, N * N * 16);
@@ -86,7 +85,8 @@ int ctx_reserve(rmat_ctx c, bool dense) {
     RMAT_CHECK(rmat_grow(c, &c->Fpl, &c->Fpl_cap, 4 * N * ld * pe));
     RMAT_CHECK(rmat_grow(c, &c->Bpl, &c->Bpl_cap, 4 * N * RMAT_MAX_NB * pe));
     RMAT_CHECK(rmat_grow(c, &c->Ypl, &c->Ypl_cap, (size_t)4 * RMAT_YPL_ROWS * RMAT_MAX_NB * pe));
-    RMAT_CHECK(rmat_grow(c, &c->Spl, &c->Spl_cap, 4 * N * RMAT_SPL_COLS * pe));
+    RMAT_CHECK(rmat_grow(c, (void**)&c->pfwd, &c->pfwd_cap, 2 * N * sizeof(int)));
+    RMAT_CHECK(rmat_grow(c, &c->Bt, &c->Bt_cap, N * nrhs * eb));
     const size_t nblk = N / 32 + 2;
     RMAT_CHECK(rmat_grow(c, (void**)&c->umax, &c->umax_cap, nblk * sizeof(unsigned)));
     RMAT_CHECK(rmat_grow(c, (void**)&c->uscale, &c->uscale_cap, nblk * sizeof(float)));
@@ -281,7 +281,7 @@ int rmat_destroy(rmat_ctx c) {
                   c->fa,   c->l_d,  c->th_d, c->Wpt, c->X,    c->Rres, c->Bw,
                   c->Fpl,  c->Bpl, c->Ypl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
                   c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows, c->Dinv,
-                  c->umax, c->uscale, c->ycs, c->Spl};
+                  c->umax, c->uscale, c->ycs, c->pfwd, c->Bt};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->hstat) cudaFreeHost(c->hstat);

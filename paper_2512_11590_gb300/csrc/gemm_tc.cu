@@ -47,10 +47,9 @@ struct TcCfg {
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
 
 struct TcMaps {
-  CUtensorMap a[4];   // A operand planes: re_hi, re_lo, im_hi, im_lo
-  CUtensorMap a2[4];  // A planes for K >= ksplit (a second source; same as a otherwise)
-  CUtensorMap b[4];   // B operand planes
-  CUtensorMap c;      // output C viewed as fp32 [rows][2*cols], reduce-add target
+  CUtensorMap a[4];  // A operand planes: re_hi, re_lo, im_hi, im_lo
+  CUtensorMap b[4];  // B operand planes
+  CUtensorMap c;     // output C viewed as fp32 [rows][2*cols], reduce-add target
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -220,8 +219,7 @@ struct TcScales {
 template <int BN, int KIND>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, int Nn, int K,
-                 int ax0, int rowA0, int bx0, int rowB0, int ksplit, int ax2, TcScales sc,
-                 int* __restrict__ err) {
+                 int ax0, int rowA0, int bx0, int rowB0, TcScales sc, int* __restrict__ err) {
   using Cfg = TcCfg<BN>;
   constexpr int KSTEP = KIND == 0 ? 8 : 16;  // K elements per 32-byte operand row
   if (sc.skip && *sc.skip) return;           // before any barrier or TMEM allocation
@@ -280,12 +278,9 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
           const uint32_t full = smem_u32(&bars[s]);
           mbar_expect_tx(full, STAGE_BYTES);
           const uint32_t st = smem_u32(stages + s * STAGE_BYTES);
-          const int kk = ks * KSTEP;
-          const bool second = kk >= ksplit;  // K past the split comes from the second A source
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            tma_load_2d(st + q * A_PLANE_BYTES, second ? &maps.a2[q] : &maps.a[q],
-                        second ? ax2 + (kk - ksplit) : ax0 + kk, rowA0 + m0, full);
+            tma_load_2d(st + q * A_PLANE_BYTES, &maps.a[q], ax0 + ks * KSTEP, rowA0 + m0, full);
 #pragma unroll
           for (int q = 0; q < 4; ++q)
             tma_load_2d(st + 4 * A_PLANE_BYTES + q * B_PLANE_BYTES, &maps.b[q], bx0 + ks * KSTEP,
@@ -487,10 +482,8 @@ struct TcCache {
   const void* y = nullptr;
   const void* cmat = nullptr;
   const void* bw = nullptr;
-  const void* s = nullptr;
   int n = -1, ldf = -1, nrhs = -1, fmt = -1;
   TcMaps upd, sol;  // trailing update (BN = 256), solve update (BN = 128)
-  TcMaps pair;      // paired update: A = permuted L21 copy (S planes), then F; B = U12^T planes
 };
 bool g_tc_attr[2][2] = {{false, false}, {false, false}};
 
@@ -502,11 +495,10 @@ TcCache& tc_cache(rmat_ctx c) {
 
 template <int BN, int KIND>
 int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, int K, int ax0,
-                int ay0, int bx0, int by0, int ksplit, int ax2, const TcScales& sc,
-                bool count_as_update) {
+                int ay0, int bx0, int by0, const TcScales& sc, bool count_as_update) {
   constexpr int KSTEP = KIND == 0 ? 8 : 16;
   if (M <= 0 || Nn <= 0 || K <= 0) return RMAT_OK;
-  if (K % KSTEP || ax0 % KSTEP || bx0 % KSTEP || ksplit % KSTEP || ax2 % KSTEP) return RMAT_ESTATE;
+  if (K % KSTEP || ax0 % KSTEP || bx0 % KSTEP) return RMAT_ESTATE;
   constexpr size_t TC_SMEM = TcCfg<BN>::SMEM;
   if (!g_tc_attr[BN == 128][KIND]) {
     RMAT_CU(cudaFuncSetAttribute(tc_update_kernel<BN, KIND>,
@@ -522,7 +514,7 @@ int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn,
     RMAT_CU(cudaEventRecord(e0, c->stream));
   }
   tc_update_kernel<BN, KIND><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(
-      maps, cx0, cy0, M, Nn, K, ax0, ay0, bx0, by0, ksplit, ax2, sc, c->dstat + ST_TIMEOUT);
+      maps, cx0, cy0, M, Nn, K, ax0, ay0, bx0, by0, sc, c->dstat + ST_TIMEOUT);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   if (count_as_update) {
@@ -538,18 +530,14 @@ int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn,
 
 template <int BN>
 int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, int K, int ax0,
-              int ay0, int bx0, int by0, const TcScales& sc, bool count_as_update,
-              int ksplit = -1, int ax2 = 0) {
+              int ay0, int bx0, int by0, const TcScales& sc, bool count_as_update) {
   // K beyond the block reads zeros: F columns past n are outside the tensor map and
   // the Y / B planes are zero-filled up to a multiple of 32
-  if (rmat_plane_fmt(c->precision) == 1) {
-    const int Kp = (int)round_up(K, 16);
-    return launch_tc_k<BN, 1>(c, maps, cx0, cy0, M, Nn, Kp, ax0, ay0, bx0, by0,
-                              ksplit < 0 ? Kp : ksplit, ax2, sc, count_as_update);
-  }
-  const int Kp = (int)round_up(K, 8);
-  return launch_tc_k<BN, 0>(c, maps, cx0, cy0, M, Nn, Kp, ax0, ay0, bx0, by0,
-                            ksplit < 0 ? Kp : ksplit, ax2, sc, count_as_update);
+  if (rmat_plane_fmt(c->precision) == 1)
+    return launch_tc_k<BN, 1>(c, maps, cx0, cy0, M, Nn, (int)round_up(K, 16), ax0, ay0, bx0, by0,
+                              sc, count_as_update);
+  return launch_tc_k<BN, 0>(c, maps, cx0, cy0, M, Nn, (int)round_up(K, 8), ax0, ay0, bx0, by0, sc,
+                            count_as_update);
 }
 
 }  // namespace
@@ -558,8 +546,7 @@ int tc_prepare(rmat_ctx c, int n, int nrhs) {
   TcCache& g_tc = tc_cache(c);
   const int ldf = c->ld, fmt = rmat_plane_fmt(c->precision);
   if (g_tc.f == c->Fpl && g_tc.b == c->Bpl && g_tc.y == c->Ypl && g_tc.cmat == c->C &&
-      g_tc.bw == c->Bw && g_tc.s == c->Spl && g_tc.n == n && g_tc.ldf == ldf &&
-      g_tc.nrhs == nrhs && g_tc.fmt == fmt)
+      g_tc.bw == c->Bw && g_tc.n == n && g_tc.ldf == ldf && g_tc.nrhs == nrhs && g_tc.fmt == fmt)
     return RMAT_OK;
   if (nrhs % 2) return RMAT_ESTATE;
   const size_t esz = rmat_plane_esz(c->precision);
@@ -568,33 +555,21 @@ int tc_prepare(rmat_ctx c, int n, int nrhs) {
   char* F = reinterpret_cast<char*>(c->Fpl);
   char* Bp = reinterpret_cast<char*>(c->Bpl);
   char* Y = reinterpret_cast<char*>(c->Ypl);
-  const size_t splane = (size_t)n * RMAT_SPL_COLS * esz;
-  char* Sp = reinterpret_cast<char*>(c->Spl);
   for (int q = 0; q < 4; ++q) {
     RMAT_CHECK(make_plane_map(&g_tc.upd.a[q], F + q * fplane, fmt, n, n, ldf, TC_BM));
-    g_tc.upd.a2[q] = g_tc.upd.a[q];
     RMAT_CHECK(make_plane_map(&g_tc.upd.b[q], Bp + q * bplane, fmt, RMAT_MAX_NB, n, RMAT_MAX_NB,
                               TC_BN));
     g_tc.sol.a[q] = g_tc.upd.a[q];
-    g_tc.sol.a2[q] = g_tc.upd.a[q];
     RMAT_CHECK(make_plane_map(&g_tc.sol.b[q], Y + q * yplane, fmt, RMAT_MAX_NB, std::max(1, nrhs),
                               RMAT_MAX_NB, 128));
-    if (Sp) {
-      RMAT_CHECK(make_plane_map(&g_tc.pair.a[q], Sp + q * splane, fmt, RMAT_SPL_COLS, n,
-                                RMAT_SPL_COLS, TC_BM));
-      g_tc.pair.a2[q] = g_tc.upd.a[q];
-      g_tc.pair.b[q] = g_tc.upd.b[q];
-    }
   }
   RMAT_CHECK(make_out_map(&g_tc.upd.c, c->C, n, n, c->ld));
-  g_tc.pair.c = g_tc.upd.c;
   RMAT_CHECK(make_out_map(&g_tc.sol.c, c->Bw, std::max(2, nrhs), n, std::max(2, nrhs)));
   g_tc.f = c->Fpl;
   g_tc.b = c->Bpl;
   g_tc.y = c->Ypl;
   g_tc.cmat = c->C;
   g_tc.bw = c->Bw;
-  g_tc.s = c->Spl;
   g_tc.n = n;
   g_tc.ldf = ldf;
   g_tc.nrhs = nrhs;
@@ -615,29 +590,16 @@ int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n) {
                           sc, true);
 }
 
-// Rectangular factor update C[rows row0.., cols col0..col0+ncols) -= A B, with A = the
-// permuted copy S of L21 (x = 0..K) when from_s, else F at x = ax0; B = the U12^T planes
-// rows col0.. at K offset 0; uniform inverse scale *cscal (FP16 planes).
-int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, int K, bool from_s,
-                     int ax0, const float* cscal) {
+// Rectangular factor update C[rows row0.., cols col0..col0+ncols) -= F B: A = the split
+// factor planes at K-columns ax0..ax0+K (rows row0..), B = the U12^T planes rows
+// col0.. at K offset 0; uniform inverse scale *cscal (FP16 planes).
+int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, int K, int ax0,
+                     const float* cscal) {
   if (M <= 0 || ncols <= 0) return RMAT_OK;
   RMAT_CHECK(tc_prepare(c, n, c->nrhs + (c->nrhs & 1)));
   TcCache& g_tc = tc_cache(c);
   TcScales sc{nullptr, 1, nullptr, rmat_plane_fmt(c->precision) == 1 ? cscal : nullptr, nullptr};
-  return launch_tc<TC_BN>(c, from_s ? g_tc.pair : g_tc.upd, col0, row0, M, ncols, K,
-                          from_s ? 0 : ax0, row0, 0, col0, sc, true);
-}
-
-// Paired trailing update C22 -= [S | F(:, k0b..k0b+jbb)] [U12_a ; U12_b] over rows and
-// columns from far0, K = jba + jbb (the first jba K-columns from S).
-int launch_pair_tc(rmat_ctx c, int n, int far0, int jba, int k0b, int jbb, const float* cscal) {
-  const int rest = n - far0;
-  if (rest <= 0) return RMAT_OK;
-  RMAT_CHECK(tc_prepare(c, n, c->nrhs + (c->nrhs & 1)));
-  TcCache& g_tc = tc_cache(c);
-  TcScales sc{nullptr, 1, nullptr, rmat_plane_fmt(c->precision) == 1 ? cscal : nullptr, nullptr};
-  return launch_tc<TC_BN>(c, g_tc.pair, far0, far0, rest, rest, jba + jbb, 0, far0, 0, far0, sc,
-                          true, jba, k0b);
+  return launch_tc<TC_BN>(c, g_tc.upd, col0, row0, M, ncols, K, ax0, row0, 0, col0, sc, true);
 }
 
 // Solve update: Bsub[M x nrhs] -= F[rows ay0.., cols k0..k0+jb] * Y, Y^T planes in Ypl.

@@ -614,27 +614,64 @@ split_block_kernel(const float2* __restrict__ S, int lds, int jb, int ncols, voi
   }
 }
 
-// Rows of the L21 copy S (columns 0..jba of the paired update's A operand) that the
-// next panel's interchanges moved: S[rows[q]] = F[rows[src[q]]] over K-columns
-// k0..k0+jba of F, four planes (q < cnt; one warp per moved row).
+// Left interchanges on the split factor planes (tensor path): block blk's row moves
+// applied to K-columns 0..k0 of F (the L parts of all earlier blocks), so F holds L
+// in the final row order (P A = L U) that the forward solve uses after one gather of
+// the right-hand sides.  The complex64 factor C keeps the deferred layout.
+// One CTA per 32 columns: moved rows gathered to shared memory, then written back.
+template <class E>
 __global__ void __launch_bounds__(256)
-permute_l21_copy_kernel(const void* __restrict__ F, int ldf, size_t fplane, int k0, int jba,
-                        void* __restrict__ Sp, size_t splane, const int* __restrict__ rows,
-                        const int* __restrict__ src, const int* __restrict__ cnt, int blk, int nbp,
-                        int esz) {
-  const int q = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (q >= cnt[blk]) return;
+permute_fpl_left_kernel(E* __restrict__ F, int ldf, size_t fplane, int k0,
+                        const int* __restrict__ rows, const int* __restrict__ src,
+                        const int* __restrict__ cnt, int blk, int nbp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E* vals = reinterpret_cast<E*>(smem_raw);  // [2 * nbp][32]
+  const int c0 = blockIdx.x * 32, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n_q = cnt[blk];
   const int* rw = rows + (size_t)blk * 2 * nbp;
-  const int dst = rw[q], from = rw[src[(size_t)blk * 2 * nbp + q]];
-  for (int pl = 0; pl < 4; ++pl)
-    for (int t = lane; t < jba; t += 32) {
-      const size_t fo = pl * fplane + (size_t)from * ldf + k0 + t;
-      const size_t so = pl * splane + (size_t)dst * RMAT_SPL_COLS + t;
-      if (esz == 2)
-        reinterpret_cast<__half*>(Sp)[so] = reinterpret_cast<const __half*>(F)[fo];
-      else
-        reinterpret_cast<float*>(Sp)[so] = reinterpret_cast<const float*>(F)[fo];
-    }
+  const int* sr = src + (size_t)blk * 2 * nbp;
+  const int col = c0 + lane;
+  for (int pl = 0; pl < 4; ++pl) {
+    E* Fp = F + pl * fplane;
+    for (int q = warp; q < n_q; q += 8)
+      if (col < k0) vals[q * 32 + lane] = Fp[(size_t)rw[sr[q]] * ldf + col];
+    __syncthreads();
+    for (int q = warp; q < n_q; q += 8)
+      if (col < k0) Fp[(size_t)rw[q] * ldf + col] = vals[q * 32 + lane];
+    __syncthreads();
+  }
+}
+
+// Composed row permutation of all blocks (applied in order): pf[i] = the original row
+// whose content ends at position i.  One CTA; tmp holds one block's moved entries.
+__global__ void __launch_bounds__(256)
+compose_perm_kernel(int n, int nb, const int* __restrict__ rows, const int* __restrict__ src,
+                    const int* __restrict__ cnt, int* __restrict__ pf) {
+  __shared__ int tmp[2 * RMAT_MAX_NB];
+  for (int i = threadIdx.x; i < n; i += 256) pf[i] = i;
+  __syncthreads();
+  const int nblk = (n + nb - 1) / nb;
+  for (int b = 0; b < nblk; ++b) {
+    const int* rw = rows + (size_t)b * 2 * nb;
+    const int* sr = src + (size_t)b * 2 * nb;
+    const int m = cnt[b];
+    for (int q = threadIdx.x; q < m; q += 256) tmp[q] = pf[rw[sr[q]]];
+    __syncthreads();
+    for (int q = threadIdx.x; q < m; q += 256) pf[rw[q]] = tmp[q];
+    __syncthreads();
+  }
+}
+
+// Bt[i] = B[pf[i]] (rows of nrhs complex64), then the caller copies Bt back.
+__global__ void row_gather_kernel(const float2* __restrict__ B, float2* __restrict__ Bt, int n,
+                                  int nrhs, const int* __restrict__ pf,
+                                  const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * nrhs;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / nrhs), cc = (int)(e % nrhs);
+    Bt[e] = B[(size_t)pf[i] * nrhs + cc];
+  }
 }
 
 // A solved right-hand-side block (jb rows of S, ncols columns) -> transposed planes
@@ -1452,6 +1489,43 @@ int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb,
   return RMAT_OK;
 }
 
+// Block blk's interchanges on K-columns 0..k0 of the split factor planes.
+int permute_fpl_left(rmat_ctx c, int n, int ld, int k0, int nb, const LUPerm& pm) {
+  if (k0 <= 0) return RMAT_OK;
+  const size_t fplane = (size_t)n * ld;
+  const int blk = k0 / nb;
+  if (rmat_plane_esz(c->precision) == 2) {
+    const size_t smem = (size_t)2 * nb * 32 * sizeof(__half);
+    permute_fpl_left_kernel<__half><<<ceil_div(k0, 32), 256, smem, c->stream>>>(
+        reinterpret_cast<__half*>(c->Fpl), ld, fplane, k0, pm.rows, pm.src, pm.cnt, blk, nb);
+  } else {
+    static bool attr = false;
+    const size_t smem = (size_t)2 * nb * 32 * sizeof(float);
+    if (!attr) {
+      RMAT_CU(cudaFuncSetAttribute(permute_fpl_left_kernel<float>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(2 * RMAT_MAX_NB * 32 * sizeof(float))));
+      attr = true;
+    }
+    permute_fpl_left_kernel<float><<<ceil_div(k0, 32), 256, smem, c->stream>>>(
+        reinterpret_cast<float*>(c->Fpl), ld, fplane, k0, pm.rows, pm.src, pm.cnt, blk, nb);
+  }
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+// End of a tensor-path factorisation: F holds L in the final row order; the forward
+// solve gathers its right-hand sides once through the composed permutation.
+int finish_fpl_order(rmat_ctx c, int n, int nb, const LUPerm& pm) {
+  compose_perm_kernel<<<1, 256, 0, c->stream>>>(n, nb, pm.rows, pm.src, pm.cnt, c->pfwd);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  c->fpl_final = true;
+  c->fpl_nb = nb;
+  return RMAT_OK;
+}
+
 // U12 = L11^-1 (P A12) for a full complex64 block through its inverse: L11^-1 is formed
 // right after the panel (identity + the register-blocked block solve, one block) into
 // its slot of the solve-path inverse table, then applied to all trailing columns by
@@ -1501,8 +1575,7 @@ int u12_by_inverse(rmat_ctx c, float2* A, int ld, int n, int k0, int nb, const L
 int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, const LUPerm& pm) {
   const int fmt = rmat_plane_fmt(c->precision);
   const size_t esz = rmat_plane_esz(c->precision);
-  const size_t fplane = (size_t)n * ld, bplane = (size_t)n * RMAT_MAX_NB,
-               splane = (size_t)n * RMAT_SPL_COLS;
+  const size_t fplane = (size_t)n * ld, bplane = (size_t)n * RMAT_MAX_NB;
   const int pslot = ceil_div(n, nb);  // umax / uscale entry of the pair's common scale
   auto absmax = [&](int row0, int jb, int col0, int ncols, unsigned* o1, unsigned* o2) {
     block_absmax_kernel<<<std::min(c->sm_count * 2, ceil_div((long long)jb * ncols, 256)), 256, 0,
@@ -1521,10 +1594,11 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
         A, ld, k0, jb, n, c->Fpl, ld, fplane, fmt);
     c->launches++;
   };
-  auto prep = [&](int k0) {
+  auto prep = [&](int k0) -> int {
     perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt, pm.src,
                                               c->dstat);
     c->launches++;
+    return permute_fpl_left(c, n, ld, k0, nb, pm);  // F's L parts follow every interchange
   };
   // U12 = L11^-1 (rows k0.., columns col0..col0+ncols), interchanges applied when perm
   auto trsm = [&](int k0, int jb, int col0, int ncols, bool perm) -> int {
@@ -1549,7 +1623,7 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
   while (k0 < n) {
     const int jba = std::min(nb, n - k0), blka = k0 / nb;
     RMAT_CHECK(launch_panel<float>(c, A, ld, k0, n, jba, ipiv));
-    prep(k0);
+    RMAT_CHECK(prep(k0));
     const int resta = n - k0 - jba;
     if (resta <= 0) break;
     RMAT_CHECK(trsm(k0, jba, k0 + jba, resta, true));
@@ -1572,25 +1646,13 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
           nullptr, nullptr);
     l21(k0, jba);
     RMAT_CU(cudaGetLastError());
-    // columns of b <- a (rows k0b.., deferred row order: panel b has not run yet)
-    RMAT_CHECK(launch_factor_tc(c, n, k0b, n - k0b, k0b, jbb, jba, false, k0, us ? us + blka : nullptr));
+    // columns of b <- a (rows k0b.., in the row order before panel b)
+    RMAT_CHECK(launch_factor_tc(c, n, k0b, n - k0b, k0b, jbb, jba, k0, us ? us + blka : nullptr));
     RMAT_CHECK(launch_panel<float>(c, A, ld, k0b, n, jbb, ipiv));
-    prep(k0b);
-    // b's interchanges on the far columns and on the copy S of L21_a
-    RMAT_CHECK(apply_perm<float>(c, pm, A + far0, ld, far, k0b, nb, jbb));
-    for (int q = 0; q < 4; ++q)
-      RMAT_CU(cudaMemcpy2DAsync(
-          reinterpret_cast<char*>(c->Spl) + (q * splane + (size_t)k0b * RMAT_SPL_COLS) * esz,
-          RMAT_SPL_COLS * esz,
-          reinterpret_cast<const char*>(c->Fpl) + (q * fplane + (size_t)k0b * ld + k0) * esz,
-          (size_t)ld * esz, (size_t)jba * esz, (size_t)(n - k0b), cudaMemcpyDeviceToDevice,
-          c->stream));
-    permute_l21_copy_kernel<<<ceil_div(2 * nb, 8), 256, 0, c->stream>>>(
-        c->Fpl, ld, fplane, k0, jba, c->Spl, splane, pm.rows, pm.src, pm.cnt, blkb, nb, (int)esz);
-    c->launches++;
-    RMAT_CU(cudaGetLastError());
+    RMAT_CHECK(prep(k0b));  // b's interchanges also reach F's L21_a
+    RMAT_CHECK(apply_perm<float>(c, pm, A + far0, ld, far, k0b, nb, jbb));  // and the far columns
     // rows of b <- a in the far columns, then U12_b
-    RMAT_CHECK(launch_factor_tc(c, n, k0b, jbb, far0, far, jba, true, 0, us ? us + blka : nullptr));
+    RMAT_CHECK(launch_factor_tc(c, n, k0b, jbb, far0, far, jba, k0, us ? us + blka : nullptr));
     RMAT_CHECK(trsm(k0b, jbb, far0, far, false));
     if (um) absmax(k0b, jbb, far0, far, um + blkb, um + pslot);
     // F rows of b (own scale); U12^T planes of both halves with the pair's common scale
@@ -1599,7 +1661,8 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
     split(k0, jba, far0, far, false, true, 0, um ? um + pslot : nullptr, nullptr, nullptr, nullptr);
     l21(k0b, jbb);
     RMAT_CU(cudaGetLastError());
-    RMAT_CHECK(launch_pair_tc(c, n, far0, jba, k0b, jbb, us ? us + pslot : nullptr));
+    // C_far -= [L21_a | L21_b] [U12_a ; U12_b]: F's K-columns k0..k0+jba+jbb are contiguous
+    RMAT_CHECK(launch_factor_tc(c, n, far0, far, far0, far, jba + jbb, k0, us ? us + pslot : nullptr));
     k0 = far0;
   }
   c->inv_blocks = 0;
@@ -1612,7 +1675,7 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
   }
   if (nb == 128) RMAT_CHECK(invert_diag_blocks<128>(c, A, ld, n, nb, true));
   if (nb == 64) RMAT_CHECK(invert_diag_blocks<64>(c, A, ld, n, nb, true));
-  return RMAT_OK;
+  return finish_fpl_order(c, n, nb, pm);
 }
 
 template <class T>
@@ -1623,11 +1686,12 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
   if (nb < 1 || nb > max_nb<T>()) return RMAT_ESTATE;
   RMAT_CHECK(set_trsm_attrs<T>());
   RMAT_CU(cudaMemsetAsync(ipiv, 0xff, (size_t)n * sizeof(int), c->stream));  // -1: "not pivoted"
+  c->fpl_final = false;
   const int fmt = rmat_plane_fmt(c->precision);
   if (tensor && fmt == 1)
     RMAT_CU(cudaMemsetAsync(c->umax, 0, (size_t)ceil_div(n, nb) * sizeof(unsigned), c->stream));
   if constexpr (sizeof(T) == 4)
-    if (tensor && c->paired && c->Spl && 2 * nb <= RMAT_MAX_NB && nb <= RMAT_SPL_COLS)
+    if (tensor && c->paired && 2 * nb <= RMAT_MAX_NB)
       return factor_pairs_tc(c, reinterpret_cast<float2*>(A), n, ld, ipiv, nb, pm);
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int jb = std::min(nb, n - k0);
@@ -1637,12 +1701,14 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
       perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt, pm.src,
                                                 c->dstat);
       c->launches++;
+      if (tensor && sizeof(T) == 4) RMAT_CHECK(permute_fpl_left(c, n, ld, k0, nb, pm));
       continue;
     }
     // G3: interchanges on the trailing columns, then U12 = L11^-1 A12
     perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt, pm.src,
                                               c->dstat);
     c->launches++;
+    if (tensor && sizeof(T) == 4) RMAT_CHECK(permute_fpl_left(c, n, ld, k0, nb, pm));
     bool fused = false;
     RMAT_CHECK(solve_block<T, true>(c, &pm, A, ld, k0, nb, jb, A + k0 + jb, ld, rest, nullptr,
                                     &fused));
@@ -1695,6 +1761,7 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
     const float2* Af = reinterpret_cast<const float2*>(A);
     if (nb == 128) RMAT_CHECK(invert_diag_blocks<128>(c, Af, ld, n, nb));
     if (nb == 64) RMAT_CHECK(invert_diag_blocks<64>(c, Af, ld, n, nb));
+    RMAT_CHECK(finish_fpl_order(c, n, nb, pm));
   }
   return RMAT_OK;
 }
@@ -1721,7 +1788,20 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     RMAT_CU(cudaGetLastError());
     return RMAT_OK;
   };
-  // forward: replay each panel's interchanges, then L11 solve and update below
+  // forward.  Tensor path: F's L parts are in the final row order, so the right-hand
+  // sides are permuted once (composed permutation) and the blocks need no replay;
+  // otherwise each panel's interchanges are replayed block by block.
+  const bool upfront = tc && c->fpl_final && c->fpl_nb == nb && c->Bt;
+  if (upfront) {
+    row_gather_kernel<<<std::min(c->sm_count * 8, ceil_div((long long)n * nrhs, 256)), 256, 0,
+                        c->stream>>>(reinterpret_cast<const float2*>(B),
+                                     reinterpret_cast<float2*>(c->Bt), n, nrhs, c->pfwd, c->skip);
+    c->launches++;
+    RMAT_CU(cudaGetLastError());
+    RMAT_CU(cudaMemcpyAsync(B, c->Bt, (size_t)n * nrhs * sizeof(C2), cudaMemcpyDeviceToDevice,
+                            c->stream));
+  }
+  const LUPerm* fpm = upfront ? nullptr : &pm;
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int jb = std::min(nb, n - k0);
     const bool need_y = tc && n - k0 - jb > 0;
@@ -1729,15 +1809,15 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
       float2* Bf = reinterpret_cast<float2*>(B);
       void* Yp = need_y ? c->Ypl : nullptr;
-      if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, false, k0, nb, Bf, ldb, nrhs, &pm, Yp));
-      else RMAT_CHECK(launch_apply_inv<64>(c, false, k0, nb, Bf, ldb, nrhs, &pm, Yp));
+      if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, false, k0, nb, Bf, ldb, nrhs, fpm, Yp));
+      else RMAT_CHECK(launch_apply_inv<64>(c, false, k0, nb, Bf, ldb, nrhs, fpm, Yp));
       fused = true;
     } else {
-      RMAT_CHECK(solve_block<T, true>(c, &pm, A, ld, k0, nb, jb, B, ldb, nrhs,
+      RMAT_CHECK(solve_block<T, true>(c, fpm, A, ld, k0, nb, jb, B, ldb, nrhs,
                                       need_y ? c->Ypl : nullptr, &fused));
     }
     if (!fused) {
-      RMAT_CHECK(apply_perm<T>(c, pm, B, ldb, nrhs, k0, nb, jb));
+      if (fpm) RMAT_CHECK(apply_perm<T>(c, pm, B, ldb, nrhs, k0, nb, jb));
       trsm_block_rhs_kernel<T, true><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B,
                                                                               ldb, nrhs, c->skip);
       c->launches++;

@@ -16,7 +16,6 @@
 #define RMAT_MAX_NB 256
 // Rows of the right-hand-side plane buffer (max nrhs on the tensor solve path).
 #define RMAT_YPL_ROWS 1024
-#define RMAT_SPL_COLS 128  /* columns of the permuted L21 copy of the paired update */
 
 struct PanelScratch {
   // barrier counter + candidate slots of the one-barrier-per-column panel
@@ -62,6 +61,9 @@ struct rmat_ctx_s {
   // device-side refinement has stopped, so the launch returns at once (null: run)
   const int* skip = nullptr;
   int paired = 1;  // complex64 tensor path: two panels per trailing update (RMAT_PARAM_PAIRED)
+  bool fpl_final = false;  // F's L parts carry all interchanges; pfwd is their composition
+  int fpl_nb = 0;
+  void* Bt = nullptr;      size_t Bt_cap = 0;       // gather target of the tensor forward solve
   int equil_param = -1;   // -1: default (on for complex64 paths), 0 off, 1 on
   bool equil = false;     // symmetric diagonal equilibration active for this problem
 
@@ -98,7 +100,7 @@ struct rmat_ctx_s {
   void* Dinv = nullptr;    size_t Dinv_cap = 0;     // inverted diagonal blocks (tensor solve path)
   int inv_blocks = 0, inv_nb = 0;      // right-hand-side block planes [4][RMAT_YPL_ROWS][256]
   void* Bpl = nullptr;     size_t Bpl_cap = 0;      // tensor B operand planes (U12^T split)
-  void* Spl = nullptr;     size_t Spl_cap = 0;      // permuted L21 copy [4][N][128] (paired update)
+  int* pfwd = nullptr;     size_t pfwd_cap = 0;     // composed row permutation (tensor forward solve)
   // FP16 planes: per U block max bits and inverse scale 2^e, per right-hand-side
   // column inverse scale of the current solved block
   unsigned* umax = nullptr; size_t umax_cap = 0;
@@ -159,9 +161,8 @@ int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n);
 // solve update: rows [row0, row0+M) of the solve buffer Bw (ld = nrhs) -= F(ay0.., k0..k0+jb) * Y
 // Cluster size the cluster panel would use for M rows of width jb (0: does not fit).
 int panel_cluster_fits(rmat_ctx c, int precision, int M, int jb);
-int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, int K, bool from_s,
-                     int ax0, const float* cscal);
-int launch_pair_tc(rmat_ctx c, int n, int far0, int jba, int k0b, int jbb, const float* cscal);
+int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, int K, int ax0,
+                     const float* cscal);
 int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n,
                     const float* rowscale, int rs_div);
 int tc_prepare(rmat_ctx c, int n, int nrhs);
