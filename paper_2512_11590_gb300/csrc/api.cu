@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "cplx.cuh"
 #include "rmat_internal.h"
@@ -274,6 +275,7 @@ int rmat_destroy(rmat_ctx c) {
   if (!c) return RMAT_OK;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->sg_exec) cudaGraphExecDestroy(c->sg_exec);
   if (c->borrowed_tables) c->Kmat = c->T0 = c->rmesh = c->fa = nullptr, c->l_d = nullptr,
                           c->th_d = nullptr, c->open_d = nullptr;
   tc_release(c);
@@ -452,12 +454,58 @@ int rmat_factor(rmat_ctx c, int* info) {
   return RMAT_OK;
 }
 
-static int solve_factors(rmat_ctx c) {
+static int solve_factors_direct(rmat_ctx c) {
   if (c->precision == RMAT_C128)
     return lu_solve_dev<double>(c, c->C, c->N, c->ld, c->perm_main, c->nb, c->Bw, c->nrhs,
                                 c->nrhs);
   return lu_solve_dev<float>(c, c->C, c->N, c->ld, c->perm_main, c->nb, c->Bw, c->nrhs, c->nrhs,
                              rmat_tensor_prec(c->precision));
+}
+
+// Tensor-path solves are replayed from a CUDA graph (a solve is ~800 launches at
+// N = 25600; replay removes the host launch cost).  Not while the stream is itself
+// being captured (batches), on the legacy stream, with per-kernel timing on, or under
+// a device-side stop flag.
+static int solve_factors(rmat_ctx c) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!rmat_tensor_prec(c->precision) || c->timing || c->skip || c->stream == nullptr ||
+      cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return solve_factors_direct(c);
+  }
+  const std::vector<long long> key = {
+      c->N, c->nb, c->nrhs, c->ld, c->precision, c->inv_blocks, c->inv_nb, c->fpl_final,
+      c->fpl_nb, (long long)(uintptr_t)c->Bw, (long long)(uintptr_t)c->Fpl,
+      (long long)(uintptr_t)c->Ypl, (long long)(uintptr_t)c->C, (long long)(uintptr_t)c->Dinv,
+      (long long)(uintptr_t)c->Bt, (long long)(uintptr_t)c->pfwd,
+      (long long)(uintptr_t)c->perm_main.rows, (long long)(uintptr_t)c->stream,
+      (long long)(uintptr_t)c->uscale, (long long)(uintptr_t)c->ycs};
+  if (!c->sg_exec || key != c->sg_key) {
+    if (c->sg_exec) {
+      cudaGraphExecDestroy(c->sg_exec);
+      c->sg_exec = nullptr;
+    }
+    const long long l0 = c->launches;
+    RMAT_CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+    const int st = solve_factors_direct(c);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (st != RMAT_OK || e != cudaSuccess || !g ||
+        cudaGraphInstantiate(&c->sg_exec, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      c->sg_exec = nullptr;
+      c->launches = l0;
+      return st != RMAT_OK ? st : solve_factors_direct(c);
+    }
+    cudaGraphDestroy(g);
+    c->sg_key = key;
+    c->sg_launches = c->launches - l0;
+    c->launches = l0;
+  }
+  RMAT_CU(cudaGraphLaunch(c->sg_exec, c->stream));
+  c->launches += c->sg_launches;
+  return RMAT_OK;
 }
 
 }  // extern "C"

@@ -1208,12 +1208,106 @@ size_t perm_smem(int nb) {
   return (size_t)2 * nb * 32 * sizeof(cplx<T>) + (size_t)3 * nb * sizeof(int);
 }
 
+// ---- FP64 complex GEMM C -= A B (row-major) on the FP64 tensor instruction ------
+// mma.sync.m8n8k4.f64 (tcgen05 has no f64 kind): the complex product as four real
+// products (-Ai*Bi through a negated copy of the Ai fragment).  64 x 64 output tile per
+// CTA, 16-deep K chunks staged as separate real / imaginary [k][64] planes (row pitch
+// 72 doubles: a fragment load's 4 k-rows x 8 entries hit distinct bank slots); each of
+// the 8 warps owns 32 x 16 (4 x 2 tiles of 8 x 8).
+constexpr int ZG_T = 64, ZG_K = 16, ZG_LD = 72;
+
+__device__ __forceinline__ void dmma_acc(double& d0, double& d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
+__global__ void __launch_bounds__(256)
+zgemm_sub_dmma_kernel(int M, int N, int K, const double2* __restrict__ A, int lda,
+                      const double2* __restrict__ B, int ldb, double2* __restrict__ C, int ldc,
+                      const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double Ar[ZG_K][ZG_LD], Am[ZG_K][ZG_LD];  // A[m0 + m][k0 + k] -> [k][m]
+  __shared__ double Br[ZG_K][ZG_LD], Bm[ZG_K][ZG_LD];  // B[k0 + k][n0 + n] -> [k][n]
+  const int m0 = blockIdx.y * ZG_T, n0 = blockIdx.x * ZG_T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wm = (warp >> 2) * 32, wn = (warp & 3) * 16;
+  const int g = lane >> 2, t = lane & 3;
+  double accr[4][2][2], acci[4][2][2];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) accr[p][q][0] = accr[p][q][1] = acci[p][q][0] = acci[p][q][1] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += ZG_K) {
+    for (int e = threadIdx.x; e < ZG_T * ZG_K; e += 256) {
+      const int kk = e & (ZG_K - 1), mm = e >> 4;
+      const int gm = m0 + mm, gk = k0 + kk;
+      const double2 a = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : make_double2(0, 0);
+      Ar[kk][mm] = a.x;
+      Am[kk][mm] = a.y;
+      const int kb = e >> 6, nn = e & (ZG_T - 1);
+      const int gk2 = k0 + kb, gn = n0 + nn;
+      const double2 b = (gk2 < K && gn < N) ? B[(size_t)gk2 * ldb + gn] : make_double2(0, 0);
+      Br[kb][nn] = b.x;
+      Bm[kb][nn] = b.y;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k4 = 0; k4 < ZG_K; k4 += 4) {
+      double ar[4], ai[4], an[4], br[2], bi[2];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        ar[p] = Ar[k4 + t][wm + 8 * p + g];
+        ai[p] = Am[k4 + t][wm + 8 * p + g];
+        an[p] = -ai[p];
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        br[q] = Br[k4 + t][wn + 8 * q + g];
+        bi[q] = Bm[k4 + t][wn + 8 * q + g];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          dmma_acc(accr[p][q][0], accr[p][q][1], ar[p], br[q]);
+          dmma_acc(accr[p][q][0], accr[p][q][1], an[p], bi[q]);
+          dmma_acc(acci[p][q][0], acci[p][q][1], ar[p], bi[q]);
+          dmma_acc(acci[p][q][0], acci[p][q][1], ai[p], br[q]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int gm = m0 + wm + 8 * p + g;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gn = n0 + wn + 8 * q + 2 * t + h;
+        if (gn >= N) continue;
+        double2* cp = C + (size_t)gm * ldc + gn;
+        double2 v = *cp;
+        v.x -= accr[p][q][h];
+        v.y -= acci[p][q][h];
+        *cp = v;
+      }
+  }
+}
+
 template <class T>
 int gemm_sub(rmat_ctx c, int M, int N, int K, const cplx<T>* A, int lda, const cplx<T>* B,
              int ldb, cplx<T>* C, int ldc) {
   if (M <= 0 || N <= 0 || K <= 0) return RMAT_OK;
-  dim3 grid(ceil_div(N, GB_N), ceil_div(M, GB_M));
-  cgemm_sub_kernel<T><<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, B, ldb, C, ldc, c->skip);
+  if constexpr (sizeof(T) == 8) {
+    dim3 grid(ceil_div(N, ZG_T), ceil_div(M, ZG_T));
+    zgemm_sub_dmma_kernel<<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, B, ldb, C, ldc, c->skip);
+  } else {
+    dim3 grid(ceil_div(N, GB_N), ceil_div(M, GB_M));
+    cgemm_sub_kernel<T><<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, B, ldb, C, ldc, c->skip);
+  }
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;

@@ -120,6 +120,11 @@ struct rmat_ctx_s {
 
   bool assembled = false, factored = false, solved = false;
   void* tc = nullptr;      // tensor-map cache of this context (gemm_tc.cu)
+  // CUDA graph of one complete solve (both sweeps), captured on first use and replayed
+  // by every later solve with the same sizes, buffers and factor layout
+  cudaGraphExec_t sg_exec = nullptr;
+  std::vector<long long> sg_key;
+  long long sg_launches = 0;
   bool borrowed_tables = false;  // mesh/channel tables owned by a batch, not freed here
 
   // statistics
