@@ -39,7 +39,8 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 TF32_PER_BF16 = 0.5          # nominal dense tf32 : bf16 tensor rate on GB300 (1.1 : 2.25 PF)
 DTYPES = {1: "c64 factor with 3xTF32 tensor updates / f64 refinement",
           2: "c64 factor with FP32 CUDA-core updates / f64 refinement",
-          3: "c64 factor with 3xFP16 (scaled split) tensor updates / f64 refinement"}
+          3: "c64 factor with 3xFP16 (scaled split) tensor updates / f64 refinement",
+          0: "c128 throughout (FP64 tensor-instruction GEMMs, FP64 refinement)"}
 
 
 def peaks():
@@ -298,7 +299,7 @@ def batch_main(args):
     torch.cuda.set_device(0)
     probs = cp.batch_problems(args.batch)
     prec = {"tf32": g.RMAT_C64_3XTF32_IR, "f16": g.RMAT_C64_3XF16_IR,
-            "simt": g.RMAT_C64_SIMT_IR}[args.precision]
+            "simt": g.RMAT_C64_SIMT_IR, "c128": g.RMAT_C128}[args.precision]
     stream = torch.cuda.Stream()                 # capturable stream for the batch's CUDA graph
     ctx = g.rmat_create(0, stream.cuda_stream)
     Vs, structs, keep = [], [], []
@@ -315,7 +316,12 @@ def batch_main(args):
     Uptr = [u.data_ptr() for u in Us]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lanes, split = g.rmat_batch_tune(b, Uptr)
+    if prec == g.RMAT_C128:   # the default plan (16 lanes, every system whose panels fit a cluster)
+        lanes, split = 16, 8192
+        g.rmat_batch_set(b, g.RMAT_BATCH_LANES, lanes)
+        g.rmat_batch_set(b, g.RMAT_BATCH_SPLIT_N, split)
+    else:
+        lanes, split = g.rmat_batch_tune(b, Uptr)
     tune_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         g.rmat_batch_run(b, Uptr)
@@ -358,7 +364,7 @@ def batch_main(args):
             "value": len(probs) / (ms * 1e-3), "unit": "systems/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPES[prec],
+            "dtype": DTYPES.get(prec, "c128"),
             "data": "synthetic",
             "config": {"workload": "config4 batch_problems(%d) seed 11593, N %d..%d, median %d"
                        % (len(probs), Ns.min(), Ns.max(), int(np.median(Ns))),
@@ -373,13 +379,107 @@ def batch_main(args):
     return 0
 
 
+def solve_once(p, precision, device=0, warm=False, energies=None):
+    """One assembled system through the C ABI on a non-default stream: wall times of
+    assemble+factor+solve+collision per energy, refinement info, U per energy."""
+    import torch
+
+    import cc_problems as cp
+    import paper_2512_11590_gb300 as g
+    stream = torch.cuda.Stream()
+    ctx = g.rmat_create(device, stream.cuda_stream)
+    m = g.rmat_mesh(p.nlag, p.a)
+    Vd = torch.from_numpy(cp.potential_at(p, m["r"]).ravel()).cuda()
+    prob, keep = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh, precision)
+    X = torch.zeros((p.nch, p.N), dtype=torch.complex128, device="cuda")
+    R = torch.zeros(p.nch * p.nch, dtype=torch.complex128, device="cuda")
+    Es = list(energies) if energies else [p.E]
+    out = []
+    for k, E in enumerate(([Es[0]] if warm else []) + Es):
+        nopen = int(np.sum(E - p.thresh > 0))
+        U = torch.zeros(max(1, nopen) ** 2, dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.rmat_assemble(ctx, prob, E, Vd.data_ptr())
+        g.rmat_factor(ctx, want_info=False)
+        st, it, rel = g.rmat_solve(ctx, X.data_ptr(), p.N, max_refine=30, tol=1e-13)
+        g.rmat_collision(ctx, R.data_ptr(), U.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if warm and k == 0:
+            continue
+        out.append({"E": E, "ms": e0.elapsed_time(e1), "status": st, "iters": it, "rel_resid": rel,
+                    "U": U.cpu().numpy()[:nopen * nopen].reshape(nopen, nopen).T})
+    g.rmat_destroy(ctx)
+    return out
+
+
+def sweep_main(args):
+    """Config 2 sweep N in {1600, 6400, 12800, 25600} and config 3b (W = -1): the
+    complex128 path against FP32+IR (split FP16) on the same systems."""
+    import torch
+
+    import cc_problems as cp
+    import paper_2512_11590_gb300 as g
+    torch.cuda.set_device(0)
+    rows = []
+    cases = [("config2", cp.config2(n)) for n in (16, 64, 128, 256)] + [("config3b", cp.config3(256, W=-1.0))]
+    for name, p in cases:
+        lo = solve_once(p, g.RMAT_C64_3XF16_IR, warm=True)[0]
+        hi = solve_once(p, g.RMAT_C128, warm=p.N <= 6400)[0]
+        fl = lu_flops(p.N, p.nch)
+        rows.append({"case": name, "N": p.N, "nrhs": p.nch,
+                     "fp32ir_ms": lo["ms"], "fp32ir_tflops": fl / (lo["ms"] * 1e-3) / 1e12,
+                     "fp32ir_iters": lo["iters"], "fp32ir_rel_resid": lo["rel_resid"],
+                     "fp64_ms": hi["ms"], "fp64_tflops": fl / (hi["ms"] * 1e-3) / 1e12,
+                     "fp64_iters": hi["iters"], "speedup": hi["ms"] / lo["ms"],
+                     "u_rel_diff": float(np.max(np.abs(lo["U"] - hi["U"])) / np.max(np.abs(hi["U"])))})
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"metric": "config 2 sweep + config 3b: FP32+IR vs FP64 (complex128) per system",
+                      "unit": "ms", "rows": rows, "data": "synthetic"}))
+    return 0
+
+
+def config5_main(args):
+    """Config 5: N = 51200 (nch = 512, nlag = 100), 512 right-hand sides, an energy sweep
+    of 8 points reusing the assembly buffers (FP32+IR), and one energy in complex128 for
+    the U error."""
+    import torch
+
+    import cc_problems as cp
+    import paper_2512_11590_gb300 as g
+    torch.cuda.set_device(0)
+    p = cp.config5(cp.CONFIG5_ENERGIES[0])
+    sweep = solve_once(p, g.RMAT_C64_3XF16_IR, warm=True, energies=cp.CONFIG5_ENERGIES)
+    fl = lu_flops(p.N, p.nch)
+    line = {"metric": "config 5: N=51200 energy sweep (8 energies), FP32+IR", "unit": "ms",
+            "N": p.N, "nrhs": p.nch, "data": "synthetic",
+            "energies": [{"E": r["E"], "ms": r["ms"], "tflops": fl / (r["ms"] * 1e-3) / 1e12,
+                          "iters": r["iters"], "rel_resid": r["rel_resid"], "status": r["status"]}
+                         for r in sweep],
+            "total_ms": sum(r["ms"] for r in sweep)}
+    if not args.no_fp64:
+        hi = solve_once(p, g.RMAT_C128, warm=False)[0]
+        lo = sweep[0]
+        line["fp64_first_energy"] = {
+            "ms": hi["ms"], "tflops": fl / (hi["ms"] * 1e-3) / 1e12, "iters": hi["iters"],
+            "u_rel_diff_fp32ir_vs_fp64": float(np.max(np.abs(lo["U"] - hi["U"])) /
+                                               np.max(np.abs(hi["U"]))),
+            "speedup_fp32ir_over_fp64": hi["ms"] / lo["ms"]}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f16", choices=["f16", "tf32", "simt"])
+    ap.add_argument("--precision", default="f16", choices=["f16", "tf32", "simt", "c128"],
+                    help="c128 only with --batch")
     ap.add_argument("--small", action="store_true", help="N=1600 instead of N=25600")
     ap.add_argument("--no-fp64", action="store_true", help="skip the complex128 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -390,6 +490,10 @@ def main():
     ap.add_argument("--no-warm", action="store_true", help="--profile-step without the warm-up step")
     ap.add_argument("--batch", type=int, default=0,
                     help="time the batch driver on this many config-4 systems instead")
+    ap.add_argument("--sweep", action="store_true",
+                    help="config 2 sweep (N=1600..25600) and config 3b, FP32+IR vs complex128")
+    ap.add_argument("--config5", action="store_true",
+                    help="config 5: N=51200, 8-energy FP32+IR sweep (+ one complex128 energy)")
     ap.add_argument("--batch-refine", type=int, default=10,
                     help="refinement-step budget of the batch (stopping decided on the device)")
     args = ap.parse_args()
@@ -405,6 +509,13 @@ def main():
                             warm=not args.no_warm)
     if args.batch:
         return batch_main(args)
+    if args.precision == "c128":
+        print("--precision c128 is for --batch (the main line times FP32+IR)", file=sys.stderr)
+        return 2
+    if args.sweep:
+        return sweep_main(args)
+    if args.config5:
+        return config5_main(args)
 
     import torch
     import paper_2512_11590_gb300 as g

@@ -167,9 +167,9 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
     }
     if constexpr (sizeof(T) == 4) {
       // ---- barrier j = all P records of parity j&1 carry generation j+1 (bounded) ----
+      constexpr int QPL = RMAT_MAX_PANEL_CTAS / 32;
+      unsigned long long r[QPL];
       if (warp == 0) {
-        constexpr int QPL = RMAT_MAX_PANEL_CTAS / 32;
-        unsigned long long r[QPL];
         long long polls = 0;
         bool ok = false;
         for (;;) {
@@ -188,12 +188,16 @@ panel_kernel(cplx<T>* __restrict__ A, int ld, int k0, int n, int jb, int* __rest
           if (__all_sync(0xffffffffu, mine)) { ok = true; break; }
           if (++polls > spin_limit) break;
         }
-        if (!ok) {
-          if (lane == 0) {
-            atomicExch(&stat[ST_TIMEOUT], 1);
-            s_abort = 1;
-          }
-        } else {
+        if (!ok && lane == 0) {
+          atomicExch(&stat[ST_TIMEOUT], 1);
+          s_abort = 1;
+        }
+      }
+      // every warp has finished the deferred update (it reads s_prow, rewritten below)
+      __syncthreads();
+      if (s_abort) return;
+      if (warp == 0) {
+        {
           asm volatile("fence.acq_rel.gpu;" ::: "memory");
           float best = -1.f;
           int bidx = INT_MAX, bc = -1;

@@ -1,0 +1,70 @@
+"""Full-size parity (-m gpu): the systems the bench times (config 3, N = 25600, and its
+worse-conditioned variant W = -1) and the complex128 path at the config-2 sweep sizes.
+
+The oracle cannot factor N = 25600 in test time, so it checks what it can compute
+at any size, independently of the GPU path:
+  * the residual Phi - C X of the GPU's X, formed by the oracle's structured product
+    (block structure of C, complex128): the FP64 floor of max|r|/max|Phi| is ~1e-12;
+  * R from the GPU's X by the oracle's contraction, and U from the GPU's R by the
+    oracle's matching: the R and U steps pinned at full size;
+  * U symmetric (C complex symmetric).
+"""
+import numpy as np
+import pytest
+
+import cc_problems as cp
+from oracle.collision import collision_matrix, r_matrix
+from oracle.mesh import lagrange_mesh
+from oracle.system import structured_residual, surface_rhs
+from rmat_gpu import relerr, run_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    import paper_2512_11590_gb300 as g
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    h = g.rmat_create(0, stream.cuda_stream)
+    yield h
+    g.rmat_destroy(h)
+
+
+def check_against_oracle(p, out, res_tol):
+    m = lagrange_mesh(p.nlag, p.a)
+    V = cp.potential_at(p, m["r"])
+    X = out["X"]
+    r = structured_residual(p, V, X, mesh=m)
+    rel = np.max(np.abs(r)) / np.max(np.abs(surface_rhs(p, m)))
+    assert rel < res_tol, rel
+    R_or = r_matrix(p, X, m["f_a"])
+    assert relerr(out["R"], R_or) < 1e-12
+    U_or, nopen = collision_matrix(p, out["R"])
+    assert nopen == out["nopen"]
+    assert relerr(out["U"], U_or) < 1e-12
+    assert relerr(out["U"], out["U"].T) < 1e-10
+    return rel
+
+
+@pytest.mark.parametrize("W", [-10.0, -1.0])
+def test_config3_full_size_fp32_ir(ctx, W):
+    """N = 25600, 256 right-hand sides, split-FP16 factor + FP64 refinement (the bench's
+    launch configuration: default block width, paired panels, graph-replayed solves)."""
+    import paper_2512_11590_gb300 as g
+    p = cp.config3(256, W=W)
+    out = run_problem(ctx, p, g.RMAT_C64_3XF16_IR, max_refine=30, tol=1e-13)
+    assert out["status"] in (g.RMAT_OK, g.RMAT_ENOCONV)
+    assert out["iters"] >= 2
+    check_against_oracle(p, out, 2e-11)
+
+
+@pytest.mark.parametrize("nch", [64, 128])
+def test_config2_sweep_complex128(ctx, nch):
+    """Plain FP64 path (complex128 throughout) at N = 6400 and 12800."""
+    import paper_2512_11590_gb300 as g
+    p = cp.config2(nch)
+    out = run_problem(ctx, p, g.RMAT_C128, max_refine=30, tol=1e-13)
+    check_against_oracle(p, out, 2e-11)

@@ -208,3 +208,17 @@ def test_paired_trailing_updates(g, ctx, prec, paired, nb):
         g.rmat_set_param(ctx, g.RMAT_PARAM_PAIRED, 1)
     assert relerr(out["U"], ref["U"]) < TOL[prec]
     assert relerr(out["X"], ref["X"]) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec,nb,ctas", [(3, 128, 2), (3, 64, 3), (1, 128, 2), (0, 64, 2)])
+def test_panel_rows_in_global_memory(g, ctx, prec, nb, ctas):
+    """Few panel CTAs, so each holds too many rows for shared memory: the grid panel
+    works on its rows in global memory (the variant the first panels of N = 51200 use)."""
+    p = cp.config2(16)
+    ref = truth(p, "c2-16")
+    g.rmat_set_param(ctx, g.RMAT_PARAM_PANEL_CTAS, ctas)
+    try:
+        out = run_problem(ctx, p, prec, max_refine=30, tol=1e-14, nb=nb)
+    finally:
+        g.rmat_set_param(ctx, g.RMAT_PARAM_PANEL_CTAS, 0)
+    assert relerr(out["U"], ref["U"]) < TOL[prec]
