@@ -635,6 +635,14 @@ def main():
         "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
+        "paper_context": {
+            "hardware": "RTX 3090 (sm_86, CUDA 11.5) + 2x Xeon Gold 6248R (48 cores)",
+            "n25600_type4_fp32_cusolver_s": 3.554, "n25600_type4_error": 8e-10,
+            "n25600_hybrid_fp32_factor_plus_2_host_ir_s": 9.85, "n25600_hybrid_error": 6e-16,
+            "n25600_type1_zgesv_cpu_s": 52.098, "n25600_legacy_zgetri_cpu_s": 144.948,
+            "paper_speedups": "about 15x over its CPU direct solver and about 41x over the "
+                              "legacy code at N=25600 (Type 4 vs Type 1 / Ref.)",
+            "note": "other hardware and workloads: context only, not a ratio target"},
         "roofline": {"kernel": "trailing update C22 -= L21 U12", "bound": bound,
                      "achieved": achieved, "peak": peak, "peak_source": pname, "unit": unit,
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,

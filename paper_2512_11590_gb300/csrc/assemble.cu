@@ -44,6 +44,7 @@ assemble_kernel(cplx<T>* __restrict__ C, int ld, int N, int nch, int nlag,
     const int sq = 32 / nlag, sr = 32 - sq * nlag;  // 32 = sq*nlag + sr
     for (int col = lane; col < ld; col += 32) {
       double re = 0.0, im = 0.0;
+      bool nz = false;  // structurally nonzero: same-channel block or same mesh point
       if (col < N) {
         if (alp == al) {
           const double kij = K[i * nlag + j];
@@ -54,18 +55,22 @@ assemble_kernel(cplx<T>* __restrict__ C, int ld, int N, int nch, int nlag,
           } else {
             re = kij;
           }
+          nz = true;
         } else if (j == i) {
           const double2 v = V[i + (size_t)nlag * (al + (size_t)nch * alp)];
           re = v.x;
           im = v.y;
+          nz = true;
         }
       }
-      if (D && col < N) {
-        const double s = drow * D[col];
-        re *= s;
-        im *= s;
+      // the FP64 scaling only where the entry can be nonzero (FP64 issue rate is low)
+      if (D && nz) {
+        const double sc = drow * D[col];
+        re *= sc;
+        im *= sc;
       }
-      Crow[col] = mkc<T>((T)re, (T)im);
+      // zeros skip the double -> float conversion too (it shares the FP64 pipe)
+      Crow[col] = nz ? mkc<T>((T)re, (T)im) : mkc<T>((T)0, (T)0);
       alp += sq;
       j += sr;
       if (j >= nlag) { j -= nlag; alp += 1; }
