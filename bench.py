@@ -51,6 +51,21 @@ def peaks():
         return dict(FALLBACK_PEAKS), "fallback"
 
 
+def max_over_ranks(ms, dist, device):
+    """The job's time: the slowest rank's (all-reduce MAX; identity on one rank)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, flops_per_step, ms):
+    """Whole-job TFLOP/s of `world` replicas, each doing flops_per_step per step."""
+    return world * flops_per_step / (ms * 1e-3) / 1e12
+
+
 def paired_update_bytes(N, nb, plane_bytes):
     """Algorithmic bytes of each tensor-core factor update launch with paired panels:
     C read + write (16 B per complex64 element) plus the operand planes (4 per
@@ -539,13 +554,12 @@ def main():
     run = Runner(p, prec, local)
     with ClockSampler(local) as clk:
         ms, stats, launches = time_steps(run, args.steps, args.warmup, sync_all)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     flops = lu_flops(p.N, p.nch)
-    value = world * flops / (ms * 1e-3) / 1e12
+    value = replica_throughput(world, flops, ms)
+    sync_all()
     e2e_ms, h2d, d2h = time_e2e(run, max(1, min(args.steps, 3)))
+    e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
     U32 = run.U_host()
     ir = dict(run.last)
     run.close()
@@ -632,7 +646,7 @@ def main():
                    "kernel_ms": {k: [stats.get(k + "_ms"), stats.get(k + "_launches")]
                                  for k in ("panel", "apply_inv", "solve_tc", "resid")}},
         "fp64_path": fp64,
-        "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+        "e2e": {"value": replica_throughput(world, flops, e2e_ms), "unit": "TFLOP/s",
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "paper_context": {

@@ -1,0 +1,65 @@
+"""The N > 1 path of bench.py (replicas, one system per rank) on CPU: two gloo ranks.
+
+Each GPU rank solves its own system with no data-path collective; the only
+cross-rank steps are the barriers around the timed region and the MAX reduction of
+the step time (the job's time is the slowest rank's).  These run here with gloo.
+"""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    dist.barrier()
+    ms = 10.0 + 5.0 * rank                       # rank 1 is the slow one
+    job_ms = bench.max_over_ranks(ms, dist, "cpu")
+    value = bench.replica_throughput(world, bench.lu_flops(25600, 256), job_ms)
+    dist.barrier()
+    with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as f:
+        json.dump({"job_ms": job_ms, "value": value}, f)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time(tmp_path):
+    world, port = 2, _free_port()
+    mp.start_processes(_rank_main, args=(world, port, str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    import bench  # noqa: E402  (ROOT is on sys.path via conftest)
+    res = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(world)]
+    assert res[0] == res[1]
+    assert res[0]["job_ms"] == 15.0
+    expect = 2 * bench.lu_flops(25600, 256) / 15e-3 / 1e12
+    assert abs(res[0]["value"] - expect) < 1e-9 * expect
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(12.5, None, "cpu") == 12.5
+    assert bench.replica_throughput(1, 2e12, 1000.0) == pytest.approx(2.0)
+
+
+def test_reference_arm_non_zero_rank_exits_quietly():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
