@@ -178,6 +178,11 @@ class Runner:
         self.last = {"status": st, "iters": it, "rel_resid": rel,
                      "history": [float("%.3g" % h) for h in g.rmat_refine_history(self.ctx)]}
 
+    def XR_host(self):
+        """X (N x nrhs) and R (nch x nch) of the last step, host complex128."""
+        self.torch.cuda.synchronize()
+        return self.X.cpu().numpy().T, self.R.cpu().numpy().reshape(self.p.nch, self.p.nch).T
+
     def U_host(self):
         n = self.nopen
         return self.U.cpu().numpy()[:n * n].reshape(n, n).T
@@ -561,6 +566,7 @@ def main():
     e2e_ms, h2d, d2h = time_e2e(run, max(1, min(args.steps, 3)))
     e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
     U32 = run.U_host()
+    X32, R32 = run.XR_host() if not args.no_fp64 else (None, None)
     ir = dict(run.last)
     run.close()
 
@@ -577,9 +583,15 @@ def main():
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
         U64 = r64.U_host()
+        X64, R64 = r64.XR_host()
+
+        def rd(a, b):
+            return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
         fp64 = {"ms_per_step": ms64, "tflops": flops / (ms64 * 1e-3) / 1e12,
                 "refine": dict(r64.last),
-                "u_rel_diff_fp32ir_vs_fp64": float(np.max(np.abs(U32 - U64)) / np.max(np.abs(U64))),
+                "u_rel_diff_fp32ir_vs_fp64": rd(U32, U64),
+                "r_rel_diff_fp32ir_vs_fp64": rd(R32, R64),
+                "x_rel_diff_fp32ir_vs_fp64": rd(X32, X64),
                 "speedup_fp32ir_over_fp64": ms64 / ms}
         r64.close()
 
