@@ -21,6 +21,16 @@ in Sec. 2:
 
 Draw order from ``numpy.random.default_rng(seed)``: the nch-1 thresholds, then
 the strict upper triangle of s in row-major order.
+
+Charged channels (``charged_problem``) add the Coulomb interaction of a
+uniformly charged sphere of radius Rc to each diagonal potential,
+V_C(r) = zz_c / r for r >= Rc and zz_c (3 - r^2/Rc^2) / (2 Rc) inside, with
+zz_c = Z1 Z2 e^2 (MeV fm) per channel, and leave the asymptotic region to the
+Coulomb functions (Sommerfeld parameter eta_c = zz_c / (2 hm k_c)).  The
+recipe follows the paper's charged-particle validation case, alpha + 208Pb
+elastic scattering at E_cm = 10-50 MeV with l up to 20 (Sec. 5, physical
+validation): reduced mass 4*208/212 amu, Z1 Z2 = 2*82, a generic complex
+Woods-Saxon in place of the published optical potential.
 """
 from __future__ import annotations
 
@@ -29,6 +39,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 HM_1AMU = 20.9  # hbar^2 / 2 mu in MeV fm^2 for a reduced mass of 1 amu
+E2 = 1.44       # e^2 in MeV fm
 
 
 @dataclass
@@ -48,6 +59,8 @@ class CCProblem:
     R0: float = 4.0               # WS radius, fm
     ad: float = 0.65              # WS diffuseness, fm
     bloch_B: float = 0.0          # Bloch boundary constant
+    zz: np.ndarray | None = None  # (nch,) float64 Z1 Z2 e^2 per channel, MeV fm (None: neutral)
+    Rc: float = 0.0               # Coulomb radius of the uniformly charged sphere, fm
     seed: int = 0
     tag: str = field(default="")
 
@@ -92,7 +105,31 @@ def potential_at(p: CCProblem, r: np.ndarray) -> np.ndarray:
     diag = (p.V0 + 1j * p.W) * ws
     for c in range(p.nch):
         V[c, c, :] = diag
+        if p.zz is not None and p.zz[c] != 0.0:
+            V[c, c, :] += coulomb_potential(float(p.zz[c]), p.Rc, r)
     return np.ascontiguousarray(V)
+
+
+def coulomb_potential(zz: float, Rc: float, r: np.ndarray) -> np.ndarray:
+    """Uniformly charged sphere: zz/r outside Rc, zz (3 - r^2/Rc^2)/(2 Rc) inside (Rc=0: point)."""
+    r = np.asarray(r, dtype=np.float64)
+    if Rc <= 0.0:
+        return zz / r
+    inside = zz * (3.0 - (r / Rc) ** 2) / (2.0 * Rc)
+    return np.where(r >= Rc, zz / np.maximum(r, Rc), inside)
+
+
+def charged_problem(seed: int, nch: int, nlag: int, E: float = 30.0, *, a: float = 16.0,
+                    Z1Z2: float = 2.0 * 82.0, mu_amu: float = 4.0 * 208.0 / 212.0,
+                    V0: float = -100.0, W: float = -10.0, R0: float = 7.7, ad: float = 0.6,
+                    Rc: float = 7.7, tag: str = "") -> CCProblem:
+    """Charged-particle system shaped like alpha + 208Pb: thresholds and couplings
+    as ``make_problem`` draws them from ``seed``, every channel charged."""
+    p = make_problem(seed, nch, nlag, E, a=a, hm=HM_1AMU / mu_amu, V0=V0, W=W, R0=R0,
+                     ad=ad, tag=tag)
+    p.zz = np.full(nch, Z1Z2 * E2)
+    p.Rc = Rc
+    return p
 
 
 # --- the five benchmark configurations ------------------------------------

@@ -1,4 +1,4 @@
-"""R-matrix contraction and collision matrix U for neutral channels (oracle).
+"""R-matrix contraction and collision matrix U (oracle).
 
 TEST INFRASTRUCTURE: imported only by tests, smoke() and bench's CPU legs.
 
@@ -109,13 +109,31 @@ def whittaker_reduced(l: int, rho: float):
     return e * w, e * dw
 
 
+def sommerfeld(p, k: np.ndarray) -> np.ndarray:
+    """eta_c = zz_c / (2 hm k_c) (zz = Z1 Z2 e^2 of the channel; 0 when neutral)."""
+    zz = getattr(p, "zz", None)
+    if zz is None:
+        return np.zeros_like(k)
+    return np.asarray(zz, dtype=np.float64) / (2.0 * p.hm * k)
+
+
 def channel_functions(p):
-    """Per-channel (open, k, I, O, I', O') at rho = k a (Bloch-shifted derivatives)."""
+    """Per-channel (open, k, I, O, I', O') at rho = k a (Bloch-shifted derivatives).
+
+    Neutral channels (eta = 0) take the Riccati-Bessel and reduced Whittaker
+    functions below; charged ones the Coulomb functions F_l(eta, rho),
+    G_l(eta, rho) and the Whittaker function W_{-eta,l+1/2}(2 rho) of
+    oracle.coulomb, with the same I = G - iF, O = G + iF (open) and O = W, I = 0
+    (closed).
+    """
+    from .coulomb import coulomb_fg, whittaker_w
+
     ecm = p.E - np.asarray(p.thresh, dtype=np.float64)
     if np.any(ecm == 0.0):
         raise ValueError("a channel sits exactly at threshold")
     is_open = ecm > 0
     k = np.sqrt(np.abs(ecm) / p.hm)
+    eta = sommerfeld(p, k)
     I = np.zeros(p.nch, dtype=np.complex128)
     O = np.zeros(p.nch, dtype=np.complex128)
     dI = np.zeros(p.nch, dtype=np.complex128)
@@ -123,11 +141,17 @@ def channel_functions(p):
     for c in range(p.nch):
         rho = k[c] * p.a
         if is_open[c]:
-            F, G, dF, dG = riccati_bessel(int(p.l[c]), rho)
+            if eta[c] == 0.0:
+                F, G, dF, dG = riccati_bessel(int(p.l[c]), rho)
+            else:
+                F, G, dF, dG = coulomb_fg(int(p.l[c]), float(eta[c]), rho)
             I[c], O[c] = G - 1j * F, G + 1j * F
             dI[c], dO[c] = dG - 1j * dF, dG + 1j * dF
         else:
-            w, dw = whittaker_reduced(int(p.l[c]), rho)
+            if eta[c] == 0.0:
+                w, dw = whittaker_reduced(int(p.l[c]), rho)
+            else:
+                w, dw = whittaker_w(int(p.l[c]), float(eta[c]), rho)
             O[c], dO[c] = w, dw
         dI[c] -= p.bloch_B / rho * I[c]
         dO[c] -= p.bloch_B / rho * O[c]

@@ -4,8 +4,9 @@
 // K_alpha + D_alpha,alpha (full nlag x nlag kinetic + Bloch matrix plus the
 // diagonal potential, centrifugal term, threshold and -E), off-diagonal blocks
 // D_alpha,alpha' = diag(V_alpha,alpha'(r_i)) (local potentials).  Row-major
-// storage; every entry of the N x ld matrix is written once (HBM write-bound:
-// 8 N^2 bytes in complex64, 16 N^2 in complex128).
+// storage; every entry of the N x ld matrix is written (HBM write-bound:
+// 8 N ld bytes in complex64, 16 N ld in complex128; the few nonzeros that share
+// a 16-byte chunk with zeros are written twice).
 //
 // Entries are formed in FP64 with explicitly rounded operations in this order:
 //   K_ij     = hm*T0_ij - (hm*(B/a)) * (f_i*f_j)            (host table Kmat)
@@ -23,8 +24,13 @@ __device__ __forceinline__ double chan_diag(double hm, int l, double ri, double 
   return __dadd_rn(__ddiv_rn(__dmul_rn(hm, ll1), __dmul_rn(ri, ri)), __dsub_rn(th, E));
 }
 
-// One warp per row; lanes stride the columns, tracking (channel, mesh index)
-// of their column incrementally instead of dividing.
+// One warp per row.  The row is mostly structural zeros (all but the nlag
+// same-channel columns and one column per other channel), so the warp first
+// clears it with 16-byte stores, skipping the chunks that lie inside the
+// same-channel block, and after __syncwarp writes the nonzeros: the
+// same-channel block (contiguous, lane-strided) and the nch-1 entries
+// (al', i) of the local couplings.  __syncwarp orders the two passes, so a
+// nonzero that shares a 16-byte chunk with cleared columns is written last.
 template <class T>
 __global__ void __launch_bounds__(256)
 assemble_kernel(cplx<T>* __restrict__ C, int ld, int N, int nch, int nlag,
@@ -32,6 +38,7 @@ assemble_kernel(cplx<T>* __restrict__ C, int ld, int N, int nch, int nlag,
                 const int* __restrict__ l, const double* __restrict__ th,
                 const double2* __restrict__ V, double hm, double E,
                 const double* __restrict__ D) {
+  constexpr int CPC = 16 / (int)sizeof(cplx<T>);  // complex entries per 16-byte chunk
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -40,40 +47,47 @@ assemble_kernel(cplx<T>* __restrict__ C, int ld, int N, int nch, int nlag,
     const double d = chan_diag(hm, l[al], r[i], th[al], E);
     const double drow = D ? D[row] : 1.0;
     cplx<T>* Crow = C + (size_t)row * ld;
-    int alp = lane / nlag, j = lane - alp * nlag;
-    const int sq = 32 / nlag, sr = 32 - sq * nlag;  // 32 = sq*nlag + sr
-    for (int col = lane; col < ld; col += 32) {
-      double re = 0.0, im = 0.0;
-      bool nz = false;  // structurally nonzero: same-channel block or same mesh point
-      if (col < N) {
-        if (alp == al) {
-          const double kij = K[i * nlag + j];
-          if (j == i) {
-            const double2 v = V[i + (size_t)nlag * (al + (size_t)nch * al)];
-            re = __dadd_rn(kij, __dadd_rn(d, v.x));
-            im = v.y;
-          } else {
-            re = kij;
-          }
-          nz = true;
-        } else if (j == i) {
-          const double2 v = V[i + (size_t)nlag * (al + (size_t)nch * alp)];
-          re = v.x;
-          im = v.y;
-          nz = true;
-        }
+    const int b0 = al * nlag, b1 = b0 + nlag;  // same-channel columns [b0, b1)
+    if ((reinterpret_cast<uintptr_t>(Crow) & 15) == 0 && ld % CPC == 0) {
+      uint4* C4 = reinterpret_cast<uint4*>(Crow);
+      const int nq = ld / CPC;
+      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll 4
+      for (int q = lane; q < nq; q += 32) {
+        const int c0 = q * CPC;
+        if (c0 >= b0 && c0 + CPC <= b1) continue;
+        C4[q] = z;
       }
-      // the FP64 scaling only where the entry can be nonzero (FP64 issue rate is low)
-      if (D && nz) {
+    } else {
+      for (int col = lane; col < ld; col += 32)
+        if (col < b0 || col >= b1) Crow[col] = mkc<T>((T)0, (T)0);
+    }
+    __syncwarp();
+    for (int j = lane; j < nlag; j += 32) {  // same-channel block K_al + D_al,al
+      double re = K[i * nlag + j], im = 0.0;
+      if (j == i) {
+        const double2 v = V[i + (size_t)nlag * (al + (size_t)nch * al)];
+        re = __dadd_rn(re, __dadd_rn(d, v.x));
+        im = v.y;
+      }
+      if (D) {
+        const double sc = drow * D[b0 + j];
+        re *= sc;
+        im *= sc;
+      }
+      Crow[b0 + j] = mkc<T>((T)re, (T)im);
+    }
+    for (int alp = lane; alp < nch; alp += 32) {  // D_al,al' = diag(V_al,al'(r_i))
+      if (alp == al) continue;
+      const double2 v = V[i + (size_t)nlag * (al + (size_t)nch * alp)];
+      double re = v.x, im = v.y;
+      const int col = alp * nlag + i;
+      if (D) {
         const double sc = drow * D[col];
         re *= sc;
         im *= sc;
       }
-      // zeros skip the double -> float conversion too (it shares the FP64 pipe)
-      Crow[col] = nz ? mkc<T>((T)re, (T)im) : mkc<T>((T)0, (T)0);
-      alp += sq;
-      j += sr;
-      if (j >= nlag) { j -= nlag; alp += 1; }
+      Crow[col] = mkc<T>((T)re, (T)im);
     }
   }
 }
