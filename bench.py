@@ -161,7 +161,7 @@ class Runner:
         self.V_host = cp.potential_at(p, m["r"]).ravel()
         self.Vd = torch.from_numpy(self.V_host).cuda()
         self.prob, self._keep = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh,
-                                                      precision)
+                                                      precision, zz=p.zz)
         self.precision = precision
         self.nopen = int(np.sum(p.E - p.thresh > 0))
         self.X = torch.zeros((p.nch, p.N), dtype=torch.complex128, device="cuda")
@@ -326,7 +326,7 @@ def batch_main(args):
     for p in probs:
         m = g.rmat_mesh(p.nlag, p.a)
         Vs.append(torch.from_numpy(cp.potential_at(p, m["r"]).ravel()).cuda())
-        s, k = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh, prec)
+        s, k = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh, prec, zz=p.zz)
         structs.append(s)
         keep.append(k)
     b = g.rmat_batch_create(ctx, structs, [p.E for p in probs], [v.data_ptr() for v in Vs],
@@ -410,7 +410,8 @@ def solve_once(p, precision, device=0, warm=False, energies=None):
     ctx = g.rmat_create(device, stream.cuda_stream)
     m = g.rmat_mesh(p.nlag, p.a)
     Vd = torch.from_numpy(cp.potential_at(p, m["r"]).ravel()).cuda()
-    prob, keep = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh, precision)
+    prob, keep = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh, precision,
+                                       zz=p.zz)
     X = torch.zeros((p.nch, p.N), dtype=torch.complex128, device="cuda")
     R = torch.zeros(p.nch * p.nch, dtype=torch.complex128, device="cuda")
     Es = list(energies) if energies else [p.E]

@@ -51,6 +51,7 @@ extern "C" {
 #define RMAT_ENODEV     (-104)  /* no CUDA device of compute capability 10.3     */
 #define RMAT_ESINGULAR     1    /* exactly zero pivot; info holds its column     */
 #define RMAT_ENOCONV       2    /* refinement stagnated above the tolerance      */
+#define RMAT_ECHANFN       3    /* a Coulomb/Whittaker function did not converge */
 
 /* ---- precisions --------------------------------------------------------- */
 /* complex128 matrix, FP64 LU (panel, TRSM and trailing update on FP64 units). */
@@ -80,6 +81,18 @@ extern "C" {
  * update of depth 2*nb (half the passes over the trailing matrix), 0 = one update
  * per panel.  Results agree to rounding. */
 #define RMAT_PARAM_PAIRED      6
+/* Which matrix an assembled problem factors (the paper's Sec. 3.3 Type 3 split
+ * M = K_diag + V_coupling, K the real kinetic + Bloch matrix shared by all channels):
+ *   0 (default) M itself;
+ *   1 Woodbury-kinetic: S = I + (K^-1 (x) I_nch) W in radial-major order
+ *     ((i, al) -> i*nch + al), S[(i,al),(j,al')] = delta + Kinv[i][j] W_al,al'(r_j),
+ *     W the per-point coupling (potential + centrifugal + threshold - E).  Every
+ *     solve maps its right-hand side through K^-1 (FP64 accumulation) and reorders;
+ *     the refinement keeps the FP64 residual of M, so X, R and U are those of M
+ *     to the same tolerance.  K^-1 is formed once per mesh (host FP64).
+ *     Equilibration is not applied to S.  Not used by rmat_load_dense or batches.
+ * Takes effect at the next rmat_assemble. */
+#define RMAT_PARAM_METHOD      7
 
 typedef struct rmat_ctx_s* rmat_ctx;
 
@@ -96,6 +109,10 @@ typedef struct {
   const int* l;          /* host [nch]: orbital momentum of each channel, >= 0 */
   const double* thresh;  /* host [nch]: channel threshold energies (MeV)       */
   int precision;         /* one of the RMAT_C128 / RMAT_C64_* precisions above */
+  const double* zz;      /* host [nch] or NULL: Z1 Z2 e^2 of each channel (MeV fm),
+                            >= 0 (repulsive); NULL or 0 = neutral channel.  The
+                            Coulomb potential itself belongs in V; zz only selects
+                            the asymptotic functions (eta_c = zz_c / (2 hm k_c)). */
 } rmat_problem;
 
 /* Create a context bound to CUDA device `device` and stream `stream` (a
@@ -178,16 +195,22 @@ int rmat_solve(rmat_ctx ctx, void* X_dev, int ldx, int max_refine, double tol,
 
 /* R-matrix and collision matrix of the last solved assembled problem.
  *   R[al][be] = (hm/a) sum_i f_i(a) X[(al,i), be]    (dimensionless, nch x nch)
- *   k_c = sqrt(|E - E_c| / hm), rho_c = k_c a; open channels (E > E_c):
- *   I = G - iF, O = G + iF with Riccati-Bessel F_l = rho j_l, G_l = -rho y_l
- *   (eta = 0); closed: O = e^-rho sum_k (l+k)!/(k!(l-k)!) (2 rho)^-k, I = 0;
+ *   k_c = sqrt(|E - E_c| / hm), rho_c = k_c a, eta_c = zz_c / (2 hm k_c);
+ *   open channels (E > E_c): I = G - iF, O = G + iF with the Coulomb functions
+ *   F_l(eta, rho), G_l(eta, rho) (Sec. 4.1; Riccati-Bessel F_l = rho j_l,
+ *   G_l = -rho y_l when eta = 0), by Steed's continued fractions and, inside
+ *   the Coulomb turning point, inward Taylor-series integration of G;
+ *   closed channels: O = W_{-eta,l+1/2}(2 rho) (for eta = 0 the closed form
+ *   e^-rho sum_k (l+k)!/(k!(l-k)!) (2 rho)^-k; for eta > 0 O = 1, O' = W'/W,
+ *   which gives the same U), I = 0;
  *   O' -> O' - (B/rho) O, I' -> I' - (B/rho) I;  R~ = a sqrt(k) R sqrt(k);
  *   U = (diag O - R~ diag O')^-1 (diag I - R~ diag I'), open x open block.
  * R_dev: device complex128 nch x nch column-major (may be NULL).
  * U_dev: device complex128 nopen x nopen column-major, open channels in
  * channel order (may be NULL).  nopen: host int (may be NULL).
  * Synchronises.  Errors: -1 ctx, RMAT_ESTATE (no solved assembled problem),
- * RMAT_ESINGULAR (the matching matrix is singular). */
+ * RMAT_ESINGULAR (the matching matrix is singular), RMAT_ECHANFN (a channel
+ * function did not converge within its iteration bound or overflowed). */
 int rmat_collision(rmat_ctx ctx, void* R_dev, void* U_dev, int* nopen);
 
 /* Counters and timers of the last factor/solve, for benchmarks:
@@ -283,7 +306,7 @@ int rmat_batch_destroy(rmat_batch b);
  * Errors: -1 prob invalid or nch > RMAT_NOALLOC_MAX_NCH, -2 E invalid or a channel
  * exactly at threshold, -3 f_a_dev NULL, -4 X_dev NULL, -5 ldx < N, -7 U_dev NULL
  * with open channels, RMAT_ESINGULAR for an exactly singular matching system,
- * RMAT_ECUDA. */
+ * RMAT_ECHANFN for a channel function that did not converge, RMAT_ECUDA. */
 #define RMAT_NOALLOC_MAX_NCH 64
 int rmat_collision_noalloc(const rmat_problem* prob, double E, const void* f_a_dev,
                            const void* X_dev, int ldx, void* R_dev, void* U_dev, int* nopen,

@@ -25,6 +25,7 @@ RMAT_ETIMEOUT = -103
 RMAT_ENODEV = -104
 RMAT_ESINGULAR = 1
 RMAT_ENOCONV = 2
+RMAT_ECHANFN = 3
 
 RMAT_C128 = 0
 RMAT_C64_3XTF32_IR = 1
@@ -52,7 +53,8 @@ EXPORTED = ("rmat_create", "rmat_destroy", "rmat_set_param", "rmat_mesh", "rmat_
 class rmat_problem(ct.Structure):
     _fields_ = [("nch", ct.c_int), ("nlag", ct.c_int), ("a", ct.c_double), ("hm", ct.c_double),
                 ("bloch_B", ct.c_double), ("l", ct.POINTER(ct.c_int)),
-                ("thresh", ct.POINTER(ct.c_double)), ("precision", ct.c_int)]
+                ("thresh", ct.POINTER(ct.c_double)), ("precision", ct.c_int),
+                ("zz", ct.POINTER(ct.c_double))]
 
 
 class RmatError(RuntimeError):
@@ -153,14 +155,19 @@ def rmat_mesh(nlag: int, a: float) -> dict:
     return out
 
 
-def make_problem_struct(nch, nlag, a, hm, l, thresh, precision, bloch_B=0.0):
-    """rmat_problem plus the host arrays it points to (keep the tuple alive)."""
+def make_problem_struct(nch, nlag, a, hm, l, thresh, precision, bloch_B=0.0, zz=None):
+    """rmat_problem plus the host arrays it points to (keep the tuple alive).
+
+    zz: per-channel Z1 Z2 e^2 (MeV fm) of charged channels, None = all neutral."""
     l_arr = np.ascontiguousarray(l, dtype=np.int32)
     t_arr = np.ascontiguousarray(thresh, dtype=np.float64)
+    z_arr = None if zz is None else np.ascontiguousarray(zz, dtype=np.float64)
+    z_ptr = (ct.POINTER(ct.c_double)() if z_arr is None
+             else z_arr.ctypes.data_as(ct.POINTER(ct.c_double)))
     s = rmat_problem(int(nch), int(nlag), float(a), float(hm), float(bloch_B),
                      l_arr.ctypes.data_as(ct.POINTER(ct.c_int)),
-                     t_arr.ctypes.data_as(ct.POINTER(ct.c_double)), int(precision))
-    return s, (l_arr, t_arr)
+                     t_arr.ctypes.data_as(ct.POINTER(ct.c_double)), int(precision), z_ptr)
+    return s, (l_arr, t_arr, z_arr)
 
 
 def rmat_assemble(ctx: int, prob: rmat_problem, E: float, V_dev: int) -> None:

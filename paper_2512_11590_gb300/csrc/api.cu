@@ -216,6 +216,7 @@ const char* rmat_status_string(int s) {
     case RMAT_ENODEV: return "no compute capability 10.3 device";
     case RMAT_ESINGULAR: return "exactly singular pivot";
     case RMAT_ENOCONV: return "refinement stagnated above tolerance";
+    case RMAT_ECHANFN: return "a Coulomb/Whittaker channel function did not converge";
     default: return s < 0 && s > -100 ? "invalid argument" : "unknown status";
   }
 }
@@ -277,13 +278,13 @@ int rmat_destroy(rmat_ctx c) {
   cudaStreamSynchronize(c->stream);
   if (c->sg_exec) cudaGraphExecDestroy(c->sg_exec);
   if (c->borrowed_tables) c->Kmat = c->T0 = c->rmesh = c->fa = nullptr, c->l_d = nullptr,
-                          c->th_d = nullptr, c->open_d = nullptr;
+                          c->th_d = nullptr, c->zz_d = nullptr, c->open_d = nullptr;
   tc_release(c);
   void* bufs[] = {c->C,    c->A64,  c->B64, c->ipiv, c->Kmat, c->T0,  c->rmesh,
-                  c->fa,   c->l_d,  c->th_d, c->Wpt, c->X,    c->Rres, c->Bw,
+                  c->fa,   c->l_d,  c->th_d, c->zz_d, c->Wpt, c->X,  c->Rres, c->Bw,
                   c->Fpl,  c->Bpl, c->Ypl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
                   c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows, c->Dinv,
-                  c->umax, c->uscale, c->ycs, c->pfwd, c->Bt};
+                  c->umax, c->uscale, c->ycs, c->pfwd, c->Bt, c->Kinv, c->Kinv32, c->W32, c->Bs};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->hstat) cudaFreeHost(c->hstat);
@@ -318,6 +319,10 @@ int rmat_set_param(rmat_ctx c, int key, long long v) {
       if (v < 0 || v > 1) return -3;
       c->paired = (int)v;
       return RMAT_OK;
+    case RMAT_PARAM_METHOD:
+      if (v < 0 || v > 1) return -3;
+      c->method_param = (int)v;
+      return RMAT_OK;
     default:
       return -2;
   }
@@ -335,7 +340,9 @@ int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_de
     return -2;
   if ((long long)pb->nch * pb->nlag > 200000) return -2;
   for (int k = 0; k < pb->nch; ++k)
-    if (pb->l[k] < 0 || pb->l[k] > 64 || !std::isfinite(pb->thresh[k])) return -2;
+    if (pb->l[k] < 0 || pb->l[k] > 64 || !std::isfinite(pb->thresh[k]) ||
+        (pb->zz && !(std::isfinite(pb->zz[k]) && pb->zz[k] >= 0.0)))
+      return -2;
   if (!std::isfinite(E)) return -3;
   if (!V_dev) return -4;
   const bool mesh_same = c->nlag == pb->nlag && c->a == pb->a && c->hm == pb->hm &&
@@ -353,15 +360,23 @@ int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_de
   c->E = E;
   c->l.assign(pb->l, pb->l + pb->nch);
   c->thresh.assign(pb->thresh, pb->thresh + pb->nch);
+  if (pb->zz) c->zz.assign(pb->zz, pb->zz + pb->nch);
+  else c->zz.assign(pb->nch, 0.0);
   c->assembled = c->factored = c->solved = false;
   c->nb = clamp_nb(c->precision, c->nb_param ? c->nb_param : default_nb(c->precision, c->N));
   RMAT_CHECK(reserve(c, false));
-  c->equil = c->equil_param == -1 ? c->precision != RMAT_C128 : c->equil_param == 1;
+  c->woodbury = c->method_param == 1;
+  c->equil = !c->woodbury &&
+             (c->equil_param == -1 ? c->precision != RMAT_C128 : c->equil_param == 1);
   if (c->equil) RMAT_CHECK(rmat_grow(c, (void**)&c->Dsc, &c->Dsc_cap, (size_t)c->N * sizeof(double)));
+  if (c->woodbury)
+    RMAT_CHECK(rmat_grow(c, &c->Bs, &c->Bs_cap,
+                         (size_t)c->N * c->nrhs * (c->precision == RMAT_C128 ? 16 : 8)));
   const int nlag = c->nlag, nch = c->nch;
   RMAT_CHECK(rmat_grow(c, (void**)&c->Wpt, &c->Wpt_cap, (size_t)nlag * nch * nch * 16));
   RMAT_CHECK(rmat_grow(c, (void**)&c->l_d, &c->l_cap, nch * sizeof(int)));
   RMAT_CHECK(rmat_grow(c, (void**)&c->th_d, &c->th_cap, nch * sizeof(double)));
+  RMAT_CHECK(rmat_grow(c, (void**)&c->zz_d, &c->zz_cap, nch * sizeof(double)));
   RMAT_CHECK(rmat_grow(c, (void**)&c->Rint, &c->Rint_cap, (size_t)nch * nch * 16));
   RMAT_CHECK(rmat_grow(c, (void**)&c->Zbuf, &c->Zbuf_cap, collision_workspace_bytes(nch)));
   RMAT_CHECK(rmat_grow(c, (void**)&c->zpiv, &c->zpiv_cap, nch * sizeof(int)));
@@ -380,17 +395,27 @@ int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_de
     RMAT_CU(cudaMemcpy(c->rmesh, r.data(), nlag * 8, cudaMemcpyHostToDevice));
     RMAT_CU(cudaMemcpy(c->fa, fa.data(), nlag * 8, cudaMemcpyHostToDevice));
     c->f_a_host = fa;
+    c->K_host = K;
+    c->kinv_nlag = 0;  // K^-1 belongs to the previous mesh
   }
+  if (c->woodbury && c->kinv_nlag != nlag) RMAT_CHECK(woodbury_prepare(c, c->K_host.data()));
   double pm = 0;
   for (double v : c->f_a_host) pm = std::max(pm, std::fabs(v));
   c->phi_max = pm;
   RMAT_CU(cudaMemcpyAsync(c->l_d, c->l.data(), nch * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   RMAT_CU(cudaMemcpyAsync(c->th_d, c->thresh.data(), nch * sizeof(double), cudaMemcpyHostToDevice,
                           c->stream));
+  RMAT_CU(cudaMemcpyAsync(c->zz_d, c->zz.data(), nch * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
   cudaEvent_t e0, e1;
   record_stage(c, &e0);
-  RMAT_CHECK(launch_assemble(c, reinterpret_cast<const double2*>(V_dev), E));
-  RMAT_CHECK(launch_point_coupling(c, reinterpret_cast<const double2*>(V_dev), E));
+  if (c->woodbury) {  // S is built from the per-point table
+    RMAT_CHECK(launch_point_coupling(c, reinterpret_cast<const double2*>(V_dev), E));
+    RMAT_CHECK(launch_schur_assemble(c));
+  } else {
+    RMAT_CHECK(launch_assemble(c, reinterpret_cast<const double2*>(V_dev), E));
+    RMAT_CHECK(launch_point_coupling(c, reinterpret_cast<const double2*>(V_dev), E));
+  }
   record_stage(c, &e1);
   c->stage_ev[0][0] = e0;
   c->stage_ev[0][1] = e1;
@@ -508,11 +533,21 @@ static int solve_factors(rmat_ctx c) {
   return RMAT_OK;
 }
 
+// One solve of the assembled system with the current factors, in place on Bw.
+// Woodbury-kinetic: Bw -> (I (x) K^-1) Bw in radial-major order, the factors
+// of S, then back to channel-major.
+static int solve_system(rmat_ctx c) {
+  if (!(c->woodbury && c->kind == 1)) return solve_factors(c);
+  RMAT_CHECK(launch_kinv_apply(c));
+  RMAT_CHECK(solve_factors(c));
+  return launch_radial_to_channel(c);
+}
+
 }  // extern "C"
 
 int enqueue_solve_refine(rmat_ctx c, int max_refine, double tol, IrState* st) {
   RMAT_CHECK(launch_w_from_phi(c));
-  RMAT_CHECK(solve_factors(c));
+  RMAT_CHECK(solve_system(c));
   RMAT_CHECK(launch_x_from_w(c));
   RMAT_CHECK(launch_ir_init(c, st));
   const int patience = c->precision == RMAT_C128 ? 2 : 1;
@@ -523,7 +558,7 @@ int enqueue_solve_refine(rmat_ctx c, int max_refine, double tol, IrState* st) {
     rc = launch_residual(c, nullptr);
     if (rc == RMAT_OK) rc = launch_ir_state(c, tol, patience, it == max_refine, st);
     if (rc != RMAT_OK || it == max_refine) break;
-    rc = solve_factors(c);
+    rc = solve_system(c);
     if (rc == RMAT_OK) rc = launch_update(c, st);
   }
   c->skip = nullptr;
@@ -542,7 +577,7 @@ int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int
   cudaEvent_t e0, e1, e2;
   record_stage(c, &e0);
   RMAT_CHECK(launch_w_from_phi(c));
-  RMAT_CHECK(solve_factors(c));
+  RMAT_CHECK(solve_system(c));
   RMAT_CHECK(launch_x_from_w(c));
   record_stage(c, &e1);
   int it = 0, status = RMAT_OK;
@@ -577,7 +612,7 @@ int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int
         stagn = 0;
       }
       prev = rel;
-      RMAT_CHECK(solve_factors(c));
+      RMAT_CHECK(solve_system(c));
       RMAT_CHECK(launch_update(c));
       ++it;
     }
@@ -619,6 +654,7 @@ int rmat_collision(rmat_ctx c, void* R_dev, void* U_dev, int* nopen) {
   c->stage_ev[4][0] = e0;
   c->stage_ev[4][1] = e1;
   if (c->hstat[ST_TIMEOUT]) return RMAT_ETIMEOUT;
+  if (c->hstat[ST_CHANFN]) return RMAT_ECHANFN;
   if (c->hstat[ST_INFO]) return RMAT_ESINGULAR;
   return RMAT_OK;
 }

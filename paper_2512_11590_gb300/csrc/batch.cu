@@ -65,6 +65,7 @@ struct rmat_batch_s {
   std::vector<MeshTab> meshes;
   int* l_all = nullptr;
   double* th_all = nullptr;
+  double* zz_all = nullptr;
   int* open_all = nullptr;
   IrState* ir = nullptr;
   int* st_dev = nullptr;
@@ -118,8 +119,10 @@ int enqueue_system(rmat_batch b, int s, void* U) {
   c->phi_max = m.phi_max;
   c->l_d = b->l_all + y.off_l;
   c->th_d = b->th_all + y.off_l;
+  c->zz_d = b->zz_all + y.off_l;
   c->open_d = b->open_all + y.off_open;
   c->borrowed_tables = true;
+  c->woodbury = false;  // batches factor M itself
   c->equil = c->equil_param == -1 ? b->precision != RMAT_C128 : c->equil_param == 1;
   RMAT_CHECK(perm_reserve(c, c->perm_main, y.N, c->nb));  // lay out, no growth (plan sized it)
   RMAT_CU(cudaMemsetAsync(c->dstat, 0, ST_COUNT * sizeof(int), c->stream));
@@ -327,6 +330,8 @@ int rmat_batch_create(rmat_ctx ctx, int nsys, const rmat_problem* probs, const d
         !p.thresh || p.precision != prec || (long long)p.nch * p.nlag > 200000 ||
         !std::isfinite(E[s]) || !V_dev[s])
       return -3;
+    for (int k = 0; k < p.nch; ++k)
+      if (p.zz && !(std::isfinite(p.zz[k]) && p.zz[k] >= 0.0)) return -3;
     if (prec != RMAT_C128 && prec != RMAT_C64_3XTF32_IR && prec != RMAT_C64_SIMT_IR &&
         prec != RMAT_C64_3XF16_IR)
       return -3;
@@ -338,7 +343,7 @@ int rmat_batch_create(rmat_ctx ctx, int nsys, const rmat_problem* probs, const d
   b->max_refine = max_refine;
   b->tol = tol;
   std::vector<int> l_h, open_h;
-  std::vector<double> th_h;
+  std::vector<double> th_h, zz_h;
   for (int s = 0; s < nsys; ++s) {
     const rmat_problem& p = probs[s];
     BatchSys y{};
@@ -356,6 +361,7 @@ int rmat_batch_create(rmat_ctx ctx, int nsys, const rmat_problem* probs, const d
     for (int k = 0; k < p.nch; ++k) {
       l_h.push_back(p.l[k]);
       th_h.push_back(p.thresh[k]);
+      zz_h.push_back(p.zz ? p.zz[k] : 0.0);
       if (E[s] - p.thresh[k] > 0) open_h.push_back(k);
     }
     y.nopen = (int)(open_h.size() - y.off_open);
@@ -395,6 +401,7 @@ int rmat_batch_create(rmat_ctx ctx, int nsys, const rmat_problem* probs, const d
   const size_t nl = l_h.size(), no = std::max<size_t>(1, open_h.size());
   if (cudaMalloc(&b->l_all, nl * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&b->th_all, nl * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&b->zz_all, nl * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&b->open_all, no * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&b->ir, nsys * sizeof(IrState)) != cudaSuccess ||
       cudaMalloc(&b->st_dev, (size_t)nsys * ST_COUNT * sizeof(int)) != cudaSuccess ||
@@ -406,6 +413,7 @@ int rmat_batch_create(rmat_ctx ctx, int nsys, const rmat_problem* probs, const d
   }
   cudaMemcpy(b->l_all, l_h.data(), nl * sizeof(int), cudaMemcpyHostToDevice);
   cudaMemcpy(b->th_all, th_h.data(), nl * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(b->zz_all, zz_h.data(), nl * sizeof(double), cudaMemcpyHostToDevice);
   if (!open_h.empty())
     cudaMemcpy(b->open_all, open_h.data(), open_h.size() * sizeof(int), cudaMemcpyHostToDevice);
   b->lane_stream[0] = ctx->stream;
@@ -509,6 +517,7 @@ int rmat_batch_run(rmat_batch b, void* const* U_dev, int* status, int* iters) {
     const int* w = b->st_host + s * ST_COUNT;
     int st = b->ir_host[s].status;
     if (w[ST_INFO]) st = RMAT_ESINGULAR;
+    if (w[ST_CHANFN]) st = RMAT_ECHANFN;
     if (w[ST_BADARG]) st = RMAT_ESTATE;
     if (w[ST_TIMEOUT]) st = RMAT_ETIMEOUT;
     if (status) status[s] = st;
@@ -547,6 +556,7 @@ int rmat_batch_destroy(rmat_batch b) {
   }
   cudaFree(b->l_all);
   cudaFree(b->th_all);
+  cudaFree(b->zz_all);
   cudaFree(b->open_all);
   cudaFree(b->ir);
   cudaFree(b->st_dev);

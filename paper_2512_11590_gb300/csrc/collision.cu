@@ -4,11 +4,12 @@
 // with C in MeV the dimensionless R-matrix carries hm/a:
 //   R = (hm/a) Phi^T X.
 // U: matching to the free asymptotic solutions at the channel radius (Sec. 1,
-// Coulomb/Whittaker functions of Sec. 4.1, here eta = 0):
+// Coulomb/Whittaker functions of Sec. 4.1):
 //   R~ = a sqrt(k) R sqrt(k),
 //   U  = (diag O - R~ diag O')^-1 (diag I - R~ diag I'),  open x open block,
-// I = G - iF, O = G + iF (Riccati-Bessel F = rho j_l, G = -rho y_l) for open
-// channels; O = reduced Whittaker function, I = 0 for closed ones.  The
+// I = G - iF, O = G + iF (Coulomb functions; Riccati-Bessel F = rho j_l,
+// G = -rho y_l for eta = 0) for open channels; O = Whittaker function (or, for
+// eta > 0, O = 1 and O' = W'/W), I = 0 for closed ones (special.cuh).  The
 // matching system (nch x nch, nopen right-hand sides) is solved with this
 // library's FP64 LU.
 #include <algorithm>
@@ -41,34 +42,16 @@ struct ChanFn {
   double k;
 };
 
+// One thread per channel; a channel function that does not converge sets
+// status (1 + channel) and the host reports RMAT_ECHANFN.
 __global__ void chan_fn_kernel(ChanFn* __restrict__ out, int nch, const int* __restrict__ l,
-                               const double* __restrict__ th, double E, double hm, double a,
-                               double B) {
+                               const double* __restrict__ th, const double* __restrict__ zz,
+                               double E, double hm, double a, double B, int* __restrict__ status) {
   const int ch = blockIdx.x * blockDim.x + threadIdx.x;
   if (ch >= nch) return;
-  const double ecm = E - th[ch];
-  const double k = sqrt(fabs(ecm) / hm), rho = k * a;
   ChanFn f;
-  f.k = k;
-  if (ecm > 0) {
-    double F, G, dF, dG;
-    riccati_fg(l[ch], rho, &F, &G, &dF, &dG);
-    f.I = make_double2(G, -F);
-    f.O = make_double2(G, F);
-    f.dI = make_double2(dG, -dF);
-    f.dO = make_double2(dG, dF);
-  } else {
-    double W, dW;
-    whittaker_w(l[ch], rho, &W, &dW);
-    f.I = make_double2(0, 0);
-    f.dI = make_double2(0, 0);
-    f.O = make_double2(W, 0);
-    f.dO = make_double2(dW, 0);
-  }
-  f.dI.x -= B / rho * f.I.x;
-  f.dI.y -= B / rho * f.I.y;
-  f.dO.x -= B / rho * f.O.x;
-  f.dO.y -= B / rho * f.O.y;
+  if (!channel_functions(l[ch], E - th[ch], hm, a, B, zz[ch], &f.I, &f.O, &f.dI, &f.dO, &f.k))
+    *status = 1 + ch;
   out[ch] = f;
 }
 
@@ -120,8 +103,9 @@ int launch_collision(rmat_ctx c, double2* R_dev, double2* U_dev, int nopen) {
   double2* ZO = reinterpret_cast<double2*>(reinterpret_cast<char*>(c->Zbuf) +
                                            round_up(sizeof(ChanFn) * nch, 256));
   double2* ZI = ZO + (size_t)nch * nch;
-  chan_fn_kernel<<<ceil_div(nch, 64), 64, 0, c->stream>>>(fn, nch, c->l_d, c->th_d, c->E, c->hm,
-                                                           c->a, c->bloch_B);
+  chan_fn_kernel<<<ceil_div(nch, 64), 64, 0, c->stream>>>(fn, nch, c->l_d, c->th_d, c->zz_d, c->E,
+                                                           c->hm, c->a, c->bloch_B,
+                                                           c->dstat + ST_CHANFN);
   z_build_kernel<<<ceil_div((long long)nch * (nch + nopen), 128), 128, 0, c->stream>>>(
       c->Rint, fn, nch, nopen, c->open_d, c->a, ZO, ZI);
   c->launches += 2;

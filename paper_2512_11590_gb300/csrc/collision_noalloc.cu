@@ -16,6 +16,7 @@
 // but in a single CTA: R contraction, channel functions, the matching system,
 // Gaussian elimination with partial pivoting (largest |Re|+|Im|, first row on
 // ties) carrying the right-hand sides, and back substitution.
+#include <cmath>
 #include <cstring>
 
 #include "cplx.cuh"
@@ -33,7 +34,8 @@ struct NoallocScratch {
   double2 ZI[MAXC * MAXC];  // right-hand sides diag I - R~ diag I' (open columns)
   double2 I[MAXC], O[MAXC], dI[MAXC], dO[MAXC];
   double k[MAXC];
-  int status;               // 0 ok, 1 + column of an exactly zero pivot
+  int status;               // 0 ok, 1 + column of an exactly zero pivot,
+                            // -(1 + channel) for a channel function that did not converge
 };
 
 // Scratch shared by every call on this device (contents persist between calls).
@@ -44,6 +46,7 @@ struct NoallocParams {
   double a, hm, B, E;
   int l[MAXC];
   double thresh[MAXC];
+  double zz[MAXC];
   int open[MAXC];
 };
 
@@ -68,29 +71,14 @@ collision_noalloc_kernel(const NoallocParams p, const double* __restrict__ fa,
     S->R[e] = r;
     if (Rout) Rout[al + (size_t)nch * be] = r;
   }
+  __syncthreads();  // status cleared before any channel can report
   // channel functions at rho = k a
   for (int ch = tid; ch < nch; ch += NA_THREADS) {
-    const double ecm = p.E - p.thresh[ch];
-    const double k = sqrt(fabs(ecm) / p.hm), rho = k * p.a;
     double2 I, O, dI, dO;
-    if (ecm > 0) {
-      double F, G, dF, dG;
-      riccati_fg(p.l[ch], rho, &F, &G, &dF, &dG);
-      I = make_double2(G, -F);
-      O = make_double2(G, F);
-      dI = make_double2(dG, -dF);
-      dO = make_double2(dG, dF);
-    } else {
-      double W, dW;
-      whittaker_w(p.l[ch], rho, &W, &dW);
-      I = dI = make_double2(0, 0);
-      O = make_double2(W, 0);
-      dO = make_double2(dW, 0);
-    }
-    dI.x -= p.B / rho * I.x;
-    dI.y -= p.B / rho * I.y;
-    dO.x -= p.B / rho * O.x;
-    dO.y -= p.B / rho * O.y;
+    double k;
+    if (!channel_functions(p.l[ch], p.E - p.thresh[ch], p.hm, p.a, p.B, p.zz[ch], &I, &O, &dI,
+                           &dO, &k))
+      S->status = -(1 + ch);
     S->I[ch] = I;
     S->O[ch] = O;
     S->dI[ch] = dI;
@@ -196,6 +184,8 @@ extern "C" int rmat_collision_noalloc(const rmat_problem* prob, double E, const 
   if (!prob || prob->nch < 1 || prob->nch > RMAT_NOALLOC_MAX_NCH || prob->nlag < 1 ||
       !(prob->a > 0) || !(prob->hm > 0) || !prob->l || !prob->thresh)
     return -1;
+  for (int c = 0; c < prob->nch; ++c)
+    if (prob->zz && !(std::isfinite(prob->zz[c]) && prob->zz[c] >= 0.0)) return -1;
   if (!(E == E)) return -2;
   if (!f_a_dev) return -3;
   if (!X_dev) return -4;
@@ -214,6 +204,7 @@ extern "C" int rmat_collision_noalloc(const rmat_problem* prob, double E, const 
     if (prob->l[c] < 0 || prob->l[c] > 64) return -1;
     p.l[c] = prob->l[c];
     p.thresh[c] = prob->thresh[c];
+    p.zz[c] = prob->zz ? prob->zz[c] : 0.0;
     if (E - prob->thresh[c] == 0.0) return -2;  // a channel exactly at threshold
     if (E - prob->thresh[c] > 0) p.open[no++] = c;
   }
@@ -242,5 +233,6 @@ extern "C" int rmat_collision_noalloc(const rmat_problem* prob, double E, const 
   if (cudaMemcpyAsync(&status, &S->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return RMAT_ECUDA;
+  if (status < 0) return RMAT_ECHANFN;
   return status ? RMAT_ESINGULAR : RMAT_OK;
 }

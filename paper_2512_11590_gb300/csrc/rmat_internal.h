@@ -45,7 +45,7 @@ struct IrState {
 };
 
 // Device status words written by kernels (read back by the host).
-enum { ST_INFO = 0, ST_TIMEOUT = 1, ST_BADARG = 2, ST_COUNT = 8 };
+enum { ST_INFO = 0, ST_TIMEOUT = 1, ST_BADARG = 2, ST_CHANFN = 3, ST_COUNT = 8 };
 
 struct rmat_ctx_s {
   int device = 0;
@@ -66,6 +66,14 @@ struct rmat_ctx_s {
   void* Bt = nullptr;      size_t Bt_cap = 0;       // gather target of the tensor forward solve
   int equil_param = -1;   // -1: default (on for complex64 paths), 0 off, 1 on
   bool equil = false;     // symmetric diagonal equilibration active for this problem
+  // RMAT_PARAM_METHOD: 0 factor M itself, 1 Woodbury-kinetic (factor S = I + (K^-1 (x) I) W)
+  int method_param = 0;
+  bool woodbury = false;  // the assembled problem's factored matrix is S
+  double* Kinv = nullptr;  size_t Kinv_cap = 0;     // K^-1 [nlag*nlag], FP64
+  float* Kinv32 = nullptr; size_t Kinv32_cap = 0;   // K^-1 rounded to FP32
+  int kinv_nlag = 0;       // mesh size K^-1 was formed for (0: stale)
+  void* W32 = nullptr;     size_t W32_cap = 0;      // FP32 copy of Wpt for the S assembly
+  void* Bs = nullptr;      size_t Bs_cap = 0;       // reordering scratch of the Woodbury solves
 
   // problem description
   int kind = 0;          // 0 none, 1 assembled, 2 dense
@@ -76,6 +84,8 @@ struct rmat_ctx_s {
   double a = 0, hm = 0, bloch_B = 0, E = 0;
   std::vector<int> l;
   std::vector<double> thresh;
+  std::vector<double> zz;  // Z1 Z2 e^2 per channel (0 = neutral)
+  std::vector<double> K_host;  // hm*T0 - hm*(B/a) f f^T of the current mesh (host)
   std::vector<double> f_a_host;
   double phi_max = 1.0;  // max |Phi| (denominator of the relative residual)
 
@@ -91,6 +101,7 @@ struct rmat_ctx_s {
   double* fa = nullptr;    size_t fa_cap = 0;       // f_i(a)
   int* l_d = nullptr;      size_t l_cap = 0;
   double* th_d = nullptr;  size_t th_cap = 0;
+  double* zz_d = nullptr;  size_t zz_cap = 0;
   double2* Wpt = nullptr;  size_t Wpt_cap = 0;      // [nlag][nch][nch] point coupling incl. diagonal
   double2* X = nullptr;    size_t X_cap = 0;        // FP64 solution, row-major N x nrhs
   double2* Rres = nullptr; size_t Rres_cap = 0;     // FP64 residual, row-major N x nrhs
@@ -166,6 +177,11 @@ int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n);
 // solve update: rows [row0, row0+M) of the solve buffer Bw (ld = nrhs) -= F(ay0.., k0..k0+jb) * Y
 // Cluster size the cluster panel would use for M rows of width jb (0: does not fit).
 int panel_cluster_fits(rmat_ctx c, int precision, int M, int jb);
+// Woodbury-kinetic form (woodbury.cu)
+int woodbury_prepare(rmat_ctx c, const double* K_host);
+int launch_schur_assemble(rmat_ctx c);
+int launch_kinv_apply(rmat_ctx c);
+int launch_radial_to_channel(rmat_ctx c);
 int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, int K, int ax0,
                      const float* cscal);
 int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n,

@@ -22,7 +22,7 @@ def run_problem(ctx, p, precision, max_refine=0, tol=0.0, nb=0, V=None):
         V = cp.potential_at(p, m["r"])
     Vd = torch.from_numpy(np.ascontiguousarray(V).ravel()).cuda()
     prob, keep = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh, precision,
-                                       p.bloch_B)
+                                       p.bloch_B, zz=p.zz)
     g.rmat_assemble(ctx, prob, p.E, Vd.data_ptr())
     fs, info = g.rmat_factor(ctx)
     X = torch.zeros((p.nch, p.N), dtype=torch.complex128, device="cuda")   # column-major N x nch

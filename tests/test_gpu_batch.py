@@ -19,6 +19,11 @@ def mixed_problems():
                                          (4, 100, 45.0), (8, 80, 9.0), (16, 40, 20.0),
                                          (16, 100, 7.0), (3, 37, 15.0)]):
         out.append(cp.make_problem(500 + k, nch, nlag, E))
+    # charged channels: above the Coulomb barrier with a closed channel, and below it
+    q = cp.charged_problem(600, 4, 80, 25.0)
+    q.thresh = np.array([0.0, 2.0, 3.5, 27.0])
+    out.append(q)
+    out.append(cp.charged_problem(601, 2, 100, 12.0))
     return out
 
 
@@ -49,7 +54,7 @@ def test_batch_matches_oracle(g, cases, prec, lanes, split, graph):
             m = g.rmat_mesh(p.nlag, p.a)
             Vs.append(torch.from_numpy(cp.potential_at(p, m["r"]).ravel()).cuda())
             s, k = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh, prec,
-                                            p.bloch_B)
+                                            p.bloch_B, zz=p.zz)
             structs.append(s)
             keep.append(k)
         b = g.rmat_batch_create(ctx, structs, [p.E for p in probs], [v.data_ptr() for v in Vs],

@@ -17,7 +17,7 @@ from rmat_gpu import relerr
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("case", ["config1", "closed-channels", "nch16"])
+@pytest.mark.parametrize("case", ["config1", "closed-channels", "nch16", "charged"])
 def test_collision_noalloc_matches_rmat_collision(case):
     import torch
 
@@ -28,6 +28,9 @@ def test_collision_noalloc_matches_rmat_collision(case):
         p = cp.config1()
         p.E = 3.0
         p.thresh = np.array([0.0, 1.0, 4.0, 4.5])
+    elif case == "charged":
+        p = cp.charged_problem(78, 6, 80, 14.0)       # sub-barrier Coulomb channels
+        p.thresh[-1] = 17.0                           # one closed charged channel
     else:
         p = cp.make_problem(77, 16, 60, 6.0)          # thresholds U(0,5): several closed channels
     torch.cuda.set_device(0)
@@ -36,7 +39,8 @@ def test_collision_noalloc_matches_rmat_collision(case):
     try:
         m = g.rmat_mesh(p.nlag, p.a)
         V = torch.from_numpy(cp.potential_at(p, m["r"]).ravel()).cuda()
-        prob, keep = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh, g.RMAT_C128)
+        prob, keep = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh, g.RMAT_C128,
+                                           zz=p.zz)
         g.rmat_assemble(ctx, prob, p.E, V.data_ptr())
         g.rmat_factor(ctx)
         X = torch.zeros((p.nch, p.N), dtype=torch.complex128, device="cuda")
