@@ -149,7 +149,7 @@ def workload(args):
 class Runner:
     """One system on one GPU through the C ABI (device-resident buffers)."""
 
-    def __init__(self, p, precision, device):
+    def __init__(self, p, precision, device, method=0):
         import torch
 
         import cc_problems as cp
@@ -157,6 +157,7 @@ class Runner:
         self.g, self.p, self.torch = g, p, torch
         self.stream = torch.cuda.current_stream()
         self.ctx = g.rmat_create(device, self.stream.cuda_stream)
+        g.rmat_set_param(self.ctx, g.RMAT_PARAM_METHOD, method)
         m = g.rmat_mesh(p.nlag, p.a)
         self.V_host = cp.potential_at(p, m["r"]).ravel()
         self.Vd = torch.from_numpy(self.V_host).cuda()
@@ -288,7 +289,7 @@ def reference_main(args):
     return 0
 
 
-def profile_step(nch, precision, warm=True):
+def profile_step(nch, precision, warm=True, method=0):
     """Launch sequence for ncu: the warm-up step uses the SIMT precision, so the
     first tensor-core launch of the run is the first trailing update at N = nch*100."""
     import torch
@@ -300,7 +301,7 @@ def profile_step(nch, precision, warm=True):
         w = Runner(cp.config3(16), g.RMAT_C64_SIMT_IR, 0)
         w.step()
         w.close()
-    run = Runner(cp.config3(nch), precision, 0)
+    run = Runner(cp.config3(nch), precision, 0, method)
     run.step()
     torch.cuda.synchronize()
     print("profile step", nch, run.last)
@@ -504,6 +505,10 @@ def main():
     ap.add_argument("--small", action="store_true", help="N=1600 instead of N=25600")
     ap.add_argument("--no-fp64", action="store_true", help="skip the complex128 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--method", default="direct", choices=["direct", "woodbury"],
+                    help="factor M itself or the Woodbury-kinetic Schur matrix S")
+    ap.add_argument("--no-woodbury", action="store_true",
+                    help="skip the Woodbury-kinetic comparison leg")
     ap.add_argument("--profile-step", action="store_true",
                     help="for ncu: one untimed SIMT warm-up step at N=1600, then one FP32+IR "
                          "tensor step at N = nch*100; no timing, no JSON")
@@ -527,7 +532,7 @@ def main():
         import paper_2512_11590_gb300 as g
         return profile_step(args.nch, {"tf32": g.RMAT_C64_3XTF32_IR, "f16": g.RMAT_C64_3XF16_IR,
                                        "simt": g.RMAT_C64_SIMT_IR}[args.precision],
-                            warm=not args.no_warm)
+                            warm=not args.no_warm, method=1 if args.method == "woodbury" else 0)
     if args.batch:
         return batch_main(args)
     if args.precision == "c128":
@@ -557,7 +562,8 @@ def main():
     p, desc = workload(args)
     prec = {"tf32": g.RMAT_C64_3XTF32_IR, "f16": g.RMAT_C64_3XF16_IR,
             "simt": g.RMAT_C64_SIMT_IR}[args.precision]
-    run = Runner(p, prec, local)
+    method = 1 if args.method == "woodbury" else 0
+    run = Runner(p, prec, local, method)
     with ClockSampler(local) as clk:
         ms, stats, launches = time_steps(run, args.steps, args.warmup, sync_all)
     ms = max_over_ranks(ms, dist, "cuda")
@@ -595,6 +601,32 @@ def main():
                 "x_rel_diff_fp32ir_vs_fp64": rd(X32, X64),
                 "speedup_fp32ir_over_fp64": ms64 / ms}
         r64.close()
+
+    other = None
+    if not args.no_woodbury:
+        # the other factored matrix (Woodbury-kinetic S vs M) on the same workload
+        rw = Runner(p, prec, local, 1 - method)
+        for _ in range(2):
+            rw.step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(rw.stream)
+        for _ in range(args.steps):
+            rw.step()
+        e1.record(rw.stream)
+        torch.cuda.synchronize()
+        msw = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+        Uw = rw.U_host()
+
+        def rdw(a, b):
+            return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        other = {"method": "direct" if method else "woodbury", "ms_per_step": msw,
+                 "value": replica_throughput(world, flops, msw), "refine": dict(rw.last),
+                 "u_rel_diff_vs_main": rdw(Uw, U32)}
+        if fp64 is not None:
+            other["u_rel_diff_vs_fp64"] = rdw(Uw, U64)
+        rw.close()
 
     pk, src = peaks()
     tu_ms, tu_flops, tu_n = stats["tu_ms"], stats["tu_flops"], stats["tu_launches"]
@@ -652,6 +684,7 @@ def main():
         "vs_baseline": None, "dtype": DTYPES[prec],
         "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "nrhs": p.nch,
+                   "method": args.method,
                    "refinement": ir, "l2": "inputs larger than L2 (C is %.1f GB)" % (p.N * p.N * 8 / 1e9),
                    "lu_block": stats["nb"], "panel_ctas": stats["panel_ctas"],
                    "stage_ms": {k: stats[k] for k in ("assemble_ms", "factor_ms", "solve_ms",
@@ -659,6 +692,7 @@ def main():
                    "kernel_ms": {k: [stats.get(k + "_ms"), stats.get(k + "_launches")]
                                  for k in ("panel", "apply_inv", "solve_tc", "resid")}},
         "fp64_path": fp64,
+        "other_method": other,
         "e2e": {"value": replica_throughput(world, flops, e2e_ms), "unit": "TFLOP/s",
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),

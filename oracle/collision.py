@@ -123,10 +123,11 @@ def channel_functions(p):
     Neutral channels (eta = 0) take the Riccati-Bessel and reduced Whittaker
     functions below; charged ones the Coulomb functions F_l(eta, rho),
     G_l(eta, rho) and the Whittaker function W_{-eta,l+1/2}(2 rho) of
-    oracle.coulomb, with the same I = G - iF, O = G + iF (open) and O = W, I = 0
-    (closed).
+    oracle.coulomb, with the same I = G - iF, O = G + iF (open) and I = 0 for
+    closed channels, where O = 1, O' = W'/W (a closed channel's column of the
+    matching matrix scales with O, so U depends on W'/W only).
     """
-    from .coulomb import coulomb_fg, whittaker_w
+    from .coulomb import coulomb_fg, whittaker_logd
 
     ecm = p.E - np.asarray(p.thresh, dtype=np.float64)
     if np.any(ecm == 0.0):
@@ -150,8 +151,8 @@ def channel_functions(p):
         else:
             if eta[c] == 0.0:
                 w, dw = whittaker_reduced(int(p.l[c]), rho)
-            else:
-                w, dw = whittaker_w(int(p.l[c]), float(eta[c]), rho)
+            else:   # only W'/W enters U: O = 1, O' = W'/W
+                w, dw = 1.0, whittaker_logd(int(p.l[c]), float(eta[c]), rho)
             O[c], dO[c] = w, dw
         dI[c] -= p.bloch_B / rho * I[c]
         dO[c] -= p.bloch_B / rho * O[c]

@@ -46,7 +46,10 @@ The Whittaker function is started from its asymptotic expansion
                              sum_k (l+1+eta)_k (eta-l)_k / k! (-1/(2 rho))^k
 
 at a radius where the terms fall below double precision, and integrated
-inward the same way (the decaying solution also grows inward).
+inward the same way (the decaying solution also grows inward).  The collision
+matrix needs only W'/W (a closed channel's column of the matching matrix scales
+with W), which whittaker_logd integrates as a Riccati equation: that stays
+finite where W itself over- or underflows (large eta, small rho).
 
 The integrations use scipy's DOP853 at rtol 1e-13.  Pins
 (tests/test_oracle_coulomb.py): F, G, F', G' and W, W' against mpmath's
@@ -155,6 +158,33 @@ def coulomb_fg(l: int, eta: float, rho: float):
     f, _ = coulomb_cf1(l, eta, rho)
     F = 1.0 / (f * G - dG)
     return F, G, f * F, dG
+
+
+def whittaker_logd(l: int, eta: float, rho: float) -> float:
+    """W'/W (rho-derivative) of W_{-eta, l+1/2}(2 rho), for any eta >= 0.
+
+    y = u'/u of the decaying solution obeys the Riccati equation y' = Q - y^2,
+    Q = 1 + 2 eta/rho + l(l+1)/rho^2, and is stable when integrated inward
+    (a deviation from the decaying branch y ~ -sqrt(Q) shrinks like
+    exp(-2 int sqrt(Q))).  It is started from the WKB value -sqrt(Q) - Q'/(4Q)
+    at rho + 40, where that start's error has decayed by more than e^-80 on
+    arrival, so no normalisation (and no overflow of W itself) is involved.
+    """
+    if rho <= 0:
+        raise ValueError("rho must be positive")
+    ll = l * (l + 1.0)
+
+    def Q(r):
+        return 1.0 + 2.0 * eta / r + ll / (r * r)
+
+    rb = rho + 40.0
+    dQ = -2.0 * eta / (rb * rb) - 2.0 * ll / rb ** 3
+    y0 = -math.sqrt(Q(rb)) - dQ / (4.0 * Q(rb))
+    sol = solve_ivp(lambda r, y: [Q(r) - y[0] * y[0]], (rb, rho), [y0], method="DOP853",
+                    rtol=1e-13, atol=1e-14)
+    if not sol.success:
+        raise ArithmeticError(sol.message)
+    return float(sol.y[0, -1])
 
 
 def whittaker_w(l: int, eta: float, rho: float):

@@ -38,6 +38,7 @@ RMAT_PARAM_SPIN_LIMIT = 3
 RMAT_PARAM_TIMING = 4
 RMAT_PARAM_EQUILIBRATE = 5
 RMAT_PARAM_PAIRED = 6
+RMAT_PARAM_METHOD = 7   # 0 factor M, 1 Woodbury-kinetic (factor S = I + (K^-1 x I) W)
 
 RMAT_BATCH_LANES = 1
 RMAT_BATCH_SPLIT_N = 2

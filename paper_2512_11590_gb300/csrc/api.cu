@@ -339,6 +339,7 @@ int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_de
       !std::isfinite(pb->bloch_B) || !pb->l || !pb->thresh || !valid_precision(pb->precision))
     return -2;
   if ((long long)pb->nch * pb->nlag > 200000) return -2;
+  if (c->method_param == 1 && pb->nch > 65535) return -2;  // one grid z-slice per channel
   for (int k = 0; k < pb->nch; ++k)
     if (pb->l[k] < 0 || pb->l[k] > 64 || !std::isfinite(pb->thresh[k]) ||
         (pb->zz && !(std::isfinite(pb->zz[k]) && pb->zz[k] >= 0.0)))

@@ -1,7 +1,8 @@
 """Pins for the charged-channel asymptotics (Coulomb and Whittaker functions).
 
 Independent checks: mpmath's own Coulomb and Whittaker functions (arbitrary
-precision, hypergeometric series), the Wronskian F'G - FG' = 1, the eta -> 0
+precision, hypergeometric series; W'/W too, at Sommerfeld parameters up to the
+42 of a closed alpha + 208Pb channel 1.5 MeV below threshold), the Wronskian F'G - FG' = 1, the eta -> 0
 limits (pinned to scipy in test_oracle_special), and scattering physics:
 a pure Coulomb interior matched to Coulomb functions has no nuclear phase
 shift (U = 1), and a Woods-Saxon plus Coulomb system agrees with direct ODE
@@ -18,7 +19,7 @@ import cc_problems as cp
 from oracle import collision as CL
 from oracle import mesh as M
 from oracle import system as S
-from oracle.coulomb import coulomb_fg, turning_point, whittaker_w
+from oracle.coulomb import coulomb_fg, turning_point, whittaker_logd, whittaker_w
 from oracle.refine import truth_solve
 
 mp = pytest.importorskip("mpmath")
@@ -83,6 +84,15 @@ def test_whittaker_vs_mpmath(l, eta, rho):
     We, dWe = _mp_whittaker(l, eta, rho)
     assert abs(W - We) <= 1e-10 * abs(We)
     assert abs(dW - dWe) <= 1e-10 * abs(dWe)
+
+
+@pytest.mark.parametrize("l", [0, 1, 5, 20])
+@pytest.mark.parametrize("eta", [0.5, 12.0, 41.8])
+@pytest.mark.parametrize("rho", [0.3, 2.0, 8.5, 30.0])
+def test_whittaker_log_derivative_vs_mpmath(l, eta, rho):
+    y = whittaker_logd(l, eta, rho)
+    W, dW = _mp_whittaker(l, eta, rho)
+    assert abs(y - dW / W) <= 1e-11 * abs(dW / W)
 
 
 # ---- scattering physics ---------------------------------------------------
