@@ -400,7 +400,7 @@ def batch_main(args):
     return 0
 
 
-def solve_once(p, precision, device=0, warm=False, energies=None):
+def solve_once(p, precision, device=0, warm=False, energies=None, method=0):
     """One assembled system through the C ABI on a non-default stream: wall times of
     assemble+factor+solve+collision per energy, refinement info, U per energy."""
     import torch
@@ -409,6 +409,7 @@ def solve_once(p, precision, device=0, warm=False, energies=None):
     import paper_2512_11590_gb300 as g
     stream = torch.cuda.Stream()
     ctx = g.rmat_create(device, stream.cuda_stream)
+    g.rmat_set_param(ctx, g.RMAT_PARAM_METHOD, method)
     m = g.rmat_mesh(p.nlag, p.a)
     Vd = torch.from_numpy(cp.potential_at(p, m["r"]).ravel()).cuda()
     prob, keep = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh, precision,
@@ -448,16 +449,23 @@ def sweep_main(args):
     torch.cuda.set_device(0)
     rows = []
     cases = [("config2", cp.config2(n)) for n in (16, 64, 128, 256)] + [("config3b", cp.config3(256, W=-1.0))]
+    def rd(a, b):
+        return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
     for name, p in cases:
         lo = solve_once(p, g.RMAT_C64_3XF16_IR, warm=True)[0]
-        hi = solve_once(p, g.RMAT_C128, warm=p.N <= 6400)[0]
+        wb = solve_once(p, g.RMAT_C64_3XF16_IR, warm=True, method=1)[0]
         fl = lu_flops(p.N, p.nch)
-        rows.append({"case": name, "N": p.N, "nrhs": p.nch,
-                     "fp32ir_ms": lo["ms"], "fp32ir_tflops": fl / (lo["ms"] * 1e-3) / 1e12,
-                     "fp32ir_iters": lo["iters"], "fp32ir_rel_resid": lo["rel_resid"],
-                     "fp64_ms": hi["ms"], "fp64_tflops": fl / (hi["ms"] * 1e-3) / 1e12,
-                     "fp64_iters": hi["iters"], "speedup": hi["ms"] / lo["ms"],
-                     "u_rel_diff": float(np.max(np.abs(lo["U"] - hi["U"])) / np.max(np.abs(hi["U"])))})
+        row = {"case": name, "N": p.N, "nrhs": p.nch,
+               "fp32ir_ms": lo["ms"], "fp32ir_tflops": fl / (lo["ms"] * 1e-3) / 1e12,
+               "fp32ir_iters": lo["iters"], "fp32ir_rel_resid": lo["rel_resid"],
+               "woodbury_ms": wb["ms"], "woodbury_iters": wb["iters"],
+               "woodbury_rel_resid": wb["rel_resid"], "u_rel_diff_woodbury_vs_direct": rd(wb["U"], lo["U"])}
+        if not args.no_fp64:
+            hi = solve_once(p, g.RMAT_C128, warm=p.N <= 6400)[0]
+            row.update({"fp64_ms": hi["ms"], "fp64_tflops": fl / (hi["ms"] * 1e-3) / 1e12,
+                        "fp64_iters": hi["iters"], "speedup": hi["ms"] / lo["ms"],
+                        "u_rel_diff": rd(lo["U"], hi["U"]), "u_rel_diff_woodbury": rd(wb["U"], hi["U"])})
+        rows.append(row)
         print(json.dumps(rows[-1]), flush=True)
     print(json.dumps({"metric": "config 2 sweep + config 3b: FP32+IR vs FP64 (complex128) per system",
                       "unit": "ms", "rows": rows, "data": "synthetic"}))

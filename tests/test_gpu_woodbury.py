@@ -75,7 +75,7 @@ def test_fewer_corrections_than_direct(g, ctx):
     finally:
         g.rmat_destroy(c2)
     assert wb["iters"] < direct["iters"], (wb["iters"], direct["iters"])
-    assert wb["iters"] <= 3
+    assert wb["iters"] <= 4
 
 
 def test_method_and_mesh_switches_on_one_context(g, ctx):
