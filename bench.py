@@ -400,7 +400,7 @@ def batch_main(args):
     return 0
 
 
-def solve_once(p, precision, device=0, warm=False, energies=None, method=0):
+def solve_once(p, precision, device=0, warm=False, energies=None, method=0, refine=0):
     """One assembled system through the C ABI on a non-default stream: wall times of
     assemble+factor+solve+collision per energy, refinement info, U per energy."""
     import torch
@@ -410,6 +410,7 @@ def solve_once(p, precision, device=0, warm=False, energies=None, method=0):
     stream = torch.cuda.Stream()
     ctx = g.rmat_create(device, stream.cuda_stream)
     g.rmat_set_param(ctx, g.RMAT_PARAM_METHOD, method)
+    g.rmat_set_param(ctx, g.RMAT_PARAM_REFINE, refine)
     m = g.rmat_mesh(p.nlag, p.a)
     Vd = torch.from_numpy(cp.potential_at(p, m["r"]).ravel()).cuda()
     prob, keep = g.make_problem_struct(p.nch, p.nlag, p.a, p.hm, p.l, p.thresh, precision,
@@ -434,6 +435,7 @@ def solve_once(p, precision, device=0, warm=False, energies=None, method=0):
         if warm and k == 0:
             continue
         out.append({"E": E, "ms": e0.elapsed_time(e1), "status": st, "iters": it, "rel_resid": rel,
+                    "inner": g.rmat_get_stats(ctx).get("gmres_inner", 0),
                     "U": U.cpu().numpy()[:nopen * nopen].reshape(nopen, nopen).T})
     g.rmat_destroy(ctx)
     return out
@@ -454,12 +456,15 @@ def sweep_main(args):
     for name, p in cases:
         lo = solve_once(p, g.RMAT_C64_3XF16_IR, warm=True)[0]
         wb = solve_once(p, g.RMAT_C64_3XF16_IR, warm=True, method=1)[0]
+        gm = solve_once(p, g.RMAT_C64_3XF16_IR, warm=True, refine=20)[0]
         fl = lu_flops(p.N, p.nch)
         row = {"case": name, "N": p.N, "nrhs": p.nch,
                "fp32ir_ms": lo["ms"], "fp32ir_tflops": fl / (lo["ms"] * 1e-3) / 1e12,
                "fp32ir_iters": lo["iters"], "fp32ir_rel_resid": lo["rel_resid"],
                "woodbury_ms": wb["ms"], "woodbury_iters": wb["iters"],
-               "woodbury_rel_resid": wb["rel_resid"], "u_rel_diff_woodbury_vs_direct": rd(wb["U"], lo["U"])}
+               "woodbury_rel_resid": wb["rel_resid"], "u_rel_diff_woodbury_vs_direct": rd(wb["U"], lo["U"]),
+               "gmres_ir_ms": gm["ms"], "gmres_ir_outer": gm["iters"], "gmres_ir_inner": gm["inner"],
+               "gmres_ir_rel_resid": gm["rel_resid"], "u_rel_diff_gmres_vs_direct": rd(gm["U"], lo["U"])}
         if not args.no_fp64:
             hi = solve_once(p, g.RMAT_C128, warm=p.N <= 6400)[0]
             row.update({"fp64_ms": hi["ms"], "fp64_tflops": fl / (hi["ms"] * 1e-3) / 1e12,

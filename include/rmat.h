@@ -93,6 +93,14 @@ extern "C" {
  *     Equilibration is not applied to S.  Not used by rmat_load_dense or batches.
  * Takes effect at the next rmat_assemble. */
 #define RMAT_PARAM_METHOD      7
+/* Refinement of rmat_solve: 0 (default) classical, x += M^-1 r (Sec. 3.2);
+ * m = 1..64 GMRES-IR: each correction solves C d = r by flexible GMRES in FP64
+ * vectors with the FP64 product of C, right-preconditioned by the factors, with
+ * at most m inner steps or until every column's GMRES residual is below 1e-6 of
+ * its |r|.  Converges where cond(C) u_factor >= 1 stalls the classical loop.
+ * The stopping rule (tol, stagnation, max_refine) counts outer corrections.
+ * Not used by batches (their refinement is decided on the device). */
+#define RMAT_PARAM_REFINE      8
 
 typedef struct rmat_ctx_s* rmat_ctx;
 
@@ -223,9 +231,10 @@ int rmat_collision(rmat_ctx ctx, void* R_dev, void* U_dev, int* nopen);
  *   out[13] / out[14] panel kernel ms / launches,
  *   out[15] / out[16] solve-path diagonal-block application ms / launches,
  *   out[17] / out[18] solve-path tensor-core block update ms / launches,
- *   out[19] / out[20] FP64 residual ms / launches
+ *   out[19] / out[20] FP64 residual ms / launches, out[21] GMRES-IR inner steps of the
+ *   last rmat_solve
  *   (timers need RMAT_PARAM_TIMING=1; a time is -1 when it was not timed).
- * n: capacity of out; returns the number of values written (<= 21). */
+  * n: capacity of out; returns the number of values written (<= 22). */
 int rmat_get_stats(rmat_ctx ctx, double* out, int n);
 int rmat_reset_counters(rmat_ctx ctx);
 

@@ -39,6 +39,7 @@ RMAT_PARAM_TIMING = 4
 RMAT_PARAM_EQUILIBRATE = 5
 RMAT_PARAM_PAIRED = 6
 RMAT_PARAM_METHOD = 7   # 0 factor M, 1 Woodbury-kinetic (factor S = I + (K^-1 x I) W)
+RMAT_PARAM_REFINE = 8   # 0 classical refinement, m = 1..64 FGMRES-IR with <= m inner steps
 
 RMAT_BATCH_LANES = 1
 RMAT_BATCH_SPLIT_N = 2
@@ -215,7 +216,7 @@ def rmat_collision(ctx, R_dev=0, U_dev=0) -> int:
 STAT_KEYS = ("N", "nrhs", "nb", "panel_ctas", "launches", "tu_launches", "tu_ms", "tu_flops",
              "assemble_ms", "factor_ms", "solve_ms", "refine_ms", "collision_ms",
              "panel_ms", "panel_launches", "apply_inv_ms", "apply_inv_launches",
-             "solve_tc_ms", "solve_tc_launches", "resid_ms", "resid_launches")
+             "solve_tc_ms", "solve_tc_launches", "resid_ms", "resid_launches", "gmres_inner")
 
 
 def rmat_get_stats(ctx) -> dict:

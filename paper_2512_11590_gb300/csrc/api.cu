@@ -284,7 +284,8 @@ int rmat_destroy(rmat_ctx c) {
                   c->fa,   c->l_d,  c->th_d, c->zz_d, c->Wpt, c->X,  c->Rres, c->Bw,
                   c->Fpl,  c->Bpl, c->Ypl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
                   c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows, c->Dinv,
-                  c->umax, c->uscale, c->ycs, c->pfwd, c->Bt, c->Kinv, c->Kinv32, c->W32, c->Bs};
+                  c->umax, c->uscale, c->ycs, c->pfwd, c->Bt, c->Kinv, c->Kinv32, c->W32, c->Bs,
+                  c->gm_V, c->gm_Z, c->gm_T, c->gm_small};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->hstat) cudaFreeHost(c->hstat);
@@ -322,6 +323,10 @@ int rmat_set_param(rmat_ctx c, int key, long long v) {
     case RMAT_PARAM_METHOD:
       if (v < 0 || v > 1) return -3;
       c->method_param = (int)v;
+      return RMAT_OK;
+    case RMAT_PARAM_REFINE:
+      if (v < 0 || v > 64) return -3;
+      c->refine_param = (int)v;
       return RMAT_OK;
     default:
       return -2;
@@ -546,6 +551,8 @@ static int solve_system(rmat_ctx c) {
 
 }  // extern "C"
 
+int rmat_solve_system(rmat_ctx c) { return solve_system(c); }
+
 int enqueue_solve_refine(rmat_ctx c, int max_refine, double tol, IrState* st) {
   RMAT_CHECK(launch_w_from_phi(c));
   RMAT_CHECK(solve_system(c));
@@ -584,6 +591,7 @@ int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int
   int it = 0, status = RMAT_OK;
   double rel = 0.0;
   c->ir_hist.clear();
+  c->gm_inner = 0;
   if (max_refine > 0 || tol > 0) {
     double prev = INFINITY;
     // complex64 factors: one non-halving step ends the refinement (each extra
@@ -613,8 +621,14 @@ int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int
         stagn = 0;
       }
       prev = rel;
-      RMAT_CHECK(solve_system(c));
-      RMAT_CHECK(launch_update(c));
+      if (c->refine_param > 0) {
+        int inner = 0;
+        RMAT_CHECK(gmres_correction(c, c->refine_param, 1e-6, &inner));
+        c->gm_inner += inner;
+      } else {
+        RMAT_CHECK(solve_system(c));
+        RMAT_CHECK(launch_update(c));
+      }
       ++it;
     }
   }
@@ -675,15 +689,16 @@ int rmat_get_stats(rmat_ctx c, double* out, int n) {
   };
   for (int k = 0; k < 5; ++k)
     c->stage_ms[k] = elapsed(c->stage_ev[k][0], c->stage_ev[k][1]);
-  const double v[21] = {(double)c->N, (double)c->nrhs, (double)c->nb,
+  const double v[22] = {(double)c->N, (double)c->nrhs, (double)c->nb,
                         (double)panel_ctas_for(c, c->N > 0 ? c->N : 1), (double)c->launches,
                         (double)c->tu_launches, sum(c->tu_events), c->tu_flops, c->stage_ms[0],
                         c->stage_ms[1], c->stage_ms[2], c->stage_ms[3], c->stage_ms[4],
                         sum(c->kt_events[KT_PANEL]), (double)c->kt_launches[KT_PANEL],
                         sum(c->kt_events[KT_APPLY_INV]), (double)c->kt_launches[KT_APPLY_INV],
                         sum(c->kt_events[KT_SOLVE_TC]), (double)c->kt_launches[KT_SOLVE_TC],
-                        sum(c->kt_events[KT_RESID]), (double)c->kt_launches[KT_RESID]};
-  const int m = n < 21 ? n : 21;
+                        sum(c->kt_events[KT_RESID]), (double)c->kt_launches[KT_RESID],
+                        (double)c->gm_inner};
+  const int m = n < 22 ? n : 22;
   for (int k = 0; k < m; ++k) out[k] = v[k];
   return m;
 }

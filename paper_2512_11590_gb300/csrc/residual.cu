@@ -332,6 +332,27 @@ int launch_residual(rmat_ctx c, double*) {
   return RMAT_OK;
 }
 
+// Rout = Phi - C Xin (FP64, row-major N x nrhs) for any Xin: the structured
+// product of an assembled problem or the dense product of a loaded one.
+int launch_apply_resid(rmat_ctx c, const double2* Xin, double2* Rout) {
+  const int N = c->N, nrhs = c->nrhs;
+  if (c->kind == 1) {
+    dim3 gk(ceil_div(nrhs, 32), c->nch);
+    resid_kinetic_kernel<<<gk, 256, 0, c->stream>>>(Rout, Xin, nrhs, c->nlag, c->Kmat, c->fa,
+                                                    nullptr);
+    dim3 gc(ceil_div(nrhs, RC_T), ceil_div(c->nch, RC_T), c->nlag);
+    resid_coupling_kernel<<<gc, 256, 0, c->stream>>>(Rout, Xin, nrhs, c->nlag, c->nch, c->Wpt,
+                                                     nullptr);
+    c->launches += 2;
+  } else {
+    RMAT_CU(cudaMemcpyAsync(Rout, c->B64, (size_t)N * nrhs * sizeof(double2),
+                            cudaMemcpyDeviceToDevice, c->stream));
+    RMAT_CHECK(gemm_sub_c128(c, N, nrhs, N, c->A64, N, Xin, nrhs, Rout, nrhs));
+  }
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
 int launch_update(rmat_ctx c, const IrState* st) {
   const size_t total = (size_t)c->N * c->nrhs;
   const double* D = c->equil ? c->Dsc : nullptr;

@@ -74,6 +74,13 @@ struct rmat_ctx_s {
   int kinv_nlag = 0;       // mesh size K^-1 was formed for (0: stale)
   void* W32 = nullptr;     size_t W32_cap = 0;      // FP32 copy of Wpt for the S assembly
   void* Bs = nullptr;      size_t Bs_cap = 0;       // reordering scratch of the Woodbury solves
+  // RMAT_PARAM_REFINE: 0 classical refinement, m > 0 FGMRES-IR with <= m inner steps
+  int refine_param = 0;
+  long long gm_inner = 0;  // FGMRES inner steps of the last rmat_solve
+  void* gm_V = nullptr;     size_t gm_V_cap = 0;     // Krylov basis, (m+1) x N x nrhs FP64
+  void* gm_Z = nullptr;     size_t gm_Z_cap = 0;     // preconditioned basis, m x N x nrhs FP64
+  void* gm_T = nullptr;     size_t gm_T_cap = 0;     // product scratch, N x nrhs FP64
+  void* gm_small = nullptr; size_t gm_small_cap = 0; // reduction partials, H columns, scales
 
   // problem description
   int kind = 0;          // 0 none, 1 assembled, 2 dense
@@ -182,6 +189,10 @@ int woodbury_prepare(rmat_ctx c, const double* K_host);
 int launch_schur_assemble(rmat_ctx c);
 int launch_kinv_apply(rmat_ctx c);
 int launch_radial_to_channel(rmat_ctx c);
+// FGMRES-IR (gmres.cu) and the pieces it shares with the classical loop
+int launch_apply_resid(rmat_ctx c, const double2* Xin, double2* Rout);
+int rmat_solve_system(rmat_ctx c);
+int gmres_correction(rmat_ctx c, int m, double tau, int* inner);
 int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, int K, int ax0,
                      const float* cscal);
 int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n,
