@@ -149,7 +149,7 @@ def workload(args):
 class Runner:
     """One system on one GPU through the C ABI (device-resident buffers)."""
 
-    def __init__(self, p, precision, device, method=0):
+    def __init__(self, p, precision, device, method=0, lookahead=0):
         import torch
 
         import cc_problems as cp
@@ -158,6 +158,7 @@ class Runner:
         self.stream = torch.cuda.current_stream()
         self.ctx = g.rmat_create(device, self.stream.cuda_stream)
         g.rmat_set_param(self.ctx, g.RMAT_PARAM_METHOD, method)
+        g.rmat_set_param(self.ctx, g.RMAT_PARAM_SOLVE_LOOKAHEAD, lookahead)
         m = g.rmat_mesh(p.nlag, p.a)
         self.V_host = cp.potential_at(p, m["r"]).ravel()
         self.Vd = torch.from_numpy(self.V_host).cuda()
@@ -522,6 +523,8 @@ def main():
                     help="factor M itself or the Woodbury-kinetic Schur matrix S")
     ap.add_argument("--no-woodbury", action="store_true",
                     help="skip the Woodbury-kinetic comparison leg")
+    ap.add_argument("--lookahead", action="store_true",
+                    help="look-ahead (second stream) in the tensor-path solves")
     ap.add_argument("--profile-step", action="store_true",
                     help="for ncu: one untimed SIMT warm-up step at N=1600, then one FP32+IR "
                          "tensor step at N = nch*100; no timing, no JSON")
@@ -576,7 +579,7 @@ def main():
     prec = {"tf32": g.RMAT_C64_3XTF32_IR, "f16": g.RMAT_C64_3XF16_IR,
             "simt": g.RMAT_C64_SIMT_IR}[args.precision]
     method = 1 if args.method == "woodbury" else 0
-    run = Runner(p, prec, local, method)
+    run = Runner(p, prec, local, method, 1 if args.lookahead else 0)
     with ClockSampler(local) as clk:
         ms, stats, launches = time_steps(run, args.steps, args.warmup, sync_all)
     ms = max_over_ranks(ms, dist, "cuda")
@@ -618,7 +621,7 @@ def main():
     other = None
     if not args.no_woodbury:
         # the other factored matrix (Woodbury-kinetic S vs M) on the same workload
-        rw = Runner(p, prec, local, 1 - method)
+        rw = Runner(p, prec, local, 1 - method, 1 if args.lookahead else 0)
         for _ in range(2):
             rw.step()
         torch.cuda.synchronize()

@@ -101,6 +101,11 @@ extern "C" {
  * The stopping rule (tol, stagnation, max_refine) counts outer corrections.
  * Not used by batches (their refinement is decided on the device). */
 #define RMAT_PARAM_REFINE      8
+/* Tensor-path solves: 1 = look-ahead, each block's update of the next block's rows
+ * runs first and the far rows' update overlaps the next block on a second stream
+ * (the concurrent reduce-adds make the rounding order, and so the last bits, vary
+ * from run to run); 0 (default) = one update per block. */
+#define RMAT_PARAM_SOLVE_LOOKAHEAD 9
 
 typedef struct rmat_ctx_s* rmat_ctx;
 

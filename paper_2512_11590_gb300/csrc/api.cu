@@ -67,7 +67,7 @@ int ctx_reserve(rmat_ctx c, bool dense) {
   if (tensor) {
     want(c->Fpl_cap, 4 * N * ld * pe);
     want(c->Bpl_cap, 4 * N * RMAT_MAX_NB * pe);
-    want(c->Ypl_cap, (size_t)4 * RMAT_YPL_ROWS * RMAT_MAX_NB * pe);
+    want(c->Ypl_cap, (size_t)8 * RMAT_YPL_ROWS * RMAT_MAX_NB * pe);
   }
   if (dense) {
     want(c->A64_cap, N * N * 16);
@@ -85,13 +85,17 @@ int ctx_reserve(rmat_ctx c, bool dense) {
   if (tensor) {
     RMAT_CHECK(rmat_grow(c, &c->Fpl, &c->Fpl_cap, 4 * N * ld * pe));
     RMAT_CHECK(rmat_grow(c, &c->Bpl, &c->Bpl_cap, 4 * N * RMAT_MAX_NB * pe));
-    RMAT_CHECK(rmat_grow(c, &c->Ypl, &c->Ypl_cap, (size_t)4 * RMAT_YPL_ROWS * RMAT_MAX_NB * pe));
+    RMAT_CHECK(rmat_grow(c, &c->Ypl, &c->Ypl_cap, (size_t)8 * RMAT_YPL_ROWS * RMAT_MAX_NB * pe));
     RMAT_CHECK(rmat_grow(c, (void**)&c->pfwd, &c->pfwd_cap, 2 * N * sizeof(int)));
     RMAT_CHECK(rmat_grow(c, &c->Bt, &c->Bt_cap, N * nrhs * eb));
     const size_t nblk = N / 32 + 2;
     RMAT_CHECK(rmat_grow(c, (void**)&c->umax, &c->umax_cap, nblk * sizeof(unsigned)));
     RMAT_CHECK(rmat_grow(c, (void**)&c->uscale, &c->uscale_cap, nblk * sizeof(float)));
-    RMAT_CHECK(rmat_grow(c, (void**)&c->ycs, &c->ycs_cap, (size_t)RMAT_YPL_ROWS * sizeof(float)));
+    RMAT_CHECK(rmat_grow(c, (void**)&c->ycs, &c->ycs_cap, (size_t)2 * RMAT_YPL_ROWS * sizeof(float)));
+    if (!c->side) {  // look-ahead stream of the tensor-path solves
+      RMAT_CU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+      for (cudaEvent_t& e : c->la_ev) RMAT_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
   }
   if (dense) {
     RMAT_CHECK(rmat_grow(c, (void**)&c->A64, &c->A64_cap, N * N * 16));
@@ -277,6 +281,10 @@ int rmat_destroy(rmat_ctx c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   if (c->sg_exec) cudaGraphExecDestroy(c->sg_exec);
+  if (c->side) cudaStreamSynchronize(c->side);
+  for (cudaEvent_t e : c->la_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->borrowed_tables) c->Kmat = c->T0 = c->rmesh = c->fa = nullptr, c->l_d = nullptr,
                           c->th_d = nullptr, c->zz_d = nullptr, c->open_d = nullptr;
   tc_release(c);
@@ -327,6 +335,10 @@ int rmat_set_param(rmat_ctx c, int key, long long v) {
     case RMAT_PARAM_REFINE:
       if (v < 0 || v > 64) return -3;
       c->refine_param = (int)v;
+      return RMAT_OK;
+    case RMAT_PARAM_SOLVE_LOOKAHEAD:
+      if (v < 0 || v > 1) return -3;
+      c->solve_lookahead = (int)v;
       return RMAT_OK;
     default:
       return -2;
@@ -510,7 +522,8 @@ static int solve_factors(rmat_ctx c) {
       (long long)(uintptr_t)c->Ypl, (long long)(uintptr_t)c->C, (long long)(uintptr_t)c->Dinv,
       (long long)(uintptr_t)c->Bt, (long long)(uintptr_t)c->pfwd,
       (long long)(uintptr_t)c->perm_main.rows, (long long)(uintptr_t)c->stream,
-      (long long)(uintptr_t)c->uscale, (long long)(uintptr_t)c->ycs};
+      (long long)(uintptr_t)c->uscale, (long long)(uintptr_t)c->ycs, c->solve_lookahead,
+      (long long)(uintptr_t)c->side};
   if (!c->sg_exec || key != c->sg_key) {
     if (c->sg_exec) {
       cudaGraphExecDestroy(c->sg_exec);

@@ -122,7 +122,8 @@ int enqueue_system(rmat_batch b, int s, void* U) {
   c->zz_d = b->zz_all + y.off_l;
   c->open_d = b->open_all + y.off_open;
   c->borrowed_tables = true;
-  c->woodbury = false;  // batches factor M itself
+  c->woodbury = false;      // batches factor M itself
+  c->solve_lookahead = 0;   // lanes are their own concurrency
   c->equil = c->equil_param == -1 ? b->precision != RMAT_C128 : c->equil_param == 1;
   RMAT_CHECK(perm_reserve(c, c->perm_main, y.N, c->nb));  // lay out, no growth (plan sized it)
   RMAT_CU(cudaMemsetAsync(c->dstat, 0, ST_COUNT * sizeof(int), c->stream));

@@ -483,7 +483,7 @@ struct TcCache {
   const void* cmat = nullptr;
   const void* bw = nullptr;
   int n = -1, ldf = -1, nrhs = -1, fmt = -1;
-  TcMaps upd, sol;  // trailing update (BN = 256), solve update (BN = 128)
+  TcMaps upd, sol[2];  // trailing update (BN = 256), solve update (BN = 128) per Y buffer
 };
 bool g_tc_attr[2][2] = {{false, false}, {false, false}};
 
@@ -506,7 +506,10 @@ int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn,
     g_tc_attr[BN == 128][KIND] = true;
   }
   const int tiles = ceil_div(M, TC_BM) * ceil_div(Nn, BN);
-  const int grid = std::min(tiles, c->sm_count);
+  // a far-row update on the solves' look-ahead stream leaves 32 SMs to the next
+  // block's diagonal application (one TC CTA fills an SM's shared memory)
+  const int cap = (c->side && c->stream == c->side) ? std::max(1, c->sm_count - 32) : c->sm_count;
+  const int grid = std::min(tiles, cap);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing && count_as_update) {
     e0 = rmat_event(c);
@@ -559,12 +562,15 @@ int tc_prepare(rmat_ctx c, int n, int nrhs) {
     RMAT_CHECK(make_plane_map(&g_tc.upd.a[q], F + q * fplane, fmt, n, n, ldf, TC_BM));
     RMAT_CHECK(make_plane_map(&g_tc.upd.b[q], Bp + q * bplane, fmt, RMAT_MAX_NB, n, RMAT_MAX_NB,
                               TC_BN));
-    g_tc.sol.a[q] = g_tc.upd.a[q];
-    RMAT_CHECK(make_plane_map(&g_tc.sol.b[q], Y + q * yplane, fmt, RMAT_MAX_NB, std::max(1, nrhs),
-                              RMAT_MAX_NB, 128));
+    for (int u = 0; u < 2; ++u) {
+      g_tc.sol[u].a[q] = g_tc.upd.a[q];
+      RMAT_CHECK(make_plane_map(&g_tc.sol[u].b[q], Y + (4 * u + q) * yplane, fmt, RMAT_MAX_NB,
+                                std::max(1, nrhs), RMAT_MAX_NB, 128));
+    }
   }
   RMAT_CHECK(make_out_map(&g_tc.upd.c, c->C, n, n, c->ld));
-  RMAT_CHECK(make_out_map(&g_tc.sol.c, c->Bw, std::max(2, nrhs), n, std::max(2, nrhs)));
+  RMAT_CHECK(make_out_map(&g_tc.sol[0].c, c->Bw, std::max(2, nrhs), n, std::max(2, nrhs)));
+  g_tc.sol[1].c = g_tc.sol[0].c;
   g_tc.f = c->Fpl;
   g_tc.b = c->Bpl;
   g_tc.y = c->Ypl;
@@ -612,10 +618,10 @@ int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int a
   if (rmat_plane_fmt(c->precision) == 1) {
     sc.rowscale = rowscale;
     sc.rs_div = rs_div;
-    sc.colscale = c->ycs;
+    sc.colscale = rmat_ycs_cur(c);
   }
   KTimer kt(c, KT_SOLVE_TC);
-  RMAT_CHECK(launch_tc<128>(c, g_tc.sol, 0, row0, M, nrhs, jb, k0, ay0, 0, 0, sc, false));
+  RMAT_CHECK(launch_tc<128>(c, g_tc.sol[c->ybuf], 0, row0, M, nrhs, jb, k0, ay0, 0, 0, sc, false));
   kt.end();
   return RMAT_OK;
 }

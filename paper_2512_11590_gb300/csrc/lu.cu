@@ -1505,7 +1505,7 @@ int launch_solve_block(rmat_ctx c, const LUPerm* pm, const cplx<T>* A, int ld, i
   solve_block_kernel<T, LOWER, JB><<<ceil_div(ncols, 32), 256, smem, c->stream>>>(
       A, ld, k0, B, ldb, ncols, nb, pm ? pm->rows : nullptr, pm ? pm->src : nullptr,
       pm ? pm->cnt : nullptr, Y, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB, (size_t)0,
-      rmat_plane_fmt(c->precision), Y ? c->ycs : nullptr, c->skip);
+      rmat_plane_fmt(c->precision), Y ? rmat_ycs_cur(c) : nullptr, c->skip);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;
@@ -1580,7 +1580,7 @@ int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb,
   apply_inv_kernel<JB><<<dim3(ceil_div(ncols, 16), JB / 16), 256, smem, c->stream>>>(
       D, k0, nb, B, ldb, ncols, pm ? pm->rows : nullptr, pm ? pm->src : nullptr,
       pm ? pm->cnt : nullptr, Yp, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB, rmat_plane_fmt(c->precision),
-      c->ycs, c->skip);
+      rmat_ycs_cur(c), c->skip);
   kt.end();
   c->launches++;
   RMAT_CU(cudaGetLastError());
@@ -1880,8 +1880,8 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
   const int fmt = rmat_plane_fmt(c->precision);
   auto split_y = [&](int row0, int jb) -> int {
     split_y_kernel<<<ceil_div(nrhs, 8), 256, 0, c->stream>>>(
-        reinterpret_cast<const float2*>(B) + (size_t)row0 * ldb, ldb, jb, nrhs, c->Ypl, yplane, fmt,
-        c->ycs, c->skip);
+        reinterpret_cast<const float2*>(B) + (size_t)row0 * ldb, ldb, jb, nrhs, rmat_ypl_cur(c),
+        yplane, fmt, rmat_ycs_cur(c), c->skip);
     c->launches++;
     RMAT_CU(cudaGetLastError());
     return RMAT_OK;
@@ -1900,19 +1900,41 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
                             c->stream));
   }
   const LUPerm* fpm = upfront ? nullptr : &pm;
+  // Look-ahead (tensor path, no per-block interchanges to replay): after block k's
+  // diagonal application, its update of the NEXT block's rows runs on the main
+  // stream and its update of the far rows on the side stream, so block k+1 can start
+  // at once.  Block k+2 waits for block k's far update (it covers block k+2's rows);
+  // the Y planes alternate between two buffers (block parity) for the same reason.
+  // The far and next-row updates of different blocks reduce-add into disjoint or
+  // commuting rows of B (TMA reduce-add is atomic per element).
+  cudaStream_t main_s = c->stream;
+  bool pending[2] = {false, false};
+  auto la_wait = [&](int b) -> int {
+    if (pending[b]) {
+      RMAT_CU(cudaStreamWaitEvent(main_s, c->la_ev[2 + b], 0));
+      pending[b] = false;
+    }
+    return RMAT_OK;
+  };
+  const bool la_fwd = tc && c->solve_lookahead && fpm == nullptr && c->side;
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int jb = std::min(nb, n - k0);
+    const int b = (k0 / nb) & 1;
+    if (tc) {
+      RMAT_CHECK(la_wait(b));
+      c->ybuf = b;
+    }
     const bool need_y = tc && n - k0 - jb > 0;
     bool fused = false;
     if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
       float2* Bf = reinterpret_cast<float2*>(B);
-      void* Yp = need_y ? c->Ypl : nullptr;
+      void* Yp = need_y ? rmat_ypl_cur(c) : nullptr;
       if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, false, k0, nb, Bf, ldb, nrhs, fpm, Yp));
       else RMAT_CHECK(launch_apply_inv<64>(c, false, k0, nb, Bf, ldb, nrhs, fpm, Yp));
       fused = true;
     } else {
       RMAT_CHECK(solve_block<T, true>(c, fpm, A, ld, k0, nb, jb, B, ldb, nrhs,
-                                      need_y ? c->Ypl : nullptr, &fused));
+                                      need_y ? rmat_ypl_cur(c) : nullptr, &fused));
     }
     if (!fused) {
       if (fpm) RMAT_CHECK(apply_perm<T>(c, pm, B, ldb, nrhs, k0, nb, jb));
@@ -1923,27 +1945,50 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
       if (need_y) RMAT_CHECK(split_y(k0, jb));
     }
     if (need_y) {
-      RMAT_CHECK(launch_solve_tc(c, k0 + jb, n - k0 - jb, nrhs, k0, jb, k0 + jb, n, nullptr, nb));
+      const int row0 = k0 + jb, M = n - k0 - jb, near = std::min(nb, M);
+      if (!la_fwd || near >= M) {
+        RMAT_CHECK(launch_solve_tc(c, row0, M, nrhs, k0, jb, row0, n, nullptr, nb));
+      } else {
+        RMAT_CHECK(launch_solve_tc(c, row0, near, nrhs, k0, jb, row0, n, nullptr, nb));
+        RMAT_CU(cudaEventRecord(c->la_ev[b], main_s));
+        RMAT_CU(cudaStreamWaitEvent(c->side, c->la_ev[b], 0));
+        c->stream = c->side;
+        const int st = launch_solve_tc(c, row0 + near, M - near, nrhs, k0, jb, row0 + near, n,
+                                       nullptr, nb);
+        c->stream = main_s;
+        RMAT_CHECK(st);
+        RMAT_CU(cudaEventRecord(c->la_ev[2 + b], c->side));
+        pending[b] = true;
+      }
     } else {
       RMAT_CHECK(gemm_sub<T>(c, n - k0 - jb, nrhs, jb, A + (size_t)(k0 + jb) * ld + k0, ld,
                              B + (size_t)k0 * ldb, ldb, B + (size_t)(k0 + jb) * ldb, ldb));
     }
   }
-  // backward: U11 solve, then update the rows above (right-looking)
+  RMAT_CHECK(la_wait(0));
+  RMAT_CHECK(la_wait(1));
+  // backward: U11 solve, then update the rows above (right-looking); look-ahead as
+  // in the forward sweep, the next block being the one above
+  const bool la_bwd = tc && c->solve_lookahead && c->side;
   const int last = ((n - 1) / nb) * nb;
   for (int k0 = last; k0 >= 0; k0 -= nb) {
     const int jb = std::min(nb, n - k0);
+    const int b = (k0 / nb) & 1;
+    if (tc) {
+      RMAT_CHECK(la_wait(b));
+      c->ybuf = b;
+    }
     const bool need_y = tc && k0 > 0;
     bool fused = false;
     if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
       float2* Bf = reinterpret_cast<float2*>(B);
-      void* Yp = need_y ? c->Ypl : nullptr;
+      void* Yp = need_y ? rmat_ypl_cur(c) : nullptr;
       if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, true, k0, nb, Bf, ldb, nrhs, nullptr, Yp));
       else RMAT_CHECK(launch_apply_inv<64>(c, true, k0, nb, Bf, ldb, nrhs, nullptr, Yp));
       fused = true;
     } else {
       RMAT_CHECK(solve_block<T, false>(c, nullptr, A, ld, k0, nb, jb, B, ldb, nrhs,
-                                       need_y ? c->Ypl : nullptr, &fused));
+                                       need_y ? rmat_ypl_cur(c) : nullptr, &fused));
     }
     if (!fused) {
       trsm_block_rhs_kernel<T, false><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B,
@@ -1954,11 +1999,27 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     }
     if (need_y) {
       // A = U rows of earlier row blocks: their per-block scales apply row-wise
-      RMAT_CHECK(launch_solve_tc(c, 0, k0, nrhs, k0, jb, 0, n, fmt == 1 ? c->uscale : nullptr, nb));
+      const float* rs = fmt == 1 ? c->uscale : nullptr;
+      const int near = std::min(nb, k0);
+      if (!la_bwd || near >= k0) {
+        RMAT_CHECK(launch_solve_tc(c, 0, k0, nrhs, k0, jb, 0, n, rs, nb));
+      } else {
+        RMAT_CHECK(launch_solve_tc(c, k0 - near, near, nrhs, k0, jb, k0 - near, n, rs, nb));
+        RMAT_CU(cudaEventRecord(c->la_ev[b], main_s));
+        RMAT_CU(cudaStreamWaitEvent(c->side, c->la_ev[b], 0));
+        c->stream = c->side;
+        const int st = launch_solve_tc(c, 0, k0 - near, nrhs, k0, jb, 0, n, rs, nb);
+        c->stream = main_s;
+        RMAT_CHECK(st);
+        RMAT_CU(cudaEventRecord(c->la_ev[2 + b], c->side));
+        pending[b] = true;
+      }
     } else {
       RMAT_CHECK(gemm_sub<T>(c, k0, nrhs, jb, A + k0, ld, B + (size_t)k0 * ldb, ldb, B, ldb));
     }
   }
+  RMAT_CHECK(la_wait(0));
+  RMAT_CHECK(la_wait(1));
   return RMAT_OK;
 }
 

@@ -124,6 +124,13 @@ struct rmat_ctx_s {
   unsigned* umax = nullptr; size_t umax_cap = 0;
   float* uscale = nullptr; size_t uscale_cap = 0;
   float* ycs = nullptr;    size_t ycs_cap = 0;
+  // The solves' Y planes and column scales are double-buffered: block k uses
+  // buffer ybuf = k & 1, so block k+1's diagonal application can run while the
+  // far-row update of block k (on the side stream) still reads buffer k & 1.
+  int ybuf = 0;
+  int solve_lookahead = 0;         // RMAT_PARAM_SOLVE_LOOKAHEAD
+  cudaStream_t side = nullptr;     // look-ahead stream of the solves
+  cudaEvent_t la_ev[4] = {};       // fork / join events of the look-ahead
   double* Dsc = nullptr;   size_t Dsc_cap = 0;      // equilibration scale per row
   std::vector<double> ir_hist;                      // refinement history of the last solve
   double2* Rint = nullptr; size_t Rint_cap = 0;     // R-matrix (row-major nch x nch)
@@ -257,6 +264,12 @@ struct KTimer {
 static inline bool rmat_tensor_prec(int p) { return p == RMAT_C64_3XTF32_IR || p == RMAT_C64_3XF16_IR; }
 static inline int rmat_plane_fmt(int p) { return p == RMAT_C64_3XF16_IR ? 1 : 0; }
 static inline size_t rmat_plane_esz(int p) { return p == RMAT_C64_3XF16_IR ? 2 : 4; }
+// current Y-plane buffer and its column scales
+static inline void* rmat_ypl_cur(rmat_ctx c) {
+  return reinterpret_cast<char*>(c->Ypl) +
+         (size_t)c->ybuf * 4 * RMAT_YPL_ROWS * RMAT_MAX_NB * rmat_plane_esz(c->precision);
+}
+static inline float* rmat_ycs_cur(rmat_ctx c) { return c->ycs + (size_t)c->ybuf * RMAT_YPL_ROWS; }
 
 static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 static inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }

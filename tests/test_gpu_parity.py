@@ -222,3 +222,22 @@ def test_panel_rows_in_global_memory(g, ctx, prec, nb, ctas):
     finally:
         g.rmat_set_param(ctx, g.RMAT_PARAM_PANEL_CTAS, 0)
     assert relerr(out["U"], ref["U"]) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+def test_solve_lookahead_vs_oracle(g, prec):
+    """RMAT_PARAM_SOLVE_LOOKAHEAD = 1: next-block updates on the main stream, far
+    rows on the side stream, double-buffered Y planes; same tolerances."""
+    import torch
+    torch.cuda.set_device(0)
+    p = cp.config3(16)
+    ref = truth(p, "c3-16")
+    h = g.rmat_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        g.rmat_set_param(h, g.RMAT_PARAM_SOLVE_LOOKAHEAD, 1)
+        out = run_problem(h, p, prec, max_refine=30, tol=1e-14, nb=64)
+    finally:
+        g.rmat_destroy(h)
+    for k in ("U", "R", "X"):
+        e = relerr(out[k], ref[k])
+        assert e < TOL[prec], (k, e)
