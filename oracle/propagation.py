@@ -27,6 +27,9 @@ out the standard propagation with Lagrange meshes:
       Rl_s = g_RR - g_RL (Rl_{s-1} + g_LL)^-1 g_LR;
 * finally R(a) = Rl_ns / a and U as for one sector (oracle.collision) at a.
 
+The sector systems are solved like oracle.pipeline's reference: LU plus
+double-double refinement (oracle.refine.truth_solve).
+
 l_i' at the nodes and l_i(0), l_i(1) come from the barycentric form of the
 Lagrange polynomials, the barycentric weights 1/prod_{m != i}(x_i - x_m)
 accumulated as logarithms (no under- or overflow at large n).
@@ -44,6 +47,7 @@ import numpy as np
 
 from .collision import collision_matrix
 from .lu import solve
+from .refine import truth_solve
 from .mesh import gauss_legendre_unit, kinetic_bloch, lagrange_mesh
 from .system import assemble_dense
 
@@ -121,7 +125,7 @@ def sector_green(p, V: np.ndarray, sm: dict):
     for al in range(nch):
         Phi[al * n:(al + 1) * n, al] = sm["fL"]
         Phi[al * n:(al + 1) * n, nch + al] = sm["fR"]
-    X = solve(C, Phi)
+    X, _ = truth_solve(C, Phi, steps=2)
     G = p.hm * (Phi.T @ X)
     return G[:nch, :nch], G[:nch, nch:], G[nch:, :nch], G[nch:, nch:]
 
@@ -143,7 +147,7 @@ def propagated_collision(p, radii, potential):
     m = lagrange_mesh(p.nlag, q.a)
     T0 = kinetic_bloch(p.nlag, q.a, m)
     C, Phi = assemble_dense(q, potential(m["r"]), m, T0)
-    X = solve(C, Phi)
+    X, _ = truth_solve(C, Phi, steps=2)
     Rl = p.hm * (Phi.T @ X)                      # = a_1 R(a_1)
     for s in range(2, len(radii)):
         sm = sector_mesh(p.nlag, radii[s - 1], radii[s])
