@@ -478,6 +478,55 @@ def sweep_main(args):
     return 0
 
 
+def propagate_main(args):
+    """R-matrix propagation: a charged alpha + 208Pb-like system (nch = 64, E = 30 MeV)
+    carried to a = 40 fm over 4 sectors of nlag = 100 (N = 6400 each) against one
+    system of nlag = 400 on (0, 40) (N = 25600), split-FP16 factors, FP64 refinement."""
+    import torch
+
+    import cc_problems as cp
+    import paper_2512_11590_gb300 as g
+    torch.cuda.set_device(0)
+    prec = g.RMAT_C64_3XF16_IR
+    a, ns, nlag = 40.0, 4, 100
+    radii = [a * s / ns for s in range(ns + 1)]
+    p = cp.charged_problem(26, 64, nlag, 30.0, a=a)
+    stream = torch.cuda.current_stream()
+    ctx = g.rmat_create(0, stream.cuda_stream)
+    Vs = []
+    for s in range(ns):
+        r = (g.rmat_mesh(nlag, radii[1])["r"] if s == 0
+             else g.rmat_sector_mesh(nlag, radii[s], radii[s + 1])["r"])
+        Vs.append(torch.from_numpy(cp.potential_at(p, r).ravel()).cuda())
+    prob, keep = g.make_problem_struct(p.nch, nlag, a, p.hm, p.l, p.thresh, prec, zz=p.zz)
+    no = int(np.sum(p.E - p.thresh > 0))
+    U = torch.zeros(no * no, dtype=torch.complex128, device="cuda")
+    times = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, _ = g.rmat_propagate(ctx, prob, p.E, radii, [v.data_ptr() for v in Vs], 30, 1e-13,
+                                 0, U.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    Up = U.cpu().numpy().reshape(no, no).T
+    g.rmat_destroy(ctx)
+    p1 = cp.charged_problem(26, 64, 4 * nlag, 30.0, a=a)
+    one = solve_once(p1, prec, warm=True)[0]
+    rd = float(np.max(np.abs(Up - one["U"])) / np.max(np.abs(one["U"])))
+    print(json.dumps({"metric": "R-matrix propagation: 4 sectors of N=6400 vs one system of N=25600 "
+                                "to a = 40 fm (charged, nch = 64)",
+                      "unit": "ms", "propagation_ms": float(np.median(times)),
+                      "single_system_ms": one["ms"], "single_system_iters": one["iters"],
+                      "speedup": one["ms"] / float(np.median(times)), "u_rel_diff": rd,
+                      "sectors": ns, "nlag_per_sector": nlag, "status": st, "data": "synthetic"}))
+    return 0
+
+
 def config5_main(args):
     """Config 5: N = 51200 (nch = 512, nlag = 100), 512 right-hand sides, an energy sweep
     of 8 points reusing the assembly buffers (FP32+IR), and one energy in complex128 for
@@ -534,6 +583,8 @@ def main():
                     help="time the batch driver on this many config-4 systems instead")
     ap.add_argument("--sweep", action="store_true",
                     help="config 2 sweep (N=1600..25600) and config 3b, FP32+IR vs complex128")
+    ap.add_argument("--propagate", action="store_true",
+                    help="R-matrix propagation over 4 sectors vs one system (charged, a = 40 fm)")
     ap.add_argument("--config5", action="store_true",
                     help="config 5: N=51200, 8-energy FP32+IR sweep (+ one complex128 energy)")
     ap.add_argument("--batch-refine", type=int, default=10,
@@ -558,6 +609,8 @@ def main():
         return sweep_main(args)
     if args.config5:
         return config5_main(args)
+    if args.propagate:
+        return propagate_main(args)
 
     import torch
     import paper_2512_11590_gb300 as g

@@ -226,6 +226,41 @@ int rmat_solve(rmat_ctx ctx, void* X_dev, int ldx, int max_refine, double tol,
  * function did not converge within its iteration bound or overflowed). */
 int rmat_collision(rmat_ctx ctx, void* R_dev, void* U_dev, int* nopen);
 
+/* ---- R-matrix propagation over radial sectors --------------------------------
+ * The internal region (0, a) cut at 0 = a_0 < a_1 < ... < a_ns = a (the ns sectors
+ * of the paper's interface, Sec. 4).  Sector 1 uses rmat_mesh's regularised
+ * basis on (0, a_1), its R-matrix in length units Rl = a_1 R(a_1) = hm Phi^T X;
+ * sector s >= 2 uses rmat_sector_mesh's basis on (a_{s-1}, a_s), the Bloch
+ * operator at both ends, and the blocks g_ab = hm phi_a^T C_s^-1 phi_b (a, b in
+ * {L, R}: boundary values at a_{s-1}, a_s) of its Green's function:
+ *   Rl <- g_RR - g_RL (Rl + g_LL)^-1 g_LR.
+ * Then R = Rl / a and U as rmat_collision at a.  Every sector system is assembled,
+ * factored and refined like rmat_assemble/rmat_factor/rmat_solve (the sector
+ * systems with the 2 nch right-hand sides [phi_R | phi_L]) in the problem's
+ * precision; the propagation step is FP64.
+ *
+ * rmat_sector_mesh: the non-regularised Lagrange-Legendre mesh of (r1, r2),
+ *   f_i(r) = l_i(x) / sqrt(h w_i), x = (r - r1)/h, l_i the Lagrange polynomials
+ *   of the Gauss-Legendre nodes of (0, 1) (weights w):  r[i] = r1 + h x_i,
+ *   lam[i] = h w_i, fL[i] = f_i(r1), fR[i] = f_i(r2), Kf[i*nlag + j] =
+ *   int_{r1}^{r2} f_i' f_j' dr (fm^-2).  Outputs may be NULL.  Needs no GPU.
+ *   Errors: -1 nlag outside 2..1024, -2 not 0 <= r1 < r2.
+ * rmat_propagate: prob->bloch_B must be 0 (the sector Bloch operators have B = 0);
+ *   radii: host [ns+1], radii[0] = 0, increasing; V_dev[s]: device complex128
+ *   cpot(nlag, nch, nch) (rmat_assemble's layout) at sector s's mesh points
+ *   (rmat_mesh of a_1 for s = 0, rmat_sector_mesh of (a_s, a_{s+1}) after that);
+ *   max_refine, tol as rmat_solve for every sector; R_dev (may be NULL), U_dev,
+ *   nopen as rmat_collision.  Synchronises.  Returns RMAT_ENOCONV when a sector's
+ *   refinement stopped above tol.  Errors: -2 prob invalid or B != 0, -3 ns or
+ *   radii invalid, -4 V_dev, -5 max_refine < 0, -6 U_dev NULL with open channels,
+ *   RMAT_ESINGULAR, RMAT_ECHANFN, RMAT_ETIMEOUT, RMAT_ENOMEM, RMAT_ECUDA.
+ *   Leaves the context without a solved problem (rmat_collision: RMAT_ESTATE). */
+int rmat_sector_mesh(int nlag, double r1, double r2, double* r, double* lam, double* fL,
+                     double* fR, double* Kf);
+int rmat_propagate(rmat_ctx ctx, const rmat_problem* prob, double E, int ns, const double* radii,
+                   const void* const* V_dev, int max_refine, double tol, void* R_dev, void* U_dev,
+                   int* nopen);
+
 /* Counters and timers of the last factor/solve, for benchmarks:
  *   out[0] N, out[1] nrhs, out[2] LU block width, out[3] panel CTAs,
  *   out[4] kernel launches enqueued since the last rmat_reset_counters,

@@ -50,7 +50,8 @@ EXPORTED = ("rmat_create", "rmat_destroy", "rmat_set_param", "rmat_mesh", "rmat_
             "rmat_load_dense", "rmat_factor", "rmat_solve", "rmat_collision", "rmat_get_stats",
             "rmat_reset_counters", "rmat_refine_history", "rmat_collision_noalloc",
             "rmat_batch_create", "rmat_batch_nopen", "rmat_batch_set", "rmat_batch_tune",
-            "rmat_batch_run", "rmat_batch_info", "rmat_batch_destroy", "rmat_status_string")
+            "rmat_batch_run", "rmat_batch_info", "rmat_batch_destroy", "rmat_status_string",
+            "rmat_sector_mesh", "rmat_propagate")
 
 
 class rmat_problem(ct.Structure):
@@ -104,6 +105,9 @@ def lib():
             "rmat_batch_destroy": (i, [vp]),
             "rmat_status_string": (ct.c_char_p, [i]),
             "rmat_last_error": (i, [ct.c_char_p, i]),
+            "rmat_sector_mesh": (i, [i, d, d, pd, pd, pd, pd, pd]),
+            "rmat_propagate": (i, [vp, ct.POINTER(rmat_problem), d, i, pd, ct.POINTER(vp), i, d,
+                                   vp, vp, pi]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -212,6 +216,32 @@ def rmat_collision(ctx, R_dev=0, U_dev=0) -> int:
     _check("rmat_collision", lib().rmat_collision(ct.c_void_p(ctx), ct.c_void_p(R_dev or None),
                                                   ct.c_void_p(U_dev or None), ct.byref(nopen)))
     return nopen.value
+
+
+def rmat_sector_mesh(nlag: int, r1: float, r2: float) -> dict:
+    """Sector mesh of (r1, r2): r, lam, fL, fR (nlag,) and Kf (nlag, nlag), float64."""
+    out = {k: np.zeros(nlag) for k in ("r", "lam", "fL", "fR")}
+    Kf = np.zeros((nlag, nlag))
+    p = lambda arr: arr.ctypes.data_as(ct.POINTER(ct.c_double))  # noqa: E731
+    _check("rmat_sector_mesh", lib().rmat_sector_mesh(int(nlag), float(r1), float(r2), p(out["r"]),
+                                                      p(out["lam"]), p(out["fL"]), p(out["fR"]),
+                                                      p(Kf)))
+    out["Kf"] = Kf
+    return out
+
+
+def rmat_propagate(ctx, prob, E, radii, V_ptrs, max_refine=30, tol=1e-13, R_dev=0, U_dev=0):
+    """R-matrix propagation over len(radii)-1 sectors; returns (status, nopen)."""
+    ns = len(radii) - 1
+    rad = np.ascontiguousarray(radii, dtype=np.float64)
+    vp = (ct.c_void_p * ns)(*[int(v) for v in V_ptrs])
+    nopen = ct.c_int(0)
+    s = lib().rmat_propagate(ct.c_void_p(ctx), ct.byref(prob), float(E), int(ns),
+                             rad.ctypes.data_as(ct.POINTER(ct.c_double)), vp, int(max_refine),
+                             float(tol), ct.c_void_p(R_dev or None), ct.c_void_p(U_dev or None),
+                             ct.byref(nopen))
+    _check("rmat_propagate", s, ok=(RMAT_OK, RMAT_ENOCONV))
+    return s, nopen.value
 
 
 STAT_KEYS = ("N", "nrhs", "nb", "panel_ctas", "launches", "tu_launches", "tu_ms", "tu_flops",

@@ -293,7 +293,7 @@ int rmat_destroy(rmat_ctx c) {
                   c->Fpl,  c->Bpl, c->Ypl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
                   c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows, c->Dinv,
                   c->umax, c->uscale, c->ycs, c->pfwd, c->Bt, c->Kinv, c->Kinv32, c->W32, c->Bs,
-                  c->gm_V, c->gm_Z, c->gm_T, c->gm_small};
+                  c->gm_V, c->gm_Z, c->gm_T, c->gm_small, c->faL, c->prop};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->hstat) cudaFreeHost(c->hstat);
@@ -350,8 +350,11 @@ int rmat_mesh(int nlag, double a, double* x, double* omx, double* lam, double* r
   return rmat_mesh_host(nlag, a, x, omx, lam, r, f_a, T0);
 }
 
-int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_dev) {
-  RMAT_CHECK(begin(c));
+// Assembly of the system of the regular mesh on (0, pb->a) (r2 <= 0) or of the
+// propagation sector (r1, r2) with right-hand sides [phi_R | phi_L].
+static int assemble_impl(rmat_ctx c, const rmat_problem* pb, double E, const void* V_dev,
+                         double r1, double r2) {
+  const bool sector = r2 > 0.0;
   if (!pb || pb->nch < 1 || pb->nlag < 1 || pb->nlag > 1024 || !(pb->a > 0) || !(pb->hm > 0) ||
       !std::isfinite(pb->bloch_B) || !pb->l || !pb->thresh || !valid_precision(pb->precision))
     return -2;
@@ -363,16 +366,19 @@ int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_de
       return -2;
   if (!std::isfinite(E)) return -3;
   if (!V_dev) return -4;
-  const bool mesh_same = c->nlag == pb->nlag && c->a == pb->a && c->hm == pb->hm &&
-                         c->bloch_B == pb->bloch_B && c->Kmat != nullptr;
+  const double a_key = sector ? r2 : pb->a, r1_key = sector ? r1 : -1.0;
+  const bool mesh_same = c->nlag == pb->nlag && c->a == a_key && c->mesh_r1 == r1_key &&
+                         c->hm == pb->hm && c->bloch_B == pb->bloch_B && c->Kmat != nullptr;
   c->kind = 1;
+  c->sector = sector;
   c->precision = pb->precision;
   c->nch = pb->nch;
   c->nlag = pb->nlag;
   c->N = pb->nch * pb->nlag;
-  c->nrhs = pb->nch;
+  c->nrhs = sector ? 2 * pb->nch : pb->nch;
   c->ld = (int)round_up(c->N, 32);
-  c->a = pb->a;
+  c->a = a_key;
+  c->mesh_r1 = r1_key;
   c->hm = pb->hm;
   c->bloch_B = pb->bloch_B;
   c->E = E;
@@ -383,7 +389,7 @@ int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_de
   c->assembled = c->factored = c->solved = false;
   c->nb = clamp_nb(c->precision, c->nb_param ? c->nb_param : default_nb(c->precision, c->N));
   RMAT_CHECK(reserve(c, false));
-  c->woodbury = c->method_param == 1;
+  c->woodbury = !sector && c->method_param == 1;
   c->equil = !c->woodbury &&
              (c->equil_param == -1 ? c->precision != RMAT_C128 : c->equil_param == 1);
   if (c->equil) RMAT_CHECK(rmat_grow(c, (void**)&c->Dsc, &c->Dsc_cap, (size_t)c->N * sizeof(double)));
@@ -401,9 +407,22 @@ int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_de
   RMAT_CHECK(rmat_grow(c, (void**)&c->open_d, &c->open_cap, nch * sizeof(int)));
   if (!mesh_same) {
     std::vector<double> r(nlag), fa(nlag), T0((size_t)nlag * nlag), K((size_t)nlag * nlag);
-    RMAT_CHECK(rmat_mesh_host(nlag, c->a, nullptr, nullptr, nullptr, r.data(), fa.data(), T0.data()));
-    const double s1 = c->hm * (c->bloch_B / c->a);
-    rmat_kinetic_table(nlag, c->hm, s1, T0.data(), fa.data(), K.data());
+    if (sector) {
+      // K = hm int f_i' f_j' (Bloch terms at both ends included); fa = f_i(r2), faL = f_i(r1)
+      std::vector<double> fL(nlag);
+      RMAT_CHECK(rmat_sector_mesh_host(nlag, r1, r2, r.data(), nullptr, fL.data(), fa.data(),
+                                       T0.data()));
+      rmat_kinetic_table(nlag, c->hm, 0.0, T0.data(), fa.data(), K.data());
+      RMAT_CHECK(rmat_grow(c, (void**)&c->faL, &c->faL_cap, nlag * 8));
+      RMAT_CU(cudaMemcpy(c->faL, fL.data(), nlag * 8, cudaMemcpyHostToDevice));
+      c->faL_host = fL;
+    } else {
+      RMAT_CHECK(rmat_mesh_host(nlag, c->a, nullptr, nullptr, nullptr, r.data(), fa.data(),
+                                T0.data()));
+      const double s1 = c->hm * (c->bloch_B / c->a);
+      rmat_kinetic_table(nlag, c->hm, s1, T0.data(), fa.data(), K.data());
+      c->faL_host.clear();
+    }
     RMAT_CHECK(rmat_grow(c, (void**)&c->Kmat, &c->Kmat_cap, K.size() * 8));
     RMAT_CHECK(rmat_grow(c, (void**)&c->T0, &c->T0_cap, T0.size() * 8));
     RMAT_CHECK(rmat_grow(c, (void**)&c->rmesh, &c->rmesh_cap, nlag * 8));
@@ -419,6 +438,8 @@ int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_de
   if (c->woodbury && c->kinv_nlag != nlag) RMAT_CHECK(woodbury_prepare(c, c->K_host.data()));
   double pm = 0;
   for (double v : c->f_a_host) pm = std::max(pm, std::fabs(v));
+  if (sector)
+    for (double v : c->faL_host) pm = std::max(pm, std::fabs(v));
   c->phi_max = pm;
   RMAT_CU(cudaMemcpyAsync(c->l_d, c->l.data(), nch * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   RMAT_CU(cudaMemcpyAsync(c->th_d, c->thresh.data(), nch * sizeof(double), cudaMemcpyHostToDevice,
@@ -439,6 +460,11 @@ int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_de
   c->stage_ev[0][1] = e1;
   c->assembled = true;
   return RMAT_OK;
+}
+
+int rmat_assemble(rmat_ctx c, const rmat_problem* pb, double E, const void* V_dev) {
+  RMAT_CHECK(begin(c));
+  return assemble_impl(c, pb, E, V_dev, 0.0, -1.0);
 }
 
 int rmat_load_dense(rmat_ctx c, int n, int nrhs, const void* A_dev, int lda, const void* B_dev,
@@ -586,15 +612,10 @@ int enqueue_solve_refine(rmat_ctx c, int max_refine, double tol, IrState* st) {
   return rc;
 }
 
-extern "C" {
-
-int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int* iters,
-               double* rel_resid) {
-  RMAT_CHECK(begin(c));
-  if (!X_dev) return -2;
-  if (ldx < c->N) return -3;
-  if (max_refine < 0) return -4;
-  if (!c->factored) return RMAT_ESTATE;
+// First solve and refinement of the factored system; X stays in c->X (FP64,
+// row-major N x nrhs).  *status: RMAT_OK or RMAT_ENOCONV.
+static int solve_refine(rmat_ctx c, int max_refine, double tol, int* iters, double* rel_resid,
+                        int* status_out) {
   cudaEvent_t e0, e1, e2;
   record_stage(c, &e0);
   RMAT_CHECK(launch_w_from_phi(c));
@@ -646,17 +667,33 @@ int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int
     }
   }
   record_stage(c, &e2);
-  RMAT_CHECK(launch_x_out(c, reinterpret_cast<double2*>(X_dev), ldx));
-  RMAT_CHECK(read_status(c));
   c->stage_ev[2][0] = e0;
   c->stage_ev[2][1] = e1;
   c->stage_ev[3][0] = e1;
   c->stage_ev[3][1] = e2;
+  if (iters) *iters = it;
+  if (rel_resid) *rel_resid = rel;
+  *status_out = status;
+  return RMAT_OK;
+}
+
+extern "C" {
+
+int rmat_solve(rmat_ctx c, void* X_dev, int ldx, int max_refine, double tol, int* iters,
+               double* rel_resid) {
+  RMAT_CHECK(begin(c));
+  if (!X_dev) return -2;
+  if (ldx < c->N) return -3;
+  if (max_refine < 0) return -4;
+  if (!c->factored) return RMAT_ESTATE;
+  if (c->sector) return RMAT_ESTATE;  // a propagation sector's state is internal
+  int status = RMAT_OK;
+  RMAT_CHECK(solve_refine(c, max_refine, tol, iters, rel_resid, &status));
+  RMAT_CHECK(launch_x_out(c, reinterpret_cast<double2*>(X_dev), ldx));
+  RMAT_CHECK(read_status(c));
   if (c->hstat[ST_TIMEOUT]) return RMAT_ETIMEOUT;
   if (c->hstat[ST_BADARG]) return RMAT_ESTATE;
   c->solved = true;
-  if (iters) *iters = it;
-  if (rel_resid) *rel_resid = rel;
   if (c->hstat[ST_INFO]) return RMAT_ESINGULAR;
   return status;
 }
@@ -685,6 +722,73 @@ int rmat_collision(rmat_ctx c, void* R_dev, void* U_dev, int* nopen) {
   if (c->hstat[ST_CHANFN]) return RMAT_ECHANFN;
   if (c->hstat[ST_INFO]) return RMAT_ESINGULAR;
   return RMAT_OK;
+}
+
+int rmat_sector_mesh(int nlag, double r1, double r2, double* r, double* lam, double* fL,
+                     double* fR, double* Kf) {
+  return rmat_sector_mesh_host(nlag, r1, r2, r, lam, fL, fR, Kf);
+}
+
+int rmat_propagate(rmat_ctx c, const rmat_problem* pb, double E, int ns, const double* radii,
+                   const void* const* V_dev, int max_refine, double tol, void* R_dev, void* U_dev,
+                   int* nopen) {
+  RMAT_CHECK(begin(c));
+  if (!pb || pb->bloch_B != 0.0 || pb->nlag < 2) return -2;
+  if (ns < 1 || ns > 4096 || !radii || radii[0] != 0.0) return -3;
+  for (int s = 1; s <= ns; ++s)
+    if (!(radii[s] > radii[s - 1]) || !std::isfinite(radii[s])) return -3;
+  if (!V_dev) return -4;
+  for (int s = 0; s < ns; ++s)
+    if (!V_dev[s]) return -4;
+  if (max_refine < 0) return -5;
+  const int nch = pb->nch;
+  c->solved = false;
+  std::vector<int> open;
+  for (int k = 0; k < nch; ++k)
+    if (E - pb->thresh[k] > 0) open.push_back(k);
+  const int no = (int)open.size();
+  if (nopen) *nopen = no;
+  if (no > 0 && !U_dev) return -6;
+  // sector 1: the regular mesh on (0, a_1); Rl = a_1 R(a_1) = hm Phi^T X
+  rmat_problem p0 = *pb;
+  p0.a = radii[1];
+  RMAT_CHECK(assemble_impl(c, &p0, E, V_dev[0], 0.0, -1.0));
+  const size_t blk = (size_t)nch * nch;
+  RMAT_CHECK(rmat_grow(c, &c->prop, &c->prop_cap, 6 * blk * sizeof(double2)));
+  double2* Rl = reinterpret_cast<double2*>(c->prop);
+  double2* G = Rl + blk;       // RR, RL, LR, LL
+  double2* P = G + 4 * blk;
+  int status = RMAT_OK, st = RMAT_OK, it = 0;
+  double rel = 0.0;
+  auto factor_solve = [&]() -> int {
+    int info = 0;
+    const int fs = rmat_factor(c, &info);
+    if (fs != RMAT_OK) return fs;
+    RMAT_CHECK(solve_refine(c, max_refine, tol, &it, &rel, &st));
+    if (st != RMAT_OK) status = st;
+    return RMAT_OK;
+  };
+  RMAT_CHECK(factor_solve());
+  RMAT_CHECK(launch_sector_g(c, Rl));
+  for (int s = 2; s <= ns; ++s) {
+    RMAT_CHECK(assemble_impl(c, pb, E, V_dev[s - 1], radii[s - 1], radii[s]));
+    RMAT_CHECK(factor_solve());
+    RMAT_CHECK(launch_sector_g(c, G));
+    // Rl <- g_RR - g_RL (Rl + g_LL)^-1 g_LR  (FP64 LU of the nch x nch matrix)
+    RMAT_CHECK(launch_prop_step(c, Rl, G, P));
+  }
+  // R(a) = Rl / a and U at a = a_ns
+  c->a = radii[ns];
+  RMAT_CHECK(launch_prop_finish(c, Rl, reinterpret_cast<double2*>(R_dev)));
+  if (no > 0)
+    RMAT_CU(cudaMemcpyAsync(c->open_d, open.data(), no * sizeof(int), cudaMemcpyHostToDevice,
+                            c->stream));
+  RMAT_CHECK(launch_u_from_rint(c, reinterpret_cast<double2*>(U_dev), no));
+  RMAT_CHECK(read_status(c));
+  if (c->hstat[ST_TIMEOUT]) return RMAT_ETIMEOUT;
+  if (c->hstat[ST_CHANFN]) return RMAT_ECHANFN;
+  if (c->hstat[ST_INFO]) return RMAT_ESINGULAR;
+  return status;
 }
 
 int rmat_get_stats(rmat_ctx c, double* out, int n) {

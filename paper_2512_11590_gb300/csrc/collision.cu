@@ -98,6 +98,11 @@ int launch_collision(rmat_ctx c, double2* R_dev, double2* U_dev, int nopen) {
       c->X, nch, c->nlag, c->nrhs, c->fa, c->hm / c->a, c->Rint, R_dev);
   c->launches++;
   RMAT_CU(cudaGetLastError());
+  return launch_u_from_rint(c, U_dev, nopen);
+}
+
+int launch_u_from_rint(rmat_ctx c, double2* U_dev, int nopen) {
+  const int nch = c->nch;
   if (!U_dev || nopen == 0) return RMAT_OK;
   ChanFn* fn = reinterpret_cast<ChanFn*>(c->Zbuf);
   double2* ZO = reinterpret_cast<double2*>(reinterpret_cast<char*>(c->Zbuf) +
@@ -121,6 +126,90 @@ int launch_collision(rmat_ctx c, double2* R_dev, double2* U_dev, int nopen) {
   c->tu_flops = tf;
   c->tu_events.resize(tev);
   u_extract_kernel<<<ceil_div(nopen * nopen, 128), 128, 0, c->stream>>>(ZI, nopen, c->open_d, U_dev);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+namespace {
+
+// G[q][al][be] = hm sum_i f_q(i) X[(al, i), col_q(be)]: q = 0 RR (f_R, columns 0..nch),
+// 1 RL (f_R, columns nch..2nch), 2 LR (f_L, columns 0..nch), 3 LL (f_L, nch..2nch).
+__global__ void sector_g_kernel(double2* __restrict__ G, const double2* __restrict__ X, int nch,
+                                int nlag, int nrhs, const double* __restrict__ fR,
+                                const double* __restrict__ fL, double hm, int nblocks) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nblocks * nch * nch) return;
+  const int q = e / (nch * nch), al = (e / nch) % nch, be = e % nch;
+  const double* f = q < 2 ? fR : fL;
+  const int col = (q & 1) ? nch + be : be;
+  double sr = 0.0, si = 0.0;
+  for (int i = 0; i < nlag; ++i) {
+    const double2 x = X[((size_t)al * nlag + i) * nrhs + col];
+    sr = fma(f[i], x.x, sr);
+    si = fma(f[i], x.y, si);
+  }
+  G[e] = make_double2(hm * sr, hm * si);
+}
+
+}  // namespace
+
+int launch_sector_g(rmat_ctx c, double2* G) {
+  const int nch = c->nch, nb = c->sector ? 4 : 1;
+  sector_g_kernel<<<ceil_div(nb * nch * nch, 128), 128, 0, c->stream>>>(
+      G, c->X, nch, c->nlag, c->nrhs, c->fa, c->sector ? c->faL : nullptr, c->hm, nb);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
+namespace {
+
+__global__ void prop_add_kernel(double2* __restrict__ P, const double2* __restrict__ A,
+                                const double2* __restrict__ B, int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) P[e] = make_double2(A[e].x + B[e].x, A[e].y + B[e].y);
+}
+
+// Rint = Rl / a (row-major) and, when requested, Rout column-major
+__global__ void prop_finish_kernel(double2* __restrict__ Rint, double2* __restrict__ Rout,
+                                   const double2* __restrict__ Rl, int nch, double inv_a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nch * nch) return;
+  const double2 r = make_double2(Rl[e].x * inv_a, Rl[e].y * inv_a);
+  Rint[e] = r;
+  if (Rout) Rout[(e / nch) + (size_t)nch * (e % nch)] = r;
+}
+
+}  // namespace
+
+// One propagation step: Rl <- g_RR - g_RL (Rl + g_LL)^-1 g_LR (G = RR, RL, LR, LL).
+int launch_prop_step(rmat_ctx c, double2* Rl, double2* G, double2* P) {
+  const int nch = c->nch, n = nch * nch;
+  const size_t blk = (size_t)n;
+  double2 *gRR = G, *gRL = G + blk, *gLR = G + 2 * blk, *gLL = G + 3 * blk;
+  prop_add_kernel<<<ceil_div(n, 128), 128, 0, c->stream>>>(P, Rl, gLL, n);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  const long long tl = c->tu_launches;
+  const double tf = c->tu_flops;
+  const size_t tev = c->tu_events.size();
+  const int nb = std::min(64, nch);
+  RMAT_CHECK(perm_reserve(c, c->perm_z, nch, nb));
+  RMAT_CHECK(lu_factor_dev<double>(c, P, nch, nch, c->zpiv, nb, false, c->perm_z));
+  RMAT_CHECK(lu_solve_dev<double>(c, P, nch, nch, c->perm_z, nb, gLR, nch, nch));  // Y in gLR
+  RMAT_CHECK(gemm_sub_c128(c, nch, nch, nch, gRL, nch, gLR, nch, gRR, nch));   // gRR -= gRL Y
+  c->tu_launches = tl;
+  c->tu_flops = tf;
+  c->tu_events.resize(tev);
+  RMAT_CU(cudaMemcpyAsync(Rl, gRR, blk * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  return RMAT_OK;
+}
+
+int launch_prop_finish(rmat_ctx c, const double2* Rl, double2* Rout) {
+  const int nch = c->nch;
+  prop_finish_kernel<<<ceil_div(nch * nch, 128), 128, 0, c->stream>>>(c->Rint, Rout, Rl, nch,
+                                                                       1.0 / c->a);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;

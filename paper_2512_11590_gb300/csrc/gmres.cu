@@ -152,6 +152,7 @@ __global__ void from_bw_kernel(double2* __restrict__ z, const cplx<T>* __restric
 // w = Phi - t  (so that w = C z when t = Phi - C z)
 __global__ void phi_minus_kernel(double2* __restrict__ w, const double2* __restrict__ t,
                                  size_t total, int nrhs, int nlag, const double* __restrict__ fa,
+                                 const double* __restrict__ faL, int nch,
                                  const double2* __restrict__ B64) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -161,7 +162,8 @@ __global__ void phi_minus_kernel(double2* __restrict__ w, const double2* __restr
     } else {
       const int row = (int)(e / nrhs), be = (int)(e % nrhs);
       const int al = row / nlag, i = row - al * nlag;
-      phi = make_double2(al == be ? fa[i] : 0.0, 0.0);
+      if (faL && be >= nch) phi = make_double2(al == be - nch ? faL[i] : 0.0, 0.0);
+      else phi = make_double2(al == be ? fa[i] : 0.0, 0.0);
     }
     w[e] = make_double2(phi.x - t[e].x, phi.y - t[e].y);
   }
@@ -237,7 +239,8 @@ struct Gmres {
   int apply(double2* w, const double2* z) {
     RMAT_CHECK(launch_apply_resid(c, z, T));
     phi_minus_kernel<<<grid_of(c, total), 256, 0, c->stream>>>(
-        w, T, total, nrhs, c->nlag, c->fa, c->kind == 2 ? c->B64 : nullptr);
+        w, T, total, nrhs, c->nlag, c->fa, c->sector ? c->faL : nullptr, c->nch,
+        c->kind == 2 ? c->B64 : nullptr);
     c->launches++;
     RMAT_CU(cudaGetLastError());
     return RMAT_OK;

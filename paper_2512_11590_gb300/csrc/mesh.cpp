@@ -151,6 +151,60 @@ int rmat_mesh_host(int nlag, double a, double* x_out, double* omx_out, double* l
   return RMAT_OK;
 }
 
+// Mesh of a propagation sector (r1, r2): the Lagrange-Legendre basis without
+// regularisation, f_i(r) = l_i(x) / sqrt(h w_i), x = (r - r1)/h, l_i the Lagrange
+// polynomial through the Gauss-Legendre nodes of (0, 1), so f_i(r_j) =
+// delta_ij / sqrt(h w_j) and f_i is non-zero at both ends.  Tables:
+//   r_i = r1 + h x_i, lam_i = h w_i, fL_i = f_i(r1), fR_i = f_i(r2),
+//   Kf_ij = int_{r1}^{r2} f_i' f_j' dr = sum_k w_k D_ki D_kj / (h^2 sqrt(w_i w_j)),
+// D_ki = l_i'(x_k) (the integrand has degree 2n - 4 < 2n: the rule is exact).
+// Barycentric weights of Gauss-Legendre nodes in closed form, beta_i ~
+// (-1)^i sqrt(x_i (1 - x_i) w_i); D_ki = (beta_i / beta_k) / (x_k - x_i) for
+// k != i and D_kk = -sum_{i != k} D_ki (the derivative of a constant vanishes).
+int rmat_sector_mesh_host(int nlag, double r1, double r2, double* r, double* lam, double* fL,
+                          double* fR, double* Kf) {
+  if (nlag < 2 || nlag > 1024) return -1;
+  if (!(r2 > r1) || !std::isfinite(r1) || !std::isfinite(r2) || r1 < 0.0) return -2;
+  const int n = nlag;
+  const double h = r2 - r1;
+  std::vector<double> x(n), omx(n), w(n), rr(n), fa(n);
+  RMAT_CHECK(rmat_mesh_host(n, 1.0, x.data(), omx.data(), w.data(), rr.data(), fa.data(), nullptr));
+  std::vector<double> beta(n), D((size_t)n * n);
+  for (int i = 0; i < n; ++i) beta[i] = ((i & 1) ? -1.0 : 1.0) * std::sqrt(x[i] * omx[i] * w[i]);
+  for (int k = 0; k < n; ++k) {
+    double diag = 0.0;
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const double d = (beta[i] / beta[k]) / (x[k] - x[i]);
+      D[(size_t)k * n + i] = d;
+      diag -= d;
+    }
+    D[(size_t)k * n + k] = diag;
+  }
+  // l_i(t) = (beta_i / (t - x_i)) / sum_m beta_m / (t - x_m) at t = 0 (t - x_m = -x_m)
+  // and t = 1 (t - x_m = 1 - x_m, correctly rounded in omx)
+  double s0 = 0.0, s1 = 0.0;
+  for (int m = 0; m < n; ++m) {
+    s0 += beta[m] / (-x[m]);
+    s1 += beta[m] / omx[m];
+  }
+  for (int i = 0; i < n; ++i) {
+    const double sc = 1.0 / std::sqrt(h * w[i]);
+    if (r) r[i] = r1 + h * x[i];
+    if (lam) lam[i] = h * w[i];
+    if (fL) fL[i] = (beta[i] / (-x[i])) / s0 * sc;
+    if (fR) fR[i] = (beta[i] / omx[i]) / s1 * sc;
+  }
+  if (Kf)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc += w[k] * D[(size_t)k * n + i] * D[(size_t)k * n + j];
+        Kf[(size_t)i * n + j] = acc / (h * h * std::sqrt(w[i] * w[j]));
+      }
+  return RMAT_OK;
+}
+
 void rmat_kinetic_table(int nlag, double hm, double s1, const double* T0, const double* fa,
                         double* K) {
   for (int i = 0; i < nlag; ++i)

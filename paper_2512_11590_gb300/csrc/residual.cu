@@ -21,7 +21,7 @@ namespace {
 __global__ void __launch_bounds__(256)
 resid_kinetic_kernel(double2* __restrict__ R, const double2* __restrict__ X, int nrhs, int nlag,
                      const double* __restrict__ K, const double* __restrict__ fa,
-                     const int* __restrict__ skip) {
+                     const double* __restrict__ faL, const int* __restrict__ skip) {
   if (skip && *skip) return;
   const int al = blockIdx.y;
   const int be = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -37,7 +37,10 @@ resid_kinetic_kernel(double2* __restrict__ R, const double2* __restrict__ X, int
       sr = fma(k, x.x, sr);
       si = fma(k, x.y, si);
     }
-    const double phi = (al == be) ? fa[i] : 0.0;
+    // surface terms: columns be < nch f_i(a) (or f_i(r2)), columns nch + be f_i(r1)
+    const int nch = gridDim.y;
+    const double phi = (faL && be >= nch) ? (al == be - nch ? faL[i] : 0.0)
+                                          : (al == be ? fa[i] : 0.0);
     R[((size_t)al * nlag + i) * nrhs + be] = make_double2(phi - sr, -si);
   }
 }
@@ -217,8 +220,8 @@ __global__ void x_from_w_kernel(double2* __restrict__ X, const cplx<T>* __restri
 // right-hand sides into the solve buffer: surface terms (assembled) or B (dense)
 template <class T>
 __global__ void w_from_phi_kernel(cplx<T>* __restrict__ Bw, int N, int nrhs, int nlag,
-                                  const double* __restrict__ fa, const double2* __restrict__ B64,
-                                  const double* __restrict__ D) {
+                                  const double* __restrict__ fa, const double* __restrict__ faL,
+                                  const double2* __restrict__ B64, const double* __restrict__ D) {
   const size_t total = (size_t)N * nrhs;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -227,8 +230,9 @@ __global__ void w_from_phi_kernel(cplx<T>* __restrict__ Bw, int N, int nrhs, int
     if (B64) {
       z = B64[e];
     } else {
-      const int al = row / nlag, i = row - al * nlag;
-      z = make_double2(al == be ? fa[i] : 0.0, 0.0);
+      const int al = row / nlag, i = row - al * nlag, nch = N / nlag;
+      if (faL && be >= nch) z = make_double2(al == be - nch ? faL[i] : 0.0, 0.0);
+      else z = make_double2(al == be ? fa[i] : 0.0, 0.0);
     }
     if (D) {
       z.x *= D[row];
@@ -308,7 +312,7 @@ int launch_residual(rmat_ctx c, double*) {
   if (c->kind == 1) {
     dim3 gk(ceil_div(nrhs, 32), c->nch);
     resid_kinetic_kernel<<<gk, 256, 0, c->stream>>>(c->Rres, c->X, nrhs, c->nlag, c->Kmat, c->fa,
-                                                    c->skip);
+                                                    c->sector ? c->faL : nullptr, c->skip);
     dim3 gc(ceil_div(nrhs, RC_T), ceil_div(c->nch, RC_T), c->nlag);
     resid_coupling_kernel<<<gc, 256, 0, c->stream>>>(c->Rres, c->X, nrhs, c->nlag, c->nch, c->Wpt,
                                                      c->skip);
@@ -339,7 +343,7 @@ int launch_apply_resid(rmat_ctx c, const double2* Xin, double2* Rout) {
   if (c->kind == 1) {
     dim3 gk(ceil_div(nrhs, 32), c->nch);
     resid_kinetic_kernel<<<gk, 256, 0, c->stream>>>(Rout, Xin, nrhs, c->nlag, c->Kmat, c->fa,
-                                                    nullptr);
+                                                    c->sector ? c->faL : nullptr, nullptr);
     dim3 gc(ceil_div(nrhs, RC_T), ceil_div(c->nch, RC_T), c->nlag);
     resid_coupling_kernel<<<gc, 256, 0, c->stream>>>(Rout, Xin, nrhs, c->nlag, c->nch, c->Wpt,
                                                      nullptr);
@@ -387,10 +391,12 @@ int launch_w_from_phi(rmat_ctx c) {
   const double* D = c->equil ? c->Dsc : nullptr;
   if (c->precision == RMAT_C128)
     w_from_phi_kernel<double><<<grid_for(c, total), 256, 0, c->stream>>>(
-        reinterpret_cast<double2*>(c->Bw), c->N, c->nrhs, c->nlag, c->fa, B64, D);
+        reinterpret_cast<double2*>(c->Bw), c->N, c->nrhs, c->nlag, c->fa,
+        c->sector ? c->faL : nullptr, B64, D);
   else
     w_from_phi_kernel<float><<<grid_for(c, total), 256, 0, c->stream>>>(
-        reinterpret_cast<float2*>(c->Bw), c->N, c->nrhs, c->nlag, c->fa, B64, D);
+        reinterpret_cast<float2*>(c->Bw), c->N, c->nrhs, c->nlag, c->fa,
+        c->sector ? c->faL : nullptr, B64, D);
   c->launches++;
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;

@@ -74,6 +74,12 @@ struct rmat_ctx_s {
   int kinv_nlag = 0;       // mesh size K^-1 was formed for (0: stale)
   void* W32 = nullptr;     size_t W32_cap = 0;      // FP32 copy of Wpt for the S assembly
   void* Bs = nullptr;      size_t Bs_cap = 0;       // reordering scratch of the Woodbury solves
+  // R-matrix propagation: a sector system (r1, r2) has right-hand sides
+  // [phi_R | phi_L] (nrhs = 2 nch): fa = f_i(r2), faL = f_i(r1)
+  bool sector = false;
+  double mesh_r1 = -1.0;   // left end of the mesh the tables belong to (-1: regular (0, a))
+  double* faL = nullptr;   size_t faL_cap = 0;
+  void* prop = nullptr;    size_t prop_cap = 0;     // Rl, the four g blocks, scratch (nch^2 each)
   // RMAT_PARAM_REFINE: 0 classical refinement, m > 0 FGMRES-IR with <= m inner steps
   int refine_param = 0;
   long long gm_inner = 0;  // FGMRES inner steps of the last rmat_solve
@@ -93,6 +99,7 @@ struct rmat_ctx_s {
   std::vector<double> thresh;
   std::vector<double> zz;  // Z1 Z2 e^2 per channel (0 = neutral)
   std::vector<double> K_host;  // hm*T0 - hm*(B/a) f f^T of the current mesh (host)
+  std::vector<double> faL_host;  // f_i(r1) of a propagation sector (host)
   std::vector<double> f_a_host;
   double phi_max = 1.0;  // max |Phi| (denominator of the relative residual)
 
@@ -225,6 +232,15 @@ int launch_x_from_w(rmat_ctx c);
 int launch_w_from_phi(rmat_ctx c);
 // collision.cu
 int launch_collision(rmat_ctx c, double2* R_dev, double2* U_dev, int nopen);
+// U from the R-matrix already in c->Rint (row-major nch x nch), at radius c->a
+int launch_u_from_rint(rmat_ctx c, double2* U_dev, int nopen);
+// G[ab][al][be] = hm phi_a^T X_b for a, b in {R, L} (sector systems; Rl only for
+// the first sector): four row-major nch x nch blocks RR, RL, LR, LL
+int launch_sector_g(rmat_ctx c, double2* G);
+int launch_prop_step(rmat_ctx c, double2* Rl, double2* G, double2* P);
+int launch_prop_finish(rmat_ctx c, const double2* Rl, double2* Rout);
+int rmat_sector_mesh_host(int nlag, double r1, double r2, double* r, double* lam, double* fL,
+                          double* fR, double* Kf);
 size_t collision_workspace_bytes(int nch);
 // mesh.cpp: K = hm*T0 - (hm*(B/a)) * (f_i*f_j) in IEEE double, no contraction
 void rmat_kinetic_table(int nlag, double hm, double s1, const double* T0, const double* fa, double* K);

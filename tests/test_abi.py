@@ -72,3 +72,24 @@ def test_no_gpu_fails_loudly(g):
         pytest.skip("a GPU is present")
     h = ct.c_void_p()
     assert g.lib().rmat_create(ct.byref(h), 0, None) in (g.RMAT_ENODEV, g.RMAT_ECUDA)
+
+
+@pytest.mark.parametrize("n,r1,r2", [(2, 0.0, 3.0), (10, 4.0, 9.0), (60, 15.0, 30.0), (150, 5.0, 25.0)])
+def test_library_sector_mesh_matches_oracle(g, n, r1, r2):
+    """Host sector mesh (closed-form barycentric weights, negative-sum diagonal)
+    against the oracle's (log-product weights, explicit diagonal sums)."""
+    from oracle import propagation as P
+    m = g.rmat_sector_mesh(n, r1, r2)
+    o = P.sector_mesh(n, r1, r2)
+    np.testing.assert_allclose(m["r"], o["r"], rtol=1e-15)
+    np.testing.assert_allclose(m["lam"], o["lam"], rtol=1e-14)
+    for k in ("fL", "fR"):
+        assert np.max(np.abs(m[k] - o[k])) <= 1e-11 * np.max(np.abs(o[k])), k
+    assert np.max(np.abs(m["Kf"] - o["Kf"])) <= 1e-10 * np.max(np.abs(o["Kf"]))
+
+
+def test_sector_mesh_argument_errors(g):
+    d = ct.POINTER(ct.c_double)()
+    assert g.lib().rmat_sector_mesh(1, 0.0, 1.0, d, d, d, d, d) == -1
+    assert g.lib().rmat_sector_mesh(10, 2.0, 2.0, d, d, d, d, d) == -2
+    assert g.lib().rmat_sector_mesh(10, -1.0, 2.0, d, d, d, d, d) == -2
