@@ -76,8 +76,12 @@ def test_propagation_matches_oracle(g, ctx, case, prec):
     U_ref, R_ref, no = P.propagated_collision(p, radii, lambda r: cp.potential_at(p, r))
     R, U, nopen = run_prop(g, ctx, p, radii, prec)
     assert nopen == no
-    assert relerr(R, R_ref) < TOL[prec]
-    assert relerr(U, U_ref) < TOL[prec]
+    # every sector's solution sits at its own FP64 refinement floor (~1e-12 of R),
+    # and the propagation chains ns of them: (ns + 1) x 1e-12 for the FP64 path
+    ns = len(radii) - 1
+    tol = (ns + 1) * 1e-12 if prec == 0 else TOL[prec]
+    assert relerr(R, R_ref) < tol
+    assert relerr(U, U_ref) < tol
 
 
 def test_one_sector_equals_single_system(g, ctx):
