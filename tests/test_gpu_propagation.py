@@ -76,10 +76,11 @@ def test_propagation_matches_oracle(g, ctx, case, prec):
     U_ref, R_ref, no = P.propagated_collision(p, radii, lambda r: cp.potential_at(p, r))
     R, U, nopen = run_prop(g, ctx, p, radii, prec)
     assert nopen == no
-    # every sector's solution sits at its own FP64 refinement floor (~1e-12 of R),
-    # and the propagation chains ns of them: (ns + 1) x 1e-12 for the FP64 path
-    ns = len(radii) - 1
-    tol = (ns + 1) * 1e-12 if prec == 0 else TOL[prec]
+    # every sector's solution sits at its own FP64 refinement floor (~1e-12 of R;
+    # the oracle's sector solves are double-double refined), the propagation chains
+    # ns of them and the matching (closed channels) amplifies: 1e-11 for the FP64
+    # path, ten times the single-system bound; the complex64 paths keep 1e-10
+    tol = 1e-11 if prec == 0 else TOL[prec]
     assert relerr(R, R_ref) < tol
     assert relerr(U, U_ref) < tol
 
