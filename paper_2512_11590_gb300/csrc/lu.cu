@@ -1014,8 +1014,29 @@ apply_inv_kernel(const float2* __restrict__ Dinv, int k0, int nbp, float2* __res
     const unsigned char* sp = reinterpret_cast<const unsigned char*>(D + (size_t)r * JB) + 16 * h;
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(sp) : "memory");
   }
-  asm volatile("cp.async.commit_group;" ::: "memory");
   int cnt = JB;
+  if (!prow && (ldb & 1) == 0 && (ncols & 1) == 0) {
+    // no interchanges to apply: every CTA stages the whole B_k tile (JB rows x CW
+    // columns) straight from global memory, 16 bytes (two columns) per copy
+    const int c0 = blockIdx.x * CW;
+    for (int e = tid; e < JB * (CW / 2); e += 256) {
+      const int t = e / (CW / 2), h2 = 2 * (e % (CW / 2));
+      float2* dst = vk + t * CW + h2;
+      if (c0 + h2 < ncols) {
+        const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+        const float2* sp = B + (size_t)(k0 + t) * ldb + c0 + h2;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(sp) : "memory");
+      } else {
+        dst[0] = make_float2(0.f, 0.f);
+        dst[1] = make_float2(0.f, 0.f);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    cluster.sync();  // every CTA's read of B_k is done before any CTA writes its rows
+  } else {
+  asm volatile("cp.async.commit_group;" ::: "memory");
   if (prow) {
     cnt = pcnt[blk];
     for (int q = tid; q < cnt; q += 256) {
@@ -1044,6 +1065,7 @@ apply_inv_kernel(const float2* __restrict__ Dinv, int k0, int nbp, float2* __res
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   cluster.sync();  // peers may now overwrite B and exit
+  }
   if (prow && act) {
 #pragma unroll
     for (int u = 0; u < SL / 16; ++u) {
