@@ -62,8 +62,11 @@ def test_null_context_arguments(g):
     assert L.rmat_factor(None, None) == -1
     assert L.rmat_solve(None, None, 1, 0, 0.0, None, None) == -1
     assert L.rmat_set_param(None, 1, 64) == -1
+    assert L.rmat_set_param(None, g.RMAT_PARAM_METHOD, 1) == -1
+    assert L.rmat_propagate(None, None, 10.0, 1, None, None, 0, 0.0, None, None, None) == -1
     assert L.rmat_destroy(None) == 0
     assert g.status_string(g.RMAT_ENOCONV).startswith("refinement")
+    assert "Coulomb" in g.status_string(g.RMAT_ECHANFN)
 
 
 def test_no_gpu_fails_loudly(g):
