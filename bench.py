@@ -208,16 +208,17 @@ def time_steps(runner, K, W, sync_all):
     g.rmat_set_param(runner.ctx, g.RMAT_PARAM_TIMING, 0)
     g.rmat_reset_counters(runner.ctx)
     sync_all()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(runner.stream)
-    for _ in range(K):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ev[0].record(runner.stream)
+    for k in range(K):
         runner.step()
-    e1.record(runner.stream)
+        ev[k + 1].record(runner.stream)
     torch.cuda.synchronize()
     sync_all()
     launches = g.rmat_get_stats(runner.ctx)["launches"]
-    return e0.elapsed_time(e1) / K, stats, launches
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
+    stats["ms_steps"] = {"best": min(per), "median": float(np.median(per)), "all": per}
+    return ev[0].elapsed_time(ev[K]) / K, stats, launches
 
 
 def time_e2e(runner, K):
@@ -527,6 +528,54 @@ def propagate_main(args):
     return 0
 
 
+def cpu_lapack_main(args):
+    """Host-core context (the paper's Type 1 and Type 2 on the CPU): SciPy LAPACK
+    complex128 LU + solve (zgetrf/zgetrs) and complex64 LU (cgetrf) + FP64
+    refinement on the config-2 systems at N = 1600 and 6400, threads as the BLAS
+    build provides them.  The matrix is assembled densely from the library's host
+    mesh tables (no GPU)."""
+    import time
+
+    import scipy.linalg as sl
+
+    import cc_problems as cp
+    import paper_2512_11590_gb300 as g
+    rows = []
+    for nch in (16, 64):
+        p = cp.config2(nch)
+        m = g.rmat_mesh(p.nlag, p.a)
+        V = cp.potential_at(p, m["r"])
+        n, L = p.N, p.nlag
+        l = np.asarray(p.l, dtype=np.float64)
+        C = np.zeros((n, n), dtype=np.complex128)
+        for al in range(p.nch):
+            blk = slice(al * L, (al + 1) * L)
+            C[blk, blk] = p.hm * m["T0"]
+            C[blk, blk] += np.diag(p.hm * l[al] * (l[al] + 1) / m["r"] ** 2 + p.thresh[al] - p.E)
+            for be in range(p.nch):
+                C[al * L + np.arange(L), be * L + np.arange(L)] += V[be, al, :]
+        B = np.zeros((n, p.nch), dtype=np.complex128)
+        for al in range(p.nch):
+            B[al * L:(al + 1) * L, al] = m["f_a"]
+        t0 = time.perf_counter()
+        X64 = sl.lu_solve(sl.lu_factor(C, check_finite=False), B, check_finite=False)
+        t1 = time.perf_counter()
+        lu32 = sl.lu_factor(C.astype(np.complex64), check_finite=False)
+        X = sl.lu_solve(lu32, B.astype(np.complex64), check_finite=False).astype(np.complex128)
+        for _ in range(8):
+            r = B - C @ X
+            if np.abs(r).max() / np.abs(B).max() < 1e-13:
+                break
+            X += sl.lu_solve(lu32, r.astype(np.complex64), check_finite=False)
+        t2 = time.perf_counter()
+        rows.append({"N": n, "nrhs": p.nch, "zgesv_s": t1 - t0, "cgetrf_ir_s": t2 - t1,
+                     "x_rel_diff": float(np.abs(X - X64).max() / np.abs(X64).max())})
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"metric": "host-core LAPACK context (Type 1 / Type 2 analogues)",
+                      "cores": len(os.sched_getaffinity(0)), "rows": rows, "data": "synthetic"}))
+    return 0
+
+
 def config5_main(args):
     """Config 5: N = 51200 (nch = 512, nlag = 100), 512 right-hand sides, an energy sweep
     of 8 points reusing the assembly buffers (FP32+IR), and one energy in complex128 for
@@ -583,6 +632,8 @@ def main():
                     help="time the batch driver on this many config-4 systems instead")
     ap.add_argument("--sweep", action="store_true",
                     help="config 2 sweep (N=1600..25600) and config 3b, FP32+IR vs complex128")
+    ap.add_argument("--cpu-lapack", action="store_true",
+                    help="host-core SciPy LAPACK context at N = 1600 and 6400 (no GPU)")
     ap.add_argument("--propagate", action="store_true",
                     help="R-matrix propagation over 4 sectors vs one system (charged, a = 40 fm)")
     ap.add_argument("--config5", action="store_true",
@@ -611,6 +662,8 @@ def main():
         return config5_main(args)
     if args.propagate:
         return propagate_main(args)
+    if args.cpu_lapack:
+        return cpu_lapack_main(args)
 
     import torch
     import paper_2512_11590_gb300 as g
@@ -756,6 +809,8 @@ def main():
                    "method": args.method,
                    "refinement": ir, "l2": "inputs larger than L2 (C is %.1f GB)" % (p.N * p.N * 8 / 1e9),
                    "lu_block": stats["nb"], "panel_ctas": stats["panel_ctas"],
+                   "ms_per_step_best_median": [stats["ms_steps"]["best"],
+                                               stats["ms_steps"]["median"]],
                    "stage_ms": {k: stats[k] for k in ("assemble_ms", "factor_ms", "solve_ms",
                                                        "refine_ms", "collision_ms")},
                    "kernel_ms": {k: [stats.get(k + "_ms"), stats.get(k + "_launches")]
