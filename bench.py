@@ -515,6 +515,18 @@ def propagate_main(args):
         if k >= args.warmup:
             times.append(e0.elapsed_time(e1))
     Up = U.cpu().numpy().reshape(no, no).T
+    g.rmat_set_param(ctx, g.RMAT_PARAM_PROP_CONCURRENT, 0)   # sectors one after the other
+    seq = []
+    for k in range(2):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.rmat_propagate(ctx, prob, p.E, radii, [v.data_ptr() for v in Vs], 30, 1e-13, 0,
+                         U.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq.append(e0.elapsed_time(e1))
     g.rmat_destroy(ctx)
     p1 = cp.charged_problem(26, 64, 4 * nlag, 30.0, a=a)
     one = solve_once(p1, prec, warm=True)[0]
@@ -522,6 +534,7 @@ def propagate_main(args):
     print(json.dumps({"metric": "R-matrix propagation: 4 sectors of N=6400 vs one system of N=25600 "
                                 "to a = 40 fm (charged, nch = 64)",
                       "unit": "ms", "propagation_ms": float(np.median(times)),
+                      "propagation_sequential_ms": float(seq[-1]),
                       "single_system_ms": one["ms"], "single_system_iters": one["iters"],
                       "speedup": one["ms"] / float(np.median(times)), "u_rel_diff": rd,
                       "sectors": ns, "nlag_per_sector": nlag, "status": st, "data": "synthetic"}))

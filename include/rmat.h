@@ -106,6 +106,12 @@ extern "C" {
  * (the concurrent reduce-adds make the rounding order, and so the last bits, vary
  * from run to run); 0 (default) = one update per block. */
 #define RMAT_PARAM_SOLVE_LOOKAHEAD 9
+/* rmat_propagate: 1 (default) = when every panel of a sector system fits one
+ * thread-block cluster, sectors 2..ns are solved concurrently on worker contexts
+ * (each with its own stream and host thread, kept in the context for later calls)
+ * while sector 1 runs on the context itself; the propagation steps then run in
+ * order.  0 = sectors one after the other.  Results are identical. */
+#define RMAT_PARAM_PROP_CONCURRENT 10
 
 typedef struct rmat_ctx_s* rmat_ctx;
 

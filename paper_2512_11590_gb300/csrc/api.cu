@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "cplx.cuh"
@@ -281,6 +282,9 @@ int rmat_destroy(rmat_ctx c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   if (c->sg_exec) cudaGraphExecDestroy(c->sg_exec);
+  for (rmat_ctx w : c->prop_workers) rmat_destroy(w);
+  for (cudaStream_t s : c->prop_streams)
+    if (s) cudaStreamDestroy(s);
   if (c->side) cudaStreamSynchronize(c->side);
   for (cudaEvent_t e : c->la_ev)
     if (e) cudaEventDestroy(e);
@@ -339,6 +343,10 @@ int rmat_set_param(rmat_ctx c, int key, long long v) {
     case RMAT_PARAM_SOLVE_LOOKAHEAD:
       if (v < 0 || v > 1) return -3;
       c->solve_lookahead = (int)v;
+      return RMAT_OK;
+    case RMAT_PARAM_PROP_CONCURRENT:
+      if (v < 0 || v > 1) return -3;
+      c->prop_concurrent = (int)v;
       return RMAT_OK;
     default:
       return -2;
@@ -724,6 +732,53 @@ int rmat_collision(rmat_ctx c, void* R_dev, void* U_dev, int* nopen) {
   return RMAT_OK;
 }
 
+}  // extern "C"
+
+// One propagation sector (r1, r2) on context w: assemble, factor, solve and refine,
+// then its four g blocks into G.  Synchronises w's stream.  *st: RMAT_OK or ENOCONV.
+static int sector_pipeline(rmat_ctx w, const rmat_problem* pb, double E, const void* V,
+                           double r1, double r2, int max_refine, double tol, double2* G,
+                           int* st) {
+  RMAT_CHECK(assemble_impl(w, pb, E, V, r1, r2));
+  int info = 0;
+  RMAT_CHECK(rmat_factor(w, &info));
+  int it = 0;
+  double rel = 0.0;
+  RMAT_CHECK(solve_refine(w, max_refine, tol, &it, &rel, st));
+  RMAT_CHECK(launch_sector_g(w, G));
+  RMAT_CHECK(read_status(w));
+  if (w->hstat[ST_TIMEOUT]) return RMAT_ETIMEOUT;
+  if (w->hstat[ST_INFO]) return RMAT_ESINGULAR;
+  return RMAT_OK;
+}
+
+// Worker contexts for concurrent sectors (created once, kept in c).
+static int prop_workers(rmat_ctx c, int n) {
+  while ((int)c->prop_workers.size() < n) {
+    cudaStream_t s = nullptr;
+    RMAT_CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    c->prop_streams.push_back(s);
+    rmat_ctx w = nullptr;
+    RMAT_CHECK(rmat_create(&w, c->device, s));
+    c->prop_workers.push_back(w);
+  }
+  for (int k = 0; k < n; ++k) {  // the caller's settings, without the options that need
+    rmat_ctx w = c->prop_workers[k];  // the whole GPU or change the matrix
+    w->nb_param = c->nb_param;
+    w->spin_limit = c->spin_limit;
+    w->equil_param = c->equil_param;
+    w->paired = c->paired;
+    w->refine_param = c->refine_param;
+    w->panel_ctas_param = 0;
+    w->method_param = 0;
+    w->solve_lookahead = 0;
+    w->timing = 0;
+  }
+  return RMAT_OK;
+}
+
+extern "C" {
+
 int rmat_sector_mesh(int nlag, double r1, double r2, double* r, double* lam, double* fL,
                      double* fR, double* Kf) {
   return rmat_sector_mesh_host(nlag, r1, r2, r, lam, fL, fR, Kf);
@@ -749,6 +804,22 @@ int rmat_propagate(rmat_ctx c, const rmat_problem* pb, double E, int ns, const d
   const int no = (int)open.size();
   if (nopen) *nopen = no;
   if (no > 0 && !U_dev) return -6;
+  // With the default block width too wide for a cluster panel, the concurrent
+  // mode uses width 64 (as batch lanes do) for every sector, sector 1 included.
+  const int Ns = nch * pb->nlag;
+  int nbq = clamp_nb(pb->precision, c->nb_param ? c->nb_param : default_nb(pb->precision, Ns));
+  bool fits = panel_cluster_fits(c, pb->precision, Ns, nbq) > 0;
+  if (!fits && !c->nb_param && nbq > 64 && panel_cluster_fits(c, pb->precision, Ns, 64) > 0) {
+    nbq = 64;
+    fits = true;
+  }
+  const bool conc = ns >= 2 && c->prop_concurrent && c->panel_ctas_param <= 0 && fits;
+  struct NbRestore {  // the caller's block-width setting comes back on every return
+    rmat_ctx c;
+    int v;
+    ~NbRestore() { c->nb_param = v; }
+  } nb_restore{c, c->nb_param};
+  if (conc) c->nb_param = nbq;
   // sector 1: the regular mesh on (0, a_1); Rl = a_1 R(a_1) = hm Phi^T X
   rmat_problem p0 = *pb;
   p0.a = radii[1];
@@ -768,14 +839,45 @@ int rmat_propagate(rmat_ctx c, const rmat_problem* pb, double E, int ns, const d
     if (st != RMAT_OK) status = st;
     return RMAT_OK;
   };
-  RMAT_CHECK(factor_solve());
-  RMAT_CHECK(launch_sector_g(c, Rl));
+  // Sectors are independent systems until the propagation steps.  When every
+  // panel of a sector fits one thread-block cluster (no cooperative grid kernel
+  // that needs every SM), sectors 2..ns run concurrently on worker contexts, each
+  // from its own host thread, while sector 1 runs here.
+  std::vector<int> wrc(ns + 1, RMAT_OK), wst(ns + 1, RMAT_OK);
+  std::vector<std::thread> threads;
+  if (conc) {
+    RMAT_CHECK(prop_workers(c, ns - 1));
+    for (int s = 2; s <= ns; ++s) {
+      rmat_ctx w = c->prop_workers[s - 2];
+      int r = rmat_grow(w, &w->prop, &w->prop_cap, 4 * blk * sizeof(double2));
+      if (r != RMAT_OK) {
+        wrc[s] = r;
+        continue;
+      }
+      threads.emplace_back([&, s, w]() {
+        cudaSetDevice(c->device);
+        wrc[s] = sector_pipeline(w, pb, E, V_dev[s - 1], radii[s - 1], radii[s], max_refine,
+                                 tol, reinterpret_cast<double2*>(w->prop), &wst[s]);
+      });
+    }
+  }
+  const int rc1 = factor_solve();
+  const int rc2 = rc1 == RMAT_OK ? launch_sector_g(c, Rl) : rc1;
+  for (std::thread& t : threads) t.join();
+  RMAT_CHECK(rc2);
   for (int s = 2; s <= ns; ++s) {
-    RMAT_CHECK(assemble_impl(c, pb, E, V_dev[s - 1], radii[s - 1], radii[s]));
-    RMAT_CHECK(factor_solve());
-    RMAT_CHECK(launch_sector_g(c, G));
+    double2* Gs = G;
+    if (conc) {
+      RMAT_CHECK(wrc[s]);
+      if (wst[s] != RMAT_OK) status = wst[s];
+      Gs = reinterpret_cast<double2*>(c->prop_workers[s - 2]->prop);
+    } else {
+      RMAT_CHECK(assemble_impl(c, pb, E, V_dev[s - 1], radii[s - 1], radii[s]));
+      RMAT_CHECK(factor_solve());
+      RMAT_CHECK(launch_sector_g(c, G));
+    }
     // Rl <- g_RR - g_RL (Rl + g_LL)^-1 g_LR  (FP64 LU of the nch x nch matrix)
-    RMAT_CHECK(launch_prop_step(c, Rl, G, P));
+    RMAT_CHECK(launch_prop_step(c, Rl, Gs, P));
   }
   // R(a) = Rl / a and U at a = a_ns
   c->a = radii[ns];

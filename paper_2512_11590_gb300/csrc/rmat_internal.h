@@ -80,6 +80,10 @@ struct rmat_ctx_s {
   double mesh_r1 = -1.0;   // left end of the mesh the tables belong to (-1: regular (0, a))
   double* faL = nullptr;   size_t faL_cap = 0;
   void* prop = nullptr;    size_t prop_cap = 0;     // Rl, the four g blocks, scratch (nch^2 each)
+  // sectors s >= 2 solved concurrently on worker contexts (own stream, own host thread)
+  int prop_concurrent = 1;                // RMAT_PARAM_PROP_CONCURRENT
+  std::vector<rmat_ctx> prop_workers;
+  std::vector<cudaStream_t> prop_streams;
   // RMAT_PARAM_REFINE: 0 classical refinement, m > 0 FGMRES-IR with <= m inner steps
   int refine_param = 0;
   long long gm_inner = 0;  // FGMRES inner steps of the last rmat_solve

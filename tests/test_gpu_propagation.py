@@ -114,3 +114,18 @@ def test_propagation_argument_errors(g, ctx):
     with pytest.raises(g.RmatError) as ei:                 # no solved single system left
         g.rmat_collision(ctx, R.data_ptr(), U.data_ptr())
     assert ei.value.status == g.RMAT_ESTATE
+
+
+@pytest.mark.parametrize("prec", [3, 0])
+def test_concurrent_sectors_equal_sequential(g, ctx, prec):
+    """Sectors on worker contexts (own streams and host threads) give the same R
+    and U as one after the other on the caller's context."""
+    p = cp.charged_problem(27, 4, 48, 25.0)
+    radii = [0.0, 6.0, 12.0, 18.0, 24.0]
+    g.rmat_set_param(ctx, g.RMAT_PARAM_PROP_CONCURRENT, 0)
+    R0, U0, _ = run_prop(g, ctx, p, radii, prec)
+    g.rmat_set_param(ctx, g.RMAT_PARAM_PROP_CONCURRENT, 1)
+    R1, U1, _ = run_prop(g, ctx, p, radii, prec)
+    R2, U2, _ = run_prop(g, ctx, p, radii, prec)          # workers reused
+    assert relerr(U1, U0) < 1e-14 and relerr(R1, R0) < 1e-14
+    assert relerr(U2, U1) < 1e-14
