@@ -110,7 +110,9 @@ extern "C" {
  * thread-block cluster, sectors 2..ns are solved concurrently on worker contexts
  * (each with its own stream and host thread, kept in the context for later calls)
  * while sector 1 runs on the context itself; the propagation steps then run in
- * order.  0 = sectors one after the other.  Results are identical. */
+ * order.  With RMAT_PARAM_NB = 0 and a default block width too wide for a cluster
+ * panel, every sector then uses width 64.  0 = sectors one after the other.
+ * Results agree to rounding (identical when the block width is the same). */
 #define RMAT_PARAM_PROP_CONCURRENT 10
 
 typedef struct rmat_ctx_s* rmat_ctx;
