@@ -106,3 +106,83 @@ def structured_residual(p, V, X, Phi=None, mesh=None, T0=None):
     """r = Phi - C X with C applied through its block structure (complex128)."""
     B = Phi if Phi is not None else surface_rhs(p, mesh)
     return B - structured_apply(p, V, X, mesh, T0)
+
+
+def channel_blocks(p, V, mesh=None, T0=None) -> np.ndarray:
+    """Kb[al] = the diagonal channel block C[(al,.),(al,.)] of the dense C, (nch, nlag, nlag).
+
+    Entry for entry the numbers assemble_dense stores: hm T0 - hm (B/a) f f^T
+    off the diagonal, fl(K_ii + fl(d_al,i + V_alal(r_i))) on it."""
+    nch, nlag = p.nch, p.nlag
+    m = mesh if mesh is not None else lagrange_mesh(nlag, p.a)
+    T = T0 if T0 is not None else kinetic_bloch(nlag, p.a, m)
+    f_a = m["f_a"]
+    K = p.hm * T - p.hm * (p.bloch_B / p.a) * np.outer(f_a, f_a)
+    d = channel_diagonal(p, m)
+    Kb = np.broadcast_to(K.astype(np.complex128), (nch, nlag, nlag)).copy()
+    ii = np.arange(nlag)
+    for al in range(nch):
+        Kb[al, ii, ii] = K[ii, ii] + (d[al] + V[al, al, :])
+    return Kb
+
+
+def structured_residual_dd(p, V, X, Phi=None, mesh=None, T0=None):
+    """r = Phi - C X with C applied through its block structure, every product and
+    every sum of C X accumulated in double-double (oracle.ddarith), rounded once.
+
+    The structure is that of Eq. (block_structure) (Sec. 2): per row (al, i)
+      (C X)[(al,i),be] = sum_j Kb[al][i,j] X[(al,j),be]
+                       + sum_{al' != al} V_{al al'}(r_i) X[(al',i),be],
+    Kb the diagonal channel blocks exactly as the dense C stores them
+    (channel_blocks).  This is the residual of the paper's refinement (Sec. 3.2,
+    Sec. 3.4 step 7) in extended precision, for the "truth" solution at sizes
+    where the dense double-double residual (ddarith.dd_residual, O(N^2 nrhs)
+    Python-level work) is out of reach.  Columns are independent: callers may
+    evaluate any subset of columns of X (and Phi) separately.
+
+    Pins (tests/test_oracle_system.py): equals ddarith.dd_residual of the dense C
+    (itself pinned to exact rational arithmetic) to the last bit, and a dropped
+    coupling or kinetic term is caught.
+    """
+    from .ddarith import dd_add, two_prod
+    nch, nlag = p.nch, p.nlag
+    m = mesh if mesh is not None else lagrange_mesh(nlag, p.a)
+    B = Phi if Phi is not None else surface_rhs(p, m)
+    nrhs = X.shape[1]
+    X3 = X.reshape(nch, nlag, nrhs)
+    Xr, Xi = np.ascontiguousarray(X3.real), np.ascontiguousarray(X3.imag)
+    Kb = channel_blocks(p, V, m, T0)
+    shape = (nch, nlag, nrhs)
+    hr, lr = np.zeros(shape), np.zeros(shape)
+    hi, li = np.zeros(shape), np.zeros(shape)
+
+    def acc(h, l, a, b, sign):
+        s, e = two_prod(a, b)
+        return dd_add(h, l, sign * s, sign * e)
+
+    # channel blocks: sum over j of Kb[al][i, j] X[(al, j), be]
+    for j in range(nlag):
+        kr = Kb[:, :, j].real[:, :, None]                 # [al, i, 1]
+        ki = Kb[:, :, j].imag[:, :, None]
+        xr = Xr[:, j, :][:, None, :]                      # [al, 1, be]
+        xi = Xi[:, j, :][:, None, :]
+        hr, lr = acc(hr, lr, kr, xr, 1.0)
+        hr, lr = acc(hr, lr, ki, xi, -1.0)
+        hi, li = acc(hi, li, kr, xi, 1.0)
+        hi, li = acc(hi, li, ki, xr, 1.0)
+    # point couplings: sum over al' != al of V_{al al'}(r_i) X[(al', i), be]
+    for alp in range(nch):
+        w = V[alp, :, :].copy()                            # [al, i] = V_{al alp}(r_i)
+        w[alp, :] = 0.0                                    # al' = al sits in Kb's diagonal
+        wr = w.real[:, :, None]
+        wi = w.imag[:, :, None]
+        xr = Xr[alp][None, :, :]                           # [1, i, be]
+        xi = Xi[alp][None, :, :]
+        hr, lr = acc(hr, lr, wr, xr, 1.0)
+        hr, lr = acc(hr, lr, wi, xi, -1.0)
+        hi, li = acc(hi, li, wr, xi, 1.0)
+        hi, li = acc(hi, li, wi, xr, 1.0)
+    B3 = B.reshape(nch, nlag, nrhs)
+    rr_h, rr_l = dd_add(B3.real, np.zeros(shape), -hr, -lr)
+    ri_h, ri_l = dd_add(B3.imag, np.zeros(shape), -hi, -li)
+    return ((rr_h + rr_l) + 1j * (ri_h + ri_l)).reshape(X.shape)

@@ -28,3 +28,21 @@ def test_refinement_reaches_double_precision(kappa):
     assert e_ref < 3e-16                        # correctly rounded to within ~1 ulp
     assert e_plain > 10 * e_ref                 # plain LU is kappa-limited
     assert hist[-1] < 1e-15
+
+
+def test_structured_truth_equals_dense_truth():
+    """LAPACK factors + structured double-double residual reach the same solution as
+    the oracle's own LU + dense double-double residual."""
+    from oracle import mesh as M
+    from oracle import system as S
+    from oracle.refine import truth_solve_structured
+    p = cp.make_problem(31, 8, 40, 9.0, W=-1.0)
+    m = M.lagrange_mesh(p.nlag, p.a)
+    V = cp.potential_at(p, m["r"])
+    C, Phi = S.assemble_dense(p, V, m)
+    X_ref, _ = truth_solve(C, Phi, steps=3)
+    X, hist, Phi2 = truth_solve_structured(p, V, m, steps=2)
+    assert np.array_equal(Phi, Phi2)
+    assert np.max(np.abs(X - X_ref)) / np.max(np.abs(X_ref)) < 1e-15
+    # r of the rounded solution is u |C||X|, not 0: the history only has to level off
+    assert max(hist) < 1e-12
