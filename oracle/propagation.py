@@ -117,15 +117,17 @@ def sector_matrix(p, V: np.ndarray, sm: dict) -> np.ndarray:
     return C
 
 
-def sector_green(p, V: np.ndarray, sm: dict):
-    """(g_LL, g_LR, g_RL, g_RR), g_ab = hm phi_a^T C^-1 phi_b, nch x nch."""
+def sector_green(p, V: np.ndarray, sm: dict, refine_steps: int = 2):
+    """(g_LL, g_LR, g_RL, g_RR), g_ab = hm phi_a^T C^-1 phi_b, nch x nch.
+
+    refine_steps = 0 gives the plain FP64 LU solve (no refinement)."""
     nch, n = p.nch, sm["r"].size
     C = sector_matrix(p, V, sm)
     Phi = np.zeros((nch * n, 2 * nch), dtype=np.complex128)
     for al in range(nch):
         Phi[al * n:(al + 1) * n, al] = sm["fL"]
         Phi[al * n:(al + 1) * n, nch + al] = sm["fR"]
-    X, _ = truth_solve(C, Phi, steps=2)
+    X, _ = truth_solve(C, Phi, steps=refine_steps)
     G = p.hm * (Phi.T @ X)
     return G[:nch, :nch], G[:nch, nch:], G[nch:, :nch], G[nch:, nch:]
 
@@ -136,10 +138,12 @@ def propagate(Rl: np.ndarray, g) -> np.ndarray:
     return gRR - gRL @ solve(Rl + gLL, gLR)
 
 
-def propagated_collision(p, radii, potential):
+def propagated_collision(p, radii, potential, refine_steps: int = 2):
     """U (and R at a = radii[-1]) with sectors (radii[s-1], radii[s]), nlag points each.
 
-    potential(r) -> V array [c2, c1, i] at radii r (cc_problems.potential_at layout)."""
+    potential(r) -> V array [c2, c1, i] at radii r (cc_problems.potential_at layout).
+    refine_steps: double-double refinement steps of every sector solve (2: the truth;
+    0: plain FP64 LU solves, which measures the FP64 floor of the propagated R, U)."""
     import copy
     radii = [float(v) for v in radii]
     q = copy.copy(p)
@@ -147,11 +151,11 @@ def propagated_collision(p, radii, potential):
     m = lagrange_mesh(p.nlag, q.a)
     T0 = kinetic_bloch(p.nlag, q.a, m)
     C, Phi = assemble_dense(q, potential(m["r"]), m, T0)
-    X, _ = truth_solve(C, Phi, steps=2)
+    X, _ = truth_solve(C, Phi, steps=refine_steps)
     Rl = p.hm * (Phi.T @ X)                      # = a_1 R(a_1)
     for s in range(2, len(radii)):
         sm = sector_mesh(p.nlag, radii[s - 1], radii[s])
-        Rl = propagate(Rl, sector_green(p, potential(sm["r"]), sm))
+        Rl = propagate(Rl, sector_green(p, potential(sm["r"]), sm, refine_steps))
     q.a = radii[-1]
     R = Rl / q.a
     U, nopen = collision_matrix(q, R)

@@ -68,6 +68,16 @@ def _closed():
     return p
 
 
+def fp64_floor(p, radii):
+    """Error of the propagated R and U when every sector is solved by a plain FP64
+    LU (oracle, no refinement) against the double-double-refined truth: the FP64
+    floor of the chained propagation and matching on this case."""
+    pot = lambda r: cp.potential_at(p, r)  # noqa: E731
+    U_t, R_t, _ = P.propagated_collision(p, radii, pot)
+    U_0, R_0, _ = P.propagated_collision(p, radii, pot, refine_steps=0)
+    return relerr(R_0, R_t), relerr(U_0, U_t)
+
+
 @pytest.mark.parametrize("prec", [0, 3, 1])
 @pytest.mark.parametrize("case", list(CASES))
 def test_propagation_matches_oracle(g, ctx, case, prec):
@@ -76,13 +86,20 @@ def test_propagation_matches_oracle(g, ctx, case, prec):
     U_ref, R_ref, no = P.propagated_collision(p, radii, lambda r: cp.potential_at(p, r))
     R, U, nopen = run_prop(g, ctx, p, radii, prec)
     assert nopen == no
-    # every sector's solution sits at its own FP64 refinement floor (~1e-12 of R;
-    # the oracle's sector solves are double-double refined), the propagation chains
-    # ns of them and the matching (closed channels) amplifies: 1e-11 for the FP64
-    # path, ten times the single-system bound; the complex64 paths keep 1e-10
-    tol = 1e-11 if prec == 0 else TOL[prec]
-    assert relerr(R, R_ref) < tol
-    assert relerr(U, U_ref) < tol
+    eR, eU = relerr(R, R_ref), relerr(U, U_ref)
+    if prec == 0:
+        # FP64 path: each sector refined to its FP64 floor, then ns - 1 FP64 propagation
+        # steps and the matching, whose rounding no refinement removes.  The bound is
+        # twice the error of the same chain with plain FP64 LU sector solves (measured
+        # by the oracle on this case: R 6e-13..2.2e-12, U 1.5e-12..2.3e-12), and never
+        # below the single-system 1e-12
+        fR, fU = fp64_floor(p, radii)
+        print(f"{case} FP64: R {eR:.2e} (floor {fR:.2e}), U {eU:.2e} (floor {fU:.2e})")
+        assert eR < max(1e-12, 2.0 * fR)
+        assert eU < max(1e-12, 2.0 * fU)
+    else:
+        assert eR < TOL[prec]
+        assert eU < TOL[prec]
 
 
 def test_one_sector_equals_single_system(g, ctx):
