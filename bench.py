@@ -38,6 +38,7 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 TF32_PER_BF16 = 0.5          # nominal dense tf32 : bf16 tensor rate on GB300 (1.1 : 2.25 PF)
 DTYPES = {1: "c64 factor with 3xTF32 tensor updates / f64 refinement",
+          4: "c64 factor with 1xFP16 (scaled) tensor updates / f64 GMRES-IR",
           2: "c64 factor with FP32 CUDA-core updates / f64 refinement",
           3: "c64 factor with 3xFP16 (scaled split) tensor updates / f64 refinement",
           0: "c128 throughout (FP64 tensor-instruction GEMMs, FP64 refinement)"}
@@ -90,6 +91,78 @@ def paired_update_bytes(N, nb, plane_bytes):
 
 def lu_flops(N, nrhs):
     return 8.0 / 3.0 * N ** 3 + 8.0 * N ** 2 * nrhs
+
+
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (no measured FP64 peak in MEASURED_PEAKS.json)
+
+
+def profile_ratio(name):
+    """DRAM bytes per algorithmic byte of one captured launch, from the summary's
+    `dram_per_algorithmic_byte:` line under profiles/ (None if absent)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            for line in f:
+                if line.startswith("dram_per_algorithmic_byte:"):
+                    return float(line.split(":")[1].split()[0])
+    except OSError:
+        pass
+    return None
+
+
+def truth_errors(W, results):
+    """max|delta|/max|truth| of X, R, U over the stored samples of the oracle's
+    N = 25600 truth (tests/golden/truth_config3_W*_n25600.txt)."""
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    try:
+        from make_truth_n25600 import load_truth, sampled_relerr, truth_file
+        if not os.path.exists(truth_file(W)):
+            return None
+        t = load_truth(W)
+    except Exception as e:  # the stored samples are optional context
+        return {"unavailable": str(e)}
+    out = {"source": os.path.relpath(truth_file(W), ROOT)}
+    for key, (X, R, U) in results.items():
+        if X is None:
+            continue
+        out[key] = {"X": sampled_relerr(X, t, "X"), "R": sampled_relerr(R, t, "R"),
+                    "U": sampled_relerr(U, t, "U")}
+    return out
+
+
+def stage_rooflines(stats, N, nch, nb, iters, pk, src):
+    """Where the rest of the step goes: per-class algorithmic work over CUDA-event time."""
+    out = {}
+    ms, n = stats.get("panel_ms"), stats.get("panel_launches")
+    if ms and ms > 0:
+        out["panel"] = {"bound": "latency", "ms": ms, "launches": n,
+                        "us_per_column": ms * 1e3 / N,
+                        "hbm_gbs": 16.0 * N * N / 2 / (ms * 1e-3) / 1e9,
+                        "note": "one grid-wide pivot search per column; bytes = each panel read "
+                                "and written once (8 N^2 in total), far below the HBM roof"}
+    solves = 1 + int(iters)
+    ms = stats.get("solve_tc_ms")
+    if ms and ms > 0:
+        fl = solves * 8.0 * nch * N * (N - nb)
+        peak = pk["bf16_tflops_sustained"] / 3.0
+        out["solve_tc"] = {"bound": "tensor", "ms": ms, "launches": stats.get("solve_tc_launches"),
+                           "achieved_tflops": fl / (ms * 1e-3) / 1e12, "peak": peak,
+                           "frac": fl / (ms * 1e-3) / 1e12 / peak,
+                           "flops": "%d solves x 8 nrhs N (N - nb) (off-diagonal block updates)" % solves}
+    ms = stats.get("apply_inv_ms")
+    if ms and ms > 0:
+        out["apply_inv"] = {"bound": "latency", "ms": ms, "launches": stats.get("apply_inv_launches"),
+                            "us_per_launch": ms * 1e3 / max(1.0, stats.get("apply_inv_launches") or 1),
+                            "note": "one diagonal block x nrhs per launch (solves and the factor's U12)"}
+    ms, n = stats.get("resid_ms"), stats.get("resid_launches")
+    if ms and ms > 0 and n:
+        nlag = N // nch
+        fl = n * (4.0 * nlag * nlag * nch * nch + 8.0 * nch * nch * nlag * nch)
+        out["fp64_residual"] = {"bound": "fp64", "ms": ms, "evaluations": n,
+                                "achieved_tflops": fl / (ms * 1e-3) / 1e12,
+                                "peak": FP64_NOMINAL_TFLOPS,
+                                "frac": fl / (ms * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS,
+                                "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
+    return out
 
 
 class ClockSampler:
@@ -149,7 +222,7 @@ def workload(args):
 class Runner:
     """One system on one GPU through the C ABI (device-resident buffers)."""
 
-    def __init__(self, p, precision, device, method=0, lookahead=0):
+    def __init__(self, p, precision, device, method=0, lookahead=0, residual=0):
         import torch
 
         import cc_problems as cp
@@ -159,6 +232,7 @@ class Runner:
         self.ctx = g.rmat_create(device, self.stream.cuda_stream)
         g.rmat_set_param(self.ctx, g.RMAT_PARAM_METHOD, method)
         g.rmat_set_param(self.ctx, g.RMAT_PARAM_SOLVE_LOOKAHEAD, lookahead)
+        g.rmat_set_param(self.ctx, g.RMAT_PARAM_RESIDUAL, residual)
         m = g.rmat_mesh(p.nlag, p.a)
         self.V_host = cp.potential_at(p, m["r"]).ravel()
         self.Vd = torch.from_numpy(self.V_host).cuda()
@@ -244,48 +318,82 @@ def time_e2e(runner, K):
     return e0.elapsed_time(e1) / K, h2d, d2h
 
 
-def cpu_baseline(budget_s=20.0):
-    """The CPU oracle (as it stands) on N=1600 systems of the same family."""
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+def _oracle_job(nch):
+    """One oracle solve of the config-3 family at nch x nlag=100 (worker process)."""
     import cc_problems as cp
     from oracle import oracle_solve
-    p = cp.config3(16)
     t0 = time.perf_counter()
-    n = 0
-    while True:
-        oracle_solve(p, refine_steps=3)
-        n += 1
-        if time.perf_counter() - t0 > budget_s or n >= 3:
-            break
-    dt = (time.perf_counter() - t0) / n
-    return {"value": lu_flops(p.N, p.nch) / dt / 1e12, "unit": "TFLOP/s", "cores": 1,
-            "kind": "oracle", "sample": f"{n} oracle solve(s) of config3 nch=16 nlag=100 "
-            f"(N=1600, 16 rhs): LU + 3 double-double refinement steps + R + U; "
-            f"{dt:.2f} s each"}
+    oracle_solve(cp.config3(nch), refine_steps=3)
+    return time.perf_counter() - t0
+
+
+def oracle_pool(cores):
+    """Spawned worker processes for the oracle, one BLAS thread each (the oracle's
+    elementwise NumPy work runs on one core per process)."""
+    import multiprocessing as mp
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["OMP_NUM_THREADS"] = "1"
+    return mp.get_context("spawn").Pool(cores)
+
+
+def oracle_round(pool, cores, nch):
+    """`cores` independent oracle solves at once; returns (TFLOP/s of the round, wall s)."""
+    import cc_problems as cp
+    p = cp.config3(nch)
+    t0 = time.perf_counter()
+    pool.map(_oracle_job, [nch] * cores)
+    wall = time.perf_counter() - t0
+    return cores * lu_flops(p.N, p.nch) / wall / 1e12, wall
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def cpu_baseline(nch=8):
+    """The CPU oracle (as it stands) on all host cores: one process per core, each
+    solving one system of the same family at N = nch*100 (a bounded sample of the
+    N = 25600 workload; LU + 3 double-double refinement steps + R + U)."""
+    cores = host_cores()
+    with oracle_pool(cores) as pool:
+        pool.map(_oracle_job, [2] * cores)        # start-up and imports outside the sample
+        val, wall = oracle_round(pool, cores, nch)
+    return {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} concurrent oracle solves (one per core) of config3 nch={nch} "
+                      f"nlag=100 (N={nch * 100}, {nch} rhs): LU + 3 double-double refinement "
+                      f"steps + R + U; {wall:.1f} s wall"}
 
 
 def reference_main(args):
+    """The reference arm: the CPU oracle on the host cores, each step one round of
+    concurrent oracle solves (one per core) at N = 400 of the workload's family."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    _, desc = workload(args)
+    nch = 4
+    cores = host_cores()
+    with oracle_pool(cores) as pool:
+        for _ in range(args.warmup):
+            oracle_round(pool, cores, nch)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle_round(pool, cores, nch)
+        dt = (time.perf_counter() - t0) / args.steps
     import cc_problems as cp
-    from oracle import oracle_solve
-    p = cp.config3(16)
-    for _ in range(args.warmup):
-        oracle_solve(p, refine_steps=3)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_solve(p, refine_steps=3)
-    dt = (time.perf_counter() - t0) / args.steps
-    val = lu_flops(p.N, p.nch) / dt / 1e12
+    p = cp.config3(nch)
+    val = cores * lu_flops(p.N, p.nch) / dt / 1e12
+    sample = (f"per step {cores} concurrent oracle solves (one per core) of config3 nch={nch} "
+              f"nlag=100 (N={p.N}, {nch} rhs): LU + 3 double-double refinement steps + R + U")
     line = {"impl": "reference", "metric": "N=25600 complex solve time & TFLOP/s: FP32+IR vs FP64 "
             "at equal U error", "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": desc, "sample": "config3 nch=16 nlag=100 N=1600"},
-            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step one oracle solve of config3 nch=16 nlag=100 (N=1600)"},
+            "data": "synthetic",
+            "config": {"workload": f"config3 nch={nch} nlag=100 N={p.N} E=10 MeV seed 11592 "
+                                   f"(bounded CPU sample of the N=25600 workload's family)",
+                       "sample": sample},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -313,16 +421,21 @@ def profile_step(nch, precision, warm=True, method=0):
 
 def batch_main(args):
     """Config 4: 512 independent systems of uneven size (N = 80 .. 6400) through
-    the batch driver (tuned lanes + CUDA graph), against a loop of single-system
+    the batch driver (tuned plan + CUDA graph), against a loop of single-system
     calls on the same inputs.  Prints one JSON line (systems/s)."""
+    print(json.dumps(batch_run(args, args.batch, args.steps, args.warmup, args.precision)))
+    return 0
+
+
+def batch_run(args, nsys, steps, warmup, precision):
     import torch
 
     import cc_problems as cp
     import paper_2512_11590_gb300 as g
     torch.cuda.set_device(0)
-    probs = cp.batch_problems(args.batch)
+    probs = cp.batch_problems(nsys)
     prec = {"tf32": g.RMAT_C64_3XTF32_IR, "f16": g.RMAT_C64_3XF16_IR,
-            "simt": g.RMAT_C64_SIMT_IR, "c128": g.RMAT_C128}[args.precision]
+            "simt": g.RMAT_C64_SIMT_IR, "c128": g.RMAT_C128}[precision]
     stream = torch.cuda.Stream()                 # capturable stream for the batch's CUDA graph
     ctx = g.rmat_create(0, stream.cuda_stream)
     Vs, structs, keep = [], [], []
@@ -346,18 +459,18 @@ def batch_main(args):
     else:
         lanes, split = g.rmat_batch_tune(b, Uptr)
     tune_s = time.perf_counter() - t0
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         g.rmat_batch_run(b, Uptr)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             st, it = g.rmat_batch_run(b, Uptr)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     info = g.rmat_batch_info(b)
     Ub = [u.cpu().numpy() for u in Us]
     g.rmat_batch_destroy(b)
@@ -385,21 +498,22 @@ def batch_main(args):
     flops = float(sum(lu_flops(p.N, p.nch) for p in probs))
     line = {"metric": "batched systems/s (config 4: %d uneven systems)" % len(probs),
             "value": len(probs) / (ms * 1e-3), "unit": "systems/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES.get(prec, "c128"),
             "data": "synthetic",
             "config": {"workload": "config4 batch_problems(%d) seed 11593, N %d..%d, median %d"
                        % (len(probs), Ns.min(), Ns.max(), int(np.median(Ns))),
                        "lanes": lanes, "split_n": split, "graph": info.get("graph"),
+                       "plan": {k: info.get(k) for k in ("small_systems", "small_n", "nb_lane",
+                                                         "nb_serial", "tc_bn_lane")},
                        "tune_s": tune_s, "max_refine": args.batch_refine},
             "tflops": flops / (ms * 1e-3) / 1e12,
             "loop": {"ms_per_step": ms_loop, "systems_per_s": len(probs) / (ms_loop * 1e-3),
                      "speedup_batch_over_loop": ms_loop / ms, "u_rel_diff_batch_vs_loop": diff},
             "statuses": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
             "refine_steps_max": int(max(it)), "clocks": clk.summary()}
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def solve_once(p, precision, device=0, warm=False, energies=None, method=0, refine=0):
@@ -625,11 +739,18 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f16", choices=["f16", "tf32", "simt", "c128"],
+    ap.add_argument("--precision", default="f16", choices=["f16", "f16x1", "tf32", "simt", "c128"],
                     help="c128 only with --batch")
     ap.add_argument("--small", action="store_true", help="N=1600 instead of N=25600")
     ap.add_argument("--no-fp64", action="store_true", help="skip the complex128 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-tf32", action="store_true", help="skip the 3xTF32 comparison leg")
+    ap.add_argument("--residual", default="auto", choices=["auto", "fp64mma", "tensor"],
+                    help="point-coupling product of the FP64 residual (RMAT_PARAM_RESIDUAL)")
+    ap.add_argument("--refine", type=int, default=0,
+                    help="GMRES-IR inner steps per correction (RMAT_PARAM_REFINE; 0 classical)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the config-4 batch leg (512 systems) of the default line")
     ap.add_argument("--method", default="direct", choices=["direct", "woodbury"],
                     help="factor M itself or the Woodbury-kinetic Schur matrix S")
     ap.add_argument("--no-woodbury", action="store_true",
@@ -669,6 +790,9 @@ def main():
     if args.precision == "c128":
         print("--precision c128 is for --batch (the main line times FP32+IR)", file=sys.stderr)
         return 2
+    if args.precision == "f16x1" and args.refine == 0:
+        print("--precision f16x1 needs --refine m (GMRES-IR)", file=sys.stderr)
+        return 2
     if args.sweep:
         return sweep_main(args)
     if args.config5:
@@ -696,9 +820,11 @@ def main():
 
     p, desc = workload(args)
     prec = {"tf32": g.RMAT_C64_3XTF32_IR, "f16": g.RMAT_C64_3XF16_IR,
-            "simt": g.RMAT_C64_SIMT_IR}[args.precision]
+            "f16x1": g.RMAT_C64_1XF16_IR, "simt": g.RMAT_C64_SIMT_IR}[args.precision]
     method = 1 if args.method == "woodbury" else 0
-    run = Runner(p, prec, local, method, 1 if args.lookahead else 0)
+    resid = {"auto": 0, "fp64mma": 1, "tensor": 2}[args.residual]
+    run = Runner(p, prec, local, method, 1 if args.lookahead else 0, resid)
+    g.rmat_set_param(run.ctx, g.RMAT_PARAM_REFINE, args.refine)
     with ClockSampler(local) as clk:
         ms, stats, launches = time_steps(run, args.steps, args.warmup, sync_all)
     ms = max_over_ranks(ms, dist, "cuda")
@@ -708,13 +834,13 @@ def main():
     e2e_ms, h2d, d2h = time_e2e(run, max(1, min(args.steps, 3)))
     e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
     U32 = run.U_host()
-    X32, R32 = run.XR_host() if not args.no_fp64 else (None, None)
+    X32, R32 = run.XR_host()
     ir = dict(run.last)
     run.close()
 
-    fp64 = None
+    fp64, fp64_arrays = None, (None, None, None)
     if not args.no_fp64:
-        r64 = Runner(p, g.RMAT_C128, local)
+        r64 = Runner(p, g.RMAT_C128, local, residual=resid)
         r64.step()                                  # warm-up (module load, buffers)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -729,6 +855,7 @@ def main():
 
         def rd(a, b):
             return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        fp64_arrays = (X64, R64, U64)
         fp64 = {"ms_per_step": ms64, "tflops": flops / (ms64 * 1e-3) / 1e12,
                 "refine": dict(r64.last),
                 "u_rel_diff_fp32ir_vs_fp64": rd(U32, U64),
@@ -740,7 +867,7 @@ def main():
     other = None
     if not args.no_woodbury:
         # the other factored matrix (Woodbury-kinetic S vs M) on the same workload
-        rw = Runner(p, prec, local, 1 - method, 1 if args.lookahead else 0)
+        rw = Runner(p, prec, local, 1 - method, 1 if args.lookahead else 0, resid)
         for _ in range(2):
             rw.step()
         torch.cuda.synchronize()
@@ -764,17 +891,57 @@ def main():
         rw.close()
 
     pk, src = peaks()
+    tf32 = None
+    if prec == g.RMAT_C64_3XF16_IR and not args.no_tf32:
+        # the FP32-class 3xTF32 split on the same system (spec precision)
+        rt = Runner(p, g.RMAT_C64_3XTF32_IR, local, residual=resid)
+        rt.step()
+        g.rmat_set_param(rt.ctx, g.RMAT_PARAM_TIMING, 1)
+        g.rmat_reset_counters(rt.ctx)
+        rt.step()
+        torch.cuda.synchronize()
+        st_t = g.rmat_get_stats(rt.ctx)
+        g.rmat_set_param(rt.ctx, g.RMAT_PARAM_TIMING, 0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kt = max(1, min(args.steps, 3))
+        e0.record(rt.stream)
+        for _ in range(kt):
+            rt.step()
+        e1.record(rt.stream)
+        torch.cuda.synchronize()
+        mst = max_over_ranks(e0.elapsed_time(e1) / kt, dist, "cuda")
+        Ut = rt.U_host()
+        Xt, Rt = rt.XR_host()
+        tpk = pk["bf16_tflops_sustained"] * TF32_PER_BF16 / 3.0
+        ach = st_t["tu_flops"] / (st_t["tu_ms"] * 1e-3) / 1e12 if st_t["tu_ms"] > 0 else None
+        tf32 = {"precision": DTYPES[g.RMAT_C64_3XTF32_IR], "ms_per_step": mst, "steps": kt,
+                "value": replica_throughput(world, flops, mst), "unit": "TFLOP/s",
+                "refine": dict(rt.last),
+                "u_rel_diff_vs_main": float(np.max(np.abs(Ut - U32)) / np.max(np.abs(U32))),
+                "roofline": {"kernel": "trailing update C22 -= L21 U12 (kind::tf32, 3 products)",
+                             "bound": "tensor", "achieved": ach, "peak": tpk, "unit": "TFLOP/s",
+                             "frac": ach / tpk if ach else None,
+                             "peak_source": "bf16 sustained (%s) x 0.5 (tf32/bf16 nominal) / 3 "
+                                            "(tf32 split products per fp32 product)" % src,
+                             "kernel_ms_per_step": st_t["tu_ms"], "launches": st_t["tu_launches"]}}
+        tf32_arrays = (Xt, Rt, Ut)
+        rt.close()
+    else:
+        tf32_arrays = (None, None, None)
     tu_ms, tu_flops, tu_n = stats["tu_ms"], stats["tu_flops"], stats["tu_launches"]
     if prec == g.RMAT_C64_3XTF32_IR:
         # each complex product = 4 real GEMMs x 3 tf32 split products: 12 tensor GEMMs
         peak = pk["bf16_tflops_sustained"] * TF32_PER_BF16 / 3.0
         bound, unit, pname = "tensor", "TFLOP/s", ("bf16 sustained (%s) x 0.5 (tf32/bf16 nominal) / 3 "
                                                     "(tf32 split products per fp32 product)" % src)
-    elif prec == g.RMAT_C64_3XF16_IR:
-        # 4 real GEMMs x 3 fp16 split products; fp16 and bf16 share the tensor rate
-        peak = pk["bf16_tflops_sustained"] / 3.0
-        bound, unit, pname = "tensor", "TFLOP/s", ("bf16 sustained (%s) / 3 (fp16 split products "
-                                                    "per fp32 product; fp16 rate = bf16 rate)" % src)
+    elif prec in (g.RMAT_C64_3XF16_IR, g.RMAT_C64_1XF16_IR):
+        # 4 real GEMMs x 3 (or 1) fp16 split products; fp16 and bf16 share the tensor rate
+        npr = 3.0 if prec == g.RMAT_C64_3XF16_IR else 1.0
+        peak = pk["bf16_tflops_sustained"] / npr
+        bound, unit, pname = "tensor", "TFLOP/s", ("bf16 sustained (%s) / %d (fp16 split products "
+                                                    "per fp32 product; fp16 rate = bf16 rate)"
+                                                    % (src, npr))
     else:
         peak = 152 * 128 * 2 * 2070e6 / 1e12
         bound, unit, pname = "alu", "TFLOP/s", "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"
@@ -799,19 +966,24 @@ def main():
                      "bf16 rate); HBM view: %.0f of %.0f GB/s algorithmic" % (src, gbs or 0.0,
                                                                                pk["hbm_gbs"]))
         # DRAM bytes per launch: the ncu capture of the first K = 256 paired update at
-        # N = 6400 moved 569.5 MB for 629 MB algorithmic; scaled by this run's average
-        traffic = 569.5e6 / 629.0e6 * (sum(alg) / len(alg))
-        tsrc = ("ncu dram__bytes_read+write of the N=6400 first paired-update capture "
-                "(profiles/trailing_update_pair_f16_n6400.md), scaled by algorithmic bytes per launch")
+        # N = 6400 (the bench's N = 25600 launches are too large to capture), its DRAM
+        # bytes per algorithmic byte scaled to this run's average launch
+        ratio = profile_ratio("trailing_update_pair_f16_n6400.md")
+        if ratio:
+            traffic = ratio * (sum(alg) / len(alg))
+            tsrc = ("scaled: ncu dram__bytes_read+write per algorithmic byte (%.3f) of the first "
+                    "paired update at N=6400 (profiles/trailing_update_pair_f16_n6400.md) x this "
+                    "run's average algorithmic bytes per launch" % ratio)
     if prec == g.RMAT_C64_3XTF32_IR:
-        # DRAM bytes per launch: the ncu capture of the same kernel at N = 6400 (first
-        # update, 6272^2 x 128) read + wrote 596.8 MB for 655 MB of algorithmic bytes
-        # (C22 read + write, 4 operand planes per side); scaled by the algorithmic
-        # bytes of this run's average launch
         alg = [r * r * 16.0 + 2 * r * nbk * 16.0 for r in rests]
-        traffic = 596.8e6 / 655.0e6 * (sum(alg) / len(alg))
-        tsrc = ("ncu dram__bytes_read+write of the N=6400 first-update capture "
-                "(profiles/trailing_update_tc_n6400.md), scaled by algorithmic bytes per launch")
+        ratio = profile_ratio("trailing_update_tc_n6400.md")
+        if ratio:
+            traffic = ratio * (sum(alg) / len(alg))
+            tsrc = ("scaled: ncu dram__bytes_read+write per algorithmic byte (%.3f) of the first "
+                    "update at N=6400 (profiles/trailing_update_tc_n6400.md) x this run's "
+                    "average algorithmic bytes per launch" % ratio)
+    W = getattr(p, "W", -10.0)
+    errs = None if p.N != 25600 else truth_errors(W, {"fp32ir": (X32, R32, U32), "fp64": fp64_arrays, "tf32": tf32_arrays})
     line = {
         "metric": "N=25600 complex solve time & TFLOP/s: FP32+IR vs FP64 at equal U error",
         "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -819,7 +991,7 @@ def main():
         "vs_baseline": None, "dtype": DTYPES[prec],
         "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "nrhs": p.nch,
-                   "method": args.method,
+                   "method": args.method, "residual": args.residual,
                    "refinement": ir, "l2": "inputs larger than L2 (C is %.1f GB)" % (p.N * p.N * 8 / 1e9),
                    "lu_block": stats["nb"], "panel_ctas": stats["panel_ctas"],
                    "ms_per_step_best_median": [stats["ms_steps"]["best"],
@@ -829,6 +1001,9 @@ def main():
                    "kernel_ms": {k: [stats.get(k + "_ms"), stats.get(k + "_launches")]
                                  for k in ("panel", "apply_inv", "solve_tc", "resid")}},
         "fp64_path": fp64,
+        "tf32_path": tf32,
+        "error_vs_truth": errs,
+        "stages_roofline": stage_rooflines(stats, p.N, p.nch, int(stats["nb"]), ir["iters"], pk, src),
         "other_method": other,
         "e2e": {"value": replica_throughput(world, flops, e2e_ms), "unit": "TFLOP/s",
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -849,6 +1024,11 @@ def main():
                      "share_of_step": (tu_ms / ms) if tu_ms and tu_ms > 0 else None},
         "clocks": clk.summary(),
     }
+    if world == 1 and not args.no_batch and not args.small:
+        # config 4 (512 uneven systems) through the tuned batch driver, 3 timed runs
+        bl = batch_run(args, 512, 3, 3, "f16")
+        line["batch"] = {k: bl[k] for k in ("metric", "value", "unit", "ms_per_step", "tflops",
+                                             "loop", "statuses", "refine_steps_max", "config")}
     if rank == 0:
         if world == 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline()

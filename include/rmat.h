@@ -50,7 +50,7 @@ extern "C" {
 #define RMAT_ETIMEOUT   (-103)  /* a bounded device-side wait gave up            */
 #define RMAT_ENODEV     (-104)  /* no CUDA device of compute capability 10.3     */
 #define RMAT_ESINGULAR     1    /* exactly zero pivot; info holds its column     */
-#define RMAT_ENOCONV       2    /* refinement stagnated above the tolerance      */
+#define RMAT_ENOCONV       2    /* refinement stagnated above the FP64 floor     */
 #define RMAT_ECHANFN       3    /* a Coulomb/Whittaker function did not converge */
 
 /* ---- precisions --------------------------------------------------------- */
@@ -66,9 +66,17 @@ extern "C" {
  * rate), with power-of-two scaling per U block and per right-hand-side column so
  * every operand stays in FP16 range; FP32 accumulation; FP64 residual refinement. */
 #define RMAT_C64_3XF16_IR    3
+/* As RMAT_C64_3XF16_IR, but the factor's trailing updates take ONE FP16 product per
+ * real product (hi x hi: ~11-bit operands, FP32 accumulation), a third of the
+ * tensor work; the factors are then accurate to ~u_16 cond(C) only, so classical
+ * refinement converges only for cond(C) u_16 < 1: meant for GMRES-IR
+ * (RMAT_PARAM_REFINE > 0), where the factors only precondition.  Solves apply the
+ * stored factors with the three-product split. */
+#define RMAT_C64_1XF16_IR    4
 
 /* ---- tunable parameters (rmat_set_param) -------------------------------- */
-#define RMAT_PARAM_NB          1  /* LU block width (multiple of 32; 0 = tuned) */
+#define RMAT_PARAM_NB          1  /* LU block width (multiple of 32; 0 = default: complex128
+                                     32, 64 from N = 2048; complex64 64, 128 from N = 4096) */
 #define RMAT_PARAM_PANEL_CTAS  2  /* CTAs of the grid panel (0 = auto: cluster panel
                                      when the rows fit one cluster, else grid) */
 #define RMAT_PARAM_SPIN_LIMIT  3  /* polls before a device wait gives up        */
@@ -114,6 +122,24 @@ extern "C" {
  * panel, every sector then uses width 64.  0 = sectors one after the other.
  * Results agree to rounding (identical when the block width is the same). */
 #define RMAT_PARAM_PROP_CONCURRENT 10
+/* Point-coupling product of the FP64 refinement residual of assembled problems
+ * (sum over al' of V_al,al'(r_i) X[(al',i),be], Sec. 3.2 with the block structure of
+ * Sec. 2): 0 (default) auto = 2 when nch >= 32, else 1; 1 = FP64 on the FP64 tensor
+ * instruction (mma.m8n8k4.f64); 2 = FP64-accurate on the FP16 tensor cores: every
+ * row of V_i (diagonal excluded, applied in FP64) and every column of X_i scaled by a
+ * power of two and cut into nine signed 6-bit integer digits, the digit products
+ * with p + q <= 8 summed exactly in FP32 tensor memory and combined in FP64
+ * (error below 2^-54 of the row and column scales; needs nch <= 2048, else 1). */
+#define RMAT_PARAM_RESIDUAL 11
+/* Tile width (output columns per CTA tile) of the factor's tensor-core trailing
+ * updates: 256 (0 = default) or 128 (twice the tiles, two accumulator sets per CTA:
+ * better balance on small trailing blocks).  Results agree to rounding. */
+#define RMAT_PARAM_TC_BN 12
+/* Sums of the kinetic part of the FP64 residual (the dominant terms of C X, whose
+ * rounding sets the refinement's floor): 1 = compensated (each product split exactly
+ * by FMA, each addition by TwoSum, r rounded once: as if summed in twice the FP64
+ * precision), 0 = FP64 sums, -1 (default) = compensated for RMAT_C128 only. */
+#define RMAT_PARAM_RESID_SUMS 13
 
 typedef struct rmat_ctx_s* rmat_ctx;
 
@@ -197,19 +223,26 @@ int rmat_load_dense(rmat_ctx ctx, int n, int nrhs, const void* A_dev, int lda,
  * Errors: -1 ctx, RMAT_ESTATE (nothing assembled), RMAT_ETIMEOUT, RMAT_ECUDA. */
 int rmat_factor(rmat_ctx ctx, int* info);
 
-/* Solve C X = Phi (or A X = B) with the factors, then refine:
+/* Solve C X = Phi (or A X = B) with the factors, then refine (Sec. 3.2):
  *   loop: r = Phi - C X in FP64 (structured for assembled problems, dense for
- *   loaded ones); stop when max|r|/max|Phi| < tol, when it fails to drop below
- *   half of the previous step's value (stagnation at the FP64 floor, or
- *   divergence: once for the complex64 precisions, twice in a row for
- *   RMAT_C128), or after max_refine steps; else solve C d = r with the
- *   factors and X += d (FP64).
+ *   loaded ones; RMAT_PARAM_RESIDUAL, RMAT_PARAM_RESID_SUMS); stop with RMAT_OK
+ *   when max|r|/max|Phi| < tol; when the normwise backward error
+ *   max|r| / (max|C||X| + max|Phi|) is at most u/2 (u = 2^-53; |C||X| of the
+ *   first solution, |.| the complex modulus: the FP64 floor, where r is the
+ *   rounding of its own evaluation; a correctly rounded solution sits at ~0.1-0.2
+ *   u, a plain FP64 LU solve near 1 u) apply one last correction and stop with
+ *   RMAT_OK (no residual is formed after it);
+ *   stop when the residual fails to drop below half of the previous step's
+ *   value (once for the complex64 precisions, twice in a row for RMAT_C128):
+ *   RMAT_OK when the backward error is then at most 2u, else RMAT_ENOCONV
+ *   (stagnation above the floor, or divergence); stop after max_refine steps
+ *   (RMAT_ENOCONV when tol > 0); else solve C d = r with the factors and
+ *   X += d (FP64).
  * X_dev: device complex128 N x nrhs column-major, ldx >= N (caller-owned).
  * iters (may be NULL): refinement steps taken.  rel_resid (may be NULL): the
  * last max|r|/max|Phi| measured (0 when max_refine == 0 and tol <= 0, in
- * which case no residual is formed).  Returns RMAT_ENOCONV when refinement
- * stopped by stagnation or step count above tol (X is still the best
- * iterate), RMAT_ESINGULAR after a zero pivot.
+ * which case no residual is formed).  Returns RMAT_ENOCONV as above (X is
+ * still the best iterate), RMAT_ESINGULAR after a zero pivot.
  * Errors: -1 ctx, -2 X_dev, -3 ldx, -4 max_refine < 0, RMAT_ESTATE. */
 int rmat_solve(rmat_ctx ctx, void* X_dev, int ldx, int max_refine, double tol,
                int* iters, double* rel_resid);
@@ -280,11 +313,22 @@ int rmat_propagate(rmat_ctx ctx, const rmat_problem* prob, double E, int ns, con
  *   out[15] / out[16] solve-path diagonal-block application ms / launches,
  *   out[17] / out[18] solve-path tensor-core block update ms / launches,
  *   out[19] / out[20] FP64 residual ms / launches, out[21] GMRES-IR inner steps of the
- *   last rmat_solve
+ *   last rmat_solve, out[22] the last normwise backward error of the last rmat_solve,
+ *   max|r| / (max|C||X| + max|Phi|) (0 when no residual was formed)
  *   (timers need RMAT_PARAM_TIMING=1; a time is -1 when it was not timed).
-  * n: capacity of out; returns the number of values written (<= 22). */
+ * n: capacity of out; returns the number of values written (<= 23). */
 int rmat_get_stats(rmat_ctx ctx, double* out, int n);
 int rmat_reset_counters(rmat_ctx ctx);
+
+/* The FP64 refinement residual of the current system for a caller's X (Sec. 3.2):
+ *   R = Phi - C X for an assembled problem (block structure of Sec. 2, the point
+ *   couplings as RMAT_PARAM_RESIDUAL selects), R = B - A X for a loaded one.
+ * X_dev, R_dev: device complex128 N x nrhs column-major, leading dimensions
+ * ldx, ldr >= N (caller-owned; X is read only).  Leaves the factors and the
+ * solution untouched.  Synchronises.
+ * Errors: -1 ctx, -2 X_dev, -3 ldx, -4 R_dev, -5 ldr, RMAT_ESTATE (nothing
+ * assembled or loaded, or a propagation sector). */
+int rmat_residual(rmat_ctx ctx, const void* X_dev, int ldx, void* R_dev, int ldr);
 
 /* Refinement history of the last rmat_solve: hist[k] = max|r|/max|Phi| measured
  * before correction k (k = 0 is the residual of the first solve).  Returns the
@@ -298,19 +342,31 @@ int rmat_refine_history(rmat_ctx ctx, double* hist, int n);
  * precision.  The whole batch (assembly, factorisation, refined solve, R and U
  * for every system) is enqueued without host synchronisation and captured into
  * one CUDA graph that later runs replay; refinement uses max_refine steps with
- * the stopping rule of rmat_solve evaluated on the device.  Systems with
- * N > split_n run one after another with the full-device path; smaller ones are
- * spread over `lanes` concurrent streams, provided their panels fit the shared
- * memory of one thread block cluster (up to 16 CTAs: N <= ~6900 in complex64,
- * ~3400 in complex128), whatever split_n says.  Refinement steps after a system
- * has stopped return at once on the device.  rmat_batch_tune
- * times candidate (lanes, split_n) plans on the batch and keeps the fastest,
- * cached in the JSON-lines file named by the environment variable
- * RMAT_TUNE_CACHE when it is set. */
+ * the stopping rule of rmat_solve evaluated on the device.  The smallest systems
+ * (RMAT_BATCH_SMALL_N) run in one persistent launch, a whole system per thread
+ * block.  Systems with N > split_n run one after another with the full-device
+ * path; the others are spread over `lanes` concurrent streams, provided their
+ * panels fit the shared memory of one thread block cluster (up to 16 CTAs:
+ * N <= ~6900 in complex64, ~3400 in complex128), whatever split_n says.
+ * Refinement steps after a system has stopped return at once on the device.
+ * rmat_batch_tune times candidate plans on the batch itself and keeps the fastest,
+ * cached in the JSON-lines file named by the environment variable RMAT_TUNE_CACHE
+ * when it is set: coordinate descent over the (lanes, split_n) plan, the
+ * small-system class on or off, and the tile shapes (LU block width in lanes and
+ * in the serial phase, tensor-update tile width in lanes). */
 typedef struct rmat_batch_s* rmat_batch;
 #define RMAT_BATCH_LANES   1  /* concurrent streams for small systems (0..16)   */
 #define RMAT_BATCH_SPLIT_N 2  /* systems with N <= split_n go to the lanes      */
 #define RMAT_BATCH_GRAPH   3  /* 1 = capture and replay a CUDA graph (default)  */
+/* Systems with N <= small_n whose complex64 (complex128) matrix fits one thread
+ * block's shared memory (N <= 160 (112) at a few channels) run in ONE persistent
+ * launch, one system per thread block at a time: assembly, LU with partial
+ * pivoting, solves, FP64 refinement, R and U without leaving the SM.  -1 (default)
+ * = every system that fits, 0 = off. */
+#define RMAT_BATCH_SMALL_N 4
+#define RMAT_BATCH_NB_LANE 5    /* LU block width in lanes: 32, 64 (0 = 32 to N 1024, else 64) */
+#define RMAT_BATCH_NB_SERIAL 6  /* LU block width of serial systems: 32, 64, 128 (0 = default) */
+#define RMAT_BATCH_TC_BN 7      /* tensor-update tile width in lanes: 128 or 256 (0 = 256) */
 
 /* probs[s], E[s], V_dev[s] (device complex128 cpot(nlag,nch,nch) of system s, as
  * in rmat_assemble) for s < nsys; the arrays are copied, V_dev must stay valid
@@ -322,7 +378,8 @@ int rmat_batch_create(rmat_ctx ctx, int nsys, const rmat_problem* probs, const d
 /* Open channels of every system (host int[nsys]). */
 int rmat_batch_nopen(rmat_batch b, int* nopen);
 int rmat_batch_set(rmat_batch b, int key, long long value);
-/* Choose lanes and split_n by timing candidate plans with the outputs U_dev. */
+/* Choose the plan (lanes, split_n, small-system class, block widths, tile width) by
+ * timing candidates with the outputs U_dev; lanes and split_n are returned. */
 int rmat_batch_tune(rmat_batch b, void* const* U_dev, int* lanes, int* split_n);
 /* Run the batch: U_dev[s] = device complex128 nopen_s x nopen_s column-major
  * collision matrix of system s (may be NULL when nopen_s = 0).  status[s] and
@@ -331,7 +388,9 @@ int rmat_batch_tune(rmat_batch b, void* const* U_dev, int* lanes, int* split_n);
  * negative status, else RMAT_OK (per-system numerical outcomes in status). */
 int rmat_batch_run(rmat_batch b, void* const* U_dev, int* status, int* iters);
 /* out[0] systems, out[1] lanes, out[2] split_n, out[3] graph (1 used, -1 capture
- * unavailable, 0 not yet), out[4] kernel launches enqueued so far. */
+ * unavailable, 0 not yet), out[4] kernel launches enqueued so far, out[5] systems in
+ * the small-system launch, out[6] small_n, out[7] lane block width, out[8] serial
+ * block width (0 = defaults), out[9] tensor-update tile width in lanes. */
 int rmat_batch_info(rmat_batch b, long long* out, int n);
 int rmat_batch_destroy(rmat_batch b);
 
@@ -355,15 +414,20 @@ int rmat_batch_destroy(rmat_batch b);
  *   R_dev     device complex128 nch x nch column-major output (may be NULL)
  *   U_dev     device complex128 nopen x nopen column-major output
  *   nopen     host int output (may be NULL)
- * The first call on a device looks up the scratch array's device address; make
- * that first call before any stream capture.  All calls share the one scratch
- * array and it keeps the last call's contents (the kernel rewrites everything
- * it reads, and clears its status word, on every call): calls that overlap on
- * the GPU, from any stream or thread, race.  Synchronises `stream`.
- * Errors: -1 prob invalid or nch > RMAT_NOALLOC_MAX_NCH, -2 E invalid or a channel
- * exactly at threshold, -3 f_a_dev NULL, -4 X_dev NULL, -5 ldx < N, -7 U_dev NULL
- * with open channels, RMAT_ESINGULAR for an exactly singular matching system,
- * RMAT_ECHANFN for a channel function that did not converge, RMAT_ECUDA. */
+ * The first call on a device (with that device current) looks up the scratch
+ * array's device address and keeps it for the life of the process; make that
+ * first call before any stream capture begins, and do not call again after a
+ * cudaDeviceReset of that device (the reset may move the array).  All calls share
+ * the one scratch array and it keeps the last call's contents (the kernel
+ * rewrites everything it reads, and clears its status word, on every call):
+ * calls that overlap on the GPU, from any stream or thread, race.  Each call
+ * copies the status word to the host and synchronises `stream` before returning.
+ * Errors: -1 prob invalid (nch outside 1..RMAT_NOALLOC_MAX_NCH, a, hm, bloch_B or
+ * a threshold not finite, ...), -2 E not finite or a channel exactly at
+ * threshold, -3 f_a_dev NULL, -4 X_dev NULL, -5 ldx < N, -7 U_dev NULL with open
+ * channels, RMAT_ESINGULAR for an exactly singular matching system, RMAT_ECHANFN
+ * for a channel function that did not converge, RMAT_ECUDA (rmat_last_error
+ * names the failing call). */
 #define RMAT_NOALLOC_MAX_NCH 64
 int rmat_collision_noalloc(const rmat_problem* prob, double E, const void* f_a_dev,
                            const void* X_dev, int ldx, void* R_dev, void* U_dev, int* nopen,

@@ -31,6 +31,7 @@ RMAT_C128 = 0
 RMAT_C64_3XTF32_IR = 1
 RMAT_C64_SIMT_IR = 2
 RMAT_C64_3XF16_IR = 3
+RMAT_C64_1XF16_IR = 4
 
 RMAT_PARAM_NB = 1
 RMAT_PARAM_PANEL_CTAS = 2
@@ -42,17 +43,24 @@ RMAT_PARAM_METHOD = 7   # 0 factor M, 1 Woodbury-kinetic (factor S = I + (K^-1 x
 RMAT_PARAM_REFINE = 8   # 0 classical refinement, m = 1..64 FGMRES-IR with <= m inner steps
 RMAT_PARAM_SOLVE_LOOKAHEAD = 9   # 1 look-ahead in the tensor-path solves, 0 (default) off
 RMAT_PARAM_PROP_CONCURRENT = 10  # 1 (default) propagation sectors on concurrent worker contexts
+RMAT_PARAM_RESIDUAL = 11  # coupling product of the FP64 residual: 0 auto, 1 FP64 MMA, 2 tensor-core digits
+RMAT_PARAM_TC_BN = 12  # tile width of the factor's tensor-core updates: 256 (0) or 128
+RMAT_PARAM_RESID_SUMS = 13  # compensated kinetic residual sums: -1 complex128 only, 0 off, 1 on
 
 RMAT_BATCH_LANES = 1
 RMAT_BATCH_SPLIT_N = 2
 RMAT_BATCH_GRAPH = 3
+RMAT_BATCH_SMALL_N = 4   # small-system class in one persistent launch: -1 all that fit, 0 off
+RMAT_BATCH_NB_LANE = 5
+RMAT_BATCH_NB_SERIAL = 6
+RMAT_BATCH_TC_BN = 7
 
 EXPORTED = ("rmat_create", "rmat_destroy", "rmat_set_param", "rmat_mesh", "rmat_assemble",
             "rmat_load_dense", "rmat_factor", "rmat_solve", "rmat_collision", "rmat_get_stats",
             "rmat_reset_counters", "rmat_refine_history", "rmat_collision_noalloc",
             "rmat_batch_create", "rmat_batch_nopen", "rmat_batch_set", "rmat_batch_tune",
             "rmat_batch_run", "rmat_batch_info", "rmat_batch_destroy", "rmat_status_string",
-            "rmat_sector_mesh", "rmat_propagate")
+            "rmat_sector_mesh", "rmat_propagate", "rmat_residual")
 
 
 class rmat_problem(ct.Structure):
@@ -95,6 +103,7 @@ def lib():
             "rmat_get_stats": (i, [vp, pd, i]),
             "rmat_reset_counters": (i, [vp]),
             "rmat_refine_history": (i, [vp, pd, i]),
+            "rmat_residual": (i, [vp, vp, i, vp, i]),
             "rmat_collision_noalloc": (i, [ct.POINTER(rmat_problem), d, vp, vp, i, vp, vp, pi, vp]),
             "rmat_batch_create": (i, [vp, i, ct.POINTER(rmat_problem), pd, ct.POINTER(vp), i, d,
                                       ct.POINTER(vp)]),
@@ -248,7 +257,8 @@ def rmat_propagate(ctx, prob, E, radii, V_ptrs, max_refine=30, tol=1e-13, R_dev=
 STAT_KEYS = ("N", "nrhs", "nb", "panel_ctas", "launches", "tu_launches", "tu_ms", "tu_flops",
              "assemble_ms", "factor_ms", "solve_ms", "refine_ms", "collision_ms",
              "panel_ms", "panel_launches", "apply_inv_ms", "apply_inv_launches",
-             "solve_tc_ms", "solve_tc_launches", "resid_ms", "resid_launches", "gmres_inner")
+             "solve_tc_ms", "solve_tc_launches", "resid_ms", "resid_launches", "gmres_inner",
+             "backward_error")
 
 
 def rmat_get_stats(ctx) -> dict:
@@ -259,6 +269,12 @@ def rmat_get_stats(ctx) -> dict:
 
 def rmat_reset_counters(ctx) -> None:
     _check("rmat_reset_counters", lib().rmat_reset_counters(ct.c_void_p(ctx)))
+
+
+def rmat_residual(ctx, X_dev, ldx, R_dev, ldr) -> None:
+    """R = Phi - C X (FP64) for a caller's X; column-major device buffers."""
+    _check("rmat_residual", lib().rmat_residual(ct.c_void_p(ctx), ct.c_void_p(X_dev), int(ldx),
+                                                ct.c_void_p(R_dev), int(ldr)))
 
 
 def rmat_refine_history(ctx) -> list:
@@ -323,9 +339,11 @@ def rmat_batch_run(b, U_ptrs):
 
 
 def rmat_batch_info(b) -> dict:
-    out = (ct.c_longlong * 5)()
-    n = lib().rmat_batch_info(ct.c_void_p(b), out, 5)
-    return dict(zip(("systems", "lanes", "split_n", "graph", "launches"), list(out)[:n]))
+    keys = ("systems", "lanes", "split_n", "graph", "launches", "small_systems", "small_n",
+            "nb_lane", "nb_serial", "tc_bn_lane")
+    out = (ct.c_longlong * len(keys))()
+    n = lib().rmat_batch_info(ct.c_void_p(b), out, len(keys))
+    return dict(zip(keys, list(out)[:n]))
 
 
 def rmat_batch_destroy(b) -> None:

@@ -23,7 +23,7 @@ int clamp_nb(int precision, int nb) { return std::min(nb, precision == RMAT_C128
 
 bool valid_precision(int p) {
   return p == RMAT_C128 || p == RMAT_C64_3XTF32_IR || p == RMAT_C64_SIMT_IR ||
-         p == RMAT_C64_3XF16_IR;
+         p == RMAT_C64_3XF16_IR || p == RMAT_C64_1XF16_IR;
 }
 
 int begin(rmat_ctx c) {
@@ -49,6 +49,17 @@ double read_red(rmat_ctx c) {
   double v;
   std::memcpy(&v, &bits, sizeof(v));
   return v;
+}
+
+// red[0] (max|r|) and red[1] (max|C||X|) in one copy
+bool read_red2(rmat_ctx c, double* r0, double* r1) {
+  if (cudaMemcpyAsync(c->hstat + ST_COUNT, c->red, 2 * sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return false;
+  std::memcpy(r0, c->hstat + ST_COUNT, sizeof(double));
+  std::memcpy(r1, c->hstat + ST_COUNT + 2, sizeof(double));
+  return true;
 }
 
 }  // namespace
@@ -292,12 +303,13 @@ int rmat_destroy(rmat_ctx c) {
   if (c->borrowed_tables) c->Kmat = c->T0 = c->rmesh = c->fa = nullptr, c->l_d = nullptr,
                           c->th_d = nullptr, c->zz_d = nullptr, c->open_d = nullptr;
   tc_release(c);
+  oz_release(c);
   void* bufs[] = {c->C,    c->A64,  c->B64, c->ipiv, c->Kmat, c->T0,  c->rmesh,
                   c->fa,   c->l_d,  c->th_d, c->zz_d, c->Wpt, c->X,  c->Rres, c->Bw,
                   c->Fpl,  c->Bpl, c->Ypl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
                   c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows, c->Dinv,
                   c->umax, c->uscale, c->ycs, c->pfwd, c->Bt, c->Kinv, c->Kinv32, c->W32, c->Bs,
-                  c->gm_V, c->gm_Z, c->gm_T, c->gm_small, c->faL, c->prop};
+                  c->gm_V, c->gm_Z, c->gm_T, c->gm_small, c->faL, c->prop, c->Xs};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->hstat) cudaFreeHost(c->hstat);
@@ -347,6 +359,18 @@ int rmat_set_param(rmat_ctx c, int key, long long v) {
     case RMAT_PARAM_PROP_CONCURRENT:
       if (v < 0 || v > 1) return -3;
       c->prop_concurrent = (int)v;
+      return RMAT_OK;
+    case RMAT_PARAM_RESIDUAL:
+      if (v < 0 || v > 2) return -3;
+      c->resid_param = (int)v;
+      return RMAT_OK;
+    case RMAT_PARAM_TC_BN:
+      if (v != 0 && v != 128 && v != 256) return -3;
+      c->tc_bn = v == 128 ? 128 : 256;
+      return RMAT_OK;
+    case RMAT_PARAM_RESID_SUMS:
+      if (v < -1 || v > 1) return -3;
+      c->resid_comp = (int)v;
       return RMAT_OK;
     default:
       return -2;
@@ -604,6 +628,7 @@ int enqueue_solve_refine(rmat_ctx c, int max_refine, double tol, IrState* st) {
   RMAT_CHECK(launch_w_from_phi(c));
   RMAT_CHECK(solve_system(c));
   RMAT_CHECK(launch_x_from_w(c));
+  RMAT_CHECK(launch_absprod(c));
   RMAT_CHECK(launch_ir_init(c, st));
   const int patience = c->precision == RMAT_C128 ? 2 : 1;
   // once the stopping rule has fired, every later kernel of the loop returns at once
@@ -635,28 +660,39 @@ static int solve_refine(rmat_ctx c, int max_refine, double tol, int* iters, doub
   c->ir_hist.clear();
   c->gm_inner = 0;
   if (max_refine > 0 || tol > 0) {
+    // |C||X| of the first solution sets the scale of the FP64 floor (X changes
+    // only in its last digits after that)
+    RMAT_CHECK(launch_absprod(c));
     double prev = INFINITY;
     // complex64 factors: one non-halving step ends the refinement (each extra
-    // correction costs a full solve); complex128: two, one more FP64 correction
-    // past the floor still sharpens X, R and U at the 1e-12 level
+    // correction costs a full solve); complex128: two
     const int patience = c->precision == RMAT_C128 ? 2 : 1;
-    int stagn = 0;
+    const int need = rmat_floor_need(c->precision);
+    int stagn = 0, floor_hits = 0;
+    bool final = false;
     for (;;) {
       RMAT_CHECK(launch_residual(c, nullptr));
-      rel = read_red(c) / c->phi_max;
+      double rmax = NAN, cx = NAN;
+      if (!read_red2(c, &rmax, &cx)) return RMAT_ECUDA;
+      rel = rmax / c->phi_max;
+      const double scale = cx + c->phi_max;  // max|C||X| + max|Phi|
       c->ir_hist.push_back(rel);
+      c->ir_berr = rmax / scale;
+      floor_hits = rmax <= RMAT_FLOOR_CONV * RMAT_U64 * scale ? floor_hits + 1 : 0;
       if (!std::isfinite(rel)) {
         status = RMAT_ENOCONV;
         break;
       }
       if (rel < tol) break;
       if (it >= max_refine) {
-        status = tol > 0 ? RMAT_ENOCONV : RMAT_OK;
+        status = (tol > 0 && rmax > RMAT_FLOOR_STALL * RMAT_U64 * scale) ? RMAT_ENOCONV : RMAT_OK;
         break;
       }
-      if (rel > 0.5 * prev) {  // no longer contracting: the FP64 floor (or divergence)
+      if (floor_hits >= need) {
+        final = true;  // at the FP64 floor: one last correction, no confirming residual
+      } else if (rel > 0.5 * prev) {  // no longer contracting above the floor (or diverging)
         if (++stagn >= patience) {
-          status = RMAT_ENOCONV;
+          status = rmax <= RMAT_FLOOR_STALL * RMAT_U64 * scale ? RMAT_OK : RMAT_ENOCONV;
           break;
         }
       } else {
@@ -672,6 +708,7 @@ static int solve_refine(rmat_ctx c, int max_refine, double tol, int* iters, doub
         RMAT_CHECK(launch_update(c));
       }
       ++it;
+      if (final) break;
     }
   }
   record_stage(c, &e2);
@@ -908,7 +945,7 @@ int rmat_get_stats(rmat_ctx c, double* out, int n) {
   };
   for (int k = 0; k < 5; ++k)
     c->stage_ms[k] = elapsed(c->stage_ev[k][0], c->stage_ev[k][1]);
-  const double v[22] = {(double)c->N, (double)c->nrhs, (double)c->nb,
+  const double v[23] = {(double)c->N, (double)c->nrhs, (double)c->nb,
                         (double)panel_ctas_for(c, c->N > 0 ? c->N : 1), (double)c->launches,
                         (double)c->tu_launches, sum(c->tu_events), c->tu_flops, c->stage_ms[0],
                         c->stage_ms[1], c->stage_ms[2], c->stage_ms[3], c->stage_ms[4],
@@ -916,10 +953,25 @@ int rmat_get_stats(rmat_ctx c, double* out, int n) {
                         sum(c->kt_events[KT_APPLY_INV]), (double)c->kt_launches[KT_APPLY_INV],
                         sum(c->kt_events[KT_SOLVE_TC]), (double)c->kt_launches[KT_SOLVE_TC],
                         sum(c->kt_events[KT_RESID]), (double)c->kt_launches[KT_RESID],
-                        (double)c->gm_inner};
-  const int m = n < 22 ? n : 22;
+                        (double)c->gm_inner, c->ir_berr};
+  const int m = n < 23 ? n : 23;
   for (int k = 0; k < m; ++k) out[k] = v[k];
   return m;
+}
+
+int rmat_residual(rmat_ctx c, const void* X_dev, int ldx, void* R_dev, int ldr) {
+  RMAT_CHECK(begin(c));
+  if (!X_dev) return -2;
+  if (ldx < c->N) return -3;
+  if (!R_dev) return -4;
+  if (ldr < c->N) return -5;
+  if (!c->assembled || c->sector) return RMAT_ESTATE;
+  RMAT_CHECK(rmat_grow(c, (void**)&c->Xs, &c->Xs_cap, (size_t)c->N * c->nrhs * 16));
+  RMAT_CHECK(launch_from_colmajor(c, reinterpret_cast<const double2*>(X_dev), ldx, c->Xs));
+  RMAT_CHECK(launch_apply_resid(c, c->Xs, c->Rres));
+  RMAT_CHECK(launch_to_colmajor(c, c->Rres, reinterpret_cast<double2*>(R_dev), ldr));
+  RMAT_CU(cudaStreamSynchronize(c->stream));
+  return RMAT_OK;
 }
 
 int rmat_refine_history(rmat_ctx c, double* hist, int n) {

@@ -187,6 +187,7 @@ int launch_point_coupling(rmat_ctx c, const double2* V, double E) {
   point_coupling_kernel<<<blocks, 256, 0, c->stream>>>(c->Wpt, c->nch, c->nlag, c->rmesh, c->l_d,
                                                        c->th_d, V, c->hm, E);
   c->launches++;
+  c->wpt_gen++;  // digit planes of the tensor-core residual are rebuilt from the new table
   RMAT_CU(cudaGetLastError());
   return RMAT_OK;
 }

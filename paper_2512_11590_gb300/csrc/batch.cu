@@ -41,7 +41,7 @@ struct BatchSys {
   const double2* V;
   int mesh;
   size_t off_l, off_open;
-  int lane;  // 0 = serial phase on the caller's stream, >= 1 concurrent lane
+  int lane;  // -1 small-system kernel, 0 serial phase on the caller's stream, >= 1 lane
   double cost;
 };
 
@@ -83,16 +83,41 @@ struct rmat_batch_s {
   cudaGraphExec_t gexec = nullptr;
   std::vector<void*> graph_U;
   int graph_ok = 0;
+  // small-system class: one persistent launch (batch_small.cu)
+  int small_n = -1;                 // N limit of the class (-1: the largest that fits, 0: off)
+  int nb_lane = 0, nb_serial = 0;   // LU block widths (0: the size-class defaults)
+  int tc_bn_lane = 256;             // tensor-update tile width of lane systems
+  std::vector<int> small_idx;       // systems of the class, largest first
+  SmallSys* small_dev = nullptr;    size_t small_dev_cap = 0;
+  std::vector<SmallSys> small_host;
+  std::vector<void*> small_U;       // U pointers the device descriptors hold
+  bool small_dirty = true;          // descriptors changed on the host since the last copy
+  int* small_next = nullptr;
+  SmallScratch small_scr{};
+  size_t small_scr_cap[3] = {0, 0, 0};
+  size_t small_smem = 0;
+  int small_grid = 0;
 };
 
 namespace {
 
 // LU block width of a system: in a lane 32 up to N = 1024 and 64 above (its panel
-// runs as one thread block cluster), the single-system default otherwise.
+// runs as one thread block cluster), the single-system default otherwise; the
+// autotuner may set either class (RMAT_BATCH_NB_LANE / RMAT_BATCH_NB_SERIAL).
 int sys_nb(rmat_batch b, const BatchSys& y) {
-  if (y.lane > 0) return y.N <= 1024 ? 32 : 64;
+  if (y.lane > 0) return b->nb_lane > 0 ? b->nb_lane : (y.N <= 1024 ? 32 : 64);
+  const int cap = b->precision == RMAT_C128 ? 64 : 128;
+  if (b->nb_serial > 0) return std::min(b->nb_serial, cap);
   if (b->precision == RMAT_C128) return y.N >= 2048 ? 64 : 32;
   return y.N >= 4096 ? 128 : 64;
+}
+
+// Whether a system goes to the small-system kernel: its matrix, right-hand sides and
+// pivots fit one thread block's shared memory and its N is within the class limit.
+bool small_fits(rmat_batch b, const BatchSys& y) {
+  if (b->small_n == 0 || y.nch > RMAT_NOALLOC_MAX_NCH) return false;
+  if (b->small_n > 0 && y.N > b->small_n) return false;
+  return small_smem_bytes(b->precision, y.N, y.nch) + 4096 <= (size_t)b->parent->smem_optin;
 }
 
 template <class T>
@@ -124,6 +149,7 @@ int enqueue_system(rmat_batch b, int s, void* U) {
   c->borrowed_tables = true;
   c->woodbury = false;      // batches factor M itself
   c->solve_lookahead = 0;   // lanes are their own concurrency
+  c->tc_bn = y.lane > 0 ? b->tc_bn_lane : 256;
   c->equil = c->equil_param == -1 ? b->precision != RMAT_C128 : c->equil_param == 1;
   RMAT_CHECK(perm_reserve(c, c->perm_main, y.N, c->nb));  // lay out, no growth (plan sized it)
   RMAT_CU(cudaMemsetAsync(c->dstat, 0, ST_COUNT * sizeof(int), c->stream));
@@ -142,7 +168,13 @@ int enqueue_all(rmat_batch b, void* const* U) {
   cudaStream_t main = b->lane_stream[0];
   RMAT_CU(cudaEventRecord(b->fork, main));
   for (int l = 1; l <= b->lanes; ++l) RMAT_CU(cudaStreamWaitEvent(b->lane_stream[l], b->fork, 0));
+  // the small-system class: one persistent launch, concurrent with the lanes
+  RMAT_CHECK(launch_batch_small(main, b->precision, b->small_dev, (int)b->small_idx.size(),
+                                b->small_next, b->small_grid, b->small_smem, b->max_refine, b->tol,
+                                b->st_dev, b->ir, b->small_scr));
+  if (!b->small_idx.empty()) b->lane_ctx[0]->launches++;
   for (size_t s = 0; s < b->sys.size(); ++s) {
+    if (b->sys[s].lane < 0) continue;
     if (b->precision == RMAT_C128)
       RMAT_CHECK(enqueue_system<double>(b, (int)s, U[s]));
     else
@@ -163,6 +195,78 @@ bool lane_fits(rmat_batch b, const BatchSys& y) {
   return panel_cluster_fits(b->parent, b->precision, y.N, sys_nb(b, t)) > 0;
 }
 
+// Device descriptors and per-CTA scratch of the small-system class.
+int plan_small(rmat_batch b) {
+  rmat_ctx c = b->parent;
+  const int n = (int)b->small_idx.size();
+  b->small_host.assign(n, SmallSys{});
+  b->small_U.assign(n, nullptr);
+  b->small_dirty = true;
+  if (n == 0) return RMAT_OK;
+  size_t slot = 0;
+  int maxN = 0, maxc = 0;
+  for (int k = 0; k < n; ++k) {
+    const BatchSys& y = b->sys[b->small_idx[k]];
+    const MeshTab& m = b->meshes[y.mesh];
+    SmallSys& d = b->small_host[k];
+    d.nch = y.nch;
+    d.nlag = y.nlag;
+    d.N = y.N;
+    d.nopen = y.nopen;
+    d.sys = b->small_idx[k];
+    d.hm = y.hm;
+    d.a = y.a;
+    d.B = y.B;
+    d.E = y.E;
+    d.phi_max = m.phi_max;
+    d.V = y.V;
+    d.K = m.K;
+    d.r = m.r;
+    d.fa = m.fa;
+    d.l = b->l_all + y.off_l;
+    d.th = b->th_all + y.off_l;
+    d.zz = b->zz_all + y.off_l;
+    d.open = b->open_all + y.off_open;
+    d.U = nullptr;
+    slot = std::max(slot, (size_t)y.N * y.nch);
+    maxN = std::max(maxN, y.N);
+    maxc = std::max(maxc, y.nch);
+  }
+  b->small_grid = std::min(n, c->sm_count);
+  b->small_smem = 0;
+  for (int k = 0; k < n; ++k)
+    b->small_smem = std::max(b->small_smem, small_smem_bytes(b->precision, b->small_host[k].N,
+                                                             b->small_host[k].nch));
+  const size_t xb = (size_t)b->small_grid * slot * sizeof(double2);
+  const size_t cb = (size_t)b->small_grid * small_coll_scratch_bytes();
+  RMAT_CHECK(rmat_grow(c, (void**)&b->small_scr.X, &b->small_scr_cap[0], xb));
+  RMAT_CHECK(rmat_grow(c, (void**)&b->small_scr.R, &b->small_scr_cap[1], xb));
+  RMAT_CHECK(rmat_grow(c, &b->small_scr.coll, &b->small_scr_cap[2], cb));
+  b->small_scr.slot = slot;
+  RMAT_CHECK(rmat_grow(c, (void**)&b->small_dev, &b->small_dev_cap, (size_t)n * sizeof(SmallSys)));
+  if (!b->small_next) RMAT_CU(cudaMalloc((void**)&b->small_next, sizeof(int)));
+  return RMAT_OK;
+}
+
+// The descriptors carry the U pointers of the run: rewritten (outside any capture)
+// whenever they change.
+int small_prepare(rmat_batch b, void* const* U) {
+  const int n = (int)b->small_idx.size();
+  if (n == 0) return RMAT_OK;
+  bool same = !b->small_dirty;
+  for (int k = 0; k < n; ++k)
+    if (b->small_U[k] != U[b->small_idx[k]]) same = false;
+  if (same) return RMAT_OK;
+  for (int k = 0; k < n; ++k) {
+    b->small_U[k] = U[b->small_idx[k]];
+    b->small_host[k].U = reinterpret_cast<double2*>(b->small_U[k]);
+  }
+  RMAT_CU(cudaMemcpy(b->small_dev, b->small_host.data(), n * sizeof(SmallSys),
+                     cudaMemcpyHostToDevice));
+  b->small_dirty = false;
+  return RMAT_OK;
+}
+
 // Assign systems to the serial phase or to lanes (longest first onto the least
 // loaded lane) and size every lane context for its largest system.
 int plan(rmat_batch b) {
@@ -175,8 +279,14 @@ int plan(rmat_batch b) {
   std::sort(order.begin(), order.end(),
             [&](int x, int y) { return b->sys[x].cost > b->sys[y].cost; });
   std::vector<double> load(b->lanes + 1, 0.0);
+  b->small_idx.clear();
   for (int s : order) {
     BatchSys& y = b->sys[s];
+    if (small_fits(b, y)) {  // whole hot path in one CTA's shared memory
+      y.lane = -1;
+      b->small_idx.push_back(s);
+      continue;
+    }
     // lanes hold systems whose panels fit one cluster
     if (y.N > b->split_n || b->lanes == 0 || !lane_fits(b, y)) {
       y.lane = 0;
@@ -214,6 +324,7 @@ int plan(rmat_batch b) {
     RMAT_CHECK(rmat_grow(c, (void**)&c->zpiv, &c->zpiv_cap, maxc * sizeof(int)));
     RMAT_CHECK(rmat_grow(c, (void**)&c->Dsc, &c->Dsc_cap, (size_t)maxN * sizeof(double)));
   }
+  RMAT_CHECK(plan_small(b));
   b->planned = true;
   b->warm = false;
   b->graph_ok = 0;
@@ -222,6 +333,7 @@ int plan(rmat_batch b) {
 
 int run_once(rmat_batch b, void* const* U, bool allow_graph) {
   cudaStream_t main = b->lane_stream[0];
+  RMAT_CHECK(small_prepare(b, U));
   if (!b->warm) {  // first pass outside capture: grows lazy buffers, sets kernel attributes
     RMAT_CHECK(enqueue_all(b, U));
     RMAT_CU(cudaStreamSynchronize(main));
@@ -278,11 +390,25 @@ std::string tune_key(rmat_batch b) {
   std::ostringstream k;
   long long h = 1469598103934665603LL;
   for (const BatchSys& y : b->sys) h = (h ^ (long long)y.N) * 1099511628211LL;
-  k << "prec" << b->precision << "_n" << b->sys.size() << "_h" << (unsigned long long)h;
+  k << "v2_prec" << b->precision << "_n" << b->sys.size() << "_h" << (unsigned long long)h;
   return k.str();
 }
 
-bool cache_lookup(const std::string& key, int* lanes, int* split) {
+// The tuned knobs of a batch plan.
+struct Knobs {
+  int lanes, split, small_n, nb_lane, nb_serial, tc_bn;
+};
+
+void apply_knobs(rmat_batch b, const Knobs& k) {
+  b->lanes = k.lanes;
+  b->split_n = k.split;
+  b->small_n = k.small_n;
+  b->nb_lane = k.nb_lane;
+  b->nb_serial = k.nb_serial;
+  b->tc_bn_lane = k.tc_bn;
+}
+
+bool cache_lookup(const std::string& key, Knobs* k) {
   const char* path = std::getenv("RMAT_TUNE_CACHE");
   if (!path) return false;
   std::ifstream f(path);
@@ -290,22 +416,25 @@ bool cache_lookup(const std::string& key, int* lanes, int* split) {
   while (std::getline(f, line)) {
     const size_t p = line.find("\"" + key + "\"");
     if (p == std::string::npos) continue;
-    int l = 0, s = 0;
-    if (std::sscanf(line.c_str() + line.find(':', p) + 1, " {\"lanes\": %d, \"split_n\": %d", &l,
-                    &s) == 2) {
-      *lanes = l;
-      *split = s;
+    Knobs t{};
+    if (std::sscanf(line.c_str() + line.find(':', p) + 1,
+                    " {\"lanes\": %d, \"split_n\": %d, \"small_n\": %d, \"nb_lane\": %d, "
+                    "\"nb_serial\": %d, \"tc_bn\": %d",
+                    &t.lanes, &t.split, &t.small_n, &t.nb_lane, &t.nb_serial, &t.tc_bn) == 6) {
+      *k = t;
       return true;
     }
   }
   return false;
 }
 
-void cache_store(const std::string& key, int lanes, int split, double secs) {
+void cache_store(const std::string& key, const Knobs& k, double secs) {
   const char* path = std::getenv("RMAT_TUNE_CACHE");
   if (!path) return;
   std::ofstream f(path, std::ios::app);
-  f << "{\"" << key << "\": {\"lanes\": " << lanes << ", \"split_n\": " << split
+  f << "{\"" << key << "\": {\"lanes\": " << k.lanes << ", \"split_n\": " << k.split
+    << ", \"small_n\": " << k.small_n << ", \"nb_lane\": " << k.nb_lane
+    << ", \"nb_serial\": " << k.nb_serial << ", \"tc_bn\": " << k.tc_bn
     << ", \"seconds\": " << secs << "}}\n";
 }
 
@@ -334,7 +463,7 @@ int rmat_batch_create(rmat_ctx ctx, int nsys, const rmat_problem* probs, const d
     for (int k = 0; k < p.nch; ++k)
       if (p.zz && !(std::isfinite(p.zz[k]) && p.zz[k] >= 0.0)) return -3;
     if (prec != RMAT_C128 && prec != RMAT_C64_3XTF32_IR && prec != RMAT_C64_SIMT_IR &&
-        prec != RMAT_C64_3XF16_IR)
+        prec != RMAT_C64_3XF16_IR && prec != RMAT_C64_1XF16_IR)
       return -3;
   }
   rmat_batch b = new (std::nothrow) rmat_batch_s();
@@ -462,6 +591,22 @@ int rmat_batch_set(rmat_batch b, int key, long long v) {
     case RMAT_BATCH_GRAPH:
       b->use_graph = v != 0;
       return RMAT_OK;
+    case RMAT_BATCH_SMALL_N:
+      if (v < -1 || v > 100000) return -3;
+      b->small_n = (int)v;
+      break;
+    case RMAT_BATCH_NB_LANE:
+      if (v != 0 && v != 32 && v != 64) return -3;
+      b->nb_lane = (int)v;
+      break;
+    case RMAT_BATCH_NB_SERIAL:
+      if (v != 0 && v != 32 && v != 64 && v != 128) return -3;
+      b->nb_serial = (int)v;
+      break;
+    case RMAT_BATCH_TC_BN:
+      if (v != 0 && v != 128 && v != 256) return -3;
+      b->tc_bn_lane = v == 128 ? 128 : 256;
+      break;
     default:
       return -2;
   }
@@ -473,28 +618,58 @@ int rmat_batch_tune(rmat_batch b, void* const* U_dev, int* lanes, int* split_n) 
   if (!b) return -1;
   if (!U_dev) return -2;
   const std::string key = tune_key(b);
-  int bl = b->lanes, bs = b->split_n;
-  if (!cache_lookup(key, &bl, &bs)) {
-    const int cand[][2] = {{0, 0}, {8, 1024}, {8, 8192}, {16, 1024}, {16, 8192}};
-    double best = INFINITY;
-    for (const auto& cd : cand) {
-      b->lanes = cd[0];
-      b->split_n = cd[1];
+  Knobs best{b->lanes, b->split_n, b->small_n, b->nb_lane, b->nb_serial, b->tc_bn_lane};
+  if (!cache_lookup(key, &best)) {
+    // coordinate descent, each candidate plan timed on the batch itself: first the
+    // lane / split plan, then the small-system class, then the LU block widths (the
+    // tile shapes of the panels, U12 solves and tensor-core updates) of the lanes and
+    // of the serial systems
+    double tbest = INFINITY;
+    auto trial = [&](const Knobs& k) -> int {
+      apply_knobs(b, k);
       RMAT_CHECK(plan(b));
       const double t = time_run(b, U_dev);
-      if (t < best) {
-        best = t;
-        bl = cd[0];
-        bs = cd[1];
+      if (t < tbest) {
+        tbest = t;
+        best = k;
+      }
+      return RMAT_OK;
+    };
+    const int cand[][2] = {{0, 0}, {8, 1024}, {8, 8192}, {16, 1024}, {16, 8192}};
+    for (const auto& cd : cand) RMAT_CHECK(trial({cd[0], cd[1], -1, 0, 0, 256}));
+    {
+      Knobs k = best;
+      k.small_n = 0;
+      RMAT_CHECK(trial(k));
+    }
+    {
+      const Knobs base = best;
+      for (int nb : {32, 64}) {
+        Knobs k = base;
+        k.nb_lane = nb;
+        RMAT_CHECK(trial(k));
       }
     }
-    cache_store(key, bl, bs, best);
+    if (rmat_tensor_prec(b->precision) && best.lanes > 0) {
+      Knobs k = best;
+      k.tc_bn = 128;
+      RMAT_CHECK(trial(k));
+    }
+    {
+      const Knobs base = best;
+      for (int nb : {32, 64, 128})
+        if (!(b->precision == RMAT_C128 && nb == 128)) {
+          Knobs k = base;
+          k.nb_serial = nb;
+          RMAT_CHECK(trial(k));
+        }
+    }
+    cache_store(key, best, tbest);
   }
-  b->lanes = bl;
-  b->split_n = bs;
+  apply_knobs(b, best);
   RMAT_CHECK(plan(b));
-  if (lanes) *lanes = bl;
-  if (split_n) *split_n = bs;
+  if (lanes) *lanes = best.lanes;
+  if (split_n) *split_n = best.split;
   return RMAT_OK;
 }
 
@@ -534,8 +709,10 @@ int rmat_batch_info(rmat_batch b, long long* out, int n) {
   long long launches = 0;
   for (int l = 0; l <= MAX_LANES; ++l)
     if (b->lane_ctx[l]) launches += b->lane_ctx[l]->launches;
-  const long long v[5] = {(long long)b->sys.size(), b->lanes, b->split_n, b->graph_ok, launches};
-  const int m = std::min(n, 5);
+  const long long v[10] = {(long long)b->sys.size(), b->lanes, b->split_n, b->graph_ok, launches,
+                           (long long)b->small_idx.size(), b->small_n, b->nb_lane, b->nb_serial,
+                           b->tc_bn_lane};
+  const int m = std::min(n, 10);
   for (int k = 0; k < m; ++k) out[k] = v[k];
   return m;
 }
@@ -555,6 +732,11 @@ int rmat_batch_destroy(rmat_batch b) {
     cudaFree(t.r);
     cudaFree(t.fa);
   }
+  cudaFree(b->small_dev);
+  cudaFree(b->small_next);
+  cudaFree(b->small_scr.X);
+  cudaFree(b->small_scr.R);
+  cudaFree(b->small_scr.coll);
   cudaFree(b->l_all);
   cudaFree(b->th_all);
   cudaFree(b->zz_all);

@@ -16,165 +16,28 @@
 // but in a single CTA: R contraction, channel functions, the matching system,
 // Gaussian elimination with partial pivoting (largest |Re|+|Im|, first row on
 // ties) carrying the right-hand sides, and back substitution.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
-#include "cplx.cuh"
-#include "rmat_internal.h"
-#include "special.cuh"
+#include "collision_cta.cuh"
 
 namespace {
 
-constexpr int MAXC = RMAT_NOALLOC_MAX_NCH;
-constexpr int NA_THREADS = 256;
-
-struct NoallocScratch {
-  double2 R[MAXC * MAXC];   // R-matrix, row-major
-  double2 ZO[MAXC * MAXC];  // matching matrix diag O - R~ diag O'
-  double2 ZI[MAXC * MAXC];  // right-hand sides diag I - R~ diag I' (open columns)
-  double2 I[MAXC], O[MAXC], dI[MAXC], dO[MAXC];
-  double k[MAXC];
-  int status;               // 0 ok, 1 + column of an exactly zero pivot,
-                            // -(1 + channel) for a channel function that did not converge
-};
-
 // Scratch shared by every call on this device (contents persist between calls).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
-
-struct NoallocParams {
-  int nch, nlag, nopen, ldx;
-  double a, hm, B, E;
-  int l[MAXC];
-  double thresh[MAXC];
-  double zz[MAXC];
-  int open[MAXC];
-};
 
 __global__ void __launch_bounds__(NA_THREADS)
 collision_noalloc_kernel(const NoallocParams p, const double* __restrict__ fa,
                          const double2* __restrict__ X, double2* __restrict__ Rout,
                          double2* __restrict__ Uout, NoallocScratch* __restrict__ S) {
-  const int tid = threadIdx.x;
-  const int nch = p.nch, no = p.nopen;
-  __shared__ int s_piv;
-  if (tid == 0) S->status = 0;  // must start at zero on every call
-  // R[al][be] = (hm/a) sum_i f_i(a) X[(al,i), be]   (X column-major, ld = ldx)
-  for (int e = tid; e < nch * nch; e += NA_THREADS) {
-    const int al = e / nch, be = e % nch;
-    double sr = 0.0, si = 0.0;
-    for (int i = 0; i < p.nlag; ++i) {
-      const double2 x = X[(size_t)al * p.nlag + i + (size_t)p.ldx * be];
-      sr = fma(fa[i], x.x, sr);
-      si = fma(fa[i], x.y, si);
-    }
-    const double2 r = make_double2(p.hm / p.a * sr, p.hm / p.a * si);
-    S->R[e] = r;
-    if (Rout) Rout[al + (size_t)nch * be] = r;
-  }
-  __syncthreads();  // status cleared before any channel can report
-  // channel functions at rho = k a
-  for (int ch = tid; ch < nch; ch += NA_THREADS) {
-    double2 I, O, dI, dO;
-    double k;
-    if (!channel_functions(p.l[ch], p.E - p.thresh[ch], p.hm, p.a, p.B, p.zz[ch], &I, &O, &dI,
-                           &dO, &k))
-      S->status = -(1 + ch);
-    S->I[ch] = I;
-    S->O[ch] = O;
-    S->dI[ch] = dI;
-    S->dO[ch] = dO;
-    S->k[ch] = k;
-  }
-  __syncthreads();
-  // matching system (every entry written, nothing relies on earlier contents)
-  for (int e = tid; e < nch * (nch + no); e += NA_THREADS) {
-    const int row = e / (nch + no), col = e % (nch + no);
-    const int cp = col < nch ? col : p.open[col - nch];
-    const double2 R = S->R[row * nch + cp];
-    const double s = p.a * sqrt(S->k[row]) * sqrt(S->k[cp]);
-    const double2 Rt = make_double2(s * R.x, s * R.y);
-    const double2 f = col < nch ? S->dO[cp] : S->dI[cp];
-    double2 z = cmul<double>(Rt, f);
-    z.x = -z.x;
-    z.y = -z.y;
-    if (row == cp) {
-      const double2 d = col < nch ? S->O[row] : S->I[row];
-      z.x += d.x;
-      z.y += d.y;
-    }
-    if (col < nch) S->ZO[row * nch + col] = z;
-    else S->ZI[row * no + (col - nch)] = z;
-  }
-  __syncthreads();
-  // Gaussian elimination with partial pivoting, right-hand sides carried along
-  for (int j = 0; j < nch; ++j) {
-    if (tid < 32) {
-      double best = -1.0;
-      int bi = nch;
-      for (int r = j + tid; r < nch; r += 32) {
-        const double m = cabs1<double>(S->ZO[r * nch + j]);
-        if (m > best) { best = m; bi = r; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (tid == 0) {
-        s_piv = bi;
-        if (!(best > 0.0) && S->status == 0) S->status = j + 1;
-      }
-    }
-    __syncthreads();
-    const int pv = s_piv;
-    if (pv != j && pv < nch) {
-      for (int c = tid; c < nch + no; c += NA_THREADS) {
-        double2* a = c < nch ? &S->ZO[j * nch + c] : &S->ZI[j * no + (c - nch)];
-        double2* b = c < nch ? &S->ZO[pv * nch + c] : &S->ZI[pv * no + (c - nch)];
-        const double2 t = *a;
-        *a = *b;
-        *b = t;
-      }
-    }
-    __syncthreads();
-    const double2 piv = S->ZO[j * nch + j];
-    if (piv.x != 0.0 || piv.y != 0.0) {
-      const int rows = nch - j - 1, cols = nch - j - 1 + no;
-      for (int e = tid; e < rows * cols; e += NA_THREADS) {
-        const int r = j + 1 + e / cols, cc = e % cols;
-        const double2 lm = cdiv<double>(S->ZO[r * nch + j], piv);
-        if (cc < nch - j - 1) {
-          const int c = j + 1 + cc;
-          csub_mul<double>(S->ZO[r * nch + c], lm, S->ZO[j * nch + c]);
-        } else {
-          const int c = cc - (nch - j - 1);
-          csub_mul<double>(S->ZI[r * no + c], lm, S->ZI[j * no + c]);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  // back substitution on the open columns
-  for (int j = nch - 1; j >= 0; --j) {
-    const double2 d = S->ZO[j * nch + j];
-    for (int c = tid; c < no; c += NA_THREADS)
-      if (d.x != 0.0 || d.y != 0.0) S->ZI[j * no + c] = cdiv<double>(S->ZI[j * no + c], d);
-    __syncthreads();
-    for (int e = tid; e < j * no; e += NA_THREADS) {
-      const int r = e / no, c = e % no;
-      csub_mul<double>(S->ZI[r * no + c], S->ZO[r * nch + j], S->ZI[j * no + c]);
-    }
-    __syncthreads();
-  }
-  // U(q, q2) = Ufull[open[q]][q2], column-major nopen x nopen
-  for (int e = tid; e < no * no; e += NA_THREADS) {
-    const int q = e % no, q2 = e / no;
-    Uout[e] = S->ZI[p.open[q] * no + q2];
-  }
+  matching_cta(p, fa, X, 1, (size_t)p.ldx, Rout, Uout, S);  // X column-major, ld = ldx
 }
 
-// Device address of the scratch array, looked up once per device.
-void* g_scratch_ptr[64] = {nullptr};
+// Device address of the scratch array, looked up once per device (the first call
+// with that device current).  A cudaDeviceReset reloads the module and may move
+// the array: the cached address then no longer belongs to it.
+std::atomic<void*> g_scratch_ptr[64];
 
 }  // namespace
 
@@ -182,11 +45,14 @@ extern "C" int rmat_collision_noalloc(const rmat_problem* prob, double E, const 
                                       const void* X_dev, int ldx, void* R_dev, void* U_dev,
                                       int* nopen, void* stream) {
   if (!prob || prob->nch < 1 || prob->nch > RMAT_NOALLOC_MAX_NCH || prob->nlag < 1 ||
-      !(prob->a > 0) || !(prob->hm > 0) || !prob->l || !prob->thresh)
+      !(prob->a > 0) || !(prob->hm > 0) || !std::isfinite(prob->a) || !std::isfinite(prob->hm) ||
+      !std::isfinite(prob->bloch_B) || !prob->l || !prob->thresh)
     return -1;
   for (int c = 0; c < prob->nch; ++c)
-    if (prob->zz && !(std::isfinite(prob->zz[c]) && prob->zz[c] >= 0.0)) return -1;
-  if (!(E == E)) return -2;
+    if (!std::isfinite(prob->thresh[c]) ||
+        (prob->zz && !(std::isfinite(prob->zz[c]) && prob->zz[c] >= 0.0)))
+      return -1;
+  if (!std::isfinite(E)) return -2;
   if (!f_a_dev) return -3;
   if (!X_dev) return -4;
   if (ldx < prob->nch * prob->nlag) return -5;
@@ -212,27 +78,26 @@ extern "C" int rmat_collision_noalloc(const rmat_problem* prob, double E, const 
   if (nopen) *nopen = no;
   if (no > 0 && !U_dev) return -7;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RMAT_ECUDA;
-  if (!g_scratch_ptr[dev]) {
+  RMAT_CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return RMAT_ECUDA;
+  void* ptr = g_scratch_ptr[dev].load();
+  if (!ptr) {
     // first call on this device: resolve the scratch array's device address
     // (the host-side symbol is only a stand-in and must not reach a kernel)
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return RMAT_ECUDA;
-    }
-    g_scratch_ptr[dev] = ptr;
+    RMAT_CU(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    if (!ptr) return RMAT_ECUDA;
+    g_scratch_ptr[dev].store(ptr);
   }
-  NoallocScratch* S = reinterpret_cast<NoallocScratch*>(g_scratch_ptr[dev]);
+  NoallocScratch* S = reinterpret_cast<NoallocScratch*>(ptr);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // an earlier, unrelated launch error must not be reported as ours
   collision_noalloc_kernel<<<1, NA_THREADS, 0, st>>>(
       p, reinterpret_cast<const double*>(f_a_dev), reinterpret_cast<const double2*>(X_dev),
       reinterpret_cast<double2*>(R_dev), reinterpret_cast<double2*>(U_dev), S);
-  if (cudaGetLastError() != cudaSuccess) return RMAT_ECUDA;
+  RMAT_CU(cudaGetLastError());
   int status = 0;
-  if (cudaMemcpyAsync(&status, &S->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return RMAT_ECUDA;
+  RMAT_CU(cudaMemcpyAsync(&status, &S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RMAT_CU(cudaStreamSynchronize(st));
   if (status < 0) return RMAT_ECHANFN;
   return status ? RMAT_ESINGULAR : RMAT_OK;
 }

@@ -43,6 +43,19 @@ __device__ __forceinline__ double2 to_c(double2 z, double) { return z; }
 __device__ __forceinline__ double2 to_d(float2 z) { return make_double2((double)z.x, (double)z.y); }
 __device__ __forceinline__ double2 to_d(double2 z) { return z; }
 
+// Compensated accumulation (Ogita, Rump, Oishi 2005, Dot2): s + c carries the sum of
+// the exact products as if accumulated in twice the working precision; each product
+// is split exactly by FMA (TwoProd), each addition by TwoSum.  The _rn intrinsics keep
+// the compiler from contracting the transformations into FMAs.
+__device__ __forceinline__ void dot2_add(double& s, double& c, double a, double b) {
+  const double p = __dmul_rn(a, b);
+  const double e = fma(a, b, -p);
+  const double t = __dadd_rn(s, p);
+  const double z = __dsub_rn(t, s);
+  c = __dadd_rn(c, __dadd_rn(__dadd_rn(__dsub_rn(s, __dsub_rn(t, z)), __dsub_rn(p, z)), e));
+  s = t;
+}
+
 // Relaxed-ordering loads that bypass L1 (data written by other CTAs).
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;

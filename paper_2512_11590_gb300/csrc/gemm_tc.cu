@@ -26,6 +26,7 @@
 #include <cstring>
 
 #include "rmat_internal.h"
+#include "tc_common.cuh"
 
 namespace {
 
@@ -44,7 +45,6 @@ struct TcCfg {
   static constexpr int NBUF = 512 / (2 * BN);                         // accumulator sets
   static constexpr size_t SMEM = (size_t)TC_STAGES * STAGE + 2 * STAGING_BYTES + 1024 + 256;
 };
-constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
 
 struct TcMaps {
   CUtensorMap a[4];  // A operand planes: re_hi, re_lo, im_hi, im_lo
@@ -52,134 +52,13 @@ struct TcMaps {
   CUtensorMap c;     // output C viewed as fp32 [rows][2*cols], reduce-add target
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait on an mbarrier phase; false on timeout or when another role aborted.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 255) == 0) {
-      if (*abort_flag) return false;
-      if (gtimer() - t0 > TC_WAIT_NS) return false;
-    }
-  }
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-// K-major operand, 32-byte rows, SWIZZLE_32B: 8-row groups 256 B apart.
-__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
-  d |= (uint64_t)1 << 16;                   // leading byte offset (unused when K fits the atom)
-  d |= (uint64_t)(256 >> 4) << 32;          // stride byte offset
-  d |= (uint64_t)1 << 46;                   // descriptor version (tcgen05)
-  d |= (uint64_t)6 << 61;                   // layout: SWIZZLE_32B
-  return d;
-}
-// Instruction descriptor: D f32, A/B K-major, N = BN, M = 128; operand format
-// TF32 (code 2, kind::tf32) or F16 (code 0, kind::f16).
-template <int BN, int KIND>
-__host__ __device__ constexpr uint32_t idesc_mma(bool negA) {
-  return (1u << 4)                                 // D format f32
-         | ((KIND == 0 ? 2u : 0u) << 7)            // A format
-         | ((KIND == 0 ? 2u : 0u) << 10)           // B format
-         | ((negA ? 1u : 0u) << 13)
-         | ((uint32_t)(BN >> 3) << 17)
-         | ((uint32_t)(TC_BM >> 4) << 24);
-}
-template <int KIND>
-__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
-                                          uint32_t accumulate) {
-  if constexpr (KIND == 0)
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
-  else
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   bar)
-               : "memory");
-}
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
-}
-__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
-  asm volatile(
-      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::
-          "l"(reinterpret_cast<uint64_t>(map)),
-      "r"(x), "r"(y), "r"(src)
-      : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read1() {
-  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void epi_bar() {  // the 128 epilogue threads only
   asm volatile("bar.sync 1, 128;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+template <int BN, int KIND>
+__host__ __device__ constexpr uint32_t idesc_mma(bool negA) {
+  return idesc_tc<TC_BM, BN, KIND>(negA);
 }
-
 // Product p of the 12 per K-step (p = 6*acc + 3*part + t):
 //   acc 0 (re): part 0 Ar*Br, part 1 -Ai*Bi;  acc 1 (im): part 0 Ar*Bi, part 1 Ai*Br
 //   t: 0 hi*hi, 1 hi*lo, 2 lo*hi.   Planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo.
@@ -202,11 +81,14 @@ struct TcScales {
   const int* skip;  // nonzero *skip: the launch does nothing (a stopped refinement)
 };
 
-template <int BN, int KIND>
+// NPROD = 3: the split products hi*hi, hi*lo, lo*hi (12 MMAs per K-step); NPROD = 1:
+// hi*hi only (4 MMAs), and only the hi planes are loaded.
+template <int BN, int KIND, int NPROD>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, int Nn, int K,
                  int ax0, int rowA0, int bx0, int rowB0, TcScales sc, int* __restrict__ err) {
   using Cfg = TcCfg<BN>;
+  static_assert(NPROD == 1 || NPROD == 3, "one or three split products");
   constexpr int KSTEP = KIND == 0 ? 8 : 16;  // K elements per 32-byte operand row
   if (sc.skip && *sc.skip) return;           // before any barrier or TMEM allocation
   constexpr uint32_t B_PLANE_BYTES = Cfg::B_PLANE, STAGE_BYTES = Cfg::STAGE;
@@ -262,13 +144,13 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
           const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
           if (!mbar_wait(smem_u32(&bars[4 + s]), ph ^ 1, abort_flag)) { ok = false; break; }
           const uint32_t full = smem_u32(&bars[s]);
-          mbar_expect_tx(full, STAGE_BYTES);
+          mbar_expect_tx(full, NPROD == 3 ? STAGE_BYTES : STAGE_BYTES / 2);
           const uint32_t st = smem_u32(stages + s * STAGE_BYTES);
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
+          for (int q = 0; q < 4; q += (NPROD == 3 ? 1 : 2))
             tma_load_2d(st + q * A_PLANE_BYTES, &maps.a[q], ax0 + ks * KSTEP, rowA0 + m0, full);
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
+          for (int q = 0; q < 4; q += (NPROD == 3 ? 1 : 2))
             tma_load_2d(st + 4 * A_PLANE_BYTES + q * B_PLANE_BYTES, &maps.b[q], bx0 + ks * KSTEP,
                         rowB0 + n0, full);
         }
@@ -281,7 +163,7 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
       for (uint32_t k = (it > TC_STAGES ? it - TC_STAGES : 0); k < it; ++k) {
         const unsigned long long t0 = gtimer();
         while (!mbar_try(smem_u32(&bars[k % TC_STAGES]), (k / TC_STAGES) & 1))
-          if (gtimer() - t0 > TC_WAIT_NS) break;
+          if (gtimer() - t0 > RMAT_TC_WAIT_NS) break;
       }
     }
   } else if (warp == 1) {
@@ -306,6 +188,7 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
           const uint32_t st = smem_u32(stages + s * STAGE_BYTES);
 #pragma unroll
           for (int p = 0; p < 12; ++p) {
+            if (NPROD == 1 && p % 3 != 0) continue;  // hi*hi only
             int qa, qb, acc, neg;
             product(p, qa, qb, acc, neg);
             const uint64_t ad = sdesc_sw32(st + qa * A_PLANE_BYTES);
@@ -327,7 +210,7 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
         mma_commit(smem_u32(&bars[8 + 2 * buf]));
         const unsigned long long t0 = gtimer();
         while (!mbar_try(smem_u32(&bars[8 + 2 * buf]), use & 1))
-          if (gtimer() - t0 > TC_WAIT_NS) break;
+          if (gtimer() - t0 > RMAT_TC_WAIT_NS) break;
       }
     }
   } else {
@@ -457,6 +340,15 @@ int make_plane_map(CUtensorMap* m, void* base, int fmt, int cols, int rows, int 
   return r == CUDA_SUCCESS ? RMAT_OK : RMAT_ECUDA;
 }
 
+}  // namespace
+
+int tc_make_plane_map_f16(CUtensorMap* m, void* base, int cols, int rows, int row_stride,
+                          int box_rows) {
+  return make_plane_map(m, base, 1, cols, rows, row_stride, box_rows);
+}
+
+namespace {
+
 // Tensor maps of the three operand sources, rebuilt when a buffer or size changes:
 //   F  full-size split factor planes, row-major [n][ldf]  (A operand; columns
 //      limited to n, so K padding beyond the matrix reads zeros)
@@ -470,8 +362,9 @@ struct TcCache {
   const void* bw = nullptr;
   int n = -1, ldf = -1, nrhs = -1, fmt = -1;
   TcMaps upd, sol[2];  // trailing update (BN = 256), solve update (BN = 128) per Y buffer
+  TcMaps upd128;       // trailing update with 128-wide tiles (RMAT_PARAM_TC_BN = 128)
 };
-bool g_tc_attr[2][2] = {{false, false}, {false, false}};
+bool g_tc_attr[2][2][2] = {};
 
 // The cache lives with its context (contexts may run concurrently on separate streams).
 TcCache& tc_cache(rmat_ctx c) {
@@ -479,17 +372,17 @@ TcCache& tc_cache(rmat_ctx c) {
   return *reinterpret_cast<TcCache*>(c->tc);
 }
 
-template <int BN, int KIND>
+template <int BN, int KIND, int NPROD>
 int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, int K, int ax0,
                 int ay0, int bx0, int by0, const TcScales& sc, bool count_as_update) {
   constexpr int KSTEP = KIND == 0 ? 8 : 16;
   if (M <= 0 || Nn <= 0 || K <= 0) return RMAT_OK;
   if (K % KSTEP || ax0 % KSTEP || bx0 % KSTEP) return RMAT_ESTATE;
   constexpr size_t TC_SMEM = TcCfg<BN>::SMEM;
-  if (!g_tc_attr[BN == 128][KIND]) {
-    RMAT_CU(cudaFuncSetAttribute(tc_update_kernel<BN, KIND>,
+  if (!g_tc_attr[BN == 128][KIND][NPROD == 1]) {
+    RMAT_CU(cudaFuncSetAttribute(tc_update_kernel<BN, KIND, NPROD>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-    g_tc_attr[BN == 128][KIND] = true;
+    g_tc_attr[BN == 128][KIND][NPROD == 1] = true;
   }
   const int tiles = ceil_div(M, TC_BM) * ceil_div(Nn, BN);
   // a far-row update on the solves' look-ahead stream leaves 32 SMs to the next
@@ -502,7 +395,7 @@ int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn,
     e1 = rmat_event(c);
     RMAT_CU(cudaEventRecord(e0, c->stream));
   }
-  tc_update_kernel<BN, KIND><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(
+  tc_update_kernel<BN, KIND, NPROD><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(
       maps, cx0, cy0, M, Nn, K, ax0, ay0, bx0, by0, sc, c->dstat + ST_TIMEOUT);
   c->launches++;
   RMAT_CU(cudaGetLastError());
@@ -522,11 +415,15 @@ int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, i
               int ay0, int bx0, int by0, const TcScales& sc, bool count_as_update) {
   // K beyond the block reads zeros: F columns past n are outside the tensor map and
   // the Y / B planes are zero-filled up to a multiple of 32
-  if (rmat_plane_fmt(c->precision) == 1)
-    return launch_tc_k<BN, 1>(c, maps, cx0, cy0, M, Nn, (int)round_up(K, 16), ax0, ay0, bx0, by0,
-                              sc, count_as_update);
-  return launch_tc_k<BN, 0>(c, maps, cx0, cy0, M, Nn, (int)round_up(K, 8), ax0, ay0, bx0, by0, sc,
-                            count_as_update);
+  if (rmat_plane_fmt(c->precision) == 1) {
+    if (count_as_update && rmat_update_products(c->precision) == 1)  // factor updates only
+        return launch_tc_k<BN, 1, 1>(c, maps, cx0, cy0, M, Nn, (int)round_up(K, 16), ax0, ay0, bx0,
+                                     by0, sc, count_as_update);
+    return launch_tc_k<BN, 1, 3>(c, maps, cx0, cy0, M, Nn, (int)round_up(K, 16), ax0, ay0, bx0, by0,
+                                 sc, count_as_update);
+  }
+  return launch_tc_k<BN, 0, 3>(c, maps, cx0, cy0, M, Nn, (int)round_up(K, 8), ax0, ay0, bx0, by0,
+                               sc, count_as_update);
 }
 
 }  // namespace
@@ -548,6 +445,9 @@ int tc_prepare(rmat_ctx c, int n, int nrhs) {
     RMAT_CHECK(make_plane_map(&g_tc.upd.a[q], F + q * fplane, fmt, n, n, ldf, TC_BM));
     RMAT_CHECK(make_plane_map(&g_tc.upd.b[q], Bp + q * bplane, fmt, RMAT_MAX_NB, n, RMAT_MAX_NB,
                               TC_BN));
+    g_tc.upd128.a[q] = g_tc.upd.a[q];
+    RMAT_CHECK(make_plane_map(&g_tc.upd128.b[q], Bp + q * bplane, fmt, RMAT_MAX_NB, n, RMAT_MAX_NB,
+                              128));
     for (int u = 0; u < 2; ++u) {
       g_tc.sol[u].a[q] = g_tc.upd.a[q];
       RMAT_CHECK(make_plane_map(&g_tc.sol[u].b[q], Y + (4 * u + q) * yplane, fmt, RMAT_MAX_NB,
@@ -555,6 +455,7 @@ int tc_prepare(rmat_ctx c, int n, int nrhs) {
     }
   }
   RMAT_CHECK(make_out_map(&g_tc.upd.c, c->C, n, n, c->ld));
+  g_tc.upd128.c = g_tc.upd.c;
   RMAT_CHECK(make_out_map(&g_tc.sol[0].c, c->Bw, std::max(2, nrhs), n, std::max(2, nrhs)));
   g_tc.sol[1].c = g_tc.sol[0].c;
   g_tc.f = c->Fpl;
@@ -578,6 +479,9 @@ int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n) {
   TcCache& g_tc = tc_cache(c);
   TcScales sc{nullptr, 1, nullptr, nullptr, nullptr};
   if (rmat_plane_fmt(c->precision) == 1) sc.cscal = c->uscale + k0 / jb;  // jb = nb here
+  if (c->tc_bn == 128)
+    return launch_tc<128>(c, g_tc.upd128, k0 + jb, k0 + jb, rest, rest, jb, k0, k0 + jb, 0, k0 + jb,
+                          sc, true);
   return launch_tc<TC_BN>(c, g_tc.upd, k0 + jb, k0 + jb, rest, rest, jb, k0, k0 + jb, 0, k0 + jb,
                           sc, true);
 }
@@ -591,6 +495,8 @@ int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, in
   RMAT_CHECK(tc_prepare(c, n, c->nrhs + (c->nrhs & 1)));
   TcCache& g_tc = tc_cache(c);
   TcScales sc{nullptr, 1, nullptr, rmat_plane_fmt(c->precision) == 1 ? cscal : nullptr, nullptr};
+  if (c->tc_bn == 128)
+    return launch_tc<128>(c, g_tc.upd128, col0, row0, M, ncols, K, ax0, row0, 0, col0, sc, true);
   return launch_tc<TC_BN>(c, g_tc.upd, col0, row0, M, ncols, K, ax0, row0, 0, col0, sc, true);
 }
 

@@ -1235,8 +1235,9 @@ size_t perm_smem(int nb) {
 }
 
 // ---- FP64 complex GEMM C -= A B (row-major) on the FP64 tensor instruction ------
-// mma.sync.m8n8k4.f64 (tcgen05 has no f64 kind): the complex product as four real
-// products (-Ai*Bi through a negated copy of the Ai fragment).  64 x 64 output tile per
+// mma.sync.m8n8k4.f64 (tcgen05 has no f64 kind): the complex product as three real
+// products (3M): T1 = Ar Br, T2 = Ai Bi, T3 = (Ar + Ai)(Br + Bi), Re = T1 - T2,
+// Im = T3 - T1 - T2, the operand sums formed in registers.  64 x 64 output tile per
 // CTA, 16-deep K chunks staged as separate real / imaginary [k][64] planes (row pitch
 // 72 doubles: a fragment load's 4 k-rows x 8 entries hit distinct bank slots); each of
 // the 8 warps owns 32 x 16 (4 x 2 tiles of 8 x 8).
@@ -1259,11 +1260,13 @@ zgemm_sub_dmma_kernel(int M, int N, int K, const double2* __restrict__ A, int ld
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wm = (warp >> 2) * 32, wn = (warp & 3) * 16;
   const int g = lane >> 2, t = lane & 3;
-  double accr[4][2][2], acci[4][2][2];
+  double t1[4][2][2], t2[4][2][2], t3[4][2][2];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 2; ++q) accr[p][q][0] = accr[p][q][1] = acci[p][q][0] = acci[p][q][1] = 0.0;
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) t1[p][q][h] = t2[p][q][h] = t3[p][q][h] = 0.0;
   for (int k0 = 0; k0 < K; k0 += ZG_K) {
     for (int e = threadIdx.x; e < ZG_T * ZG_K; e += 256) {
       const int kk = e & (ZG_K - 1), mm = e >> 4;
@@ -1280,26 +1283,26 @@ zgemm_sub_dmma_kernel(int M, int N, int K, const double2* __restrict__ A, int ld
     __syncthreads();
 #pragma unroll
     for (int k4 = 0; k4 < ZG_K; k4 += 4) {
-      double ar[4], ai[4], an[4], br[2], bi[2];
+      double ar[4], ai[4], as[4], br[2], bi[2], bs[2];
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         ar[p] = Ar[k4 + t][wm + 8 * p + g];
         ai[p] = Am[k4 + t][wm + 8 * p + g];
-        an[p] = -ai[p];
+        as[p] = ar[p] + ai[p];
       }
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         br[q] = Br[k4 + t][wn + 8 * q + g];
         bi[q] = Bm[k4 + t][wn + 8 * q + g];
+        bs[q] = br[q] + bi[q];
       }
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          dmma_acc(accr[p][q][0], accr[p][q][1], ar[p], br[q]);
-          dmma_acc(accr[p][q][0], accr[p][q][1], an[p], bi[q]);
-          dmma_acc(acci[p][q][0], acci[p][q][1], ar[p], bi[q]);
-          dmma_acc(acci[p][q][0], acci[p][q][1], ai[p], br[q]);
+          dmma_acc(t1[p][q][0], t1[p][q][1], ar[p], br[q]);
+          dmma_acc(t2[p][q][0], t2[p][q][1], ai[p], bi[q]);
+          dmma_acc(t3[p][q][0], t3[p][q][1], as[p], bs[q]);
         }
     }
     __syncthreads();
@@ -1316,8 +1319,8 @@ zgemm_sub_dmma_kernel(int M, int N, int K, const double2* __restrict__ A, int ld
         if (gn >= N) continue;
         double2* cp = C + (size_t)gm * ldc + gn;
         double2 v = *cp;
-        v.x -= accr[p][q][h];
-        v.y -= acci[p][q][h];
+        v.x -= t1[p][q][h] - t2[p][q][h];
+        v.y -= t3[p][q][h] - t1[p][q][h] - t2[p][q][h];
         *cp = v;
       }
   }

@@ -38,10 +38,45 @@ struct LUPerm {
   size_t cap = 0;  // bytes
 };
 
+// Refinement stopping rule at the FP64 floor: u = 2^-53; a residual is at the floor
+// when max|r| <= RMAT_FLOOR_CONV u (max|C||X| + max|Phi|) (the floor of a correctly
+// rounded solution is ~0.1-0.2 u on the config-3 family; a plain FP64 LU solve sits
+// near 1 u).  Once the floor has been seen, one last correction is applied and the
+// loop stops without the residual that would only confirm the floor.  A stalled
+// refinement counts as converged below RMAT_FLOOR_STALL u.
+#define RMAT_U64 1.1102230246251565e-16
+#define RMAT_FLOOR_CONV 0.5
+#define RMAT_FLOOR_STALL 2.0
+static inline int rmat_floor_need(int) { return 1; }
+
 // State of a device-driven refinement loop (graph-capturable solve).
 struct IrState {
   double prev, rel;
-  int stagn, done, status, iters;
+  int stagn, done, status, iters, floor_hits, final;
+};
+
+// One system of a batch's small-system class (batch_small.cu): device pointers.
+struct SmallSys {
+  int nch, nlag, N, nopen;
+  int sys;                      // index in the batch (status, refinement count)
+  double hm, a, B, E, phi_max;
+  const double2* V;             // cpot(nlag, nch, nch) of the system
+  const double* K;              // hm T0 - hm (B/a) f f^T of its mesh, nlag x nlag
+  const double* r;              // mesh points
+  const double* fa;             // f_i(a)
+  const int* l;
+  const double* th;
+  const double* zz;
+  const int* open;
+  double2* U;                   // column-major nopen x nopen output (null when nopen = 0)
+};
+// Per-CTA scratch of the small-system kernel: FP64 X and r (slot doubles2 each) and
+// the matching system of collision_cta.cuh.
+struct SmallScratch {
+  double2* X;
+  double2* R;
+  size_t slot;
+  void* coll;
 };
 
 // Device status words written by kernels (read back by the host).
@@ -144,6 +179,8 @@ struct rmat_ctx_s {
   cudaEvent_t la_ev[4] = {};       // fork / join events of the look-ahead
   double* Dsc = nullptr;   size_t Dsc_cap = 0;      // equilibration scale per row
   std::vector<double> ir_hist;                      // refinement history of the last solve
+  double ir_berr = 0.0;  // last max|r| / (max|C||X| + max|Phi|) of the last solve
+  double2* Xs = nullptr;   size_t Xs_cap = 0;       // rmat_residual's row-major copy of X
   double2* Rint = nullptr; size_t Rint_cap = 0;     // R-matrix (row-major nch x nch)
   double2* Zbuf = nullptr; size_t Zbuf_cap = 0;     // matching system (nch x nch + nch x nopen)
   int* zpiv = nullptr;     size_t zpiv_cap = 0;
@@ -156,6 +193,13 @@ struct rmat_ctx_s {
 
   bool assembled = false, factored = false, solved = false;
   void* tc = nullptr;      // tensor-map cache of this context (gemm_tc.cu)
+  void* oz = nullptr;      // tensor-core FP64 residual state (resid_oz.cu)
+  // RMAT_PARAM_RESIDUAL: 0 auto (tensor-core coupling product from nch >= 32),
+  // 1 FP64 tensor instruction (mma.m8n8k4.f64), 2 tensor-core digit slices
+  int resid_param = 0;
+  int tc_bn = 256;         // tile width of the factor's tensor-core updates (RMAT_PARAM_TC_BN)
+  int resid_comp = -1;     // compensated kinetic sums (RMAT_PARAM_RESID_SUMS; -1 = complex128 only)
+  long long wpt_gen = 0;   // bumped whenever the point-coupling table is rewritten
   // CUDA graph of one complete solve (both sweeps), captured on first use and replayed
   // by every later solve with the same sizes, buffers and factor layout
   cudaGraphExec_t sg_exec = nullptr;
@@ -227,6 +271,18 @@ int launch_x_out(rmat_ctx c, double2* Xo, int ldx);
 int launch_absmax(rmat_ctx c, const double2* v, size_t n);
 int launch_update(rmat_ctx c, const IrState* st = nullptr);
 int launch_ir_init(rmat_ctx c, IrState* st);
+int launch_absprod(rmat_ctx c);
+size_t small_coll_scratch_bytes();
+size_t small_smem_bytes(int precision, int N, int nch);
+int launch_batch_small(cudaStream_t st, int precision, const SmallSys* sys, int nsmall, int* next,
+                       int grid, size_t smem, int max_refine, double tol, int* st_all,
+                       IrState* ir_all, const SmallScratch& scr);
+bool oz_enabled(rmat_ctx c);
+int structured_residual(rmat_ctx c, const double2* Xin, double2* Rout, const int* skip);
+int launch_to_colmajor(rmat_ctx c, const double2* src, double2* dst, int ld);
+int launch_from_colmajor(rmat_ctx c, const double2* src, int ld, double2* dst);
+int launch_oz_coupling(rmat_ctx c, const double2* Xin, double2* Rout, const int* skip);
+void oz_release(rmat_ctx c);
 int launch_ir_state(rmat_ctx c, double tol, int patience, int last, IrState* st);
 // api.cu: solve + refinement enqueued without host synchronisation (fixed step
 // budget, device-side stopping rule); X stays in the context's FP64 buffer.
@@ -281,9 +337,16 @@ struct KTimer {
 };
 
 // Tensor-core operand planes: format 0 = TF32 hi/lo held in fp32 words, 1 = FP16 hi/lo.
-static inline bool rmat_tensor_prec(int p) { return p == RMAT_C64_3XTF32_IR || p == RMAT_C64_3XF16_IR; }
-static inline int rmat_plane_fmt(int p) { return p == RMAT_C64_3XF16_IR ? 1 : 0; }
-static inline size_t rmat_plane_esz(int p) { return p == RMAT_C64_3XF16_IR ? 2 : 4; }
+static inline bool rmat_tensor_prec(int p) {
+  return p == RMAT_C64_3XTF32_IR || p == RMAT_C64_3XF16_IR || p == RMAT_C64_1XF16_IR;
+}
+static inline int rmat_plane_fmt(int p) {
+  return (p == RMAT_C64_3XF16_IR || p == RMAT_C64_1XF16_IR) ? 1 : 0;
+}
+static inline size_t rmat_plane_esz(int p) { return rmat_plane_fmt(p) == 1 ? 2 : 4; }
+// split products per real product in the factor's trailing updates (the solves' block
+// updates always take three)
+static inline int rmat_update_products(int p) { return p == RMAT_C64_1XF16_IR ? 1 : 3; }
 // current Y-plane buffer and its column scales
 static inline void* rmat_ypl_cur(rmat_ctx c) {
   return reinterpret_cast<char*>(c->Ypl) +

@@ -1,14 +1,23 @@
 """Full-size parity (-m gpu): the systems the bench times (config 3, N = 25600, and its
 worse-conditioned variant W = -1) and the complex128 path at the config-2 sweep sizes.
 
-The oracle cannot factor N = 25600 in test time, so it checks what it can compute
-at any size, independently of the GPU path:
+Against the oracle's truth at N = 25600 (tests/golden/truth_config3_W*_n25600.txt,
+written by tests/golden/make_truth_n25600.py from the oracle alone: LAPACK factors
+of the dense C plus double-double structured-residual refinement): X, R and U of
+both the split-FP16 + FP64-refinement path and the complex128 path, on the stored
+samples, element by element.
+
+The oracle cannot factor N = 25600 in test time, so the other tests check what it
+can compute at any size, independently of the GPU path:
   * the residual Phi - C X of the GPU's X, formed by the oracle's structured product
     (block structure of C, complex128): the FP64 floor of max|r|/max|Phi| is ~1e-12;
   * R from the GPU's X by the oracle's contraction, and U from the GPU's R by the
     oracle's matching: the R and U steps pinned at full size;
   * U symmetric (C complex symmetric).
 """
+import os
+import sys
+
 import numpy as np
 import pytest
 
@@ -17,6 +26,9 @@ from oracle.collision import collision_matrix, r_matrix
 from oracle.mesh import lagrange_mesh
 from oracle.system import structured_residual, surface_rhs
 from rmat_gpu import relerr, run_problem
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+from make_truth_n25600 import load_truth, sampled_relerr  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -68,3 +80,28 @@ def test_config2_sweep_complex128(ctx, nch):
     p = cp.config2(nch)
     out = run_problem(ctx, p, g.RMAT_C128, max_refine=30, tol=1e-13)
     check_against_oracle(p, out, 2e-11)
+
+
+# Bounds against the N = 25600 truth: U to 1e-12 (FP64 path) and 1e-10 (after
+# mixed-precision refinement), the targets for U; X and R are held to the same bounds.
+TRUTH_TOL = {"c128": 1e-12, "f16": 1e-10}
+
+
+@pytest.mark.parametrize("W", [-10.0, -1.0])
+@pytest.mark.parametrize("path", ["f16", "c128"])
+def test_config3_full_size_against_truth(ctx, W, path):
+    import paper_2512_11590_gb300 as g
+    t = load_truth(W)
+    p = cp.config3(256, W=W)
+    prec = g.RMAT_C64_3XF16_IR if path == "f16" else g.RMAT_C128
+    out = run_problem(ctx, p, prec, max_refine=30, tol=1e-13)
+    assert out["nopen"] == t["nopen"]
+    eX = sampled_relerr(out["X"], t, "X")
+    eR = sampled_relerr(out["R"], t, "R")
+    eU = sampled_relerr(out["U"], t, "U")
+    print(f"N=25600 W={W:g} {path}: status {out['status']} corrections {out['iters']} "
+          f"X {eX:.2e} R {eR:.2e} U {eU:.2e}")
+    assert out["status"] == g.RMAT_OK
+    assert eU < TRUTH_TOL[path]
+    assert eR < TRUTH_TOL[path]
+    assert eX < TRUTH_TOL[path]

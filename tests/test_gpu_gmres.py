@@ -74,3 +74,19 @@ def test_refine_param_range(g, ctx):
     for bad in (-1, 65):
         with pytest.raises(g.RmatError):
             g.rmat_set_param(ctx, g.RMAT_PARAM_REFINE, bad)
+
+
+@pytest.mark.parametrize("case", ["config1", "nch16"])
+def test_single_product_factor_under_gmres_ir(g, ctx, case):
+    """RMAT_C64_1XF16_IR: the factor's trailing updates take one FP16 product (a third
+    of the tensor work), so the factors are only ~u_16 cond(C) accurate; as the
+    preconditioner of GMRES-IR they still give X, R, U at the refined bounds."""
+    p = cp.config1() if case == "config1" else cp.config3(16)
+    ref = oracle_solve(p, refine_steps=3)
+    g.rmat_set_param(ctx, g.RMAT_PARAM_REFINE, 64)
+    out = run_problem(ctx, p, g.RMAT_C64_1XF16_IR, max_refine=20, tol=1e-14)
+    inner = g.rmat_get_stats(ctx)["gmres_inner"]
+    print(f"1xF16 + GMRES-IR {case}: status {out['status']} outer {out['iters']} inner {inner:.0f}")
+    assert out["status"] == g.RMAT_OK
+    for k in ("X", "R", "U"):
+        assert relerr(out[k], ref[k]) < 1e-10, k

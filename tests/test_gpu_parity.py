@@ -159,10 +159,13 @@ def test_equilibration_switch(g, ctx, equil, prec):
     try:
         out = run_problem(ctx, p, prec, max_refine=40, tol=1e-14)
         hist = g.rmat_refine_history(ctx)
+        berr = g.rmat_get_stats(ctx)["backward_error"]
     finally:
         g.rmat_set_param(ctx, g.RMAT_PARAM_EQUILIBRATE, -1)
     assert relerr(out["U"], ref["U"]) < TOL[prec]
-    assert len(hist) == out["iters"] + 1 and hist[-1] < 1e-11
+    # stopped at the FP64 floor: one correction after the floor-level residual
+    assert out["status"] == g.RMAT_OK and berr <= 0.5 * 2.0 ** -53
+    assert len(hist) == out["iters"]
 
 
 @pytest.mark.parametrize("scale_a,scale_b", [(1e7, 1e-12), (1e-6, 1e9)])
@@ -241,3 +244,33 @@ def test_solve_lookahead_vs_oracle(g, prec):
     for k in ("U", "R", "X"):
         e = relerr(out[k], ref[k])
         assert e < TOL[prec], (k, e)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_refinement_stops_at_fp64_floor(g, ctx, prec):
+    """The refinement ends with RMAT_OK at the FP64 floor: once the normwise backward
+    error max|r| / (max|C||X| + max|Phi|) is at most u/2 (u = 2^-53; the correctly
+    rounded solution itself sits at 0.1-0.2 u on this family, measured by the oracle)
+    one last correction is applied and no confirming residual is formed.  X, R, U are
+    then at the truth's bounds."""
+    p = cp.config3(16)
+    ref = truth(p, "c3-16")
+    out = run_problem(ctx, p, prec, max_refine=30, tol=1e-14)
+    berr = g.rmat_get_stats(ctx)["backward_error"]
+    u = 2.0 ** -53
+    assert out["status"] == g.RMAT_OK, (out["status"], berr / u)
+    assert berr <= 0.5 * u
+    hist = g.rmat_refine_history(ctx)
+    assert len(hist) == out["iters"]
+    for k in ("U", "R", "X"):
+        assert relerr(out[k], ref[k]) < TOL[prec], k
+
+
+def test_refinement_reports_stagnation_above_floor(g, ctx):
+    """kappa = 1e10 with complex64 factors: classical refinement stalls far above the
+    FP64 floor and says so (RMAT_ENOCONV, backward error > 2u)."""
+    A, B, _ = cp.prescribed_kappa_hermitian(7, 512, 1e10, nrhs=3)
+    out = run_dense(ctx, A, B, 2, max_refine=20, tol=1e-14)
+    berr = g.rmat_get_stats(ctx)["backward_error"]
+    assert out["status"] == g.RMAT_ENOCONV
+    assert berr > 2.0 * 2.0 ** -53
