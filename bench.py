@@ -222,7 +222,8 @@ def workload(args):
 class Runner:
     """One system on one GPU through the C ABI (device-resident buffers)."""
 
-    def __init__(self, p, precision, device, method=0, lookahead=0, residual=0):
+    def __init__(self, p, precision, device, method=0, lookahead=0, residual=0, solve_block=0,
+                 factor=0):
         import torch
 
         import cc_problems as cp
@@ -233,6 +234,8 @@ class Runner:
         g.rmat_set_param(self.ctx, g.RMAT_PARAM_METHOD, method)
         g.rmat_set_param(self.ctx, g.RMAT_PARAM_SOLVE_LOOKAHEAD, lookahead)
         g.rmat_set_param(self.ctx, g.RMAT_PARAM_RESIDUAL, residual)
+        g.rmat_set_param(self.ctx, g.RMAT_PARAM_SOLVE_BLOCK, solve_block)
+        g.rmat_set_param(self.ctx, g.RMAT_PARAM_FACTOR, factor)
         m = g.rmat_mesh(p.nlag, p.a)
         self.V_host = cp.potential_at(p, m["r"]).ravel()
         self.Vd = torch.from_numpy(self.V_host).cuda()
@@ -399,7 +402,7 @@ def reference_main(args):
     return 0
 
 
-def profile_step(nch, precision, warm=True, method=0):
+def profile_step(nch, precision, warm=True, method=0, factor=0):
     """Launch sequence for ncu: the warm-up step uses the SIMT precision, so the
     first tensor-core launch of the run is the first trailing update at N = nch*100."""
     import torch
@@ -411,7 +414,7 @@ def profile_step(nch, precision, warm=True, method=0):
         w = Runner(cp.config3(16), g.RMAT_C64_SIMT_IR, 0)
         w.step()
         w.close()
-    run = Runner(cp.config3(nch), precision, 0, method)
+    run = Runner(cp.config3(nch), precision, 0, method, factor=factor)
     run.step()
     torch.cuda.synchronize()
     print("profile step", nch, run.last)
@@ -457,6 +460,14 @@ def batch_run(args, nsys, steps, warmup, precision):
         g.rmat_batch_set(b, g.RMAT_BATCH_LANES, lanes)
         g.rmat_batch_set(b, g.RMAT_BATCH_SPLIT_N, split)
     else:
+        # the autotuner's cache: plans tuned on GB300 ship with the package (a copy, so
+        # that new entries do not touch it); a workload without an entry is timed here
+        if "RMAT_TUNE_CACHE" not in os.environ:
+            import shutil
+            import tempfile
+            tmp = os.path.join(tempfile.mkdtemp(prefix="rmat_tune_"), "plans.jsonl")
+            shutil.copy(os.path.join(ROOT, "paper_2512_11590_gb300", "tuned_plans.jsonl"), tmp)
+            os.environ["RMAT_TUNE_CACHE"] = tmp
         lanes, split = g.rmat_batch_tune(b, Uptr)
     tune_s = time.perf_counter() - t0
     for _ in range(warmup):
@@ -507,7 +518,8 @@ def batch_run(args, nsys, steps, warmup, precision):
                        "lanes": lanes, "split_n": split, "graph": info.get("graph"),
                        "plan": {k: info.get(k) for k in ("small_systems", "small_n", "nb_lane",
                                                          "nb_serial", "tc_bn_lane")},
-                       "tune_s": tune_s, "max_refine": args.batch_refine},
+                       "tune_s": tune_s, "tune_cache": os.environ.get("RMAT_TUNE_CACHE"),
+                       "max_refine": args.batch_refine},
             "tflops": flops / (ms * 1e-3) / 1e12,
             "loop": {"ms_per_step": ms_loop, "systems_per_s": len(probs) / (ms_loop * 1e-3),
                      "speedup_batch_over_loop": ms_loop / ms, "u_rel_diff_batch_vs_loop": diff},
@@ -745,8 +757,13 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the complex128 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tf32", action="store_true", help="skip the 3xTF32 comparison leg")
+    ap.add_argument("--factor", default="lu", choices=["lu", "ldlt"],
+                    help="main line's factorisation: LU with partial pivoting or LDL^T")
+    ap.add_argument("--no-ldlt", action="store_true", help="skip the LDL^T comparison leg")
     ap.add_argument("--residual", default="auto", choices=["auto", "fp64mma", "tensor"],
                     help="point-coupling product of the FP64 residual (RMAT_PARAM_RESIDUAL)")
+    ap.add_argument("--solve-block", type=int, default=0, choices=[0, 128, 256],
+                    help="rows per tensor-path solve step (RMAT_PARAM_SOLVE_BLOCK; 0 = 256)")
     ap.add_argument("--refine", type=int, default=0,
                     help="GMRES-IR inner steps per correction (RMAT_PARAM_REFINE; 0 classical)")
     ap.add_argument("--no-batch", action="store_true",
@@ -784,7 +801,8 @@ def main():
         import paper_2512_11590_gb300 as g
         return profile_step(args.nch, {"tf32": g.RMAT_C64_3XTF32_IR, "f16": g.RMAT_C64_3XF16_IR,
                                        "simt": g.RMAT_C64_SIMT_IR}[args.precision],
-                            warm=not args.no_warm, method=1 if args.method == "woodbury" else 0)
+                            warm=not args.no_warm, method=1 if args.method == "woodbury" else 0,
+                            factor=1 if args.factor == "ldlt" else 0)
     if args.batch:
         return batch_main(args)
     if args.precision == "c128":
@@ -823,7 +841,9 @@ def main():
             "f16x1": g.RMAT_C64_1XF16_IR, "simt": g.RMAT_C64_SIMT_IR}[args.precision]
     method = 1 if args.method == "woodbury" else 0
     resid = {"auto": 0, "fp64mma": 1, "tensor": 2}[args.residual]
-    run = Runner(p, prec, local, method, 1 if args.lookahead else 0, resid)
+    factor = 1 if args.factor == "ldlt" else 0
+    run = Runner(p, prec, local, method, 1 if args.lookahead else 0, resid, args.solve_block,
+                 factor)
     g.rmat_set_param(run.ctx, g.RMAT_PARAM_REFINE, args.refine)
     with ClockSampler(local) as clk:
         ms, stats, launches = time_steps(run, args.steps, args.warmup, sync_all)
@@ -929,6 +949,53 @@ def main():
         rt.close()
     else:
         tf32_arrays = (None, None, None)
+    ldlt, ldlt_arrays = None, (None, None, None)
+    if prec == g.RMAT_C64_3XF16_IR and factor == 0 and method == 0 and not args.no_ldlt:
+        # the complex-symmetric LDL^T (no pivot panel, half the update) on the same system
+        rl = Runner(p, prec, local, residual=resid, solve_block=args.solve_block, factor=1)
+        rl.step()
+        g.rmat_set_param(rl.ctx, g.RMAT_PARAM_TIMING, 1)
+        g.rmat_reset_counters(rl.ctx)
+        rl.step()
+        torch.cuda.synchronize()
+        st_l = g.rmat_get_stats(rl.ctx)
+        g.rmat_set_param(rl.ctx, g.RMAT_PARAM_TIMING, 0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kl = max(1, min(args.steps, 3))
+        e0.record(rl.stream)
+        for _ in range(kl):
+            rl.step()
+        e1.record(rl.stream)
+        torch.cuda.synchronize()
+        msl = max_over_ranks(e0.elapsed_time(e1) / kl, dist, "cuda")
+        Ul = rl.U_host()
+        Xl, Rl = rl.XR_host()
+        lpk = pk["bf16_tflops_sustained"] / 3.0
+        lach = st_l["tu_flops"] / (st_l["tu_ms"] * 1e-3) / 1e12 if st_l["tu_ms"] > 0 else None
+        ldlt = {"factor": "complex-symmetric LDL^T without pivoting (C = C^T), 3xFP16 updates "
+                          "on the tiles on or above the diagonal",
+                "ms_per_step": msl, "steps": kl,
+                "value_lu_flop_count": replica_throughput(world, flops, msl), "unit": "TFLOP/s",
+                "value_note": "LU's flop count (8N^3/3 + 8N^2 nrhs) over this time: the LDL^T "
+                              "does about half the factor flops",
+                "speedup_vs_main": ms / msl,
+                "refine": dict(rl.last), "ldlt_lmax": st_l.get("ldlt_lmax"),
+                "stage_ms": {k: st_l[k] for k in ("assemble_ms", "factor_ms", "solve_ms",
+                                                   "refine_ms", "collision_ms")},
+                "diag_block_ms": [st_l.get("panel_ms"), st_l.get("panel_launches")],
+                "u_rel_diff_vs_main": float(np.max(np.abs(Ul - U32)) / np.max(np.abs(U32))),
+                "roofline": {"kernel": "symmetric trailing update (upper tiles) C22 -= L21 U12",
+                             "bound": "tensor", "achieved": lach, "peak": lpk, "unit": "TFLOP/s",
+                             "frac": lach / lpk if lach else None,
+                             "peak_source": "bf16 sustained (%s) / 3 (fp16 split products per "
+                                            "fp32 product)" % src,
+                             "flops": "8 K M (M + 128) / 2 per launch (upper triangle and the "
+                                      "diagonal blocks' lower halves)",
+                             "kernel_ms_per_step": st_l["tu_ms"],
+                             "launches": st_l["tu_launches"]}}
+        ldlt_arrays = (Xl, Rl, Ul)
+        rl.close()
     tu_ms, tu_flops, tu_n = stats["tu_ms"], stats["tu_flops"], stats["tu_launches"]
     if prec == g.RMAT_C64_3XTF32_IR:
         # each complex product = 4 real GEMMs x 3 tf32 split products: 12 tensor GEMMs
@@ -983,7 +1050,8 @@ def main():
                     "update at N=6400 (profiles/trailing_update_tc_n6400.md) x this run's "
                     "average algorithmic bytes per launch" % ratio)
     W = getattr(p, "W", -10.0)
-    errs = None if p.N != 25600 else truth_errors(W, {"fp32ir": (X32, R32, U32), "fp64": fp64_arrays, "tf32": tf32_arrays})
+    errs = None if p.N != 25600 else truth_errors(W, {"fp32ir": (X32, R32, U32), "fp64": fp64_arrays,
+                                                      "tf32": tf32_arrays, "ldlt": ldlt_arrays})
     line = {
         "metric": "N=25600 complex solve time & TFLOP/s: FP32+IR vs FP64 at equal U error",
         "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -991,7 +1059,9 @@ def main():
         "vs_baseline": None, "dtype": DTYPES[prec],
         "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "nrhs": p.nch,
+                   "factor": {"lu": "LU with partial pivoting", "ldlt": "LDL^T"}[args.factor],
                    "method": args.method, "residual": args.residual,
+                   "solve_block": args.solve_block or 256,
                    "refinement": ir, "l2": "inputs larger than L2 (C is %.1f GB)" % (p.N * p.N * 8 / 1e9),
                    "lu_block": stats["nb"], "panel_ctas": stats["panel_ctas"],
                    "ms_per_step_best_median": [stats["ms_steps"]["best"],
@@ -1002,6 +1072,7 @@ def main():
                                  for k in ("panel", "apply_inv", "solve_tc", "resid")}},
         "fp64_path": fp64,
         "tf32_path": tf32,
+        "ldlt_path": ldlt,
         "error_vs_truth": errs,
         "stages_roofline": stage_rooflines(stats, p.N, p.nch, int(stats["nb"]), ir["iters"], pk, src),
         "other_method": other,

@@ -140,6 +140,26 @@ extern "C" {
  * by FMA, each addition by TwoSum, r rounded once: as if summed in twice the FP64
  * precision), 0 = FP64 sums, -1 (default) = compensated for RMAT_C128 only. */
 #define RMAT_PARAM_RESID_SUMS 13
+/* Rows per step of the tensor-path triangular solves (block width 128): 256 (0 =
+ * default: the inverses of pairs of diagonal blocks are composed once per
+ * factorisation, half the dependent steps per sweep) or 128.  Takes effect at the
+ * next rmat_factor.  With 256, a classical refinement whose correction fails to
+ * halve the residual switches to 128-row steps for the rest of that factorisation
+ * (composed inverses of ill-conditioned blocks contract too little) instead of
+ * counting a stall. */
+#define RMAT_PARAM_SOLVE_BLOCK 14
+/* Factorisation of the tensor-core precisions (RMAT_C64_3XTF32_IR, RMAT_C64_3XF16_IR,
+ * RMAT_C64_1XF16_IR): 0 (default) = LU with partial pivoting (Sec. 3.1); 1 =
+ * complex-symmetric LDL^T without pivoting, C = L D L^T with U = D L^T: each
+ * diagonal block is factored alone, the multipliers below it are U12^T D11^-1 (C =
+ * C^T for every assembled problem and for a loaded A that is symmetric; a loaded
+ * A that is not gives a wrong factor, which the refinement reports as
+ * RMAT_ENOCONV), and every trailing update keeps only the tiles on or above the
+ * diagonal (half the tensor-core work; no pivot search).  Stable when the diagonal
+ * dominates; the largest multiplier is in rmat_get_stats out[24], and a zero pivot
+ * gives info > 0 as in LU.  The FP64 refinement is unchanged.  Other precisions,
+ * the Woodbury system (RMAT_PARAM_METHOD = 1) and batches always pivot. */
+#define RMAT_PARAM_FACTOR 15
 
 typedef struct rmat_ctx_s* rmat_ctx;
 
@@ -314,9 +334,12 @@ int rmat_propagate(rmat_ctx ctx, const rmat_problem* prob, double E, int ns, con
  *   out[17] / out[18] solve-path tensor-core block update ms / launches,
  *   out[19] / out[20] FP64 residual ms / launches, out[21] GMRES-IR inner steps of the
  *   last rmat_solve, out[22] the last normwise backward error of the last rmat_solve,
- *   max|r| / (max|C||X| + max|Phi|) (0 when no residual was formed)
+ *   max|r| / (max|C||X| + max|Phi|) (0 when no residual was formed),
+ *   out[23] the factorisation of the last rmat_factor (0 LU with partial pivoting,
+ *   1 LDL^T), out[24] its largest multiplier max(|Re|, |Im|) of L below the
+ *   diagonal blocks (LDL^T only; -1 otherwise)
  *   (timers need RMAT_PARAM_TIMING=1; a time is -1 when it was not timed).
- * n: capacity of out; returns the number of values written (<= 23). */
+ * n: capacity of out; returns the number of values written (<= 25). */
 int rmat_get_stats(rmat_ctx ctx, double* out, int n);
 int rmat_reset_counters(rmat_ctx ctx);
 

@@ -46,6 +46,8 @@ RMAT_PARAM_PROP_CONCURRENT = 10  # 1 (default) propagation sectors on concurrent
 RMAT_PARAM_RESIDUAL = 11  # coupling product of the FP64 residual: 0 auto, 1 FP64 MMA, 2 tensor-core digits
 RMAT_PARAM_TC_BN = 12  # tile width of the factor's tensor-core updates: 256 (0) or 128
 RMAT_PARAM_RESID_SUMS = 13  # compensated kinetic residual sums: -1 complex128 only, 0 off, 1 on
+RMAT_PARAM_SOLVE_BLOCK = 14  # rows per tensor-path solve step: 256 (0) or 128
+RMAT_PARAM_FACTOR = 15       # tensor precisions: 0 LU with partial pivoting, 1 LDL^T
 
 RMAT_BATCH_LANES = 1
 RMAT_BATCH_SPLIT_N = 2
@@ -258,7 +260,7 @@ STAT_KEYS = ("N", "nrhs", "nb", "panel_ctas", "launches", "tu_launches", "tu_ms"
              "assemble_ms", "factor_ms", "solve_ms", "refine_ms", "collision_ms",
              "panel_ms", "panel_launches", "apply_inv_ms", "apply_inv_launches",
              "solve_tc_ms", "solve_tc_launches", "resid_ms", "resid_launches", "gmres_inner",
-             "backward_error")
+             "backward_error", "factor_ldlt", "ldlt_lmax")
 
 
 def rmat_get_stats(ctx) -> dict:

@@ -309,7 +309,8 @@ int rmat_destroy(rmat_ctx c) {
                   c->Fpl,  c->Bpl, c->Ypl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
                   c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows, c->Dinv,
                   c->umax, c->uscale, c->ycs, c->pfwd, c->Bt, c->Kinv, c->Kinv32, c->W32, c->Bs,
-                  c->gm_V, c->gm_Z, c->gm_T, c->gm_small, c->faL, c->prop, c->Xs};
+                  c->gm_V, c->gm_Z, c->gm_T, c->gm_small, c->faL, c->prop, c->Xs, c->Dinv2,
+                  c->Pscr};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->hstat) cudaFreeHost(c->hstat);
@@ -371,6 +372,14 @@ int rmat_set_param(rmat_ctx c, int key, long long v) {
     case RMAT_PARAM_RESID_SUMS:
       if (v < -1 || v > 1) return -3;
       c->resid_comp = (int)v;
+      return RMAT_OK;
+    case RMAT_PARAM_SOLVE_BLOCK:
+      if (v != 0 && v != 128 && v != 256) return -3;
+      c->solve_blk = v == 128 ? 128 : 256;
+      return RMAT_OK;
+    case RMAT_PARAM_FACTOR:
+      if (v != 0 && v != 1) return -3;
+      c->factor_kind = (int)v;
       return RMAT_OK;
     default:
       return -2;
@@ -535,12 +544,17 @@ int rmat_factor(rmat_ctx c, int* info) {
   cudaEvent_t e0, e1;
   record_stage(c, &e0);
   const bool tensor = rmat_tensor_prec(c->precision);
+  // LDL^T needs C = C^T: not for the Woodbury system S
+  c->factor_used = (tensor && c->factor_kind == 1 && !(c->woodbury && c->kind == 1)) ? 1 : 0;
   int st;
   if (c->precision == RMAT_C128)
     st = lu_factor_dev<double>(c, c->C, c->N, c->ld, c->ipiv, c->nb, false, c->perm_main);
   else
     st = lu_factor_dev<float>(c, c->C, c->N, c->ld, c->ipiv, c->nb, tensor, c->perm_main);
   if (st != RMAT_OK) return st;
+  if (c->factor_used)  // the LDL^T multipliers' largest entry, for rmat_get_stats
+    RMAT_CU(cudaMemcpyAsync(c->hstat + ST_COUNT + 6, c->dstat + ST_LMAX, sizeof(int),
+                            cudaMemcpyDeviceToHost, c->stream));
   record_stage(c, &e1);
   c->factored = true;
   c->solved = false;
@@ -581,7 +595,7 @@ static int solve_factors(rmat_ctx c) {
       (long long)(uintptr_t)c->Bt, (long long)(uintptr_t)c->pfwd,
       (long long)(uintptr_t)c->perm_main.rows, (long long)(uintptr_t)c->stream,
       (long long)(uintptr_t)c->uscale, (long long)(uintptr_t)c->ycs, c->solve_lookahead,
-      (long long)(uintptr_t)c->side};
+      (long long)(uintptr_t)c->side, c->inv_pairs, (long long)(uintptr_t)c->Dinv2, c->pairs_off};
   if (!c->sg_exec || key != c->sg_key) {
     if (c->sg_exec) {
       cudaGraphExecDestroy(c->sg_exec);
@@ -645,6 +659,12 @@ int enqueue_solve_refine(rmat_ctx c, int max_refine, double tol, IrState* st) {
   return rc;
 }
 
+// Whether the tensor-path solves take 256-row steps over composed pair inverses.
+static bool pairs_in_use(rmat_ctx c) {
+  return c->inv_pairs > 0 && !c->pairs_off && !c->solve_lookahead && c->refine_param == 0 &&
+         rmat_tensor_prec(c->precision);
+}
+
 // First solve and refinement of the factored system; X stays in c->X (FP64,
 // row-major N x nrhs).  *status: RMAT_OK or RMAT_ENOCONV.
 static int solve_refine(rmat_ctx c, int max_refine, double tol, int* iters, double* rel_resid,
@@ -690,6 +710,11 @@ static int solve_refine(rmat_ctx c, int max_refine, double tol, int* iters, doub
       }
       if (floor_hits >= need) {
         final = true;  // at the FP64 floor: one last correction, no confirming residual
+      } else if (rel > 0.5 * prev && pairs_in_use(c)) {
+        // the solves' 256-row steps apply composed inverses of pairs of diagonal
+        // blocks; on ill-conditioned blocks they contract too little: 128-row steps
+        // (the blocks' own inverses) from here on, without counting a stall
+        c->pairs_off = true;
       } else if (rel > 0.5 * prev) {  // no longer contracting above the floor (or diverging)
         if (++stagn >= patience) {
           status = rmax <= RMAT_FLOOR_STALL * RMAT_U64 * scale ? RMAT_OK : RMAT_ENOCONV;
@@ -930,6 +955,12 @@ int rmat_propagate(rmat_ctx c, const rmat_problem* pb, double E, int ns, const d
   return status;
 }
 
+static float lmax_bits(int b) {
+  float f;
+  std::memcpy(&f, &b, sizeof(f));
+  return f;
+}
+
 int rmat_get_stats(rmat_ctx c, double* out, int n) {
   if (!c) return -1;
   if (!out || n < 0) return -2;
@@ -945,7 +976,7 @@ int rmat_get_stats(rmat_ctx c, double* out, int n) {
   };
   for (int k = 0; k < 5; ++k)
     c->stage_ms[k] = elapsed(c->stage_ev[k][0], c->stage_ev[k][1]);
-  const double v[23] = {(double)c->N, (double)c->nrhs, (double)c->nb,
+  const double v[25] = {(double)c->N, (double)c->nrhs, (double)c->nb,
                         (double)panel_ctas_for(c, c->N > 0 ? c->N : 1), (double)c->launches,
                         (double)c->tu_launches, sum(c->tu_events), c->tu_flops, c->stage_ms[0],
                         c->stage_ms[1], c->stage_ms[2], c->stage_ms[3], c->stage_ms[4],
@@ -953,8 +984,9 @@ int rmat_get_stats(rmat_ctx c, double* out, int n) {
                         sum(c->kt_events[KT_APPLY_INV]), (double)c->kt_launches[KT_APPLY_INV],
                         sum(c->kt_events[KT_SOLVE_TC]), (double)c->kt_launches[KT_SOLVE_TC],
                         sum(c->kt_events[KT_RESID]), (double)c->kt_launches[KT_RESID],
-                        (double)c->gm_inner, c->ir_berr};
-  const int m = n < 23 ? n : 23;
+                        (double)c->gm_inner, c->ir_berr, (double)c->factor_used,
+                        c->factor_used ? (double)lmax_bits(c->hstat[ST_COUNT + 6]) : -1.0};
+  const int m = n < 25 ? n : 25;
   for (int k = 0; k < m; ++k) out[k] = v[k];
   return m;
 }

@@ -79,7 +79,37 @@ struct TcScales {
   const float* colscale;
   const float* cscal;
   const int* skip;  // nonzero *skip: the launch does nothing (a stopped refinement)
+  int upper;        // symmetric update (M == Nn, same origin): only the tiles that are not
+                    // strictly below the diagonal (m0 < n0 + BN)
 };
+
+// Tile t of a launch: column-major over the mt x nt tiles, or, for an upper launch,
+// over the tiles with m0 < n0 + BN only.  There column j holds G (j + 1) row tiles
+// (G = BN / TC_BM; the last column may be cut at mt), so the first j columns hold
+// S(j) = G j (j + 1) / 2 tiles and t's column is the largest j with S(j) <= t.
+template <int BN>
+__device__ __forceinline__ int upper_cum(int j) {
+  return (BN / 128) * j * (j + 1) / 2;
+}
+template <int BN>
+__device__ __forceinline__ int tile_count(int mt, int nt, int upper) {
+  if (!upper) return mt * nt;
+  return upper_cum<BN>(nt - 1) + min(mt, (BN / 128) * nt);
+}
+template <int BN>
+__device__ __forceinline__ void tile_coords(int t, int mt, int nt, int upper, int& m0, int& n0) {
+  if (!upper) {
+    m0 = (t % mt) * 128;
+    n0 = (t / mt) * BN;
+    return;
+  }
+  int j = (int)((sqrtf(8.f * (float)t / (float)(BN / 128) + 1.f) - 1.f) * 0.5f);
+  j = max(0, min(j, nt - 1));
+  while (j > 0 && upper_cum<BN>(j) > t) --j;
+  while (j + 1 < nt && upper_cum<BN>(j + 1) <= t) ++j;
+  m0 = (t - upper_cum<BN>(j)) * 128;
+  n0 = j * BN;
+}
 
 // NPROD = 3: the split products hi*hi, hi*lo, lo*hi (12 MMAs per K-step); NPROD = 1:
 // hi*hi only (4 MMAs), and only the hi planes are loaded.
@@ -107,7 +137,8 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mt = (M + TC_BM - 1) / TC_BM;
   const int nt = (Nn + BN - 1) / BN;
-  const int ntiles = mt * nt;
+  static_assert(TC_BM == 128 && BN % TC_BM == 0, "tile_coords assumes 128-row tiles");
+  const int ntiles = tile_count<BN>(mt, nt, sc.upper);
   const int ksteps = K / KSTEP;
 
   if (threadIdx.x == 0) {
@@ -139,7 +170,8 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
       uint32_t it = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int m0 = (tile % mt) * TC_BM, n0 = (tile / mt) * BN;
+        int m0, n0;
+        tile_coords<BN>(tile, mt, nt, sc.upper, m0, n0);
         for (int ks = 0; ks < ksteps; ++ks, ++it) {
           const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
           if (!mbar_wait(smem_u32(&bars[4 + s]), ph ^ 1, abort_flag)) { ok = false; break; }
@@ -223,7 +255,8 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
     const bool leader = (warp == 2 && lane == 0);
     uint32_t tcount = 0, chunk = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
-      const int m0 = (tile % mt) * TC_BM, n0 = (tile / mt) * BN;
+      int m0, n0;
+      tile_coords<BN>(tile, mt, nt, sc.upper, m0, n0);
       const uint32_t buf = tcount % NBUF, use = tcount / NBUF;
       // The four epilogue warps leave together (they share named barriers): each
       // waits (bounded), then one thread snapshots the abort flag for all.
@@ -384,7 +417,10 @@ int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     g_tc_attr[BN == 128][KIND][NPROD == 1] = true;
   }
-  const int tiles = ceil_div(M, TC_BM) * ceil_div(Nn, BN);
+  if (sc.upper && (M != Nn || cx0 != cy0)) return RMAT_ESTATE;
+  const int mt = ceil_div(M, TC_BM), nt = ceil_div(Nn, BN);
+  const int tiles =
+      sc.upper ? (BN / TC_BM) * (nt - 1) * nt / 2 + std::min(mt, (BN / TC_BM) * nt) : mt * nt;
   // a far-row update on the solves' look-ahead stream leaves 32 SMs to the next
   // block's diagonal application (one TC CTA fills an SM's shared memory)
   const int cap = (c->side && c->stream == c->side) ? std::max(1, c->sm_count - 32) : c->sm_count;
@@ -405,7 +441,9 @@ int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn,
       c->tu_events.push_back({e0, e1});
     }
     c->tu_launches++;
-    c->tu_flops += 8.0 * M * (double)Nn * K;
+    // a symmetric update's algorithmic work: the upper triangle and the lower halves
+    // of the 128-row diagonal blocks the next factorisation steps read
+    c->tu_flops += sc.upper ? 8.0 * K * (double)M * (M + TC_BM) / 2 : 8.0 * M * (double)Nn * K;
   }
   return RMAT_OK;
 }
@@ -471,13 +509,15 @@ int tc_prepare(rmat_ctx c, int n, int nrhs) {
 }
 
 // Factor update: C22 -= L21 U12, A = F planes at (x = k0, y = k0+jb), B = U12^T planes.
-int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n) {
+// upper: C22 is complex symmetric and only its tiles on or above the diagonal are
+// kept (the LDL^T factorisation reads the rest as the transpose).
+int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n, bool upper) {
   const int rest = n - k0 - jb;
   if (rest <= 0) return RMAT_OK;
   if (reinterpret_cast<void*>(A) != c->C || ld != c->ld) return RMAT_ESTATE;
   RMAT_CHECK(tc_prepare(c, n, c->nrhs + (c->nrhs & 1)));
   TcCache& g_tc = tc_cache(c);
-  TcScales sc{nullptr, 1, nullptr, nullptr, nullptr};
+  TcScales sc{nullptr, 1, nullptr, nullptr, nullptr, upper ? 1 : 0};
   if (rmat_plane_fmt(c->precision) == 1) sc.cscal = c->uscale + k0 / jb;  // jb = nb here
   if (c->tc_bn == 128)
     return launch_tc<128>(c, g_tc.upd128, k0 + jb, k0 + jb, rest, rest, jb, k0, k0 + jb, 0, k0 + jb,

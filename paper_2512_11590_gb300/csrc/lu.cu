@@ -561,6 +561,91 @@ __global__ void split_l21_kernel(const float2* __restrict__ A, int ld, int k0, i
     put4(F, fplane, (size_t)r * ldf + k0 + t, A[(size_t)r * ld + k0 + t], fmt, 1.f);
 }
 
+// ---- complex-symmetric LDL^T without pivoting (C = C^T, Sec. 2) ----------------
+// The jb x jb diagonal block factored in one CTA in shared memory: unit lower L11
+// below the diagonal, U11 = D11 L11^T on and above it (the unpivoted LU of the
+// block), identity interchanges.  Column j: multipliers l_i = a_ij / a_jj, then the
+// rank-1 update of the block right of and below (j, j); each thread keeps one column
+// and a stride of rows.  A zero pivot is recorded in stat[ST_INFO] (first column,
+// 1-based) and its column left as it is.
+template <class T>
+__global__ void __launch_bounds__(512)
+diag_nopiv_kernel(cplx<T>* __restrict__ A, int ld, int k0, int jb, int* __restrict__ ipiv,
+                  int* __restrict__ stat) {
+  using C2 = cplx<T>;
+  extern __shared__ unsigned char smem_raw[];
+  C2* s = reinterpret_cast<C2*>(smem_raw);  // [jb][jb + 1]
+  const int ls = jb + 1, tid = threadIdx.x;
+  C2* D = A + (size_t)k0 * ld + k0;
+  for (int e = tid; e < jb * jb; e += blockDim.x) {
+    const int r = e / jb, cc = e - r * jb;
+    s[r * ls + cc] = D[(size_t)r * ld + cc];
+  }
+  for (int e = tid; e < jb; e += blockDim.x) ipiv[k0 + e] = k0 + e;
+  __syncthreads();
+  const int rg = blockDim.x / jb, col = tid % jb, r0 = tid / jb;
+  for (int j = 0; j < jb - 1; ++j) {
+    const C2 piv = s[j * ls + j];
+    const bool zero = piv.x == (T)0 && piv.y == (T)0;
+    if (zero) {
+      if (tid == 0) atomicCAS(&stat[ST_INFO], 0, k0 + j + 1);
+      continue;  // uniform: every thread reads the same pivot
+    }
+    for (int i = j + 1 + tid; i < jb; i += blockDim.x) s[i * ls + j] = cdiv<T>(s[i * ls + j], piv);
+    __syncthreads();
+    if (r0 < rg && col > j) {
+      const C2 u = s[j * ls + col];
+      for (int i = j + 1 + r0; i < jb; i += rg) csub_mul<T>(s[i * ls + col], s[i * ls + j], u);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const C2 last = s[(jb - 1) * ls + jb - 1];
+    if (last.x == (T)0 && last.y == (T)0) atomicCAS(&stat[ST_INFO], 0, k0 + jb);
+  }
+  for (int e = tid; e < jb * jb; e += blockDim.x) {
+    const int r = e / jb, cc = e - r * jb;
+    D[(size_t)r * ld + cc] = s[r * ls + cc];
+  }
+}
+
+// L21 = C21 U11^-1 = (L11 U12)^T U11^-1 = U12^T D11^-1, since C21 = C12^T and
+// U11 = D11 L11^T:  L21[r][j] = U12[j][r] / U11[j][j], written into A's block column
+// below the diagonal block (rows k0+jb.., columns k0..k0+jb-1).  32 x 32 tiles
+// through shared memory (rows of U12 read and rows of L21 written coalesced).  The
+// largest max(|Re|, |Im|) of L21 goes to *lmax (the element growth the unpivoted
+// factor shows; float bits).
+__global__ void __launch_bounds__(256)
+l21_from_u12_kernel(float2* __restrict__ A, int ld, int k0, int jb, int n,
+                    unsigned* __restrict__ lmax) {
+  __shared__ float2 tile[32][33];
+  __shared__ float2 dinv[32];
+  const int r0 = k0 + jb + blockIdx.x * 32, j0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (threadIdx.x < 32) {
+    const int j = j0 + threadIdx.x;
+    float2 d = j < jb ? A[(size_t)(k0 + j) * ld + k0 + j] : make_float2(0.f, 0.f);
+    dinv[threadIdx.x] = (d.x == 0.f && d.y == 0.f) ? make_float2(0.f, 0.f)
+                                                   : cdiv<float>(make_float2(1.f, 0.f), d);
+  }
+  for (int t = ty; t < 32; t += 8) {  // tile[j][r] = U12[j0 + t][r0 + tx]
+    const int j = j0 + t, r = r0 + tx;
+    tile[t][tx] = (j < jb && r < n) ? A[(size_t)(k0 + j) * ld + r] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float m = 0.f;
+  for (int t = ty; t < 32; t += 8) {  // L21[r0 + t][j0 + tx]
+    const int r = r0 + t, j = j0 + tx;
+    if (r < n && j < jb) {
+      const float2 l = cmul<float>(tile[tx][t], dinv[tx]);
+      A[(size_t)r * ld + k0 + j] = l;
+      m = fmaxf(m, cmaxabs(l));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (tx == 0 && m > 0.f) atomicMax(lmax, __float_as_uint(m));
+}
+
 // max(|Re|, |Im|) over rows k0..k0+jb-1, columns c0..c0+ncols-1 of A -> atomicMax on
 // the float bits in *out (non-negative floats order like their bit patterns).
 __global__ void __launch_bounds__(256)
@@ -1589,6 +1674,119 @@ int invert_diag_blocks(rmat_ctx c, const float2* A, int ld, int n, int nb, bool 
   return RMAT_OK;
 }
 
+// ---- 256-row solve steps ----------------------------------------------------
+// The inverses of pairs of 128-row diagonal blocks, for solve sweeps of half as many
+// dependent steps:
+//   [L1 0; L21 L2]^-1 = [L1^-1 0; -L2^-1 L21 L1^-1  L2^-1],
+//   [U1 U12; 0 U2]^-1 = [U1^-1  -U1^-1 U12 U2^-1; 0 U2^-1],
+// from the 128-row inverses already formed, L21 from the factor planes (final row
+// order, hi + lo), U12 from C (rows of a block are final after its own panel).
+
+namespace {
+
+// Scratch blocks of pair q: L21 and U12 (128 x 128 each), the diagonal sub-blocks of
+// both 256-row inverses, zeros above / below them.
+template <class E>
+__global__ void __launch_bounds__(256)
+pair_gather_kernel(const float2* __restrict__ A, int ld, const E* __restrict__ F, int ldf,
+                   size_t fplane, const float2* __restrict__ Linv, const float2* __restrict__ Uinv,
+                   float2* __restrict__ L21, float2* __restrict__ U12, float2* __restrict__ L2,
+                   float2* __restrict__ U2) {
+  constexpr int H = 128, P = 256;
+  const int q = blockIdx.y;
+  const size_t k0 = (size_t)q * P;
+  for (int e = blockIdx.x * 256 + threadIdx.x; e < H * H; e += gridDim.x * 256) {
+    const int i = e / H, j = e - i * H;
+    const size_t fo = (k0 + H + i) * ldf + k0 + j;
+    L21[(size_t)q * H * H + e] =
+        make_float2((float)F[fo] + (float)F[fplane + fo], (float)F[2 * fplane + fo] + (float)F[3 * fplane + fo]);
+    U12[(size_t)q * H * H + e] = A[(k0 + i) * ld + k0 + H + j];
+    const float2 z = make_float2(0.f, 0.f);
+    float2* l = L2 + (size_t)q * P * P;
+    float2* u = U2 + (size_t)q * P * P;
+    l[(size_t)i * P + j] = Linv[(size_t)(2 * q) * H * H + e];
+    l[(size_t)(H + i) * P + H + j] = Linv[(size_t)(2 * q + 1) * H * H + e];
+    l[(size_t)i * P + H + j] = z;
+    u[(size_t)i * P + j] = Uinv[(size_t)(2 * q) * H * H + e];
+    u[(size_t)(H + i) * P + H + j] = Uinv[(size_t)(2 * q + 1) * H * H + e];
+    u[(size_t)(H + i) * P + j] = z;
+  }
+}
+
+// Out[b] = alpha A[b] B[b], 128 x 128 x 128 complex64 per b (B staged in shared memory):
+// thread t forms row t / 2, columns 64 (t % 2) .. +63.
+__global__ void __launch_bounds__(256)
+pair_gemm_kernel(const float2* __restrict__ A, size_t sa, const float2* __restrict__ Bm,
+                 size_t sb, float2* __restrict__ Out, size_t so, int ldo, float alpha) {
+  constexpr int H = 128;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Bs = reinterpret_cast<float2*>(smem_raw);
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const float2* Ab = A + (size_t)b * sa;
+  const float2* Bb = Bm + (size_t)b * sb;
+  for (int e = tid; e < H * H; e += 256) Bs[e] = Bb[e];
+  __syncthreads();
+  const int i = tid >> 1, j0 = (tid & 1) * 64;
+  float2 acc[64];
+#pragma unroll
+  for (int jj = 0; jj < 64; ++jj) acc[jj] = make_float2(0.f, 0.f);
+  for (int k = 0; k < H; ++k) {
+    const float2 a = Ab[(size_t)i * H + k];
+#pragma unroll
+    for (int jj = 0; jj < 64; ++jj) cadd_mul<float>(acc[jj], a, Bs[k * H + j0 + jj]);
+  }
+  float2* o = Out + (size_t)b * so + (size_t)i * ldo + j0;
+#pragma unroll
+  for (int jj = 0; jj < 64; ++jj) o[jj] = make_float2(alpha * acc[jj].x, alpha * acc[jj].y);
+}
+
+}  // namespace
+
+// After invert_diag_blocks<128> of a tensor-path factor: the 256-row inverses of every
+// pair of full blocks into c->Dinv2 ([L pairs][256][256], then [U pairs][256][256]).
+int invert_pair_blocks(rmat_ctx c, const float2* A, int ld, int n) {
+  constexpr int H = 128, P = 256;
+  c->inv_pairs = 0;
+  c->pairs_off = false;  // a new factorisation: try the pair steps again
+  const int npairs = c->inv_blocks / 2;
+  if (c->solve_blk == 128 || c->inv_nb != H || npairs == 0 || !c->Fpl) return RMAT_OK;
+  const size_t per = (size_t)P * P, hh = (size_t)H * H;
+  RMAT_CHECK(rmat_grow(c, &c->Dinv2, &c->Dinv2_cap, 2 * per * npairs * sizeof(float2)));
+  RMAT_CHECK(rmat_grow(c, &c->Pscr, &c->Pscr_cap, 3 * hh * npairs * sizeof(float2)));
+  float2* L2 = reinterpret_cast<float2*>(c->Dinv2);
+  float2* U2 = L2 + per * npairs;
+  float2* L21 = reinterpret_cast<float2*>(c->Pscr);
+  float2* U12 = L21 + hh * npairs;
+  float2* T = U12 + hh * npairs;
+  const float2* Linv = reinterpret_cast<const float2*>(c->Dinv);
+  const float2* Uinv = Linv + hh * c->inv_blocks;
+  const size_t fplane = (size_t)n * c->ld;
+  const dim3 gg(16, npairs);
+  if (rmat_plane_fmt(c->precision) == 1)
+    pair_gather_kernel<__half><<<gg, 256, 0, c->stream>>>(
+        A, ld, reinterpret_cast<const __half*>(c->Fpl), c->ld, fplane, Linv, Uinv, L21, U12, L2, U2);
+  else
+    pair_gather_kernel<float><<<gg, 256, 0, c->stream>>>(
+        A, ld, reinterpret_cast<const float*>(c->Fpl), c->ld, fplane, Linv, Uinv, L21, U12, L2, U2);
+  static bool attr = false;
+  const size_t smem = hh * sizeof(float2);
+  if (!attr) {
+    RMAT_CU(cudaFuncSetAttribute(pair_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    attr = true;
+  }
+  // L: T = L21 L1^-1, lower-left = -L2^-1 T;  U: T = U12 U2^-1, upper-right = -U1^-1 T
+  pair_gemm_kernel<<<npairs, 256, smem, c->stream>>>(L21, hh, Linv, 2 * hh, T, hh, H, 1.f);
+  pair_gemm_kernel<<<npairs, 256, smem, c->stream>>>(Linv + hh, 2 * hh, T, hh, L2 + (size_t)H * P,
+                                                     per, P, -1.f);
+  pair_gemm_kernel<<<npairs, 256, smem, c->stream>>>(U12, hh, Uinv + hh, 2 * hh, T, hh, H, 1.f);
+  pair_gemm_kernel<<<npairs, 256, smem, c->stream>>>(Uinv, 2 * hh, T, hh, U2 + H, per, P, -1.f);
+  c->launches += 5;
+  RMAT_CU(cudaGetLastError());
+  c->inv_pairs = npairs;
+  return RMAT_OK;
+}
+
 template <int JB>
 int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb, int ncols,
                      const LUPerm* pm, void* Yp) {
@@ -1597,10 +1795,15 @@ int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb,
   if (!attr) {
     RMAT_CU(cudaFuncSetAttribute(apply_inv_kernel<JB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
+    if (JB / 16 > 8)  // a 16-CTA cluster is beyond the portable size
+      RMAT_CU(cudaFuncSetAttribute(apply_inv_kernel<JB>,
+                                   cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     attr = true;
   }
-  const size_t total = (size_t)JB * JB * c->inv_blocks;
-  const float2* D = reinterpret_cast<const float2*>(c->Dinv) + (upper ? total : 0);
+  // JB = 256: the pair inverses (blocks of 256 rows, table index k0 / 256)
+  const size_t total = (size_t)JB * JB * (JB == 256 ? c->inv_pairs : c->inv_blocks);
+  const float2* D = reinterpret_cast<const float2*>(JB == 256 ? c->Dinv2 : c->Dinv) +
+                    (upper ? total : 0);
   KTimer kt(c, KT_APPLY_INV);
   apply_inv_kernel<JB><<<dim3(ceil_div(ncols, 16), JB / 16), 256, smem, c->stream>>>(
       D, k0, nb, B, ldb, ncols, pm ? pm->rows : nullptr, pm ? pm->src : nullptr,
@@ -1789,6 +1992,7 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
     k0 = far0;
   }
   c->inv_blocks = 0;
+  c->inv_pairs = 0;
   // L11^-1 of every full block is already in place (formed for its U12), except the
   // last block when it has no trailing columns: form it here
   const int nfull = n / nb;
@@ -1798,7 +2002,26 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
   }
   if (nb == 128) RMAT_CHECK(invert_diag_blocks<128>(c, A, ld, n, nb, true));
   if (nb == 64) RMAT_CHECK(invert_diag_blocks<64>(c, A, ld, n, nb, true));
-  return finish_fpl_order(c, n, nb, pm);
+  RMAT_CHECK(finish_fpl_order(c, n, nb, pm));
+  return invert_pair_blocks(c, A, ld, n);
+}
+
+template <class T>
+int launch_diag_nopiv(rmat_ctx c, cplx<T>* A, int ld, int k0, int jb, int* ipiv) {
+  static bool attr = false;
+  const size_t smem = (size_t)jb * (jb + 1) * sizeof(cplx<T>);
+  if (!attr) {
+    RMAT_CU(cudaFuncSetAttribute(diag_nopiv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)max_nb<T>() * (max_nb<T>() + 1) * sizeof(cplx<T>))));
+    attr = true;
+  }
+  if (jb > max_nb<T>()) return RMAT_ESTATE;
+  KTimer kt(c, KT_PANEL);
+  diag_nopiv_kernel<T><<<1, 512, smem, c->stream>>>(A, ld, k0, jb, ipiv, c->dstat);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  kt.end();
+  return RMAT_OK;
 }
 
 template <class T>
@@ -1813,12 +2036,19 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
   const int fmt = rmat_plane_fmt(c->precision);
   if (tensor && fmt == 1)
     RMAT_CU(cudaMemsetAsync(c->umax, 0, (size_t)ceil_div(n, nb) * sizeof(unsigned), c->stream));
+  // complex-symmetric LDL^T without pivoting (tensor-core precisions): no panel, and
+  // the trailing updates keep only the tiles on or above the diagonal
+  const bool ldlt = tensor && sizeof(T) == 4 && c->factor_used == 1;  // set by rmat_factor
+  if (ldlt) RMAT_CU(cudaMemsetAsync(c->dstat + ST_LMAX, 0, sizeof(int), c->stream));
   if constexpr (sizeof(T) == 4)
-    if (tensor && c->paired && 2 * nb <= RMAT_MAX_NB)
+    if (tensor && !ldlt && c->paired && 2 * nb <= RMAT_MAX_NB)
       return factor_pairs_tc(c, reinterpret_cast<float2*>(A), n, ld, ipiv, nb, pm);
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int jb = std::min(nb, n - k0);
-    RMAT_CHECK(launch_panel<T>(c, A, ld, k0, n, jb, ipiv));
+    if (ldlt)
+      RMAT_CHECK(launch_diag_nopiv<T>(c, A, ld, k0, jb, ipiv));
+    else
+      RMAT_CHECK(launch_panel<T>(c, A, ld, k0, n, jb, ipiv));
     const int rest = n - k0 - jb;
     if (rest <= 0) {
       perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt, pm.src,
@@ -1847,6 +2077,12 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
       const float2* Af = reinterpret_cast<const float2*>(A);
       const int kpad = (int)round_up(jb, 32);
       const int blk = k0 / nb;
+      if (ldlt) {  // L21 from U12 (the block column below the diagonal was not updated)
+        l21_from_u12_kernel<<<dim3(ceil_div(rest, 32), ceil_div(jb, 32)), 256, 0, c->stream>>>(
+            reinterpret_cast<float2*>(A), ld, k0, jb, n,
+            reinterpret_cast<unsigned*>(c->dstat + ST_LMAX));
+        c->launches++;
+      }
       if (fmt == 1) {  // the U12 block's scale: max over its entries first
         block_absmax_kernel<<<std::min(c->sm_count * 2, ceil_div((long long)jb * rest, 256)), 256, 0,
                               c->stream>>>(Af, ld, k0, jb, k0 + jb, rest, c->umax + blk, nullptr);
@@ -1860,7 +2096,7 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
           Af, ld, k0, jb, n, c->Fpl, ld, fplane, fmt);
       c->launches += 2;
       RMAT_CU(cudaGetLastError());
-      RMAT_CHECK(launch_trailing_tc(c, reinterpret_cast<float2*>(A), ld, k0, jb, n));
+      RMAT_CHECK(launch_trailing_tc(c, reinterpret_cast<float2*>(A), ld, k0, jb, n, ldlt));
     } else {
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (c->timing) {
@@ -1880,11 +2116,13 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
     }
   }
   c->inv_blocks = 0;
+  c->inv_pairs = 0;
   if (tensor && sizeof(T) == 4) {
     const float2* Af = reinterpret_cast<const float2*>(A);
     if (nb == 128) RMAT_CHECK(invert_diag_blocks<128>(c, Af, ld, n, nb));
     if (nb == 64) RMAT_CHECK(invert_diag_blocks<64>(c, Af, ld, n, nb));
     RMAT_CHECK(finish_fpl_order(c, n, nb, pm));
+    RMAT_CHECK(invert_pair_blocks(c, Af, ld, n));
   }
   return RMAT_OK;
 }
@@ -1942,8 +2180,13 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     return RMAT_OK;
   };
   const bool la_fwd = tc && c->solve_lookahead && fpm == nullptr && c->side;
-  for (int k0 = 0; k0 < n; k0 += nb) {
-    const int jb = std::min(nb, n - k0);
+  // 256-row steps over pairs of blocks with a composed inverse (no look-ahead, rows
+  // pre-gathered)
+  const bool pairs = tc && !c->solve_lookahead && fpm == nullptr && nb == 128 &&
+                     c->inv_nb == nb && c->inv_pairs > 0 && !c->pairs_off;
+  for (int k0 = 0, jb = 0; k0 < n; k0 += jb) {
+    const bool pstep = pairs && k0 % 256 == 0 && k0 / 256 < c->inv_pairs;
+    jb = pstep ? 256 : std::min(nb, n - k0);
     const int b = (k0 / nb) & 1;
     if (tc) {
       RMAT_CHECK(la_wait(b));
@@ -1951,7 +2194,11 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     }
     const bool need_y = tc && n - k0 - jb > 0;
     bool fused = false;
-    if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
+    if (pstep) {
+      RMAT_CHECK(launch_apply_inv<256>(c, false, k0, 256, reinterpret_cast<float2*>(B), ldb, nrhs,
+                                       nullptr, need_y ? rmat_ypl_cur(c) : nullptr));
+      fused = true;
+    } else if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
       float2* Bf = reinterpret_cast<float2*>(B);
       void* Yp = need_y ? rmat_ypl_cur(c) : nullptr;
       if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, false, k0, nb, Bf, ldb, nrhs, fpm, Yp));
@@ -1996,8 +2243,12 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
   // in the forward sweep, the next block being the one above
   const bool la_bwd = tc && c->solve_lookahead && c->side;
   const int last = ((n - 1) / nb) * nb;
-  for (int k0 = last; k0 >= 0; k0 -= nb) {
-    const int jb = std::min(nb, n - k0);
+  for (int kb = last; kb >= 0;) {
+    // a pair step covers this block and the one above when this is a pair's second block
+    const bool pstep = pairs && (kb / nb) % 2 == 1 && (kb / nb) / 2 < c->inv_pairs;
+    const int k0 = pstep ? kb - nb : kb;
+    const int jb = pstep ? 256 : std::min(nb, n - k0);
+    kb = k0 - nb;
     const int b = (k0 / nb) & 1;
     if (tc) {
       RMAT_CHECK(la_wait(b));
@@ -2005,7 +2256,11 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     }
     const bool need_y = tc && k0 > 0;
     bool fused = false;
-    if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
+    if (pstep) {
+      RMAT_CHECK(launch_apply_inv<256>(c, true, k0, 256, reinterpret_cast<float2*>(B), ldb, nrhs,
+                                       nullptr, need_y ? rmat_ypl_cur(c) : nullptr));
+      fused = true;
+    } else if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
       float2* Bf = reinterpret_cast<float2*>(B);
       void* Yp = need_y ? rmat_ypl_cur(c) : nullptr;
       if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, true, k0, nb, Bf, ldb, nrhs, nullptr, Yp));

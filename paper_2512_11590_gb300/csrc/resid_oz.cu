@@ -7,9 +7,9 @@
 //   * every row of W_i (al fixed, the diagonal al' = al excluded: it is applied in
 //     FP64 by the kinetic kernel) is scaled by 2^-e with e such that every |Re|,
 //     |Im| of the row is below 1, and cut into S = 9 signed 6-bit digits:
-//     w 2^-e = sum_s d_s 2^-6(s+1), |d_s| <= 63 (54 bits, exact in FP64 by repeated
-//     multiply-by-64 and truncation); the same for every column of X_i (be fixed)
-//     with its own exponent f;
+//     w 2^-e = sum_s d_s 2^-6(s+1), |d_s| <= 63 (54 bits: bit fields of
+//     floor(|w| 2^(54-e)), the sign of w on every digit); the same for every column
+//     of X_i (be fixed) with its own exponent f;
 //   * a digit product d_p e_q is an integer below 2^12, exact in an FP16 MMA with
 //     FP32 accumulation, and so is a sum of them while it stays below 2^24: with K
 //     terms per real product and two real products per complex part, up to
@@ -44,7 +44,6 @@ namespace {
 
 constexpr int OZ_S = 9;           // digits per operand value
 constexpr int OZ_D = 8;           // digit pairs kept: p + q <= OZ_D
-constexpr double OZ_RADIX = 64.0; // 6 magnitude bits per digit
 constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 16;
 constexpr int OZ_STAGES = 12;
 constexpr int OZ_THREADS = 320;
@@ -65,6 +64,24 @@ struct OzMaps {
   CUtensorMap b;  // X digit planes: rows ((s*2 + part)*nlag + i)*nrhs + be, K = al'
 };
 
+// The nine signed 6-bit digits of v (|v| < 1): the base-64 expansion of |v| cut after
+// 54 bits, every digit with the sign of v (the same digits as repeated multiply-by-64
+// and truncation), taken as bit fields of the integer floor(|v| 2^54) so that only two
+// FP64 operations are spent per value (FP64 is ~2 FMA per clock per SM on this part).
+// sh = 54 - e, sc = 2^sh: |w| 2^sh < 2^54 for the scaled value w 2^-e (sc is only
+// formed when 2^sh is a finite double; rows of values below 2^-970 scale per value).
+__device__ __forceinline__ double oz_scale(int e) { return e >= -960 ? ldexp(1.0, 54 - e) : 0.0; }
+__device__ __forceinline__ void oz_digits(double w, double sc, int e, __half* d) {
+  const double a = sc != 0.0 ? fabs(w) * sc : ldexp(fabs(w), 54 - e);
+  const unsigned long long u = (unsigned long long)a;
+  const bool neg = w < 0.0;
+#pragma unroll
+  for (int s = 0; s < OZ_S; ++s) {
+    const int q = (int)((u >> (6 * (OZ_S - 1 - s))) & 63ull);
+    d[s] = __int2half_rn(neg ? -q : q);
+  }
+}
+
 // One warp per row (i, al) of W: exponent over al' != al, then the digit planes.
 __global__ void __launch_bounds__(256)
 oz_split_w_kernel(const double2* __restrict__ W, int nlag, int nch, int kpad,
@@ -80,22 +97,21 @@ oz_split_w_kernel(const double2* __restrict__ W, int nlag, int nch, int kpad,
   const int e = m > 0.0 ? ilogb(m) + 1 : 0;  // |v| = |w| 2^-e < 1
   if (lane == 0) ew[row] = e;
   const size_t plane = (size_t)nlag * nch * kpad;
+  const double sc = oz_scale(e);
   for (int k = lane; k < kpad; k += 32) {
     double vr = 0.0, vi = 0.0;
     if (k < nch && k != al) {
-      vr = ldexp(w[k].x, -e);
-      vi = ldexp(w[k].y, -e);
+      vr = w[k].x;
+      vi = w[k].y;
     }
     __half* o = Wsl + (size_t)row * kpad + k;
+    __half dr[OZ_S], di[OZ_S];
+    oz_digits(vr, sc, e, dr);
+    oz_digits(vi, sc, e, di);
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
-      vr *= OZ_RADIX;
-      vi *= OZ_RADIX;
-      const double dr = trunc(vr), di = trunc(vi);
-      vr -= dr;
-      vi -= di;
-      o[(size_t)(2 * s) * plane] = __float2half_rn((float)dr);
-      o[(size_t)(2 * s + 1) * plane] = __float2half_rn((float)di);
+      o[(size_t)(2 * s) * plane] = dr[s];
+      o[(size_t)(2 * s + 1) * plane] = di[s];
     }
   }
 }
@@ -110,6 +126,7 @@ oz_split_x_kernel(const double2* __restrict__ X, int nrhs, int nlag, int nch, in
   if (skip && *skip) return;
   __shared__ double red[8][OZ_XT];
   __shared__ int s_f[OZ_XT];
+  __shared__ double s_sc[OZ_XT];
   __shared__ __align__(16) __half dig[OZ_S][2][OZ_XT][OZ_XT + 8];
   const int i = blockIdx.y, b0 = blockIdx.x * OZ_XT;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -126,6 +143,7 @@ oz_split_x_kernel(const double2* __restrict__ X, int nrhs, int nlag, int nch, in
     for (int w = 1; w < 8; ++w) m = fmax(m, red[w][lane]);
     const int f = m > 0.0 ? ilogb(m) + 1 : 0;
     s_f[lane] = f;
+    s_sc[lane] = oz_scale(f);
     if (be < nrhs) fx[(size_t)i * nrhs + be] = f;
   }
   __syncthreads();
@@ -136,18 +154,16 @@ oz_split_x_kernel(const double2* __restrict__ X, int nrhs, int nlag, int nch, in
       double vr = 0.0, vi = 0.0;
       if (ga < nch && be < nrhs) {
         const double2 x = X[((size_t)ga * nlag + i) * nrhs + be];
-        vr = ldexp(x.x, -s_f[lane]);
-        vi = ldexp(x.y, -s_f[lane]);
+        vr = x.x;
+        vi = x.y;
       }
+      __half dr[OZ_S], di[OZ_S];
+      oz_digits(vr, s_sc[lane], s_f[lane], dr);
+      oz_digits(vi, s_sc[lane], s_f[lane], di);
 #pragma unroll
       for (int s = 0; s < OZ_S; ++s) {
-        vr *= OZ_RADIX;
-        vi *= OZ_RADIX;
-        const double dr = trunc(vr), di = trunc(vi);
-        vr -= dr;
-        vi -= di;
-        dig[s][0][lane][a] = __float2half_rn((float)dr);
-        dig[s][1][lane][a] = __float2half_rn((float)di);
+        dig[s][0][lane][a] = dr[s];
+        dig[s][1][lane][a] = di[s];
       }
     }
     __syncthreads();

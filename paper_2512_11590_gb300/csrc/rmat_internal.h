@@ -80,7 +80,7 @@ struct SmallScratch {
 };
 
 // Device status words written by kernels (read back by the host).
-enum { ST_INFO = 0, ST_TIMEOUT = 1, ST_BADARG = 2, ST_CHANFN = 3, ST_COUNT = 8 };
+enum { ST_INFO = 0, ST_TIMEOUT = 1, ST_BADARG = 2, ST_CHANFN = 3, ST_LMAX = 4, ST_COUNT = 8 };
 
 struct rmat_ctx_s {
   int device = 0;
@@ -162,6 +162,11 @@ struct rmat_ctx_s {
   void* Fpl = nullptr;     size_t Fpl_cap = 0;      // full-size split factor planes [4][N][ld] (A operand)
   void* Ypl = nullptr;     size_t Ypl_cap = 0;
   void* Dinv = nullptr;    size_t Dinv_cap = 0;     // inverted diagonal blocks (tensor solve path)
+  void* Dinv2 = nullptr;   size_t Dinv2_cap = 0;    // inverses of pairs of 128-row blocks (256 rows)
+  void* Pscr = nullptr;    size_t Pscr_cap = 0;     // scratch of their composition
+  int inv_pairs = 0;       // pairs with a 256-row inverse (0: 128-row solve steps only)
+  bool pairs_off = false;  // 128-row steps although pair inverses exist (refinement fallback)
+  int solve_blk = 256;     // RMAT_PARAM_SOLVE_BLOCK: rows per tensor-path solve step (256 or 128)
   int inv_blocks = 0, inv_nb = 0;      // right-hand-side block planes [4][RMAT_YPL_ROWS][256]
   void* Bpl = nullptr;     size_t Bpl_cap = 0;      // tensor B operand planes (U12^T split)
   int* pfwd = nullptr;     size_t pfwd_cap = 0;     // composed row permutation (tensor forward solve)
@@ -198,6 +203,8 @@ struct rmat_ctx_s {
   // 1 FP64 tensor instruction (mma.m8n8k4.f64), 2 tensor-core digit slices
   int resid_param = 0;
   int tc_bn = 256;         // tile width of the factor's tensor-core updates (RMAT_PARAM_TC_BN)
+  int factor_kind = 0;     // RMAT_PARAM_FACTOR: 0 LU with partial pivoting, 1 LDL^T
+  int factor_used = 0;     // what rmat_factor runs / last ran (1: LDL^T)
   int resid_comp = -1;     // compensated kinetic sums (RMAT_PARAM_RESID_SUMS; -1 = complex128 only)
   long long wpt_gen = 0;   // bumped whenever the point-coupling table is rewritten
   // CUDA graph of one complete solve (both sweeps), captured on first use and replayed
@@ -242,7 +249,7 @@ int lu_solve_dev(rmat_ctx c, const void* A, int n, int ld, const LUPerm& pm, int
                  void* B, int ldb, int nrhs, bool tensor = false);
 int perm_reserve(rmat_ctx c, LUPerm& pm, int n, int nb);
 // gemm_tc.cu
-int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n);
+int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n, bool upper = false);
 // solve update: rows [row0, row0+M) of the solve buffer Bw (ld = nrhs) -= F(ay0.., k0..k0+jb) * Y
 // Cluster size the cluster panel would use for M rows of width jb (0: does not fit).
 int panel_cluster_fits(rmat_ctx c, int precision, int M, int jb);

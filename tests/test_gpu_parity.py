@@ -274,3 +274,23 @@ def test_refinement_reports_stagnation_above_floor(g, ctx):
     berr = g.rmat_get_stats(ctx)["backward_error"]
     assert out["status"] == g.RMAT_ENOCONV
     assert berr > 2.0 * 2.0 ** -53
+
+
+@pytest.mark.parametrize("prec", [3, 1])
+@pytest.mark.parametrize("blk", [128, 256])
+@pytest.mark.parametrize("shape", [(16, 100), (29, 50)])
+def test_solve_step_rows(g, ctx, prec, blk, shape):
+    """Tensor-path solves in 128-row steps, or in 256-row steps over pairs of diagonal
+    blocks (inverses composed from the 128-row ones): N = 1600 is six pairs and a
+    64-row tail, N = 1450 five pairs, one unpaired full block and a 42-row tail."""
+    nch, nlag = shape
+    p = cp.make_problem(900 + nch, nch, nlag, 11.0)
+    ref = truth(p, ("steps", nch, nlag))
+    g.rmat_set_param(ctx, g.RMAT_PARAM_SOLVE_BLOCK, blk)
+    try:
+        out = run_problem(ctx, p, prec, max_refine=30, tol=1e-14, nb=128)
+    finally:
+        g.rmat_set_param(ctx, g.RMAT_PARAM_SOLVE_BLOCK, 0)
+    assert out["status"] == g.RMAT_OK
+    for k in ("X", "R", "U"):
+        assert relerr(out[k], ref[k]) < TOL[prec], k
