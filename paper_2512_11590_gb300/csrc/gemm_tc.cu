@@ -528,13 +528,15 @@ int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n, boo
 
 // Rectangular factor update C[rows row0.., cols col0..col0+ncols) -= F B: A = the split
 // factor planes at K-columns ax0..ax0+K (rows row0..), B = the U12^T planes rows
-// col0.. at K offset 0; uniform inverse scale *cscal (FP16 planes).
+// col0.. at K offset 0; uniform inverse scale *cscal (FP16 planes).  upper (row0 ==
+// col0, M == ncols): only the tiles on or above the diagonal (symmetric C).
 int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, int K, int ax0,
-                     const float* cscal) {
+                     const float* cscal, bool upper) {
   if (M <= 0 || ncols <= 0) return RMAT_OK;
   RMAT_CHECK(tc_prepare(c, n, c->nrhs + (c->nrhs & 1)));
   TcCache& g_tc = tc_cache(c);
-  TcScales sc{nullptr, 1, nullptr, rmat_plane_fmt(c->precision) == 1 ? cscal : nullptr, nullptr};
+  TcScales sc{nullptr, 1, nullptr, rmat_plane_fmt(c->precision) == 1 ? cscal : nullptr, nullptr,
+              upper ? 1 : 0};
   if (c->tc_bn == 128)
     return launch_tc<128>(c, g_tc.upd128, col0, row0, M, ncols, K, ax0, row0, 0, col0, sc, true);
   return launch_tc<TC_BN>(c, g_tc.upd, col0, row0, M, ncols, K, ax0, row0, 0, col0, sc, true);

@@ -562,40 +562,69 @@ __global__ void split_l21_kernel(const float2* __restrict__ A, int ld, int k0, i
 }
 
 // ---- complex-symmetric LDL^T without pivoting (C = C^T, Sec. 2) ----------------
-// The jb x jb diagonal block factored in one CTA in shared memory: unit lower L11
-// below the diagonal, U11 = D11 L11^T on and above it (the unpivoted LU of the
-// block), identity interchanges.  Column j: multipliers l_i = a_ij / a_jj, then the
-// rank-1 update of the block right of and below (j, j); each thread keeps one column
-// and a stride of rows.  A zero pivot is recorded in stat[ST_INFO] (first column,
-// 1-based) and its column left as it is.
+// The jb x jb diagonal block (jb <= 128) factored in one CTA in shared memory: unit
+// lower L11 below the diagonal, U11 = D11 L11^T on and above it (the unpivoted LU of
+// the block), identity interchanges.  Column j: multipliers l_i = a_ij (1 / a_jj),
+// then the rank-1 update of the block right of and below (j, j).  Each of the 512
+// threads owns two adjacent columns (rows padded to jb + 2 entries) and every eighth
+// row.  A zero pivot is recorded
+// in stat[ST_INFO] (first column, 1-based) and its column left as it is.
+constexpr int DIAG_THREADS = 512;
 template <class T>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(DIAG_THREADS)
 diag_nopiv_kernel(cplx<T>* __restrict__ A, int ld, int k0, int jb, int* __restrict__ ipiv,
                   int* __restrict__ stat) {
   using C2 = cplx<T>;
-  extern __shared__ unsigned char smem_raw[];
-  C2* s = reinterpret_cast<C2*>(smem_raw);  // [jb][jb + 1]
-  const int ls = jb + 1, tid = threadIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* s = reinterpret_cast<C2*>(smem_raw);  // [jb][jb + 2]
+  const int ls = jb + 2, tid = threadIdx.x;
   C2* D = A + (size_t)k0 * ld + k0;
-  for (int e = tid; e < jb * jb; e += blockDim.x) {
+  for (int e = tid; e < jb * jb; e += DIAG_THREADS) {
     const int r = e / jb, cc = e - r * jb;
     s[r * ls + cc] = D[(size_t)r * ld + cc];
   }
-  for (int e = tid; e < jb; e += blockDim.x) ipiv[k0 + e] = k0 + e;
+  for (int e = tid; e < jb; e += DIAG_THREADS) ipiv[k0 + e] = k0 + e;
   __syncthreads();
-  const int rg = blockDim.x / jb, col = tid % jb, r0 = tid / jb;
+  const int c0 = 2 * (tid & 63), r0 = tid >> 6;  // columns c0, c0 + 1; rows r0 + 8k
   for (int j = 0; j < jb - 1; ++j) {
     const C2 piv = s[j * ls + j];
-    const bool zero = piv.x == (T)0 && piv.y == (T)0;
-    if (zero) {
+    if (piv.x == (T)0 && piv.y == (T)0) {  // uniform: every thread reads the same pivot
       if (tid == 0) atomicCAS(&stat[ST_INFO], 0, k0 + j + 1);
-      continue;  // uniform: every thread reads the same pivot
+      continue;
     }
-    for (int i = j + 1 + tid; i < jb; i += blockDim.x) s[i * ls + j] = cdiv<T>(s[i * ls + j], piv);
+    const C2 inv = cdiv<T>(mkc<T>((T)1, (T)0), piv);
+    if (tid > j && tid < jb) s[tid * ls + j] = cmul<T>(s[tid * ls + j], inv);
     __syncthreads();
-    if (r0 < rg && col > j) {
-      const C2 u = s[j * ls + col];
-      for (int i = j + 1 + r0; i < jb; i += rg) csub_mul<T>(s[i * ls + col], s[i * ls + j], u);
+    if (c0 + 1 > j && c0 < jb) {
+      const C2 u0 = s[j * ls + c0], u1 = s[j * ls + c0 + 1];
+      const bool w0 = c0 > j;  // column c0 lies right of j (c0 + 1 always does here)
+      // rows in two chunks of eight: all loads of a chunk before its stores, so the
+      // shared-memory latency overlaps (the stores could alias the next loads)
+#pragma unroll
+      for (int kc = 0; kc < 2; ++kc) {
+        if (r0 + 8 * (8 * kc + 7) <= j) continue;  // the whole chunk is at or above row j
+        C2 l[8], a0[8], a1[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int i = r0 + 8 * (8 * kc + t);
+          const bool on = i > j && i < jb;
+          l[t] = on ? s[i * ls + j] : mkc<T>((T)0, (T)0);
+          a0[t] = on ? s[i * ls + c0] : mkc<T>((T)0, (T)0);
+          a1[t] = on ? s[i * ls + c0 + 1] : mkc<T>((T)0, (T)0);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int i = r0 + 8 * (8 * kc + t);
+          if (i > j && i < jb) {
+            if (w0) {
+              csub_mul<T>(a0[t], l[t], u0);
+              s[i * ls + c0] = a0[t];
+            }
+            csub_mul<T>(a1[t], l[t], u1);
+            s[i * ls + c0 + 1] = a1[t];
+          }
+        }
+      }
     }
     __syncthreads();
   }
@@ -603,7 +632,7 @@ diag_nopiv_kernel(cplx<T>* __restrict__ A, int ld, int k0, int jb, int* __restri
     const C2 last = s[(jb - 1) * ls + jb - 1];
     if (last.x == (T)0 && last.y == (T)0) atomicCAS(&stat[ST_INFO], 0, k0 + jb);
   }
-  for (int e = tid; e < jb * jb; e += blockDim.x) {
+  for (int e = tid; e < jb * jb; e += DIAG_THREADS) {
     const int r = e / jb, cc = e - r * jb;
     D[(size_t)r * ld + cc] = s[r * ls + cc];
   }
@@ -1890,6 +1919,24 @@ int u12_by_inverse(rmat_ctx c, float2* A, int ld, int n, int k0, int nb, const L
   return RMAT_OK;
 }
 
+template <class T>
+int launch_diag_nopiv(rmat_ctx c, cplx<T>* A, int ld, int k0, int jb, int* ipiv) {
+  static bool attr = false;
+  const size_t smem = (size_t)jb * (jb + 2) * sizeof(cplx<T>);
+  if (!attr) {
+    RMAT_CU(cudaFuncSetAttribute(diag_nopiv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)max_nb<T>() * (max_nb<T>() + 2) * sizeof(cplx<T>))));
+    attr = true;
+  }
+  if (jb > max_nb<T>()) return RMAT_ESTATE;
+  KTimer kt(c, KT_PANEL);
+  diag_nopiv_kernel<T><<<1, DIAG_THREADS, smem, c->stream>>>(A, ld, k0, jb, ipiv, c->dstat);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  kt.end();
+  return RMAT_OK;
+}
+
 // Paired tensor-core factorisation (complex64): two panels share one trailing
 // update with K = 2 nb, halving the read-modify-write passes over C22 (the update
 // is bound by that traffic with FP16 operands).  For a pair (a at k0, b at k0b):
@@ -1898,7 +1945,12 @@ int u12_by_inverse(rmat_ctx c, float2* A, int ld, int n, int k0, int nb, const L
 //   (F keeps the deferred-interchange layout the solves replay); rows of b updated
 //   by a (strip); U12_b; then C_far -= [S | L21_b] [U12_a ; U12_b] with one common
 //   scale for both U12 halves.
-int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, const LUPerm& pm) {
+// LDL^T (ldlt, C = C^T, no interchanges): diagonal block a; U12_a over all trailing
+//   columns and L21_a = U12_a^T D_a^-1; rows of b updated by a over all trailing
+//   columns (the diagonal block b and U12_b's rows); diagonal block b; U12_b and
+//   L21_b; then the far update keeps only its tiles on or above the diagonal.
+int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, const LUPerm& pm,
+                    bool ldlt) {
   const int fmt = rmat_plane_fmt(c->precision);
   const size_t esz = rmat_plane_esz(c->precision);
   const size_t fplane = (size_t)n * ld, bplane = (size_t)n * RMAT_MAX_NB;
@@ -1943,23 +1995,36 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
     RMAT_CU(cudaGetLastError());
     return RMAT_OK;
   };
+  auto panel = [&](int k0, int jb) -> int {
+    return ldlt ? launch_diag_nopiv<float>(c, A, ld, k0, jb, ipiv)
+                : launch_panel<float>(c, A, ld, k0, n, jb, ipiv);
+  };
+  // LDL^T: the multipliers below block k0 from its U12 (the block column below the
+  // diagonal block was never updated)
+  auto mult = [&](int k0, int jb) {
+    if (!ldlt || n - k0 - jb <= 0) return;
+    l21_from_u12_kernel<<<dim3(ceil_div(n - k0 - jb, 32), ceil_div(jb, 32)), 256, 0, c->stream>>>(
+        A, ld, k0, jb, n, reinterpret_cast<unsigned*>(c->dstat + ST_LMAX));
+    c->launches++;
+  };
   unsigned* um = fmt == 1 ? c->umax : nullptr;
   float* us = fmt == 1 ? c->uscale : nullptr;
   int k0 = 0;
   while (k0 < n) {
     const int jba = std::min(nb, n - k0), blka = k0 / nb;
-    RMAT_CHECK(launch_panel<float>(c, A, ld, k0, n, jba, ipiv));
+    RMAT_CHECK(panel(k0, jba));
     RMAT_CHECK(prep(k0));
     const int resta = n - k0 - jba;
     if (resta <= 0) break;
-    RMAT_CHECK(trsm(k0, jba, k0 + jba, resta, true));
+    RMAT_CHECK(trsm(k0, jba, k0 + jba, resta, !ldlt));
+    mult(k0, jba);
     if (resta <= nb) {  // block b is the last one: a single update
       if (um) absmax(k0, jba, k0 + jba, resta, um + blka, nullptr);
       split(k0, jba, k0 + jba, resta, true, true, 0, um ? um + blka : nullptr,
             us ? us + blka : nullptr, nullptr, nullptr);
       l21(k0, jba);
       RMAT_CU(cudaGetLastError());
-      RMAT_CHECK(launch_trailing_tc(c, A, ld, k0, jba, n));
+      RMAT_CHECK(launch_trailing_tc(c, A, ld, k0, jba, n, ldlt));
       k0 += jba;
       continue;
     }
@@ -1972,14 +2037,22 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
           nullptr, nullptr);
     l21(k0, jba);
     RMAT_CU(cudaGetLastError());
-    // columns of b <- a (rows k0b.., in the row order before panel b)
-    RMAT_CHECK(launch_factor_tc(c, n, k0b, n - k0b, k0b, jbb, jba, k0, us ? us + blka : nullptr));
-    RMAT_CHECK(launch_panel<float>(c, A, ld, k0b, n, jbb, ipiv));
-    RMAT_CHECK(prep(k0b));  // b's interchanges also reach F's L21_a
-    RMAT_CHECK(apply_perm<float>(c, pm, A + far0, ld, far, k0b, nb, jbb));  // and the far columns
-    // rows of b <- a in the far columns, then U12_b
-    RMAT_CHECK(launch_factor_tc(c, n, k0b, jbb, far0, far, jba, k0, us ? us + blka : nullptr));
-    RMAT_CHECK(trsm(k0b, jbb, far0, far, false));
+    if (ldlt) {
+      // rows of b <- a over all trailing columns: the diagonal block b and U12_b's rows
+      RMAT_CHECK(launch_factor_tc(c, n, k0b, jbb, k0b, resta, jba, k0, us ? us + blka : nullptr));
+      RMAT_CHECK(panel(k0b, jbb));
+      RMAT_CHECK(prep(k0b));
+    } else {
+      // columns of b <- a (rows k0b.., in the row order before panel b)
+      RMAT_CHECK(launch_factor_tc(c, n, k0b, n - k0b, k0b, jbb, jba, k0, us ? us + blka : nullptr));
+      RMAT_CHECK(panel(k0b, jbb));
+      RMAT_CHECK(prep(k0b));  // b's interchanges also reach F's L21_a
+      RMAT_CHECK(apply_perm<float>(c, pm, A + far0, ld, far, k0b, nb, jbb));  // and the far columns
+      // rows of b <- a in the far columns
+      RMAT_CHECK(launch_factor_tc(c, n, k0b, jbb, far0, far, jba, k0, us ? us + blka : nullptr));
+    }
+    RMAT_CHECK(trsm(k0b, jbb, far0, far, false));  // U12_b
+    mult(k0b, jbb);
     if (um) absmax(k0b, jbb, far0, far, um + blkb, um + pslot);
     // F rows of b (own scale); U12^T planes of both halves with the pair's common scale
     split(k0b, jbb, far0, far, true, true, jba, um ? um + blkb : nullptr, us ? us + blkb : nullptr,
@@ -1988,7 +2061,8 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
     l21(k0b, jbb);
     RMAT_CU(cudaGetLastError());
     // C_far -= [L21_a | L21_b] [U12_a ; U12_b]: F's K-columns k0..k0+jba+jbb are contiguous
-    RMAT_CHECK(launch_factor_tc(c, n, far0, far, far0, far, jba + jbb, k0, us ? us + pslot : nullptr));
+    RMAT_CHECK(launch_factor_tc(c, n, far0, far, far0, far, jba + jbb, k0, us ? us + pslot : nullptr,
+                                ldlt));
     k0 = far0;
   }
   c->inv_blocks = 0;
@@ -2004,24 +2078,6 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
   if (nb == 64) RMAT_CHECK(invert_diag_blocks<64>(c, A, ld, n, nb, true));
   RMAT_CHECK(finish_fpl_order(c, n, nb, pm));
   return invert_pair_blocks(c, A, ld, n);
-}
-
-template <class T>
-int launch_diag_nopiv(rmat_ctx c, cplx<T>* A, int ld, int k0, int jb, int* ipiv) {
-  static bool attr = false;
-  const size_t smem = (size_t)jb * (jb + 1) * sizeof(cplx<T>);
-  if (!attr) {
-    RMAT_CU(cudaFuncSetAttribute(diag_nopiv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((size_t)max_nb<T>() * (max_nb<T>() + 1) * sizeof(cplx<T>))));
-    attr = true;
-  }
-  if (jb > max_nb<T>()) return RMAT_ESTATE;
-  KTimer kt(c, KT_PANEL);
-  diag_nopiv_kernel<T><<<1, 512, smem, c->stream>>>(A, ld, k0, jb, ipiv, c->dstat);
-  c->launches++;
-  RMAT_CU(cudaGetLastError());
-  kt.end();
-  return RMAT_OK;
 }
 
 template <class T>
@@ -2041,8 +2097,8 @@ int lu_factor_dev(rmat_ctx c, void* Av, int n, int ld, int* ipiv, int nb, bool t
   const bool ldlt = tensor && sizeof(T) == 4 && c->factor_used == 1;  // set by rmat_factor
   if (ldlt) RMAT_CU(cudaMemsetAsync(c->dstat + ST_LMAX, 0, sizeof(int), c->stream));
   if constexpr (sizeof(T) == 4)
-    if (tensor && !ldlt && c->paired && 2 * nb <= RMAT_MAX_NB)
-      return factor_pairs_tc(c, reinterpret_cast<float2*>(A), n, ld, ipiv, nb, pm);
+    if (tensor && c->paired && 2 * nb <= RMAT_MAX_NB)
+      return factor_pairs_tc(c, reinterpret_cast<float2*>(A), n, ld, ipiv, nb, pm, ldlt);
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int jb = std::min(nb, n - k0);
     if (ldlt)

@@ -263,7 +263,7 @@ int launch_apply_resid(rmat_ctx c, const double2* Xin, double2* Rout);
 int rmat_solve_system(rmat_ctx c);
 int gmres_correction(rmat_ctx c, int m, double tau, int* inner);
 int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, int K, int ax0,
-                     const float* cscal);
+                     const float* cscal, bool upper = false);
 int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n,
                     const float* rowscale, int rs_div);
 int tc_prepare(rmat_ctx c, int n, int nrhs);

@@ -43,13 +43,14 @@ def truth(p, key):
 
 
 def with_params(g, ctx, params, fn):
+    default = {g.RMAT_PARAM_PAIRED: 1}
     for k, v in params.items():
         g.rmat_set_param(ctx, k, v)
     try:
         return fn()
     finally:
         for k in params:
-            g.rmat_set_param(ctx, k, 0)
+            g.rmat_set_param(ctx, k, default.get(k, 0))
 
 
 @pytest.mark.parametrize("prec", [3, 1, 4])
@@ -65,11 +66,29 @@ def test_ldlt_matches_oracle(g, ctx, prec, tc_bn, shape):
                       lambda: run_problem(ctx, p, prec, max_refine=30, tol=1e-14, nb=128))
     st = g.rmat_get_stats(ctx)
     assert st["factor_ldlt"] == 1
-    assert 0 < st["ldlt_lmax"] < 4          # the kinetic diagonal dominates: small multipliers
+    if p.N > 128:                           # multipliers below the first diagonal block
+        assert 0 < st["ldlt_lmax"] < 4      # the kinetic diagonal dominates: small multipliers
+    else:
+        assert st["ldlt_lmax"] == 0
     assert out["info"] == 0
     assert out["status"] == g.RMAT_OK
     for k in ("X", "R", "U"):
         assert relerr(out[k], ref[k]) < TOL[prec], k
+
+
+@pytest.mark.parametrize("paired", [1, 0])
+@pytest.mark.parametrize("shape", [(16, 100), (29, 50), (5, 50)])
+def test_ldlt_paired_and_single_updates(g, ctx, paired, shape):
+    """Paired (two diagonal blocks per symmetric far update of depth 256, the default)
+    and one update per block; N = 250 is a pair with a ragged second block."""
+    nch, nlag = shape
+    p = cp.make_problem(740 + nch, nch, nlag, 13.0)
+    ref = truth(p, ("ldlt-pairs", nch, nlag))
+    out = with_params(g, ctx, {g.RMAT_PARAM_FACTOR: 1, g.RMAT_PARAM_PAIRED: paired},
+                      lambda: run_problem(ctx, p, 3, max_refine=30, tol=1e-14, nb=128))
+    assert out["status"] == g.RMAT_OK
+    for k in ("X", "R", "U"):
+        assert relerr(out[k], ref[k]) < 1e-10, k
 
 
 def test_ldlt_config3_block(g, ctx):
