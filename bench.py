@@ -222,7 +222,7 @@ def workload(args):
 class Runner:
     """One system on one GPU through the C ABI (device-resident buffers)."""
 
-    def __init__(self, p, precision, device, method=0, lookahead=0, residual=0, solve_block=0,
+    def __init__(self, p, precision, device, method=0, lookahead=1, residual=0, solve_block=0,
                  factor=0):
         import torch
 
@@ -772,8 +772,8 @@ def main():
                     help="factor M itself or the Woodbury-kinetic Schur matrix S")
     ap.add_argument("--no-woodbury", action="store_true",
                     help="skip the Woodbury-kinetic comparison leg")
-    ap.add_argument("--lookahead", action="store_true",
-                    help="look-ahead (second stream) in the tensor-path solves")
+    ap.add_argument("--no-lookahead", action="store_true",
+                    help="tensor-path solves without look-ahead (bitwise reproducible)")
     ap.add_argument("--profile-step", action="store_true",
                     help="for ncu: one untimed SIMT warm-up step at N=1600, then one FP32+IR "
                          "tensor step at N = nch*100; no timing, no JSON")
@@ -842,7 +842,7 @@ def main():
     method = 1 if args.method == "woodbury" else 0
     resid = {"auto": 0, "fp64mma": 1, "tensor": 2}[args.residual]
     factor = 1 if args.factor == "ldlt" else 0
-    run = Runner(p, prec, local, method, 1 if args.lookahead else 0, resid, args.solve_block,
+    run = Runner(p, prec, local, method, 0 if args.no_lookahead else 1, resid, args.solve_block,
                  factor)
     g.rmat_set_param(run.ctx, g.RMAT_PARAM_REFINE, args.refine)
     with ClockSampler(local) as clk:
@@ -887,7 +887,7 @@ def main():
     other = None
     if not args.no_woodbury:
         # the other factored matrix (Woodbury-kinetic S vs M) on the same workload
-        rw = Runner(p, prec, local, 1 - method, 1 if args.lookahead else 0, resid)
+        rw = Runner(p, prec, local, 1 - method, 0 if args.no_lookahead else 1, resid)
         for _ in range(2):
             rw.step()
         torch.cuda.synchronize()
@@ -1062,6 +1062,7 @@ def main():
                    "factor": {"lu": "LU with partial pivoting", "ldlt": "LDL^T"}[args.factor],
                    "method": args.method, "residual": args.residual,
                    "solve_block": args.solve_block or 256,
+                   "solve_lookahead": not args.no_lookahead,
                    "refinement": ir, "l2": "inputs larger than L2 (C is %.1f GB)" % (p.N * p.N * 8 / 1e9),
                    "lu_block": stats["nb"], "panel_ctas": stats["panel_ctas"],
                    "ms_per_step_best_median": [stats["ms_steps"]["best"],

@@ -109,10 +109,12 @@ extern "C" {
  * The stopping rule (tol, stagnation, max_refine) counts outer corrections.
  * Not used by batches (their refinement is decided on the device). */
 #define RMAT_PARAM_REFINE      8
-/* Tensor-path solves: 1 = look-ahead, each block's update of the next block's rows
- * runs first and the far rows' update overlaps the next block on a second stream
- * (the concurrent reduce-adds make the rounding order, and so the last bits, vary
- * from run to run); 0 (default) = one update per block. */
+/* Tensor-path solves: 1 (default) = look-ahead: each step's update of the next
+ * step's rows runs first (its K range split over a few CTAs) and the far rows' update
+ * overlaps the next step on a second stream, leaving SMs to the next row update (the
+ * concurrent reduce-adds make the rounding order, and so the last bits before the
+ * FP64 refinement, vary from run to run); 0 = one update per step (every bit
+ * reproducible). */
 #define RMAT_PARAM_SOLVE_LOOKAHEAD 9
 /* rmat_propagate: 1 (default) = when every panel of a sector system fits one
  * thread-block cluster, sectors 2..ns are solved concurrently on worker contexts

@@ -80,6 +80,7 @@ int ctx_reserve(rmat_ctx c, bool dense) {
     want(c->Fpl_cap, 4 * N * ld * pe);
     want(c->Bpl_cap, 4 * N * RMAT_MAX_NB * pe);
     want(c->Ypl_cap, (size_t)8 * RMAT_YPL_ROWS * RMAT_MAX_NB * pe);
+    want(c->Mpl_cap, (size_t)4 * 128 * 128 * pe);
   }
   if (dense) {
     want(c->A64_cap, N * N * 16);
@@ -98,9 +99,10 @@ int ctx_reserve(rmat_ctx c, bool dense) {
     RMAT_CHECK(rmat_grow(c, &c->Fpl, &c->Fpl_cap, 4 * N * ld * pe));
     RMAT_CHECK(rmat_grow(c, &c->Bpl, &c->Bpl_cap, 4 * N * RMAT_MAX_NB * pe));
     RMAT_CHECK(rmat_grow(c, &c->Ypl, &c->Ypl_cap, (size_t)8 * RMAT_YPL_ROWS * RMAT_MAX_NB * pe));
+    RMAT_CHECK(rmat_grow(c, &c->Mpl, &c->Mpl_cap, (size_t)4 * 128 * 128 * pe));
     RMAT_CHECK(rmat_grow(c, (void**)&c->pfwd, &c->pfwd_cap, 2 * N * sizeof(int)));
     RMAT_CHECK(rmat_grow(c, &c->Bt, &c->Bt_cap, N * nrhs * eb));
-    const size_t nblk = N / 32 + 2;
+    const size_t nblk = N / 32 + 4;  // per-block scales + the pair slot + two U12 slots
     RMAT_CHECK(rmat_grow(c, (void**)&c->umax, &c->umax_cap, nblk * sizeof(unsigned)));
     RMAT_CHECK(rmat_grow(c, (void**)&c->uscale, &c->uscale_cap, nblk * sizeof(float)));
     RMAT_CHECK(rmat_grow(c, (void**)&c->ycs, &c->ycs_cap, (size_t)2 * RMAT_YPL_ROWS * sizeof(float)));
@@ -310,7 +312,7 @@ int rmat_destroy(rmat_ctx c) {
                   c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows, c->Dinv,
                   c->umax, c->uscale, c->ycs, c->pfwd, c->Bt, c->Kinv, c->Kinv32, c->W32, c->Bs,
                   c->gm_V, c->gm_Z, c->gm_T, c->gm_small, c->faL, c->prop, c->Xs, c->Dinv2,
-                  c->Pscr};
+                  c->Pscr, c->Mpl};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->hstat) cudaFreeHost(c->hstat);
@@ -661,7 +663,7 @@ int enqueue_solve_refine(rmat_ctx c, int max_refine, double tol, IrState* st) {
 
 // Whether the tensor-path solves take 256-row steps over composed pair inverses.
 static bool pairs_in_use(rmat_ctx c) {
-  return c->inv_pairs > 0 && !c->pairs_off && !c->solve_lookahead && c->refine_param == 0 &&
+  return c->inv_pairs > 0 && !c->pairs_off && c->refine_param == 0 &&
          rmat_tensor_prec(c->precision);
 }
 

@@ -30,7 +30,7 @@
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 8, TC_STAGES = 4;
+constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 8;
 constexpr int TC_THREADS = 192;
 constexpr uint32_t A_PLANE_BYTES = TC_BM * TC_BK * 4;                              // 4 KB
 constexpr uint32_t STAGING_BYTES = TC_BM * 32 * 4;  // 16 complex columns x 128 rows, 128B swizzle
@@ -38,12 +38,15 @@ constexpr uint32_t STAGING_BYTES = TC_BM * 32 * 4;  // 16 complex columns x 128 
 // Tile width BN = 256 (trailing updates) or 128 (solve updates: twice the tiles for
 // the same rows, and two accumulator sets in the 512 TMEM columns, so the epilogue
 // of one tile overlaps the MMAs of the next).
+// BN = 128 keeps three pipeline stages (130 KB of shared memory), so a solve-path
+// diagonal application (76 KB) fits beside a running update on the same SM.
 template <int BN>
 struct TcCfg {
   static constexpr uint32_t B_PLANE = BN * TC_BK * 4;                 // 8 / 4 KB
   static constexpr uint32_t STAGE = 4 * A_PLANE_BYTES + 4 * B_PLANE;  // 48 / 32 KB
   static constexpr int NBUF = 512 / (2 * BN);                         // accumulator sets
-  static constexpr size_t SMEM = (size_t)TC_STAGES * STAGE + 2 * STAGING_BYTES + 1024 + 256;
+  static constexpr int STAGES = BN == 128 ? 3 : 4;
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE + 2 * STAGING_BYTES + 1024 + 256;
 };
 
 struct TcMaps {
@@ -81,6 +84,8 @@ struct TcScales {
   const int* skip;  // nonzero *skip: the launch does nothing (a stopped refinement)
   int upper;        // symmetric update (M == Nn, same origin): only the tiles that are not
                     // strictly below the diagonal (m0 < n0 + BN)
+  int ksplit;       // > 1: every tile's K range in ksplit parts on different CTAs, each
+                    // reduce-adding its partial product (K / KSTEP divisible by ksplit)
 };
 
 // Tile t of a launch: column-major over the mt x nt tiles, or, for an upper launch,
@@ -122,15 +127,16 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
   constexpr int KSTEP = KIND == 0 ? 8 : 16;  // K elements per 32-byte operand row
   if (sc.skip && *sc.skip) return;           // before any barrier or TMEM allocation
   constexpr uint32_t B_PLANE_BYTES = Cfg::B_PLANE, STAGE_BYTES = Cfg::STAGE;
-  constexpr int NBUF = Cfg::NBUF;
+  constexpr int NBUF = Cfg::NBUF, NST = Cfg::STAGES;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   unsigned char* stages = smem;
-  unsigned char* staging = stages + TC_STAGES * STAGE_BYTES;  // 2 x 16 KB, 1024-aligned
+  unsigned char* staging = stages + NST * STAGE_BYTES;  // 2 x 16 KB, 1024-aligned
   uint64_t* bars = reinterpret_cast<uint64_t*>(staging + 2 * STAGING_BYTES);
-  // bars[0..3] full, [4..7] empty, [8 + 2b] tmem_full of set b, [9 + 2b] tmem_empty
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12);
+  // bars[0, NST) full, [NST, 2 NST) empty, [2 NST + 2b] tmem_full of accumulator set b,
+  // [2 NST + 2b + 1] its tmem_empty
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 2 * NBUF);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* epi_abort = abort_flag + 1;
 
@@ -139,16 +145,18 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
   const int nt = (Nn + BN - 1) / BN;
   static_assert(TC_BM == 128 && BN % TC_BM == 0, "tile_coords assumes 128-row tiles");
   const int ntiles = tile_count<BN>(mt, nt, sc.upper);
-  const int ksteps = K / KSTEP;
+  const int ksp = sc.ksplit > 1 ? sc.ksplit : 1;
+  const int nunits = ntiles * ksp;           // unit u: tile u / ksp, K part u % ksp
+  const int ksteps = K / KSTEP / ksp;        // K-steps per unit
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(smem_u32(&bars[s]), 1);
-      mbar_init(smem_u32(&bars[4 + s]), 1);
+      mbar_init(smem_u32(&bars[NST + s]), 1);
     }
     for (int b = 0; b < NBUF; ++b) {
-      mbar_init(smem_u32(&bars[8 + 2 * b]), 1);
-      mbar_init(smem_u32(&bars[9 + 2 * b]), 4);
+      mbar_init(smem_u32(&bars[2 * NST + 2 * b]), 1);
+      mbar_init(smem_u32(&bars[2 * NST + 2 * b + 1]), 4);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -169,12 +177,14 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         int m0, n0;
-        tile_coords<BN>(tile, mt, nt, sc.upper, m0, n0);
-        for (int ks = 0; ks < ksteps; ++ks, ++it) {
-          const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
-          if (!mbar_wait(smem_u32(&bars[4 + s]), ph ^ 1, abort_flag)) { ok = false; break; }
+        tile_coords<BN>(u / ksp, mt, nt, sc.upper, m0, n0);
+        const int kbase = (u % ksp) * ksteps;
+        for (int kk = 0; kk < ksteps; ++kk, ++it) {
+          const int ks = kbase + kk;
+          const uint32_t s = it % NST, ph = (it / NST) & 1;
+          if (!mbar_wait(smem_u32(&bars[NST + s]), ph ^ 1, abort_flag)) { ok = false; break; }
           const uint32_t full = smem_u32(&bars[s]);
           mbar_expect_tx(full, NPROD == 3 ? STAGE_BYTES : STAGE_BYTES / 2);
           const uint32_t st = smem_u32(stages + s * STAGE_BYTES);
@@ -191,10 +201,10 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
         *abort_flag = 1;
         atomicExch(err, 2);
       }
-      // drain: the last (up to TC_STAGES) issued stages must land before exit
-      for (uint32_t k = (it > TC_STAGES ? it - TC_STAGES : 0); k < it; ++k) {
+      // drain: the last (up to NST) issued stages must land before exit
+      for (uint32_t k = (it > (uint32_t)NST ? it - NST : 0); k < it; ++k) {
         const unsigned long long t0 = gtimer();
-        while (!mbar_try(smem_u32(&bars[k % TC_STAGES]), (k / TC_STAGES) & 1))
+        while (!mbar_try(smem_u32(&bars[k % NST]), (k / NST) & 1))
           if (gtimer() - t0 > RMAT_TC_WAIT_NS) break;
       }
     }
@@ -205,16 +215,17 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
       bool ok = true;
       uint32_t idesc[2] = {idesc_mma<BN, KIND>(false), idesc_mma<BN, KIND>(true)};
       uint32_t buf = 0, use = 0;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tcount) {
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++tcount) {
         buf = tcount % NBUF;
-        use = tcount / NBUF;  // earlier tiles that used this accumulator set
-        if (use > 0 && !mbar_wait(smem_u32(&bars[9 + 2 * buf]), (use - 1) & 1, abort_flag)) {
+        use = tcount / NBUF;  // earlier units that used this accumulator set
+        if (use > 0 &&
+            !mbar_wait(smem_u32(&bars[2 * NST + 2 * buf + 1]), (use - 1) & 1, abort_flag)) {
           ok = false;
           break;
         }
         fence_after();
         for (int ks = 0; ks < ksteps; ++ks, ++it) {
-          const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1;
+          const uint32_t s = it % NST, ph = (it / NST) & 1;
           if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag)) { ok = false; break; }
           fence_after();
           const uint32_t st = smem_u32(stages + s * STAGE_BYTES);
@@ -228,10 +239,10 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
             const uint32_t first = (ks == 0) && (p == 0 || p == 6);
             mma_issue<KIND>(tmem + buf * 2 * BN + acc * BN, ad, bd, idesc[neg], first ? 0u : 1u);
           }
-          mma_commit(smem_u32(&bars[4 + s]));  // frees the stage once these MMAs have read it
+          mma_commit(smem_u32(&bars[NST + s]));  // frees the stage once these MMAs have read it
         }
         if (!ok) break;
-        mma_commit(smem_u32(&bars[8 + 2 * buf]));  // accumulator set ready for the epilogue
+        mma_commit(smem_u32(&bars[2 * NST + 2 * buf]));  // accumulator set ready for the epilogue
       }
       if (!ok) {
         *abort_flag = 1;
@@ -239,9 +250,9 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
         // let every MMA issued so far finish before TMEM is released
         buf = tcount % NBUF;
         use = tcount / NBUF;
-        mma_commit(smem_u32(&bars[8 + 2 * buf]));
+        mma_commit(smem_u32(&bars[2 * NST + 2 * buf]));
         const unsigned long long t0 = gtimer();
-        while (!mbar_try(smem_u32(&bars[8 + 2 * buf]), use & 1))
+        while (!mbar_try(smem_u32(&bars[2 * NST + 2 * buf]), use & 1))
           if (gtimer() - t0 > RMAT_TC_WAIT_NS) break;
       }
     }
@@ -254,13 +265,13 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
     const int row = quad * 32 + lane;
     const bool leader = (warp == 2 && lane == 0);
     uint32_t tcount = 0, chunk = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++tcount) {
       int m0, n0;
-      tile_coords<BN>(tile, mt, nt, sc.upper, m0, n0);
+      tile_coords<BN>(u / ksp, mt, nt, sc.upper, m0, n0);
       const uint32_t buf = tcount % NBUF, use = tcount / NBUF;
       // The four epilogue warps leave together (they share named barriers): each
       // waits (bounded), then one thread snapshots the abort flag for all.
-      if (!mbar_wait(smem_u32(&bars[8 + 2 * buf]), use & 1, abort_flag)) {
+      if (!mbar_wait(smem_u32(&bars[2 * NST + 2 * buf]), use & 1, abort_flag)) {
         *abort_flag = 1;
         atomicExch(err, 2);
       }
@@ -282,7 +293,7 @@ tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, i
         if (ch == BN / 16 - 1) {             // accumulator set fully read: release it
           fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(&bars[9 + 2 * buf]));
+          if (lane == 0) mbar_arrive(smem_u32(&bars[2 * NST + 2 * buf + 1]));
         }
         unsigned char* sbuf = staging + (chunk & 1) * STAGING_BYTES;
         if (leader) bulk_wait_read1();       // the reduce that used this buffer has read it
@@ -396,6 +407,8 @@ struct TcCache {
   int n = -1, ldf = -1, nrhs = -1, fmt = -1;
   TcMaps upd, sol[2];  // trailing update (BN = 256), solve update (BN = 128) per Y buffer
   TcMaps upd128;       // trailing update with 128-wide tiles (RMAT_PARAM_TC_BN = 128)
+  TcMaps u12;          // U12 product: A = the (I - L11^-1) planes, B = upd128's
+  const void* mpl = nullptr;
 };
 bool g_tc_attr[2][2][2] = {};
 
@@ -415,15 +428,24 @@ int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn,
   if (!g_tc_attr[BN == 128][KIND][NPROD == 1]) {
     RMAT_CU(cudaFuncSetAttribute(tc_update_kernel<BN, KIND, NPROD>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    // the whole unified memory as shared memory, so other kernels' CTAs fit beside
+    RMAT_CU(cudaFuncSetAttribute(tc_update_kernel<BN, KIND, NPROD>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     g_tc_attr[BN == 128][KIND][NPROD == 1] = true;
   }
   if (sc.upper && (M != Nn || cx0 != cy0)) return RMAT_ESTATE;
+  const int ksp = sc.ksplit > 1 ? sc.ksplit : 1;
+  if ((K / KSTEP) % ksp) return RMAT_ESTATE;
   const int mt = ceil_div(M, TC_BM), nt = ceil_div(Nn, BN);
   const int tiles =
-      sc.upper ? (BN / TC_BM) * (nt - 1) * nt / 2 + std::min(mt, (BN / TC_BM) * nt) : mt * nt;
-  // a far-row update on the solves' look-ahead stream leaves 32 SMs to the next
-  // block's diagonal application (one TC CTA fills an SM's shared memory)
-  const int cap = (c->side && c->stream == c->side) ? std::max(1, c->sm_count - 32) : c->sm_count;
+      (sc.upper ? (BN / TC_BM) * (nt - 1) * nt / 2 + std::min(mt, (BN / TC_BM) * nt) : mt * nt) *
+      ksp;
+  // a far-row update on the solves' look-ahead stream leaves SMs to the next step's
+  // row update (its split-K units); the next diagonal application runs beside the
+  // far update's CTAs (three-stage 128-wide tiles leave it the shared memory)
+  const int cap = (c->side && c->stream == c->side) ? std::max(1, c->sm_count - c->la_free_sms)
+                                                    : c->sm_count;
   const int grid = std::min(tiles, cap);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing && count_as_update) {
@@ -505,6 +527,7 @@ int tc_prepare(rmat_ctx c, int n, int nrhs) {
   g_tc.ldf = ldf;
   g_tc.nrhs = nrhs;
   g_tc.fmt = fmt;
+  g_tc.mpl = nullptr;  // the U12 maps follow the plane format
   return RMAT_OK;
 }
 
@@ -526,6 +549,28 @@ int launch_trailing_tc(rmat_ctx c, float2* A, int ld, int k0, int jb, int n, boo
                           sc, true);
 }
 
+int launch_u12_tc(rmat_ctx c, int n, int k0, int jb, int col0, int ncols, const float* minv_scale,
+                  const float* b_scale) {
+  if (ncols <= 0) return RMAT_OK;
+  if (jb > 128 || !c->Mpl) return RMAT_ESTATE;
+  RMAT_CHECK(tc_prepare(c, n, c->nrhs + (c->nrhs & 1)));
+  TcCache& g_tc = tc_cache(c);
+  const int fmt = rmat_plane_fmt(c->precision);
+  if (g_tc.mpl != c->Mpl || g_tc.fmt != fmt) {
+    const size_t mplane = (size_t)128 * 128 * rmat_plane_esz(c->precision);
+    for (int q = 0; q < 4; ++q)
+      RMAT_CHECK(make_plane_map(&g_tc.u12.a[q], reinterpret_cast<char*>(c->Mpl) + q * mplane, fmt,
+                                128, 128, 128, TC_BM));
+    g_tc.mpl = c->Mpl;
+  }
+  for (int q = 0; q < 4; ++q) g_tc.u12.b[q] = g_tc.upd128.b[q];
+  g_tc.u12.c = g_tc.upd.c;
+  // one 128-row tile row: the K range in two parts doubles the CTAs at work
+  TcScales sc{fmt == 1 ? minv_scale : nullptr, 128, nullptr, fmt == 1 ? b_scale : nullptr, nullptr,
+              0, 2};
+  return launch_tc<128>(c, g_tc.u12, col0, k0, jb, ncols, jb, 0, 0, 0, col0, sc, false);
+}
+
 // Rectangular factor update C[rows row0.., cols col0..col0+ncols) -= F B: A = the split
 // factor planes at K-columns ax0..ax0+K (rows row0..), B = the U12^T planes rows
 // col0.. at K offset 0; uniform inverse scale *cscal (FP16 planes).  upper (row0 ==
@@ -545,10 +590,10 @@ int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, in
 // Solve update: Bsub[M x nrhs] -= F[rows ay0.., cols k0..k0+jb] * Y, Y^T planes in Ypl.
 // rowscale (FP16 planes): inverse scale per rs_div rows of F (the U blocks).
 int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n,
-                    const float* rowscale, int rs_div) {
+                    const float* rowscale, int rs_div, int ksplit) {
   RMAT_CHECK(tc_prepare(c, n, nrhs));
   TcCache& g_tc = tc_cache(c);
-  TcScales sc{nullptr, 1, nullptr, nullptr, c->skip};
+  TcScales sc{nullptr, 1, nullptr, nullptr, c->skip, 0, ksplit};
   if (rmat_plane_fmt(c->precision) == 1) {
     sc.rowscale = rowscale;
     sc.rs_div = rs_div;

@@ -561,15 +561,108 @@ __global__ void split_l21_kernel(const float2* __restrict__ A, int ld, int k0, i
     put4(F, fplane, (size_t)r * ldf + k0 + t, A[(size_t)r * ld + k0 + t], fmt, 1.f);
 }
 
+// ---- inverse of a unit lower triangular diagonal block ------------------------
+// X = L11^-1 for the JB x JB block at (k0, k0) (unit diagonal implied; JB = 64 or 128),
+// written in full (ones on the diagonal, zeros above) to Xout [JB][JB].  One CTA:
+//   level 0: each 32 x 32 diagonal block inverted in place by one warp, column by
+//     column from the right: X[i][j] = -(L[i][j] + sum_{j<k<i} X[i][k] L[k][j]), the
+//     column's L entries passed between lanes by shuffles before they are replaced;
+//   level h = 32, 64: every 2h x 2h diagonal block [A 0; B C] with A^-1, C^-1 in place
+//     gets its lower-left block -C^-1 (B A^-1): T = B A^-1 into a scratch block, then
+//     -C^-1 T over B (thread: one column, every eighth row; the triangular factors'
+//     zero parts skipped).
+constexpr int TINV_THREADS = 512;
+template <int JB>
+__global__ void __launch_bounds__(TINV_THREADS)
+tri_inv_lower_kernel(const float2* __restrict__ A, int ld, int k0, float2* __restrict__ Xout) {
+  constexpr int LDX = JB + 1, LDT = JB / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* X = reinterpret_cast<float2*>(smem_raw);  // [JB][LDX]
+  float2* Tb = X + JB * LDX;                        // [JB / 2][LDT]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float2 zero = make_float2(0.f, 0.f);
+  for (int e = tid; e < JB * JB; e += TINV_THREADS) {
+    const int r = e / JB, c = e - r * JB;
+    X[r * LDX + c] = c < r ? A[(size_t)(k0 + r) * ld + k0 + c] : zero;
+  }
+  __syncthreads();
+  if (warp < JB / 32) {  // level 0
+    float2* Xb = X + 32 * warp * (LDX + 1);
+    for (int j = 30; j >= 0; --j) {
+      const float2 lj = lane > j ? Xb[lane * LDX + j] : zero;
+      float2 acc = lj;
+      for (int k = j + 1; k < 31; ++k) {
+        const float2 lk = make_float2(__shfl_sync(0xffffffffu, lj.x, k),
+                                      __shfl_sync(0xffffffffu, lj.y, k));
+        if (k < lane) cadd_mul<float>(acc, Xb[lane * LDX + k], lk);
+      }
+      __syncwarp();
+      if (lane > j) Xb[lane * LDX + j] = make_float2(-acc.x, -acc.y);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int h = 32; h < JB; h *= 2) {
+    const int c = tid % h, r0 = (tid / h) % 8, d = tid / (8 * h);
+    const bool on = d < JB / (2 * h);
+    const int R0 = 2 * h * d + h, C0 = 2 * h * d;
+    constexpr int MM = JB / 16;  // rows per thread at h = JB / 2 (the larger level)
+    const int mm = h / 8;
+    float2 t[MM];
+    if (on) {
+      // T = B A^-1:  T[i][c] = B[i][c] + sum_{k > c} B[i][k] X_A[k][c]
+#pragma unroll
+      for (int m = 0; m < MM; ++m) t[m] = m < mm ? X[(R0 + r0 + 8 * m) * LDX + C0 + c] : zero;
+      for (int k = c + 1; k < h; ++k) {
+        const float2 xk = X[(C0 + k) * LDX + C0 + c];
+#pragma unroll
+        for (int m = 0; m < MM; ++m)
+          if (m < mm) cadd_mul<float>(t[m], X[(R0 + r0 + 8 * m) * LDX + C0 + k], xk);
+      }
+#pragma unroll
+      for (int m = 0; m < MM; ++m)
+        if (m < mm) Tb[(h * d + r0 + 8 * m) * LDT + c] = t[m];
+    }
+    __syncthreads();
+    if (on) {
+      // B := -C^-1 T:  X[R0+i][C0+c] = -(T[i][c] + sum_{k < i} X_C[i][k] T[k][c])
+#pragma unroll
+      for (int m = 0; m < MM; ++m) t[m] = m < mm ? Tb[(h * d + r0 + 8 * m) * LDT + c] : zero;
+      const int imax = r0 + 8 * (mm - 1);
+      for (int k = 0; k < imax; ++k) {
+        const float2 tk = Tb[(h * d + k) * LDT + c];
+#pragma unroll
+        for (int m = 0; m < MM; ++m) {
+          const int i = r0 + 8 * m;
+          if (m < mm && k < i) cadd_mul<float>(t[m], X[(R0 + i) * LDX + R0 + k], tk);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < MM; ++m)
+        if (m < mm) X[(R0 + r0 + 8 * m) * LDX + C0 + c] = make_float2(-t[m].x, -t[m].y);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < JB * JB; e += TINV_THREADS) {
+    const int r = e / JB, c = e - r * JB;
+    Xout[e] = c < r ? X[r * LDX + c] : make_float2(c == r ? 1.f : 0.f, 0.f);
+  }
+}
+
 // ---- complex-symmetric LDL^T without pivoting (C = C^T, Sec. 2) ----------------
 // The jb x jb diagonal block (jb <= 128) factored in one CTA in shared memory: unit
 // lower L11 below the diagonal, U11 = D11 L11^T on and above it (the unpivoted LU of
-// the block), identity interchanges.  Column j: multipliers l_i = a_ij (1 / a_jj),
-// then the rank-1 update of the block right of and below (j, j).  Each of the 512
-// threads owns two adjacent columns (rows padded to jb + 2 entries) and every eighth
-// row.  A zero pivot is recorded
-// in stat[ST_INFO] (first column, 1-based) and its column left as it is.
-constexpr int DIAG_THREADS = 512;
+// the block), identity interchanges.  Right-looking in panels of DIAG_W columns:
+//   column j of a panel: multipliers l_i = a_ij (1 / a_jj) for every row below j,
+//     then the rank-1 update of the panel's columns right of j (all rows below j)
+//     and of the panel's rows below j right of the panel (their U part);
+//   after the panel: the block right of and below it -= L(panel columns) U(panel
+//     rows), a GEMM of depth DIAG_W in which every thread keeps the U part of its two
+//     columns in registers and reads each L row once (a warp-wide broadcast).
+// A zero pivot is recorded in stat[ST_INFO] (first column, 1-based) and its column
+// left as it is.
+constexpr int DIAG_THREADS = 512, DIAG_W = 8;
 template <class T>
 __global__ void __launch_bounds__(DIAG_THREADS)
 diag_nopiv_kernel(cplx<T>* __restrict__ A, int ld, int k0, int jb, int* __restrict__ ipiv,
@@ -585,52 +678,58 @@ diag_nopiv_kernel(cplx<T>* __restrict__ A, int ld, int k0, int jb, int* __restri
   }
   for (int e = tid; e < jb; e += DIAG_THREADS) ipiv[k0 + e] = k0 + e;
   __syncthreads();
-  const int c0 = 2 * (tid & 63), r0 = tid >> 6;  // columns c0, c0 + 1; rows r0 + 8k
-  for (int j = 0; j < jb - 1; ++j) {
-    const C2 piv = s[j * ls + j];
-    if (piv.x == (T)0 && piv.y == (T)0) {  // uniform: every thread reads the same pivot
-      if (tid == 0) atomicCAS(&stat[ST_INFO], 0, k0 + j + 1);
-      continue;
+  for (int p0 = 0; p0 < jb; p0 += DIAG_W) {
+    const int pe = min(p0 + DIAG_W, jb);  // panel columns [p0, pe)
+    for (int j = p0; j < pe; ++j) {
+      const C2 piv = s[j * ls + j];
+      if (piv.x == (T)0 && piv.y == (T)0) {  // uniform: every thread reads the same pivot
+        if (tid == 0) atomicCAS(&stat[ST_INFO], 0, k0 + j + 1);
+        continue;
+      }
+      if (j + 1 == jb) break;
+      const C2 inv = cdiv<T>(mkc<T>((T)1, (T)0), piv);
+      if (tid > j && tid < jb) s[tid * ls + j] = cmul<T>(s[tid * ls + j], inv);
+      __syncthreads();
+      // region a: rows (j, jb) x panel columns (j, pe), a thread per (row, column) with
+      // DIAG_W columns per row; region b: panel rows (j, pe) x columns [pe, jb), 128
+      // columns per row (DIAG_W, 128 and the block size are powers of two: shifts)
+      static_assert(DIAG_W == 8 && DIAG_THREADS == 512, "thread maps below");
+      for (int t = tid; (t >> 3) < jb - 1 - j; t += DIAG_THREADS) {
+        const int i = j + 1 + (t >> 3), c = j + 1 + (t & 7);
+        if (c < pe) csub_mul<T>(s[i * ls + c], s[i * ls + j], s[j * ls + c]);
+      }
+      for (int t = tid; (t >> 7) < pe - 1 - j; t += DIAG_THREADS) {
+        const int i = j + 1 + (t >> 7), c = pe + (t & 127);
+        if (c < jb) csub_mul<T>(s[i * ls + c], s[i * ls + j], s[j * ls + c]);
+      }
+      __syncthreads();
     }
-    const C2 inv = cdiv<T>(mkc<T>((T)1, (T)0), piv);
-    if (tid > j && tid < jb) s[tid * ls + j] = cmul<T>(s[tid * ls + j], inv);
-    __syncthreads();
-    if (c0 + 1 > j && c0 < jb) {
-      const C2 u0 = s[j * ls + c0], u1 = s[j * ls + c0 + 1];
-      const bool w0 = c0 > j;  // column c0 lies right of j (c0 + 1 always does here)
-      // rows in two chunks of eight: all loads of a chunk before its stores, so the
-      // shared-memory latency overlaps (the stores could alias the next loads)
+    if (pe >= jb) break;
+    // trailing block [pe, jb) x [pe, jb) -= L[., p0:pe) U[p0:pe, .)
+    const int c0 = pe + 2 * (tid & 63), r0 = tid >> 6;
+    if (c0 < jb) {
+      const bool two = c0 + 1 < jb;
+      C2 u0[DIAG_W], u1[DIAG_W];
 #pragma unroll
-      for (int kc = 0; kc < 2; ++kc) {
-        if (r0 + 8 * (8 * kc + 7) <= j) continue;  // the whole chunk is at or above row j
-        C2 l[8], a0[8], a1[8];
+      for (int k = 0; k < DIAG_W; ++k) {
+        const bool on = p0 + k < pe;
+        u0[k] = on ? s[(p0 + k) * ls + c0] : mkc<T>((T)0, (T)0);
+        u1[k] = on && two ? s[(p0 + k) * ls + c0 + 1] : mkc<T>((T)0, (T)0);
+      }
+      for (int i = pe + r0; i < jb; i += DIAG_THREADS / 64) {
+        const C2* li = s + i * ls + p0;
+        C2 a0 = s[i * ls + c0], a1 = two ? s[i * ls + c0 + 1] : mkc<T>((T)0, (T)0);
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int i = r0 + 8 * (8 * kc + t);
-          const bool on = i > j && i < jb;
-          l[t] = on ? s[i * ls + j] : mkc<T>((T)0, (T)0);
-          a0[t] = on ? s[i * ls + c0] : mkc<T>((T)0, (T)0);
-          a1[t] = on ? s[i * ls + c0 + 1] : mkc<T>((T)0, (T)0);
+        for (int k = 0; k < DIAG_W; ++k) {
+          const C2 l = p0 + k < pe ? li[k] : mkc<T>((T)0, (T)0);
+          csub_mul<T>(a0, l, u0[k]);
+          csub_mul<T>(a1, l, u1[k]);
         }
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int i = r0 + 8 * (8 * kc + t);
-          if (i > j && i < jb) {
-            if (w0) {
-              csub_mul<T>(a0[t], l[t], u0);
-              s[i * ls + c0] = a0[t];
-            }
-            csub_mul<T>(a1[t], l[t], u1);
-            s[i * ls + c0 + 1] = a1[t];
-          }
-        }
+        s[i * ls + c0] = a0;
+        if (two) s[i * ls + c0 + 1] = a1;
       }
     }
     __syncthreads();
-  }
-  if (tid == 0) {
-    const C2 last = s[(jb - 1) * ls + jb - 1];
-    if (last.x == (T)0 && last.y == (T)0) atomicCAS(&stat[ST_INFO], 0, k0 + jb);
   }
   for (int e = tid; e < jb * jb; e += DIAG_THREADS) {
     const int r = e / jb, cc = e - r * jb;
@@ -673,6 +772,37 @@ l21_from_u12_kernel(float2* __restrict__ A, int ld, int k0, int jb, int n,
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (tx == 0 && m > 0.f) atomicMax(lmax, __float_as_uint(m));
+}
+
+// ipiv[i] = i: the interchange record of a factorisation without pivoting.
+__global__ void identity_pivots_kernel(int* __restrict__ ipiv, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    ipiv[i] = i;
+}
+
+// The A operand of the tensor-core U12 product: M = I - L11^-1 (strictly lower, the
+// negated entries of the inverse below its unit diagonal) split into four planes
+// [JB][128]; FP16 planes carry the power-of-two scale of max |M|, its inverse to
+// *inv_scale.  One CTA.
+__global__ void __launch_bounds__(1024)
+minv_planes_kernel(const float2* __restrict__ Linv, int JB, void* __restrict__ M, size_t mplane,
+                   int fmt, float* __restrict__ inv_scale) {
+  __shared__ float red[32];
+  float m = 0.f;
+  for (int e = threadIdx.x; e < JB * JB; e += 1024)
+    if (e % JB < e / JB) m = fmaxf(m, cmaxabs(Linv[e]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0.f;
+  for (int w = 0; w < 32; ++w) m = fmaxf(m, red[w]);
+  const float sc = fmt == 1 ? pow2_scale(m) : 1.f;
+  if (threadIdx.x == 0 && inv_scale) *inv_scale = 1.f / sc;
+  for (int e = threadIdx.x; e < JB * JB; e += 1024) {
+    const int i = e / JB, k = e - i * JB;
+    const float2 v = k < i ? make_float2(-Linv[e].x, -Linv[e].y) : make_float2(0.f, 0.f);
+    put4(M, mplane, (size_t)i * 128 + k, v, fmt, sc);
+  }
 }
 
 // max(|Re|, |Im|) over rows k0..k0+jb-1, columns c0..c0+ncols-1 of A -> atomicMax on
@@ -1521,14 +1651,17 @@ int panel_cluster_max(rmat_ctx c) {
   return m;
 }
 
-// Cluster size for a panel of M rows: about 128 rows per CTA, up to the device's
-// maximum; 0 when the rows do not fit the cluster's shared memory (grid variant).
+// Cluster size for a panel of M rows: about 128 rows per CTA (complex64) or 32
+// (complex128: the rank-1 updates run at this part's FP64 rate, ~2 FMA per clock per
+// SM, so they are spread over more SMs), up to the device's maximum; 0 when the rows
+// do not fit the cluster's shared memory (grid variant).
 template <class T>
 int panel_cluster_size(rmat_ctx c, int M, int jb, int* rpc_out, int* ldr_out) {
   const int cmax = panel_cluster_max<T>(c);
   if (cmax == 0) return 0;
+  const int per = sizeof(T) == 8 ? 32 : 128;
   int cs = 1;
-  while (cs < cmax && ceil_div(M, cs) > 128) cs *= 2;
+  while (cs < cmax && ceil_div(M, cs) > per) cs *= 2;
   const int rpc = ceil_div(M, cs);
   const size_t limit = panel_smem_limit(c);
   int ldr = jb + 1;
@@ -1827,6 +1960,9 @@ int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb,
     if (JB / 16 > 8)  // a 16-CTA cluster is beyond the portable size
       RMAT_CU(cudaFuncSetAttribute(apply_inv_kernel<JB>,
                                    cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    RMAT_CU(cudaFuncSetAttribute(apply_inv_kernel<JB>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     attr = true;
   }
   // JB = 256: the pair inverses (blocks of 256 rows, table index k0 / 256)
@@ -1882,9 +2018,9 @@ int finish_fpl_order(rmat_ctx c, int n, int nb, const LUPerm& pm) {
 }
 
 // U12 = L11^-1 (P A12) for a full complex64 block through its inverse: L11^-1 is formed
-// right after the panel (identity + the register-blocked block solve, one block) into
-// its slot of the solve-path inverse table, then applied to all trailing columns by
-// the cluster kernel of the solve path (gather of the interchanged rows included).
+// right after the panel (tri_inv_lower_kernel, one CTA) into its slot of the solve-path
+// inverse table, then applied to all trailing columns on the tensor cores (the
+// interchanges applied first; launch_u12_tc).
 // Block widths 64 and 128; returns false when it does not apply.
 template <int JB>
 int u12_by_inverse_jb(rmat_ctx c, float2* A, int ld, int n, int k0, const LUPerm* pm, int col0,
@@ -1893,21 +2029,38 @@ int u12_by_inverse_jb(rmat_ctx c, float2* A, int ld, int n, int k0, const LUPerm
   const size_t per = (size_t)JB * JB;
   RMAT_CHECK(rmat_grow(c, &c->Dinv, &c->Dinv_cap, 2 * per * nfull * sizeof(float2)));
   float2* Lk = reinterpret_cast<float2*>(c->Dinv) + (size_t)(k0 / JB) * per;
-  identity_blocks_kernel<float><<<ceil_div((long long)per, 256), 256, 0, c->stream>>>(Lk, JB, per);
   static bool attr = false;
-  const size_t smem = solve_block_smem<float, JB>();
+  const size_t smem = (size_t)(JB * (JB + 1) + (JB / 2) * (JB / 2 + 1)) * sizeof(float2);
   if (!attr) {
-    RMAT_CU(cudaFuncSetAttribute(solve_block_kernel<float, true, JB>,
+    RMAT_CU(cudaFuncSetAttribute(tri_inv_lower_kernel<JB>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  solve_block_kernel<float, true, JB><<<dim3(JB / 32, 1), 256, smem, c->stream>>>(
-      A + (size_t)k0 * ld + k0, ld, 0, Lk, JB, JB, JB, nullptr, nullptr, nullptr, nullptr, 0, per, 0,
-      nullptr, nullptr);
-  c->launches += 2;
+  tri_inv_lower_kernel<JB><<<1, TINV_THREADS, smem, c->stream>>>(A, ld, k0, Lk);
+  c->launches++;
   RMAT_CU(cudaGetLastError());
   if (ncols <= 0) return RMAT_OK;
-  return launch_apply_inv<JB>(c, false, k0, JB, A + col0, ld, ncols, pm, nullptr);
+  if (!c->Mpl || !c->Bpl) return launch_apply_inv<JB>(c, false, k0, JB, A + col0, ld, ncols, pm, nullptr);
+  // on the tensor cores, in place: U12 = A12 - (I - L11^-1) A12, after the interchanges
+  if (pm) RMAT_CHECK(apply_perm<float>(c, *pm, A + col0, ld, ncols, k0, JB, JB));
+  const int fmt = rmat_plane_fmt(c->precision);
+  const int sa = ceil_div(n, JB) + 1, sm = sa + 1;  // scale slots past the per-block ones
+  unsigned* um = fmt == 1 ? c->umax + sa : nullptr;
+  if (um) {
+    RMAT_CU(cudaMemsetAsync(um, 0, sizeof(unsigned), c->stream));
+    block_absmax_kernel<<<std::min(c->sm_count * 2, ceil_div((long long)JB * ncols, 256)), 256, 0,
+                          c->stream>>>(A, ld, k0, JB, col0, ncols, um, nullptr);
+    c->launches++;
+  }
+  split_block_kernel<<<dim3(ceil_div(ncols, 32), JB / 32), 256, 0, c->stream>>>(
+      A + (size_t)k0 * ld + col0, ld, JB, ncols, nullptr, 0, 0, 0, 0, c->Bpl,
+      (size_t)n * RMAT_MAX_NB, col0, 0, fmt, um, fmt == 1 ? c->uscale + sa : nullptr, nullptr,
+      nullptr);
+  minv_planes_kernel<<<1, 1024, 0, c->stream>>>(Lk, JB, c->Mpl, (size_t)128 * 128, fmt,
+                                                c->uscale + sm);
+  c->launches += 2;
+  RMAT_CU(cudaGetLastError());
+  return launch_u12_tc(c, n, k0, JB, col0, ncols, c->uscale + sm, c->uscale + sa);
 }
 
 int u12_by_inverse(rmat_ctx c, float2* A, int ld, int n, int k0, int nb, const LUPerm* pm,
@@ -1973,11 +2126,19 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
     c->launches++;
   };
   auto prep = [&](int k0) -> int {
+    if (ldlt) return RMAT_OK;  // identity interchanges, listed once before the loop
     perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt, pm.src,
                                               c->dstat);
     c->launches++;
     return permute_fpl_left(c, n, ld, k0, nb, pm);  // F's L parts follow every interchange
   };
+  if (ldlt) {  // every block's (identity) row list at once, for the solves
+    identity_pivots_kernel<<<ceil_div(n, 256), 256, 0, c->stream>>>(ipiv, n);
+    perm_prep_kernel<<<ceil_div(n, nb), 32, 0, c->stream>>>(ipiv, n, nb, 0, pm.rows, pm.idx,
+                                                           pm.cnt, pm.src, c->dstat);
+    c->launches += 2;
+    RMAT_CU(cudaGetLastError());
+  }
   // U12 = L11^-1 (rows k0.., columns col0..col0+ncols), interchanges applied when perm
   auto trsm = [&](int k0, int jb, int col0, int ncols, bool perm) -> int {
     bool fused = false;
@@ -2236,14 +2397,21 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     return RMAT_OK;
   };
   const bool la_fwd = tc && c->solve_lookahead && fpm == nullptr && c->side;
-  // 256-row steps over pairs of blocks with a composed inverse (no look-ahead, rows
-  // pre-gathered)
-  const bool pairs = tc && !c->solve_lookahead && fpm == nullptr && nb == 128 &&
-                     c->inv_nb == nb && c->inv_pairs > 0 && !c->pairs_off;
-  for (int k0 = 0, jb = 0; k0 < n; k0 += jb) {
-    const bool pstep = pairs && k0 % 256 == 0 && k0 / 256 < c->inv_pairs;
+  // 256-row steps over pairs of blocks with a composed inverse (rows pre-gathered)
+  const bool pairs = tc && fpm == nullptr && nb == 128 && c->inv_nb == nb && c->inv_pairs > 0 &&
+                     !c->pairs_off;
+  auto pair_at = [&](int r0) { return pairs && r0 % 256 == 0 && r0 / 256 < c->inv_pairs; };
+  // the look-ahead's update of the next step's rows (few output tiles, on the SMs the
+  // far update leaves free) splits its K range over CTAs
+  auto ksplit_for = [&](int jbk) {
+    const int kst = fmt == 1 ? 16 : 8, steps = (int)round_up(jbk, kst) / kst;
+    return steps % 4 == 0 ? 4 : steps % 2 == 0 ? 2 : 1;
+  };
+  int step = 0;
+  for (int k0 = 0, jb = 0; k0 < n; k0 += jb, ++step) {
+    const bool pstep = pair_at(k0);
     jb = pstep ? 256 : std::min(nb, n - k0);
-    const int b = (k0 / nb) & 1;
+    const int b = step & 1;
     if (tc) {
       RMAT_CHECK(la_wait(b));
       c->ybuf = b;
@@ -2273,11 +2441,13 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
       if (need_y) RMAT_CHECK(split_y(k0, jb));
     }
     if (need_y) {
-      const int row0 = k0 + jb, M = n - k0 - jb, near = std::min(nb, M);
+      const int row0 = k0 + jb, M = n - k0 - jb;
+      const int near = std::min(pair_at(row0) ? 256 : nb, M);
       if (!la_fwd || near >= M) {
         RMAT_CHECK(launch_solve_tc(c, row0, M, nrhs, k0, jb, row0, n, nullptr, nb));
       } else {
-        RMAT_CHECK(launch_solve_tc(c, row0, near, nrhs, k0, jb, row0, n, nullptr, nb));
+        RMAT_CHECK(launch_solve_tc(c, row0, near, nrhs, k0, jb, row0, n, nullptr, nb,
+                                   ksplit_for(jb)));
         RMAT_CU(cudaEventRecord(c->la_ev[b], main_s));
         RMAT_CU(cudaStreamWaitEvent(c->side, c->la_ev[b], 0));
         c->stream = c->side;
@@ -2299,13 +2469,15 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
   // in the forward sweep, the next block being the one above
   const bool la_bwd = tc && c->solve_lookahead && c->side;
   const int last = ((n - 1) / nb) * nb;
-  for (int kb = last; kb >= 0;) {
-    // a pair step covers this block and the one above when this is a pair's second block
-    const bool pstep = pairs && (kb / nb) % 2 == 1 && (kb / nb) / 2 < c->inv_pairs;
+  // a pair step covers block kb and the one above when kb is a pair's second block
+  auto pair_end = [&](int kb) { return pairs && (kb / nb) % 2 == 1 && (kb / nb) / 2 < c->inv_pairs; };
+  step = 0;
+  for (int kb = last; kb >= 0; ++step) {
+    const bool pstep = pair_end(kb);
     const int k0 = pstep ? kb - nb : kb;
     const int jb = pstep ? 256 : std::min(nb, n - k0);
     kb = k0 - nb;
-    const int b = (k0 / nb) & 1;
+    const int b = step & 1;
     if (tc) {
       RMAT_CHECK(la_wait(b));
       c->ybuf = b;
@@ -2336,11 +2508,12 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     if (need_y) {
       // A = U rows of earlier row blocks: their per-block scales apply row-wise
       const float* rs = fmt == 1 ? c->uscale : nullptr;
-      const int near = std::min(nb, k0);
+      const int near = std::min(pair_end(kb) ? 256 : nb, k0);  // the next (upper) step's rows
       if (!la_bwd || near >= k0) {
         RMAT_CHECK(launch_solve_tc(c, 0, k0, nrhs, k0, jb, 0, n, rs, nb));
       } else {
-        RMAT_CHECK(launch_solve_tc(c, k0 - near, near, nrhs, k0, jb, k0 - near, n, rs, nb));
+        RMAT_CHECK(launch_solve_tc(c, k0 - near, near, nrhs, k0, jb, k0 - near, n, rs, nb,
+                                   ksplit_for(jb)));
         RMAT_CU(cudaEventRecord(c->la_ev[b], main_s));
         RMAT_CU(cudaStreamWaitEvent(c->side, c->la_ev[b], 0));
         c->stream = c->side;

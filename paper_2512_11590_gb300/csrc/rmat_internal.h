@@ -166,9 +166,11 @@ struct rmat_ctx_s {
   void* Pscr = nullptr;    size_t Pscr_cap = 0;     // scratch of their composition
   int inv_pairs = 0;       // pairs with a 256-row inverse (0: 128-row solve steps only)
   bool pairs_off = false;  // 128-row steps although pair inverses exist (refinement fallback)
+  int la_free_sms = 16;    // SMs a look-ahead far update leaves to the next step's row update
   int solve_blk = 256;     // RMAT_PARAM_SOLVE_BLOCK: rows per tensor-path solve step (256 or 128)
   int inv_blocks = 0, inv_nb = 0;      // right-hand-side block planes [4][RMAT_YPL_ROWS][256]
   void* Bpl = nullptr;     size_t Bpl_cap = 0;      // tensor B operand planes (U12^T split)
+  void* Mpl = nullptr;     size_t Mpl_cap = 0;      // (I - L11^-1) planes, A operand of the U12 product
   int* pfwd = nullptr;     size_t pfwd_cap = 0;     // composed row permutation (tensor forward solve)
   // FP16 planes: per U block max bits and inverse scale 2^e, per right-hand-side
   // column inverse scale of the current solved block
@@ -179,7 +181,7 @@ struct rmat_ctx_s {
   // buffer ybuf = k & 1, so block k+1's diagonal application can run while the
   // far-row update of block k (on the side stream) still reads buffer k & 1.
   int ybuf = 0;
-  int solve_lookahead = 0;         // RMAT_PARAM_SOLVE_LOOKAHEAD
+  int solve_lookahead = 1;         // RMAT_PARAM_SOLVE_LOOKAHEAD
   cudaStream_t side = nullptr;     // look-ahead stream of the solves
   cudaEvent_t la_ev[4] = {};       // fork / join events of the look-ahead
   double* Dsc = nullptr;   size_t Dsc_cap = 0;      // equilibration scale per row
@@ -262,10 +264,15 @@ int launch_radial_to_channel(rmat_ctx c);
 int launch_apply_resid(rmat_ctx c, const double2* Xin, double2* Rout);
 int rmat_solve_system(rmat_ctx c);
 int gmres_correction(rmat_ctx c, int m, double tau, int* inner);
+// U12 = L11^-1 A12 in place on the tensor cores: C[k0.., col0..] -= Mpl B with the
+// (I - L11^-1) planes in c->Mpl and A12^T split in c->Bpl rows col0.. (FP16 planes:
+// inverse scales *minv_scale of Mpl and *b_scale of Bpl).
+int launch_u12_tc(rmat_ctx c, int n, int k0, int jb, int col0, int ncols, const float* minv_scale,
+                  const float* b_scale);
 int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, int K, int ax0,
                      const float* cscal, bool upper = false);
 int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n,
-                    const float* rowscale, int rs_div);
+                    const float* rowscale, int rs_div, int ksplit = 1);
 int tc_prepare(rmat_ctx c, int n, int nrhs);
 void tc_release(rmat_ctx c);
 // lu.cu (SIMT complex GEMM C -= A B, row-major)

@@ -228,19 +228,24 @@ def test_panel_rows_in_global_memory(g, ctx, prec, nb, ctas):
 
 
 @pytest.mark.parametrize("prec", [1, 3])
-def test_solve_lookahead_vs_oracle(g, prec):
-    """RMAT_PARAM_SOLVE_LOOKAHEAD = 1: next-block updates on the main stream, far
-    rows on the side stream, double-buffered Y planes; same tolerances."""
+@pytest.mark.parametrize("nb,shape", [(64, (16, 100)), (128, (16, 100)), (128, (29, 50))])
+def test_solve_lookahead_vs_oracle(g, prec, nb, shape):
+    """RMAT_PARAM_SOLVE_LOOKAHEAD = 1: next-step updates on the main stream (K split
+    over CTAs), far rows on the side stream, double-buffered Y planes; with block
+    width 128 the steps are pairs of blocks (N = 1450: five pairs, one single block
+    and a 42-row tail); same tolerances."""
     import torch
     torch.cuda.set_device(0)
-    p = cp.config3(16)
-    ref = truth(p, "c3-16")
+    nch, nlag = shape
+    p = cp.config3(16) if shape == (16, 100) else cp.make_problem(900 + nch, nch, nlag, 11.0)
+    ref = truth(p, "c3-16" if shape == (16, 100) else ("steps", nch, nlag))
     h = g.rmat_create(0, torch.cuda.current_stream().cuda_stream)
     try:
         g.rmat_set_param(h, g.RMAT_PARAM_SOLVE_LOOKAHEAD, 1)
-        out = run_problem(h, p, prec, max_refine=30, tol=1e-14, nb=64)
+        out = run_problem(h, p, prec, max_refine=30, tol=1e-14, nb=nb)
     finally:
         g.rmat_destroy(h)
+    assert out["status"] == g.RMAT_OK
     for k in ("U", "R", "X"):
         e = relerr(out[k], ref[k])
         assert e < TOL[prec], (k, e)

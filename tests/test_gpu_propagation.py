@@ -136,13 +136,19 @@ def test_propagation_argument_errors(g, ctx):
 @pytest.mark.parametrize("prec", [3, 0])
 def test_concurrent_sectors_equal_sequential(g, ctx, prec):
     """Sectors on worker contexts (own streams and host threads) give the same R
-    and U as one after the other on the caller's context."""
+    and U as one after the other on the caller's context (solve look-ahead off on the
+    caller, as on the workers: its concurrent reduce-adds would vary the last bits
+    from run to run)."""
     p = cp.charged_problem(27, 4, 48, 25.0)
     radii = [0.0, 6.0, 12.0, 18.0, 24.0]
-    g.rmat_set_param(ctx, g.RMAT_PARAM_PROP_CONCURRENT, 0)
-    R0, U0, _ = run_prop(g, ctx, p, radii, prec)
-    g.rmat_set_param(ctx, g.RMAT_PARAM_PROP_CONCURRENT, 1)
-    R1, U1, _ = run_prop(g, ctx, p, radii, prec)
-    R2, U2, _ = run_prop(g, ctx, p, radii, prec)          # workers reused
+    g.rmat_set_param(ctx, g.RMAT_PARAM_SOLVE_LOOKAHEAD, 0)
+    try:
+        g.rmat_set_param(ctx, g.RMAT_PARAM_PROP_CONCURRENT, 0)
+        R0, U0, _ = run_prop(g, ctx, p, radii, prec)
+        g.rmat_set_param(ctx, g.RMAT_PARAM_PROP_CONCURRENT, 1)
+        R1, U1, _ = run_prop(g, ctx, p, radii, prec)
+        R2, U2, _ = run_prop(g, ctx, p, radii, prec)      # workers reused
+    finally:
+        g.rmat_set_param(ctx, g.RMAT_PARAM_SOLVE_LOOKAHEAD, 1)
     assert relerr(U1, U0) < 1e-14 and relerr(R1, R0) < 1e-14
     assert relerr(U2, U1) < 1e-14
