@@ -161,7 +161,10 @@ def stage_rooflines(stats, N, nch, nb, iters, pk, src):
                                 "achieved_tflops": fl / (ms * 1e-3) / 1e12,
                                 "peak": FP64_NOMINAL_TFLOPS,
                                 "frac": fl / (ms * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS,
-                                "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
+                                "peak_source": "nominal GB300 FP64 (no measured FP64 peak)",
+                                "note": "FP64-accurate products; from nch >= 32 they run as "
+                                        "exact integer-digit products on the FP16 tensor cores "
+                                        "(a frac above 1 is that arithmetic, not FP64 units)"}
     return out
 
 
@@ -760,8 +763,8 @@ def main():
     ap.add_argument("--factor", default="lu", choices=["lu", "ldlt"],
                     help="main line's factorisation: LU with partial pivoting or LDL^T")
     ap.add_argument("--no-ldlt", action="store_true", help="skip the LDL^T comparison leg")
-    ap.add_argument("--residual", default="auto", choices=["auto", "fp64mma", "tensor"],
-                    help="point-coupling product of the FP64 residual (RMAT_PARAM_RESIDUAL)")
+    ap.add_argument("--residual", default="auto", choices=["auto", "fp64mma", "tensor", "tensor-all"],
+                    help="products of the FP64 residual (RMAT_PARAM_RESIDUAL 0..3)")
     ap.add_argument("--solve-block", type=int, default=0, choices=[0, 128, 256],
                     help="rows per tensor-path solve step (RMAT_PARAM_SOLVE_BLOCK; 0 = 256)")
     ap.add_argument("--refine", type=int, default=0,
@@ -840,7 +843,7 @@ def main():
     prec = {"tf32": g.RMAT_C64_3XTF32_IR, "f16": g.RMAT_C64_3XF16_IR,
             "f16x1": g.RMAT_C64_1XF16_IR, "simt": g.RMAT_C64_SIMT_IR}[args.precision]
     method = 1 if args.method == "woodbury" else 0
-    resid = {"auto": 0, "fp64mma": 1, "tensor": 2}[args.residual]
+    resid = {"auto": 0, "fp64mma": 1, "tensor": 2, "tensor-all": 3}[args.residual]
     factor = 1 if args.factor == "ldlt" else 0
     run = Runner(p, prec, local, method, 0 if args.no_lookahead else 1, resid, args.solve_block,
                  factor)

@@ -124,14 +124,19 @@ extern "C" {
  * panel, every sector then uses width 64.  0 = sectors one after the other.
  * Results agree to rounding (identical when the block width is the same). */
 #define RMAT_PARAM_PROP_CONCURRENT 10
-/* Point-coupling product of the FP64 refinement residual of assembled problems
- * (sum over al' of V_al,al'(r_i) X[(al',i),be], Sec. 3.2 with the block structure of
- * Sec. 2): 0 (default) auto = 2 when nch >= 32, else 1; 1 = FP64 on the FP64 tensor
- * instruction (mma.m8n8k4.f64); 2 = FP64-accurate on the FP16 tensor cores: every
- * row of V_i (diagonal excluded, applied in FP64) and every column of X_i scaled by a
- * power of two and cut into nine signed 6-bit integer digits, the digit products
- * with p + q <= 8 summed exactly in FP32 tensor memory and combined in FP64
- * (error below 2^-54 of the row and column scales; needs nch <= 2048, else 1). */
+/* Products of the FP64 refinement residual of assembled problems (Sec. 3.2 with the
+ * block structure of Sec. 2): the point couplings (sum over al' of V_al,al'(r_i)
+ * X[(al',i),be]) and the kinetic part (sum over j of K_ij X[(al,j),be]).
+ * 1 = couplings in FP64 on the FP64 tensor instruction (mma.m8n8k4.f64), kinetic in
+ * FP64; 2 = couplings FP64-accurate on the FP16 tensor cores: every row of V_i
+ * (diagonal excluded, applied in FP64) and every column of X_i scaled by a power of
+ * two and cut into nine signed 6-bit integer digits, the digit products with
+ * p + q <= 8 summed exactly in FP32 tensor memory and combined in FP64 (error below
+ * 2^-54 of the row and column scales; needs nch <= 2048, else 1), kinetic in FP64;
+ * 3 = both products that way (the kinetic one with rows of K and columns of X_al
+ * cut the same way; needs nlag <= 2048).  0 (default) auto = 3 when nch >= 32,
+ * nlag >= 32 and the kinetic sums are not compensated (RMAT_PARAM_RESID_SUMS), 2
+ * when nch >= 32, else 1.  Propagation sectors keep the kinetic part in FP64. */
 #define RMAT_PARAM_RESIDUAL 11
 /* Tile width (output columns per CTA tile) of the factor's tensor-core trailing
  * updates: 256 (0 = default) or 128 (twice the tiles, two accumulator sets per CTA:

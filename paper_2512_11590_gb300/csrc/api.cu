@@ -364,7 +364,7 @@ int rmat_set_param(rmat_ctx c, int key, long long v) {
       c->prop_concurrent = (int)v;
       return RMAT_OK;
     case RMAT_PARAM_RESIDUAL:
-      if (v < 0 || v > 2) return -3;
+      if (v < 0 || v > 3) return -3;
       c->resid_param = (int)v;
       return RMAT_OK;
     case RMAT_PARAM_TC_BN:
@@ -471,6 +471,7 @@ static int assemble_impl(rmat_ctx c, const rmat_problem* pb, double E, const voi
     RMAT_CHECK(rmat_grow(c, (void**)&c->rmesh, &c->rmesh_cap, nlag * 8));
     RMAT_CHECK(rmat_grow(c, (void**)&c->fa, &c->fa_cap, nlag * 8));
     RMAT_CU(cudaMemcpy(c->Kmat, K.data(), K.size() * 8, cudaMemcpyHostToDevice));
+    c->kmat_gen++;  // the tensor-core residual's digit planes of K follow
     RMAT_CU(cudaMemcpy(c->T0, T0.data(), T0.size() * 8, cudaMemcpyHostToDevice));
     RMAT_CU(cudaMemcpy(c->rmesh, r.data(), nlag * 8, cudaMemcpyHostToDevice));
     RMAT_CU(cudaMemcpy(c->fa, fa.data(), nlag * 8, cudaMemcpyHostToDevice));

@@ -565,9 +565,10 @@ int launch_u12_tc(rmat_ctx c, int n, int k0, int jb, int col0, int ncols, const 
   }
   for (int q = 0; q < 4; ++q) g_tc.u12.b[q] = g_tc.upd128.b[q];
   g_tc.u12.c = g_tc.upd.c;
-  // one 128-row tile row: the K range in two parts doubles the CTAs at work
+  // one 128-row tile row; no split of K (one reduce-add per element: every bit
+  // reproducible)
   TcScales sc{fmt == 1 ? minv_scale : nullptr, 128, nullptr, fmt == 1 ? b_scale : nullptr, nullptr,
-              0, 2};
+              0, 1};
   return launch_tc<128>(c, g_tc.u12, col0, k0, jb, ncols, jb, 0, 0, 0, col0, sc, false);
 }
 

@@ -2040,8 +2040,12 @@ int u12_by_inverse_jb(rmat_ctx c, float2* A, int ld, int n, int k0, const LUPerm
   c->launches++;
   RMAT_CU(cudaGetLastError());
   if (ncols <= 0) return RMAT_OK;
-  if (!c->Mpl || !c->Bpl) return launch_apply_inv<JB>(c, false, k0, JB, A + col0, ld, ncols, pm, nullptr);
-  // on the tensor cores, in place: U12 = A12 - (I - L11^-1) A12, after the interchanges
+  // On the tensor cores, in place: U12 = A12 - (I - L11^-1) A12, after the interchanges.
+  // The FP16 planes carry one power-of-two scale per block, so only when the rows of a
+  // block are of one magnitude: the symmetric equilibration (unit diagonal) sees to
+  // that; otherwise the CUDA-core application keeps every entry's relative precision.
+  if (!c->Mpl || !c->Bpl || !c->equil)
+    return launch_apply_inv<JB>(c, false, k0, JB, A + col0, ld, ncols, pm, nullptr);
   if (pm) RMAT_CHECK(apply_perm<float>(c, *pm, A + col0, ld, ncols, k0, JB, JB));
   const int fmt = rmat_plane_fmt(c->precision);
   const int sa = ceil_div(n, JB) + 1, sm = sa + 1;  // scale slots past the per-block ones

@@ -60,8 +60,23 @@ struct OzPlan {
 };
 
 struct OzMaps {
-  CUtensorMap a;  // W digit planes: rows ((s*2 + part)*nlag + i)*nch + al, K = al'
-  CUtensorMap b;  // X digit planes: rows ((s*2 + part)*nlag + i)*nrhs + be, K = al'
+  CUtensorMap a;  // A digit planes: rows ((s*2 + part)*a_pts + pt)*a_rows + row
+  CUtensorMap b;  // X digit planes: rows ((s*2 + part)*npts + pt)*nrhs + be
+};
+
+// Which product a launch forms.  Coupling: points = mesh points i, A = W_i (rows al,
+// K = al', one per point, complex), output row (al, i).  Kinetic: points = channels
+// al, A = the real kinetic matrix (rows i, K = j, shared by every channel), output
+// row (al, i).
+struct OzGeom {
+  int npts;          // points (independent products)
+  int mrows;         // A rows per point (nch or nlag)
+  int a_rows;        // A plane rows per point (mrows, or padded to the tile)
+  int a_pts;         // A planes per digit and part: npts, or 1 (shared by every point)
+  int a_real;        // A is real: two MMAs per K-step, its imaginary planes never read
+  int pt_major;      // output row pt * nlag + row (kinetic) instead of row * nlag + pt
+  int ew_shared;     // A row exponents per row only (not per point)
+  int nlag;
 };
 
 // The nine signed 6-bit digits of v (|v| < 1): the base-64 expansion of |v| cut after
@@ -116,13 +131,43 @@ oz_split_w_kernel(const double2* __restrict__ W, int nlag, int nch, int kpad,
   }
 }
 
-// X (FP64, row-major [(al',i)][be]) -> digit planes [s][part][i][be][al'] with one
-// exponent per (i, be): max over al' first, then 32 x 32 blocks transposed through
-// shared memory so the planes are written along al'.
+// The real kinetic matrix K (nlag x nlag, FP64, row-major) -> digit planes
+// [s][part 0][row][kpad] with rows padded to a_rows (zeros); one exponent per row
+// over the whole row.  One warp per row.
+__global__ void __launch_bounds__(256)
+oz_split_k_kernel(const double* __restrict__ K, int nlag, int a_rows, int kpad,
+                  __half* __restrict__ Ksl, int* __restrict__ ek) {
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= a_rows) return;
+  const double* kr = K + (size_t)row * nlag;
+  double m = 0.0;
+  if (row < nlag)
+    for (int k = lane; k < nlag; k += 32) m = fmax(m, fabs(kr[k]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int e = m > 0.0 ? ilogb(m) + 1 : 0;
+  if (lane == 0) ek[row] = e;
+  const size_t plane = (size_t)a_rows * kpad;
+  const double sc = oz_scale(e);
+  for (int k = lane; k < kpad; k += 32) {
+    const double v = (row < nlag && k < nlag) ? kr[k] : 0.0;
+    __half d[OZ_S];
+    oz_digits(v, sc, e, d);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) Ksl[(size_t)(2 * s) * plane + (size_t)row * kpad + k] = d[s];
+  }
+}
+
+// X (FP64, row-major [(al',j)][be]) -> digit planes [s][part][pt][be][k] with one
+// exponent per (pt, be): max over k first, then 32 x 32 blocks transposed through
+// shared memory so the planes are written along k.  The element of point pt and K
+// index k is row pt * pt_stride + k * k_stride of X: the coupling product takes
+// pt = mesh point i, k = channel al' (strides 1, nlag), the kinetic product pt =
+// channel al, k = mesh point j (strides nlag, 1).
 constexpr int OZ_XT = 32;
 __global__ void __launch_bounds__(256)
-oz_split_x_kernel(const double2* __restrict__ X, int nrhs, int nlag, int nch, int kpad,
-                  __half* __restrict__ Xsl, int* __restrict__ fx, const int* __restrict__ skip) {
+oz_split_x_kernel(const double2* __restrict__ X, int nrhs, int npts, int kext, int pt_stride,
+                  int k_stride, int kpad, __half* __restrict__ Xsl, int* __restrict__ fx,
+                  const int* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ double red[8][OZ_XT];
   __shared__ int s_f[OZ_XT];
@@ -133,8 +178,8 @@ oz_split_x_kernel(const double2* __restrict__ X, int nrhs, int nlag, int nch, in
   const int be = b0 + lane;
   double m = 0.0;
   if (be < nrhs)
-    for (int a = warp; a < nch; a += 8) {
-      const double2 x = X[((size_t)a * nlag + i) * nrhs + be];
+    for (int a = warp; a < kext; a += 8) {
+      const double2 x = X[((size_t)i * pt_stride + (size_t)a * k_stride) * nrhs + be];
       m = fmax(m, fmax(fabs(x.x), fabs(x.y)));
     }
   red[warp][lane] = m;
@@ -147,13 +192,13 @@ oz_split_x_kernel(const double2* __restrict__ X, int nrhs, int nlag, int nch, in
     if (be < nrhs) fx[(size_t)i * nrhs + be] = f;
   }
   __syncthreads();
-  const size_t plane = (size_t)nlag * nrhs * kpad;
+  const size_t plane = (size_t)npts * nrhs * kpad;
   for (int c0 = 0; c0 < kpad; c0 += OZ_XT) {
     for (int a = warp; a < OZ_XT; a += 8) {
       const int ga = c0 + a;
       double vr = 0.0, vi = 0.0;
-      if (ga < nch && be < nrhs) {
-        const double2 x = X[((size_t)ga * nlag + i) * nrhs + be];
+      if (ga < kext && be < nrhs) {
+        const double2 x = X[((size_t)i * pt_stride + (size_t)ga * k_stride) * nrhs + be];
         vr = x.x;
         vi = x.y;
       }
@@ -182,10 +227,10 @@ oz_split_x_kernel(const double2* __restrict__ X, int nrhs, int nlag, int nch, in
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-oz_coupling_kernel(const __grid_constant__ OzMaps maps, const __grid_constant__ OzPlan plan,
-                   double2* __restrict__ R, int nrhs, int nlag, int nch, int kpad,
-                   const int* __restrict__ ew, const int* __restrict__ fx,
-                   const int* __restrict__ skip, int* __restrict__ err) {
+oz_product_kernel(const __grid_constant__ OzMaps maps, const __grid_constant__ OzPlan plan,
+                  const OzGeom geo, double2* __restrict__ R, int nrhs, int kpad,
+                  const int* __restrict__ ew, const int* __restrict__ fx,
+                  const int* __restrict__ skip, int* __restrict__ err) {
   if (skip && *skip) return;  // before any barrier or TMEM allocation
   extern __shared__ unsigned char smem_raw[];
   unsigned char* stages =
@@ -196,8 +241,8 @@ oz_coupling_kernel(const __grid_constant__ OzMaps maps, const __grid_constant__ 
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mt = (nch + OZ_BM - 1) / OZ_BM, nt = (nrhs + OZ_BN - 1) / OZ_BN;
-  const int ntiles = nlag * mt * nt;
+  const int mt = (geo.mrows + OZ_BM - 1) / OZ_BM, nt = (nrhs + OZ_BN - 1) / OZ_BN;
+  const int ntiles = geo.npts * mt * nt;
   const int ksteps = kpad / OZ_BK;
   const int G = plan.ngroups;
 
@@ -235,17 +280,20 @@ oz_coupling_kernel(const __grid_constant__ OzMaps maps, const __grid_constant__ 
         for (int g = 0; g < G && ok; ++g)
           for (int pr = plan.first[g]; pr < plan.first[g] + plan.count[g] && ok; ++pr) {
             const int p = plan.p[pr], q = plan.q[pr];
-            const int ar = ((2 * p) * nlag + i) * nch + m0, ai = ((2 * p + 1) * nlag + i) * nch + m0;
-            const int br = ((2 * q) * nlag + i) * nrhs + n0, bi = ((2 * q + 1) * nlag + i) * nrhs + n0;
+            const int ia = geo.a_pts == 1 ? 0 : i;
+            const int ar = ((2 * p) * geo.a_pts + ia) * geo.a_rows + m0;
+            const int ai = ((2 * p + 1) * geo.a_pts + ia) * geo.a_rows + m0;
+            const int br = ((2 * q) * geo.npts + i) * nrhs + n0;
+            const int bi = ((2 * q + 1) * geo.npts + i) * nrhs + n0;
             for (int ks = 0; ks < ksteps; ++ks, ++it) {
               const uint32_t s = it % OZ_STAGES, ph = (it / OZ_STAGES) & 1;
               if (!mbar_wait(smem_u32(&bars[OZ_STAGES + s]), ph ^ 1, abort_flag)) { ok = false; break; }
               const uint32_t full = smem_u32(&bars[s]);
-              mbar_expect_tx(full, OZ_STAGE);
+              mbar_expect_tx(full, geo.a_real ? OZ_STAGE - OZ_A_BYTES : OZ_STAGE);
               const uint32_t st = smem_u32(stages + s * OZ_STAGE);
               const int x = ks * OZ_BK;
               tma_load_2d(st, &maps.a, x, ar, full);
-              tma_load_2d(st + OZ_A_BYTES, &maps.a, x, ai, full);
+              if (!geo.a_real) tma_load_2d(st + OZ_A_BYTES, &maps.a, x, ai, full);
               tma_load_2d(st + 2 * OZ_A_BYTES, &maps.b, x, br, full);
               tma_load_2d(st + 2 * OZ_A_BYTES + OZ_B_BYTES, &maps.b, x, bi, full);
             }
@@ -288,9 +336,11 @@ oz_coupling_kernel(const __grid_constant__ OzMaps maps, const __grid_constant__ 
               const uint64_t b_r = sdesc_sw32(st + 2 * OZ_A_BYTES);
               const uint64_t b_i = sdesc_sw32(st + 2 * OZ_A_BYTES + OZ_B_BYTES);
               mma_issue<1>(dre, a_r, b_r, id_pos, first ? 0u : 1u);
-              mma_issue<1>(dre, a_i, b_i, id_neg, 1u);
               mma_issue<1>(dim, a_r, b_i, id_pos, first ? 0u : 1u);
-              mma_issue<1>(dim, a_i, b_r, id_pos, 1u);
+              if (!geo.a_real) {
+                mma_issue<1>(dre, a_i, b_i, id_neg, 1u);
+                mma_issue<1>(dim, a_i, b_r, id_pos, 1u);
+              }
               first = false;
               mma_commit(smem_u32(&bars[OZ_STAGES + s]));
             }
@@ -347,10 +397,11 @@ oz_coupling_kernel(const __grid_constant__ OzMaps maps, const __grid_constant__ 
         for (int c = 0; c < 32; ++c) aci[c] = fma((double)v[c], w, aci[c]);
       }
       if (!ok) break;
-      const int al = m0 + row;
-      if (al < nch) {
-        const int e = ew[(size_t)i * nch + al];
-        double2* r = R + ((size_t)al * nlag + i) * nrhs;
+      const int arow = m0 + row;
+      if (arow < geo.mrows) {
+        const int e = ew[(geo.ew_shared ? 0 : (size_t)i * geo.mrows) + arow];
+        double2* r = R + ((geo.pt_major ? (size_t)i * geo.nlag + arow
+                                         : (size_t)arow * geo.nlag + i)) * nrhs;
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int be = n0 + half * 32 + c;
@@ -403,6 +454,20 @@ struct OzState {
   __half* xsl = nullptr; size_t xsl_cap = 0;
   int* ew = nullptr;     size_t ew_cap = 0;
   int* fx = nullptr;     size_t fx_cap = 0;
+  // kinetic product: K's digit planes (once per mesh), X's along the mesh index
+  __half* ksl = nullptr; size_t ksl_cap = 0;
+  __half* xksl = nullptr; size_t xksl_cap = 0;
+  int* ek = nullptr;     size_t ek_cap = 0;
+  int* fxk = nullptr;    size_t fxk_cap = 0;
+  const void* k_src = nullptr;
+  long long k_gen = -1;
+  int k_nlag = -1;
+  OzMaps kmaps;
+  const void* kmap_k = nullptr;
+  const void* kmap_x = nullptr;
+  int kmap_key[3] = {-1, -1, -1};
+  OzPlan kplan;
+  int kplan_kpad = -1;
   const void* w_src = nullptr;  // W digit planes built from this table ...
   long long w_gen = -1;         // ... at this point-coupling generation
   OzMaps maps;
@@ -420,6 +485,23 @@ OzState& oz_state(rmat_ctx c) {
 
 bool g_oz_attr = false;
 
+int launch_product(rmat_ctx c, const OzMaps& maps, const OzPlan& plan, const OzGeom& geo,
+                   double2* Rout, int kpad, const int* ew, const int* fx, const int* skip) {
+  if (!g_oz_attr) {
+    RMAT_CU(cudaFuncSetAttribute(oz_product_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)OZ_SMEM));
+    g_oz_attr = true;
+  }
+  const int tiles = geo.npts * ceil_div(geo.mrows, OZ_BM) * ceil_div(c->nrhs, OZ_BN);
+  const int grid = std::min(tiles, c->sm_count);
+  oz_product_kernel<<<grid, OZ_THREADS, OZ_SMEM, c->stream>>>(maps, plan, geo, Rout, c->nrhs, kpad,
+                                                              ew, fx, skip,
+                                                              c->dstat + ST_TIMEOUT);
+  c->launches++;
+  RMAT_CU(cudaGetLastError());
+  return RMAT_OK;
+}
+
 }  // namespace
 
 // Whether the residual of this context takes the tensor-core coupling product.
@@ -427,7 +509,7 @@ bool oz_enabled(rmat_ctx c) {
   if (c->kind != 1 || c->resid_param == 1) return false;
   const int kpad = (int)round_up(c->nch, 16);
   if (kpad > 2048) return false;
-  return c->resid_param == 2 || c->nch >= 32;
+  return c->resid_param >= 2 || c->nch >= 32;
 }
 
 // R -= (W_i off-diagonal) X_i at every mesh point on the tensor cores.
@@ -462,21 +544,61 @@ int launch_oz_coupling(rmat_ctx c, const double2* Xin, double2* Rout, const int*
     std::copy(key, key + 4, z.map_key);
   }
   dim3 gx(ceil_div(nrhs, OZ_XT), nlag);
-  oz_split_x_kernel<<<gx, 256, 0, c->stream>>>(Xin, nrhs, nlag, nch, kpad, z.xsl, z.fx, skip);
+  oz_split_x_kernel<<<gx, 256, 0, c->stream>>>(Xin, nrhs, nlag, nch, 1, nlag, kpad, z.xsl, z.fx,
+                                               skip);
   c->launches++;
   RMAT_CU(cudaGetLastError());
-  if (!g_oz_attr) {
-    RMAT_CU(cudaFuncSetAttribute(oz_coupling_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)OZ_SMEM));
-    g_oz_attr = true;
+  const OzGeom geo{nlag, nch, nch, nlag, 0, 0, 0, nlag};
+  return launch_product(c, z.maps, z.plan, geo, Rout, kpad, z.ew, z.fx, skip);
+}
+
+// Whether the kinetic part of the residual takes the tensor-core digit product too.
+bool oz_kinetic_enabled(rmat_ctx c) {
+  if (!oz_enabled(c) || c->sector) return false;
+  if (c->resid_param == 3) return c->nlag <= 2048;
+  const bool comp = c->resid_comp == 1 || (c->resid_comp == -1 && c->precision == RMAT_C128);
+  return c->resid_param == 0 && !comp && c->nlag >= 32 && c->nlag <= 2048;
+}
+
+// R -= K X_al for every channel al on the tensor cores (K the real kinetic matrix).
+int launch_oz_kinetic(rmat_ctx c, const double2* Xin, double2* Rout, const int* skip) {
+  OzState& z = oz_state(c);
+  const int nch = c->nch, nlag = c->nlag, nrhs = c->nrhs;
+  const int kpad = (int)round_up(nlag, 16), a_rows = (int)round_up(nlag, OZ_BM);
+  if (z.kplan_kpad != kpad) {
+    if (!make_plan(kpad, &z.kplan)) return RMAT_ESTATE;
+    z.kplan_kpad = kpad;
   }
-  const int tiles = nlag * ceil_div(nch, OZ_BM) * ceil_div(nrhs, OZ_BN);
-  const int grid = std::min(tiles, c->sm_count);
-  oz_coupling_kernel<<<grid, OZ_THREADS, OZ_SMEM, c->stream>>>(
-      z.maps, z.plan, Rout, nrhs, nlag, nch, kpad, z.ew, z.fx, skip, c->dstat + ST_TIMEOUT);
+  const size_t krows = (size_t)2 * OZ_S * a_rows, xrows = (size_t)2 * OZ_S * nch * nrhs;
+  RMAT_CHECK(rmat_grow(c, (void**)&z.ksl, &z.ksl_cap, krows * kpad * sizeof(__half)));
+  RMAT_CHECK(rmat_grow(c, (void**)&z.xksl, &z.xksl_cap, xrows * kpad * sizeof(__half)));
+  RMAT_CHECK(rmat_grow(c, (void**)&z.ek, &z.ek_cap, (size_t)a_rows * sizeof(int)));
+  RMAT_CHECK(rmat_grow(c, (void**)&z.fxk, &z.fxk_cap, (size_t)nch * nrhs * sizeof(int)));
+  if (z.k_src != c->Kmat || z.k_gen != c->kmat_gen || z.k_nlag != nlag ||
+      z.kmap_k != z.ksl) {  // K's digit planes, once per mesh
+    oz_split_k_kernel<<<ceil_div(a_rows, 8), 256, 0, c->stream>>>(c->Kmat, nlag, a_rows, kpad,
+                                                                  z.ksl, z.ek);
+    c->launches++;
+    RMAT_CU(cudaGetLastError());
+    z.k_src = c->Kmat;
+    z.k_gen = c->kmat_gen;
+    z.k_nlag = nlag;
+  }
+  const int key[3] = {nch, nrhs, kpad};
+  if (z.kmap_k != z.ksl || z.kmap_x != z.xksl || !std::equal(key, key + 3, z.kmap_key)) {
+    RMAT_CHECK(tc_make_plane_map_f16(&z.kmaps.a, z.ksl, kpad, (int)krows, kpad, OZ_BM));
+    RMAT_CHECK(tc_make_plane_map_f16(&z.kmaps.b, z.xksl, kpad, (int)xrows, kpad, OZ_BN));
+    z.kmap_k = z.ksl;
+    z.kmap_x = z.xksl;
+    std::copy(key, key + 3, z.kmap_key);
+  }
+  dim3 gx(ceil_div(nrhs, OZ_XT), nch);
+  oz_split_x_kernel<<<gx, 256, 0, c->stream>>>(Xin, nrhs, nch, nlag, nlag, 1, kpad, z.xksl, z.fxk,
+                                               skip);
   c->launches++;
   RMAT_CU(cudaGetLastError());
-  return RMAT_OK;
+  const OzGeom geo{nch, nlag, a_rows, 1, 1, 1, 1, nlag};
+  return launch_product(c, z.kmaps, z.kplan, geo, Rout, kpad, z.ek, z.fxk, skip);
 }
 
 void oz_release(rmat_ctx c) {
@@ -486,6 +608,10 @@ void oz_release(rmat_ctx c) {
   cudaFree(z.xsl);
   cudaFree(z.ew);
   cudaFree(z.fx);
+  cudaFree(z.ksl);
+  cudaFree(z.xksl);
+  cudaFree(z.ek);
+  cudaFree(z.fxk);
   delete &z;
   c->oz = nullptr;
 }

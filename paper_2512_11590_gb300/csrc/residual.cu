@@ -78,6 +78,27 @@ resid_kinetic_kernel(double2* __restrict__ R, const double2* __restrict__ X,
   }
 }
 
+// R = Phi - Wd X: the surface right-hand side and the diagonal point coupling
+// W_i[al][al] X[(al,i),be] in FP64, when the kinetic and the off-diagonal coupling
+// products are both formed on the tensor cores.
+__global__ void __launch_bounds__(256)
+resid_diag_kernel(double2* __restrict__ R, const double2* __restrict__ X, int nrhs, int nlag,
+                  int nch, const double2* __restrict__ Wd, const double* __restrict__ fa,
+                  const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const size_t total = (size_t)nch * nlag * nrhs;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int be = (int)(e % nrhs);
+    const size_t row = e / nrhs;
+    const int i = (int)(row % nlag), al = (int)(row / nlag);
+    const double2 w = Wd[((size_t)i * nch + al) * nch + al];
+    const double2 x = X[e];
+    const double phi = al == be ? fa[i] : 0.0;
+    R[e] = make_double2(phi - fma(w.x, x.x, -w.y * x.y), -fma(w.x, x.y, w.y * x.x));
+  }
+}
+
 __global__ void absx_kernel(const double2* __restrict__ X, double* __restrict__ Ax, size_t total) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x)
@@ -436,6 +457,14 @@ int grid_for(rmat_ctx c, size_t total) {
 int structured_residual(rmat_ctx c, const double2* Xin, double2* Rout, const int* skip) {
   const int nrhs = c->nrhs;
   const bool oz = oz_enabled(c);
+  if (oz_kinetic_enabled(c)) {  // every product on the tensor cores
+    resid_diag_kernel<<<grid_for(c, (size_t)c->N * nrhs), 256, 0, c->stream>>>(
+        Rout, Xin, nrhs, c->nlag, c->nch, c->Wpt, c->fa, skip);
+    c->launches++;
+    RMAT_CU(cudaGetLastError());
+    RMAT_CHECK(launch_oz_kinetic(c, Xin, Rout, skip));
+    return launch_oz_coupling(c, Xin, Rout, skip);
+  }
   dim3 gk(ceil_div(nrhs, 32), c->nch);
   const bool comp = c->resid_comp == 1 || (c->resid_comp == -1 && c->precision == RMAT_C128);
   if (comp)

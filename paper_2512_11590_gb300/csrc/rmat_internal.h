@@ -209,6 +209,7 @@ struct rmat_ctx_s {
   int factor_used = 0;     // what rmat_factor runs / last ran (1: LDL^T)
   int resid_comp = -1;     // compensated kinetic sums (RMAT_PARAM_RESID_SUMS; -1 = complex128 only)
   long long wpt_gen = 0;   // bumped whenever the point-coupling table is rewritten
+  long long kmat_gen = 0;  // bumped whenever the kinetic matrix is rewritten
   // CUDA graph of one complete solve (both sweeps), captured on first use and replayed
   // by every later solve with the same sizes, buffers and factor layout
   cudaGraphExec_t sg_exec = nullptr;
@@ -296,6 +297,8 @@ int structured_residual(rmat_ctx c, const double2* Xin, double2* Rout, const int
 int launch_to_colmajor(rmat_ctx c, const double2* src, double2* dst, int ld);
 int launch_from_colmajor(rmat_ctx c, const double2* src, int ld, double2* dst);
 int launch_oz_coupling(rmat_ctx c, const double2* Xin, double2* Rout, const int* skip);
+bool oz_kinetic_enabled(rmat_ctx c);
+int launch_oz_kinetic(rmat_ctx c, const double2* Xin, double2* Rout, const int* skip);
 void oz_release(rmat_ctx c);
 int launch_ir_state(rmat_ctx c, double tol, int patience, int last, IrState* st);
 // api.cu: solve + refinement enqueued without host synchronisation (fixed step

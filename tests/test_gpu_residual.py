@@ -1,8 +1,9 @@
 """The FP64 refinement residual r = Phi - C X on the GPU (-m gpu), through rmat_residual.
 
-Both point-coupling products (RMAT_PARAM_RESIDUAL = 1: FP64 tensor instruction;
-= 2: integer digit products on the FP16 tensor cores) are compared element by
-element with the oracle's double-double structured residual of the same X.  The
+Every product mode (RMAT_PARAM_RESIDUAL = 1: point couplings on the FP64 tensor
+instruction; = 2: point couplings as integer digit products on the FP16 tensor cores;
+= 3: the kinetic part that way too) is compared element by element with the oracle's
+double-double structured residual of the same X.  The
 bound is the rounding of an FP64 evaluation: 16 u max(|C||X|) (u = 2^-53; a sum
 of nlag + nch products rounds to ~sqrt(nlag + nch) u of its terms), checked on
 the truth solution (r cancels to ~1e-12 of Phi: the regime the refinement works
@@ -76,7 +77,7 @@ def test_residual_matches_double_double(g, ctx, case, which):
     r_dd = S.structured_residual_dd(p, V, X, Phi, m)
     C, _ = S.assemble_dense(p, V, m)
     scale = np.max(np.abs(C) @ np.abs(X))
-    for mode in (1, 2):
+    for mode in (1, 2, 3):
         r = gpu_residual(g, ctx, p, X, mode)
         err = np.max(np.abs(r - r_dd)) / (U64 * scale)
         print(f"{case} {which} mode {mode}: max|r - r_dd| = {err:.2f} u max|C||X|")
@@ -91,6 +92,7 @@ def test_residual_modes_agree_on_the_bench_family(g, ctx):
     X = (rng.standard_normal((p.N, p.nch)) + 1j * rng.standard_normal((p.N, p.nch))) * 1e-3
     r1 = gpu_residual(g, ctx, p, X, 1)
     r2 = gpu_residual(g, ctx, p, X, 2)
+    r3 = gpu_residual(g, ctx, p, X, 3)
     m = M.lagrange_mesh(p.nlag, p.a)
     V = cp.potential_at(p, m["r"])
     Kb = S.channel_blocks(p, V, m)
@@ -102,8 +104,9 @@ def test_residual_modes_agree_on_the_bench_family(g, ctx):
         Wabs[:, al, al] = 0.0
     absCX += np.einsum("iac,cib->aib", Wabs, X3)
     err = np.max(np.abs(r1 - r2)) / (U64 * np.max(absCX))
-    print(f"nch128: max|r_fp64mma - r_tensor| = {err:.2f} u max|C||X|")
-    assert err < 16.0
+    err3 = np.max(np.abs(r1 - r3)) / (U64 * np.max(absCX))
+    print(f"nch128: max|r_fp64mma - r_tensor| = {err:.2f}, kinetic too {err3:.2f} u max|C||X|")
+    assert err < 16.0 and err3 < 16.0
 
 
 def test_residual_argument_errors(g, ctx):
@@ -116,4 +119,4 @@ def test_residual_argument_errors(g, ctx):
         g.rmat_residual(ctx, 0, 2, X.data_ptr(), 2)
     assert ei.value.status == -2
     with pytest.raises(g.RmatError):
-        g.rmat_set_param(ctx, g.RMAT_PARAM_RESIDUAL, 3)
+        g.rmat_set_param(ctx, g.RMAT_PARAM_RESIDUAL, 4)
