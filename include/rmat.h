@@ -134,9 +134,11 @@ extern "C" {
  * p + q <= 8 summed exactly in FP32 tensor memory and combined in FP64 (error below
  * 2^-54 of the row and column scales; needs nch <= 2048, else 1), kinetic in FP64;
  * 3 = both products that way (the kinetic one with rows of K and columns of X_al
- * cut the same way; needs nlag <= 2048).  0 (default) auto = 3 when nch >= 32,
- * nlag >= 32 and the kinetic sums are not compensated (RMAT_PARAM_RESID_SUMS), 2
- * when nch >= 32, else 1.  Propagation sectors keep the kinetic part in FP64. */
+ * cut the same way; needs nlag <= 2048): faster, but K's rows are dominated by their
+ * diagonal, so the cut at 2^-54 of each row's largest entry leaves ~nlag/2 u of
+ * |K||X| per row and the refinement stops on a higher floor (about 2e-10 relative
+ * residual at N = 25600 instead of 1e-12).  0 (default) auto = 2 when nch >= 32,
+ * else 1.  Propagation sectors keep the kinetic part in FP64. */
 #define RMAT_PARAM_RESIDUAL 11
 /* Tile width (output columns per CTA tile) of the factor's tensor-core trailing
  * updates: 256 (0 = default) or 128 (twice the tiles, two accumulator sets per CTA:
@@ -167,6 +169,23 @@ extern "C" {
  * gives info > 0 as in LU.  The FP64 refinement is unchanged.  Other precisions,
  * the Woodbury system (RMAT_PARAM_METHOD = 1) and batches always pivot. */
 #define RMAT_PARAM_FACTOR 15
+/* Pivoted LU of the tensor-core precisions with paired panels (RMAT_PARAM_PAIRED = 1):
+ * 1 (default) = look-ahead: while the far block is at least RMAT_PARAM_LA_MIN_ROWS
+ * tall, each pair's far update is issued in two parts, the next pair's 2*nb columns
+ * first on the context's stream and the rest on a second stream with three pipeline
+ * stages (room on every SM for a panel CTA beside it); the next pair's two panels
+ * then run beside it on the same SMs as 32-column sub-panels (the interchanges, U12
+ * and the CUDA-core update of each sub-panel applied to the block's other columns
+ * and to the second panel's columns before the next sub-panel), and the interchanges
+ * that reach the far columns and the earlier L columns wait for it.  The pivots are
+ * those of partial pivoting (the same columns in the same state); results agree with
+ * 0 to rounding.  0 = one far update at a time.  LDL^T factorisations do not use it. */
+#define RMAT_PARAM_FACTOR_LOOKAHEAD 16
+/* CTAs of a look-ahead sub-panel (grid variant; rows in shared memory when they fit):
+ * 0 = default (every SM), 1..RMAT_MAX_PANEL_CTAS. */
+#define RMAT_PARAM_LA_PANEL_CTAS 17
+/* Smallest far block (rows) whose update the look-ahead splits: 0 = default 12288. */
+#define RMAT_PARAM_LA_MIN_ROWS 18
 
 typedef struct rmat_ctx_s* rmat_ctx;
 

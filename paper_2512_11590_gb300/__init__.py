@@ -48,6 +48,9 @@ RMAT_PARAM_TC_BN = 12  # tile width of the factor's tensor-core updates: 256 (0)
 RMAT_PARAM_RESID_SUMS = 13  # compensated kinetic residual sums: -1 complex128 only, 0 off, 1 on
 RMAT_PARAM_SOLVE_BLOCK = 14  # rows per tensor-path solve step: 256 (0) or 128
 RMAT_PARAM_FACTOR = 15       # tensor precisions: 0 LU with partial pivoting, 1 LDL^T
+RMAT_PARAM_FACTOR_LOOKAHEAD = 16  # pivoted paired LU: next pair's panels beside the far update
+RMAT_PARAM_LA_PANEL_CTAS = 17     # CTAs of a look-ahead sub-panel (0 = every SM)
+RMAT_PARAM_LA_MIN_ROWS = 18       # smallest far block that looks ahead (0 = 12288)
 
 RMAT_BATCH_LANES = 1
 RMAT_BATCH_SPLIT_N = 2

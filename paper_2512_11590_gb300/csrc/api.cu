@@ -102,10 +102,11 @@ int ctx_reserve(rmat_ctx c, bool dense) {
     RMAT_CHECK(rmat_grow(c, &c->Mpl, &c->Mpl_cap, (size_t)4 * 128 * 128 * pe));
     RMAT_CHECK(rmat_grow(c, (void**)&c->pfwd, &c->pfwd_cap, 2 * N * sizeof(int)));
     RMAT_CHECK(rmat_grow(c, &c->Bt, &c->Bt_cap, N * nrhs * eb));
-    const size_t nblk = N / 32 + 4;  // per-block scales + the pair slot + two U12 slots
+    const size_t nblk = N / 32 + 5;  // per-block scales + the pair slot + two U12 slots + early U12
     RMAT_CHECK(rmat_grow(c, (void**)&c->umax, &c->umax_cap, nblk * sizeof(unsigned)));
     RMAT_CHECK(rmat_grow(c, (void**)&c->uscale, &c->uscale_cap, nblk * sizeof(float)));
     RMAT_CHECK(rmat_grow(c, (void**)&c->ycs, &c->ycs_cap, (size_t)2 * RMAT_YPL_ROWS * sizeof(float)));
+    RMAT_CHECK(perm_reserve(c, c->perm_sub, (int)N, 32));  // look-ahead sub-panel row moves
     if (!c->side) {  // look-ahead stream of the tensor-path solves
       RMAT_CU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
       for (cudaEvent_t& e : c->la_ev) RMAT_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -309,7 +310,7 @@ int rmat_destroy(rmat_ctx c) {
   void* bufs[] = {c->C,    c->A64,  c->B64, c->ipiv, c->Kmat, c->T0,  c->rmesh,
                   c->fa,   c->l_d,  c->th_d, c->zz_d, c->Wpt, c->X,  c->Rres, c->Bw,
                   c->Fpl,  c->Bpl, c->Ypl,  c->Rint, c->Zbuf, c->zpiv, c->open_d, c->red,
-                  c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows, c->Dinv,
+                  c->ps_mem, c->dstat, c->Dsc, c->perm_main.rows, c->perm_z.rows, c->perm_sub.rows, c->Dinv,
                   c->umax, c->uscale, c->ycs, c->pfwd, c->Bt, c->Kinv, c->Kinv32, c->W32, c->Bs,
                   c->gm_V, c->gm_Z, c->gm_T, c->gm_small, c->faL, c->prop, c->Xs, c->Dinv2,
                   c->Pscr, c->Mpl};
@@ -382,6 +383,18 @@ int rmat_set_param(rmat_ctx c, int key, long long v) {
     case RMAT_PARAM_FACTOR:
       if (v != 0 && v != 1) return -3;
       c->factor_kind = (int)v;
+      return RMAT_OK;
+    case RMAT_PARAM_FACTOR_LOOKAHEAD:
+      if (v != 0 && v != 1) return -3;
+      c->factor_lookahead = (int)v;
+      return RMAT_OK;
+    case RMAT_PARAM_LA_PANEL_CTAS:
+      if (v < 0 || v > RMAT_MAX_PANEL_CTAS) return -3;
+      c->la_panel_ctas = (int)v;
+      return RMAT_OK;
+    case RMAT_PARAM_LA_MIN_ROWS:
+      if (v < 0 || v > (1LL << 30)) return -3;
+      c->la_min_rows = (int)v;
       return RMAT_OK;
     default:
       return -2;
@@ -837,6 +850,7 @@ static int prop_workers(rmat_ctx c, int n) {
     w->panel_ctas_param = 0;
     w->method_param = 0;
     w->solve_lookahead = 0;
+    w->factor_lookahead = 0;
     w->timing = 0;
   }
   return RMAT_OK;

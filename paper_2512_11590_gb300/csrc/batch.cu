@@ -149,6 +149,7 @@ int enqueue_system(rmat_batch b, int s, void* U) {
   c->borrowed_tables = true;
   c->woodbury = false;      // batches factor M itself
   c->solve_lookahead = 0;   // lanes are their own concurrency
+  c->factor_lookahead = 0;
   c->tc_bn = y.lane > 0 ? b->tc_bn_lane : 256;
   c->equil = c->equil_param == -1 ? b->precision != RMAT_C128 : c->equil_param == 1;
   RMAT_CHECK(perm_reserve(c, c->perm_main, y.N, c->nb));  // lay out, no growth (plan sized it)

@@ -40,12 +40,14 @@ constexpr uint32_t STAGING_BYTES = TC_BM * 32 * 4;  // 16 complex columns x 128 
 // of one tile overlaps the MMAs of the next).
 // BN = 128 keeps three pipeline stages (130 KB of shared memory), so a solve-path
 // diagonal application (76 KB) fits beside a running update on the same SM.
-template <int BN>
+// LEAN (BN = 256): three stages (177 KB), so a look-ahead panel CTA of up to ~48 KB
+// fits beside each CTA of a far update that covers every SM.
+template <int BN, bool LEAN = false>
 struct TcCfg {
   static constexpr uint32_t B_PLANE = BN * TC_BK * 4;                 // 8 / 4 KB
   static constexpr uint32_t STAGE = 4 * A_PLANE_BYTES + 4 * B_PLANE;  // 48 / 32 KB
   static constexpr int NBUF = 512 / (2 * BN);                         // accumulator sets
-  static constexpr int STAGES = BN == 128 ? 3 : 4;
+  static constexpr int STAGES = (BN == 128 || LEAN) ? 3 : 4;
   static constexpr size_t SMEM = (size_t)STAGES * STAGE + 2 * STAGING_BYTES + 1024 + 256;
 };
 
@@ -118,11 +120,11 @@ __device__ __forceinline__ void tile_coords(int t, int mt, int nt, int upper, in
 
 // NPROD = 3: the split products hi*hi, hi*lo, lo*hi (12 MMAs per K-step); NPROD = 1:
 // hi*hi only (4 MMAs), and only the hi planes are loaded.
-template <int BN, int KIND, int NPROD>
+template <int BN, int KIND, int NPROD, bool LEAN = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_update_kernel(const __grid_constant__ TcMaps maps, int cx0, int cy0, int M, int Nn, int K,
                  int ax0, int rowA0, int bx0, int rowB0, TcScales sc, int* __restrict__ err) {
-  using Cfg = TcCfg<BN>;
+  using Cfg = TcCfg<BN, LEAN>;
   static_assert(NPROD == 1 || NPROD == 3, "one or three split products");
   constexpr int KSTEP = KIND == 0 ? 8 : 16;  // K elements per 32-byte operand row
   if (sc.skip && *sc.skip) return;           // before any barrier or TMEM allocation
@@ -410,7 +412,7 @@ struct TcCache {
   TcMaps u12;          // U12 product: A = the (I - L11^-1) planes, B = upd128's
   const void* mpl = nullptr;
 };
-bool g_tc_attr[2][2][2] = {};
+bool g_tc_attr[2][2][2][2] = {};
 
 // The cache lives with its context (contexts may run concurrently on separate streams).
 TcCache& tc_cache(rmat_ctx c) {
@@ -418,21 +420,21 @@ TcCache& tc_cache(rmat_ctx c) {
   return *reinterpret_cast<TcCache*>(c->tc);
 }
 
-template <int BN, int KIND, int NPROD>
+template <int BN, int KIND, int NPROD, bool LEAN = false>
 int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, int K, int ax0,
                 int ay0, int bx0, int by0, const TcScales& sc, bool count_as_update) {
   constexpr int KSTEP = KIND == 0 ? 8 : 16;
   if (M <= 0 || Nn <= 0 || K <= 0) return RMAT_OK;
   if (K % KSTEP || ax0 % KSTEP || bx0 % KSTEP) return RMAT_ESTATE;
-  constexpr size_t TC_SMEM = TcCfg<BN>::SMEM;
-  if (!g_tc_attr[BN == 128][KIND][NPROD == 1]) {
-    RMAT_CU(cudaFuncSetAttribute(tc_update_kernel<BN, KIND, NPROD>,
+  constexpr size_t TC_SMEM = TcCfg<BN, LEAN>::SMEM;
+  if (!g_tc_attr[BN == 128][KIND][NPROD == 1][LEAN]) {
+    RMAT_CU(cudaFuncSetAttribute(tc_update_kernel<BN, KIND, NPROD, LEAN>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     // the whole unified memory as shared memory, so other kernels' CTAs fit beside
-    RMAT_CU(cudaFuncSetAttribute(tc_update_kernel<BN, KIND, NPROD>,
+    RMAT_CU(cudaFuncSetAttribute(tc_update_kernel<BN, KIND, NPROD, LEAN>,
                                  cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared));
-    g_tc_attr[BN == 128][KIND][NPROD == 1] = true;
+    g_tc_attr[BN == 128][KIND][NPROD == 1][LEAN] = true;
   }
   if (sc.upper && (M != Nn || cx0 != cy0)) return RMAT_ESTATE;
   const int ksp = sc.ksplit > 1 ? sc.ksplit : 1;
@@ -443,8 +445,10 @@ int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn,
       ksp;
   // a far-row update on the solves' look-ahead stream leaves SMs to the next step's
   // row update (its split-K units); the next diagonal application runs beside the
-  // far update's CTAs (three-stage 128-wide tiles leave it the shared memory)
-  const int cap = (c->side && c->stream == c->side) ? std::max(1, c->sm_count - c->la_free_sms)
+  // far update's CTAs (three-stage 128-wide tiles leave it the shared memory); the
+  // factorisation's far update leaves the next pair's panels their CTAs (side_free)
+  const int free_sms = c->side_free >= 0 ? c->side_free : c->la_free_sms;
+  const int cap = (c->side && c->stream == c->side) ? std::max(1, c->sm_count - free_sms)
                                                     : c->sm_count;
   const int grid = std::min(tiles, cap);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -453,7 +457,7 @@ int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn,
     e1 = rmat_event(c);
     RMAT_CU(cudaEventRecord(e0, c->stream));
   }
-  tc_update_kernel<BN, KIND, NPROD><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(
+  tc_update_kernel<BN, KIND, NPROD, LEAN><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(
       maps, cx0, cy0, M, Nn, K, ax0, ay0, bx0, by0, sc, c->dstat + ST_TIMEOUT);
   c->launches++;
   RMAT_CU(cudaGetLastError());
@@ -475,6 +479,19 @@ int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, i
               int ay0, int bx0, int by0, const TcScales& sc, bool count_as_update) {
   // K beyond the block reads zeros: F columns past n are outside the tensor map and
   // the Y / B planes are zero-filled up to a multiple of 32
+  if constexpr (BN == 256) {
+    if (c->tc_lean) {  // a far update with look-ahead panels beside it
+      if (rmat_plane_fmt(c->precision) == 1) {
+        if (count_as_update && rmat_update_products(c->precision) == 1)
+          return launch_tc_k<BN, 1, 1, true>(c, maps, cx0, cy0, M, Nn, (int)round_up(K, 16), ax0,
+                                             ay0, bx0, by0, sc, count_as_update);
+        return launch_tc_k<BN, 1, 3, true>(c, maps, cx0, cy0, M, Nn, (int)round_up(K, 16), ax0, ay0,
+                                           bx0, by0, sc, count_as_update);
+      }
+      return launch_tc_k<BN, 0, 3, true>(c, maps, cx0, cy0, M, Nn, (int)round_up(K, 8), ax0, ay0,
+                                         bx0, by0, sc, count_as_update);
+    }
+  }
   if (rmat_plane_fmt(c->precision) == 1) {
     if (count_as_update && rmat_update_products(c->precision) == 1)  // factor updates only
         return launch_tc_k<BN, 1, 1>(c, maps, cx0, cy0, M, Nn, (int)round_up(K, 16), ax0, ay0, bx0,

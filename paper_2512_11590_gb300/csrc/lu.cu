@@ -1678,10 +1678,14 @@ int panel_cluster_fits(rmat_ctx c, int precision, int M, int jb) {
                                 : panel_cluster_size<float>(c, M, jb, &rpc, &ldr);
 }
 
+// la_ctas > 0: a look-ahead panel beside a far update that leaves it about that many
+// SMs: grid variant on at most la_ctas CTAs (a cluster would need its CTAs free in one
+// GPC at once).  No kernel it runs beside waits for it, so its CTAs that are not yet
+// resident start when those kernels' CTAs retire.
 template <class T>
-int launch_panel(rmat_ctx c, cplx<T>* A, int ld, int k0, int n, int jb, int* ipiv) {
+int launch_panel(rmat_ctx c, cplx<T>* A, int ld, int k0, int n, int jb, int* ipiv, int la_ctas = 0) {
   const int M = n - k0;
-  if (c->panel_ctas_param <= 0) {  // rows fit one cluster's shared memory: cluster panel
+  if (c->panel_ctas_param <= 0 && la_ctas <= 0) {  // rows fit one cluster's shared memory
     int rpc = 0, ldr = 0;
     const int cs = panel_cluster_size<T>(c, M, jb, &rpc, &ldr);
     if (cs > 0) {
@@ -1705,7 +1709,11 @@ int launch_panel(rmat_ctx c, cplx<T>* A, int ld, int k0, int n, int jb, int* ipi
       return RMAT_OK;
     }
   }
-  const int P = panel_ctas_for(c, M);
+  int P = panel_ctas_for(c, M);
+  if (la_ctas > 0) {
+    P = std::min({la_ctas, RMAT_MAX_PANEL_CTAS, std::max(1, ceil_div(M, 32))});
+    while (ceil_div(M, P) > MAX_RPC) ++P;
+  }
   const int rpc = ceil_div(M, P);
   int ldr = jb + 1;
   const size_t limit = panel_smem_limit(c);
@@ -1716,6 +1724,10 @@ int launch_panel(rmat_ctx c, cplx<T>* A, int ld, int k0, int n, int jb, int* ipi
   if (!attr_set[sizeof(T) == 8]) {
     RMAT_CU(cudaFuncSetAttribute(panel_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)limit));
+    // the SM's unified memory as shared memory, so a look-ahead panel CTA fits beside a
+    // far update's CTA
+    RMAT_CU(cudaFuncSetAttribute(panel_kernel<T, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     RMAT_CU(cudaFuncSetAttribute(panel_kernel<T, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)panel_smem<T>(MAX_RPC, 0, false)));
@@ -2022,9 +2034,11 @@ int finish_fpl_order(rmat_ctx c, int n, int nb, const LUPerm& pm) {
 // inverse table, then applied to all trailing columns on the tensor cores (the
 // interchanges applied first; launch_u12_tc).
 // Block widths 64 and 128; returns false when it does not apply.
+// have_inv: L11^-1 of this block is in place already (an earlier call for other
+// columns of the same block).
 template <int JB>
 int u12_by_inverse_jb(rmat_ctx c, float2* A, int ld, int n, int k0, const LUPerm* pm, int col0,
-                      int ncols) {
+                      int ncols, bool have_inv) {
   const int nfull = n / JB;
   const size_t per = (size_t)JB * JB;
   RMAT_CHECK(rmat_grow(c, &c->Dinv, &c->Dinv_cap, 2 * per * nfull * sizeof(float2)));
@@ -2036,9 +2050,11 @@ int u12_by_inverse_jb(rmat_ctx c, float2* A, int ld, int n, int k0, const LUPerm
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  tri_inv_lower_kernel<JB><<<1, TINV_THREADS, smem, c->stream>>>(A, ld, k0, Lk);
-  c->launches++;
-  RMAT_CU(cudaGetLastError());
+  if (!have_inv) {
+    tri_inv_lower_kernel<JB><<<1, TINV_THREADS, smem, c->stream>>>(A, ld, k0, Lk);
+    c->launches++;
+    RMAT_CU(cudaGetLastError());
+  }
   if (ncols <= 0) return RMAT_OK;
   // On the tensor cores, in place: U12 = A12 - (I - L11^-1) A12, after the interchanges.
   // The FP16 planes carry one power-of-two scale per block, so only when the rows of a
@@ -2068,10 +2084,10 @@ int u12_by_inverse_jb(rmat_ctx c, float2* A, int ld, int n, int k0, const LUPerm
 }
 
 int u12_by_inverse(rmat_ctx c, float2* A, int ld, int n, int k0, int nb, const LUPerm* pm,
-                   int col0, int ncols, bool* done) {
+                   int col0, int ncols, bool* done, bool have_inv = false) {
   *done = true;
-  if (nb == 128) return u12_by_inverse_jb<128>(c, A, ld, n, k0, pm, col0, ncols);
-  if (nb == 64) return u12_by_inverse_jb<64>(c, A, ld, n, k0, pm, col0, ncols);
+  if (nb == 128) return u12_by_inverse_jb<128>(c, A, ld, n, k0, pm, col0, ncols, have_inv);
+  if (nb == 64) return u12_by_inverse_jb<64>(c, A, ld, n, k0, pm, col0, ncols, have_inv);
   *done = false;
   return RMAT_OK;
 }
@@ -2091,6 +2107,44 @@ int launch_diag_nopiv(rmat_ctx c, cplx<T>* A, int ld, int k0, int jb, int* ipiv)
   c->launches++;
   RMAT_CU(cudaGetLastError());
   kt.end();
+  return RMAT_OK;
+}
+
+// Look-ahead panel (complex64): the block's jb columns factored as sub-panels of 32
+// columns, whose rows (~47 KB per CTA at N = 25600 on every SM) fit in the shared
+// memory a three-stage far update leaves on each SM, so the panel runs beside it on
+// all SMs.  After each sub-panel: its interchanges applied to the block's other
+// columns (left: the L parts of the earlier sub-panels follow every later
+// interchange, as inside one panel; right: before they are updated) and to `extra`
+// columns right of the block, then U12 = L11^-1 A12 of the sub-panel on all those
+// right columns and A22 -= L21 U12 below it (CUDA cores: every kernel here stays
+// small enough to share an SM with the far update).  With extra = the next block's
+// width, that block leaves updated by this one, its U12 rows in place.  Same pivots
+// as one panel (partial pivoting on the updated columns); results agree to rounding.
+int la_panel(rmat_ctx c, float2* A, int ld, int k0, int n, int jb, int extra, int* ipiv,
+             int la_ctas) {
+  constexpr int W = 32;
+  const LUPerm& ps = c->perm_sub;
+  if (k0 % W || !ps.rows) return RMAT_ESTATE;
+  for (int s0 = k0; s0 < k0 + jb; s0 += W) {
+    const int w = std::min(W, k0 + jb - s0);
+    RMAT_CHECK(launch_panel<float>(c, A, ld, s0, n, w, ipiv, la_ctas));
+    const int r0 = s0 + w, rc = k0 + jb + extra - r0;
+    if (s0 == k0 && rc <= 0) continue;
+    perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, W, s0, ps.rows, ps.idx, ps.cnt, ps.src,
+                                              c->dstat);
+    c->launches++;
+    if (s0 > k0) RMAT_CHECK(apply_perm<float>(c, ps, A + k0, ld, s0 - k0, s0, W, w));
+    if (rc <= 0) continue;
+    RMAT_CHECK(apply_perm<float>(c, ps, A + r0, ld, rc, s0, W, w));
+    trsm_block_rhs_kernel<float, true><<<ceil_div(rc, 32), 256, trsm_smem<float>(w), c->stream>>>(
+        A, ld, s0, w, A + r0, ld, rc, nullptr);
+    c->launches++;
+    RMAT_CU(cudaGetLastError());
+    if (n > r0)
+      RMAT_CHECK(gemm_sub<float>(c, n - r0, rc, w, A + (size_t)r0 * ld + s0, ld,
+                                 A + (size_t)s0 * ld + r0, ld, A + (size_t)r0 * ld + r0, ld));
+  }
   return RMAT_OK;
 }
 
@@ -2144,10 +2198,10 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
     RMAT_CU(cudaGetLastError());
   }
   // U12 = L11^-1 (rows k0.., columns col0..col0+ncols), interchanges applied when perm
-  auto trsm = [&](int k0, int jb, int col0, int ncols, bool perm) -> int {
+  auto trsm = [&](int k0, int jb, int col0, int ncols, bool perm, bool have_inv = false) -> int {
     bool fused = false;
     if (jb == nb) RMAT_CHECK(u12_by_inverse(c, A, ld, n, k0, nb, perm ? &pm : nullptr, col0, ncols,
-                                            &fused));
+                                            &fused, have_inv));
     if (!fused)
       RMAT_CHECK(solve_block<float, true>(c, perm ? &pm : nullptr, A, ld, k0, nb, jb, A + col0, ld,
                                           ncols, nullptr, &fused));
@@ -2174,48 +2228,105 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
   };
   unsigned* um = fmt == 1 ? c->umax : nullptr;
   float* us = fmt == 1 ? c->uscale : nullptr;
+  // Look-ahead (pivoted LU): a pair's far update is issued as the next pair's 2 nb
+  // columns (this stream) and the rest (far-far, side stream, three pipeline stages
+  // so that every SM keeps room for a look-ahead panel CTA).  While the far-far update
+  // runs, the next pair's panel a (32-column sub-panels, with U12_a on b's columns
+  // and b's update by a) and panel b run beside it on the same SMs; everything that
+  // touches the far-far columns or the earlier L columns of F (the far-far update's
+  // A operand) waits for it: a's and b's interchanges there, U12_a on the far
+  // columns, and the pair scale slot the far-far update reads.  Only far blocks of
+  // at least la_min rows look ahead: below that the far update is shorter than the
+  // two panels and the serial order is faster.
+  const bool la = !ldlt && c->factor_lookahead && c->side && (nb == 64 || nb == 128);
+  const int la_ctas = c->la_panel_ctas > 0 ? c->la_panel_ctas : c->sm_count;
+  const int la_min = c->la_min_rows > 0 ? c->la_min_rows : 12288;
+  cudaStream_t main_s = c->stream;
+  bool pending = false;  // a far-far update is in flight on the side stream
+  auto join = [&]() -> int {
+    if (pending) {
+      RMAT_CU(cudaStreamWaitEvent(main_s, c->la_ev[2], 0));
+      pending = false;
+    }
+    return RMAT_OK;
+  };
+  auto perm_list = [&](int k0) {
+    perm_prep_kernel<<<1, 32, 0, c->stream>>>(ipiv, n, nb, k0, pm.rows, pm.idx, pm.cnt, pm.src,
+                                              c->dstat);
+    c->launches++;
+  };
   int k0 = 0;
   while (k0 < n) {
     const int jba = std::min(nb, n - k0), blka = k0 / nb;
-    RMAT_CHECK(panel(k0, jba));
-    RMAT_CHECK(prep(k0));
-    const int resta = n - k0 - jba;
-    if (resta <= 0) break;
-    RMAT_CHECK(trsm(k0, jba, k0 + jba, resta, !ldlt));
-    mult(k0, jba);
-    if (resta <= nb) {  // block b is the last one: a single update
-      if (um) absmax(k0, jba, k0 + jba, resta, um + blka, nullptr);
-      split(k0, jba, k0 + jba, resta, true, true, 0, um ? um + blka : nullptr,
-            us ? us + blka : nullptr, nullptr, nullptr);
-      l21(k0, jba);
+    if (pending) {
+      // the previous far block was wider than 2 nb: this is a full pair whose 2 nb
+      // columns are up to date, beside the far-far update: panel a (with U12_a on b's
+      // columns and b's update by a), panel b
+      const int k0b = k0 + jba, jbb = nb, far0 = k0b + jbb, far = n - far0;
+      const int resta = n - k0 - jba;
+      RMAT_CHECK(la_panel(c, A, ld, k0, n, jba, jbb, ipiv, la_ctas));
+      perm_list(k0);
+      l21(k0, jba);  // F's L21_a (its own columns: the far-far update reads earlier ones)
       RMAT_CU(cudaGetLastError());
-      RMAT_CHECK(launch_trailing_tc(c, A, ld, k0, jba, n, ldlt));
-      k0 += jba;
-      continue;
-    }
-    const int k0b = k0 + jba, jbb = nb, blkb = k0b / nb, far0 = k0b + jbb, far = n - far0;
-    if (um) {
-      RMAT_CU(cudaMemsetAsync(um + pslot, 0, sizeof(unsigned), c->stream));
-      absmax(k0, jba, k0b, resta, um + blka, um + pslot);
-    }
-    split(k0, jba, k0b, resta, true, true, 0, um ? um + blka : nullptr, us ? us + blka : nullptr,
-          nullptr, nullptr);
-    l21(k0, jba);
-    RMAT_CU(cudaGetLastError());
-    if (ldlt) {
-      // rows of b <- a over all trailing columns: the diagonal block b and U12_b's rows
-      RMAT_CHECK(launch_factor_tc(c, n, k0b, jbb, k0b, resta, jba, k0, us ? us + blka : nullptr));
-      RMAT_CHECK(panel(k0b, jbb));
-      RMAT_CHECK(prep(k0b));
-    } else {
-      // columns of b <- a (rows k0b.., in the row order before panel b)
-      RMAT_CHECK(launch_factor_tc(c, n, k0b, n - k0b, k0b, jbb, jba, k0, us ? us + blka : nullptr));
-      RMAT_CHECK(panel(k0b, jbb));
-      RMAT_CHECK(prep(k0b));  // b's interchanges also reach F's L21_a
-      RMAT_CHECK(apply_perm<float>(c, pm, A + far0, ld, far, k0b, nb, jbb));  // and the far columns
+      RMAT_CHECK(la_panel(c, A, ld, k0b, n, jbb, 0, ipiv, la_ctas));
+      perm_list(k0b);
+      RMAT_CHECK(join());
+      RMAT_CHECK(permute_fpl_left(c, n, ld, k0, nb, pm));
+      RMAT_CHECK(permute_fpl_left(c, n, ld, k0b, nb, pm));  // b's interchanges reach L21_a too
+      RMAT_CHECK(trsm(k0, jba, far0, far, true));          // U12_a on the far columns
+      if (um) {
+        RMAT_CU(cudaMemsetAsync(um + pslot, 0, sizeof(unsigned), c->stream));
+        absmax(k0, jba, k0b, resta, um + blka, um + pslot);
+      }
+      // F rows of a (the backward solve's U12_a, one scale) and the U12_a^T planes
+      split(k0, jba, k0b, resta, true, true, 0, um ? um + blka : nullptr, us ? us + blka : nullptr,
+            nullptr, nullptr);
+      RMAT_CHECK(apply_perm<float>(c, pm, A + far0, ld, far, k0b, nb, jbb));  // b's, far columns
+      RMAT_CU(cudaGetLastError());
       // rows of b <- a in the far columns
       RMAT_CHECK(launch_factor_tc(c, n, k0b, jbb, far0, far, jba, k0, us ? us + blka : nullptr));
+    } else {
+      RMAT_CHECK(panel(k0, jba));
+      RMAT_CHECK(prep(k0));
+      const int resta = n - k0 - jba;
+      if (resta <= 0) break;
+      RMAT_CHECK(trsm(k0, jba, k0 + jba, resta, !ldlt));
+      mult(k0, jba);
+      if (resta <= nb) {  // block b is the last one: a single update
+        if (um) absmax(k0, jba, k0 + jba, resta, um + blka, nullptr);
+        split(k0, jba, k0 + jba, resta, true, true, 0, um ? um + blka : nullptr,
+              us ? us + blka : nullptr, nullptr, nullptr);
+        l21(k0, jba);
+        RMAT_CU(cudaGetLastError());
+        RMAT_CHECK(launch_trailing_tc(c, A, ld, k0, jba, n, ldlt));
+        k0 += jba;
+        continue;
+      }
+      const int k0b = k0 + jba, jbb = nb, far0 = k0b + jbb, far = n - far0;
+      if (um) {
+        RMAT_CU(cudaMemsetAsync(um + pslot, 0, sizeof(unsigned), c->stream));
+        absmax(k0, jba, k0b, resta, um + blka, um + pslot);
+      }
+      split(k0, jba, k0b, resta, true, true, 0, um ? um + blka : nullptr, us ? us + blka : nullptr,
+            nullptr, nullptr);
+      l21(k0, jba);
+      RMAT_CU(cudaGetLastError());
+      if (ldlt) {
+        // rows of b <- a over all trailing columns: the diagonal block b and U12_b's rows
+        RMAT_CHECK(launch_factor_tc(c, n, k0b, jbb, k0b, resta, jba, k0, us ? us + blka : nullptr));
+        RMAT_CHECK(panel(k0b, jbb));
+        RMAT_CHECK(prep(k0b));
+      } else {
+        // columns of b <- a (rows k0b.., in the row order before panel b)
+        RMAT_CHECK(launch_factor_tc(c, n, k0b, n - k0b, k0b, jbb, jba, k0, us ? us + blka : nullptr));
+        RMAT_CHECK(panel(k0b, jbb));
+        RMAT_CHECK(prep(k0b));  // b's interchanges also reach F's L21_a
+        RMAT_CHECK(apply_perm<float>(c, pm, A + far0, ld, far, k0b, nb, jbb));  // and the far columns
+        // rows of b <- a in the far columns
+        RMAT_CHECK(launch_factor_tc(c, n, k0b, jbb, far0, far, jba, k0, us ? us + blka : nullptr));
+      }
     }
+    const int k0b = k0 + jba, jbb = nb, blkb = k0b / nb, far0 = k0b + jbb, far = n - far0;
     RMAT_CHECK(trsm(k0b, jbb, far0, far, false));  // U12_b
     mult(k0b, jbb);
     if (um) absmax(k0b, jbb, far0, far, um + blkb, um + pslot);
@@ -2226,10 +2337,32 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
     l21(k0b, jbb);
     RMAT_CU(cudaGetLastError());
     // C_far -= [L21_a | L21_b] [U12_a ; U12_b]: F's K-columns k0..k0+jba+jbb are contiguous
-    RMAT_CHECK(launch_factor_tc(c, n, far0, far, far0, far, jba + jbb, k0, us ? us + pslot : nullptr,
-                                ldlt));
+    if (la && far > 2 * nb && far >= la_min) {
+      // the next pair's columns here, then the far-far columns on the side stream
+      // (forked after everything above); launched in this order so the narrow update's
+      // CTAs are dispatched first and the side stream's fill the SMs they leave
+      RMAT_CU(cudaEventRecord(c->la_ev[0], main_s));
+      RMAT_CU(cudaStreamWaitEvent(c->side, c->la_ev[0], 0));
+      RMAT_CHECK(launch_factor_tc(c, n, far0, far, far0, 2 * nb, jba + jbb, k0,
+                                  us ? us + pslot : nullptr, false));
+      c->stream = c->side;
+      c->side_free = 0;
+      c->tc_lean = true;
+      const int st = launch_factor_tc(c, n, far0, far, far0 + 2 * nb, far - 2 * nb, jba + jbb, k0,
+                                      us ? us + pslot : nullptr, false);
+      c->tc_lean = false;
+      c->side_free = -1;
+      c->stream = main_s;
+      RMAT_CHECK(st);
+      RMAT_CU(cudaEventRecord(c->la_ev[2], c->side));
+      pending = true;
+    } else {
+      RMAT_CHECK(launch_factor_tc(c, n, far0, far, far0, far, jba + jbb, k0,
+                                  us ? us + pslot : nullptr, ldlt));
+    }
     k0 = far0;
   }
+  RMAT_CHECK(join());
   c->inv_blocks = 0;
   c->inv_pairs = 0;
   // L11^-1 of every full block is already in place (formed for its U12), except the

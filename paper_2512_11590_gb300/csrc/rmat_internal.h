@@ -148,6 +148,7 @@ struct rmat_ctx_s {
   double2* B64 = nullptr;  size_t B64_cap = 0;      // dense loaded right-hand sides (row-major N x nrhs)
   int* ipiv = nullptr;     size_t ipiv_cap = 0;
   LUPerm perm_main, perm_z;                         // main factor / matching-system factor
+  LUPerm perm_sub;                                  // 32-column sub-panels of a look-ahead panel
   double* Kmat = nullptr;  size_t Kmat_cap = 0;     // hm*T0 - hm*(B/a) f f^T  [nlag*nlag]
   double* T0 = nullptr;    size_t T0_cap = 0;       // T0 [nlag*nlag]
   double* rmesh = nullptr; size_t rmesh_cap = 0;    // r_i
@@ -167,6 +168,11 @@ struct rmat_ctx_s {
   int inv_pairs = 0;       // pairs with a 256-row inverse (0: 128-row solve steps only)
   bool pairs_off = false;  // 128-row steps although pair inverses exist (refinement fallback)
   int la_free_sms = 16;    // SMs a look-ahead far update leaves to the next step's row update
+  int side_free = -1;      // SMs a side-stream tensor update leaves free (-1: la_free_sms)
+  bool tc_lean = false;    // 256-wide tensor updates with three stages (look-ahead far update)
+  int factor_lookahead = 1;  // RMAT_PARAM_FACTOR_LOOKAHEAD: next pair's panels beside the far update
+  int la_panel_ctas = 0;     // RMAT_PARAM_LA_PANEL_CTAS: CTAs of a look-ahead panel (0: all SMs)
+  int la_min_rows = 0;       // RMAT_PARAM_LA_MIN_ROWS: far blocks at least this tall look ahead (0: 12288)
   int solve_blk = 256;     // RMAT_PARAM_SOLVE_BLOCK: rows per tensor-path solve step (256 or 128)
   int inv_blocks = 0, inv_nb = 0;      // right-hand-side block planes [4][RMAT_YPL_ROWS][256]
   void* Bpl = nullptr;     size_t Bpl_cap = 0;      // tensor B operand planes (U12^T split)

@@ -38,6 +38,20 @@ def test_every_declared_symbol_is_exported(g):
     assert set(g.EXPORTED) <= set(names)
 
 
+def test_python_constants_match_header(g):
+    """Every RMAT_* integer the binding defines has the header's value, and every
+    RMAT_PARAM_* of the header has a binding constant."""
+    src = open(os.path.join(ROOT, "include", "rmat.h")).read()
+    defs = dict(re.findall(r"^#define\s+(RMAT_\w+)\s+\(?(-?\d+)\)?", src, flags=re.M))
+    assert len(defs) > 20
+    for name, val in defs.items():
+        if hasattr(g, name):
+            assert getattr(g, name) == int(val), name
+    for name in defs:
+        if name.startswith("RMAT_PARAM_"):
+            assert hasattr(g, name), name
+
+
 @pytest.mark.parametrize("n,a", [(1, 3.0), (4, 15.0), (50, 15.0), (100, 15.0), (60, 18.0), (137, 7.5)])
 def test_library_mesh_bitwise_equals_oracle(g, n, a):
     from oracle import mesh as M

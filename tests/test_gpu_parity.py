@@ -251,6 +251,37 @@ def test_solve_lookahead_vs_oracle(g, prec, nb, shape):
         assert e < TOL[prec], (k, e)
 
 
+@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("la,la_ctas", [(0, 0), (1, 0), (1, 1)])
+@pytest.mark.parametrize("nb,shape", [(64, (16, 100)), (128, (16, 100)), (128, (29, 50))])
+def test_factor_lookahead_vs_oracle(g, prec, la, la_ctas, nb, shape):
+    """RMAT_PARAM_FACTOR_LOOKAHEAD: each pair's far update split into the next pair's
+    2 nb columns and the rest (side stream), the next pair's panels (as 32-column
+    sub-panels with interchanges, U12 and updates between them), U12 on the second
+    panel's columns and its column update beside the far part, the far columns' and
+    earlier L columns' interchanges after it.  One look-ahead CTA puts the sub-panel's
+    rows in global memory (up to 1536 rows of 32 columns at N = 1600); with block
+    width 128, N = 1450 ends in a 42-row block.  Same tolerances, both paths."""
+    import torch
+    torch.cuda.set_device(0)
+    nch, nlag = shape
+    p = cp.config3(16) if shape == (16, 100) else cp.make_problem(900 + nch, nch, nlag, 11.0)
+    ref = truth(p, "c3-16" if shape == (16, 100) else ("steps", nch, nlag))
+    h = g.rmat_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        g.rmat_set_param(h, g.RMAT_PARAM_FACTOR_LOOKAHEAD, la)
+        g.rmat_set_param(h, g.RMAT_PARAM_LA_PANEL_CTAS, la_ctas)
+        g.rmat_set_param(h, g.RMAT_PARAM_LA_MIN_ROWS, 1)  # look ahead at every pair
+        out = run_problem(h, p, prec, max_refine=30, tol=1e-14, nb=nb)
+    finally:
+        g.rmat_destroy(h)
+    assert out["status"] == g.RMAT_OK
+    assert out["info"] == 0
+    for k in ("U", "R", "X"):
+        e = relerr(out[k], ref[k])
+        assert e < TOL[prec], (k, e)
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_refinement_stops_at_fp64_floor(g, ctx, prec):
     """The refinement ends with RMAT_OK at the FP64 floor: once the normwise backward

@@ -4,8 +4,9 @@ Every product mode (RMAT_PARAM_RESIDUAL = 1: point couplings on the FP64 tensor
 instruction; = 2: point couplings as integer digit products on the FP16 tensor cores;
 = 3: the kinetic part that way too) is compared element by element with the oracle's
 double-double structured residual of the same X.  The
-bound is the rounding of an FP64 evaluation: 16 u max(|C||X|) (u = 2^-53; a sum
-of nlag + nch products rounds to ~sqrt(nlag + nch) u of its terms), checked on
+bound is the rounding of an FP64 evaluation, 16 u max(|C||X|) (u = 2^-53; a sum
+of nlag + nch products rounds to ~sqrt(nlag + nch) u of its terms), for modes 1
+and 2, and the digit cut of the kinetic rows for mode 3 (bound_for), checked on
 the truth solution (r cancels to ~1e-12 of Phi: the regime the refinement works
 in) and on a random X, at sizes with ragged tiles (nch and nrhs not multiples of
 the 128 x 64 tiles, K padded to 16).
@@ -47,6 +48,14 @@ CASES = {
 }
 
 
+def bound_for(mode, nlag):
+    """Error bound in u max|C||X|: FP64 rounding (16 u) for the FP64 products and the
+    digit products of the couplings; for the digit product of the kinetic part
+    (mode 3) the cut of each row of K at 2^-54 of its largest (diagonal) entry and of
+    X at 2^-54 of its column maximum, summed over nlag terms: up to ~nlag/2 u."""
+    return 16.0 if mode in (1, 2) else max(16.0, 0.5 * nlag)
+
+
 def gpu_residual(g, ctx, p, X, mode):
     import torch
     g.rmat_set_param(ctx, g.RMAT_PARAM_RESIDUAL, mode)
@@ -81,7 +90,7 @@ def test_residual_matches_double_double(g, ctx, case, which):
         r = gpu_residual(g, ctx, p, X, mode)
         err = np.max(np.abs(r - r_dd)) / (U64 * scale)
         print(f"{case} {which} mode {mode}: max|r - r_dd| = {err:.2f} u max|C||X|")
-        assert err < 16.0, (mode, err)
+        assert err < bound_for(mode, p.nlag), (mode, err)
 
 
 def test_residual_modes_agree_on_the_bench_family(g, ctx):
@@ -106,7 +115,7 @@ def test_residual_modes_agree_on_the_bench_family(g, ctx):
     err = np.max(np.abs(r1 - r2)) / (U64 * np.max(absCX))
     err3 = np.max(np.abs(r1 - r3)) / (U64 * np.max(absCX))
     print(f"nch128: max|r_fp64mma - r_tensor| = {err:.2f}, kinetic too {err3:.2f} u max|C||X|")
-    assert err < 16.0 and err3 < 16.0
+    assert err < 16.0 and err3 < bound_for(3, p.nlag)
 
 
 def test_residual_argument_errors(g, ctx):
