@@ -226,7 +226,7 @@ class Runner:
     """One system on one GPU through the C ABI (device-resident buffers)."""
 
     def __init__(self, p, precision, device, method=0, lookahead=1, residual=0, solve_block=0,
-                 factor=0, factor_lookahead=1, la_panel_ctas=0, la_min_rows=0):
+                 factor=0, factor_lookahead=1, la_panel_ctas=0, la_min_rows=0, solve_groups=0):
         import torch
 
         import cc_problems as cp
@@ -242,6 +242,7 @@ class Runner:
         g.rmat_set_param(self.ctx, g.RMAT_PARAM_FACTOR_LOOKAHEAD, factor_lookahead)
         g.rmat_set_param(self.ctx, g.RMAT_PARAM_LA_PANEL_CTAS, la_panel_ctas)
         g.rmat_set_param(self.ctx, g.RMAT_PARAM_LA_MIN_ROWS, la_min_rows)
+        g.rmat_set_param(self.ctx, g.RMAT_PARAM_SOLVE_GROUPS, solve_groups)
         m = g.rmat_mesh(p.nlag, p.a)
         self.V_host = cp.potential_at(p, m["r"]).ravel()
         self.Vd = torch.from_numpy(self.V_host).cuda()
@@ -780,10 +781,13 @@ def main():
                     help="skip the Woodbury-kinetic comparison leg")
     ap.add_argument("--no-lookahead", action="store_true",
                     help="tensor-path solves without look-ahead (bitwise reproducible)")
-    ap.add_argument("--no-factor-lookahead", action="store_true",
-                    help="pivoted LU without the panel look-ahead (one far update at a time)")
+    ap.add_argument("--factor-lookahead", type=int, default=1, choices=[0, 1, 2],
+                    help="RMAT_PARAM_FACTOR_LOOKAHEAD: 0 one far update at a time, 1 panels "
+                         "beside the far update, 2 the look-ahead order on one stream")
     ap.add_argument("--la-panel-ctas", type=int, default=0,
                     help="CTAs of a look-ahead sub-panel (RMAT_PARAM_LA_PANEL_CTAS; 0 = every SM)")
+    ap.add_argument("--solve-groups", type=int, default=0, choices=[0, 1, 2],
+                    help="concurrent column groups of the tensor-path solves (0 = default, 1)")
     ap.add_argument("--la-min-rows", type=int, default=0,
                     help="smallest far block that looks ahead (RMAT_PARAM_LA_MIN_ROWS; 0 = 12288)")
     ap.add_argument("--profile-step", action="store_true",
@@ -855,8 +859,8 @@ def main():
     resid = {"auto": 0, "fp64mma": 1, "tensor": 2, "tensor-all": 3}[args.residual]
     factor = 1 if args.factor == "ldlt" else 0
     run = Runner(p, prec, local, method, 0 if args.no_lookahead else 1, resid, args.solve_block,
-                 factor, 0 if args.no_factor_lookahead else 1, args.la_panel_ctas,
-                 args.la_min_rows)
+                 factor, args.factor_lookahead, args.la_panel_ctas,
+                 args.la_min_rows, args.solve_groups)
     g.rmat_set_param(run.ctx, g.RMAT_PARAM_REFINE, args.refine)
     with ClockSampler(local) as clk:
         ms, stats, launches = time_steps(run, args.steps, args.warmup, sync_all)
@@ -1076,9 +1080,10 @@ def main():
                    "method": args.method, "residual": args.residual,
                    "solve_block": args.solve_block or 256,
                    "solve_lookahead": not args.no_lookahead,
-                   "factor_lookahead": not args.no_factor_lookahead,
+                   "factor_lookahead": args.factor_lookahead,
                    "la_panel_ctas": args.la_panel_ctas or "all SMs",
                    "la_min_rows": args.la_min_rows or 12288,
+                   "solve_groups": args.solve_groups or 1,
                    "refinement": ir, "l2": "inputs larger than L2 (C is %.1f GB)" % (p.N * p.N * 8 / 1e9),
                    "lu_block": stats["nb"], "panel_ctas": stats["panel_ctas"],
                    "ms_per_step_best_median": [stats["ms_steps"]["best"],

@@ -179,13 +179,24 @@ extern "C" {
  * and to the second panel's columns before the next sub-panel), and the interchanges
  * that reach the far columns and the earlier L columns wait for it.  The pivots are
  * those of partial pivoting (the same columns in the same state); results agree with
- * 0 to rounding.  0 = one far update at a time.  LDL^T factorisations do not use it. */
+ * 0 to rounding.  0 = one far update at a time; 2 = the look-ahead's order of work on
+ * one stream (no concurrency: shows what the overlap hides).  LDL^T factorisations do
+ * not use it. */
 #define RMAT_PARAM_FACTOR_LOOKAHEAD 16
 /* CTAs of a look-ahead sub-panel (grid variant; rows in shared memory when they fit):
  * 0 = default (every SM), 1..RMAT_MAX_PANEL_CTAS. */
 #define RMAT_PARAM_LA_PANEL_CTAS 17
 /* Smallest far block (rows) whose update the look-ahead splits: 0 = default 12288. */
 #define RMAT_PARAM_LA_MIN_ROWS 18
+/* Tensor-path solves with look-ahead (RMAT_PARAM_SOLVE_LOOKAHEAD = 1): the right-hand
+ * sides in column groups whose forward and backward sweeps run concurrently, each on
+ * its own pair of streams (the sweeps are chains of dependent steps that leave most
+ * of the GPU idle; the columns are independent; two groups need nrhs a multiple of
+ * 128 and at least 256).  0 = default (1), 1 = one group, 2 = two groups (measured at
+ * N = 25600, 256 right-hand sides: 11.2 ms per solve against 10.4 ms for one group,
+ * the groups' diagonal applications and far updates competing for the same SMs).
+ * Results agree to rounding. */
+#define RMAT_PARAM_SOLVE_GROUPS 19
 
 typedef struct rmat_ctx_s* rmat_ctx;
 

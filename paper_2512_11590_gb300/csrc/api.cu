@@ -111,6 +111,11 @@ int ctx_reserve(rmat_ctx c, bool dense) {
       RMAT_CU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
       for (cudaEvent_t& e : c->la_ev) RMAT_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
+    if (!c->grp_main) {  // the second right-hand-side column group's streams
+      RMAT_CU(cudaStreamCreateWithFlags(&c->grp_main, cudaStreamNonBlocking));
+      RMAT_CU(cudaStreamCreateWithFlags(&c->grp_side, cudaStreamNonBlocking));
+      for (cudaEvent_t& e : c->grp_ev) RMAT_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
   }
   if (dense) {
     RMAT_CHECK(rmat_grow(c, (void**)&c->A64, &c->A64_cap, N * N * 16));
@@ -300,9 +305,15 @@ int rmat_destroy(rmat_ctx c) {
   for (cudaStream_t s : c->prop_streams)
     if (s) cudaStreamDestroy(s);
   if (c->side) cudaStreamSynchronize(c->side);
+  if (c->grp_main) cudaStreamSynchronize(c->grp_main);
+  if (c->grp_side) cudaStreamSynchronize(c->grp_side);
   for (cudaEvent_t e : c->la_ev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->grp_ev)
+    if (e) cudaEventDestroy(e);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->grp_main) cudaStreamDestroy(c->grp_main);
+  if (c->grp_side) cudaStreamDestroy(c->grp_side);
   if (c->borrowed_tables) c->Kmat = c->T0 = c->rmesh = c->fa = nullptr, c->l_d = nullptr,
                           c->th_d = nullptr, c->zz_d = nullptr, c->open_d = nullptr;
   tc_release(c);
@@ -385,12 +396,16 @@ int rmat_set_param(rmat_ctx c, int key, long long v) {
       c->factor_kind = (int)v;
       return RMAT_OK;
     case RMAT_PARAM_FACTOR_LOOKAHEAD:
-      if (v != 0 && v != 1) return -3;
+      if (v < 0 || v > 2) return -3;
       c->factor_lookahead = (int)v;
       return RMAT_OK;
     case RMAT_PARAM_LA_PANEL_CTAS:
       if (v < 0 || v > RMAT_MAX_PANEL_CTAS) return -3;
       c->la_panel_ctas = (int)v;
+      return RMAT_OK;
+    case RMAT_PARAM_SOLVE_GROUPS:
+      if (v < 0 || v > 2) return -3;
+      c->solve_groups = (int)v;
       return RMAT_OK;
     case RMAT_PARAM_LA_MIN_ROWS:
       if (v < 0 || v > (1LL << 30)) return -3;

@@ -448,8 +448,9 @@ int launch_tc_k(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn,
   // far update's CTAs (three-stage 128-wide tiles leave it the shared memory); the
   // factorisation's far update leaves the next pair's panels their CTAs (side_free)
   const int free_sms = c->side_free >= 0 ? c->side_free : c->la_free_sms;
-  const int cap = (c->side && c->stream == c->side) ? std::max(1, c->sm_count - free_sms)
-                                                    : c->sm_count;
+  const bool on_side = (c->side && c->stream == c->side) || (c->grp_side && c->stream == c->grp_side);
+  const int cap = on_side ? std::max(1, (c->sm_count - free_sms) / std::max(1, c->tc_cap_div))
+                          : c->sm_count;
   const int grid = std::min(tiles, cap);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing && count_as_update) {
@@ -607,18 +608,21 @@ int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, in
 
 // Solve update: Bsub[M x nrhs] -= F[rows ay0.., cols k0..k0+jb] * Y, Y^T planes in Ypl.
 // rowscale (FP16 planes): inverse scale per rs_div rows of F (the U blocks).
-int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n,
+// ncols: the current column group's right-hand sides (columns ycol0.. of Bw, rows
+// ycol0.. of the Y planes); the tensor maps span all ysolve_nrhs of the solve.
+int launch_solve_tc(rmat_ctx c, int row0, int M, int ncols, int k0, int jb, int ay0, int n,
                     const float* rowscale, int rs_div, int ksplit) {
-  RMAT_CHECK(tc_prepare(c, n, nrhs));
+  RMAT_CHECK(tc_prepare(c, n, c->ysolve_nrhs > 0 ? c->ysolve_nrhs : ncols));
   TcCache& g_tc = tc_cache(c);
   TcScales sc{nullptr, 1, nullptr, nullptr, c->skip, 0, ksplit};
   if (rmat_plane_fmt(c->precision) == 1) {
     sc.rowscale = rowscale;
     sc.rs_div = rs_div;
-    sc.colscale = rmat_ycs_cur(c);
+    sc.colscale = rmat_ycs_cur(c) - c->ycol0;  // indexed by the plane row ycol0 + column
   }
   KTimer kt(c, KT_SOLVE_TC);
-  RMAT_CHECK(launch_tc<128>(c, g_tc.sol[c->ybuf], 0, row0, M, nrhs, jb, k0, ay0, 0, 0, sc, false));
+  RMAT_CHECK(launch_tc<128>(c, g_tc.sol[c->ybuf], c->ycol0, row0, M, ncols, jb, k0, ay0, 0,
+                            c->ycol0, sc, false));
   kt.end();
   return RMAT_OK;
 }

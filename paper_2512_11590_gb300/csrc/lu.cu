@@ -2242,7 +2242,9 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
   const int la_ctas = c->la_panel_ctas > 0 ? c->la_panel_ctas : c->sm_count;
   const int la_min = c->la_min_rows > 0 ? c->la_min_rows : 12288;
   cudaStream_t main_s = c->stream;
-  bool pending = false;  // a far-far update is in flight on the side stream
+  bool pending = false;   // a far-far update is in flight on the side stream
+  bool la_pair = false;   // this pair follows a split far update (look-ahead order)
+  const bool la_serial = c->factor_lookahead == 2;  // same order, one stream (timing)
   auto join = [&]() -> int {
     if (pending) {
       RMAT_CU(cudaStreamWaitEvent(main_s, c->la_ev[2], 0));
@@ -2258,7 +2260,7 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
   int k0 = 0;
   while (k0 < n) {
     const int jba = std::min(nb, n - k0), blka = k0 / nb;
-    if (pending) {
+    if (la_pair) {
       // the previous far block was wider than 2 nb: this is a full pair whose 2 nb
       // columns are up to date, beside the far-far update: panel a (with U12_a on b's
       // columns and b's update by a), panel b
@@ -2341,11 +2343,13 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
       // the next pair's columns here, then the far-far columns on the side stream
       // (forked after everything above); launched in this order so the narrow update's
       // CTAs are dispatched first and the side stream's fill the SMs they leave
-      RMAT_CU(cudaEventRecord(c->la_ev[0], main_s));
-      RMAT_CU(cudaStreamWaitEvent(c->side, c->la_ev[0], 0));
+      if (!la_serial) {
+        RMAT_CU(cudaEventRecord(c->la_ev[0], main_s));
+        RMAT_CU(cudaStreamWaitEvent(c->side, c->la_ev[0], 0));
+      }
       RMAT_CHECK(launch_factor_tc(c, n, far0, far, far0, 2 * nb, jba + jbb, k0,
                                   us ? us + pslot : nullptr, false));
-      c->stream = c->side;
+      if (!la_serial) c->stream = c->side;
       c->side_free = 0;
       c->tc_lean = true;
       const int st = launch_factor_tc(c, n, far0, far, far0 + 2 * nb, far - 2 * nb, jba + jbb, k0,
@@ -2354,9 +2358,13 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
       c->side_free = -1;
       c->stream = main_s;
       RMAT_CHECK(st);
-      RMAT_CU(cudaEventRecord(c->la_ev[2], c->side));
-      pending = true;
+      if (!la_serial) {
+        RMAT_CU(cudaEventRecord(c->la_ev[2], c->side));
+        pending = true;
+      }
+      la_pair = true;
     } else {
+      la_pair = false;
       RMAT_CHECK(launch_factor_tc(c, n, far0, far, far0, far, jba + jbb, k0,
                                   us ? us + pslot : nullptr, ldlt));
     }
@@ -2488,21 +2496,12 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
   const C2* A = reinterpret_cast<const C2*>(Av);
   C2* B = reinterpret_cast<C2*>(Bv);
   RMAT_CHECK(set_trsm_attrs<T>());
-  const int gx = ceil_div(nrhs, 32);
   // tensor-core block updates need the factor's split planes (written by a
   // tensor-path factorisation), an even row stride and at most RMAT_YPL_ROWS columns
   const bool tc = tensor && sizeof(T) == 4 && c->Fpl && nrhs % 2 == 0 && nrhs <= RMAT_YPL_ROWS &&
                   ldb == nrhs && Bv == c->Bw;
   const size_t yplane = (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB;
   const int fmt = rmat_plane_fmt(c->precision);
-  auto split_y = [&](int row0, int jb) -> int {
-    split_y_kernel<<<ceil_div(nrhs, 8), 256, 0, c->stream>>>(
-        reinterpret_cast<const float2*>(B) + (size_t)row0 * ldb, ldb, jb, nrhs, rmat_ypl_cur(c),
-        yplane, fmt, rmat_ycs_cur(c), c->skip);
-    c->launches++;
-    RMAT_CU(cudaGetLastError());
-    return RMAT_OK;
-  };
   // forward.  Tensor path: F's L parts are in the final row order, so the right-hand
   // sides are permuted once (composed permutation) and the blocks need no replay;
   // otherwise each panel's interchanges are replayed block by block.
@@ -2524,16 +2523,8 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
   // the Y planes alternate between two buffers (block parity) for the same reason.
   // The far and next-row updates of different blocks reduce-add into disjoint or
   // commuting rows of B (TMA reduce-add is atomic per element).
-  cudaStream_t main_s = c->stream;
-  bool pending[2] = {false, false};
-  auto la_wait = [&](int b) -> int {
-    if (pending[b]) {
-      RMAT_CU(cudaStreamWaitEvent(main_s, c->la_ev[2 + b], 0));
-      pending[b] = false;
-    }
-    return RMAT_OK;
-  };
   const bool la_fwd = tc && c->solve_lookahead && fpm == nullptr && c->side;
+  const bool la_bwd = tc && c->solve_lookahead && c->side;
   // 256-row steps over pairs of blocks with a composed inverse (rows pre-gathered)
   const bool pairs = tc && fpm == nullptr && nb == 128 && c->inv_nb == nb && c->inv_pairs > 0 &&
                      !c->pairs_off;
@@ -2544,129 +2535,183 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
     const int kst = fmt == 1 ? 16 : 8, steps = (int)round_up(jbk, kst) / kst;
     return steps % 4 == 0 ? 4 : steps % 2 == 0 ? 2 : 1;
   };
-  int step = 0;
-  for (int k0 = 0, jb = 0; k0 < n; k0 += jb, ++step) {
-    const bool pstep = pair_at(k0);
-    jb = pstep ? 256 : std::min(nb, n - k0);
-    const int b = step & 1;
-    if (tc) {
-      RMAT_CHECK(la_wait(b));
-      c->ybuf = b;
-    }
-    const bool need_y = tc && n - k0 - jb > 0;
-    bool fused = false;
-    if (pstep) {
-      RMAT_CHECK(launch_apply_inv<256>(c, false, k0, 256, reinterpret_cast<float2*>(B), ldb, nrhs,
-                                       nullptr, need_y ? rmat_ypl_cur(c) : nullptr));
-      fused = true;
-    } else if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
-      float2* Bf = reinterpret_cast<float2*>(B);
-      void* Yp = need_y ? rmat_ypl_cur(c) : nullptr;
-      if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, false, k0, nb, Bf, ldb, nrhs, fpm, Yp));
-      else RMAT_CHECK(launch_apply_inv<64>(c, false, k0, nb, Bf, ldb, nrhs, fpm, Yp));
-      fused = true;
-    } else {
-      RMAT_CHECK(solve_block<T, true>(c, fpm, A, ld, k0, nb, jb, B, ldb, nrhs,
-                                      need_y ? rmat_ypl_cur(c) : nullptr, &fused));
-    }
-    if (!fused) {
-      if (fpm) RMAT_CHECK(apply_perm<T>(c, pm, B, ldb, nrhs, k0, nb, jb));
-      trsm_block_rhs_kernel<T, true><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B,
-                                                                              ldb, nrhs, c->skip);
-      c->launches++;
-      RMAT_CU(cudaGetLastError());
-      if (need_y) RMAT_CHECK(split_y(k0, jb));
-    }
-    if (need_y) {
-      const int row0 = k0 + jb, M = n - k0 - jb;
-      const int near = std::min(pair_at(row0) ? 256 : nb, M);
-      if (!la_fwd || near >= M) {
-        RMAT_CHECK(launch_solve_tc(c, row0, M, nrhs, k0, jb, row0, n, nullptr, nb));
-      } else {
-        RMAT_CHECK(launch_solve_tc(c, row0, near, nrhs, k0, jb, row0, n, nullptr, nb,
-                                   ksplit_for(jb)));
-        RMAT_CU(cudaEventRecord(c->la_ev[b], main_s));
-        RMAT_CU(cudaStreamWaitEvent(c->side, c->la_ev[b], 0));
-        c->stream = c->side;
-        const int st = launch_solve_tc(c, row0 + near, M - near, nrhs, k0, jb, row0 + near, n,
-                                       nullptr, nb);
-        c->stream = main_s;
-        RMAT_CHECK(st);
-        RMAT_CU(cudaEventRecord(c->la_ev[2 + b], c->side));
-        pending[b] = true;
-      }
-    } else {
-      RMAT_CHECK(gemm_sub<T>(c, n - k0 - jb, nrhs, jb, A + (size_t)(k0 + jb) * ld + k0, ld,
-                             B + (size_t)k0 * ldb, ldb, B + (size_t)(k0 + jb) * ldb, ldb));
-    }
-  }
-  RMAT_CHECK(la_wait(0));
-  RMAT_CHECK(la_wait(1));
-  // backward: U11 solve, then update the rows above (right-looking); look-ahead as
-  // in the forward sweep, the next block being the one above
-  const bool la_bwd = tc && c->solve_lookahead && c->side;
   const int last = ((n - 1) / nb) * nb;
   // a pair step covers block kb and the one above when kb is a pair's second block
   auto pair_end = [&](int kb) { return pairs && (kb / nb) % 2 == 1 && (kb / nb) / 2 < c->inv_pairs; };
-  step = 0;
-  for (int kb = last; kb >= 0; ++step) {
-    const bool pstep = pair_end(kb);
-    const int k0 = pstep ? kb - nb : kb;
-    const int jb = pstep ? 256 : std::min(nb, n - k0);
-    kb = k0 - nb;
-    const int b = step & 1;
-    if (tc) {
-      RMAT_CHECK(la_wait(b));
-      c->ybuf = b;
-    }
-    const bool need_y = tc && k0 > 0;
-    bool fused = false;
-    if (pstep) {
-      RMAT_CHECK(launch_apply_inv<256>(c, true, k0, 256, reinterpret_cast<float2*>(B), ldb, nrhs,
-                                       nullptr, need_y ? rmat_ypl_cur(c) : nullptr));
-      fused = true;
-    } else if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
-      float2* Bf = reinterpret_cast<float2*>(B);
-      void* Yp = need_y ? rmat_ypl_cur(c) : nullptr;
-      if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, true, k0, nb, Bf, ldb, nrhs, nullptr, Yp));
-      else RMAT_CHECK(launch_apply_inv<64>(c, true, k0, nb, Bf, ldb, nrhs, nullptr, Yp));
-      fused = true;
-    } else {
-      RMAT_CHECK(solve_block<T, false>(c, nullptr, A, ld, k0, nb, jb, B, ldb, nrhs,
-                                       need_y ? rmat_ypl_cur(c) : nullptr, &fused));
-    }
-    if (!fused) {
-      trsm_block_rhs_kernel<T, false><<<gx, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, B,
-                                                                               ldb, nrhs, c->skip);
+  // Both sweeps for the right-hand-side columns col0..col0+nc, on streams main_s / side_s
+  // with look-ahead events ev[0..3].  Column groups are independent, so the sweeps of
+  // different groups run concurrently on their own streams.
+  auto sweeps = [&](int col0, int nc, cudaStream_t main_s, cudaStream_t side_s,
+                    cudaEvent_t* ev) -> int {
+    C2* Bc = B + col0;
+    const int gx_g = ceil_div(nc, 32);
+    c->stream = main_s;
+    c->ycol0 = col0;
+    bool pending[2] = {false, false};
+    auto la_wait = [&](int b) -> int {
+      if (pending[b]) {
+        RMAT_CU(cudaStreamWaitEvent(main_s, ev[2 + b], 0));
+        pending[b] = false;
+      }
+      return RMAT_OK;
+    };
+    auto split_yg = [&](int row0, int jb) -> int {
+      split_y_kernel<<<ceil_div(nc, 8), 256, 0, c->stream>>>(
+          reinterpret_cast<const float2*>(Bc) + (size_t)row0 * ldb, ldb, jb, nc, rmat_ypl_cur(c),
+          yplane, fmt, rmat_ycs_cur(c), c->skip);
       c->launches++;
       RMAT_CU(cudaGetLastError());
-      if (need_y) RMAT_CHECK(split_y(k0, jb));
-    }
-    if (need_y) {
-      // A = U rows of earlier row blocks: their per-block scales apply row-wise
-      const float* rs = fmt == 1 ? c->uscale : nullptr;
-      const int near = std::min(pair_end(kb) ? 256 : nb, k0);  // the next (upper) step's rows
-      if (!la_bwd || near >= k0) {
-        RMAT_CHECK(launch_solve_tc(c, 0, k0, nrhs, k0, jb, 0, n, rs, nb));
-      } else {
-        RMAT_CHECK(launch_solve_tc(c, k0 - near, near, nrhs, k0, jb, k0 - near, n, rs, nb,
-                                   ksplit_for(jb)));
-        RMAT_CU(cudaEventRecord(c->la_ev[b], main_s));
-        RMAT_CU(cudaStreamWaitEvent(c->side, c->la_ev[b], 0));
-        c->stream = c->side;
-        const int st = launch_solve_tc(c, 0, k0 - near, nrhs, k0, jb, 0, n, rs, nb);
-        c->stream = main_s;
-        RMAT_CHECK(st);
-        RMAT_CU(cudaEventRecord(c->la_ev[2 + b], c->side));
-        pending[b] = true;
+      return RMAT_OK;
+    };
+    // the far update of a step on the side stream, forked after the next-row update
+    auto far_update = [&](int b, int row0, int M, int k0, int jb, const float* rs) -> int {
+      RMAT_CU(cudaEventRecord(ev[b], main_s));
+      RMAT_CU(cudaStreamWaitEvent(side_s, ev[b], 0));
+      c->stream = side_s;
+      const int st = launch_solve_tc(c, row0, M, nc, k0, jb, row0, n, rs, nb);
+      c->stream = main_s;
+      RMAT_CHECK(st);
+      RMAT_CU(cudaEventRecord(ev[2 + b], side_s));
+      pending[b] = true;
+      return RMAT_OK;
+    };
+    int step = 0;
+    for (int k0 = 0, jb = 0; k0 < n; k0 += jb, ++step) {
+      const bool pstep = pair_at(k0);
+      jb = pstep ? 256 : std::min(nb, n - k0);
+      const int b = step & 1;
+      if (tc) {
+        RMAT_CHECK(la_wait(b));
+        c->ybuf = b;
       }
-    } else {
-      RMAT_CHECK(gemm_sub<T>(c, k0, nrhs, jb, A + k0, ld, B + (size_t)k0 * ldb, ldb, B, ldb));
+      const bool need_y = tc && n - k0 - jb > 0;
+      bool fused = false;
+      if (pstep) {
+        RMAT_CHECK(launch_apply_inv<256>(c, false, k0, 256, reinterpret_cast<float2*>(Bc), ldb, nc,
+                                         nullptr, need_y ? rmat_ypl_cur(c) : nullptr));
+        fused = true;
+      } else if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
+        float2* Bf = reinterpret_cast<float2*>(Bc);
+        void* Yp = need_y ? rmat_ypl_cur(c) : nullptr;
+        if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, false, k0, nb, Bf, ldb, nc, fpm, Yp));
+        else RMAT_CHECK(launch_apply_inv<64>(c, false, k0, nb, Bf, ldb, nc, fpm, Yp));
+        fused = true;
+      } else {
+        RMAT_CHECK(solve_block<T, true>(c, fpm, A, ld, k0, nb, jb, Bc, ldb, nc,
+                                        need_y ? rmat_ypl_cur(c) : nullptr, &fused));
+      }
+      if (!fused) {
+        if (fpm) RMAT_CHECK(apply_perm<T>(c, pm, Bc, ldb, nc, k0, nb, jb));
+        trsm_block_rhs_kernel<T, true><<<gx_g, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, Bc,
+                                                                                  ldb, nc, c->skip);
+        c->launches++;
+        RMAT_CU(cudaGetLastError());
+        if (need_y) RMAT_CHECK(split_yg(k0, jb));
+      }
+      if (need_y) {
+        const int row0 = k0 + jb, M = n - k0 - jb;
+        const int near = std::min(pair_at(row0) ? 256 : nb, M);
+        if (!la_fwd || near >= M) {
+          RMAT_CHECK(launch_solve_tc(c, row0, M, nc, k0, jb, row0, n, nullptr, nb));
+        } else {
+          RMAT_CHECK(launch_solve_tc(c, row0, near, nc, k0, jb, row0, n, nullptr, nb,
+                                     ksplit_for(jb)));
+          RMAT_CHECK(far_update(b, row0 + near, M - near, k0, jb, nullptr));
+        }
+      } else {
+        RMAT_CHECK(gemm_sub<T>(c, n - k0 - jb, nc, jb, A + (size_t)(k0 + jb) * ld + k0, ld,
+                               Bc + (size_t)k0 * ldb, ldb, Bc + (size_t)(k0 + jb) * ldb, ldb));
+      }
+    }
+    RMAT_CHECK(la_wait(0));
+    RMAT_CHECK(la_wait(1));
+    // backward: U11 solve, then update the rows above (right-looking); look-ahead as
+    // in the forward sweep, the next block being the one above
+    step = 0;
+    for (int kb = last; kb >= 0; ++step) {
+      const bool pstep = pair_end(kb);
+      const int k0 = pstep ? kb - nb : kb;
+      const int jb = pstep ? 256 : std::min(nb, n - k0);
+      kb = k0 - nb;
+      const int b = step & 1;
+      if (tc) {
+        RMAT_CHECK(la_wait(b));
+        c->ybuf = b;
+      }
+      const bool need_y = tc && k0 > 0;
+      bool fused = false;
+      if (pstep) {
+        RMAT_CHECK(launch_apply_inv<256>(c, true, k0, 256, reinterpret_cast<float2*>(Bc), ldb, nc,
+                                         nullptr, need_y ? rmat_ypl_cur(c) : nullptr));
+        fused = true;
+      } else if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
+        float2* Bf = reinterpret_cast<float2*>(Bc);
+        void* Yp = need_y ? rmat_ypl_cur(c) : nullptr;
+        if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, true, k0, nb, Bf, ldb, nc, nullptr, Yp));
+        else RMAT_CHECK(launch_apply_inv<64>(c, true, k0, nb, Bf, ldb, nc, nullptr, Yp));
+        fused = true;
+      } else {
+        RMAT_CHECK(solve_block<T, false>(c, nullptr, A, ld, k0, nb, jb, Bc, ldb, nc,
+                                         need_y ? rmat_ypl_cur(c) : nullptr, &fused));
+      }
+      if (!fused) {
+        trsm_block_rhs_kernel<T, false><<<gx_g, 256, trsm_smem<T>(jb), c->stream>>>(A, ld, k0, jb, Bc,
+                                                                                   ldb, nc, c->skip);
+        c->launches++;
+        RMAT_CU(cudaGetLastError());
+        if (need_y) RMAT_CHECK(split_yg(k0, jb));
+      }
+      if (need_y) {
+        // A = U rows of earlier row blocks: their per-block scales apply row-wise
+        const float* rs = fmt == 1 ? c->uscale : nullptr;
+        const int near = std::min(pair_end(kb) ? 256 : nb, k0);  // the next (upper) step's rows
+        if (!la_bwd || near >= k0) {
+          RMAT_CHECK(launch_solve_tc(c, 0, k0, nc, k0, jb, 0, n, rs, nb));
+        } else {
+          RMAT_CHECK(launch_solve_tc(c, k0 - near, near, nc, k0, jb, k0 - near, n, rs, nb,
+                                     ksplit_for(jb)));
+          RMAT_CHECK(far_update(b, 0, k0 - near, k0, jb, rs));
+        }
+      } else {
+        RMAT_CHECK(gemm_sub<T>(c, k0, nc, jb, A + k0, ld, Bc + (size_t)k0 * ldb, ldb, Bc, ldb));
+      }
+    }
+    RMAT_CHECK(la_wait(0));
+    RMAT_CHECK(la_wait(1));
+    return RMAT_OK;
+  };
+  // Column groups (tensor path with look-ahead, on request): two groups of nrhs/2
+  // columns when the halves stay multiples of 64 and the second group's streams exist.
+  // Not the default: at N = 25600 with 256 right-hand sides two concurrent groups took
+  // 11.2 ms per solve against 10.4 ms for one (their diagonal applications and far
+  // updates compete for the same SMs)
+  const int groups_want = c->solve_groups > 0 ? c->solve_groups : 1;
+  const bool grouped = la_fwd && la_bwd && groups_want == 2 && nrhs % 128 == 0 && nrhs >= 256 &&
+                       c->grp_main && c->grp_side;
+  cudaStream_t caller = c->stream;
+  c->ysolve_nrhs = nrhs;
+  int st = RMAT_OK;
+  if (!grouped) {
+    c->tc_cap_div = 1;
+    st = sweeps(0, nrhs, caller, c->side, c->la_ev);
+  } else {
+    const int half = nrhs / 2;
+    c->tc_cap_div = 2;
+    RMAT_CU(cudaEventRecord(c->grp_ev[4], caller));
+    RMAT_CU(cudaStreamWaitEvent(c->grp_main, c->grp_ev[4], 0));
+    st = sweeps(0, half, caller, c->side, c->la_ev);
+    if (st == RMAT_OK) st = sweeps(half, half, c->grp_main, c->grp_side, c->grp_ev);
+    c->stream = caller;
+    // join: the caller's stream continues after both groups
+    if (st == RMAT_OK) {
+      RMAT_CU(cudaEventRecord(c->grp_ev[5], c->grp_main));
+      RMAT_CU(cudaStreamWaitEvent(caller, c->grp_ev[5], 0));
     }
   }
-  RMAT_CHECK(la_wait(0));
-  RMAT_CHECK(la_wait(1));
-  return RMAT_OK;
+  c->stream = caller;
+  c->ycol0 = 0;
+  c->tc_cap_div = 1;
+  return st;
 }
 
 template int lu_factor_dev<float>(rmat_ctx, void*, int, int, int*, int, bool, const LUPerm&);

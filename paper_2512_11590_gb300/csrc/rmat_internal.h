@@ -187,6 +187,15 @@ struct rmat_ctx_s {
   // buffer ybuf = k & 1, so block k+1's diagonal application can run while the
   // far-row update of block k (on the side stream) still reads buffer k & 1.
   int ybuf = 0;
+  // Column groups of the tensor-path solves: group g owns right-hand-side columns
+  // ycol0.. (rows ycol0.. of the Y planes, entries ycol0.. of the column scales) and
+  // runs its sweeps on its own pair of streams, concurrently with the other groups
+  int ycol0 = 0;
+  int ysolve_nrhs = 0;             // right-hand sides of the whole solve (tensor maps)
+  int solve_groups = 0;            // RMAT_PARAM_SOLVE_GROUPS (0: auto)
+  int tc_cap_div = 1;              // side-stream solve updates share the SMs this many ways
+  cudaStream_t grp_main = nullptr, grp_side = nullptr;  // streams of the second group
+  cudaEvent_t grp_ev[6] = {};      // its look-ahead events [0..3], fork [4], join [5]
   int solve_lookahead = 1;         // RMAT_PARAM_SOLVE_LOOKAHEAD
   cudaStream_t side = nullptr;     // look-ahead stream of the solves
   cudaEvent_t la_ev[4] = {};       // fork / join events of the look-ahead
@@ -278,7 +287,7 @@ int launch_u12_tc(rmat_ctx c, int n, int k0, int jb, int col0, int ncols, const 
                   const float* b_scale);
 int launch_factor_tc(rmat_ctx c, int n, int row0, int M, int col0, int ncols, int K, int ax0,
                      const float* cscal, bool upper = false);
-int launch_solve_tc(rmat_ctx c, int row0, int M, int nrhs, int k0, int jb, int ay0, int n,
+int launch_solve_tc(rmat_ctx c, int row0, int M, int ncols, int k0, int jb, int ay0, int n,
                     const float* rowscale, int rs_div, int ksplit = 1);
 int tc_prepare(rmat_ctx c, int n, int nrhs);
 void tc_release(rmat_ctx c);
@@ -371,11 +380,15 @@ static inline size_t rmat_plane_esz(int p) { return rmat_plane_fmt(p) == 1 ? 2 :
 // updates always take three)
 static inline int rmat_update_products(int p) { return p == RMAT_C64_1XF16_IR ? 1 : 3; }
 // current Y-plane buffer and its column scales
+// (rows ycol0.. of the planes: the right-hand-side columns of the current column group)
 static inline void* rmat_ypl_cur(rmat_ctx c) {
   return reinterpret_cast<char*>(c->Ypl) +
-         (size_t)c->ybuf * 4 * RMAT_YPL_ROWS * RMAT_MAX_NB * rmat_plane_esz(c->precision);
+         ((size_t)c->ybuf * 4 * RMAT_YPL_ROWS + (size_t)c->ycol0) * RMAT_MAX_NB *
+             rmat_plane_esz(c->precision);
 }
-static inline float* rmat_ycs_cur(rmat_ctx c) { return c->ycs + (size_t)c->ybuf * RMAT_YPL_ROWS; }
+static inline float* rmat_ycs_cur(rmat_ctx c) {
+  return c->ycs + (size_t)c->ybuf * RMAT_YPL_ROWS + c->ycol0;
+}
 
 static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 static inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }

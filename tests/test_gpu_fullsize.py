@@ -45,13 +45,40 @@ def ctx():
     g.rmat_destroy(h)
 
 
-def check_against_oracle(p, out, res_tol):
+def abs_apply(p, V, X, m):
+    """|C| |X| through the block structure (complex128 moduli, the kinetic diagonal
+    and the channel diagonal taken separately: an upper bound of sum_j |C_ij| |X_j|)."""
+    from oracle.mesh import kinetic_bloch
+    from oracle.system import channel_diagonal
+    nch, nlag = p.nch, p.nlag
+    X3 = np.abs(X).reshape(nch, nlag, -1)
+    T = kinetic_bloch(nlag, p.a, m)
+    K = p.hm * T - p.hm * (p.bloch_B / p.a) * np.outer(m["f_a"], m["f_a"])
+    y = np.einsum("ij,ajb->aib", np.abs(K), X3)
+    y += np.abs(channel_diagonal(p, m))[:, :, None] * X3
+    y += np.einsum("iac,cib->aib", np.abs(np.transpose(V, (2, 1, 0))), X3)
+    return y.reshape(X.shape)
+
+
+U64 = 2.0 ** -53
+
+
+def check_against_oracle(p, out, res_tol, berr_tol=None):
+    """res_tol bounds max|r| / max|Phi|; berr_tol (in units of u = 2^-53) bounds the
+    normwise backward error max|r| / (max|C||X| + max|Phi|), the quantity the
+    refinement stops on at the FP64 floor (for an ill-conditioned system |C||X| is
+    far above |Phi| and the relative residual stops where rounding leaves it)."""
     m = lagrange_mesh(p.nlag, p.a)
     V = cp.potential_at(p, m["r"])
     X = out["X"]
     r = structured_residual(p, V, X, mesh=m)
-    rel = np.max(np.abs(r)) / np.max(np.abs(surface_rhs(p, m)))
-    assert rel < res_tol, rel
+    phi = np.max(np.abs(surface_rhs(p, m)))
+    rel = np.max(np.abs(r)) / phi
+    if res_tol is not None:
+        assert rel < res_tol, rel
+    if berr_tol is not None:
+        berr = np.max(np.abs(r)) / (np.max(abs_apply(p, V, X, m)) + phi)
+        assert berr < berr_tol * U64, (berr / U64, rel)
     R_or = r_matrix(p, X, m["f_a"])
     assert relerr(out["R"], R_or) < 1e-12
     U_or, nopen = collision_matrix(p, out["R"])
@@ -70,7 +97,9 @@ def test_config3_full_size_fp32_ir(ctx, W):
     out = run_problem(ctx, p, g.RMAT_C64_3XF16_IR, max_refine=30, tol=1e-13)
     assert out["status"] in (g.RMAT_OK, g.RMAT_ENOCONV)
     assert out["iters"] >= 2
-    check_against_oracle(p, out, 2e-11)
+    # W = -1 (weak absorption) is ill-conditioned: the relative residual at the floor
+    # varies with rounding (1e-11 .. 3e-10 measured), the backward error does not
+    check_against_oracle(p, out, 2e-11 if W == -10.0 else None, berr_tol=2.0)
 
 
 @pytest.mark.parametrize("nch", [64, 128])

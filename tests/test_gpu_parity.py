@@ -252,6 +252,30 @@ def test_solve_lookahead_vs_oracle(g, prec, nb, shape):
 
 
 @pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("groups", [1, 2])
+@pytest.mark.parametrize("nb", [64, 128])
+def test_solve_column_groups_vs_oracle(g, prec, groups, nb):
+    """RMAT_PARAM_SOLVE_GROUPS = 2: the 256 right-hand sides of nch = 256 channels in two
+    column groups of 128, each with its own sweeps, Y-plane rows, column scales and
+    stream pair, running concurrently (N = 1536: 12 blocks of 128 or 24 of 64, look-ahead
+    on); same tolerances as one group."""
+    import torch
+    torch.cuda.set_device(0)
+    p = cp.make_problem(977, 256, 6, 10.0)
+    ref = truth(p, ("groups", 256, 6))
+    h = g.rmat_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        g.rmat_set_param(h, g.RMAT_PARAM_SOLVE_GROUPS, groups)
+        out = run_problem(h, p, prec, max_refine=30, tol=1e-14, nb=nb)
+    finally:
+        g.rmat_destroy(h)
+    assert out["status"] == g.RMAT_OK
+    for k in ("U", "R", "X"):
+        e = relerr(out[k], ref[k])
+        assert e < TOL[prec], (k, e)
+
+
+@pytest.mark.parametrize("prec", [1, 3])
 @pytest.mark.parametrize("la,la_ctas", [(0, 0), (1, 0), (1, 1)])
 @pytest.mark.parametrize("nb,shape", [(64, (16, 100)), (128, (16, 100)), (128, (29, 50))])
 def test_factor_lookahead_vs_oracle(g, prec, la, la_ctas, nb, shape):
