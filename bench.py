@@ -226,7 +226,8 @@ class Runner:
     """One system on one GPU through the C ABI (device-resident buffers)."""
 
     def __init__(self, p, precision, device, method=0, lookahead=1, residual=0, solve_block=0,
-                 factor=0, factor_lookahead=1, la_panel_ctas=0, la_min_rows=0, solve_groups=0):
+                 factor=0, factor_lookahead=1, la_panel_ctas=0, la_min_rows=0, solve_groups=0,
+                 la_both_rows=0, tc_bn=0):
         import torch
 
         import cc_problems as cp
@@ -243,6 +244,8 @@ class Runner:
         g.rmat_set_param(self.ctx, g.RMAT_PARAM_LA_PANEL_CTAS, la_panel_ctas)
         g.rmat_set_param(self.ctx, g.RMAT_PARAM_LA_MIN_ROWS, la_min_rows)
         g.rmat_set_param(self.ctx, g.RMAT_PARAM_SOLVE_GROUPS, solve_groups)
+        g.rmat_set_param(self.ctx, g.RMAT_PARAM_LA_BOTH_ROWS, la_both_rows)
+        g.rmat_set_param(self.ctx, g.RMAT_PARAM_TC_BN, tc_bn)
         m = g.rmat_mesh(p.nlag, p.a)
         self.V_host = cp.potential_at(p, m["r"]).ravel()
         self.Vd = torch.from_numpy(self.V_host).cuda()
@@ -789,7 +792,12 @@ def main():
     ap.add_argument("--solve-groups", type=int, default=0, choices=[0, 1, 2],
                     help="concurrent column groups of the tensor-path solves (0 = default, 1)")
     ap.add_argument("--la-min-rows", type=int, default=0,
-                    help="smallest far block that looks ahead (RMAT_PARAM_LA_MIN_ROWS; 0 = 12288)")
+                    help="smallest far block that looks ahead (RMAT_PARAM_LA_MIN_ROWS; 0 = 6144)")
+    ap.add_argument("--la-both-rows", type=int, default=0,
+                    help="smallest far block with both next panels beside its update "
+                         "(RMAT_PARAM_LA_BOTH_ROWS; 0 = 20480)")
+    ap.add_argument("--tc-bn", type=int, default=0, choices=[0, 128, 256],
+                    help="tile width of the factor's tensor-core updates (RMAT_PARAM_TC_BN)")
     ap.add_argument("--profile-step", action="store_true",
                     help="for ncu: one untimed SIMT warm-up step at N=1600, then one FP32+IR "
                          "tensor step at N = nch*100; no timing, no JSON")
@@ -860,7 +868,7 @@ def main():
     factor = 1 if args.factor == "ldlt" else 0
     run = Runner(p, prec, local, method, 0 if args.no_lookahead else 1, resid, args.solve_block,
                  factor, args.factor_lookahead, args.la_panel_ctas,
-                 args.la_min_rows, args.solve_groups)
+                 args.la_min_rows, args.solve_groups, args.la_both_rows, args.tc_bn)
     g.rmat_set_param(run.ctx, g.RMAT_PARAM_REFINE, args.refine)
     with ClockSampler(local) as clk:
         ms, stats, launches = time_steps(run, args.steps, args.warmup, sync_all)
@@ -900,6 +908,38 @@ def main():
                 "x_rel_diff_fp32ir_vs_fp64": rd(X32, X64),
                 "speedup_fp32ir_over_fp64": ms64 / ms}
         r64.close()
+
+    serial = None
+    if factor == 0 and method == 0 and args.factor_lookahead != 0:
+        # the same step without the factorisation's look-ahead: the trailing update
+        # then runs alone on every SM (its kernel-only roofline) and the panels in order
+        rs = Runner(p, prec, local, method, 0 if args.no_lookahead else 1, resid,
+                    args.solve_block, factor, 0, 0, 0, args.solve_groups, 0, args.tc_bn)
+        rs.step()
+        g.rmat_set_param(rs.ctx, g.RMAT_PARAM_TIMING, 1)
+        g.rmat_reset_counters(rs.ctx)
+        rs.step()
+        torch.cuda.synchronize()
+        st_s = g.rmat_get_stats(rs.ctx)
+        g.rmat_set_param(rs.ctx, g.RMAT_PARAM_TIMING, 0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ks = max(1, min(args.steps, 3))
+        e0.record(rs.stream)
+        for _ in range(ks):
+            rs.step()
+        e1.record(rs.stream)
+        torch.cuda.synchronize()
+        mss = max_over_ranks(e0.elapsed_time(e1) / ks, dist, "cuda")
+        serial = {"factor_lookahead": 0, "ms_per_step": mss, "steps": ks,
+                  "value": replica_throughput(world, flops, mss), "refine": dict(rs.last),
+                  "stage_ms": {k: st_s[k] for k in ("factor_ms", "solve_ms", "refine_ms")},
+                  "panel_ms": [st_s.get("panel_ms"), st_s.get("panel_launches")],
+                  "trailing_update": {"kernel_ms_per_step": st_s["tu_ms"],
+                                      "launches": st_s["tu_launches"],
+                                      "achieved_tflops": st_s["tu_flops"] / (st_s["tu_ms"] * 1e-3) / 1e12
+                                      if st_s["tu_ms"] > 0 else None}}
+        rs.close()
 
     other = None
     if not args.no_woodbury:
@@ -1030,6 +1070,7 @@ def main():
         peak = 152 * 128 * 2 * 2070e6 / 1e12
         bound, unit, pname = "alu", "TFLOP/s", "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"
     achieved = tu_flops / (tu_ms * 1e-3) / 1e12 if tu_ms and tu_ms > 0 else None
+    compute_peak = peak
     traffic, tsrc = None, None
     nbk = int(stats["nb"])
     rests = [p.N - (k + 1) * nbk for k in range(p.N // nbk) if p.N - (k + 1) * nbk > 0]
@@ -1066,6 +1107,12 @@ def main():
             tsrc = ("scaled: ncu dram__bytes_read+write per algorithmic byte (%.3f) of the first "
                     "update at N=6400 (profiles/trailing_update_tc_n6400.md) x this run's "
                     "average algorithmic bytes per launch" % ratio)
+    if serial is not None and serial["trailing_update"]["achieved_tflops"]:
+        serial["trailing_update"]["peak"] = compute_peak
+        serial["trailing_update"]["frac"] = (serial["trailing_update"]["achieved_tflops"]
+                                             / compute_peak)
+        serial["trailing_update"]["note"] = ("the trailing update alone on every SM; in the main "
+                                             "line the far part shares the SMs with the next panels")
     W = getattr(p, "W", -10.0)
     errs = None if p.N != 25600 else truth_errors(W, {"fp32ir": (X32, R32, U32), "fp64": fp64_arrays,
                                                       "tf32": tf32_arrays, "ldlt": ldlt_arrays})
@@ -1082,7 +1129,9 @@ def main():
                    "solve_lookahead": not args.no_lookahead,
                    "factor_lookahead": args.factor_lookahead,
                    "la_panel_ctas": args.la_panel_ctas or "all SMs",
-                   "la_min_rows": args.la_min_rows or 12288,
+                   "la_min_rows": args.la_min_rows or 6144,
+                   "la_both_rows": args.la_both_rows or 20480,
+                   "tc_bn": args.tc_bn or 256,
                    "solve_groups": args.solve_groups or 1,
                    "refinement": ir, "l2": "inputs larger than L2 (C is %.1f GB)" % (p.N * p.N * 8 / 1e9),
                    "lu_block": stats["nb"], "panel_ctas": stats["panel_ctas"],
@@ -1093,6 +1142,7 @@ def main():
                    "kernel_ms": {k: [stats.get(k + "_ms"), stats.get(k + "_launches")]
                                  for k in ("panel", "apply_inv", "solve_tc", "resid")}},
         "fp64_path": fp64,
+        "no_factor_lookahead": serial,
         "tf32_path": tf32,
         "ldlt_path": ldlt,
         "error_vs_truth": errs,
@@ -1109,7 +1159,9 @@ def main():
             "paper_speedups": "about 15x over its CPU direct solver and about 41x over the "
                               "legacy code at N=25600 (Type 4 vs Type 1 / Ref.)",
             "note": "other hardware and workloads: context only, not a ratio target"},
-        "roofline": {"kernel": "trailing update C22 -= L21 U12", "bound": bound,
+        "roofline": {"kernel": "trailing update C22 -= L21 U12 (with the factorisation's "
+                               "look-ahead its far part runs beside the next panels)",
+                     "bound": bound,
                      "achieved": achieved, "peak": peak, "peak_source": pname, "unit": unit,
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "traffic_source": tsrc,

@@ -173,8 +173,9 @@ extern "C" {
  * 1 (default) = look-ahead: while the far block is at least RMAT_PARAM_LA_MIN_ROWS
  * tall, each pair's far update is issued in two parts, the next pair's 2*nb columns
  * first on the context's stream and the rest on a second stream with three pipeline
- * stages (room on every SM for a panel CTA beside it); the next pair's two panels
- * then run beside it on the same SMs as 32-column sub-panels (the interchanges, U12
+ * stages (room on every SM for a panel CTA beside it); the next pair's first panel
+ * (and, while the far block is at least RMAT_PARAM_LA_BOTH_ROWS tall, its second)
+ * then runs beside it on the same SMs as 32-column sub-panels (the interchanges, U12
  * and the CUDA-core update of each sub-panel applied to the block's other columns
  * and to the second panel's columns before the next sub-panel), and the interchanges
  * that reach the far columns and the earlier L columns wait for it.  The pivots are
@@ -186,7 +187,7 @@ extern "C" {
 /* CTAs of a look-ahead sub-panel (grid variant; rows in shared memory when they fit):
  * 0 = default (every SM), 1..RMAT_MAX_PANEL_CTAS. */
 #define RMAT_PARAM_LA_PANEL_CTAS 17
-/* Smallest far block (rows) whose update the look-ahead splits: 0 = default 12288. */
+/* Smallest far block (rows) whose update the look-ahead splits: 0 = default 6144. */
 #define RMAT_PARAM_LA_MIN_ROWS 18
 /* Tensor-path solves with look-ahead (RMAT_PARAM_SOLVE_LOOKAHEAD = 1): the right-hand
  * sides in column groups whose forward and backward sweeps run concurrently, each on
@@ -197,6 +198,10 @@ extern "C" {
  * the groups' diagonal applications and far updates competing for the same SMs).
  * Results agree to rounding. */
 #define RMAT_PARAM_SOLVE_GROUPS 19
+/* Smallest far block (rows) beside whose far-far update both panels of the next pair
+ * run (smaller ones down to RMAT_PARAM_LA_MIN_ROWS: the first panel only): 0 = default
+ * 20480. */
+#define RMAT_PARAM_LA_BOTH_ROWS 20
 
 typedef struct rmat_ctx_s* rmat_ctx;
 

@@ -50,8 +50,9 @@ RMAT_PARAM_SOLVE_BLOCK = 14  # rows per tensor-path solve step: 256 (0) or 128
 RMAT_PARAM_FACTOR = 15       # tensor precisions: 0 LU with partial pivoting, 1 LDL^T
 RMAT_PARAM_FACTOR_LOOKAHEAD = 16  # pivoted paired LU: next pair's panels beside the far update
 RMAT_PARAM_LA_PANEL_CTAS = 17     # CTAs of a look-ahead sub-panel (0 = every SM)
-RMAT_PARAM_LA_MIN_ROWS = 18       # smallest far block that looks ahead (0 = 12288)
+RMAT_PARAM_LA_MIN_ROWS = 18       # smallest far block that looks ahead (0 = 6144)
 RMAT_PARAM_SOLVE_GROUPS = 19      # concurrent column groups of the tensor-path solves (0 = 1)
+RMAT_PARAM_LA_BOTH_ROWS = 20      # smallest far block with both next panels beside it (0 = 20480)
 
 RMAT_BATCH_LANES = 1
 RMAT_BATCH_SPLIT_N = 2

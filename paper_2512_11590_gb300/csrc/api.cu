@@ -403,6 +403,10 @@ int rmat_set_param(rmat_ctx c, int key, long long v) {
       if (v < 0 || v > RMAT_MAX_PANEL_CTAS) return -3;
       c->la_panel_ctas = (int)v;
       return RMAT_OK;
+    case RMAT_PARAM_LA_BOTH_ROWS:
+      if (v < 0 || v > (1LL << 30)) return -3;
+      c->la_both_rows = (int)v;
+      return RMAT_OK;
     case RMAT_PARAM_SOLVE_GROUPS:
       if (v < 0 || v > 2) return -3;
       c->solve_groups = (int)v;

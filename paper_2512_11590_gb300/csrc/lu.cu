@@ -2235,15 +2235,18 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
   // and b's update by a) and panel b run beside it on the same SMs; everything that
   // touches the far-far columns or the earlier L columns of F (the far-far update's
   // A operand) waits for it: a's and b's interchanges there, U12_a on the far
-  // columns, and the pair scale slot the far-far update reads.  Only far blocks of
-  // at least la_min rows look ahead: below that the far update is shorter than the
-  // two panels and the serial order is faster.
+  // columns, and the pair scale slot the far-far update reads.  Far blocks of at
+  // least la_both_min rows take both panels beside their far-far update, those of
+  // at least la_min rows only the first (a shorter far update would leave the second
+  // exposed after the first), smaller ones none (the serial order is then faster).
   const bool la = !ldlt && c->factor_lookahead && c->side && (nb == 64 || nb == 128);
   const int la_ctas = c->la_panel_ctas > 0 ? c->la_panel_ctas : c->sm_count;
-  const int la_min = c->la_min_rows > 0 ? c->la_min_rows : 12288;
+  const int la_min = c->la_min_rows > 0 ? c->la_min_rows : 6144;
+  const int la_both_min = c->la_both_rows > 0 ? c->la_both_rows : 20480;
   cudaStream_t main_s = c->stream;
   bool pending = false;   // a far-far update is in flight on the side stream
   bool la_pair = false;   // this pair follows a split far update (look-ahead order)
+  bool la_both = false;   // ... and both its panels run beside it (else only the first)
   const bool la_serial = c->factor_lookahead == 2;  // same order, one stream (timing)
   auto join = [&]() -> int {
     if (pending) {
@@ -2260,7 +2263,7 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
   int k0 = 0;
   while (k0 < n) {
     const int jba = std::min(nb, n - k0), blka = k0 / nb;
-    if (la_pair) {
+    if (la_pair && la_both) {
       // the previous far block was wider than 2 nb: this is a full pair whose 2 nb
       // columns are up to date, beside the far-far update: panel a (with U12_a on b's
       // columns and b's update by a), panel b
@@ -2288,8 +2291,17 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
       // rows of b <- a in the far columns
       RMAT_CHECK(launch_factor_tc(c, n, k0b, jbb, far0, far, jba, k0, us ? us + blka : nullptr));
     } else {
-      RMAT_CHECK(panel(k0, jba));
-      RMAT_CHECK(prep(k0));
+      if (la_pair) {
+        // panel a alone beside the far-far update (a shorter far update would leave
+        // the second panel exposed anyway); then the serial order
+        RMAT_CHECK(la_panel(c, A, ld, k0, n, jba, 0, ipiv, la_ctas));
+        perm_list(k0);
+        RMAT_CHECK(join());
+        RMAT_CHECK(permute_fpl_left(c, n, ld, k0, nb, pm));
+      } else {
+        RMAT_CHECK(panel(k0, jba));
+        RMAT_CHECK(prep(k0));
+      }
       const int resta = n - k0 - jba;
       if (resta <= 0) break;
       RMAT_CHECK(trsm(k0, jba, k0 + jba, resta, !ldlt));
@@ -2363,6 +2375,7 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
         pending = true;
       }
       la_pair = true;
+      la_both = far >= la_both_min;
     } else {
       la_pair = false;
       RMAT_CHECK(launch_factor_tc(c, n, far0, far, far0, far, jba + jbb, k0,

@@ -172,7 +172,8 @@ struct rmat_ctx_s {
   bool tc_lean = false;    // 256-wide tensor updates with three stages (look-ahead far update)
   int factor_lookahead = 1;  // RMAT_PARAM_FACTOR_LOOKAHEAD: next pair's panels beside the far update
   int la_panel_ctas = 0;     // RMAT_PARAM_LA_PANEL_CTAS: CTAs of a look-ahead panel (0: all SMs)
-  int la_min_rows = 0;       // RMAT_PARAM_LA_MIN_ROWS: far blocks at least this tall look ahead (0: 12288)
+  int la_min_rows = 0;       // RMAT_PARAM_LA_MIN_ROWS: far blocks at least this tall look ahead (0: 6144)
+  int la_both_rows = 0;      // RMAT_PARAM_LA_BOTH_ROWS: ... with both panels beside the far update (0: 20480)
   int solve_blk = 256;     // RMAT_PARAM_SOLVE_BLOCK: rows per tensor-path solve step (256 or 128)
   int inv_blocks = 0, inv_nb = 0;      // right-hand-side block planes [4][RMAT_YPL_ROWS][256]
   void* Bpl = nullptr;     size_t Bpl_cap = 0;      // tensor B operand planes (U12^T split)

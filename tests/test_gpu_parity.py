@@ -276,16 +276,19 @@ def test_solve_column_groups_vs_oracle(g, prec, groups, nb):
 
 
 @pytest.mark.parametrize("prec", [1, 3])
-@pytest.mark.parametrize("la,la_ctas", [(0, 0), (1, 0), (1, 1)])
+@pytest.mark.parametrize("la,la_ctas,both", [(0, 0, 1), (1, 0, 1), (1, 1, 1), (1, 0, 1 << 30),
+                                             (2, 0, 1)])
 @pytest.mark.parametrize("nb,shape", [(64, (16, 100)), (128, (16, 100)), (128, (29, 50))])
-def test_factor_lookahead_vs_oracle(g, prec, la, la_ctas, nb, shape):
+def test_factor_lookahead_vs_oracle(g, prec, la, la_ctas, both, nb, shape):
     """RMAT_PARAM_FACTOR_LOOKAHEAD: each pair's far update split into the next pair's
     2 nb columns and the rest (side stream), the next pair's panels (as 32-column
     sub-panels with interchanges, U12 and updates between them), U12 on the second
     panel's columns and its column update beside the far part, the far columns' and
     earlier L columns' interchanges after it.  One look-ahead CTA puts the sub-panel's
-    rows in global memory (up to 1536 rows of 32 columns at N = 1600); with block
-    width 128, N = 1450 ends in a 42-row block.  Same tolerances, both paths."""
+    rows in global memory (up to 1536 rows of 32 columns at N = 1600); both = 2^30
+    keeps only the first panel beside the far update; la = 2 issues the same order on
+    one stream; with block width 128, N = 1450 ends in a 42-row block.  Same
+    tolerances, all paths."""
     import torch
     torch.cuda.set_device(0)
     nch, nlag = shape
@@ -296,6 +299,7 @@ def test_factor_lookahead_vs_oracle(g, prec, la, la_ctas, nb, shape):
         g.rmat_set_param(h, g.RMAT_PARAM_FACTOR_LOOKAHEAD, la)
         g.rmat_set_param(h, g.RMAT_PARAM_LA_PANEL_CTAS, la_ctas)
         g.rmat_set_param(h, g.RMAT_PARAM_LA_MIN_ROWS, 1)  # look ahead at every pair
+        g.rmat_set_param(h, g.RMAT_PARAM_LA_BOTH_ROWS, both)
         out = run_problem(h, p, prec, max_refine=30, tol=1e-14, nb=nb)
     finally:
         g.rmat_destroy(h)
