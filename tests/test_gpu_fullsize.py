@@ -63,7 +63,7 @@ def abs_apply(p, V, X, m):
 U64 = 2.0 ** -53
 
 
-def check_against_oracle(p, out, res_tol, berr_tol=None):
+def check_against_oracle(p, out, res_tol, berr_tol=2.0):
     """res_tol bounds max|r| / max|Phi|; berr_tol (in units of u = 2^-53) bounds the
     normwise backward error max|r| / (max|C||X| + max|Phi|), the quantity the
     refinement stops on at the FP64 floor (for an ill-conditioned system |C||X| is
