@@ -782,6 +782,8 @@ def main():
                     help="factor M itself or the Woodbury-kinetic Schur matrix S")
     ap.add_argument("--no-woodbury", action="store_true",
                     help="skip the Woodbury-kinetic comparison leg")
+    ap.add_argument("--solve-lookahead", type=int, default=1, choices=[1, 2],
+                    help="RMAT_PARAM_SOLVE_LOOKAHEAD mode (2: next rows in the diagonal step)")
     ap.add_argument("--no-lookahead", action="store_true",
                     help="tensor-path solves without look-ahead (bitwise reproducible)")
     ap.add_argument("--factor-lookahead", type=int, default=1, choices=[0, 1, 2],
@@ -866,7 +868,7 @@ def main():
     method = 1 if args.method == "woodbury" else 0
     resid = {"auto": 0, "fp64mma": 1, "tensor": 2, "tensor-all": 3}[args.residual]
     factor = 1 if args.factor == "ldlt" else 0
-    run = Runner(p, prec, local, method, 0 if args.no_lookahead else 1, resid, args.solve_block,
+    run = Runner(p, prec, local, method, 0 if args.no_lookahead else args.solve_lookahead, resid, args.solve_block,
                  factor, args.factor_lookahead, args.la_panel_ctas,
                  args.la_min_rows, args.solve_groups, args.la_both_rows, args.tc_bn)
     g.rmat_set_param(run.ctx, g.RMAT_PARAM_REFINE, args.refine)
@@ -913,7 +915,7 @@ def main():
     if factor == 0 and method == 0 and args.factor_lookahead != 0:
         # the same step without the factorisation's look-ahead: the trailing update
         # then runs alone on every SM (its kernel-only roofline) and the panels in order
-        rs = Runner(p, prec, local, method, 0 if args.no_lookahead else 1, resid,
+        rs = Runner(p, prec, local, method, 0 if args.no_lookahead else args.solve_lookahead, resid,
                     args.solve_block, factor, 0, 0, 0, args.solve_groups, 0, args.tc_bn)
         rs.step()
         g.rmat_set_param(rs.ctx, g.RMAT_PARAM_TIMING, 1)
@@ -944,7 +946,7 @@ def main():
     other = None
     if not args.no_woodbury:
         # the other factored matrix (Woodbury-kinetic S vs M) on the same workload
-        rw = Runner(p, prec, local, 1 - method, 0 if args.no_lookahead else 1, resid)
+        rw = Runner(p, prec, local, 1 - method, 0 if args.no_lookahead else args.solve_lookahead, resid)
         for _ in range(2):
             rw.step()
         torch.cuda.synchronize()
@@ -1126,7 +1128,7 @@ def main():
                    "factor": {"lu": "LU with partial pivoting", "ldlt": "LDL^T"}[args.factor],
                    "method": args.method, "residual": args.residual,
                    "solve_block": args.solve_block or 256,
-                   "solve_lookahead": not args.no_lookahead,
+                   "solve_lookahead": 0 if args.no_lookahead else args.solve_lookahead,
                    "factor_lookahead": args.factor_lookahead,
                    "la_panel_ctas": args.la_panel_ctas or "all SMs",
                    "la_min_rows": args.la_min_rows or 6144,

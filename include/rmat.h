@@ -110,11 +110,15 @@ extern "C" {
  * Not used by batches (their refinement is decided on the device). */
 #define RMAT_PARAM_REFINE      8
 /* Tensor-path solves: 1 (default) = look-ahead: each step's update of the next
- * step's rows runs first (its K range split over a few CTAs) and the far rows' update
- * overlaps the next step on a second stream, leaving SMs to the next row update (the
- * concurrent reduce-adds make the rounding order, and so the last bits before the
- * FP64 refinement, vary from run to run); 0 = one update per step (every bit
- * reproducible). */
+ * step's rows runs first as a tensor-core launch of its own (its K range split over a
+ * few CTAs); 2 = look-ahead with that update done inside the step's diagonal-block
+ * application instead (the step's solution rows are in that kernel's shared memory,
+ * the factor's split planes give the next rows' multipliers; CUDA cores, atomic
+ * subtraction), one launch less per step but slower at N = 25600 (13.0 ms per solve
+ * against 10.4 ms: the fused part takes ~25 us per step); in both the far rows'
+ * update overlaps the next step on a second stream (the concurrent additions make the
+ * rounding order, and so the last bits before the FP64 refinement, vary from run to
+ * run); 0 = one update per step (every bit reproducible). */
 #define RMAT_PARAM_SOLVE_LOOKAHEAD 9
 /* rmat_propagate: 1 (default) = when every panel of a sector system fits one
  * thread-block cluster, sectors 2..ns are solved concurrently on worker contexts

@@ -41,7 +41,7 @@ RMAT_PARAM_EQUILIBRATE = 5
 RMAT_PARAM_PAIRED = 6
 RMAT_PARAM_METHOD = 7   # 0 factor M, 1 Woodbury-kinetic (factor S = I + (K^-1 x I) W)
 RMAT_PARAM_REFINE = 8   # 0 classical refinement, m = 1..64 FGMRES-IR with <= m inner steps
-RMAT_PARAM_SOLVE_LOOKAHEAD = 9   # 1 (default) look-ahead in the tensor-path solves, 0 off
+RMAT_PARAM_SOLVE_LOOKAHEAD = 9   # 1 (default) look-ahead; 2 next rows inside the diagonal step; 0 off
 RMAT_PARAM_PROP_CONCURRENT = 10  # 1 (default) propagation sectors on concurrent worker contexts
 RMAT_PARAM_RESIDUAL = 11  # FP64 residual products: 0 auto, 1 FP64 MMA, 2 tensor couplings, 3 + kinetic
 RMAT_PARAM_TC_BN = 12  # tile width of the factor's tensor-core updates: 256 (0) or 128

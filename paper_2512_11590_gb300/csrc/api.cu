@@ -368,7 +368,7 @@ int rmat_set_param(rmat_ctx c, int key, long long v) {
       c->refine_param = (int)v;
       return RMAT_OK;
     case RMAT_PARAM_SOLVE_LOOKAHEAD:
-      if (v < 0 || v > 1) return -3;
+      if (v < 0 || v > 2) return -3;
       c->solve_lookahead = (int)v;
       return RMAT_OK;
     case RMAT_PARAM_PROP_CONCURRENT:
@@ -630,7 +630,8 @@ static int solve_factors(rmat_ctx c) {
       (long long)(uintptr_t)c->Bt, (long long)(uintptr_t)c->pfwd,
       (long long)(uintptr_t)c->perm_main.rows, (long long)(uintptr_t)c->stream,
       (long long)(uintptr_t)c->uscale, (long long)(uintptr_t)c->ycs, c->solve_lookahead,
-      (long long)(uintptr_t)c->side, c->inv_pairs, (long long)(uintptr_t)c->Dinv2, c->pairs_off};
+      (long long)(uintptr_t)c->side, c->inv_pairs, (long long)(uintptr_t)c->Dinv2, c->pairs_off,
+      c->solve_groups, (long long)(uintptr_t)c->grp_main};
   if (!c->sg_exec || key != c->sg_key) {
     if (c->sg_exec) {
       cudaGraphExecDestroy(c->sg_exec);

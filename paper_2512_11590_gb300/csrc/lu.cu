@@ -1225,12 +1225,41 @@ __global__ void identity_blocks_kernel(cplx<T>* __restrict__ D, int JB, size_t t
 // Every read of B happens before the first cluster barrier and every write after
 // the second, and no two clusters touch the same column, so the in-place update
 // has no race.
+// One complex entry of split operand planes (fmt 0: TF32 hi/lo as fp32 words, 1: FP16
+// hi/lo carrying a power-of-two scale, undone by the caller): hi + lo per real part.
+__device__ __forceinline__ float2 get4(const void* base, size_t plane, size_t o, int fmt) {
+  if (fmt == 0) {
+    const float* b = reinterpret_cast<const float*>(base);
+    return make_float2(b[o] + b[plane + o], b[2 * plane + o] + b[3 * plane + o]);
+  }
+  const __half* b = reinterpret_cast<const __half*>(base);
+  return make_float2(__half2float(b[o]) + __half2float(b[plane + o]),
+                     __half2float(b[2 * plane + o]) + __half2float(b[3 * plane + o]));
+}
+
+// The solves' look-ahead update of the next step's rows, fused into the diagonal-block
+// application that produces its right operand: B[row0 + r, cols] -= F[row0 + r,
+// kcol0 .. kcol0 + JB) * Y for r < nrows, Y the block's solution rows (JB x 16 per
+// cluster, gathered from the CTAs' shared memory), F the factor's split planes (the
+// final row order of the tensor path: L rows of the next block in the forward sweep,
+// U rows of the block above in the backward sweep, FP16 planes scaled per rs_div rows
+// by rowscale).  The far rows' update may still be reduce-adding into these rows from
+// the side stream, so the subtraction is atomic.
+struct NearUpd {
+  const void* F = nullptr;  // null: no fused update
+  size_t fplane = 0;
+  int ldf = 0, fmt = 0;
+  int row0 = 0, nrows = 0, kcol0 = 0;
+  const float* rowscale = nullptr;
+  int rs_div = 1;
+};
+
 template <int JB>
 __global__ void __cluster_dims__(1, JB / 16, 1) __launch_bounds__(256)
 apply_inv_kernel(const float2* __restrict__ Dinv, int k0, int nbp, float2* __restrict__ B,
                  int ldb, int ncols, const int* __restrict__ prow, const int* __restrict__ psrc,
                  const int* __restrict__ pcnt, void* __restrict__ Yp, size_t yplane, int fmt,
-                 float* __restrict__ ycs, const int* __restrict__ skip) {
+                 float* __restrict__ ycs, const int* __restrict__ skip, const NearUpd nu) {
   namespace cg = cooperative_groups;
   if (skip && *skip) return;  // uniform over the cluster: no CTA reaches a cluster barrier
   constexpr int CW = 16;          // columns per cluster
@@ -1323,10 +1352,12 @@ apply_inv_kernel(const float2* __restrict__ Dinv, int k0, int nbp, float2* __res
   for (int t = 0; t < JB; ++t) cadd_mul<float>(acc, Ds[ri * LDD + t], vk[t * CW + cl]);
   const int i = 16 * s + ri;
   if (act) B[(size_t)(k0 + i) * ldb + col] = acc;
-  if (Yp) {
-    __shared__ float cmax[CW];
+  if (Yp || nu.F) {
     ys[ri * (CW + 1) + cl] = acc;
     __syncthreads();
+  }
+  if (Yp) {
+    __shared__ float cmax[CW];
     const int cc = tid >> 4, ii = tid & 15;
     float sc = 1.f;
     if (fmt == 1) {
@@ -1347,6 +1378,45 @@ apply_inv_kernel(const float2* __restrict__ Dinv, int k0, int nbp, float2* __res
     const int gc = blockIdx.x * CW + cc;
     if (gc < ncols)
       put4(Yp, yplane, (size_t)gc * RMAT_MAX_NB + 16 * s + ii, ys[ii * (CW + 1) + cc], fmt, sc);
+  }
+  if (nu.F) {
+    cluster.sync();  // every CTA's 16 solution rows are in its ys
+    for (int e = tid; e < JB * CW; e += 256) {
+      const int t = e / CW;
+      const float2* peer = cluster.map_shared_rank(ys, t / 16);
+      vk[e] = peer[(t % 16) * (CW + 1) + (e % CW)];
+    }
+    // rows 16 s + q JB .. of the next step's block (the inverse rows in Ds are done)
+    for (int q0 = 16 * s; q0 < nu.nrows; q0 += JB) {
+      __syncthreads();
+      for (int e = tid; e < 16 * JB; e += 256) {
+        const int r = e / JB, t = e - r * JB;
+        float2 v = make_float2(0.f, 0.f);
+        if (q0 + r < nu.nrows) {
+          const int row = nu.row0 + q0 + r;
+          v = get4(nu.F, nu.fplane, (size_t)row * nu.ldf + nu.kcol0 + t, nu.fmt);
+          if (nu.rowscale) {
+            const float sc = nu.rowscale[row / nu.rs_div];
+            v.x *= sc;
+            v.y *= sc;
+          }
+        }
+        Ds[r * LDD + t] = v;
+      }
+      __syncthreads();
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll 8
+      for (int t = 0; t < JB; t += 2) {
+        cadd_mul<float>(a0, Ds[ri * LDD + t], vk[t * CW + cl]);
+        cadd_mul<float>(a1, Ds[ri * LDD + t + 1], vk[(t + 1) * CW + cl]);
+      }
+      if (act && q0 + ri < nu.nrows) {
+        float2* dst = B + (size_t)(nu.row0 + q0 + ri) * ldb + col;
+        atomicAdd(&dst->x, -(a0.x + a1.x));
+        atomicAdd(&dst->y, -(a0.y + a1.y));
+      }
+    }
+    cluster.sync();  // the peers' reads of this CTA's ys are done before it exits
   }
 }
 
@@ -1963,7 +2033,7 @@ int invert_pair_blocks(rmat_ctx c, const float2* A, int ld, int n) {
 
 template <int JB>
 int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb, int ncols,
-                     const LUPerm* pm, void* Yp) {
+                     const LUPerm* pm, void* Yp, const NearUpd& nu = NearUpd()) {
   static bool attr = false;
   const size_t smem = apply_inv_smem<JB>();
   if (!attr) {
@@ -1985,7 +2055,7 @@ int launch_apply_inv(rmat_ctx c, bool upper, int k0, int nb, float2* B, int ldb,
   apply_inv_kernel<JB><<<dim3(ceil_div(ncols, 16), JB / 16), 256, smem, c->stream>>>(
       D, k0, nb, B, ldb, ncols, pm ? pm->rows : nullptr, pm ? pm->src : nullptr,
       pm ? pm->cnt : nullptr, Yp, (size_t)RMAT_YPL_ROWS * RMAT_MAX_NB, rmat_plane_fmt(c->precision),
-      rmat_ycs_cur(c), c->skip);
+      rmat_ycs_cur(c), c->skip, nu);
   kt.end();
   c->launches++;
   RMAT_CU(cudaGetLastError());
@@ -2538,6 +2608,10 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
   // commuting rows of B (TMA reduce-add is atomic per element).
   const bool la_fwd = tc && c->solve_lookahead && fpm == nullptr && c->side;
   const bool la_bwd = tc && c->solve_lookahead && c->side;
+  // mode 2: each step's update of the next step's rows inside its diagonal application
+  // (the factor's split planes in their final row order), one launch less per step but
+  // ~25 us more per diagonal application at N = 25600, so not the default
+  const bool fuse_near = c->solve_lookahead == 2 && c->fpl_final;
   // 256-row steps over pairs of blocks with a composed inverse (rows pre-gathered)
   const bool pairs = tc && fpm == nullptr && nb == 128 && c->inv_nb == nb && c->inv_pairs > 0 &&
                      !c->pairs_off;
@@ -2599,16 +2673,33 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
       }
       const bool need_y = tc && n - k0 - jb > 0;
       bool fused = false;
+      // the next step's rows updated inside the diagonal application (look-ahead mode 2)
+      NearUpd nu;
+      const int nrow0 = k0 + jb, nM = n - k0 - jb;
+      const int nnear = std::min(pair_at(nrow0) ? 256 : nb, nM);
+      const bool fuse = need_y && la_fwd && fuse_near && nnear > 0;
+      if (fuse) {
+        nu.F = c->Fpl;
+        nu.fplane = (size_t)n * ld;
+        nu.ldf = ld;
+        nu.fmt = fmt;
+        nu.row0 = nrow0;
+        nu.nrows = nnear;
+        nu.kcol0 = k0;
+      }
+      bool near_done = false;
       if (pstep) {
         RMAT_CHECK(launch_apply_inv<256>(c, false, k0, 256, reinterpret_cast<float2*>(Bc), ldb, nc,
-                                         nullptr, need_y ? rmat_ypl_cur(c) : nullptr));
+                                         nullptr, need_y ? rmat_ypl_cur(c) : nullptr, nu));
         fused = true;
+        near_done = fuse;
       } else if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
         float2* Bf = reinterpret_cast<float2*>(Bc);
         void* Yp = need_y ? rmat_ypl_cur(c) : nullptr;
-        if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, false, k0, nb, Bf, ldb, nc, fpm, Yp));
-        else RMAT_CHECK(launch_apply_inv<64>(c, false, k0, nb, Bf, ldb, nc, fpm, Yp));
+        if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, false, k0, nb, Bf, ldb, nc, fpm, Yp, nu));
+        else RMAT_CHECK(launch_apply_inv<64>(c, false, k0, nb, Bf, ldb, nc, fpm, Yp, nu));
         fused = true;
+        near_done = fuse;
       } else {
         RMAT_CHECK(solve_block<T, true>(c, fpm, A, ld, k0, nb, jb, Bc, ldb, nc,
                                         need_y ? rmat_ypl_cur(c) : nullptr, &fused));
@@ -2624,7 +2715,9 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
       if (need_y) {
         const int row0 = k0 + jb, M = n - k0 - jb;
         const int near = std::min(pair_at(row0) ? 256 : nb, M);
-        if (!la_fwd || near >= M) {
+        if (near_done) {
+          if (near < M) RMAT_CHECK(far_update(b, row0 + near, M - near, k0, jb, nullptr));
+        } else if (!la_fwd || near >= M) {
           RMAT_CHECK(launch_solve_tc(c, row0, M, nc, k0, jb, row0, n, nullptr, nb));
         } else {
           RMAT_CHECK(launch_solve_tc(c, row0, near, nc, k0, jb, row0, n, nullptr, nb,
@@ -2653,16 +2746,33 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
       }
       const bool need_y = tc && k0 > 0;
       bool fused = false;
+      NearUpd nu;
+      const int bnear = std::min(pair_end(kb) ? 256 : nb, k0);  // the next (upper) step's rows
+      const bool fuse = need_y && la_bwd && fuse_near && bnear > 0;
+      if (fuse) {
+        nu.F = c->Fpl;
+        nu.fplane = (size_t)n * ld;
+        nu.ldf = ld;
+        nu.fmt = fmt;
+        nu.row0 = k0 - bnear;
+        nu.nrows = bnear;
+        nu.kcol0 = k0;
+        nu.rowscale = fmt == 1 ? c->uscale : nullptr;  // U rows: one scale per row block
+        nu.rs_div = nb;
+      }
+      bool near_done = false;
       if (pstep) {
         RMAT_CHECK(launch_apply_inv<256>(c, true, k0, 256, reinterpret_cast<float2*>(Bc), ldb, nc,
-                                         nullptr, need_y ? rmat_ypl_cur(c) : nullptr));
+                                         nullptr, need_y ? rmat_ypl_cur(c) : nullptr, nu));
         fused = true;
+        near_done = fuse;
       } else if (tc && jb == nb && k0 / nb < c->inv_blocks && c->inv_nb == nb) {
         float2* Bf = reinterpret_cast<float2*>(Bc);
         void* Yp = need_y ? rmat_ypl_cur(c) : nullptr;
-        if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, true, k0, nb, Bf, ldb, nc, nullptr, Yp));
-        else RMAT_CHECK(launch_apply_inv<64>(c, true, k0, nb, Bf, ldb, nc, nullptr, Yp));
+        if (nb == 128) RMAT_CHECK(launch_apply_inv<128>(c, true, k0, nb, Bf, ldb, nc, nullptr, Yp, nu));
+        else RMAT_CHECK(launch_apply_inv<64>(c, true, k0, nb, Bf, ldb, nc, nullptr, Yp, nu));
         fused = true;
+        near_done = fuse;
       } else {
         RMAT_CHECK(solve_block<T, false>(c, nullptr, A, ld, k0, nb, jb, Bc, ldb, nc,
                                          need_y ? rmat_ypl_cur(c) : nullptr, &fused));
@@ -2678,7 +2788,9 @@ int lu_solve_dev(rmat_ctx c, const void* Av, int n, int ld, const LUPerm& pm, in
         // A = U rows of earlier row blocks: their per-block scales apply row-wise
         const float* rs = fmt == 1 ? c->uscale : nullptr;
         const int near = std::min(pair_end(kb) ? 256 : nb, k0);  // the next (upper) step's rows
-        if (!la_bwd || near >= k0) {
+        if (near_done) {
+          if (near < k0) RMAT_CHECK(far_update(b, 0, k0 - near, k0, jb, rs));
+        } else if (!la_bwd || near >= k0) {
           RMAT_CHECK(launch_solve_tc(c, 0, k0, nc, k0, jb, 0, n, rs, nb));
         } else {
           RMAT_CHECK(launch_solve_tc(c, k0 - near, near, nc, k0, jb, k0 - near, n, rs, nb,

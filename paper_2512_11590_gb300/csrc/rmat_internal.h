@@ -197,7 +197,7 @@ struct rmat_ctx_s {
   int tc_cap_div = 1;              // side-stream solve updates share the SMs this many ways
   cudaStream_t grp_main = nullptr, grp_side = nullptr;  // streams of the second group
   cudaEvent_t grp_ev[6] = {};      // its look-ahead events [0..3], fork [4], join [5]
-  int solve_lookahead = 1;         // RMAT_PARAM_SOLVE_LOOKAHEAD
+  int solve_lookahead = 1;         // RMAT_PARAM_SOLVE_LOOKAHEAD (2: next rows in the diagonal step)
   cudaStream_t side = nullptr;     // look-ahead stream of the solves
   cudaEvent_t la_ev[4] = {};       // fork / join events of the look-ahead
   double* Dsc = nullptr;   size_t Dsc_cap = 0;      // equilibration scale per row

@@ -228,12 +228,14 @@ def test_panel_rows_in_global_memory(g, ctx, prec, nb, ctas):
 
 
 @pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("nb,shape", [(64, (16, 100)), (128, (16, 100)), (128, (29, 50))])
-def test_solve_lookahead_vs_oracle(g, prec, nb, shape):
+def test_solve_lookahead_vs_oracle(g, prec, mode, nb, shape):
     """RMAT_PARAM_SOLVE_LOOKAHEAD = 1: next-step updates on the main stream (K split
-    over CTAs), far rows on the side stream, double-buffered Y planes; with block
-    width 128 the steps are pairs of blocks (N = 1450: five pairs, one single block
-    and a 42-row tail); same tolerances."""
+    over CTAs), = 2: inside the diagonal-block application (atomic, CUDA cores); far
+    rows on the side stream, double-buffered Y planes; with block width 128 the steps
+    are pairs of blocks (N = 1450: five pairs, one single block and a 42-row tail);
+    same tolerances."""
     import torch
     torch.cuda.set_device(0)
     nch, nlag = shape
@@ -241,7 +243,7 @@ def test_solve_lookahead_vs_oracle(g, prec, nb, shape):
     ref = truth(p, "c3-16" if shape == (16, 100) else ("steps", nch, nlag))
     h = g.rmat_create(0, torch.cuda.current_stream().cuda_stream)
     try:
-        g.rmat_set_param(h, g.RMAT_PARAM_SOLVE_LOOKAHEAD, 1)
+        g.rmat_set_param(h, g.RMAT_PARAM_SOLVE_LOOKAHEAD, mode)
         out = run_problem(h, p, prec, max_refine=30, tol=1e-14, nb=nb)
     finally:
         g.rmat_destroy(h)
