@@ -264,6 +264,7 @@ int rmat_create(rmat_ctx* out, int device, void* stream) {
   c->stream = reinterpret_cast<cudaStream_t>(stream);
   c->sm_count = prop.multiProcessorCount;
   c->smem_optin = (int)prop.sharedMemPerBlockOptin;
+  c->smem_per_sm = (int)prop.sharedMemPerMultiprocessor;
   const size_t cs = sizeof(double2);
   const size_t ps_bytes = 256 + 2 * RMAT_MAX_PANEL_CTAS * sizeof(double) +
                           2 * RMAT_MAX_PANEL_CTAS * sizeof(int) +

@@ -506,6 +506,8 @@ int launch_tc(rmat_ctx c, const TcMaps& maps, int cx0, int cy0, int M, int Nn, i
 
 }  // namespace
 
+size_t tc_lean_smem() { return TcCfg<256, true>::SMEM; }
+
 int tc_prepare(rmat_ctx c, int n, int nrhs) {
   TcCache& g_tc = tc_cache(c);
   const int ldf = c->ld, fmt = rmat_plane_fmt(c->precision);

@@ -2312,6 +2312,17 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
   const bool la = !ldlt && c->factor_lookahead && c->side && (nb == 64 || nb == 128);
   const int la_ctas = c->la_panel_ctas > 0 ? c->la_panel_ctas : c->sm_count;
   const int la_min = c->la_min_rows > 0 ? c->la_min_rows : 6144;
+  // the next pair's 32-column sub-panel CTAs (rows in shared memory) must fit beside a
+  // far-part CTA on each SM, else they would wait for the far part to end: a far
+  // block of M rows looks ahead only while that holds (up to ~25600 rows on 152 SMs)
+  auto fits_beside = [&](int M) {
+    const int P = std::min({la_ctas, RMAT_MAX_PANEL_CTAS, std::max(1, ceil_div(M, 32))});
+    // the panel's dynamic shared memory plus its 288 static bytes, beside the far part's,
+    // with the 1 KB each CTA reserves
+    const size_t need = panel_smem<float>(ceil_div(M, P), 33, true) + 288;
+    const size_t room = (size_t)c->smem_per_sm - tc_lean_smem() - 2 * 1024;
+    return need <= room;
+  };
   const int la_both_min = c->la_both_rows > 0 ? c->la_both_rows : 20480;
   cudaStream_t main_s = c->stream;
   bool pending = false;   // a far-far update is in flight on the side stream
@@ -2421,7 +2432,7 @@ int factor_pairs_tc(rmat_ctx c, float2* A, int n, int ld, int* ipiv, int nb, con
     l21(k0b, jbb);
     RMAT_CU(cudaGetLastError());
     // C_far -= [L21_a | L21_b] [U12_a ; U12_b]: F's K-columns k0..k0+jba+jbb are contiguous
-    if (la && far > 2 * nb && far >= la_min) {
+    if (la && far > 2 * nb && far >= la_min && fits_beside(far)) {
       // the next pair's columns here, then the far-far columns on the side stream
       // (forked after everything above); launched in this order so the narrow update's
       // CTAs are dispatched first and the side stream's fill the SMs they leave

@@ -92,6 +92,7 @@ struct rmat_ctx_s {
   long long spin_limit = 20000000LL;   // ~ seconds of polling
   int timing = 0;
   int smem_optin = 232448;  // cudaDeviceProp::sharedMemPerBlockOptin
+  int smem_per_sm = 233472; // cudaDeviceProp::sharedMemPerMultiprocessor
   // device flag read by the refinement-loop kernels: nonzero = this system's
   // device-side refinement has stopped, so the launch returns at once (null: run)
   const int* skip = nullptr;
@@ -296,6 +297,9 @@ void tc_release(rmat_ctx c);
 int gemm_sub_c128(rmat_ctx c, int M, int N, int K, const double2* A, int lda, const double2* B,
                   int ldb, double2* C, int ldc);
 int panel_ctas_for(rmat_ctx c, int M);
+// Dynamic shared memory of a three-stage 256-wide tensor update CTA (the look-ahead's
+// far part).
+size_t tc_lean_smem();
 // residual.cu
 int launch_residual(rmat_ctx c, double* relres_dev_unused);
 int launch_x_out(rmat_ctx c, double2* Xo, int ldx);
