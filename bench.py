@@ -972,7 +972,7 @@ def main():
     pk, src = peaks()
     tf32 = None
     if prec == g.RMAT_C64_3XF16_IR and not args.no_tf32:
-        # the FP32-class 3xTF32 split on the same system (spec precision)
+        # the FP32-class 3xTF32 split on the same system (the FP32 factorisation of the method)
         rt = Runner(p, g.RMAT_C64_3XTF32_IR, local, residual=resid)
         rt.step()
         g.rmat_set_param(rt.ctx, g.RMAT_PARAM_TIMING, 1)
