@@ -138,7 +138,9 @@ def stage_rooflines(stats, N, nch, nb, iters, pk, src):
                         "us_per_column": ms * 1e3 / N,
                         "hbm_gbs": 16.0 * N * N / 2 / (ms * 1e-3) / 1e9,
                         "note": "one grid-wide pivot search per column; bytes = each panel read "
-                                "and written once (8 N^2 in total), far below the HBM roof"}
+                                "and written once (8 N^2 in total), far below the HBM roof; with "
+                                "the factorisation's look-ahead part of this time runs beside the "
+                                "far updates (32-column sub-panels, counted as launches here)"}
     solves = 1 + int(iters)
     ms = stats.get("solve_tc_ms")
     if ms and ms > 0:
